@@ -1,0 +1,430 @@
+/*
+ * Plain FP64 CPU oracle for the pipelined Krylov solvers of Rupp, Weinbub, Juengel and
+ * Grasser, "Pipelined Iterative Solvers with Kernel Fusion for Graphics Processing Units"
+ * (ACM TOMS 2015, arXiv:1410.4054).
+ *
+ * TEST INFRASTRUCTURE ONLY.  Nothing on the product path links, loads or calls this file:
+ * only the test suite, the smoke check and the CPU-baseline leg of the benchmark do.  It
+ * shares no code, header, table or helper with the CUDA library.
+ *
+ * Everything is sequential, left-to-right FP64 in natural row order, following the
+ * algorithms step by step:
+ *   orc_cg_classical        Algorithm 1 (classical CG)
+ *   orc_cg_pipelined        Algorithm 2 (pipelined CG, beta from Eq. (3))
+ *   orc_bicgstab_classical  Algorithm 3 (classical BiCGStab)
+ *   orc_bicgstab_pipelined  Algorithm 4 (pipelined BiCGStab, beta = -<As,r0*>/<Ap,r0*>,
+ *                           residual-norm expansion of Sec. 3.2)
+ *   orc_gmres               Algorithms 5 and 6 (restarted simpler GMRES with classical
+ *                           Gram-Schmidt; classical form updates the residual, pipelined
+ *                           form uses xi_i = <v_0, v_i>)
+ *
+ * Readings of points the paper leaves open (they are listed with reasons in the design
+ * notes of the repository):
+ *   - r0* = r0 (Alg. 3/4 "choose r0* arbitrary").
+ *   - Stop when ||r||_2 <= tol * ||b||_2; b = 0 gives x = 0 after zero iterations.
+ *   - CG: the squared residual <r_i, r_i> that the update step produces is tested before
+ *     A p_i is formed; "iterations" counts updates of x.  <p, Ap> <= 0 -> NOT_SPD.
+ *   - BiCGStab: ||s|| <= tol ||b|| ends the iteration after x += alpha p (standard early
+ *     exit); otherwise the iteration completes and the directly computed <r_{i+1}, r_{i+1}>
+ *     is tested.  The pipelined form also records the Sec. 3.2 expansion
+ *     <s,s> - 2 omega <s,As> + omega^2 <As,As>.  A zero or non-finite denominator is a
+ *     BREAKDOWN.
+ *   - GMRES: R_{i,i} = ||v_i|| before normalisation; the update is
+ *     x <- x0 + rho0 (eta_1 v_0 + sum_{i=2..k} eta_i v_{i-1}) with R eta = xi.
+ *     Within a cycle the residual estimate rho0 sqrt(max(0, 1 - sum xi_j^2)) (pipelined)
+ *     or rho0 ||r|| (classical) ends the cycle when <= tol ||b||, when the squared relative
+ *     estimate is <= 1e-14, at k = m, or when the iteration budget is spent.  Convergence is
+ *     declared only from the true residual b - A x at a cycle boundary.  maxit counts
+ *     Arnoldi steps over all cycles.  R_{i,i} <= 1e-14 ||A v_{i-1}|| ends the cycle before
+ *     step i (lucky breakdown).
+ */
+#include <math.h>
+#include <stdint.h>
+#include <stdlib.h>
+#include <string.h>
+
+/* status codes of the oracle */
+enum { ORC_OK = 0, ORC_NOT_CONVERGED = 4, ORC_BREAKDOWN = 5, ORC_NOT_SPD = 6, ORC_NAN = 7,
+       ORC_ERR_ARG = 1, ORC_ERR_OOM = 3 };
+
+/* ---------------------------------------------------------------- basic operations */
+
+/* y = A x, row by row, each row summed left to right (Sec. 2.2 CSR product). */
+void orc_spmv(int32_t n, const int32_t* rp, const int32_t* ci, const double* va,
+              const double* x, double* y) {
+  for (int32_t i = 0; i < n; ++i) {
+    double s = 0.0;
+    for (int32_t j = rp[i]; j < rp[i + 1]; ++j) s += va[j] * x[ci[j]];
+    y[i] = s;
+  }
+}
+
+/* <x, y> summed left to right. */
+double orc_dot(int32_t n, const double* x, const double* y) {
+  double s = 0.0;
+  for (int32_t i = 0; i < n; ++i) s += x[i] * y[i];
+  return s;
+}
+
+static void record(double* tr, int32_t cap, int32_t k, double v) {
+  if (tr && k >= 0 && k < cap) tr[k] = v;
+}
+
+static int finite3(double a, double b, double c) { return isfinite(a) && isfinite(b) && isfinite(c); }
+
+/* ---------------------------------------------------------------- CG, Algorithm 1 */
+
+int orc_cg_classical(int32_t n, const int32_t* rp, const int32_t* ci, const double* va,
+                     const double* b, double* x, double tol, int32_t maxit, int32_t cap,
+                     double* tr_alpha, double* tr_beta, double* tr_res2, int32_t* iters_out) {
+  *iters_out = 0;
+  if (n <= 0) return ORC_OK;
+  double bb = orc_dot(n, b, b);
+  if (bb == 0.0) { memset(x, 0, sizeof(double) * (size_t)n); return ORC_OK; }
+  double thr2 = tol * tol * bb;
+  double *r = malloc(sizeof(double) * (size_t)n), *p = malloc(sizeof(double) * (size_t)n),
+         *ap = malloc(sizeof(double) * (size_t)n);
+  if (!r || !p || !ap) { free(r); free(p); free(ap); return ORC_ERR_OOM; }
+  int status = ORC_NOT_CONVERGED;
+  /* p0 = r0 = b - A x0 */
+  orc_spmv(n, rp, ci, va, x, ap);
+  for (int32_t k = 0; k < n; ++k) { r[k] = b[k] - ap[k]; p[k] = r[k]; }
+  double rr = orc_dot(n, r, r);
+  if (!isfinite(rr)) { status = ORC_NAN; goto done; }
+  if (rr <= thr2) { status = ORC_OK; goto done; }
+  for (int32_t i = 0; i < maxit; ++i) {
+    orc_spmv(n, rp, ci, va, p, ap);              /* A p_i */
+    double pap = orc_dot(n, p, ap);              /* <p_i, A p_i> */
+    if (!isfinite(pap)) { status = ORC_NAN; break; }
+    if (pap <= 0.0) { status = ORC_NOT_SPD; break; }
+    double alpha = rr / pap;
+    for (int32_t k = 0; k < n; ++k) x[k] += alpha * p[k];
+    for (int32_t k = 0; k < n; ++k) r[k] -= alpha * ap[k];
+    double rr_new = orc_dot(n, r, r);            /* <r_{i+1}, r_{i+1}> */
+    record(tr_alpha, cap, i, alpha);
+    record(tr_res2, cap, i, rr_new);
+    *iters_out = i + 1;
+    if (!isfinite(rr_new)) { status = ORC_NAN; break; }
+    if (rr_new <= thr2) { status = ORC_OK; break; }
+    double beta = rr_new / rr;
+    record(tr_beta, cap, i, beta);
+    for (int32_t k = 0; k < n; ++k) p[k] = r[k] + beta * p[k];
+    rr = rr_new;
+  }
+done:
+  free(r); free(p); free(ap);
+  return status;
+}
+
+/* ---------------------------------------------------------------- CG, Algorithm 2 */
+
+int orc_cg_pipelined(int32_t n, const int32_t* rp, const int32_t* ci, const double* va,
+                     const double* b, double* x, double tol, int32_t maxit, int32_t cap,
+                     double* tr_alpha, double* tr_beta, double* tr_res2, int32_t* iters_out) {
+  *iters_out = 0;
+  if (n <= 0) return ORC_OK;
+  double bb = orc_dot(n, b, b);
+  if (bb == 0.0) { memset(x, 0, sizeof(double) * (size_t)n); return ORC_OK; }
+  double thr2 = tol * tol * bb;
+  double *r = malloc(sizeof(double) * (size_t)n), *p = malloc(sizeof(double) * (size_t)n),
+         *ap = malloc(sizeof(double) * (size_t)n);
+  if (!r || !p || !ap) { free(r); free(p); free(ap); return ORC_ERR_OOM; }
+  int status = ORC_NOT_CONVERGED;
+  /* p0 = r0 = b - A x0 */
+  orc_spmv(n, rp, ci, va, x, ap);
+  for (int32_t k = 0; k < n; ++k) { r[k] = b[k] - ap[k]; p[k] = r[k]; }
+  double rr = orc_dot(n, r, r);
+  if (!isfinite(rr)) { status = ORC_NAN; goto done; }
+  if (rr <= thr2) { status = ORC_OK; goto done; }
+  /* A p0, alpha_0 = <r0,r0>/<p0,Ap0>, beta_0 = alpha_0^2 <Ap0,Ap0>/<r0,r0> - 1 */
+  orc_spmv(n, rp, ci, va, p, ap);
+  double apap = orc_dot(n, ap, ap);
+  double pap = orc_dot(n, p, ap);
+  if (!finite3(apap, pap, rr)) { status = ORC_NAN; goto done; }
+  if (pap <= 0.0) { status = ORC_NOT_SPD; goto done; }
+  double alpha = rr / pap;
+  double beta = alpha * alpha * apap / rr - 1.0;
+  record(tr_alpha, cap, 0, alpha);
+  record(tr_beta, cap, 0, beta);
+  for (int32_t i = 1; i <= maxit; ++i) {
+    /* x_i, r_i, p_i from alpha_{i-1}, beta_{i-1} */
+    for (int32_t k = 0; k < n; ++k) x[k] += alpha * p[k];
+    for (int32_t k = 0; k < n; ++k) r[k] -= alpha * ap[k];
+    for (int32_t k = 0; k < n; ++k) p[k] = r[k] + beta * p[k];
+    rr = orc_dot(n, r, r);                        /* <r_i, r_i> */
+    record(tr_res2, cap, i - 1, rr);
+    *iters_out = i;
+    if (!isfinite(rr)) { status = ORC_NAN; break; }
+    if (rr <= thr2) { status = ORC_OK; break; }
+    if (i == maxit) break;
+    orc_spmv(n, rp, ci, va, p, ap);               /* A p_i */
+    apap = orc_dot(n, ap, ap);                    /* <Ap_i, Ap_i> */
+    pap = orc_dot(n, p, ap);                      /* <p_i, Ap_i> */
+    if (!finite3(apap, pap, rr)) { status = ORC_NAN; break; }
+    if (pap <= 0.0) { status = ORC_NOT_SPD; break; }
+    alpha = rr / pap;
+    beta = alpha * alpha * apap / rr - 1.0;       /* Eq. (3) */
+    record(tr_alpha, cap, i, alpha);
+    record(tr_beta, cap, i, beta);
+  }
+done:
+  free(r); free(p); free(ap);
+  return status;
+}
+
+/* ---------------------------------------------------------------- BiCGStab, Algorithm 3 */
+
+int orc_bicgstab_classical(int32_t n, const int32_t* rp, const int32_t* ci, const double* va,
+                           const double* b, double* x, double tol, int32_t maxit, int32_t cap,
+                           double* tr_alpha, double* tr_beta, double* tr_omega, double* tr_res2,
+                           int32_t* iters_out) {
+  *iters_out = 0;
+  if (n <= 0) return ORC_OK;
+  double bb = orc_dot(n, b, b);
+  if (bb == 0.0) { memset(x, 0, sizeof(double) * (size_t)n); return ORC_OK; }
+  double thr2 = tol * tol * bb;
+  size_t sz = sizeof(double) * (size_t)n;
+  double *r = malloc(sz), *p = malloc(sz), *ap = malloc(sz), *s = malloc(sz), *as = malloc(sz),
+         *r0s = malloc(sz);
+  if (!r || !p || !ap || !s || !as || !r0s) {
+    free(r); free(p); free(ap); free(s); free(as); free(r0s); return ORC_ERR_OOM;
+  }
+  int status = ORC_NOT_CONVERGED;
+  orc_spmv(n, rp, ci, va, x, ap);
+  for (int32_t k = 0; k < n; ++k) { r[k] = b[k] - ap[k]; p[k] = r[k]; r0s[k] = r[k]; }
+  double rr = orc_dot(n, r, r);
+  double rr0s = orc_dot(n, r, r0s);                    /* <r0, r0*> */
+  if (!isfinite(rr)) { status = ORC_NAN; goto done; }
+  if (rr <= thr2) { status = ORC_OK; goto done; }
+  for (int32_t i = 0; i < maxit; ++i) {
+    orc_spmv(n, rp, ci, va, p, ap);                    /* A p_i */
+    double apr0s = orc_dot(n, ap, r0s);                /* <Ap_i, r0*> */
+    if (!isfinite(apr0s)) { status = ORC_NAN; break; }
+    if (apr0s == 0.0 || rr0s == 0.0) { status = ORC_BREAKDOWN; break; }
+    double alpha = rr0s / apr0s;
+    for (int32_t k = 0; k < n; ++k) s[k] = r[k] - alpha * ap[k];
+    record(tr_alpha, cap, i, alpha);
+    double ss = orc_dot(n, s, s);
+    if (!isfinite(ss)) { status = ORC_NAN; break; }
+    if (ss <= thr2) {                                  /* early exit on a small s */
+      for (int32_t k = 0; k < n; ++k) x[k] += alpha * p[k];
+      record(tr_res2, cap, i, ss);
+      *iters_out = i + 1; status = ORC_OK; break;
+    }
+    orc_spmv(n, rp, ci, va, s, as);                    /* A s_i */
+    double ass = orc_dot(n, as, s);
+    double asas = orc_dot(n, as, as);
+    if (!finite3(ass, asas, 0.0)) { status = ORC_NAN; break; }
+    if (asas == 0.0) { status = ORC_BREAKDOWN; break; }
+    double omega = ass / asas;
+    record(tr_omega, cap, i, omega);
+    for (int32_t k = 0; k < n; ++k) x[k] += alpha * p[k] + omega * s[k];
+    for (int32_t k = 0; k < n; ++k) r[k] = s[k] - omega * as[k];
+    double rr0s_new = orc_dot(n, r, r0s);              /* <r_{i+1}, r0*> */
+    if (omega == 0.0) { status = ORC_BREAKDOWN; *iters_out = i + 1; break; }
+    double beta = (rr0s_new / rr0s) * (alpha / omega);
+    record(tr_beta, cap, i, beta);
+    for (int32_t k = 0; k < n; ++k) p[k] = r[k] + beta * (p[k] - omega * ap[k]);
+    rr0s = rr0s_new;
+    rr = orc_dot(n, r, r);                             /* explicit residual norm */
+    record(tr_res2, cap, i, rr);
+    *iters_out = i + 1;
+    if (!finite3(rr, beta, rr0s)) { status = ORC_NAN; break; }
+    if (rr <= thr2) { status = ORC_OK; break; }
+  }
+done:
+  free(r); free(p); free(ap); free(s); free(as); free(r0s);
+  return status;
+}
+
+/* ---------------------------------------------------------------- BiCGStab, Algorithm 4 */
+
+int orc_bicgstab_pipelined(int32_t n, const int32_t* rp, const int32_t* ci, const double* va,
+                           const double* b, double* x, double tol, int32_t maxit, int32_t cap,
+                           double* tr_alpha, double* tr_beta, double* tr_omega, double* tr_res2,
+                           double* tr_res2_est, int32_t* iters_out) {
+  *iters_out = 0;
+  if (n <= 0) return ORC_OK;
+  double bb = orc_dot(n, b, b);
+  if (bb == 0.0) { memset(x, 0, sizeof(double) * (size_t)n); return ORC_OK; }
+  double thr2 = tol * tol * bb;
+  size_t sz = sizeof(double) * (size_t)n;
+  double *r = malloc(sz), *p = malloc(sz), *ap = malloc(sz), *s = malloc(sz), *as = malloc(sz),
+         *r0s = malloc(sz);
+  if (!r || !p || !ap || !s || !as || !r0s) {
+    free(r); free(p); free(ap); free(s); free(as); free(r0s); return ORC_ERR_OOM;
+  }
+  int status = ORC_NOT_CONVERGED;
+  orc_spmv(n, rp, ci, va, x, ap);
+  for (int32_t k = 0; k < n; ++k) { r[k] = b[k] - ap[k]; p[k] = r[k]; r0s[k] = r[k]; }
+  double rr = orc_dot(n, r, r);
+  double rr0s = orc_dot(n, r, r0s);
+  if (!isfinite(rr)) { status = ORC_NAN; goto done; }
+  if (rr <= thr2) { status = ORC_OK; goto done; }
+  for (int32_t i = 0; i < maxit; ++i) {
+    /* A p_i and <Ap_i, r0*> -> alpha_i */
+    orc_spmv(n, rp, ci, va, p, ap);
+    double apr0s = orc_dot(n, ap, r0s);
+    if (!isfinite(apr0s)) { status = ORC_NAN; break; }
+    if (apr0s == 0.0 || rr0s == 0.0) { status = ORC_BREAKDOWN; break; }
+    double alpha = rr0s / apr0s;
+    record(tr_alpha, cap, i, alpha);
+    /* s_i = r_i - alpha_i A p_i and <s_i, s_i> */
+    for (int32_t k = 0; k < n; ++k) s[k] = r[k] - alpha * ap[k];
+    double ss = orc_dot(n, s, s);
+    if (!isfinite(ss)) { status = ORC_NAN; break; }
+    if (ss <= thr2) {
+      for (int32_t k = 0; k < n; ++k) x[k] += alpha * p[k];
+      record(tr_res2, cap, i, ss);
+      *iters_out = i + 1; status = ORC_OK; break;
+    }
+    /* A s_i and <As_i, s_i>, <As_i, As_i>, <As_i, r0*> -> omega_i, beta_i */
+    orc_spmv(n, rp, ci, va, s, as);
+    double ass = orc_dot(n, as, s);
+    double asas = orc_dot(n, as, as);
+    double asr0s = orc_dot(n, as, r0s);
+    if (!finite3(ass, asas, asr0s)) { status = ORC_NAN; break; }
+    if (asas == 0.0) { status = ORC_BREAKDOWN; break; }
+    double beta = -asr0s / apr0s;
+    double omega = ass / asas;
+    double est = ss - 2.0 * omega * ass + omega * omega * asas;   /* Sec. 3.2 expansion */
+    if (est < 0.0) est = 0.0;
+    record(tr_beta, cap, i, beta);
+    record(tr_omega, cap, i, omega);
+    record(tr_res2_est, cap, i, est);
+    /* x_{i+1}, r_{i+1}, p_{i+1} and <r_{i+1}, r0*> (plus <r_{i+1}, r_{i+1}> for the test) */
+    for (int32_t k = 0; k < n; ++k) x[k] += alpha * p[k] + omega * s[k];
+    for (int32_t k = 0; k < n; ++k) r[k] = s[k] - omega * as[k];
+    for (int32_t k = 0; k < n; ++k) p[k] = r[k] + beta * (p[k] - omega * ap[k]);
+    rr0s = orc_dot(n, r, r0s);
+    rr = orc_dot(n, r, r);
+    record(tr_res2, cap, i, rr);
+    *iters_out = i + 1;
+    if (!finite3(rr, rr0s, omega)) { status = ORC_NAN; break; }
+    if (rr <= thr2) { status = ORC_OK; break; }
+  }
+done:
+  free(r); free(p); free(ap); free(s); free(as); free(r0s);
+  return status;
+}
+
+/* ---------------------------------------------------------------- GMRES(m), Alg. 5 / 6 */
+
+/*
+ * pipelined = 1: Algorithm 6 (xi_i = <v_0, v_i>, no residual update);
+ * pipelined = 0: Algorithm 5 (xi_i = <r, v_i>, r <- r - xi_i v_i, monitor rho0 ||r||).
+ * tr_R (m*m, row-major R[j-1][i-1]) and tr_xi (m) receive the first cycle's values;
+ * tr_est (cap) the per-step residual estimate; tr_res (cap) the true residual norm at
+ * every cycle boundary (index = cycle).
+ */
+int orc_gmres(int32_t n, const int32_t* rp, const int32_t* ci, const double* va,
+              const double* b, double* x, double tol, int32_t maxit, int32_t m, int32_t pipelined,
+              int32_t cap, double* tr_R, double* tr_xi, double* tr_est, double* tr_res,
+              int32_t* iters_out, int32_t* cycles_out) {
+  *iters_out = 0;
+  if (cycles_out) *cycles_out = 0;
+  if (n <= 0) return ORC_OK;
+  if (m < 1) return ORC_ERR_ARG;
+  double bb = orc_dot(n, b, b);
+  if (bb == 0.0) { memset(x, 0, sizeof(double) * (size_t)n); return ORC_OK; }
+  double bnorm = sqrt(bb);
+  size_t sz = sizeof(double) * (size_t)n;
+  double* V = malloc(sz * (size_t)(m + 1));          /* v_0 .. v_m, each length n */
+  double* r = malloc(sz);
+  double* acc = malloc(sz);
+  double* R = calloc((size_t)(m + 1) * (size_t)(m + 1), sizeof(double)); /* R[j][i], 1-based */
+  double* xi = calloc((size_t)(m + 1), sizeof(double));
+  double* eta = calloc((size_t)(m + 1), sizeof(double));
+  if (!V || !r || !acc || !R || !xi || !eta) {
+    free(V); free(r); free(acc); free(R); free(xi); free(eta); return ORC_ERR_OOM;
+  }
+#define VEC(i) (V + (size_t)(i) * (size_t)n)
+#define RR(j, i) R[(size_t)(j) * (size_t)(m + 1) + (size_t)(i)]
+  int status = ORC_NOT_CONVERGED;
+  int32_t total = 0, cycle = 0, est_k = 0;
+  for (;;) {
+    /* r0 = b - A x0, rho0 = ||r0|| (true residual at the cycle boundary) */
+    orc_spmv(n, rp, ci, va, x, r);
+    for (int32_t k = 0; k < n; ++k) r[k] = b[k] - r[k];
+    double rho0 = sqrt(orc_dot(n, r, r));
+    record(tr_res, cap, cycle, rho0);
+    if (!isfinite(rho0)) { status = ORC_NAN; break; }
+    if (rho0 <= tol * bnorm) { status = ORC_OK; break; }
+    if (total >= maxit) { status = ORC_NOT_CONVERGED; break; }
+    /* v_0 = r = r0 / rho0 */
+    for (int32_t k = 0; k < n; ++k) { VEC(0)[k] = r[k] / rho0; r[k] = VEC(0)[k]; }
+    memset(R, 0, sizeof(double) * (size_t)(m + 1) * (size_t)(m + 1));
+    double sumxi2 = 0.0;
+    int32_t kdone = 0;
+    int broke = 0;
+    for (int32_t i = 1; i <= m; ++i) {
+      if (total >= maxit) break;
+      double* vi = VEC(i);
+      orc_spmv(n, rp, ci, va, VEC(i - 1), vi);         /* v_i = A v_{i-1} */
+      for (int32_t j = 1; j <= i - 1; ++j) RR(j, i) = orc_dot(n, VEC(j), vi); /* CGS */
+      for (int32_t j = 1; j <= i - 1; ++j) {
+        double rji = RR(j, i);
+        const double* vj = VEC(j);
+        for (int32_t k = 0; k < n; ++k) vi[k] -= rji * vj[k];
+      }
+      double nrm2 = orc_dot(n, vi, vi);
+      double rii = sqrt(nrm2);
+      double col2 = nrm2;                               /* ||A v_{i-1}||^2 = sum R_{j,i}^2 */
+      for (int32_t j = 1; j <= i - 1; ++j) col2 += RR(j, i) * RR(j, i);
+      if (!isfinite(rii)) { status = ORC_NAN; broke = 2; break; }
+      if (rii == 0.0 || rii <= 1e-14 * sqrt(col2)) { broke = 1; break; }  /* lucky breakdown */
+      RR(i, i) = rii;
+      for (int32_t k = 0; k < n; ++k) vi[k] /= rii;
+      double xii;
+      if (pipelined) {
+        xii = orc_dot(n, VEC(0), vi);                   /* xi_i = <v_0, v_i> */
+      } else {
+        xii = orc_dot(n, r, vi);                        /* xi_i = <r, v_i> */
+        for (int32_t k = 0; k < n; ++k) r[k] -= xii * vi[k];
+      }
+      xi[i] = xii;
+      total++;
+      kdone = i;
+      double rel2;
+      if (pipelined) {
+        sumxi2 += xii * xii;
+        rel2 = 1.0 - sumxi2;
+      } else {
+        rel2 = orc_dot(n, r, r);
+      }
+      if (rel2 < 0.0) rel2 = 0.0;
+      double est = rho0 * sqrt(rel2);
+      record(tr_est, cap, est_k++, est);
+      if (est <= tol * bnorm || rel2 <= 1e-14) break;
+    }
+    if (cycle == 0) {
+      if (tr_R)
+        for (int32_t j = 1; j <= m; ++j)
+          for (int32_t i = 1; i <= m; ++i) tr_R[(size_t)(j - 1) * m + (i - 1)] = RR(j, i);
+      if (tr_xi)
+        for (int32_t i = 1; i <= m; ++i) tr_xi[i - 1] = xi[i];
+    }
+    if (broke == 2) break;
+    if (kdone == 0) { status = ORC_BREAKDOWN; break; }
+    /* solve R eta = xi (upper triangular, k x k) by back-substitution */
+    for (int32_t i = kdone; i >= 1; --i) {
+      double s = xi[i];
+      for (int32_t j = i + 1; j <= kdone; ++j) s -= RR(i, j) * eta[j];
+      eta[i] = s / RR(i, i);
+    }
+    /* x <- x0 + rho0 (eta_1 v_0 + sum_{i=2..k} eta_i v_{i-1}) */
+    for (int32_t k = 0; k < n; ++k) {
+      double a = 0.0;
+      for (int32_t i = 1; i <= kdone; ++i) a += eta[i] * VEC(i - 1)[k];
+      x[k] += rho0 * a;
+    }
+    cycle++;
+    (void)broke;
+  }
+#undef VEC
+#undef RR
+  *iters_out = total;
+  if (cycles_out) *cycles_out = cycle;
+  free(V); free(r); free(acc); free(R); free(xi); free(eta);
+  return status;
+}

@@ -1,0 +1,252 @@
+"""Seeded synthetic inputs shared by the CUDA path, its tests and the oracle.
+
+This module only *builds inputs*: sparse matrices in CSR form (int32 row pointers
+and column indices, float64 values), exact solutions x* and right-hand sides
+b = A x*.  It contains none of the solvers' arithmetic.  Both the CUDA path and
+the CPU oracle receive the very same arrays from here, so neither draws random
+numbers of its own.
+
+Shapes follow the paper's workloads (Section 4): 2D/3D Poisson-type stencils
+(the finite-element Poisson benchmark of Sec. 4.1 and the 3D elasticity
+benchmark of Sec. 4.2 have about 7 nonzeros per row), nonsymmetric
+convection-diffusion operators, and power-law random matrices standing in for the
+nonsymmetric SuiteSparse matrices of Table 1 (3.8 to 98 nonzeros per row), plus
+uniform random matrices with 4 and 28 nonzeros per row for the fused
+SpMV + inner product experiment of Sec. 2.2.
+
+x* uses splitmix64 (Steele, Lea, Flood, "Fast splittable pseudorandom number
+generators", OOPSLA 2014) evaluated at counter i, mapped to uniform[-1, 1).
+"""
+from __future__ import annotations
+
+from dataclasses import dataclass
+
+import numpy as np
+
+_GOLDEN = np.uint64(0x9E3779B97F4A7C15)
+_M1 = np.uint64(0xBF58476D1CE4E5B9)
+_M2 = np.uint64(0x94D049BB133111EB)
+
+
+def splitmix64(seed: int, count: int) -> np.ndarray:
+    """Outputs 0..count-1 of splitmix64 started at ``seed`` (uint64 array)."""
+    with np.errstate(over="ignore"):
+        i = np.arange(1, count + 1, dtype=np.uint64)
+        z = np.uint64(seed & 0xFFFFFFFFFFFFFFFF) + i * _GOLDEN
+        z = (z ^ (z >> np.uint64(30))) * _M1
+        z = (z ^ (z >> np.uint64(27))) * _M2
+        z = z ^ (z >> np.uint64(31))
+    return z
+
+
+def uniform_pm1(seed: int, count: int) -> np.ndarray:
+    """uniform[-1, 1) doubles: (u >> 11) * 2^-53 * 2 - 1 with u = splitmix64 output."""
+    u = splitmix64(seed, count) >> np.uint64(11)
+    return u.astype(np.float64) * (2.0 ** -53) * 2.0 - 1.0
+
+
+@dataclass
+class CSR:
+    """A square sparse matrix in CSR form (row_ptr int32[n+1], col int32[nnz], val f64[nnz])."""
+
+    n: int
+    row_ptr: np.ndarray
+    col: np.ndarray
+    val: np.ndarray
+    name: str = ""
+
+    @property
+    def nnz(self) -> int:
+        return int(self.row_ptr[-1])
+
+    def matvec(self, x: np.ndarray) -> np.ndarray:
+        """y = A x through scipy's CSR kernel (used only to manufacture right-hand sides)."""
+        import scipy.sparse as sp
+
+        a = sp.csr_matrix((self.val, self.col, self.row_ptr), shape=(self.n, self.n))
+        return a @ x
+
+    def to_dense(self) -> np.ndarray:
+        d = np.zeros((self.n, self.n))
+        for i in range(self.n):
+            for j in range(self.row_ptr[i], self.row_ptr[i + 1]):
+                d[i, self.col[j]] += self.val[j]
+        return d
+
+
+def _from_coo(n: int, rows: np.ndarray, cols: np.ndarray, vals: np.ndarray, name: str) -> CSR:
+    order = np.lexsort((cols, rows))
+    rows, cols, vals = rows[order], cols[order], vals[order]
+    counts = np.bincount(rows, minlength=n)
+    row_ptr = np.zeros(n + 1, dtype=np.int64)
+    np.cumsum(counts, out=row_ptr[1:])
+    assert row_ptr[-1] < 2**31
+    return CSR(n, row_ptr.astype(np.int32), cols.astype(np.int32), vals.astype(np.float64), name)
+
+
+def _stencil(shape: tuple, diag: float, lower: float, upper: float, name: str, shift=None) -> CSR:
+    """Grid stencil on a lexicographically ordered grid (last axis fastest).
+
+    Each row couples to its 2*d axis neighbours inside the grid (Dirichlet: neighbours
+    outside are dropped); ``lower`` is the coefficient of the neighbour at index-1 along
+    an axis, ``upper`` that at index+1.  ``shift`` (scalar) is added to the diagonal.
+    """
+    shape = tuple(int(s) for s in shape)
+    n = int(np.prod(shape))
+    idx = np.arange(n, dtype=np.int64).reshape(shape)
+    rows = [idx.ravel()]
+    cols = [idx.ravel()]
+    d = diag + (0.0 if shift is None else shift)
+    vals = [np.full(n, d)]
+    for ax in range(len(shape)):
+        lo = [slice(None)] * len(shape)
+        hi = [slice(None)] * len(shape)
+        lo[ax] = slice(1, None)
+        hi[ax] = slice(0, -1)
+        r = idx[tuple(lo)].ravel()
+        c = idx[tuple(hi)].ravel()
+        rows += [r, c]
+        cols += [c, r]
+        vals += [np.full(r.size, lower), np.full(r.size, upper)]
+    return _from_coo(n, np.concatenate(rows), np.concatenate(cols), np.concatenate(vals), name)
+
+
+def laplace_2d(k: int, ky: int | None = None, shift: float = 0.0) -> CSR:
+    """5-point Laplacian (diag 4 [+shift], neighbours -1) on a ky x k grid, Dirichlet."""
+    ky = k if ky is None else ky
+    return _stencil((ky, k), 4.0, -1.0, -1.0, f"lap2d_{ky}x{k}", shift)
+
+
+def laplace_3d(k: int) -> CSR:
+    """7-point Laplacian (diag 6, neighbours -1) on a k^3 grid, Dirichlet."""
+    return _stencil((k, k, k), 6.0, -1.0, -1.0, f"lap3d_{k}")
+
+
+def convdiff_3d(k: int, peclet: float = 0.5) -> CSR:
+    """First-order upwind convection-diffusion, velocity (1,1,1), cell Peclet ``peclet``.
+
+    Scaled by h^2/D: diffusion gives 6 / -1; upwind convection adds 2*Pe per axis to the
+    diagonal and -2*Pe to the upstream (index-1) neighbour.  Pe = 0.5: diag 9, upstream -2,
+    downstream -1.
+    """
+    c = 2.0 * peclet
+    return _stencil((k, k, k), 6.0 + 3.0 * c, -1.0 - c, -1.0, f"convdiff3d_{k}")
+
+
+def _power_law_pmf(lmin: int, lmax: int, mean: float) -> np.ndarray:
+    lengths = np.arange(lmin, lmax + 1, dtype=np.float64)
+
+    def mean_for(a):
+        w = lengths ** (-a)
+        return float((w * lengths).sum() / w.sum())
+
+    lo, hi = 0.0, 10.0  # mean_for is decreasing in a
+    for _ in range(200):
+        mid = 0.5 * (lo + hi)
+        if mean_for(mid) > mean:
+            lo = mid
+        else:
+            hi = mid
+    w = lengths ** (-0.5 * (lo + hi))
+    return w / w.sum()
+
+
+def power_law(n: int, seed: int = 0, lmin: int = 3, lmax: int = 256, mean: float = 12.0) -> CSR:
+    """Random nonsymmetric matrix with power-law row lengths.
+
+    Row length L (diagonal included) ~ P(L) proportional to L^-a on [lmin, lmax], with a set
+    by bisection so that E[L] = mean.  The L-1 off-diagonal columns are distinct and uniform
+    over the other columns; off-diagonal values are N(0,1); the diagonal is 1.1 times the
+    row's absolute off-diagonal sum (strict diagonal dominance).
+    """
+    rng = np.random.default_rng(seed)
+    pmf = _power_law_pmf(lmin, lmax, mean)
+    lengths = rng.choice(np.arange(lmin, lmax + 1), size=n, p=pmf).astype(np.int64)
+    lengths = np.minimum(lengths, n)
+    noff = lengths - 1
+    total = int(noff.sum())
+    rows = np.repeat(np.arange(n, dtype=np.int64), noff)
+    # draw columns from the n-1 "other" columns, then redraw duplicates within a row
+    cols = rng.integers(0, n - 1, size=total, dtype=np.int64)
+    for _ in range(64):
+        key = rows * n + cols
+        order = np.argsort(key, kind="stable")
+        dup = np.zeros(total, dtype=bool)
+        sk = key[order]
+        dup[order[1:]] = sk[1:] == sk[:-1]
+        if not dup.any():
+            break
+        cols[dup] = rng.integers(0, n - 1, size=int(dup.sum()), dtype=np.int64)
+    cols = np.where(cols >= rows, cols + 1, cols)  # skip the diagonal
+    vals = rng.standard_normal(total)
+    absum = np.bincount(rows, weights=np.abs(vals), minlength=n)
+    diag_rows = np.arange(n, dtype=np.int64)
+    return _from_coo(
+        n,
+        np.concatenate([rows, diag_rows]),
+        np.concatenate([cols, diag_rows]),
+        np.concatenate([vals, 1.1 * absum]),
+        f"powerlaw_{n}",
+    )
+
+
+def random_uniform(n: int, per_row: int, seed: int = 0) -> CSR:
+    """``per_row`` distinct uniformly random columns per row, diagonal included, values N(0,1)
+    and a dominant diagonal (the random matrices of the fused SpMV + dot experiment)."""
+    rng = np.random.default_rng(seed)
+    per_row = min(per_row, n)
+    rows = np.repeat(np.arange(n, dtype=np.int64), per_row - 1)
+    cols = rng.integers(0, n - 1, size=rows.size, dtype=np.int64)
+    for _ in range(64):
+        key = rows * n + cols
+        order = np.argsort(key, kind="stable")
+        sk = key[order]
+        dup = np.zeros(rows.size, dtype=bool)
+        dup[order[1:]] = sk[1:] == sk[:-1]
+        if not dup.any():
+            break
+        cols[dup] = rng.integers(0, n - 1, size=int(dup.sum()), dtype=np.int64)
+    cols = np.where(cols >= rows, cols + 1, cols)
+    vals = rng.standard_normal(rows.size)
+    absum = np.bincount(rows, weights=np.abs(vals), minlength=n)
+    d = np.arange(n, dtype=np.int64)
+    return _from_coo(n, np.concatenate([rows, d]), np.concatenate([cols, d]),
+                     np.concatenate([vals, 1.1 * absum + 1.0]), f"rand{per_row}_{n}")
+
+
+def spd_random(n: int, seed: int = 0, density: float = 0.3, cond_shift: float = 1.0) -> CSR:
+    """Small dense-ish SPD matrix: B^T B + shift I sparsified symmetrically (tiny tests only)."""
+    rng = np.random.default_rng(seed)
+    b = rng.standard_normal((n, n))
+    mask = rng.random((n, n)) < density
+    mask = mask | mask.T | np.eye(n, dtype=bool)
+    s = (b + b.T) * mask
+    s = s + np.diag(np.abs(s).sum(axis=1) + cond_shift)
+    r, c = np.nonzero(s)
+    return _from_coo(n, r, c, s[r, c], f"spd_{n}")
+
+
+def manufactured(a: CSR, seed: int = 0):
+    """x* uniform[-1,1) from splitmix64(seed), b = A x*, x0 = 0."""
+    xs = uniform_pm1(seed, a.n)
+    b = a.matvec(xs)
+    return xs, b, np.zeros(a.n)
+
+
+def batched_rectangles(nsys: int = 512, seed: int = 0, lo: int = 32, hi: int = 256):
+    """Uneven batch of shifted 2D Laplacians on a x b rectangles.
+
+    Sides a, b = round(exp(U[ln lo, ln hi])); diagonal shift sigma ~ U[0.01, 1].
+    Returns a list of CSR matrices.
+    """
+    rng = np.random.default_rng(seed)
+    sides = np.rint(np.exp(rng.uniform(np.log(lo), np.log(hi), size=(nsys, 2)))).astype(int)
+    shifts = rng.uniform(0.01, 1.0, size=nsys)
+    return [laplace_2d(int(s[0]), int(s[1]), float(sh)) for s, sh in zip(sides, shifts)]
+
+
+# Named configurations (sizes of the paper-shaped workloads)
+LAPLACE_3D_SWEEP = (16, 32, 64, 100, 160)
+LAPLACE_2D_SWEEP = (256, 1024, 2048)
+CONVDIFF_SWEEP = (32, 64, 128)
+POWER_LAW_SWEEP = (10_000, 100_000, 1_000_000)

@@ -1,0 +1,56 @@
+"""Plants plausible mistakes in the oracle (on the CPU) and checks the pins catch each one.
+
+Each mutant is a copy of oracle/pk_oracle.c with one edit (a flipped sign, a swapped
+operand, an off-by-one index, a dropped factor), compiled with gcc into a temporary
+library; the pin suite then runs against it in a subprocess and must fail.
+"""
+import os
+import subprocess
+import sys
+from pathlib import Path
+
+import pytest
+
+ROOT = Path(__file__).resolve().parents[1]
+SRC = (ROOT / "oracle" / "pk_oracle.c").read_text()
+
+MUTANTS = {
+    "cg_pipelined_beta_sign": ("alpha * alpha * apap / rr - 1.0", "alpha * alpha * apap / rr + 1.0"),
+    "cg_residual_sign": ("r[k] -= alpha * ap[k]", "r[k] += alpha * ap[k]"),
+    "cg_classical_beta_inverted": ("double beta = rr_new / rr;", "double beta = rr / rr_new;"),
+    "cg_pipelined_pap_operand": ("pap = orc_dot(n, p, ap);                      /* <p_i, Ap_i> */",
+                                 "pap = orc_dot(n, ap, ap);                     /* <p_i, Ap_i> */"),
+    "bicgstab_pipelined_beta_sign": ("double beta = -asr0s / apr0s;", "double beta = asr0s / apr0s;"),
+    "bicgstab_p_update_sign": ("beta * (p[k] - omega * ap[k])", "beta * (p[k] + omega * ap[k])"),
+    "bicgstab_omega_inverted": ("double omega = ass / asas;", "double omega = asas / ass;"),
+    "bicgstab_x_drops_omega_s": ("x[k] += alpha * p[k] + omega * s[k];", "x[k] += alpha * p[k];"),
+    "gmres_xi_wrong_vector": ("xii = orc_dot(n, VEC(0), vi);", "xii = orc_dot(n, VEC(1), vi);"),
+    "gmres_backsub_multiplies": ("eta[i] = s / RR(i, i);", "eta[i] = s * RR(i, i);"),
+    "gmres_cgs_includes_v0": [("for (int32_t j = 1; j <= i - 1; ++j) RR(j, i) = orc_dot",
+                               "for (int32_t j = 0; j <= i - 1; ++j) RR(j, i) = orc_dot"),
+                              ("for (int32_t j = 1; j <= i - 1; ++j) {\n        double rji",
+                               "for (int32_t j = 0; j <= i - 1; ++j) {\n        double rji")],
+    "gmres_update_index_shift": ("a += eta[i] * VEC(i - 1)[k];", "a += eta[i] * VEC(i)[k];"),
+    "gmres_update_drops_rho0": ("x[k] += rho0 * a;", "x[k] += a;"),
+    "spmv_transposed_gather": ("s += va[j] * x[ci[j]];", "s += va[j] * x[i];"),
+}
+
+
+@pytest.mark.parametrize("name", sorted(MUTANTS))
+def test_pins_catch_mutant(name, tmp_path):
+    edits = MUTANTS[name]
+    edits = edits if isinstance(edits, list) else [edits]
+    text = SRC
+    for old, new in edits:
+        assert old in text, f"mutation site vanished: {name}"
+        text = text.replace(old, new)
+    src = tmp_path / "mutant.c"
+    src.write_text(text)
+    so = tmp_path / "libmutant.so"
+    subprocess.run(["gcc", "-O2", "-std=c11", "-fPIC", "-shared", "-ffp-contract=off", "-o",
+                    str(so), str(src), "-lm"], check=True)
+    env = dict(os.environ, PK_ORACLE_LIB=str(so))
+    res = subprocess.run([sys.executable, "-m", "pytest", "-x", "-q", "-p", "no:cacheprovider",
+                          str(ROOT / "tests" / "test_oracle_pins.py")],
+                         cwd=ROOT, env=env, capture_output=True, text=True, timeout=300)
+    assert res.returncode != 0, f"mutant {name} survived the pins:\n{res.stdout[-2000:]}"
