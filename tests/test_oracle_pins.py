@@ -358,6 +358,18 @@ def test_gmres_edge_cases():
         assert r["status"] == O.NOT_CONVERGED and r["iters"] == 13 and r["cycles"] == 3
 
 
+def test_dot_is_compensated():
+    """orc_dot agrees with math.fsum (correctly rounded sum of the rounded products)."""
+    import math
+    for n in (10, 1000, 300_000):
+        x = W.uniform_pm1(11, n)
+        y = W.uniform_pm1(12, n)
+        for a_, b_ in ((x, y), (np.abs(x), np.abs(y))):
+            exact = math.fsum((a_ * b_).tolist())
+            bound = 2.3e-16 * abs(exact) + 1e-30 * float(np.sum(np.abs(a_ * b_)))
+            assert abs(O.dot(a_, b_) - exact) <= max(bound, 4.5e-16 * abs(exact))
+
+
 def test_spmv_and_dot_against_dense():
     a = W.power_law(300, seed=1)
     x = W.uniform_pm1(1, a.n)
