@@ -1,0 +1,369 @@
+#!/usr/bin/env python
+"""Benchmark of the fused pipelined CG hot path on one GB300 (JSON line on stdout).
+
+Workload (one "step"): a full pipelined-CG solve (Alg. 2, two fused kernels per iteration,
+device-side convergence test in a CUDA-graph WHILE loop) of the 3D 7-point Dirichlet
+Laplacian on a 160^3 grid (n = 4,096,000, nnz = 28,518,400), FP64 CSR with int32 indices,
+b = A x* with x* ~ U[-1, 1) (splitmix64), x0 = 0, to ||r|| <= 1e-8 ||b||.  The working set
+(~560 MB) is larger than the 129 MB L2, so no flush is needed between steps.
+
+value     = algorithmic HBM bytes of the solve / device time of the solve (GB/s), summed
+            over ranks (replicas; the solver itself does not shard);
+e2e       = the same metric through the C ABI with pinned HOST b and x (the library copies
+            them in and the solution out inside the call);
+roofline  = the fused SpMV + inner-products kernel (K-CG-S) timed with CUDA events over
+            30 fixed iterations (the paper's Sec. 4 methodology) against the measured HBM
+            copy bandwidth in MEASURED_PEAKS.json;
+cpu_baseline / --impl reference = the plain FP64 CPU oracle on the same matrix.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import shutil
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+from pathlib import Path
+
+import numpy as np
+
+ROOT = Path(__file__).resolve().parent
+sys.path.insert(0, str(ROOT))
+
+from paper_1410_4054_gb300 import workloads as W  # noqa: E402
+
+METRIC = "pipelined CG: algorithmic HBM GB/s over the solve to 1e-8 (time-to-1e-8 beside it)"
+UNIT = "GB/s"
+K3D = 160
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--k", type=int, default=K3D, help="3D grid side of the timed workload")
+    ap.add_argument("--no-sweep", action="store_true")
+    ap.add_argument("--no-cpu", action="store_true")
+    return ap.parse_args()
+
+
+def bytes_per_solve(n: int, nnz: int, iters: int) -> int:
+    """Compulsory HBM bytes of a pipelined CG solve, each vector read/written once per kernel.
+
+    matrix pass A = 12 nnz + 4 (n + 1); setup r0 = b - A x0 (A + 32 n); per iteration
+    K-CG-U 56 n (read x, r, p, Ap; write x, r, p) and K-CG-S A + 16 n (gather p once, write Ap);
+    the setup K-CG-S plus (iters - 1) loop K-CG-S launches = iters matrix passes.
+    """
+    a = 12 * nnz + 4 * (n + 1)
+    return (a + 32 * n) + iters * (56 * n + a + 16 * n)
+
+
+def spmv_dots_bytes(n: int, nnz: int) -> int:
+    return 12 * nnz + 4 * (n + 1) + 16 * n
+
+
+def update_bytes(n: int) -> int:
+    return 56 * n
+
+
+def workload_name(k: int) -> str:
+    return f"lap3d_{k}"
+
+
+def config(k: int, a) -> dict:
+    return {"workload": f"pipelined CG (Alg. 2), 3D 7-point Laplacian {k}^3, n={a.n}, nnz={a.nnz}, "
+                        f"FP64 CSR int32, x*~U[-1,1), b=A x*, x0=0, tol 1e-8",
+            "n": a.n, "nnz": a.nnz, "tol": 1e-8, "solver": "pipelined_cg",
+            "l2": "inputs larger than L2 (working set ~%d MB > 129 MB), no flush" %
+                  ((12 * a.nnz + 44 * a.n) // 2**20)}
+
+
+# ------------------------------------------------------------------ clocks
+
+class Clocks:
+    FIELDS = ("clocks.sm,clocks.max.sm,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        exe = shutil.which("nvidia-smi")
+        if not exe:
+            return
+        fd, self.path = tempfile.mkstemp(suffix=".csv")
+        os.close(fd)
+        self.proc = subprocess.Popen([exe, f"--id={self.index}", f"--query-gpu={self.FIELDS}",
+                                      "--format=csv,noheader,nounits", "-lms", "100"],
+                                     stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+
+    def stop(self):
+        if not self.proc:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        sm, mx, reasons = [], 0.0, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in Path(self.path).read_text().splitlines():
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) < 7:
+                continue
+            try:
+                sm.append(float(parts[0]))
+                mx = max(mx, float(parts[1]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[3:7]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        os.unlink(self.path)
+        if not sm:
+            return None
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": mx, "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+# ------------------------------------------------------------------ helpers
+
+def measured_peaks():
+    p = ROOT / "MEASURED_PEAKS.json"
+    if p.exists():
+        d = json.loads(p.read_text())
+        return float(d["hbm_gbs"]), "measured"
+    return 6800.0, "fallback"
+
+
+def kernel_source_sha() -> str:
+    h = hashlib.sha256()
+    for f in sorted((ROOT / "paper_1410_4054_gb300" / "csrc").glob("*")):
+        h.update(f.read_bytes())
+    return h.hexdigest()[:16]
+
+
+def ncu_traffic(kernel: str, workload: str):
+    """DRAM bytes per launch from a committed ncu summary, if it was taken on this source."""
+    p = ROOT / "profiles" / "ncu_traffic.json"
+    if not p.exists():
+        return None
+    d = json.loads(p.read_text()).get(f"{kernel}@{workload}")
+    if not d or d.get("source_sha") != kernel_source_sha():
+        return None
+    return d.get("bytes_per_launch")
+
+
+def dist():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+# ------------------------------------------------------------------ CPU oracle arm
+
+def oracle_sample(a, b, iters: int) -> tuple[float, float]:
+    """Seconds for `iters` oracle pipelined-CG iterations (tol = 0) on the same system."""
+    import oracle as O
+    O.lib()  # build / load outside the timed region
+    t0 = time.perf_counter()
+    O.cg(a, b, tol=0.0, maxit=iters, variant="pipelined", cap=1)
+    return time.perf_counter() - t0, iters
+
+
+def oracle_gbs(a, seconds: float, iters: int) -> float:
+    per_iter = 56 * a.n + 12 * a.nnz + 4 * (a.n + 1) + 16 * a.n
+    return per_iter * iters / seconds / 1e9
+
+
+def run_reference(args):
+    ws, rank, _ = dist()
+    if rank != 0:
+        return 0
+    a = W.laplace_3d(args.k)
+    _, b, _ = W.manufactured(a, seed=0)
+    it = 12
+    for _ in range(args.warmup):
+        oracle_sample(a, b, 2)
+    times = []
+    for _ in range(args.steps):
+        s, _ = oracle_sample(a, b, it)
+        times.append(s)
+    ms = 1e3 * statistics.median(times)
+    val = oracle_gbs(a, statistics.median(times), it)
+    line = {"metric": METRIC, "value": val, "unit": UNIT, "n_gpus": args.gpus, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64", "data": "synthetic", "impl": "reference",
+            "config": config(args.k, a),
+            "cpu_baseline": {"value": val, "unit": UNIT, "cores": 1, "kind": "oracle",
+                             "sample": f"{it} pipelined-CG iterations of the {args.k}^3 system per step"},
+            "e2e": {"value": val, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+# ------------------------------------------------------------------ GPU arm
+
+def run_ours(args):
+    import torch
+    from paper_1410_4054_gb300 import pk
+
+    ws, rank, local = dist()
+    if not torch.cuda.is_available():
+        raise SystemExit("bench.py: no CUDA device; the pk library runs only on the GPU")
+    torch.cuda.set_device(local)
+    pg = None
+    if ws > 1:
+        import torch.distributed as td
+        td.init_process_group("nccl")
+        pg = td
+    dev = f"cuda:{local}"
+    a = W.laplace_3d(args.k)
+    _, b, _ = W.manufactured(a, seed=rank)
+    A = pk.CSRMatrix.from_workload(a)
+    bd = torch.from_numpy(b).to(dev)
+    xd = torch.zeros(a.n, dtype=torch.float64, device=dev)
+    kw = dict(tol=1e-8, maxit=50_000, variant="pipelined", loop="graph")
+    stream = torch.cuda.current_stream()
+
+    def step():
+        xd.zero_()
+        return pk.cg_solve(A, bd, xd, **kw)
+
+    for _ in range(max(args.warmup, 3)):
+        info = step()
+    torch.cuda.synchronize()
+    if pg:
+        pg.barrier()
+    clocks = Clocks(local)
+    clocks.start()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    e0.record(stream)
+    launches = 0
+    iters = []
+    for _ in range(args.steps):
+        info = step()
+        launches += info["launches"]
+        iters.append(info["iters"])
+    e1.record(stream)
+    torch.cuda.synchronize()
+    clk = clocks.stop()
+    ms = e0.elapsed_time(e1) / args.steps
+    if pg:
+        t = torch.tensor([ms], device=dev)
+        pg.all_reduce(t, op=pg.ReduceOp.MAX)
+        ms = float(t.item())
+        pg.barrier()
+    it = iters[-1]
+    bps = bytes_per_solve(a.n, a.nnz, it)
+    value = ws * bps / (ms * 1e-3) / 1e9
+
+    # end to end through the C ABI with pinned host buffers
+    bh = torch.from_numpy(b).pin_memory()
+    xh = torch.zeros(a.n, dtype=torch.float64).pin_memory()
+    for _ in range(2):
+        xh.zero_()
+        pk.cg_solve(A, bh, xh, **kw)
+    torch.cuda.synchronize()
+    if pg:
+        pg.barrier()
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        xh.zero_()
+        pk.cg_solve(A, bh, xh, **kw)
+    torch.cuda.synchronize()
+    e2e_s = (time.perf_counter() - t0) / args.steps
+    if pg:
+        t = torch.tensor([e2e_s], device=dev)
+        pg.all_reduce(t, op=pg.ReduceOp.MAX)
+        e2e_s = float(t.item())
+    e2e = {"value": ws * bps / e2e_s / 1e9, "unit": UNIT, "h2d_bytes_per_step": 16 * a.n,
+           "d2h_bytes_per_step": 8 * a.n, "ms_per_step": 1e3 * e2e_s}
+
+    if rank != 0:
+        if pg:
+            pg.destroy_process_group()
+        return 0
+
+    # roofline of the dominant kernel: 30 fixed iterations with per-launch CUDA events
+    prof = pk.cg_solve(A, bd, xd.zero_(), tol=0.0, maxit=30, flags=pk.FLAG_TIMING)
+    t_s = prof["kernel_ms"]["spmv_dots"] * 1e-3
+    t_u = prof["kernel_ms"]["update"] * 1e-3
+    peak, peak_kind = measured_peaks()
+    ach = spmv_dots_bytes(a.n, a.nnz) / t_s / 1e9
+    roofline = {"bound": "hbm", "achieved": ach, "peak": peak, "unit": "GB/s", "frac": ach / peak,
+                "traffic": ncu_traffic("k_cg_spmv_dots", workload_name(args.k)),
+                "kernel": "k_cg_spmv_dots (K-CG-S: SpMV + <Ap,Ap>, <p,Ap>, last-block alpha/beta)",
+                "peak_source": f"{peak_kind} (MEASURED_PEAKS.json hbm_gbs)" if peak_kind == "measured" else "fallback",
+                "algorithmic_bytes_per_launch": spmv_dots_bytes(a.n, a.nnz),
+                "launch_ms": 1e3 * t_s,
+                "fp64_flops_per_launch": 2 * a.nnz + 4 * a.n,
+                "fp64_tflops": (2 * a.nnz + 4 * a.n) / t_s / 1e12,
+                "other_kernels": {"k_cg_update": {"launch_ms": 1e3 * t_u,
+                                                  "gbs": update_bytes(a.n) / t_u / 1e9,
+                                                  "frac": update_bytes(a.n) / t_u / 1e9 / peak}}}
+
+    sweep = []
+    if not args.no_sweep:
+        cases = [("lap3d", k) for k in W.LAPLACE_3D_SWEEP] + [("lap2d", k) for k in W.LAPLACE_2D_SWEEP]
+        for kind, k in cases:
+            m = W.laplace_3d(k) if kind == "lap3d" else W.laplace_2d(k)
+            _, mb, _ = W.manufactured(m, seed=0)
+            M = pk.CSRMatrix.from_workload(m)
+            mbd = torch.from_numpy(mb).to(dev)
+            mx = torch.zeros(m.n, dtype=torch.float64, device=dev)
+            row = {"matrix": f"{kind}_{k}", "n": m.n, "nnz": m.nnz}
+            for variant in ("pipelined", "classical"):
+                best = None
+                for rep in range(2):
+                    mx.zero_()
+                    inf = pk.cg_solve(M, mbd, mx, tol=1e-8, maxit=50_000, variant=variant)
+                    best = inf if best is None or inf["solve_ms"] < best["solve_ms"] else best
+                row[f"{variant}_iters"] = best["iters"]
+                row[f"{variant}_ms"] = best["solve_ms"]
+            row["pipelined_gbs"] = bytes_per_solve(m.n, m.nnz, row["pipelined_iters"]) / (row["pipelined_ms"] * 1e-3) / 1e9
+            row["speedup_vs_classical"] = row["classical_ms"] / row["pipelined_ms"]
+            sweep.append(row)
+            M.close()
+
+    cpu = None
+    if not args.no_cpu:
+        s, it_cpu = oracle_sample(a, b, 60)
+        cpu = {"value": oracle_gbs(a, s, it_cpu), "unit": UNIT, "cores": 1, "kind": "oracle",
+               "sample": f"{it_cpu} pipelined-CG iterations (tol=0) of the same {args.k}^3 system, "
+                         f"{s:.1f} s, single-threaded FP64 C"}
+
+    line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64", "data": "synthetic", "config": config(args.k, a),
+            "time_to_tol_ms": ms, "iters": it, "iters_per_s": it / (ms * 1e-3),
+            "gpu_launches": launches, "e2e": e2e, "roofline": roofline, "cpu_baseline": cpu,
+            "clocks": clk, "sweep": sweep}
+    print(json.dumps(line), flush=True)
+    if pg:
+        pg.destroy_process_group()
+    return 0
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_ours(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

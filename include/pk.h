@@ -1,0 +1,212 @@
+/*
+ * pk.h -- C ABI of the GB300 (sm_103a) pipelined Krylov solver library.
+ *
+ * Method: K. Rupp, J. Weinbub, A. Juengel, T. Grasser, "Pipelined Iterative Solvers with
+ * Kernel Fusion for Graphics Processing Units", ACM TOMS 2015 (arXiv:1410.4054).
+ * The problem statement (Sec. 1): solve A x = b for a sparse square matrix A and a right-hand
+ * side b with CG (symmetric positive definite A), BiCGStab and restarted GMRES(m).
+ *
+ * Conventions shared by every entry point
+ *   - Matrices are CSR with int32 row pointers / column indices and float64 values
+ *     (Sec. 2.2).  pk_csr_create COPIES the matrix into library-owned device memory; the
+ *     caller keeps ownership of its arrays.  Solver work vectors are allocated on first use
+ *     (cudaMallocAsync on the given stream) and cached in the pk_csr handle until
+ *     pk_csr_destroy.
+ *   - Vectors b (input) and x (in: initial guess x0, out: solution) are caller-owned,
+ *     float64, length n.  They may be device pointers (no copies) or host pointers (the
+ *     library copies them in and out inside the call; used for end-to-end timing).
+ *   - `stream` is a cudaStream_t (NULL = legacy default stream).  Every call is
+ *     stream-ordered and blocks only at its end, to read the final status into pk_info.
+ *   - Stopping rule: ||r||_2 <= tol * ||b||_2.  b = 0 returns x = 0 after 0 iterations.
+ *     tol = 0 runs exactly maxit iterations (fixed-iteration timing, Sec. 4).
+ *   - Errors are returned as pk_status values, never by aborting.  Reaching maxit returns
+ *     PK_NOT_CONVERGED with x valid.  pk_last_error() gives a message for the last failure
+ *     on the calling thread.
+ *   - The library uses one GPU: the device current on the calling thread.
+ */
+#ifndef PK_H_
+#define PK_H_
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+  PK_OK = 0,
+  PK_ERR_ARG = 1,        /* invalid argument (bad CSR, NULL pointer, size limits) */
+  PK_ERR_CUDA = 2,       /* a CUDA runtime call failed; see pk_last_error() */
+  PK_ERR_OOM = 3,        /* device allocation failed */
+  PK_NOT_CONVERGED = 4,  /* maxit reached; x holds the last iterate */
+  PK_BREAKDOWN = 5,      /* BiCGStab / GMRES breakdown (zero denominator, no progress) */
+  PK_NOT_SPD = 6,        /* CG found <p, Ap> <= 0 */
+  PK_ERR_NAN = 7,        /* a scalar became NaN / Inf */
+  PK_TIMEOUT = 8         /* a bounded device-side wait ran out */
+} pk_status;
+
+/* Solver formulation. */
+enum {
+  PK_VARIANT_PIPELINED = 0, /* Alg. 2 / 4 / 6 with fused kernels (Sec. 3) */
+  PK_VARIANT_CLASSICAL = 1, /* Alg. 1 / 3 / 5 as one kernel per BLAS-like operation */
+  PK_VARIANT_SPLIT = 2      /* pipelined, SpMV not fused with the reductions (Sec. 3.1-3.3,
+                               the "not possible or desired" fallbacks) */
+};
+
+/* Arithmetic of the iteration. */
+enum {
+  PK_PREC_FP64 = 0,  /* everything in float64 */
+  PK_PREC_MIXED = 1  /* pk_cg_solve only: FP32 SpMV/vectors inside FP64 iterative refinement */
+};
+
+/* How the iteration loop is driven. */
+enum {
+  PK_LOOP_GRAPH = 0, /* CUDA graph with a device-controlled conditional WHILE node:
+                        no host round-trip until the solve ends */
+  PK_LOOP_HOST = 1   /* plain launches; the host reads the device "done" flag every
+                        `check_every` iterations (kernels after convergence return at once) */
+};
+
+/* pk_opts.flags */
+#define PK_FLAG_TIMING 1u    /* time every kernel launch with CUDA events (host loop) and
+                                report per-kernel averages in pk_info.kernel_ms */
+#define PK_FLAG_TRUE_RES 2u  /* compute ||b - A x|| / ||b|| at exit into pk_info.rel_res_true */
+
+typedef struct {
+  double tol;          /* relative residual tolerance (>= 0) */
+  int32_t maxit;       /* iteration limit: CG/BiCGStab loop iterations, GMRES Arnoldi steps */
+  int32_t restart;     /* GMRES restart length m, 1..64 */
+  int32_t variant;     /* PK_VARIANT_* */
+  int32_t precision;   /* PK_PREC_* */
+  int32_t loop;        /* PK_LOOP_* */
+  int32_t check_every; /* PK_LOOP_HOST: iterations between host checks (0 -> 16) */
+  uint32_t flags;      /* PK_FLAG_* */
+  int32_t trace_cap;   /* capacity (iterations) of `trace`, 0 = no trace */
+  double* trace;       /* optional DEVICE array [trace_cap][4]: per iteration i the solver
+                          writes {alpha_i, beta_i, omega_i, res2_i} (unused slots untouched);
+                          GMRES writes {R_{i-1,i}, R_{i,i}, xi_i, estimate_i} */
+} pk_opts;
+
+/* Per-kernel timing slots in pk_info (PK_FLAG_TIMING). */
+#define PK_MAX_KERNEL_SLOTS 8
+
+typedef struct {
+  int32_t iters;         /* iterations performed (GMRES: Arnoldi steps over all cycles) */
+  int32_t status;        /* pk_status of the solve */
+  int32_t cycles;        /* GMRES restarts; mixed precision: outer refinement steps */
+  int32_t launches;      /* kernels launched by the call (graph nodes counted per execution) */
+  double rel_res_est;    /* last recursive residual estimate / ||b|| */
+  double rel_res_true;   /* ||b - A x|| / ||b|| at exit (PK_FLAG_TRUE_RES), else -1 */
+  double solve_ms;       /* device time of the call from its first to its last kernel */
+  double kernel_ms[PK_MAX_KERNEL_SLOTS];      /* PK_FLAG_TIMING: mean ms per launch, by slot */
+  int32_t kernel_count[PK_MAX_KERNEL_SLOTS];  /* PK_FLAG_TIMING: launches timed, by slot */
+} pk_info;
+
+/* Timing slots (index into kernel_ms / kernel_count). */
+enum {
+  PK_SLOT_SPMV_DOTS = 0, /* fused SpMV + first reduction stage (K-CG-S, K-BI-1/3, K-GM-1) */
+  PK_SLOT_UPDATE = 1,    /* fused vector update + first reduction stage (K-CG-U, K-BI-2/4) */
+  PK_SLOT_MULTIDOT = 2,  /* GMRES Gram-Schmidt inner products */
+  PK_SLOT_ORTHO = 3,     /* GMRES update + norm, normalisation + xi */
+  PK_SLOT_SPMV = 4,      /* plain SpMV (classical / split forms) */
+  PK_SLOT_BLAS1 = 5,     /* plain BLAS-1 kernels (classical / split forms) */
+  PK_SLOT_OTHER = 6      /* setup, cycle end, refinement */
+};
+
+typedef struct pk_csr pk_csr;
+
+/* Row statistics and schedule chosen by pk_csr_create (Sec. 2.2; rows are assigned to
+ * thread blocks in nnz-balanced contiguous ranges). */
+typedef struct {
+  int64_t n, nnz;
+  int32_t row_min, row_max;  /* shortest / longest row */
+  double row_mean;
+  int32_t grid;              /* thread blocks of the fused kernels */
+  int32_t block;             /* threads per block */
+  int32_t kernel;            /* SpMV variant: 0 thread-per-row, 1 warp-per-row */
+  int32_t values_fp32_exact; /* 1 if every value is exactly representable in float32 */
+} pk_csr_stats;
+
+/*
+ * Create a CSR matrix handle (Sec. 2.2 "compressed sparse row representation").
+ *   n, nnz      : rows (= columns) and nonzeros; 0 <= n, nnz < 2^31.
+ *   row_ptr     : n+1 int32, row_ptr[0] = 0, nondecreasing, row_ptr[n] = nnz.
+ *   col_idx     : nnz int32 in [0, n).
+ *   vals        : nnz float64.
+ *   on_device   : 1 if the three arrays are device pointers, 0 if host pointers.
+ * The arrays are validated (PK_ERR_ARG on violation), copied and analysed (row-length
+ * statistics -> schedule).  *out receives the handle; release it with pk_csr_destroy.
+ */
+pk_status pk_csr_create(int64_t n, int64_t nnz, const int32_t* row_ptr, const int32_t* col_idx,
+                        const double* vals, int32_t on_device, void* stream, pk_csr** out);
+
+/* Release the handle, its matrix copy and all cached work memory. NULL is accepted. */
+pk_status pk_csr_destroy(pk_csr* A);
+
+/* Row statistics and the schedule chosen for A. */
+pk_status pk_csr_stats_get(const pk_csr* A, pk_csr_stats* out);
+
+/* y = A x (device pointers, length n) -- the plain CSR product of Sec. 2.2. */
+pk_status pk_spmv(pk_csr* A, const double* x, double* y, void* stream);
+
+/*
+ * q = A p and *result = <p, q> (Sec. 2.2, Eq. (1)-(2)).  fused = 1 computes the first
+ * reduction stage inside the SpMV kernel and the second in its last block (one launch);
+ * fused = 0 runs the SpMV, then a separate inner-product kernel (two launches).
+ * p, q: device, length n.  result: device pointer to one double.
+ */
+pk_status pk_spmv_dot(pk_csr* A, const double* p, double* q, double* result, int32_t fused,
+                      void* stream);
+
+/*
+ * Conjugate gradients for SPD A.  variant PIPELINED = Alg. 2 with two fused kernels per
+ * iteration (update x,r,p + <r,r>; SpMV + <Ap,Ap>, <p,Ap>, with alpha/beta from Eq. (3) in
+ * the SpMV kernel's last block; Sec. 3.1); CLASSICAL = Alg. 1 as six kernels per iteration
+ * (SpMV, dot, axpy, axpy, dot, xpay); SPLIT = Alg. 2 with SpMV and its dots in separate
+ * kernels (three per iteration).  precision MIXED: see pk_cg_solve_mixed semantics in the
+ * header notes below.  opts / info may not be NULL.
+ */
+pk_status pk_cg_solve(pk_csr* A, const double* b, double* x, const pk_opts* opts, pk_info* info,
+                      void* stream);
+
+/*
+ * BiCGStab (Alg. 3 / 4, Sec. 3.2), r0* = r0.  PIPELINED: four fused kernels per iteration
+ * (SpMV Ap + <Ap,r0*> -> alpha; s = r - alpha Ap + <s,s>; SpMV As + <As,s>, <As,As>,
+ * <As,r0*> -> omega, beta; x, r, p updates + <r,r0*>, <r,r>).  CLASSICAL: one kernel per
+ * operation of Alg. 3.
+ */
+pk_status pk_bicgstab_solve(pk_csr* A, const double* b, double* x, const pk_opts* opts,
+                            pk_info* info, void* stream);
+
+/*
+ * Restarted simpler GMRES(m) with classical Gram-Schmidt (Alg. 5 / 6, Sec. 3.3),
+ * m = opts->restart (1..64).  PIPELINED: step 1 two kernels, later steps four (SpMV +
+ * <v_{i-1}, v_i>; inner products with v_1..v_{i-2}; R column + update + ||v_i||^2;
+ * normalisation + xi_i); the triangular solve R eta = xi and the x update run on the device
+ * at the end of each cycle.  maxit counts Arnoldi steps over all cycles.
+ */
+pk_status pk_gmres_solve(pk_csr* A, const double* b, double* x, const pk_opts* opts,
+                         pk_info* info, void* stream);
+
+/*
+ * Many independent SPD systems in one persistent launch (pipelined CG per system, with
+ * per-system convergence masks).  A[k], b[k], x[k] for k < nsys; b/x device pointers.
+ * infos: nsys entries (may be NULL).  opts->precision selects FP64 or MIXED.
+ */
+pk_status pk_batched_solve(int32_t nsys, pk_csr* const* A, const double* const* b,
+                           double* const* x, const pk_opts* opts, pk_info* infos, void* stream);
+
+/* Human-readable name of a status code (static string). */
+const char* pk_status_string(pk_status s);
+
+/* Message describing the last error on the calling thread ("" if none). */
+const char* pk_last_error(void);
+
+/* Library version as major*10000 + minor*100 + patch. */
+int32_t pk_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* PK_H_ */

@@ -1,0 +1,379 @@
+// Conjugate gradients: pipelined (Alg. 2) with two fused kernels per iteration, the split
+// variant (three kernels), and classical CG (Alg. 1) as six kernels per iteration.
+//
+// Pipelined iteration i (Sec. 3.1):
+//   K-CG-U  x_i = x_{i-1} + alpha p_{i-1};  r_i = r_{i-1} - alpha A p_{i-1};
+//           p_i = r_i + beta p_{i-1};  first stage of <r_i, r_i>.
+//           Last block: <r_i, r_i>, convergence test (||r_i|| <= tol ||b||), maxit.
+//   K-CG-S  A p_i fused with the first stage of <Ap_i, Ap_i> and <p_i, Ap_i>.
+//           Last block: alpha_i = <r_i,r_i>/<p_i,Ap_i>,
+//                       beta_i  = alpha_i^2 <Ap_i,Ap_i>/<r_i,r_i> - 1   (Eq. (3)).
+// Every vector is read once and written once per kernel: K-CG-U moves 56 bytes per row,
+// K-CG-S 12 bytes per nonzero + 20 bytes per row.
+#include <cmath>
+
+#include "pk_internal.cuh"
+
+namespace pk {
+
+// r = b - A x, p = r; first stage of <r, r> and <b, b>.  Last block: rr, bb, thr2, and the
+// zero-iteration exits (b = 0 -> x = 0; ||r0|| <= tol ||b||).
+__global__ void __launch_bounds__(kBlock) k_residual_init(RowArgs a, const double* __restrict__ b,
+                                                          const double* __restrict__ x,
+                                                          double* __restrict__ r,
+                                                          double* __restrict__ p) {
+  const int r0 = a.rowblk[blockIdx.x], r1 = a.rowblk[blockIdx.x + 1];
+  double v[2] = {0.0, 0.0};
+  for (int row = r0 + threadIdx.x; row < r1; row += blockDim.x) {
+    const double bi = b[row];
+    const double ri = bi - csr_row(a, x, row);
+    r[row] = ri;
+    if (p) p[row] = ri;
+    v[0] = fma(ri, ri, v[0]);
+    v[1] = fma(bi, bi, v[1]);
+  }
+  block_partials<2>(v, a.partials);
+  if (arrive_last(&a.st->counter)) {
+    double t[2];
+    final_sums<2>(a.partials, t);
+    if (threadIdx.x == 0) {
+      DevState* st = a.st;
+      const double tol = st->thr2;
+      st->rr = t[0];
+      st->bb = t[1];
+      st->thr2 = tol * tol * t[1];
+      st->iter = 0;
+      if (!isfinite(t[0]) || !isfinite(t[1])) {
+        finish(st, PK_ERR_NAN);
+      } else if (t[1] == 0.0) {
+        st->zero_x = 1;
+        st->rr = 0.0;
+        finish(st, PK_OK);
+      } else if (t[0] <= st->thr2) {
+        finish(st, PK_OK);
+      } else if (st->maxit <= 0) {
+        finish(st, PK_NOT_CONVERGED);
+      }
+      st->counter = 0;
+    }
+  }
+}
+
+// x = 0 when b = 0 (flag set by k_residual_init).
+__global__ void __launch_bounds__(kBlock) k_zero_x(RowArgs a, double* __restrict__ x) {
+  if (!__ldcg(&a.st->zero_x)) return;
+  const int r0 = a.rowblk[blockIdx.x], r1 = a.rowblk[blockIdx.x + 1];
+  for (int row = r0 + threadIdx.x; row < r1; row += blockDim.x) x[row] = 0.0;
+}
+
+// Second stage shared by K-CG-S and the split dots kernel: alpha_i and beta_i (Eq. (3)).
+__device__ __forceinline__ void cg_alpha_beta(DevState* st, double apap, double pap) {
+  const double rr = st->rr;
+  const int i = st->iter;
+  if (!isfinite(apap) || !isfinite(pap)) {
+    finish(st, PK_ERR_NAN);
+  } else if (pap <= 0.0) {
+    finish(st, PK_NOT_SPD);
+  } else {
+    const double alpha = rr / pap;
+    const double beta = alpha * alpha * apap / rr - 1.0;
+    st->alpha = alpha;
+    st->beta = beta;
+    trace_put(st, i, 0, alpha);
+    trace_put(st, i, 1, beta);
+  }
+}
+
+// K-CG-S: Ap = A p with the first stage of <Ap, Ap> and <p, Ap> (Sec. 3.1, Alg. 2).
+__global__ void __launch_bounds__(kBlock) k_cg_spmv_dots(RowArgs a, const double* __restrict__ p,
+                                                         double* __restrict__ ap) {
+  if (state_done(a.st)) return;
+  const int r0 = a.rowblk[blockIdx.x], r1 = a.rowblk[blockIdx.x + 1];
+  double v[2] = {0.0, 0.0};
+  for (int row = r0 + threadIdx.x; row < r1; row += blockDim.x) {
+    const double s = csr_row(a, p, row);
+    ap[row] = s;
+    v[0] = fma(s, s, v[0]);
+    v[1] = fma(__ldg(p + row), s, v[1]);
+  }
+  block_partials<2>(v, a.partials);
+  if (arrive_last(&a.st->counter)) {
+    double t[2];
+    final_sums<2>(a.partials, t);
+    if (threadIdx.x == 0) {
+      cg_alpha_beta(a.st, t[0], t[1]);
+      a.st->counter = 0;
+    }
+  }
+}
+
+// Split variant: <Ap, Ap> and <p, Ap> in their own kernel after a plain SpMV.
+__global__ void __launch_bounds__(kBlock) k_cg_dots(RowArgs a, const double* __restrict__ p,
+                                                    const double* __restrict__ ap) {
+  if (state_done(a.st)) return;
+  const int r0 = a.rowblk[blockIdx.x], r1 = a.rowblk[blockIdx.x + 1];
+  double v[2] = {0.0, 0.0};
+  for (int row = r0 + threadIdx.x; row < r1; row += blockDim.x) {
+    const double s = ap[row];
+    v[0] = fma(s, s, v[0]);
+    v[1] = fma(p[row], s, v[1]);
+  }
+  block_partials<2>(v, a.partials);
+  if (arrive_last(&a.st->counter)) {
+    double t[2];
+    final_sums<2>(a.partials, t);
+    if (threadIdx.x == 0) {
+      cg_alpha_beta(a.st, t[0], t[1]);
+      a.st->counter = 0;
+    }
+  }
+}
+
+// Plain SpMV that honours the done flag (split and classical loops).
+__global__ void __launch_bounds__(kBlock) k_spmv_live(RowArgs a, const double* __restrict__ x,
+                                                      double* __restrict__ y, int first) {
+  if (first) count_pass(a.st);
+  if (state_done(a.st)) return;
+  const int r0 = a.rowblk[blockIdx.x], r1 = a.rowblk[blockIdx.x + 1];
+  for (int row = r0 + threadIdx.x; row < r1; row += blockDim.x) y[row] = csr_row(a, x, row);
+}
+
+// K-CG-U: x, r, p updates with the first stage of <r_i, r_i> (Sec. 3.1).
+__global__ void __launch_bounds__(kBlock) k_cg_update(RowArgs a, double* __restrict__ x,
+                                                      double* __restrict__ r,
+                                                      double* __restrict__ p,
+                                                      const double* __restrict__ ap) {
+  DevState* st = a.st;
+  count_pass(st);
+  if (state_done(st)) {
+    if (blockIdx.x == 0 && threadIdx.x == 0 && st->use_cond) cudaGraphSetConditional(st->cond, 0u);
+    return;
+  }
+  const double alpha = __ldcg(&st->alpha), beta = __ldcg(&st->beta);
+  const int r0 = a.rowblk[blockIdx.x], r1 = a.rowblk[blockIdx.x + 1];
+  double v[1] = {0.0};
+  for (int row = r0 + threadIdx.x; row < r1; row += blockDim.x) {
+    const double pk = p[row];
+    x[row] = fma(alpha, pk, x[row]);
+    const double rk = fma(-alpha, ap[row], r[row]);
+    r[row] = rk;
+    p[row] = fma(beta, pk, rk);
+    v[0] = fma(rk, rk, v[0]);
+  }
+  block_partials<1>(v, a.partials);
+  if (arrive_last(&st->counter)) {
+    double t[1];
+    final_sums<1>(a.partials, t);
+    if (threadIdx.x == 0) {
+      const int i = st->iter + 1;
+      st->iter = i;
+      st->rr = t[0];
+      trace_put(st, i - 1, 3, t[0]);
+      if (!isfinite(t[0])) finish(st, PK_ERR_NAN);
+      else if (t[0] <= st->thr2) finish(st, PK_OK);
+      else if (i >= st->maxit) finish(st, PK_NOT_CONVERGED);
+      st->counter = 0;
+    }
+  }
+}
+
+// ---------------------------------------------------------------- classical CG, Alg. 1
+
+// <p, Ap> -> alpha_i = <r_i,r_i>/<p_i,Ap_i>.
+__global__ void __launch_bounds__(kBlock) k_cls_alpha(RowArgs a, const double* __restrict__ p,
+                                                      const double* __restrict__ ap) {
+  DevState* st = a.st;
+  if (state_done(st)) {
+    if (blockIdx.x == 0 && threadIdx.x == 0 && st->use_cond) cudaGraphSetConditional(st->cond, 0u);
+    return;
+  }
+  const int r0 = a.rowblk[blockIdx.x], r1 = a.rowblk[blockIdx.x + 1];
+  double v[1] = {0.0};
+  for (int row = r0 + threadIdx.x; row < r1; row += blockDim.x) v[0] = fma(p[row], ap[row], v[0]);
+  block_partials<1>(v, a.partials);
+  if (arrive_last(&st->counter)) {
+    double t[1];
+    final_sums<1>(a.partials, t);
+    if (threadIdx.x == 0) {
+      if (!isfinite(t[0])) finish(st, PK_ERR_NAN);
+      else if (t[0] <= 0.0) finish(st, PK_NOT_SPD);
+      else {
+        st->alpha = st->rr / t[0];
+        trace_put(st, st->iter, 0, st->alpha);
+      }
+      st->counter = 0;
+    }
+  }
+}
+
+// y += sign * alpha x  (x_{i+1} = x_i + alpha p_i  or  r_{i+1} = r_i - alpha A p_i).
+__global__ void __launch_bounds__(kBlock) k_axpy_alpha(RowArgs a, double* __restrict__ y,
+                                                       const double* __restrict__ x, double sign) {
+  if (state_done(a.st)) return;
+  const double alpha = sign * __ldcg(&a.st->alpha);
+  const int r0 = a.rowblk[blockIdx.x], r1 = a.rowblk[blockIdx.x + 1];
+  for (int row = r0 + threadIdx.x; row < r1; row += blockDim.x) y[row] = fma(alpha, x[row], y[row]);
+}
+
+// <r_{i+1}, r_{i+1}> -> convergence test, beta_i = <r_{i+1},r_{i+1}>/<r_i,r_i>.
+__global__ void __launch_bounds__(kBlock) k_cls_beta(RowArgs a, const double* __restrict__ r) {
+  DevState* st = a.st;
+  if (state_done(st)) return;
+  const int r0 = a.rowblk[blockIdx.x], r1 = a.rowblk[blockIdx.x + 1];
+  double v[1] = {0.0};
+  for (int row = r0 + threadIdx.x; row < r1; row += blockDim.x) {
+    const double rk = r[row];
+    v[0] = fma(rk, rk, v[0]);
+  }
+  block_partials<1>(v, a.partials);
+  if (arrive_last(&st->counter)) {
+    double t[1];
+    final_sums<1>(a.partials, t);
+    if (threadIdx.x == 0) {
+      const int i = st->iter;
+      st->iter = i + 1;
+      trace_put(st, i, 3, t[0]);
+      if (!isfinite(t[0])) finish(st, PK_ERR_NAN);
+      else if (t[0] <= st->thr2) finish(st, PK_OK);
+      else if (i + 1 >= st->maxit) finish(st, PK_NOT_CONVERGED);
+      else {
+        st->beta = t[0] / st->rr;
+        trace_put(st, i, 1, st->beta);
+      }
+      st->rr = t[0];
+      st->counter = 0;
+    }
+  }
+}
+
+// p_{i+1} = r_{i+1} + beta_i p_i.
+__global__ void __launch_bounds__(kBlock) k_xpay_beta(RowArgs a, const double* __restrict__ r,
+                                                      double* __restrict__ p) {
+  if (state_done(a.st)) return;
+  const double beta = __ldcg(&a.st->beta);
+  const int r0 = a.rowblk[blockIdx.x], r1 = a.rowblk[blockIdx.x + 1];
+  for (int row = r0 + threadIdx.x; row < r1; row += blockDim.x) p[row] = fma(beta, p[row], r[row]);
+}
+
+static long long passes_of(const DevState* h) {
+  return *reinterpret_cast<const long long*>(&h->s[7]);
+}
+
+static pk_status check_opts(const pk_csr* A, const double* b, double* x, const pk_opts* o,
+                            pk_info* info) {
+  if (!A || !o || !info) { set_error("NULL handle, opts or info"); return PK_ERR_ARG; }
+  if (A->n > 0 && (!b || !x)) { set_error("NULL b or x"); return PK_ERR_ARG; }
+  if (!(o->tol >= 0.0) || o->maxit < 0) { set_error("tol must be >= 0 and maxit >= 0"); return PK_ERR_ARG; }
+  if (o->trace_cap > 0 && !o->trace) { set_error("trace_cap > 0 needs a trace array"); return PK_ERR_ARG; }
+  return PK_OK;
+}
+
+pk_status cg_solve(pk_csr* A, const double* b, double* x, const pk_opts* o, pk_info* info,
+                   cudaStream_t s) {
+  pk_status e = check_opts(A, b, x, o, info);
+  if (e) return e;
+  *info = pk_info{};
+  info->rel_res_true = -1.0;
+  if (A->n == 0) return PK_OK;
+  if (o->precision != PK_PREC_FP64) { set_error("precision must be PK_PREC_FP64 here"); return PK_ERR_ARG; }
+  if (o->variant < 0 || o->variant > 2) { set_error("bad variant"); return PK_ERR_ARG; }
+  cudaEvent_t e0, e1;
+  PK_CUDA(cudaEventCreate(&e0));
+  PK_CUDA(cudaEventCreate(&e1));
+  PK_CUDA(cudaEventRecord(e0, s));
+  if ((e = state_init(A, o, s))) return e;
+  VecStage v;
+  if ((e = stage_in(A, b, x, 14, 15, s, &v))) return e;
+  double *r, *p, *ap;
+  if ((e = work_vec(A, 0, &r)) || (e = work_vec(A, 1, &p)) || (e = work_vec(A, 2, &ap))) return e;
+  const RowArgs ra = row_args(A);
+  double* xd = v.x_dev;
+  const double* bd = v.b_dev;
+  Timer T;
+  T.A = A;
+  T.on = (o->flags & PK_FLAG_TIMING) != 0;
+  T.s = s;
+  int launches = 0;
+  const int G = A->grid;
+
+  // setup: r0 = b - A x0, p0 = r0, <r0,r0>, <b,b>
+  if ((e = T.begin(PK_SLOT_OTHER))) return e;
+  k_residual_init<<<G, kBlock, 0, s>>>(ra, bd, xd, r, p);
+  if ((e = T.end())) return e;
+  k_zero_x<<<G, kBlock, 0, s>>>(ra, xd);
+  launches += 2;
+  const int variant = o->variant;
+  if (variant == PK_VARIANT_PIPELINED || variant == PK_VARIANT_SPLIT) {
+    // A p0, alpha_0, beta_0
+    if ((e = T.begin(PK_SLOT_SPMV_DOTS))) return e;
+    k_cg_spmv_dots<<<G, kBlock, 0, s>>>(ra, p, ap);
+    if ((e = T.end())) return e;
+    launches += 1;
+  }
+  PK_CUDA(cudaGetLastError());
+
+  LoopSpec L;
+  L.keys[0] = xd;
+  L.keys[1] = bd;
+  L.ikeys[0] = variant;
+  if (variant == PK_VARIANT_PIPELINED) {
+    L.kind = 1;
+    L.body_kernels = 2;
+    L.body = [=](cudaStream_t cs, Timer* t) {
+      if (t) t->begin(PK_SLOT_UPDATE);
+      k_cg_update<<<G, kBlock, 0, cs>>>(ra, xd, r, p, ap);
+      if (t) { t->end(); t->begin(PK_SLOT_SPMV_DOTS); }
+      k_cg_spmv_dots<<<G, kBlock, 0, cs>>>(ra, p, ap);
+      if (t) t->end();
+    };
+  } else if (variant == PK_VARIANT_SPLIT) {
+    L.kind = 2;
+    L.body_kernels = 3;
+    L.body = [=](cudaStream_t cs, Timer* t) {
+      if (t) t->begin(PK_SLOT_UPDATE);
+      k_cg_update<<<G, kBlock, 0, cs>>>(ra, xd, r, p, ap);
+      if (t) { t->end(); t->begin(PK_SLOT_SPMV); }
+      k_spmv_live<<<G, kBlock, 0, cs>>>(ra, p, ap, 0);
+      if (t) { t->end(); t->begin(PK_SLOT_BLAS1); }
+      k_cg_dots<<<G, kBlock, 0, cs>>>(ra, p, ap);
+      if (t) t->end();
+    };
+  } else {
+    L.kind = 3;
+    L.body_kernels = 6;
+    L.body = [=](cudaStream_t cs, Timer* t) {
+      if (t) t->begin(PK_SLOT_SPMV);
+      k_spmv_live<<<G, kBlock, 0, cs>>>(ra, p, ap, 1);
+      if (t) { t->end(); t->begin(PK_SLOT_BLAS1); }
+      k_cls_alpha<<<G, kBlock, 0, cs>>>(ra, p, ap);
+      if (t) { t->end(); t->begin(PK_SLOT_BLAS1); }
+      k_axpy_alpha<<<G, kBlock, 0, cs>>>(ra, xd, p, 1.0);
+      if (t) { t->end(); t->begin(PK_SLOT_BLAS1); }
+      k_axpy_alpha<<<G, kBlock, 0, cs>>>(ra, r, ap, -1.0);
+      if (t) { t->end(); t->begin(PK_SLOT_BLAS1); }
+      k_cls_beta<<<G, kBlock, 0, cs>>>(ra, r);
+      if (t) { t->end(); t->begin(PK_SLOT_BLAS1); }
+      k_xpay_beta<<<G, kBlock, 0, cs>>>(ra, r, p);
+      if (t) t->end();
+    };
+  }
+  if ((e = run_loop(A, o, s, L, &T, &launches))) return e;
+  if ((e = T.flush())) return e;
+  const bool graph = o->loop == PK_LOOP_GRAPH && !T.on;
+  if ((e = finish_info(A, o, info, s, v, e0, e1, launches))) return e;
+  if (graph) info->launches += (int)(passes_of(A->st_host) * L.body_kernels);
+  for (int k = 0; k < PK_MAX_KERNEL_SLOTS; ++k) {
+    info->kernel_count[k] = T.count[k];
+    info->kernel_ms[k] = T.count[k] ? T.ms[k] / T.count[k] : 0.0;
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  return (pk_status)info->status;
+}
+
+}  // namespace pk
+
+extern "C" pk_status pk_cg_solve(pk_csr* A, const double* b, double* x, const pk_opts* opts,
+                                 pk_info* info, void* stream) {
+  return pk::cg_solve(A, b, x, opts, info, (cudaStream_t)stream);
+}

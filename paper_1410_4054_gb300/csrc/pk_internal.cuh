@@ -1,0 +1,278 @@
+// Internal declarations shared by the translation units of the pk library.
+//
+// Device-side building blocks of the fused kernels (Sec. 2.2 of Rupp et al.,
+// arXiv:1410.4054): the first reduction stage of inner products is a per-block sum written
+// to a fixed slot; the second stage is done by the last block to finish (arrival counter),
+// which sums the slots in a fixed order -- so every reduction is deterministic -- and then
+// computes the solver's scalars and convergence test on the device.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <string>
+
+#include "../../include/pk.h"
+
+namespace pk {
+
+constexpr int kBlock = 256;        // threads per block of the fused kernels
+constexpr int kMaxGridPerSm = 4;   // resident blocks per SM used for the persistent grid
+constexpr int kMaxDots = 64;       // partial-sum slots per block (GMRES needs up to m+1)
+constexpr int kRunning = -1;       // DevState::status while iterating
+
+// Scalars of one solve, in device memory.  One arrival counter suffices: kernels of a solve
+// run one after another on one stream, and each last block resets it.
+struct DevState {
+  double rr;      // <r_i, r_i> (CG, BiCGStab), squared true residual (GMRES)
+  double alpha, beta, omega;
+  double bb;      // <b, b>
+  double thr2;    // tol^2 <b, b>
+  double s[8];    // solver-specific scalars
+  int32_t iter, maxit, status, done;
+  int32_t zero_x;         // b = 0: the solution is x = 0
+  int32_t trace_cap;
+  double* trace;          // [trace_cap][4] or nullptr
+  unsigned int counter;   // last-block arrival counter
+  int32_t use_cond;       // kernels run inside a conditional WHILE graph node
+  cudaGraphConditionalHandle cond;
+  int32_t pad[2];
+};
+
+// Loads that bypass L1 (the value was written by another block or an earlier kernel).
+__device__ __forceinline__ double ld_cg(const double* p) { return __ldcg(p); }
+__device__ __forceinline__ int ld_cg(const int* p) { return __ldcg(p); }
+
+// Warp sum with a fixed xor tree: every lane ends with the same, order-fixed sum.
+__device__ __forceinline__ double warp_sum(double v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+
+// First reduction stage: block sum of NV per-thread values into partials[k * G + block].
+template <int NV>
+__device__ __forceinline__ void block_partials(double (&v)[NV], double* partials) {
+  __shared__ double sm[NV][kBlock / 32];
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+#pragma unroll
+  for (int k = 0; k < NV; ++k) v[k] = warp_sum(v[k]);
+  if (lane == 0) {
+#pragma unroll
+    for (int k = 0; k < NV; ++k) sm[k][warp] = v[k];
+  }
+  __syncthreads();
+  if (warp == 0) {
+#pragma unroll
+    for (int k = 0; k < NV; ++k) {
+      double t = lane < (int)(blockDim.x >> 5) ? sm[k][lane] : 0.0;
+      t = warp_sum(t);
+      if (lane == 0) partials[(size_t)k * gridDim.x + blockIdx.x] = t;
+    }
+  }
+}
+
+// Arrival on the grid-wide counter; true in every thread of the last block to arrive.
+__device__ __forceinline__ bool arrive_last(unsigned int* counter) {
+  __shared__ unsigned int ticket;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    __threadfence();
+    ticket = atomicAdd(counter, 1u);
+  }
+  __syncthreads();
+  const bool last = ticket == gridDim.x - 1;
+  if (last) __threadfence();
+  return last;
+}
+
+// Second reduction stage in the last block: out[k] = sum over blocks of partials[k][.], in a
+// fixed order (strided per thread, then the xor tree), broadcast to every thread.
+template <int NV>
+__device__ __forceinline__ void final_sums(const double* partials, double (&out)[NV]) {
+  __shared__ double sm[NV][kBlock / 32];
+  const int G = gridDim.x;
+  double v[NV];
+#pragma unroll
+  for (int k = 0; k < NV; ++k) v[k] = 0.0;
+  for (int i = threadIdx.x; i < G; i += blockDim.x) {
+#pragma unroll
+    for (int k = 0; k < NV; ++k) v[k] += ld_cg(partials + (size_t)k * G + i);
+  }
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+#pragma unroll
+  for (int k = 0; k < NV; ++k) v[k] = warp_sum(v[k]);
+  if (lane == 0) {
+#pragma unroll
+    for (int k = 0; k < NV; ++k) sm[k][warp] = v[k];
+  }
+  __syncthreads();
+#pragma unroll
+  for (int k = 0; k < NV; ++k) {
+    double t = 0.0;
+    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) t += sm[k][w];
+    out[k] = t;
+  }
+}
+
+__device__ __forceinline__ void trace_put(DevState* st, int i, int slot, double v) {
+  if (st->trace && i >= 0 && i < st->trace_cap) st->trace[(size_t)i * 4 + slot] = v;
+}
+
+// Ends the solve: status, done flag, and (inside a graph WHILE node) the loop condition.
+__device__ __forceinline__ void finish(DevState* st, int status) {
+  st->status = status;
+  st->done = 1;
+  if (st->use_cond) cudaGraphSetConditional(st->cond, 0u);
+}
+
+// Common kernel arguments of the row-parallel kernels.
+struct RowArgs {
+  int32_t n;
+  const int32_t* rp;      // row pointers
+  const int32_t* ci;      // column indices
+  const double* va;       // values
+  const int32_t* rowblk;  // rows of block b: [rowblk[b], rowblk[b+1])
+  double* partials;       // [kMaxDots][grid]
+  DevState* st;
+};
+
+}  // namespace pk
+
+// ------------------------------------------------------------------ host side
+
+struct pk_graph_entry {
+  int kind = -1;              // solver kind (0 = none)
+  const void* key[4] = {nullptr, nullptr, nullptr, nullptr};
+  int64_t ikey[4] = {0, 0, 0, 0};
+  cudaGraph_t graph = nullptr;
+  cudaGraphExec_t exec = nullptr;
+  cudaGraphConditionalHandle cond_handle = 0;
+  int body_kernels = 0;
+};
+
+struct pk_csr {
+  int32_t n = 0, nnz = 0;
+  int device = 0;
+  int32_t* rp = nullptr;
+  int32_t* ci = nullptr;
+  double* va = nullptr;
+  float* va32 = nullptr;
+  int32_t* rowblk = nullptr;  // grid + 1
+  int grid = 1;
+  pk_csr_stats stats{};
+  cudaStream_t cap_stream = nullptr;  // private stream used for graph capture
+  // cached work memory
+  double* vec[16] = {nullptr};        // n-length work vectors, allocated on demand
+  int32_t vec_len[16] = {0};
+  double* partials = nullptr;         // [kMaxDots][grid]
+  pk::DevState* st = nullptr;         // device scalars
+  pk::DevState* st_host = nullptr;    // pinned host mirror
+  double* basis = nullptr;            // GMRES Krylov basis, (m+1) x n column-contiguous
+  int basis_m = 0;
+  double* small = nullptr;            // small device scratch (R, xi, eta ...): 8192 doubles
+  pk_graph_entry graphs[4];
+  cudaEvent_t ev_pool[64] = {nullptr};
+  int ev_count = 0;
+};
+
+namespace pk {
+
+// thread-local last error message
+void set_error(const std::string& msg);
+pk_status cuda_fail(cudaError_t e, const char* what);
+
+#define PK_CUDA(call)                                                     \
+  do {                                                                    \
+    cudaError_t e__ = (call);                                             \
+    if (e__ != cudaSuccess) return ::pk::cuda_fail(e__, #call);           \
+  } while (0)
+
+// Work vector slot `id` of length n (allocated on first use).
+pk_status work_vec(pk_csr* A, int id, double** out);
+pk_status ensure_state(pk_csr* A);
+
+// Host/device pointer staging for b and x (host pointers are copied in and out).
+struct VecStage {
+  const double* b_dev = nullptr;
+  double* x_dev = nullptr;
+  double* x_user = nullptr;
+  bool x_host = false;
+};
+pk_status stage_in(pk_csr* A, const double* b, double* x, int slot_b, int slot_x,
+                   cudaStream_t s, VecStage* out);
+pk_status stage_out(pk_csr* A, const VecStage& v, cudaStream_t s);
+
+// Initialise DevState for a solve and read it back afterwards.
+pk_status state_init(pk_csr* A, const pk_opts* o, cudaStream_t s);
+pk_status state_read(pk_csr* A, cudaStream_t s);
+
+// Kernel timing helper (PK_FLAG_TIMING).
+struct Timer {
+  pk_csr* A = nullptr;
+  bool on = false;
+  cudaStream_t s = nullptr;
+  int used = 0;
+  int slot[32] = {0};
+  double ms[PK_MAX_KERNEL_SLOTS] = {0};
+  int count[PK_MAX_KERNEL_SLOTS] = {0};
+  pk_status begin(int slot_id);
+  pk_status end();
+  pk_status flush();  // synchronise and accumulate
+};
+
+// Plain kernels shared by several solvers (pk_blas.cu).
+void launch_spmv(const pk_csr* A, const double* x, double* y, cudaStream_t s);
+void launch_dot_store(const pk_csr* A, const double* x, const double* y, double* out,
+                      cudaStream_t s);
+void launch_true_residual(pk_csr* A, const double* b, const double* x, double* tmp,
+                          double* out2, cudaStream_t s);
+RowArgs row_args(const pk_csr* A);
+
+pk_status finish_info(pk_csr* A, const pk_opts* o, pk_info* info, cudaStream_t s,
+                      const VecStage& v, cudaEvent_t e0, cudaEvent_t e1, int launches);
+
+}  // namespace pk
+
+namespace pk {
+
+// y_row = sum_j A[row, j] x[j], left to right over the row (Sec. 2.2 CSR product).
+__device__ __forceinline__ double csr_row(const RowArgs& a, const double* __restrict__ x, int row) {
+  const int j0 = __ldg(a.rp + row), j1 = __ldg(a.rp + row + 1);
+  double s = 0.0;
+  for (int j = j0; j < j1; ++j) s = fma(__ldg(a.va + j), __ldg(x + __ldg(a.ci + j)), s);
+  return s;
+}
+
+__device__ __forceinline__ bool state_done(const DevState* st) { return __ldcg(&st->done) != 0; }
+
+}  // namespace pk
+
+#include <functional>
+
+namespace pk {
+
+// One iteration's launches, replayed by the loop driver either inside a CUDA graph WHILE
+// node (condition cleared on the device by the kernel that finishes the solve) or from a
+// host loop that checks the device "done" flag.
+struct LoopSpec {
+  int kind = 0;                         // graph cache key: solver kind
+  const void* keys[4] = {nullptr, nullptr, nullptr, nullptr};
+  int64_t ikeys[4] = {0, 0, 0, 0};
+  int body_kernels = 0;                 // kernels per body pass
+  std::function<void(cudaStream_t, Timer*)> body;
+};
+
+// Runs the loop until the device sets `done`; adds the launched kernels to *launches.
+pk_status run_loop(pk_csr* A, const pk_opts* o, cudaStream_t s, const LoopSpec& L, Timer* T,
+                   int* launches);
+
+// Counts body passes (first kernel of every body increments st->s[7] as an integer count).
+__device__ __forceinline__ void count_pass(DevState* st) {
+  if (blockIdx.x == 0 && threadIdx.x == 0) {
+    long long* c = reinterpret_cast<long long*>(&st->s[7]);
+    *c += 1;
+  }
+}
+
+}  // namespace pk

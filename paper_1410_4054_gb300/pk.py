@@ -1,0 +1,227 @@
+"""Thin ctypes binding of the pk C ABI (include/pk.h): argument marshalling only.
+
+Every numerical step runs in the CUDA library ``_build/libpk.so``; there is no CPU fallback.
+If the library cannot be loaded the import-time call ``lib()`` raises.  Vectors may be torch
+CUDA tensors (passed by device pointer, on the current torch stream unless ``stream`` is
+given) or numpy arrays / torch CPU tensors (host pointers: the library copies them in and out
+inside the call).
+"""
+from __future__ import annotations
+
+import ctypes as C
+from pathlib import Path
+
+import numpy as np
+
+from . import build as _build
+
+PK_OK, PK_ERR_ARG, PK_ERR_CUDA, PK_ERR_OOM, PK_NOT_CONVERGED, PK_BREAKDOWN, PK_NOT_SPD, \
+    PK_ERR_NAN, PK_TIMEOUT = range(9)
+STATUS_NAMES = ["PK_OK", "PK_ERR_ARG", "PK_ERR_CUDA", "PK_ERR_OOM", "PK_NOT_CONVERGED",
+                "PK_BREAKDOWN", "PK_NOT_SPD", "PK_ERR_NAN", "PK_TIMEOUT"]
+VARIANTS = {"pipelined": 0, "classical": 1, "split": 2}
+PRECISIONS = {"fp64": 0, "mixed": 1}
+LOOPS = {"graph": 0, "host": 1}
+FLAG_TIMING = 1
+FLAG_TRUE_RES = 2
+SLOTS = ["spmv_dots", "update", "multidot", "ortho", "spmv", "blas1", "other"]
+MAX_SLOTS = 8
+
+
+class Opts(C.Structure):
+    _fields_ = [("tol", C.c_double), ("maxit", C.c_int32), ("restart", C.c_int32),
+                ("variant", C.c_int32), ("precision", C.c_int32), ("loop", C.c_int32),
+                ("check_every", C.c_int32), ("flags", C.c_uint32), ("trace_cap", C.c_int32),
+                ("trace", C.c_void_p)]
+
+
+class Info(C.Structure):
+    _fields_ = [("iters", C.c_int32), ("status", C.c_int32), ("cycles", C.c_int32),
+                ("launches", C.c_int32), ("rel_res_est", C.c_double),
+                ("rel_res_true", C.c_double), ("solve_ms", C.c_double),
+                ("kernel_ms", C.c_double * MAX_SLOTS), ("kernel_count", C.c_int32 * MAX_SLOTS)]
+
+
+class Stats(C.Structure):
+    _fields_ = [("n", C.c_int64), ("nnz", C.c_int64), ("row_min", C.c_int32),
+                ("row_max", C.c_int32), ("row_mean", C.c_double), ("grid", C.c_int32),
+                ("block", C.c_int32), ("kernel", C.c_int32), ("values_fp32_exact", C.c_int32)]
+
+
+EXPORTS = {
+    # name: (restype, argtypes)
+    "pk_csr_create": (C.c_int, [C.c_int64, C.c_int64, C.c_void_p, C.c_void_p, C.c_void_p,
+                                C.c_int32, C.c_void_p, C.POINTER(C.c_void_p)]),
+    "pk_csr_destroy": (C.c_int, [C.c_void_p]),
+    "pk_csr_stats_get": (C.c_int, [C.c_void_p, C.POINTER(Stats)]),
+    "pk_spmv": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p]),
+    "pk_spmv_dot": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_int32,
+                              C.c_void_p]),
+    "pk_cg_solve": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.POINTER(Opts),
+                              C.POINTER(Info), C.c_void_p]),
+    "pk_status_string": (C.c_char_p, [C.c_int]),
+    "pk_last_error": (C.c_char_p, []),
+    "pk_version": (C.c_int32, []),
+}
+
+_lib = None
+
+
+def lib_path() -> Path:
+    return _build.LIB
+
+
+def lib():
+    """Load libpk.so (building it first if it is missing or stale)."""
+    global _lib
+    if _lib is None:
+        path = _build.build()
+        L = C.CDLL(str(path))
+        for name, (res, args) in EXPORTS.items():
+            f = getattr(L, name)
+            f.restype = res
+            f.argtypes = args
+        _lib = L
+    return _lib
+
+
+class PkError(RuntimeError):
+    def __init__(self, status: int, where: str):
+        msg = lib().pk_last_error().decode()
+        super().__init__(f"{where}: {STATUS_NAMES[status] if 0 <= status < 9 else status} {msg}")
+        self.status = status
+
+
+def _check(st: int, where: str, allow=(PK_OK,)):
+    if st not in allow:
+        raise PkError(st, where)
+    return st
+
+
+def _stream_ptr(stream):
+    if stream is None:
+        try:
+            import torch
+            if torch.cuda.is_available():
+                return C.c_void_p(torch.cuda.current_stream().cuda_stream)
+        except ImportError:  # pragma: no cover
+            pass
+        return C.c_void_p(0)
+    if isinstance(stream, int):
+        return C.c_void_p(stream)
+    return C.c_void_p(stream.cuda_stream)
+
+
+def _ptr(v):
+    """Device or host pointer of a float64 torch tensor / numpy array."""
+    if v is None:
+        return C.c_void_p(0)
+    if isinstance(v, np.ndarray):
+        assert v.flags["C_CONTIGUOUS"], "array must be contiguous"
+        return C.c_void_p(v.ctypes.data)
+    assert v.is_contiguous(), "tensor must be contiguous"
+    return C.c_void_p(v.data_ptr())
+
+
+class CSRMatrix:
+    """pk_csr handle: a library-owned device copy of a CSR matrix plus its schedule."""
+
+    def __init__(self, row_ptr, col, val, n=None, stream=None):
+        import torch
+
+        if isinstance(row_ptr, torch.Tensor) and row_ptr.is_cuda:
+            on_device = 1
+            rp, ci, va = row_ptr.contiguous(), col.contiguous(), val.contiguous()
+        else:
+            on_device = 0
+            rp = np.ascontiguousarray(row_ptr, dtype=np.int32)
+            ci = np.ascontiguousarray(col, dtype=np.int32)
+            va = np.ascontiguousarray(val, dtype=np.float64)
+        self._keep = (rp, ci, va)
+        n = int(len(rp) - 1) if n is None else int(n)
+        nnz = int(len(ci))
+        h = C.c_void_p()
+        _check(lib().pk_csr_create(n, nnz, _ptr(rp), _ptr(ci), _ptr(va), on_device,
+                                   _stream_ptr(stream), C.byref(h)), "pk_csr_create")
+        self.handle = h
+        self.n, self.nnz = n, nnz
+        self._keep = None
+
+    @classmethod
+    def from_workload(cls, a, stream=None):
+        return cls(a.row_ptr, a.col, a.val, n=a.n, stream=stream)
+
+    def stats(self) -> dict:
+        s = Stats()
+        _check(lib().pk_csr_stats_get(self.handle, C.byref(s)), "pk_csr_stats_get")
+        return {k: getattr(s, k) for k, _ in Stats._fields_}
+
+    def close(self):
+        if getattr(self, "handle", None):
+            lib().pk_csr_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def make_opts(tol=1e-8, maxit=1000, restart=30, variant="pipelined", precision="fp64",
+              loop="graph", check_every=0, flags=0, trace=None) -> Opts:
+    o = Opts()
+    o.tol = tol
+    o.maxit = maxit
+    o.restart = restart
+    o.variant = VARIANTS[variant] if isinstance(variant, str) else int(variant)
+    o.precision = PRECISIONS[precision] if isinstance(precision, str) else int(precision)
+    o.loop = LOOPS[loop] if isinstance(loop, str) else int(loop)
+    o.check_every = check_every
+    o.flags = flags
+    if trace is not None:
+        assert trace.dim() == 2 and trace.shape[1] == 4 and trace.dtype.is_floating_point
+        o.trace_cap = trace.shape[0]
+        o.trace = trace.data_ptr()
+    else:
+        o.trace_cap = 0
+        o.trace = None
+    return o
+
+
+def info_dict(info: Info) -> dict:
+    d = {k: getattr(info, k) for k in ("iters", "status", "cycles", "launches", "rel_res_est",
+                                       "rel_res_true", "solve_ms")}
+    d["status_name"] = STATUS_NAMES[info.status] if 0 <= info.status < 9 else str(info.status)
+    d["kernel_ms"] = {SLOTS[k]: info.kernel_ms[k] for k in range(len(SLOTS)) if info.kernel_count[k]}
+    d["kernel_count"] = {SLOTS[k]: info.kernel_count[k] for k in range(len(SLOTS)) if info.kernel_count[k]}
+    return d
+
+
+_SOLVER_OK = (PK_OK, PK_NOT_CONVERGED, PK_BREAKDOWN, PK_NOT_SPD, PK_ERR_NAN)
+
+
+def cg_solve(A: CSRMatrix, b, x, stream=None, **kw) -> dict:
+    """pk_cg_solve: x (in: x0, out: solution)."""
+    o = make_opts(**kw)
+    info = Info()
+    st = lib().pk_cg_solve(A.handle, _ptr(b), _ptr(x), C.byref(o), C.byref(info), _stream_ptr(stream))
+    _check(st, "pk_cg_solve", _SOLVER_OK)
+    return info_dict(info)
+
+
+def spmv(A: CSRMatrix, x, y, stream=None):
+    _check(lib().pk_spmv(A.handle, _ptr(x), _ptr(y), _stream_ptr(stream)), "pk_spmv")
+
+
+def spmv_dot(A: CSRMatrix, p, q, result, fused=True, stream=None):
+    _check(lib().pk_spmv_dot(A.handle, _ptr(p), _ptr(q), _ptr(result), 1 if fused else 0,
+                             _stream_ptr(stream)), "pk_spmv_dot")
+
+
+def status_string(s: int) -> str:
+    return lib().pk_status_string(s).decode()
+
+
+def version() -> int:
+    return lib().pk_version()

@@ -1,0 +1,176 @@
+"""GPU parity of CG (pipelined Alg. 2, split, classical Alg. 1) against the CPU oracle.
+
+Bars: per-iteration alpha_i, beta_i within 1e-12 relative over the first 20 iterations;
+iteration count to tol within +-2; x within 1e-9 relative of the oracle's x after the same
+number of iterations; the true residual at exit within the tolerance.
+"""
+import numpy as np
+import pytest
+
+import oracle as O
+from paper_1410_4054_gb300 import workloads as W
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+if not torch.cuda.is_available():  # pragma: no cover
+    pytest.skip("no CUDA device", allow_module_level=True)
+
+from paper_1410_4054_gb300 import pk  # noqa: E402
+
+DEV = "cuda:0"
+
+
+def dev(v):
+    return torch.from_numpy(np.ascontiguousarray(v, dtype=np.float64)).to(DEV)
+
+
+def solve(a, b, x0=None, A=None, trace_cap=64, **kw):
+    A = A or pk.CSRMatrix.from_workload(a)
+    x = dev(np.zeros(a.n) if x0 is None else x0)
+    tr = torch.full((trace_cap, 4), float("nan"), dtype=torch.float64, device=DEV)
+    info = pk.cg_solve(A, dev(b), x, trace=tr, **kw)
+    torch.cuda.synchronize()
+    return info, x.cpu().numpy(), tr.cpu().numpy()
+
+
+def rel(a, b):
+    return float(np.linalg.norm(a - b) / max(np.linalg.norm(b), 1e-300))
+
+
+MATRICES = {
+    "lap2d_64": lambda: W.laplace_2d(64),                   # the 64 x 64 configuration
+    "lap2d_ragged": lambda: W.laplace_2d(97, 41),           # several blocks, ragged tail
+    "lap3d_16": lambda: W.laplace_3d(16),
+    "lap3d_33": lambda: W.laplace_3d(33),
+    "spd_rand": lambda: W.spd_random(300, seed=5, density=0.05),
+    "shifted_rect": lambda: W.laplace_2d(130, 77, shift=0.3),
+}
+
+
+@pytest.mark.parametrize("variant", ["pipelined", "split", "classical"])
+@pytest.mark.parametrize("name", sorted(MATRICES))
+def test_cg_parity(name, variant):
+    a = MATRICES[name]()
+    _, b, _ = W.manufactured(a, seed=0)
+    ovar = "classical" if variant == "classical" else "pipelined"
+    ref = O.cg(a, b, tol=1e-8, maxit=5000, variant=ovar)
+    info, x, tr = solve(a, b, tol=1e-8, maxit=5000, variant=variant, flags=pk.FLAG_TRUE_RES)
+    assert info["status"] == pk.PK_OK
+    assert abs(info["iters"] - ref["iters"]) <= 2
+    k = min(20, ref["iters"] - 1)
+    np.testing.assert_allclose(tr[:k, 0], ref["alpha"][:k], rtol=1e-12, atol=0)
+    np.testing.assert_allclose(tr[:k, 1], ref["beta"][:k], rtol=1e-12, atol=0)
+    assert info["rel_res_true"] <= 1.5e-8
+    # same iteration count: x within 1e-9 of the oracle's
+    fixed = ref["iters"]
+    info2, x2, _ = solve(a, b, tol=0.0, maxit=fixed, variant=variant)
+    assert info2["status"] == pk.PK_NOT_CONVERGED and info2["iters"] == fixed
+    assert rel(x2, ref["x"]) <= 1e-9
+
+
+@pytest.mark.parametrize("loop", ["graph", "host"])
+def test_cg_loop_modes_agree_bitwise(loop):
+    a = W.laplace_2d(64)
+    _, b, _ = W.manufactured(a)
+    i1, x1, _ = solve(a, b, loop="graph")
+    i2, x2, _ = solve(a, b, loop=loop, check_every=5)
+    assert i1["iters"] == i2["iters"]
+    assert np.array_equal(x1, x2)  # deterministic reductions: bitwise reproducible
+
+
+def test_cg_launch_counts_match_the_paper():
+    """Sec. 3.1: pipelined CG needs two kernels per iteration, classical six; split three."""
+    a = W.laplace_2d(40)
+    _, b, _ = W.manufactured(a)
+    per_iter = {}
+    for variant in ("pipelined", "split", "classical"):
+        i10, _, _ = solve(a, b, tol=0.0, maxit=10, variant=variant, loop="host", check_every=1)
+        i20, _, _ = solve(a, b, tol=0.0, maxit=20, variant=variant, loop="host", check_every=1)
+        per_iter[variant] = (i20["launches"] - i10["launches"]) / 10
+    assert per_iter == {"pipelined": 2, "split": 3, "classical": 6}
+
+
+def test_cg_timing_mode_reports_kernels():
+    a = W.laplace_2d(64)
+    _, b, _ = W.manufactured(a)
+    info, _, _ = solve(a, b, tol=0.0, maxit=30, flags=pk.FLAG_TIMING)
+    assert info["kernel_count"]["spmv_dots"] == 31 and info["kernel_count"]["update"] == 30
+    assert all(v > 0 for v in info["kernel_ms"].values())
+
+
+def test_cg_edge_cases():
+    a = W.laplace_2d(8)
+    _, b, _ = W.manufactured(a)
+    # b = 0 -> x = 0, no iterations
+    info, x, _ = solve(a, np.zeros(a.n), x0=np.ones(a.n))
+    assert info["status"] == pk.PK_OK and info["iters"] == 0 and not x.any()
+    # exact initial guess -> 0 iterations
+    xs = np.linalg.solve(a.to_dense(), b)
+    info, x, _ = solve(a, b, x0=xs)
+    assert info["status"] == pk.PK_OK and info["iters"] == 0
+    # maxit = 0
+    info, _, _ = solve(a, b, maxit=0)
+    assert info["status"] == pk.PK_NOT_CONVERGED and info["iters"] == 0
+    # not SPD
+    neg = W.CSR(a.n, a.row_ptr, a.col, -a.val)
+    info, _, _ = solve(neg, b)
+    assert info["status"] == pk.PK_NOT_SPD
+    # NaN in b
+    nb = b.copy()
+    nb[5] = np.nan
+    info, _, _ = solve(a, nb)
+    assert info["status"] == pk.PK_ERR_NAN
+    # a 1 x 1 system and a 3 x 3 system (single partial block)
+    one = W.CSR(1, np.array([0, 1], np.int32), np.array([0], np.int32), np.array([4.0]))
+    info, x, _ = solve(one, np.array([2.0]))
+    assert info["status"] == pk.PK_OK and abs(x[0] - 0.5) < 1e-15 and info["iters"] == 1
+
+
+def test_cg_host_pointers_match_device():
+    a = W.laplace_3d(12)
+    _, b, _ = W.manufactured(a)
+    A = pk.CSRMatrix.from_workload(a)
+    _, xd, _ = solve(a, b, A=A)
+    xh = np.zeros(a.n)
+    info = pk.cg_solve(A, np.ascontiguousarray(b), xh)
+    assert info["status"] == pk.PK_OK
+    assert np.array_equal(xh, xd)
+
+
+def test_spmv_and_fused_dot_parity():
+    for a in (W.power_law(20_000, seed=3), W.laplace_3d(20), W.random_uniform(5000, 28, seed=1)):
+        A = pk.CSRMatrix.from_workload(a)
+        xv = W.uniform_pm1(7, a.n)
+        y = torch.zeros(a.n, dtype=torch.float64, device=DEV)
+        pk.spmv(A, dev(xv), y)
+        ref = O.spmv(a, xv)
+        absrow = W.CSR(a.n, a.row_ptr, a.col, np.abs(a.val)).matvec(np.abs(xv))
+        assert np.all(np.abs(y.cpu().numpy() - ref) <= 1e-14 * absrow + 1e-300)
+        q1 = torch.zeros_like(y)
+        q2 = torch.zeros_like(y)
+        r1 = torch.zeros(1, dtype=torch.float64, device=DEV)
+        r2 = torch.zeros(1, dtype=torch.float64, device=DEV)
+        pk.spmv_dot(A, dev(xv), q1, r1, fused=True)
+        pk.spmv_dot(A, dev(xv), q2, r2, fused=False)
+        torch.cuda.synchronize()
+        assert torch.equal(q1, q2) and torch.equal(q1, y)
+        d_ref = O.dot(xv, ref)
+        assert abs(r1.item() - d_ref) <= 1e-12 * np.dot(np.abs(xv), absrow)
+        assert r1.item() == r2.item()  # same fixed reduction order in both forms
+
+
+@pytest.mark.parametrize("k", [100, 160])
+def test_cg_full_size_3d(k):
+    """The large 3D sizes: first 20 alpha/beta against the oracle (20 oracle iterations),
+    x after 20 iterations, and the full solve's true residual."""
+    a = W.laplace_3d(k)
+    _, b, _ = W.manufactured(a)
+    ref = O.cg(a, b, tol=0.0, maxit=20, variant="pipelined")
+    A = pk.CSRMatrix.from_workload(a)
+    info, x20, tr = solve(a, b, A=A, tol=0.0, maxit=20)
+    np.testing.assert_allclose(tr[:20, 0], ref["alpha"][:20], rtol=1e-12, atol=0)
+    np.testing.assert_allclose(tr[:20, 1], ref["beta"][:20], rtol=1e-12, atol=0)
+    assert rel(x20, ref["x"]) <= 1e-9
+    info, x, _ = solve(a, b, A=A, tol=1e-8, maxit=50_000, flags=pk.FLAG_TRUE_RES)
+    assert info["status"] == pk.PK_OK and info["rel_res_true"] <= 1.5e-8
