@@ -51,7 +51,30 @@ def parse():
     ap.add_argument("--k", type=int, default=K3D, help="3D grid side of the timed workload")
     ap.add_argument("--no-sweep", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--mode", default="bench", choices=["bench", "kernels"],
+                    help="kernels: run only --iters fixed pipelined-CG iterations (profiler driver)")
+    ap.add_argument("--iters", type=int, default=30)
+    ap.add_argument("--variant", default="pipelined")
     return ap.parse_args()
+
+
+def run_kernels(args):
+    """A fixed number of CG iterations on the --k^3 Laplacian, host-driven launches: the
+    command that the committed ncu summaries under profiles/ profile."""
+    import torch
+    from paper_1410_4054_gb300 import pk
+
+    a = W.laplace_3d(args.k)
+    _, b, _ = W.manufactured(a, seed=0)
+    A = pk.CSRMatrix.from_workload(a)
+    bd = torch.from_numpy(b).cuda()
+    xd = torch.zeros(a.n, dtype=torch.float64, device="cuda")
+    info = pk.cg_solve(A, bd, xd, tol=0.0, maxit=args.iters, variant=args.variant, loop="host",
+                       check_every=args.iters)
+    torch.cuda.synchronize()
+    print(json.dumps({"mode": "kernels", "k": args.k, "n": a.n, "iters": info["iters"],
+                      "launches": info["launches"], "solve_ms": info["solve_ms"]}))
+    return 0
 
 
 def bytes_per_solve(n: int, nnz: int, iters: int) -> int:
@@ -360,6 +383,8 @@ def run_ours(args):
 
 def main():
     args = parse()
+    if args.mode == "kernels":
+        return run_kernels(args)
     if args.impl == "reference":
         return run_reference(args)
     return run_ours(args)

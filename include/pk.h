@@ -71,6 +71,8 @@ enum {
 #define PK_FLAG_TIMING 1u    /* time every kernel launch with CUDA events (host loop) and
                                 report per-kernel averages in pk_info.kernel_ms */
 #define PK_FLAG_TRUE_RES 2u  /* compute ||b - A x|| / ||b|| at exit into pk_info.rel_res_true */
+#define PK_FLAG_NO_TMA 4u    /* use the thread-per-row kernels instead of the warp-specialised
+                                bulk-copy tile kernels (for comparison) */
 
 typedef struct {
   double tol;          /* relative residual tolerance (>= 0) */
@@ -123,7 +125,7 @@ typedef struct {
   double row_mean;
   int32_t grid;              /* thread blocks of the fused kernels */
   int32_t block;             /* threads per block */
-  int32_t kernel;            /* SpMV variant: 0 thread-per-row, 1 warp-per-row */
+  int32_t kernel;            /* SpMV engine: 0 thread-per-row loads, 2 warp-specialised bulk-copy tiles */
   int32_t values_fp32_exact; /* 1 if every value is exactly representable in float32 */
 } pk_csr_stats;
 

@@ -10,9 +10,10 @@
 //                       beta_i  = alpha_i^2 <Ap_i,Ap_i>/<r_i,r_i> - 1   (Eq. (3)).
 // Every vector is read once and written once per kernel: K-CG-U moves 56 bytes per row,
 // K-CG-S 12 bytes per nonzero + 20 bytes per row.
+#include <algorithm>
 #include <cmath>
 
-#include "pk_internal.cuh"
+#include "pk_tile.cuh"
 
 namespace pk {
 
@@ -85,7 +86,7 @@ __device__ __forceinline__ void cg_alpha_beta(DevState* st, double apap, double 
 }
 
 // K-CG-S: Ap = A p with the first stage of <Ap, Ap> and <p, Ap> (Sec. 3.1, Alg. 2).
-__global__ void __launch_bounds__(kBlock) k_cg_spmv_dots(RowArgs a, const double* __restrict__ p,
+__global__ void __launch_bounds__(kBlock, 8) k_cg_spmv_dots(RowArgs a, const double* __restrict__ p,
                                                          double* __restrict__ ap) {
   if (state_done(a.st)) return;
   const int r0 = a.rowblk[blockIdx.x], r1 = a.rowblk[blockIdx.x + 1];
@@ -150,9 +151,29 @@ __global__ void __launch_bounds__(kBlock) k_cg_update(RowArgs a, double* __restr
     return;
   }
   const double alpha = __ldcg(&st->alpha), beta = __ldcg(&st->beta);
-  const int r0 = a.rowblk[blockIdx.x], r1 = a.rowblk[blockIdx.x + 1];
+  int r0, r1;
+  ew_range(a.n, r0, r1);
   double v[1] = {0.0};
-  for (int row = r0 + threadIdx.x; row < r1; row += blockDim.x) {
+  // two rows per thread with 16-byte accesses (block ranges start on a multiple of 32 rows)
+  const int pairs = (r1 - r0) >> 1;
+  for (int k = threadIdx.x; k < pairs; k += blockDim.x) {
+    const int row = r0 + 2 * k;
+    const double2 pk = ld2(p + row), xk = ld2(x + row), ak = ld2(ap + row), rk0 = ld2(r + row);
+    double2 rk, xn, pn;
+    xn.x = fma(alpha, pk.x, xk.x);
+    xn.y = fma(alpha, pk.y, xk.y);
+    rk.x = fma(-alpha, ak.x, rk0.x);
+    rk.y = fma(-alpha, ak.y, rk0.y);
+    pn.x = fma(beta, pk.x, rk.x);
+    pn.y = fma(beta, pk.y, rk.y);
+    st2(x + row, xn);
+    st2(r + row, rk);
+    st2(p + row, pn);
+    v[0] = fma(rk.x, rk.x, v[0]);
+    v[0] = fma(rk.y, rk.y, v[0]);
+  }
+  if (((r1 - r0) & 1) && threadIdx.x == 0) {
+    const int row = r1 - 1;
     const double pk = p[row];
     x[row] = fma(alpha, pk, x[row]);
     const double rk = fma(-alpha, ap[row], r[row]);
@@ -175,6 +196,121 @@ __global__ void __launch_bounds__(kBlock) k_cg_update(RowArgs a, double* __restr
       st->counter = 0;
     }
   }
+}
+
+// ---------------------------------------------------------------- warp-specialised forms
+
+// K-CG-U on the streaming tile engine: inputs p, x, Ap, r arrive in shared memory through
+// bulk copies; results are stored straight to global memory.
+__global__ void __launch_bounds__(kTileThreads, 2) k_cg_update_tma(int n, double* __restrict__ x,
+                                                                   double* __restrict__ r,
+                                                                   double* __restrict__ p,
+                                                                   const double* __restrict__ ap,
+                                                                   double* partials, DevState* st) {
+  extern __shared__ __align__(128) unsigned char smem[];
+  count_pass(st);
+  if (state_done(st)) {
+    if (blockIdx.x == 0 && threadIdx.x == 0 && st->use_cond) cudaGraphSetConditional(st->cond, 0u);
+    return;
+  }
+  const double alpha = __ldcg(&st->alpha), beta = __ldcg(&st->beta);
+  int r0, r1;
+  ew_range(n, r0, r1);
+  double v[1] = {0.0};
+  StreamIn<4> in{{p, x, ap, r}};
+  stream_tiles<4>(in, r0, r1, smem, st, [&](int row, const double2* val, int nv) {
+    const double2 pk = val[0], xk = val[1], ak = val[2], rq = val[3];
+    double2 xn, rn, pn;
+    xn.x = fma(alpha, pk.x, xk.x);
+    xn.y = fma(alpha, pk.y, xk.y);
+    rn.x = fma(-alpha, ak.x, rq.x);
+    rn.y = fma(-alpha, ak.y, rq.y);
+    pn.x = fma(beta, pk.x, rn.x);
+    pn.y = fma(beta, pk.y, rn.y);
+    if (nv == 2) {
+      st2(x + row, xn);
+      st2(r + row, rn);
+      st2(p + row, pn);
+      v[0] = fma(rn.x, rn.x, v[0]);
+      v[0] = fma(rn.y, rn.y, v[0]);
+    } else {
+      x[row] = xn.x;
+      r[row] = rn.x;
+      p[row] = pn.x;
+      v[0] = fma(rn.x, rn.x, v[0]);
+    }
+  });
+  tile_block_partials<1>(v, partials);
+  if (arrive_last(&st->counter)) {
+    double t[1];
+    final_sums<1>(partials, t);
+    if (threadIdx.x == 0) {
+      const int i = st->iter + 1;
+      st->iter = i;
+      st->rr = t[0];
+      trace_put(st, i - 1, 3, t[0]);
+      if (__ldcg(&st->timeout)) finish(st, PK_TIMEOUT);
+      else if (!isfinite(t[0])) finish(st, PK_ERR_NAN);
+      else if (t[0] <= st->thr2) finish(st, PK_OK);
+      else if (i >= st->maxit) finish(st, PK_NOT_CONVERGED);
+      st->counter = 0;
+    }
+  }
+}
+
+// K-CG-S on the CSR tile engine.
+__global__ void __launch_bounds__(kTileThreads, 2) k_cg_spmv_dots_tma(CsrTiles T,
+                                                                      const double* __restrict__ p,
+                                                                      double* __restrict__ ap,
+                                                                      double* partials, DevState* st) {
+  extern __shared__ __align__(128) unsigned char smem[];
+  if (state_done(st)) return;
+  double v[2] = {0.0, 0.0};
+  csr_tiles(T, smem, st, [&](int ra, int ja0, int ja1, int rb, int jb0, int jb1,
+                             const double* sva, const int32_t* sci) {
+    double sa, sb;
+    smem_row2(sva, sci, ja0, ja1, jb0, jb1, p, sa, sb);
+    ap[ra] = sa;
+    v[0] = fma(sa, sa, v[0]);
+    v[1] = fma(__ldg(p + ra), sa, v[1]);
+    if (rb >= 0) {
+      ap[rb] = sb;
+      v[0] = fma(sb, sb, v[0]);
+      v[1] = fma(__ldg(p + rb), sb, v[1]);
+    }
+  });
+  tile_block_partials<2>(v, partials);
+  if (arrive_last(&st->counter)) {
+    double t[2];
+    final_sums<2>(partials, t);
+    if (threadIdx.x == 0) {
+      if (__ldcg(&st->timeout)) finish(st, PK_TIMEOUT);
+      else cg_alpha_beta(st, t[0], t[1]);
+      st->counter = 0;
+    }
+  }
+}
+
+static pk_status tma_setup() {
+  static bool done = false;
+  if (!done) {
+    PK_CUDA(cudaFuncSetAttribute(k_cg_update_tma, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 stream_smem_bytes<4>()));
+    PK_CUDA(cudaFuncSetAttribute(k_cg_spmv_dots_tma, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 csr_smem_bytes()));
+    done = true;
+  }
+  return PK_OK;
+}
+
+CsrTiles csr_tiles_of(const pk_csr* A) {
+  CsrTiles t;
+  t.rp = A->rp;
+  t.ci = A->ci;
+  t.va = A->va;
+  t.tile_row = A->tile_row;
+  t.blk_tile = A->blk_tile;
+  return t;
 }
 
 // ---------------------------------------------------------------- classical CG, Alg. 1
@@ -288,6 +424,17 @@ pk_status cg_solve(pk_csr* A, const double* b, double* x, const pk_opts* o, pk_i
   if ((e = work_vec(A, 0, &r)) || (e = work_vec(A, 1, &p)) || (e = work_vec(A, 2, &ap))) return e;
   const RowArgs ra = row_args(A);
   double* xd = v.x_dev;
+  // The bulk-copy kernels read x in 16-byte units: a caller's x that is not 16-byte aligned or
+  // has odd length is iterated in a padded library copy.
+  const bool tma_engine = A->tma_ok && !(o->flags & PK_FLAG_NO_TMA);
+  double* x_copy_back = nullptr;
+  if (tma_engine && (((uintptr_t)xd & 15) || (A->n & 1))) {
+    double* xi;
+    if ((e = work_vec(A, 13, &xi))) return e;
+    PK_CUDA(cudaMemcpyAsync(xi, xd, sizeof(double) * A->n, cudaMemcpyDeviceToDevice, s));
+    x_copy_back = xd;
+    xd = xi;
+  }
   const double* bd = v.b_dev;
   Timer T;
   T.A = A;
@@ -295,6 +442,15 @@ pk_status cg_solve(pk_csr* A, const double* b, double* x, const pk_opts* o, pk_i
   T.s = s;
   int launches = 0;
   const int G = A->grid;
+  if (!A->grid_ew) {
+    // elementwise kernels run as many resident blocks as their register use allows
+    int nb = 1, sms = 1;
+    PK_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_cg_update, kBlock, 0));
+    PK_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, A->device));
+    const int64_t need = ((int64_t)A->n + 2 * kBlock - 1) / (2 * kBlock);
+    A->grid_ew = (int)std::max<int64_t>(1, std::min<int64_t>((int64_t)std::max(nb, 1) * sms, need));
+  }
+  const int Gu = A->grid_ew;
 
   // setup: r0 = b - A x0, p0 = r0, <r0,r0>, <b,b>
   if ((e = T.begin(PK_SLOT_OTHER))) return e;
@@ -303,10 +459,18 @@ pk_status cg_solve(pk_csr* A, const double* b, double* x, const pk_opts* o, pk_i
   k_zero_x<<<G, kBlock, 0, s>>>(ra, xd);
   launches += 2;
   const int variant = o->variant;
+  const bool tma = tma_engine;
+  if (tma && (e = tma_setup())) return e;
+  const CsrTiles ct = csr_tiles_of(A);
+  const int Gt = A->grid_tma, Gs = A->grid_stream;
+  double* part = A->partials;
+  DevState* dst = A->st;
+  const int n = A->n;
   if (variant == PK_VARIANT_PIPELINED || variant == PK_VARIANT_SPLIT) {
     // A p0, alpha_0, beta_0
     if ((e = T.begin(PK_SLOT_SPMV_DOTS))) return e;
-    k_cg_spmv_dots<<<G, kBlock, 0, s>>>(ra, p, ap);
+    if (tma) k_cg_spmv_dots_tma<<<Gt, kTileThreads, csr_smem_bytes(), s>>>(ct, p, ap, part, dst);
+    else k_cg_spmv_dots<<<G, kBlock, 0, s>>>(ra, p, ap);
     if ((e = T.end())) return e;
     launches += 1;
   }
@@ -319,11 +483,14 @@ pk_status cg_solve(pk_csr* A, const double* b, double* x, const pk_opts* o, pk_i
   if (variant == PK_VARIANT_PIPELINED) {
     L.kind = 1;
     L.body_kernels = 2;
+    L.ikeys[1] = tma;
     L.body = [=](cudaStream_t cs, Timer* t) {
       if (t) t->begin(PK_SLOT_UPDATE);
-      k_cg_update<<<G, kBlock, 0, cs>>>(ra, xd, r, p, ap);
+      if (tma) k_cg_update_tma<<<Gs, kTileThreads, stream_smem_bytes<4>(), cs>>>(n, xd, r, p, ap, part, dst);
+      else k_cg_update<<<Gu, kBlock, 0, cs>>>(ra, xd, r, p, ap);
       if (t) { t->end(); t->begin(PK_SLOT_SPMV_DOTS); }
-      k_cg_spmv_dots<<<G, kBlock, 0, cs>>>(ra, p, ap);
+      if (tma) k_cg_spmv_dots_tma<<<Gt, kTileThreads, csr_smem_bytes(), cs>>>(ct, p, ap, part, dst);
+      else k_cg_spmv_dots<<<G, kBlock, 0, cs>>>(ra, p, ap);
       if (t) t->end();
     };
   } else if (variant == PK_VARIANT_SPLIT) {
@@ -331,7 +498,7 @@ pk_status cg_solve(pk_csr* A, const double* b, double* x, const pk_opts* o, pk_i
     L.body_kernels = 3;
     L.body = [=](cudaStream_t cs, Timer* t) {
       if (t) t->begin(PK_SLOT_UPDATE);
-      k_cg_update<<<G, kBlock, 0, cs>>>(ra, xd, r, p, ap);
+      k_cg_update<<<Gu, kBlock, 0, cs>>>(ra, xd, r, p, ap);
       if (t) { t->end(); t->begin(PK_SLOT_SPMV); }
       k_spmv_live<<<G, kBlock, 0, cs>>>(ra, p, ap, 0);
       if (t) { t->end(); t->begin(PK_SLOT_BLAS1); }
@@ -359,6 +526,8 @@ pk_status cg_solve(pk_csr* A, const double* b, double* x, const pk_opts* o, pk_i
   }
   if ((e = run_loop(A, o, s, L, &T, &launches))) return e;
   if ((e = T.flush())) return e;
+  if (x_copy_back)
+    PK_CUDA(cudaMemcpyAsync(x_copy_back, xd, sizeof(double) * A->n, cudaMemcpyDeviceToDevice, s));
   const bool graph = o->loop == PK_LOOP_GRAPH && !T.on;
   if ((e = finish_info(A, o, info, s, v, e0, e1, launches))) return e;
   if (graph) info->launches += (int)(passes_of(A->st_host) * L.body_kernels);

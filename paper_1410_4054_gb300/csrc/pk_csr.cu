@@ -8,7 +8,7 @@
 #include <cstring>
 #include <vector>
 
-#include "pk_internal.cuh"
+#include "pk_tile.cuh"
 
 namespace pk {
 
@@ -48,7 +48,10 @@ pk_status ensure_state(pk_csr* A) {
     PK_CUDA(cudaMemset(A->st, 0, sizeof(DevState)));
     PK_CUDA(cudaMallocHost(&A->st_host, sizeof(DevState)));
     memset(A->st_host, 0, sizeof(DevState));
-    PK_CUDA(cudaMalloc(&A->partials, sizeof(double) * (size_t)kMaxDots * A->grid));
+    int sms = 1;
+    PK_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, A->device));
+    A->partial_cap = std::max(A->grid, sms * kMaxGridPerSm);
+    PK_CUDA(cudaMalloc(&A->partials, sizeof(double) * (size_t)kMaxDots * A->partial_cap));
     PK_CUDA(cudaMalloc(&A->small, sizeof(double) * 8192));
     PK_CUDA(cudaMemset(A->small, 0, sizeof(double) * 8192));
   }
@@ -254,6 +257,7 @@ pk_status finish_info(pk_csr* A, const pk_opts* o, pk_info* info, cudaStream_t s
   info->iters = h->iter;
   info->status = h->status == kRunning ? PK_NOT_CONVERGED : h->status;
   info->launches = launches;
+  if (h->timeout) info->status = PK_TIMEOUT;
   info->rel_res_est = h->bb > 0 ? std::sqrt(std::max(h->rr, 0.0) / h->bb) : 0.0;
   info->rel_res_true = -1.0;
   if (o->flags & PK_FLAG_TRUE_RES) {
@@ -367,6 +371,49 @@ pk_status pk_csr_create(int64_t n, int64_t nnz, const int32_t* row_ptr, const in
   }
   rb[A->grid] = (int32_t)n;
 
+  // warp-specialised CSR tiles: 2 blocks per SM, nnz-balanced block ranges, tiles of at most
+  // kTileRows rows and kTileNnz nonzeros
+  std::vector<int32_t> tile_row, blk_tile;
+  A->tma_ok = 1;
+  A->grid_tma = (int)std::max<int64_t>(1, std::min<int64_t>((int64_t)sms * 2, (n + kTileRows - 1) / kTileRows));
+  {
+    const int Gt = A->grid_tma;
+    std::vector<int32_t> tb(Gt + 1);
+    tb[0] = 0;
+    for (int b = 1; b < Gt; ++b) {
+      const double target = wtot * b / Gt;
+      int64_t lo = tb[b - 1], hi = n;
+      while (lo < hi) {
+        const int64_t mid = (lo + hi) / 2;
+        if ((double)rp[mid] + 2.0 * (double)mid < target) lo = mid + 1; else hi = mid;
+      }
+      tb[b] = (int32_t)std::max<int64_t>((lo / 32) * 32, tb[b - 1]);
+    }
+    tb[Gt] = (int32_t)n;
+    blk_tile.push_back(0);
+    for (int b = 0; b < Gt && A->tma_ok; ++b) {
+      int64_t R = tb[b];
+      while (R < tb[b + 1]) {
+        int64_t R1 = std::min<int64_t>(R + kTileRows, tb[b + 1]);
+        if (rp[R1] - rp[R] > kTileNnz) {
+          int64_t lo = R, hi = R1;  // largest R1 with rp[R1] - rp[R] <= kTileNnz
+          while (lo < hi) {
+            const int64_t mid = (lo + hi + 1) / 2;
+            if (rp[mid] - rp[R] <= kTileNnz) lo = mid; else hi = mid - 1;
+          }
+          R1 = lo;
+        }
+        if (R1 == R) { A->tma_ok = 0; break; }  // a single row longer than a tile
+        tile_row.push_back((int32_t)R);
+        R = R1;
+      }
+      blk_tile.push_back((int32_t)tile_row.size());
+    }
+    tile_row.push_back((int32_t)n);
+    A->ntiles = (int)tile_row.size() - 1;
+  }
+  A->grid_stream = (int)std::max<int64_t>(1, std::min<int64_t>((int64_t)sms * 2, (n + 511) / 512));
+
   auto fail = [&](pk_status e) { pk_csr_destroy(A); return e; };
   cudaError_t e;
   if ((e = cudaStreamCreateWithFlags(&A->cap_stream, cudaStreamNonBlocking)) != cudaSuccess)
@@ -385,6 +432,12 @@ pk_status pk_csr_create(int64_t n, int64_t nnz, const int32_t* row_ptr, const in
     if ((e = cudaMemcpyAsync(A->va, va.data(), sizeof(double) * nnz, cudaMemcpyHostToDevice, s)) != cudaSuccess) return fail(cuda_fail(e, "copy val"));
   }
   if ((e = cudaMemcpyAsync(A->rowblk, rb.data(), sizeof(int32_t) * (A->grid + 1), cudaMemcpyHostToDevice, s)) != cudaSuccess) return fail(cuda_fail(e, "copy rowblk"));
+  if (A->tma_ok) {
+    if ((e = cudaMalloc(&A->tile_row, sizeof(int32_t) * tile_row.size())) != cudaSuccess) return fail(cuda_fail(e, "cudaMalloc(tiles)"));
+    if ((e = cudaMalloc(&A->blk_tile, sizeof(int32_t) * blk_tile.size())) != cudaSuccess) return fail(cuda_fail(e, "cudaMalloc(tiles)"));
+    if ((e = cudaMemcpyAsync(A->tile_row, tile_row.data(), sizeof(int32_t) * tile_row.size(), cudaMemcpyHostToDevice, s)) != cudaSuccess) return fail(cuda_fail(e, "copy tiles"));
+    if ((e = cudaMemcpyAsync(A->blk_tile, blk_tile.data(), sizeof(int32_t) * blk_tile.size(), cudaMemcpyHostToDevice, s)) != cudaSuccess) return fail(cuda_fail(e, "copy tiles"));
+  }
   if ((e = cudaStreamSynchronize(s)) != cudaSuccess) return fail(cuda_fail(e, "sync"));
 
   pk_csr_stats& st = A->stats;
@@ -395,7 +448,7 @@ pk_status pk_csr_create(int64_t n, int64_t nnz, const int32_t* row_ptr, const in
   st.row_mean = n ? (double)nnz / (double)n : 0.0;
   st.grid = A->grid;
   st.block = kBlock;
-  st.kernel = 0;
+  st.kernel = A->tma_ok ? 2 : 0;
   st.values_fp32_exact = fp32_exact;
   pk_status ps = ensure_state(A);
   if (ps) return fail(ps);
@@ -422,6 +475,8 @@ pk_status pk_csr_destroy(pk_csr* A) {
   if (A->va) cudaFree(A->va);
   if (A->va32) cudaFree(A->va32);
   if (A->rowblk) cudaFree(A->rowblk);
+  if (A->tile_row) cudaFree(A->tile_row);
+  if (A->blk_tile) cudaFree(A->blk_tile);
   if (A->cap_stream) cudaStreamDestroy(A->cap_stream);
   delete A;
   return PK_OK;

@@ -17,7 +17,7 @@
 namespace pk {
 
 constexpr int kBlock = 256;        // threads per block of the fused kernels
-constexpr int kMaxGridPerSm = 4;   // resident blocks per SM used for the persistent grid
+constexpr int kMaxGridPerSm = 8;   // resident blocks per SM used for the persistent grid
 constexpr int kMaxDots = 64;       // partial-sum slots per block (GMRES needs up to m+1)
 constexpr int kRunning = -1;       // DevState::status while iterating
 
@@ -36,7 +36,8 @@ struct DevState {
   unsigned int counter;   // last-block arrival counter
   int32_t use_cond;       // kernels run inside a conditional WHILE graph node
   cudaGraphConditionalHandle cond;
-  int32_t pad[2];
+  int32_t timeout;        // a bounded device-side wait ran out
+  int32_t pad[1];
 };
 
 // Loads that bypass L1 (the value was written by another block or an earlier kernel).
@@ -90,7 +91,7 @@ __device__ __forceinline__ bool arrive_last(unsigned int* counter) {
 // fixed order (strided per thread, then the xor tree), broadcast to every thread.
 template <int NV>
 __device__ __forceinline__ void final_sums(const double* partials, double (&out)[NV]) {
-  __shared__ double sm[NV][kBlock / 32];
+  __shared__ double sm[NV][32];
   const int G = gridDim.x;
   double v[NV];
 #pragma unroll
@@ -126,6 +127,7 @@ __device__ __forceinline__ void finish(DevState* st, int status) {
   if (st->use_cond) cudaGraphSetConditional(st->cond, 0u);
 }
 
+// Host-side maxima of the tile engine (defined in pk_tile.cuh).
 // Common kernel arguments of the row-parallel kernels.
 struct RowArgs {
   int32_t n;
@@ -160,6 +162,15 @@ struct pk_csr {
   float* va32 = nullptr;
   int32_t* rowblk = nullptr;  // grid + 1
   int grid = 1;
+  int grid_ew = 0;             // grid of the elementwise update kernels (0 = not chosen yet)
+  // warp-specialised CSR tiles (cp.async.bulk pipeline); tma_ok = 0 if a row is too long
+  int tma_ok = 0;
+  int grid_tma = 0;
+  int32_t* tile_row = nullptr;  // ntiles + 1
+  int32_t* blk_tile = nullptr;  // grid_tma + 1
+  int ntiles = 0;
+  int grid_stream = 0;          // grid of the streaming (vector-only) tile kernels
+  int partial_cap = 0;         // blocks the partials buffer can hold
   pk_csr_stats stats{};
   cudaStream_t cap_stream = nullptr;  // private stream used for graph capture
   // cached work memory
@@ -237,12 +248,53 @@ pk_status finish_info(pk_csr* A, const pk_opts* o, pk_info* info, cudaStream_t s
 namespace pk {
 
 // y_row = sum_j A[row, j] x[j], left to right over the row (Sec. 2.2 CSR product).
+// The row is walked in chunks of 4: all value / column loads of a chunk are issued before
+// the dependent gathers of x, so a thread keeps several independent loads in flight instead
+// of one load -> gather -> FMA round trip per nonzero.  The summation order is unchanged.
 __device__ __forceinline__ double csr_row(const RowArgs& a, const double* __restrict__ x, int row) {
-  const int j0 = __ldg(a.rp + row), j1 = __ldg(a.rp + row + 1);
+  int j = __ldg(a.rp + row);
+  const int j1 = __ldg(a.rp + row + 1);
   double s = 0.0;
-  for (int j = j0; j < j1; ++j) s = fma(__ldg(a.va + j), __ldg(x + __ldg(a.ci + j)), s);
+  for (; j + 4 <= j1; j += 4) {
+    int c[4];
+    double v[4], xv[4];
+#pragma unroll
+    for (int k = 0; k < 4; ++k) { c[k] = __ldg(a.ci + j + k); v[k] = __ldg(a.va + j + k); }
+#pragma unroll
+    for (int k = 0; k < 4; ++k) xv[k] = __ldg(x + c[k]);
+#pragma unroll
+    for (int k = 0; k < 4; ++k) s = fma(v[k], xv[k], s);
+  }
+  if (j < j1) {
+    int c[3];
+    double v[3], xv[3];
+    const int m = j1 - j;  // 1..3
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+      c[k] = k < m ? __ldg(a.ci + j + k) : 0;
+      v[k] = k < m ? __ldg(a.va + j + k) : 0.0;
+    }
+#pragma unroll
+    for (int k = 0; k < 3; ++k) xv[k] = k < m ? __ldg(x + c[k]) : 0.0;
+#pragma unroll
+    for (int k = 0; k < 3; ++k)
+      if (k < m) s = fma(v[k], xv[k], s);
+  }
   return s;
 }
+
+// Rows of this block for elementwise kernels: equal chunks (multiples of 32 rows) over the
+// launch grid, independent of the SpMV schedule.
+__device__ __forceinline__ void ew_range(int n, int& r0, int& r1) {
+  const int G = gridDim.x;
+  const int chunk = (int)((((long long)n + G - 1) / G + 31) & ~31LL);
+  const long long lo = (long long)blockIdx.x * chunk;
+  r0 = (int)(lo < n ? lo : n);
+  r1 = (int)(lo + chunk < n ? lo + chunk : n);
+}
+
+__device__ __forceinline__ double2 ld2(const double* p) { return *reinterpret_cast<const double2*>(p); }
+__device__ __forceinline__ void st2(double* p, double2 v) { *reinterpret_cast<double2*>(p) = v; }
 
 __device__ __forceinline__ bool state_done(const DevState* st) { return __ldcg(&st->done) != 0; }
 

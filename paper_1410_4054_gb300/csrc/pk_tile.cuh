@@ -1,0 +1,390 @@
+// Warp-specialised tile engine for the bandwidth-bound fused kernels (sm_100+ / sm_103a).
+//
+// On GB300 the FP64 pipe (about 2 FMA per clock per SM) is as much of a bound as HBM for the
+// fused Krylov kernels, and a warp that waits for its own loads cannot feed the FP64 pipe.
+// Here one producer warp per block streams the block's data into a ring of shared-memory
+// stages with bulk asynchronous copies (cp.async.bulk, completion counted on an mbarrier)
+// while eight consumer warps do the floating-point work on stages that have already arrived,
+// so memory traffic and FP64 work overlap.  Every wait on an mbarrier is bounded: after
+// 2 s the kernel records PK_TIMEOUT and returns.
+#pragma once
+
+#include "pk_internal.cuh"
+
+namespace pk {
+
+constexpr int kConsumerWarps = 8;
+constexpr int kConsumers = kConsumerWarps * 32;        // 256 consumer threads
+constexpr int kTileThreads = kConsumers + 32;          // + one producer warp
+constexpr uint64_t kWaitNs = 2000000000ull;            // 2 s bound on every mbarrier wait
+
+__device__ __forceinline__ uint32_t smem_addr(const void* p) {
+  return (uint32_t)__cvta_generic_to_shared(p);
+}
+
+__device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_addr(bar)), "r"(count) : "memory");
+}
+
+__device__ __forceinline__ void mbar_fence_init() {
+  asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+}
+
+__device__ __forceinline__ void mbar_expect_tx(uint64_t* bar, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_addr(bar)),
+               "r"(bytes)
+               : "memory");
+}
+
+__device__ __forceinline__ void mbar_arrive(uint64_t* bar) {
+  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_addr(bar)) : "memory");
+}
+
+__device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n\t.reg .pred p;\n\t"
+      "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+      "selp.u32 %0, 1, 0, p;\n\t}"
+      : "=r"(ok)
+      : "r"(smem_addr(bar)), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+
+__device__ __forceinline__ uint64_t global_ns() {
+  uint64_t t;
+  asm volatile("mov.u64 %0, %globaltimer;" : "=l"(t));
+  return t;
+}
+
+// Bounded wait on phase `parity`: false once about kWaitNs nanoseconds have passed.
+__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity) {
+  if (mbar_try_wait(bar, parity)) return true;
+  const uint64_t t0 = global_ns();
+  for (;;) {
+    if (mbar_try_wait(bar, parity)) return true;
+    if (global_ns() - t0 > kWaitNs) return false;
+  }
+}
+
+// Bulk copy global -> shared (16-byte aligned addresses, size a multiple of 16), completion
+// signalled on `bar` as transaction bytes.
+__device__ __forceinline__ void bulk_load(void* dst, const void* src, uint32_t bytes, uint64_t* bar) {
+  asm volatile(
+      "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+          smem_addr(dst)),
+      "l"(src), "r"(bytes), "r"(smem_addr(bar))
+      : "memory");
+}
+
+// L2 policy that evicts the streamed data first (the matrix is read once per pass and does not
+// fit in L2; the gathered vector should stay there).
+__device__ __forceinline__ uint64_t l2_evict_first() {
+  uint64_t pol;
+  asm volatile("createpolicy.fractional.L2::evict_first.b64 %0, 1.0;" : "=l"(pol));
+  return pol;
+}
+
+__device__ __forceinline__ void bulk_load_hint(void* dst, const void* src, uint32_t bytes,
+                                               uint64_t* bar, uint64_t pol) {
+  asm volatile(
+      "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes.L2::cache_hint [%0], [%1], "
+      "%2, [%3], %4;" ::"r"(smem_addr(dst)),
+      "l"(src), "r"(bytes), "r"(smem_addr(bar)), "l"(pol)
+      : "memory");
+}
+
+// Record a timed-out wait (first writer wins) so the host sees PK_TIMEOUT.
+__device__ __forceinline__ void report_timeout(DevState* st) {
+  atomicExch(&st->timeout, 1);
+}
+
+// Reduction of NV values over the consumer threads of a tile block (the producer warp
+// contributes zeros), written to partials[k * gridDim.x + blockIdx.x].
+template <int NV>
+__device__ __forceinline__ void tile_block_partials(double (&v)[NV], double* partials) {
+  __shared__ double sm[NV][kTileThreads / 32];
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+#pragma unroll
+  for (int k = 0; k < NV; ++k) v[k] = warp_sum(v[k]);
+  if (lane == 0) {
+#pragma unroll
+    for (int k = 0; k < NV; ++k) sm[k][warp] = v[k];
+  }
+  __syncthreads();
+  if (warp == 0) {
+#pragma unroll
+    for (int k = 0; k < NV; ++k) {
+      double t = lane < kTileThreads / 32 ? sm[k][lane] : 0.0;
+      t = warp_sum(t);
+      if (lane == 0) partials[(size_t)k * gridDim.x + blockIdx.x] = t;
+    }
+  }
+}
+
+// ----------------------------------------------------------------------------------------
+// Streaming tiles: NIN length-n float64 vectors, TROWS rows per tile, NST stages.
+// Rows of block b: equal chunks of the grid (multiples of 32 rows).
+
+template <int NIN>
+struct StreamIn {
+  const double* v[NIN];
+};
+
+constexpr int kStreamRows = 512;  // rows per streaming tile: 2 per consumer thread
+constexpr int kStreamStages = 5;
+
+template <int NIN>
+constexpr int stream_smem_bytes() {
+  return kStreamStages * NIN * kStreamRows * 8 + 2 * kStreamStages * 8;
+}
+
+// Runs the streaming pipeline; `body(row, vals, nvalid)` is called by consumer threads for
+// row pairs (vals[k] = double2 of input k at rows row, row+1; nvalid = 1 or 2).
+// Returns false in threads that saw a timeout.
+template <int NIN, class Body>
+__device__ __forceinline__ bool stream_tiles(const StreamIn<NIN>& in, int r0, int r1,
+                                             unsigned char* smem, DevState* st, Body&& body) {
+  double* buf = reinterpret_cast<double*>(smem);
+  uint64_t* full = reinterpret_cast<uint64_t*>(smem + kStreamStages * NIN * kStreamRows * 8);
+  uint64_t* empty = full + kStreamStages;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  if (threadIdx.x == 0) {
+    for (int s = 0; s < kStreamStages; ++s) {
+      mbar_init(&full[s], 1);
+      mbar_init(&empty[s], kConsumerWarps);
+    }
+    mbar_fence_init();
+  }
+  __syncthreads();
+  const int ntiles = r1 > r0 ? (r1 - r0 + kStreamRows - 1) / kStreamRows : 0;
+  bool ok = true;
+  if (warp == kConsumerWarps) {
+    // producer warp: one elected lane issues the copies
+    if (lane == 0) {
+      for (int t = 0; t < ntiles; ++t) {
+        const int s = t % kStreamStages;
+        const int use = t / kStreamStages;
+        if (use > 0 && !mbar_wait(&empty[s], (use - 1) & 1)) { ok = false; report_timeout(st); break; }
+        const int row0 = r0 + t * kStreamRows;
+        const int rows = min(kStreamRows, r1 - row0);
+        const uint32_t bytes = (uint32_t)(((rows + 1) & ~1) * 8);  // whole 16-byte units
+        mbar_expect_tx(&full[s], bytes * NIN);
+#pragma unroll
+        for (int k = 0; k < NIN; ++k)
+          bulk_load(buf + ((size_t)s * NIN + k) * kStreamRows, in.v[k] + row0, bytes, &full[s]);
+      }
+      // drain: wait (bounded) until the copies this block issued have landed
+      for (int t = max(0, ntiles - kStreamStages); t < ntiles && ok; ++t)
+        if (!mbar_wait(&full[t % kStreamStages], (t / kStreamStages) & 1)) { ok = false; report_timeout(st); }
+    }
+    return ok;
+  }
+  // consumer warps
+  for (int t = 0; t < ntiles; ++t) {
+    const int s = t % kStreamStages;
+    if (!mbar_wait(&full[s], (t / kStreamStages) & 1)) { report_timeout(st); return false; }
+    const int row0 = r0 + t * kStreamRows;
+    const int rows = min(kStreamRows, r1 - row0);
+    const int i = 2 * threadIdx.x;  // consumer thread -> row pair
+    if (i < rows) {
+      double2 vals[NIN];
+#pragma unroll
+      for (int k = 0; k < NIN; ++k)
+        vals[k] = *reinterpret_cast<const double2*>(buf + ((size_t)s * NIN + k) * kStreamRows + i);
+      body(row0 + i, vals, min(2, rows - i));
+    }
+    __syncwarp();
+    if (lane == 0) mbar_arrive(&empty[s]);
+  }
+  return true;
+}
+
+// ----------------------------------------------------------------------------------------
+// CSR tiles: each tile holds <= kTileRows rows and <= kTileNnz nonzeros; the producer copies
+// the tile's row pointers, values and column indices (16-byte aligned windows).
+
+constexpr int kTileRows = 512;       // two rows per consumer thread
+constexpr int kTileNnz = 4096;
+constexpr int kCsrStages = 2;
+constexpr int kRpWords = kTileRows + 8;       // ints, incl. alignment slack
+constexpr int kVaWords = kTileNnz + 2;        // doubles
+constexpr int kCiWords = kTileNnz + 8;        // ints (window rounded out to 16 bytes on both ends)
+constexpr int kStageBytes = ((kRpWords * 4 + 15) & ~15) + kVaWords * 8 + ((kCiWords * 4 + 15) & ~15);
+
+constexpr int csr_smem_bytes() { return kCsrStages * kStageBytes + 2 * kCsrStages * 8 + kCsrStages * 8; }
+
+struct CsrTiles {
+  const int32_t* rp;
+  const int32_t* ci;
+  const double* va;
+  const int32_t* tile_row;  // row start of every tile (global tile list), plus n at the end
+  const int32_t* blk_tile;  // tiles of block b: [blk_tile[b], blk_tile[b+1])
+};
+
+// Runs the CSR pipeline.  Consumer thread t handles rows R0 + t and R0 + t + 256 of every
+// tile together: `rows_fn(ra, ja0, ja1, rb, jb0, jb1, sva, sci)` receives both rows (rb = -1
+// if the tile has no second row for this thread) and their nonzero windows in shared memory
+// (sva/sci are offset so that entry j is sva[j], sci[j]).
+template <class RowFn>
+__device__ __forceinline__ bool csr_tiles(const CsrTiles& T, unsigned char* smem, DevState* st,
+                                          RowFn&& row_fn) {
+  uint64_t* full = reinterpret_cast<uint64_t*>(smem + kCsrStages * kStageBytes);
+  uint64_t* empty = full + kCsrStages;
+  int2* meta = reinterpret_cast<int2*>(empty + kCsrStages);  // tile rows [R0, R1) per stage
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  if (threadIdx.x == 0) {
+    for (int s = 0; s < kCsrStages; ++s) {
+      mbar_init(&full[s], 1);
+      mbar_init(&empty[s], kConsumerWarps);
+    }
+    mbar_fence_init();
+  }
+  __syncthreads();
+  const int t0 = T.blk_tile[blockIdx.x], t1 = T.blk_tile[blockIdx.x + 1];
+  const int ntiles = t1 - t0;
+  auto stage_rp = [&](int s) { return reinterpret_cast<int32_t*>(smem + (size_t)s * kStageBytes); };
+  auto stage_va = [&](int s) {
+    return reinterpret_cast<double*>(smem + (size_t)s * kStageBytes + ((kRpWords * 4 + 15) & ~15));
+  };
+  auto stage_ci = [&](int s) {
+    return reinterpret_cast<int32_t*>(smem + (size_t)s * kStageBytes + ((kRpWords * 4 + 15) & ~15) +
+                                      kVaWords * 8);
+  };
+  bool ok = true;
+  if (warp == kConsumerWarps) {
+    // producer warp: lanes prefetch tile bounds 32 tiles at a time, lane 0 issues copies
+    int issued = 0;
+    const uint64_t pol = l2_evict_first();
+    for (int base = 0; base < ntiles && ok; base += 32) {
+      const int tt = t0 + base + lane;
+      int R0 = 0, R1 = 0, z0 = 0, z1 = 0;
+      if (tt < t1) {
+        R0 = __ldg(T.tile_row + tt);
+        R1 = __ldg(T.tile_row + tt + 1);
+        z0 = __ldg(T.rp + R0);
+        z1 = __ldg(T.rp + R1);
+      }
+      const int cnt = min(32, ntiles - base);
+      for (int q = 0; q < cnt; ++q) {
+        const int a0 = __shfl_sync(0xffffffffu, R0, q), a1 = __shfl_sync(0xffffffffu, R1, q);
+        const int b0 = __shfl_sync(0xffffffffu, z0, q), b1 = __shfl_sync(0xffffffffu, z1, q);
+        if (lane == 0) {
+          const int t = base + q;
+          const int s = t % kCsrStages;
+          const int use = t / kCsrStages;
+          if (use > 0 && !mbar_wait(&empty[s], (use - 1) & 1)) { ok = false; report_timeout(st); }
+          if (ok) {
+            const int rs = a0 & ~3, re = (a1 + 1 + 3) & ~3;    // row pointers a0..a1
+            const int vs = b0 & ~1, ve = (b1 + 1) & ~1;        // values b0..b1-1
+            const int cs = b0 & ~3, ce = (b1 + 3) & ~3;        // columns b0..b1-1
+            const uint32_t nrp = (uint32_t)(re - rs) * 4, nva = (uint32_t)(ve - vs) * 8,
+                           nci = (uint32_t)(ce - cs) * 4;
+            meta[s] = make_int2(a0, a1);  // published by the arrive below (release)
+            mbar_expect_tx(&full[s], nrp + nva + nci);
+            bulk_load_hint(stage_rp(s), T.rp + rs, nrp, &full[s], pol);
+            if (nva) bulk_load_hint(stage_va(s), T.va + vs, nva, &full[s], pol);
+            if (nci) bulk_load_hint(stage_ci(s), T.ci + cs, nci, &full[s], pol);
+            issued = t + 1;
+          }
+        }
+        ok = __shfl_sync(0xffffffffu, ok, 0);
+        if (!ok) break;
+      }
+    }
+    if (lane == 0) {
+      for (int t = max(0, issued - kCsrStages); t < issued; ++t)
+        if (!mbar_wait(&full[t % kCsrStages], (t / kCsrStages) & 1)) { report_timeout(st); break; }
+    }
+    return ok;
+  }
+  for (int t = 0; t < ntiles; ++t) {
+    const int s = t % kCsrStages;
+    if (!mbar_wait(&full[s], (t / kCsrStages) & 1)) { report_timeout(st); return false; }
+    const int2 m = meta[s];
+    const int R0 = m.x, R1 = m.y;
+    const int ra = R0 + (int)threadIdx.x;
+    if (ra < R1) {
+      const int32_t* srp = stage_rp(s) - (R0 & ~3);
+      const int z0 = srp[R0];
+      const int vs = z0 & ~1;  // the window of this tile starts at the first row's nonzeros
+      const int cs = z0 & ~3;
+      const int rb = ra + kConsumers < R1 ? ra + kConsumers : -1;
+      const int jb0 = rb >= 0 ? srp[rb] : 0, jb1 = rb >= 0 ? srp[rb + 1] : 0;
+      row_fn(ra, srp[ra], srp[ra + 1], rb, jb0, jb1, stage_va(s) - vs, stage_ci(s) - cs);
+    }
+    __syncwarp();
+    if (lane == 0) mbar_arrive(&empty[s]);
+  }
+  return true;
+}
+
+// Two row products from a shared-memory window.  Each pass loads up to 8 entries of both
+// rows and issues all their gathers before the FMAs, so a thread keeps up to 16 gathers in
+// flight; each row is still summed left to right.
+__device__ __forceinline__ void smem_row2(const double* sva, const int32_t* sci, int ja, int ja1,
+                                          int jb, int jb1, const double* __restrict__ x,
+                                          double& sa, double& sb) {
+  sa = 0.0;
+  sb = 0.0;
+  for (;;) {
+    const int ma = min(8, ja1 - ja), mb = min(8, jb1 - jb);
+    if (ma <= 0 && mb <= 0) break;
+    int ca[8], cb[8];
+    double va[8], vb[8], xa[8], xb[8];
+#pragma unroll
+    for (int k = 0; k < 8; ++k) {
+      ca[k] = k < ma ? sci[ja + k] : 0;
+      va[k] = k < ma ? sva[ja + k] : 0.0;
+      cb[k] = k < mb ? sci[jb + k] : 0;
+      vb[k] = k < mb ? sva[jb + k] : 0.0;
+    }
+#pragma unroll
+    for (int k = 0; k < 8; ++k) {
+      xa[k] = k < ma ? __ldg(x + ca[k]) : 0.0;
+      xb[k] = k < mb ? __ldg(x + cb[k]) : 0.0;
+    }
+#pragma unroll
+    for (int k = 0; k < 8; ++k) {
+      if (k < ma) sa = fma(va[k], xa[k], sa);
+      if (k < mb) sb = fma(vb[k], xb[k], sb);
+    }
+    ja += ma > 0 ? ma : 0;
+    jb += mb > 0 ? mb : 0;
+  }
+}
+
+// Row product from a shared-memory window, chunked like csr_row (same summation order).
+__device__ __forceinline__ double smem_row(const double* sva, const int32_t* sci, int j, int j1,
+                                           const double* __restrict__ x) {
+  double s = 0.0;
+  for (; j + 4 <= j1; j += 4) {
+    int c[4];
+    double v[4], xv[4];
+#pragma unroll
+    for (int k = 0; k < 4; ++k) { c[k] = sci[j + k]; v[k] = sva[j + k]; }
+#pragma unroll
+    for (int k = 0; k < 4; ++k) xv[k] = __ldg(x + c[k]);
+#pragma unroll
+    for (int k = 0; k < 4; ++k) s = fma(v[k], xv[k], s);
+  }
+  if (j < j1) {
+    const int m = j1 - j;
+    int c[3];
+    double v[3], xv[3];
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+      c[k] = k < m ? sci[j + k] : 0;
+      v[k] = k < m ? sva[j + k] : 0.0;
+    }
+#pragma unroll
+    for (int k = 0; k < 3; ++k) xv[k] = k < m ? __ldg(x + c[k]) : 0.0;
+#pragma unroll
+    for (int k = 0; k < 3; ++k)
+      if (k < m) s = fma(v[k], xv[k], s);
+  }
+  return s;
+}
+
+}  // namespace pk

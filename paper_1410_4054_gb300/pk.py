@@ -24,6 +24,7 @@ PRECISIONS = {"fp64": 0, "mixed": 1}
 LOOPS = {"graph": 0, "host": 1}
 FLAG_TIMING = 1
 FLAG_TRUE_RES = 2
+FLAG_NO_TMA = 4
 SLOTS = ["spmv_dots", "update", "multidot", "ortho", "spmv", "blas1", "other"]
 MAX_SLOTS = 8
 

@@ -174,3 +174,33 @@ def test_cg_full_size_3d(k):
     assert rel(x20, ref["x"]) <= 1e-9
     info, x, _ = solve(a, b, A=A, tol=1e-8, maxit=50_000, flags=pk.FLAG_TRUE_RES)
     assert info["status"] == pk.PK_OK and info["rel_res_true"] <= 1.5e-8
+
+
+@pytest.mark.parametrize("name", ["lap2d_64", "lap3d_33", "spd_rand", "lap2d_ragged"])
+def test_cg_tile_engine_matches_row_kernels(name):
+    """The warp-specialised bulk-copy kernels and the thread-per-row kernels agree to the
+    parity bars (their reductions differ only in block partitioning)."""
+    a = MATRICES[name]()
+    _, b, _ = W.manufactured(a, seed=1)
+    A = pk.CSRMatrix.from_workload(a)
+    assert A.stats()["kernel"] == 2
+    i1, x1, t1 = solve(a, b, A=A)
+    i2, x2, t2 = solve(a, b, A=A, flags=pk.FLAG_NO_TMA)
+    assert abs(i1["iters"] - i2["iters"]) <= 2
+    k = min(20, i1["iters"] - 1)
+    np.testing.assert_allclose(t1[:k, :2], t2[:k, :2], rtol=1e-12)
+    assert rel(x1, x2) < 1e-7
+
+
+def test_cg_unaligned_and_odd_length_x():
+    """x that is not 16-byte aligned, and odd n, go through a padded library copy."""
+    a = W.laplace_2d(33, 31)  # n = 1023, odd
+    _, b, _ = W.manufactured(a)
+    A = pk.CSRMatrix.from_workload(a)
+    _, x_ref, _ = solve(a, b, A=A)
+    buf = torch.zeros(a.n + 1, dtype=torch.float64, device=DEV)
+    xv = buf[1:]  # 8-byte offset
+    info = pk.cg_solve(A, dev(b), xv)
+    torch.cuda.synchronize()
+    assert info["status"] == pk.PK_OK
+    assert np.array_equal(xv.cpu().numpy(), x_ref) and buf[0].item() == 0.0
