@@ -209,17 +209,18 @@ __global__ void __launch_bounds__(kTileThreads, 2) k_cg_update_tma(int n, double
                                                                    double* partials, DevState* st) {
   extern __shared__ __align__(128) unsigned char smem[];
   count_pass(st);
-  if (state_done(st)) {
-    if (blockIdx.x == 0 && threadIdx.x == 0 && st->use_cond) cudaGraphSetConditional(st->cond, 0u);
-    return;
-  }
-  const double alpha = __ldcg(&st->alpha), beta = __ldcg(&st->beta);
   int r0, r1;
   ew_range(n, r0, r1);
   double v[1] = {0.0};
-  StreamIn<4> in{{p, x, ap, r}};
-  stream_tiles<4>(in, r0, r1, smem, st, [&](int row, const double2* val, int nv) {
-    const double2 pk = val[0], xk = val[1], ak = val[2], rq = val[3];
+  double alpha = 0.0, beta = 0.0;
+  // x and r do not depend on the preceding K-CG-S: prefetched before the dependency wait
+  StreamIn<4> in{{x, r, p, ap}};
+  const bool live = stream_tiles<4, 2>(in, r0, r1, smem, st, [&]() {
+    alpha = __ldcg(&st->alpha);
+    beta = __ldcg(&st->beta);
+    return !state_done(st);
+  }, [&](int row, const double2* val, int nv) {
+    const double2 xk = val[0], rq = val[1], pk = val[2], ak = val[3];
     double2 xn, rn, pn;
     xn.x = fma(alpha, pk.x, xk.x);
     xn.y = fma(alpha, pk.y, xk.y);
@@ -240,6 +241,12 @@ __global__ void __launch_bounds__(kTileThreads, 2) k_cg_update_tma(int n, double
       v[0] = fma(rn.x, rn.x, v[0]);
     }
   });
+  griddep_trigger();
+  if (!__syncthreads_or(threadIdx.x < kConsumers && live)) {
+    // the solve had finished before this launch: only clear the loop condition
+    if (blockIdx.x == 0 && threadIdx.x == 0 && st->use_cond) cudaGraphSetConditional(st->cond, 0u);
+    return;
+  }
   tile_block_partials<1>(v, partials);
   if (arrive_last(&st->counter)) {
     double t[1];
@@ -264,10 +271,10 @@ __global__ void __launch_bounds__(kTileThreads, 2) k_cg_spmv_dots_tma(CsrTiles T
                                                                       double* __restrict__ ap,
                                                                       double* partials, DevState* st) {
   extern __shared__ __align__(128) unsigned char smem[];
-  if (state_done(st)) return;
   double v[2] = {0.0, 0.0};
-  csr_tiles(T, smem, st, [&](int ra, int ja0, int ja1, int rb, int jb0, int jb1,
-                             const double* sva, const int32_t* sci) {
+  const bool live = csr_tiles(T, smem, st, [&]() { return !state_done(st); },
+                              [&](int ra, int ja0, int ja1, int rb, int jb0, int jb1,
+                                  const double* sva, const int32_t* sci) {
     double sa, sb;
     smem_row2(sva, sci, ja0, ja1, jb0, jb1, p, sa, sb);
     ap[ra] = sa;
@@ -279,6 +286,8 @@ __global__ void __launch_bounds__(kTileThreads, 2) k_cg_spmv_dots_tma(CsrTiles T
       v[1] = fma(__ldg(p + rb), sb, v[1]);
     }
   });
+  griddep_trigger();
+  if (!__syncthreads_or(threadIdx.x < kConsumers && live)) return;
   tile_block_partials<2>(v, partials);
   if (arrive_last(&st->counter)) {
     double t[2];
@@ -289,6 +298,24 @@ __global__ void __launch_bounds__(kTileThreads, 2) k_cg_spmv_dots_tma(CsrTiles T
       st->counter = 0;
     }
   }
+}
+
+// Launch with the programmatic-stream-serialization attribute: the kernel may start while
+// the preceding kernel of the stream finishes; it orders itself with griddep_wait().
+template <typename... KArgs, typename... Args>
+static void launch_pdl(void (*kern)(KArgs...), int grid, int block, size_t smem, cudaStream_t s,
+                       Args... args) {
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3(grid);
+  cfg.blockDim = dim3(block);
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = s;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  attr[0].val.programmaticStreamSerializationAllowed = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  cudaLaunchKernelEx(&cfg, kern, static_cast<KArgs>(args)...);
 }
 
 static pk_status tma_setup() {
@@ -483,13 +510,14 @@ pk_status cg_solve(pk_csr* A, const double* b, double* x, const pk_opts* o, pk_i
   if (variant == PK_VARIANT_PIPELINED) {
     L.kind = 1;
     L.body_kernels = 2;
+    L.unroll = tma ? 4 : 1;  // more back-to-back programmatic launches per graph body pass
     L.ikeys[1] = tma;
     L.body = [=](cudaStream_t cs, Timer* t) {
       if (t) t->begin(PK_SLOT_UPDATE);
-      if (tma) k_cg_update_tma<<<Gs, kTileThreads, stream_smem_bytes<4>(), cs>>>(n, xd, r, p, ap, part, dst);
+      if (tma) launch_pdl(k_cg_update_tma, Gs, kTileThreads, stream_smem_bytes<4>(), cs, n, xd, r, p, ap, part, dst);
       else k_cg_update<<<Gu, kBlock, 0, cs>>>(ra, xd, r, p, ap);
       if (t) { t->end(); t->begin(PK_SLOT_SPMV_DOTS); }
-      if (tma) k_cg_spmv_dots_tma<<<Gt, kTileThreads, csr_smem_bytes(), cs>>>(ct, p, ap, part, dst);
+      if (tma) launch_pdl(k_cg_spmv_dots_tma, Gt, kTileThreads, csr_smem_bytes(), cs, ct, (const double*)p, ap, part, dst);
       else k_cg_spmv_dots<<<G, kBlock, 0, cs>>>(ra, p, ap);
       if (t) t->end();
     };

@@ -36,7 +36,7 @@ static pk_status build_graph(pk_csr* A, const LoopSpec& L, pk_graph_entry* g) {
   cudaGraph_t body = cp->conditional.phGraph_out[0];
   PK_CUDA(cudaStreamBeginCaptureToGraph(A->cap_stream, body, nullptr, nullptr, 0,
                                         cudaStreamCaptureModeThreadLocal));
-  L.body(A->cap_stream, nullptr);
+  for (int u = 0; u < L.unroll; ++u) L.body(A->cap_stream, nullptr);
   cudaGraph_t captured;
   cudaError_t ce = cudaStreamEndCapture(A->cap_stream, &captured);
   if (ce != cudaSuccess) {

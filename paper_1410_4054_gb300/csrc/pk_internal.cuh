@@ -311,7 +311,8 @@ struct LoopSpec {
   int kind = 0;                         // graph cache key: solver kind
   const void* keys[4] = {nullptr, nullptr, nullptr, nullptr};
   int64_t ikeys[4] = {0, 0, 0, 0};
-  int body_kernels = 0;                 // kernels per body pass
+  int body_kernels = 0;                 // kernels per body() call
+  int unroll = 1;                       // body() calls per graph body pass
   std::function<void(cudaStream_t, Timer*)> body;
 };
 

@@ -95,6 +95,21 @@ __device__ __forceinline__ void bulk_load_hint(void* dst, const void* src, uint3
       : "memory");
 }
 
+// Adds expected transaction bytes to the current phase without arriving.
+__device__ __forceinline__ void mbar_add_tx(uint64_t* bar, uint32_t bytes) {
+  asm volatile("mbarrier.expect_tx.relaxed.cta.shared::cta.b64 [%0], %1;" ::"r"(smem_addr(bar)),
+               "r"(bytes)
+               : "memory");
+}
+
+// Programmatic dependent launch: wait until the preceding kernel of the stream has completed
+// and its memory is visible (a no-op when launched without the programmatic attribute) ...
+__device__ __forceinline__ void griddep_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+// ... and allow the next kernel to be scheduled once every block of this one got here.
+__device__ __forceinline__ void griddep_trigger() {
+  asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
+}
+
 // Record a timed-out wait (first writer wins) so the host sees PK_TIMEOUT.
 __device__ __forceinline__ void report_timeout(DevState* st) {
   atomicExch(&st->timeout, 1);
@@ -140,12 +155,18 @@ constexpr int stream_smem_bytes() {
   return kStreamStages * NIN * kStreamRows * 8 + 2 * kStreamStages * 8;
 }
 
-// Runs the streaming pipeline; `body(row, vals, nvalid)` is called by consumer threads for
-// row pairs (vals[k] = double2 of input k at rows row, row+1; nvalid = 1 or 2).
-// Returns false in threads that saw a timeout.
-template <int NIN, class Body>
+// Runs the streaming pipeline.  The first NPRE inputs do not depend on the preceding
+// kernel: the producer copies them for the first stages before the grid-dependency wait
+// (programmatic dependent launch), the remaining inputs after it.  After the wait every
+// consumer calls `setup()`, which reads the solver state and returns false if the solve has
+// already finished (the block then only drains what was prefetched).  `body(row, vals,
+// nvalid)` is called for row pairs (vals[k] = double2 of input k at rows row, row+1; nvalid =
+// 1 or 2).  Returns, in consumer threads, whether the solve was live (a timed-out wait is
+// recorded in the state and ends the loop early).
+template <int NIN, int NPRE, class Setup, class Body>
 __device__ __forceinline__ bool stream_tiles(const StreamIn<NIN>& in, int r0, int r1,
-                                             unsigned char* smem, DevState* st, Body&& body) {
+                                             unsigned char* smem, DevState* st, Setup&& setup,
+                                             Body&& body) {
   double* buf = reinterpret_cast<double*>(smem);
   uint64_t* full = reinterpret_cast<uint64_t*>(smem + kStreamStages * NIN * kStreamRows * 8);
   uint64_t* empty = full + kStreamStages;
@@ -159,46 +180,76 @@ __device__ __forceinline__ bool stream_tiles(const StreamIn<NIN>& in, int r0, in
   }
   __syncthreads();
   const int ntiles = r1 > r0 ? (r1 - r0 + kStreamRows - 1) / kStreamRows : 0;
+  const int npro = min(kStreamStages, ntiles);
+  auto tile_bytes = [&](int t) {
+    const int rows = min(kStreamRows, r1 - (r0 + t * kStreamRows));
+    return (uint32_t)(((rows + 1) & ~1) * 8);  // whole 16-byte units
+  };
+  auto issue = [&](int t, int k0, int k1) {
+    const int s = t % kStreamStages;
+    const int row0 = r0 + t * kStreamRows;
+    const uint32_t bytes = tile_bytes(t);
+#pragma unroll
+    for (int k = 0; k < NIN; ++k)
+      if (k >= k0 && k < k1)
+        bulk_load(buf + ((size_t)s * NIN + k) * kStreamRows, in.v[k] + row0, bytes, &full[s]);
+  };
   bool ok = true;
   if (warp == kConsumerWarps) {
-    // producer warp: one elected lane issues the copies
     if (lane == 0) {
-      for (int t = 0; t < ntiles; ++t) {
-        const int s = t % kStreamStages;
-        const int use = t / kStreamStages;
-        if (use > 0 && !mbar_wait(&empty[s], (use - 1) & 1)) { ok = false; report_timeout(st); break; }
-        const int row0 = r0 + t * kStreamRows;
-        const int rows = min(kStreamRows, r1 - row0);
-        const uint32_t bytes = (uint32_t)(((rows + 1) & ~1) * 8);  // whole 16-byte units
-        mbar_expect_tx(&full[s], bytes * NIN);
-#pragma unroll
-        for (int k = 0; k < NIN; ++k)
-          bulk_load(buf + ((size_t)s * NIN + k) * kStreamRows, in.v[k] + row0, bytes, &full[s]);
+      // prologue: inputs independent of the preceding kernel, first stages
+      for (int t = 0; t < npro; ++t) {
+        mbar_add_tx(&full[t], tile_bytes(t) * NPRE);
+        issue(t, 0, NPRE);
+      }
+      griddep_wait();
+      const bool live = !state_done(st);
+      for (int t = 0; t < npro; ++t) {
+        if (live) {
+          mbar_expect_tx(&full[t], tile_bytes(t) * (NIN - NPRE));
+          issue(t, NPRE, NIN);
+        } else {
+          mbar_arrive(&full[t]);
+        }
+      }
+      int issued = npro;
+      if (live) {
+        for (int t = npro; t < ntiles; ++t) {
+          const int s = t % kStreamStages;
+          if (!mbar_wait(&empty[s], ((t / kStreamStages) - 1) & 1)) { ok = false; report_timeout(st); break; }
+          mbar_expect_tx(&full[s], tile_bytes(t) * NIN);
+          issue(t, 0, NIN);
+          issued = t + 1;
+        }
       }
       // drain: wait (bounded) until the copies this block issued have landed
-      for (int t = max(0, ntiles - kStreamStages); t < ntiles && ok; ++t)
-        if (!mbar_wait(&full[t % kStreamStages], (t / kStreamStages) & 1)) { ok = false; report_timeout(st); }
+      for (int t = max(0, issued - kStreamStages); t < issued; ++t)
+        if (!mbar_wait(&full[t % kStreamStages], (t / kStreamStages) & 1)) { ok = false; report_timeout(st); break; }
     }
     return ok;
   }
-  // consumer warps
-  for (int t = 0; t < ntiles; ++t) {
+  griddep_wait();
+  const bool live = setup();
+  const int nproc = live ? ntiles : npro;
+  for (int t = 0; t < nproc; ++t) {
     const int s = t % kStreamStages;
-    if (!mbar_wait(&full[s], (t / kStreamStages) & 1)) { report_timeout(st); return false; }
-    const int row0 = r0 + t * kStreamRows;
-    const int rows = min(kStreamRows, r1 - row0);
-    const int i = 2 * threadIdx.x;  // consumer thread -> row pair
-    if (i < rows) {
-      double2 vals[NIN];
+    if (!mbar_wait(&full[s], (t / kStreamStages) & 1)) { report_timeout(st); break; }
+    if (live) {
+      const int row0 = r0 + t * kStreamRows;
+      const int rows = min(kStreamRows, r1 - row0);
+      const int i = 2 * threadIdx.x;  // consumer thread -> row pair
+      if (i < rows) {
+        double2 vals[NIN];
 #pragma unroll
-      for (int k = 0; k < NIN; ++k)
-        vals[k] = *reinterpret_cast<const double2*>(buf + ((size_t)s * NIN + k) * kStreamRows + i);
-      body(row0 + i, vals, min(2, rows - i));
+        for (int k = 0; k < NIN; ++k)
+          vals[k] = *reinterpret_cast<const double2*>(buf + ((size_t)s * NIN + k) * kStreamRows + i);
+        body(row0 + i, vals, min(2, rows - i));
+      }
     }
     __syncwarp();
     if (lane == 0) mbar_arrive(&empty[s]);
   }
-  return true;
+  return live;
 }
 
 // ----------------------------------------------------------------------------------------
@@ -227,9 +278,9 @@ struct CsrTiles {
 // tile together: `rows_fn(ra, ja0, ja1, rb, jb0, jb1, sva, sci)` receives both rows (rb = -1
 // if the tile has no second row for this thread) and their nonzero windows in shared memory
 // (sva/sci are offset so that entry j is sva[j], sci[j]).
-template <class RowFn>
+template <class Setup, class RowFn>
 __device__ __forceinline__ bool csr_tiles(const CsrTiles& T, unsigned char* smem, DevState* st,
-                                          RowFn&& row_fn) {
+                                          Setup&& setup, RowFn&& row_fn) {
   uint64_t* full = reinterpret_cast<uint64_t*>(smem + kCsrStages * kStageBytes);
   uint64_t* empty = full + kCsrStages;
   int2* meta = reinterpret_cast<int2*>(empty + kCsrStages);  // tile rows [R0, R1) per stage
@@ -252,12 +303,16 @@ __device__ __forceinline__ bool csr_tiles(const CsrTiles& T, unsigned char* smem
     return reinterpret_cast<int32_t*>(smem + (size_t)s * kStageBytes + ((kRpWords * 4 + 15) & ~15) +
                                       kVaWords * 8);
   };
+  const int npro = min(kCsrStages, ntiles);
   bool ok = true;
   if (warp == kConsumerWarps) {
-    // producer warp: lanes prefetch tile bounds 32 tiles at a time, lane 0 issues copies
+    // producer warp: lanes prefetch tile bounds 32 tiles at a time, lane 0 issues copies.
+    // The matrix does not depend on the preceding kernel: the first stages are issued before
+    // the grid-dependency wait; after it the producer stops if the solve has finished.
     int issued = 0;
+    bool live = true;
     const uint64_t pol = l2_evict_first();
-    for (int base = 0; base < ntiles && ok; base += 32) {
+    for (int base = 0; base < ntiles && ok && live; base += 32) {
       const int tt = t0 + base + lane;
       int R0 = 0, R1 = 0, z0 = 0, z1 = 0;
       if (tt < t1) {
@@ -291,17 +346,31 @@ __device__ __forceinline__ bool csr_tiles(const CsrTiles& T, unsigned char* smem
         }
         ok = __shfl_sync(0xffffffffu, ok, 0);
         if (!ok) break;
+        if (base + q + 1 == npro) {
+          griddep_wait();
+          live = !state_done(st);
+          if (!live) break;
+        }
       }
     }
+    if (npro == 0) griddep_wait();
     if (lane == 0) {
       for (int t = max(0, issued - kCsrStages); t < issued; ++t)
         if (!mbar_wait(&full[t % kCsrStages], (t / kCsrStages) & 1)) { report_timeout(st); break; }
     }
     return ok;
   }
-  for (int t = 0; t < ntiles; ++t) {
+  griddep_wait();
+  const bool live = setup();
+  const int nproc = live ? ntiles : npro;
+  for (int t = 0; t < nproc; ++t) {
     const int s = t % kCsrStages;
-    if (!mbar_wait(&full[s], (t / kCsrStages) & 1)) { report_timeout(st); return false; }
+    if (!mbar_wait(&full[s], (t / kCsrStages) & 1)) { report_timeout(st); break; }
+    if (!live) {
+      __syncwarp();
+      if (lane == 0) mbar_arrive(&empty[s]);
+      continue;
+    }
     const int2 m = meta[s];
     const int R0 = m.x, R1 = m.y;
     const int ra = R0 + (int)threadIdx.x;
@@ -317,7 +386,7 @@ __device__ __forceinline__ bool csr_tiles(const CsrTiles& T, unsigned char* smem
     __syncwarp();
     if (lane == 0) mbar_arrive(&empty[s]);
   }
-  return true;
+  return live;
 }
 
 // Two row products from a shared-memory window.  Each pass loads up to 8 entries of both
