@@ -198,6 +198,30 @@ pk_status pk_gmres_solve(pk_csr* A, const double* b, double* x, const pk_opts* o
 pk_status pk_batched_solve(int32_t nsys, pk_csr* const* A, const double* const* b,
                            double* const* x, const pk_opts* opts, pk_info* infos, void* stream);
 
+/*
+ * Allocation-free q = A p and *result = <p, q>.  The paper has no counterpart: this entry
+ * point exists for callers that cannot allocate device memory where they need the product
+ * -- code running inside CUDA stream capture (cudaMalloc is not permitted there), loops with
+ * a memory budget fixed in advance, or hosts that must not go through a caching allocator.
+ * Unlike pk_spmv_dot it needs no pk_csr handle: the caller passes its own DEVICE CSR arrays
+ * (same layout as pk_csr_create, not validated here), p, q (length n) and result (one
+ * double), and the call allocates nothing.  Its scratch (per-block partial sums and the
+ * last-block arrival counter) lives in a fixed device array of PK_NOALLOC_SCRATCH_BYTES
+ * that every GPU loading the library holds until the process exits.
+ *   - n must be in [0, PK_NOALLOC_MAX_N]; larger n returns PK_ERR_ARG with a message.
+ *   - The first call on a device looks up the array's device address (cudaGetSymbolAddress)
+ *     with that device current; make that first call before any stream capture.
+ *   - All calls on a device share the array (each call zeroes the counter first): calls that
+ *     overlap on the GPU, e.g. on two streams at once, race and give wrong results.
+ * Stream-ordered on `stream`; returns without synchronising.
+ */
+#define PK_NOALLOC_MAX_N 16777216
+#define PK_NOALLOC_MAX_BLOCKS 2048
+#define PK_NOALLOC_SCRATCH_BYTES (256 + 8 * PK_NOALLOC_MAX_BLOCKS)
+pk_status pk_spmv_dot_noalloc(int64_t n, const int32_t* row_ptr, const int32_t* col_idx,
+                              const double* vals, const double* p, double* q, double* result,
+                              void* stream);
+
 /* Human-readable name of a status code (static string). */
 const char* pk_status_string(pk_status s);
 

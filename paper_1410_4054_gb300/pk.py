@@ -60,6 +60,8 @@ EXPORTS = {
                               C.c_void_p]),
     "pk_cg_solve": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.POINTER(Opts),
                               C.POINTER(Info), C.c_void_p]),
+    "pk_spmv_dot_noalloc": (C.c_int, [C.c_int64, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p,
+                                      C.c_void_p, C.c_void_p, C.c_void_p]),
     "pk_status_string": (C.c_char_p, [C.c_int]),
     "pk_last_error": (C.c_char_p, []),
     "pk_version": (C.c_int32, []),
@@ -226,3 +228,12 @@ def status_string(s: int) -> str:
 
 def version() -> int:
     return lib().pk_version()
+
+
+NOALLOC_MAX_N = 16777216
+
+
+def spmv_dot_noalloc(n, row_ptr, col, val, p, q, result, stream=None):
+    """pk_spmv_dot_noalloc: q = A p, result = <p, q> from device CSR arrays, no allocation."""
+    _check(lib().pk_spmv_dot_noalloc(int(n), _ptr(row_ptr), _ptr(col), _ptr(val), _ptr(p), _ptr(q),
+                                     _ptr(result), _stream_ptr(stream)), "pk_spmv_dot_noalloc")
