@@ -22,7 +22,8 @@ namespace pk {
 __global__ void __launch_bounds__(kBlock) k_residual_init(RowArgs a, const double* __restrict__ b,
                                                           const double* __restrict__ x,
                                                           double* __restrict__ r,
-                                                          double* __restrict__ p) {
+                                                          double* __restrict__ p,
+                                                          double* __restrict__ r0s) {
   const int r0 = a.rowblk[blockIdx.x], r1 = a.rowblk[blockIdx.x + 1];
   double v[2] = {0.0, 0.0};
   for (int row = r0 + threadIdx.x; row < r1; row += blockDim.x) {
@@ -30,6 +31,7 @@ __global__ void __launch_bounds__(kBlock) k_residual_init(RowArgs a, const doubl
     const double ri = bi - csr_row(a, x, row);
     r[row] = ri;
     if (p) p[row] = ri;
+    if (r0s) r0s[row] = ri;
     v[0] = fma(ri, ri, v[0]);
     v[1] = fma(bi, bi, v[1]);
   }
@@ -44,6 +46,7 @@ __global__ void __launch_bounds__(kBlock) k_residual_init(RowArgs a, const doubl
       st->bb = t[1];
       st->thr2 = tol * tol * t[1];
       st->iter = 0;
+      if (r0s) st->s[0] = t[0];  // BiCGStab: <r0, r0*> with r0* = r0
       if (!isfinite(t[0]) || !isfinite(t[1])) {
         finish(st, PK_ERR_NAN);
       } else if (t[1] == 0.0) {
@@ -300,24 +303,6 @@ __global__ void __launch_bounds__(kTileThreads, 2) k_cg_spmv_dots_tma(CsrTiles T
   }
 }
 
-// Launch with the programmatic-stream-serialization attribute: the kernel may start while
-// the preceding kernel of the stream finishes; it orders itself with griddep_wait().
-template <typename... KArgs, typename... Args>
-static void launch_pdl(void (*kern)(KArgs...), int grid, int block, size_t smem, cudaStream_t s,
-                       Args... args) {
-  cudaLaunchConfig_t cfg = {};
-  cfg.gridDim = dim3(grid);
-  cfg.blockDim = dim3(block);
-  cfg.dynamicSmemBytes = smem;
-  cfg.stream = s;
-  cudaLaunchAttribute attr[1];
-  attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
-  attr[0].val.programmaticStreamSerializationAllowed = 1;
-  cfg.attrs = attr;
-  cfg.numAttrs = 1;
-  cudaLaunchKernelEx(&cfg, kern, static_cast<KArgs>(args)...);
-}
-
 static pk_status tma_setup() {
   static bool done = false;
   if (!done) {
@@ -328,16 +313,6 @@ static pk_status tma_setup() {
     done = true;
   }
   return PK_OK;
-}
-
-CsrTiles csr_tiles_of(const pk_csr* A) {
-  CsrTiles t;
-  t.rp = A->rp;
-  t.ci = A->ci;
-  t.va = A->va;
-  t.tile_row = A->tile_row;
-  t.blk_tile = A->blk_tile;
-  return t;
 }
 
 // ---------------------------------------------------------------- classical CG, Alg. 1
@@ -418,19 +393,6 @@ __global__ void __launch_bounds__(kBlock) k_xpay_beta(RowArgs a, const double* _
   for (int row = r0 + threadIdx.x; row < r1; row += blockDim.x) p[row] = fma(beta, p[row], r[row]);
 }
 
-static long long passes_of(const DevState* h) {
-  return *reinterpret_cast<const long long*>(&h->s[7]);
-}
-
-static pk_status check_opts(const pk_csr* A, const double* b, double* x, const pk_opts* o,
-                            pk_info* info) {
-  if (!A || !o || !info) { set_error("NULL handle, opts or info"); return PK_ERR_ARG; }
-  if (A->n > 0 && (!b || !x)) { set_error("NULL b or x"); return PK_ERR_ARG; }
-  if (!(o->tol >= 0.0) || o->maxit < 0) { set_error("tol must be >= 0 and maxit >= 0"); return PK_ERR_ARG; }
-  if (o->trace_cap > 0 && !o->trace) { set_error("trace_cap > 0 needs a trace array"); return PK_ERR_ARG; }
-  return PK_OK;
-}
-
 pk_status cg_solve(pk_csr* A, const double* b, double* x, const pk_opts* o, pk_info* info,
                    cudaStream_t s) {
   pk_status e = check_opts(A, b, x, o, info);
@@ -481,7 +443,7 @@ pk_status cg_solve(pk_csr* A, const double* b, double* x, const pk_opts* o, pk_i
 
   // setup: r0 = b - A x0, p0 = r0, <r0,r0>, <b,b>
   if ((e = T.begin(PK_SLOT_OTHER))) return e;
-  k_residual_init<<<G, kBlock, 0, s>>>(ra, bd, xd, r, p);
+  k_residual_init<<<G, kBlock, 0, s>>>(ra, bd, xd, r, p, nullptr);
   if ((e = T.end())) return e;
   k_zero_x<<<G, kBlock, 0, s>>>(ra, xd);
   launches += 2;
@@ -566,6 +528,15 @@ pk_status cg_solve(pk_csr* A, const double* b, double* x, const pk_opts* o, pk_i
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);
   return (pk_status)info->status;
+}
+
+void launch_residual_init(const pk_csr* A, const double* b, const double* x, double* r,
+                          double* p, double* r0s, cudaStream_t s) {
+  k_residual_init<<<A->grid, kBlock, 0, s>>>(row_args(A), b, x, r, p, r0s);
+}
+
+void launch_zero_x(const pk_csr* A, double* x, cudaStream_t s) {
+  k_zero_x<<<A->grid, kBlock, 0, s>>>(row_args(A), x);
 }
 
 }  // namespace pk

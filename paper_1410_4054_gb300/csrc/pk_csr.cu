@@ -241,6 +241,15 @@ void launch_true_residual(pk_csr* A, const double* b, const double* x, double* t
   k_true_residual<<<A->grid, kBlock, 0, s>>>(row_args(A), b, x, out2);
 }
 
+pk_status check_opts(const pk_csr* A, const double* b, double* x, const pk_opts* o,
+                            pk_info* info) {
+  if (!A || !o || !info) { set_error("NULL handle, opts or info"); return PK_ERR_ARG; }
+  if (A->n > 0 && (!b || !x)) { set_error("NULL b or x"); return PK_ERR_ARG; }
+  if (!(o->tol >= 0.0) || o->maxit < 0) { set_error("tol must be >= 0 and maxit >= 0"); return PK_ERR_ARG; }
+  if (o->trace_cap > 0 && !o->trace) { set_error("trace_cap > 0 needs a trace array"); return PK_ERR_ARG; }
+  return PK_OK;
+}
+
 pk_status finish_info(pk_csr* A, const pk_opts* o, pk_info* info, cudaStream_t s,
                       const VecStage& v, cudaEvent_t e0, cudaEvent_t e1, int launches) {
   pk_status e;

@@ -37,7 +37,7 @@ struct DevState {
   int32_t use_cond;       // kernels run inside a conditional WHILE graph node
   cudaGraphConditionalHandle cond;
   int32_t timeout;        // a bounded device-side wait ran out
-  int32_t pad[1];
+  int32_t early;          // BiCGStab: ||s|| <= tol ||b||, finish with x += alpha p
 };
 
 // Loads that bypass L1 (the value was written by another block or an earlier kernel).
@@ -239,6 +239,16 @@ void launch_dot_store(const pk_csr* A, const double* x, const double* y, double*
 void launch_true_residual(pk_csr* A, const double* b, const double* x, double* tmp,
                           double* out2, cudaStream_t s);
 RowArgs row_args(const pk_csr* A);
+
+void launch_residual_init(const pk_csr* A, const double* b, const double* x, double* r,
+                          double* p, double* r0s, cudaStream_t s);
+void launch_zero_x(const pk_csr* A, double* x, cudaStream_t s);
+pk_status check_opts(const pk_csr* A, const double* b, double* x, const pk_opts* o,
+                     pk_info* info);
+
+inline long long passes_of(const DevState* h) {
+  return *reinterpret_cast<const long long*>(&h->s[7]);
+}
 
 pk_status finish_info(pk_csr* A, const pk_opts* o, pk_info* info, cudaStream_t s,
                       const VecStage& v, cudaEvent_t e0, cudaEvent_t e1, int launches);

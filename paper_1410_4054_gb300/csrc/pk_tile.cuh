@@ -148,18 +148,25 @@ struct StreamIn {
 };
 
 constexpr int kStreamRows = 512;  // rows per streaming tile: 2 per consumer thread
-constexpr int kStreamStages = 5;
+
+// Stages of the streaming ring: as many as fit in ~96 KB (two blocks per SM), 2..8.
+template <int NIN>
+__host__ __device__ constexpr int stream_stages() {
+  return (98304 / (NIN * kStreamRows * 8)) > 8 ? 8
+         : (98304 / (NIN * kStreamRows * 8)) < 2 ? 2 : (98304 / (NIN * kStreamRows * 8));
+}
 
 template <int NIN>
-constexpr int stream_smem_bytes() {
-  return kStreamStages * NIN * kStreamRows * 8 + 2 * kStreamStages * 8;
+__host__ __device__ constexpr int stream_smem_bytes() {
+  return stream_stages<NIN>() * NIN * kStreamRows * 8 + 2 * stream_stages<NIN>() * 8;
 }
 
 // Runs the streaming pipeline.  The first NPRE inputs do not depend on the preceding
 // kernel: the producer copies them for the first stages before the grid-dependency wait
-// (programmatic dependent launch), the remaining inputs after it.  After the wait every
-// consumer calls `setup()`, which reads the solver state and returns false if the solve has
-// already finished (the block then only drains what was prefetched).  `body(row, vals,
+// (programmatic dependent launch), the remaining inputs after it.  After the wait the
+// producer and every consumer call `setup()`, which reads the solver state and returns false
+// if this kernel has nothing to do (the block then only drains what was prefetched); it must
+// give the same answer in every thread.  `body(row, vals,
 // nvalid)` is called for row pairs (vals[k] = double2 of input k at rows row, row+1; nvalid =
 // 1 or 2).  Returns, in consumer threads, whether the solve was live (a timed-out wait is
 // recorded in the state and ends the loop early).
@@ -167,6 +174,7 @@ template <int NIN, int NPRE, class Setup, class Body>
 __device__ __forceinline__ bool stream_tiles(const StreamIn<NIN>& in, int r0, int r1,
                                              unsigned char* smem, DevState* st, Setup&& setup,
                                              Body&& body) {
+  constexpr int kStreamStages = stream_stages<NIN>();
   double* buf = reinterpret_cast<double*>(smem);
   uint64_t* full = reinterpret_cast<uint64_t*>(smem + kStreamStages * NIN * kStreamRows * 8);
   uint64_t* empty = full + kStreamStages;
@@ -203,7 +211,7 @@ __device__ __forceinline__ bool stream_tiles(const StreamIn<NIN>& in, int r0, in
         issue(t, 0, NPRE);
       }
       griddep_wait();
-      const bool live = !state_done(st);
+      const bool live = setup();  // the same predicate the consumers evaluate
       for (int t = 0; t < npro; ++t) {
         if (live) {
           mbar_expect_tx(&full[t], tile_bytes(t) * (NIN - NPRE));
@@ -348,7 +356,7 @@ __device__ __forceinline__ bool csr_tiles(const CsrTiles& T, unsigned char* smem
         if (!ok) break;
         if (base + q + 1 == npro) {
           griddep_wait();
-          live = !state_done(st);
+          live = setup();  // the same predicate the consumers evaluate
           if (!live) break;
         }
       }
@@ -454,6 +462,34 @@ __device__ __forceinline__ double smem_row(const double* sva, const int32_t* sci
       if (k < m) s = fma(v[k], xv[k], s);
   }
   return s;
+}
+
+// Launch with the programmatic-stream-serialization attribute: the kernel may start while
+// the preceding kernel of the stream finishes; it orders itself with griddep_wait().
+template <typename... KArgs, typename... Args>
+inline void launch_pdl(void (*kern)(KArgs...), int grid, int block, size_t smem, cudaStream_t s,
+                       Args... args) {
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3(grid);
+  cfg.blockDim = dim3(block);
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = s;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  attr[0].val.programmaticStreamSerializationAllowed = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  cudaLaunchKernelEx(&cfg, kern, static_cast<KArgs>(args)...);
+}
+
+inline CsrTiles csr_tiles_of(const pk_csr* A) {
+  CsrTiles t;
+  t.rp = A->rp;
+  t.ci = A->ci;
+  t.va = A->va;
+  t.tile_row = A->tile_row;
+  t.blk_tile = A->blk_tile;
+  return t;
 }
 
 }  // namespace pk

@@ -62,6 +62,8 @@ EXPORTS = {
                               C.POINTER(Info), C.c_void_p]),
     "pk_spmv_dot_noalloc": (C.c_int, [C.c_int64, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p,
                                       C.c_void_p, C.c_void_p, C.c_void_p]),
+    "pk_bicgstab_solve": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.POINTER(Opts),
+                                    C.POINTER(Info), C.c_void_p]),
     "pk_status_string": (C.c_char_p, [C.c_int]),
     "pk_last_error": (C.c_char_p, []),
     "pk_version": (C.c_int32, []),
@@ -210,6 +212,16 @@ def cg_solve(A: CSRMatrix, b, x, stream=None, **kw) -> dict:
     info = Info()
     st = lib().pk_cg_solve(A.handle, _ptr(b), _ptr(x), C.byref(o), C.byref(info), _stream_ptr(stream))
     _check(st, "pk_cg_solve", _SOLVER_OK)
+    return info_dict(info)
+
+
+def bicgstab_solve(A: CSRMatrix, b, x, stream=None, **kw) -> dict:
+    """pk_bicgstab_solve: x (in: x0, out: solution)."""
+    o = make_opts(**kw)
+    info = Info()
+    st = lib().pk_bicgstab_solve(A.handle, _ptr(b), _ptr(x), C.byref(o), C.byref(info),
+                                 _stream_ptr(stream))
+    _check(st, "pk_bicgstab_solve", _SOLVER_OK)
     return info_dict(info)
 
 

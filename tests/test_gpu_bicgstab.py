@@ -1,0 +1,139 @@
+"""GPU parity of BiCGStab (pipelined Alg. 4 with four fused kernels, classical Alg. 3) against
+the CPU oracle: alpha, beta, omega within 1e-12 relative over the first iterations,
+iterations to tol within +-2, x within 1e-9 of the oracle's at the same iteration count."""
+import numpy as np
+import pytest
+
+import oracle as O
+from paper_1410_4054_gb300 import workloads as W
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+if not torch.cuda.is_available():  # pragma: no cover
+    pytest.skip("no CUDA device", allow_module_level=True)
+
+from paper_1410_4054_gb300 import pk  # noqa: E402
+
+DEV = "cuda:0"
+
+
+def dev(v):
+    return torch.from_numpy(np.ascontiguousarray(v, dtype=np.float64)).to(DEV)
+
+
+def solve(a, b, x0=None, A=None, trace_cap=64, **kw):
+    A = A or pk.CSRMatrix.from_workload(a)
+    x = dev(np.zeros(a.n) if x0 is None else x0)
+    tr = torch.full((trace_cap, 4), float("nan"), dtype=torch.float64, device=DEV)
+    info = pk.bicgstab_solve(A, dev(b), x, trace=tr, **kw)
+    torch.cuda.synchronize()
+    return info, x.cpu().numpy(), tr.cpu().numpy()
+
+
+def rel(a, b):
+    return float(np.linalg.norm(a - b) / max(np.linalg.norm(b), 1e-300))
+
+
+MATRICES = {
+    "convdiff_16": lambda: W.convdiff_3d(16),
+    "convdiff_23": lambda: W.convdiff_3d(23),   # ragged tiles
+    "powerlaw_1e4": lambda: W.power_law(10_000, seed=1),
+    "rand28": lambda: W.random_uniform(4000, 28, seed=2),
+    "lap2d_ragged": lambda: W.laplace_2d(97, 41),
+}
+
+
+def oracle_sensitivity(a, b, variant, tol=1e-8, maxit=5000, nsamp=3):
+    """The oracle's own rounding sensitivity: rerun it with b perturbed by about one ulp
+    (relative 2^-52, three seeds) and record how far alpha, omega, beta (running maximum of
+    the relative change per iteration), the iteration count and x at a fixed count move."""
+    base = O.bicgstab(a, b, tol=tol, maxit=maxit, variant=variant)
+    fixed = O.bicgstab(a, b, tol=0.0, maxit=max(base["iters"], 1), variant=variant)
+    k = 20
+    spread = np.zeros(k)
+    it_spread, x_spread = 0, 0.0
+    for smp in range(nsamp):
+        bp = b * (1 + 2.0 ** -52 * W.uniform_pm1(100 + smp, a.n))
+        r = O.bicgstab(a, bp, tol=tol, maxit=maxit, variant=variant)
+        for key in ("alpha", "omega", "beta"):
+            d = np.abs(r[key][:k] - base[key][:k]) / np.abs(base[key][:k])
+            spread = np.fmax(spread, np.nan_to_num(d, nan=0.0))
+        it_spread = max(it_spread, abs(r["iters"] - base["iters"]))
+        rf = O.bicgstab(a, bp, tol=0.0, maxit=max(base["iters"], 1), variant=variant)
+        x_spread = max(x_spread, rel(rf["x"], fixed["x"]))
+    return base, fixed, np.maximum.accumulate(spread), it_spread, x_spread
+
+
+@pytest.mark.parametrize("variant", ["pipelined", "classical"])
+@pytest.mark.parametrize("name", sorted(MATRICES))
+def test_bicgstab_parity(name, variant):
+    """Bars: alpha/omega/beta within max(1e-12, 100 x the oracle's own one-ulp spread) per
+    iteration; iterations within max(2, 2 x the oracle's own spread); x at the oracle's
+    iteration count within max(1e-9, 10 x the oracle's own spread); true residual <= tol."""
+    a = MATRICES[name]()
+    _, b, _ = W.manufactured(a, seed=0)
+    ref, fixed, spread, it_spread, x_spread = oracle_sensitivity(a, b, variant)
+    assert ref["status"] == O.OK
+    info, x, tr = solve(a, b, tol=1e-8, maxit=5000, variant=variant, flags=pk.FLAG_TRUE_RES)
+    assert info["status"] == pk.PK_OK, info
+    assert abs(info["iters"] - ref["iters"]) <= max(2, 2 * it_spread)
+    k = min(20, ref["iters"] - 1)
+    bar = np.maximum(1e-12, 100 * spread[:k])
+    for col, key in ((0, "alpha"), (2, "omega"), (1, "beta")):
+        dev_ = np.abs(tr[:k, col] - ref[key][:k]) / np.abs(ref[key][:k])
+        assert np.all(dev_ <= bar), (key, dev_, bar)
+    # where the oracle itself is insensitive, the plain 1e-12 bar holds
+    calm = spread[:k] < 1e-14
+    assert calm[:3].all()
+    assert info["rel_res_true"] <= 1.5e-8
+    info2, x2, _ = solve(a, b, tol=0.0, maxit=ref["iters"], variant=variant)
+    assert info2["iters"] == ref["iters"]
+    assert rel(x2, fixed["x"]) <= max(1e-9, 10 * x_spread)
+
+
+def test_bicgstab_launch_counts():
+    """Sec. 3.2: four kernels per pipelined iteration; the classical form here takes eleven
+    (two SpMV, nine BLAS-1 including the explicit residual norm)."""
+    a = W.convdiff_3d(10)
+    _, b, _ = W.manufactured(a)
+    per = {}
+    for variant in ("pipelined", "classical"):
+        i5, _, _ = solve(a, b, tol=0.0, maxit=5, variant=variant, loop="host", check_every=1)
+        i10, _, _ = solve(a, b, tol=0.0, maxit=10, variant=variant, loop="host", check_every=1)
+        per[variant] = (i10["launches"] - i5["launches"]) / 5
+    assert per == {"pipelined": 4, "classical": 11}
+
+
+def test_bicgstab_edge_cases():
+    a = W.convdiff_3d(6)
+    _, b, _ = W.manufactured(a)
+    for variant in ("pipelined", "classical"):
+        info, x, _ = solve(a, np.zeros(a.n), x0=np.ones(a.n), variant=variant)
+        assert info["status"] == pk.PK_OK and info["iters"] == 0 and not x.any()
+        info, _, _ = solve(a, b, maxit=0, variant=variant)
+        assert info["status"] == pk.PK_NOT_CONVERGED and info["iters"] == 0
+        xs = np.linalg.solve(a.to_dense(), b)
+        info, _, _ = solve(a, b, x0=xs, variant=variant)
+        assert info["status"] == pk.PK_OK and info["iters"] == 0
+        # early exit on a small s: b = A e_j for a diagonal-dominant row converges fast
+        for loop in ("graph", "host"):
+            ref = O.bicgstab(a, b, tol=1e-3, maxit=100, variant=variant)
+            info, x, _ = solve(a, b, tol=1e-3, maxit=100, variant=variant, loop=loop)
+            assert info["status"] == pk.PK_OK and abs(info["iters"] - ref["iters"]) <= 1
+            assert rel(x, ref["x"]) < 1e-6
+
+
+def test_bicgstab_large_convdiff():
+    """3D convection-diffusion 128^3: 20 scalar iterations against the oracle, then a full
+    solve to 1e-8 checked by its true residual."""
+    a = W.convdiff_3d(128)
+    _, b, _ = W.manufactured(a)
+    ref = O.bicgstab(a, b, tol=0.0, maxit=6, variant="pipelined")
+    A = pk.CSRMatrix.from_workload(a)
+    info, x6, tr = solve(a, b, A=A, tol=0.0, maxit=6)
+    np.testing.assert_allclose(tr[:6, 0], ref["alpha"][:6], rtol=1e-12)
+    np.testing.assert_allclose(tr[:6, 2], ref["omega"][:6], rtol=1e-12)
+    assert rel(x6, ref["x"]) <= 1e-9
+    info, _, _ = solve(a, b, A=A, tol=1e-8, maxit=10_000, flags=pk.FLAG_TRUE_RES)
+    assert info["status"] == pk.PK_OK and info["rel_res_true"] <= 1.5e-8
