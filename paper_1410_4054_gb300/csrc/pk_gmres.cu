@@ -1,0 +1,617 @@
+// Restarted simpler GMRES(m) with classical Gram-Schmidt (Walker-Zhou), pipelined form
+// (Alg. 6) and classical form (Alg. 5), fully device resident.
+//
+// One cycle (Sec. 3.3):
+//   START  r = b - A x (true residual) with the first stages of <r,r> and <b,b>; last block:
+//          rho0 = ||r||, convergence test at the cycle boundary, v_0 <- r.
+//   SCALE  v_0 = r / rho0.
+//   step i = 1..k (k <= m):
+//     K-GM-1  v_i = A v_{i-1} with the first stage of <v_{i-1}, v_i>      -> R_{i-1,i}
+//     K-GM-2  first stages of <v_j, v_i>, j = 1..i-2 (one pass over the basis) -> R_{j,i}
+//     K-GM-3  v_i -= sum_{j<i} R_{j,i} v_j with the first stage of ||v_i||^2 -> R_{i,i}
+//     K-GM-4  v_i /= R_{i,i} with the first stage of xi_i = <v_0, v_i>; last block: residual
+//             estimate rho0 sqrt(1 - sum xi^2) and the end-of-cycle decision.
+//   END    R eta = xi by back-substitution (every block, redundantly) and
+//          x += rho0 (eta_1 v_0 + sum_{i>=2} eta_i v_{i-1}).
+// The classical form replaces K-GM-4 by a normalisation kernel, xi_i = <r, v_i>, the residual
+// update r -= xi_i v_i and ||r|| as separate kernels (r is only monitored, R12).
+// The graph is an outer WHILE loop over cycles around an inner WHILE loop over steps.
+#include <algorithm>
+#include <cmath>
+
+#include "pk_tile.cuh"
+
+namespace pk {
+
+enum { GM_START = 0, GM_STEP = 1, GM_END = 2 };
+constexpr int kGmMax = 64;           // largest restart length
+constexpr int kRld = kGmMax + 1;     // leading dimension of R in device scratch
+constexpr int kXiOff = kRld * kRld;  // xi after R
+
+struct GmArgs {
+  int n, ld;
+  double* V;         // basis v_0..v_m, column j at V + j * ld
+  double* R;         // R[j * kRld + i]
+  double* xi;        // xi[i]
+  double* r;         // classical form: the monitored residual
+  const double* b;
+  double* x;
+  double* partials;
+  DevState* st;
+};
+
+__device__ __forceinline__ void cond2_set(DevState* st, unsigned v) {
+  if (st->use_cond) cudaGraphSetConditional(st->cond2, v);
+}
+
+__device__ __forceinline__ void gm_finish(DevState* st, int status) {
+  finish(st, status);
+  cond2_set(st, 0u);
+}
+
+__device__ __forceinline__ bool gm_step_live(const DevState* st) {
+  return !state_done(st) && __ldcg(&st->gm_phase) == GM_STEP;
+}
+
+// START: r = b - A x into v_0, <r,r>, <b,b>; cycle-boundary tests.
+__global__ void __launch_bounds__(kTileThreads, 2) k_gm_start(CsrTiles T, GmArgs g) {
+  extern __shared__ __align__(128) unsigned char smem[];
+  DevState* st = g.st;
+  if (blockIdx.x == 0 && threadIdx.x == 0) {
+    long long* c = reinterpret_cast<long long*>(&st->s[6]);
+    *c += 1;  // cycles started (launch accounting)
+  }
+  double* r = g.V;
+  double v[2] = {0.0, 0.0};
+  const bool live = csr_tiles(T, smem, st, [&]() { return !state_done(st); },
+                              [&](int ra, int ja0, int ja1, int rb, int jb0, int jb1,
+                                  const double* sva, const int32_t* sci) {
+    double sa, sb;
+    smem_row2(sva, sci, ja0, ja1, jb0, jb1, g.x, sa, sb);
+    const double ba = __ldg(g.b + ra), qa = ba - sa;
+    r[ra] = qa;
+    v[0] = fma(qa, qa, v[0]);
+    v[1] = fma(ba, ba, v[1]);
+    if (rb >= 0) {
+      const double bb = __ldg(g.b + rb), qb = bb - sb;
+      r[rb] = qb;
+      v[0] = fma(qb, qb, v[0]);
+      v[1] = fma(bb, bb, v[1]);
+    }
+  });
+  if (!__syncthreads_or(threadIdx.x < kConsumers && live)) {
+    if (blockIdx.x == 0 && threadIdx.x == 0 && st->use_cond) {
+      cudaGraphSetConditional(st->cond, 0u);
+      cudaGraphSetConditional(st->cond2, 0u);
+    }
+    return;
+  }
+  tile_block_partials<2>(v, g.partials);
+  if (arrive_last(&st->counter)) {
+    double t[2];
+    final_sums<2>(g.partials, t);
+    if (threadIdx.x == 0) {
+      if (st->gm_cycle == 0) {
+        const double tol = st->thr2;
+        st->bb = t[1];
+        st->thr2 = tol * tol * t[1];
+      }
+      st->rr = t[0];
+      if (__ldcg(&st->timeout)) gm_finish(st, PK_TIMEOUT);
+      else if (!isfinite(t[0]) || !isfinite(t[1])) gm_finish(st, PK_ERR_NAN);
+      else if (st->bb == 0.0) { st->zero_x = 1; st->rr = 0.0; gm_finish(st, PK_OK); }
+      else if (t[0] <= st->thr2) gm_finish(st, PK_OK);
+      else if (st->iter >= st->maxit) gm_finish(st, PK_NOT_CONVERGED);
+      else if (st->gm_cycle > 0 && st->gm_k == 0) gm_finish(st, PK_BREAKDOWN);
+      else {
+        st->s[0] = sqrt(t[0]);  // rho0
+        st->s[1] = 0.0;         // sum of xi^2
+        st->gm_i = 1;
+        st->gm_k = 0;
+        st->gm_phase = GM_STEP;
+        cond2_set(st, 1u);
+      }
+      st->counter = 0;
+    }
+  }
+}
+
+// SCALE: v_0 = r / rho0 (also the classical form's monitored residual r = v_0).
+__global__ void __launch_bounds__(kTileThreads, 2) k_gm_scale(GmArgs g) {
+  extern __shared__ __align__(128) unsigned char smem[];
+  DevState* st = g.st;
+  int r0, r1;
+  ew_range(g.n, r0, r1);
+  double inv = 0.0;
+  double* v0 = g.V;
+  double* rc = g.r;
+  StreamIn<1> in{{v0}};
+  stream_tiles<1, 1>(in, r0, r1, smem, st, [&]() {
+    inv = 1.0 / __ldcg(&st->s[0]);
+    return gm_step_live(st);
+  }, [&](int row, const double2* val, int nv) {
+    double2 w = val[0];
+    w.x *= inv;
+    w.y *= inv;
+    if (nv == 2) {
+      st2(v0 + row, w);
+      if (rc) st2(rc + row, w);
+    } else {
+      v0[row] = w.x;
+      if (rc) rc[row] = w.x;
+    }
+  });
+}
+
+// K-GM-1: v_i = A v_{i-1} and the first stage of <v_{i-1}, v_i> (i >= 2).
+__global__ void __launch_bounds__(kTileThreads, 2) k_gm1(CsrTiles T, GmArgs g) {
+  extern __shared__ __align__(128) unsigned char smem[];
+  DevState* st = g.st;
+  count_pass(st);
+  const int i = __ldcg(&st->gm_i);
+  const double* vp = g.V + (size_t)(i - 1) * g.ld;
+  double* vi = g.V + (size_t)i * g.ld;
+  double v[1] = {0.0};
+  const bool live = csr_tiles(T, smem, st, [&]() { return gm_step_live(st); },
+                              [&](int ra, int ja0, int ja1, int rb, int jb0, int jb1,
+                                  const double* sva, const int32_t* sci) {
+    double sa, sb;
+    smem_row2(sva, sci, ja0, ja1, jb0, jb1, vp, sa, sb);
+    vi[ra] = sa;
+    v[0] = fma(__ldg(vp + ra), sa, v[0]);
+    if (rb >= 0) {
+      vi[rb] = sb;
+      v[0] = fma(__ldg(vp + rb), sb, v[0]);
+    }
+  });
+  if (!__syncthreads_or(threadIdx.x < kConsumers && live)) return;
+  tile_block_partials<1>(v, g.partials);
+  if (arrive_last(&st->counter)) {
+    double t[1];
+    final_sums<1>(g.partials, t);
+    if (threadIdx.x == 0) {
+      if (i >= 2) g.R[(i - 1) * kRld + i] = t[0];
+      st->counter = 0;
+    }
+  }
+}
+
+// K-GM-2: first stages of <v_j, v_i>, j = 1..i-2.  Warp w owns columns j = 1 + w + 8c; its lanes
+// walk the block's rows, so every basis element is read once, coalesced.
+__global__ void __launch_bounds__(kBlock) k_gm2(GmArgs g) {
+  DevState* st = g.st;
+  if (!gm_step_live(st)) return;
+  const int i = __ldcg(&st->gm_i);
+  const int nj = i - 2;
+  if (nj <= 0) return;
+  int r0, r1;
+  ew_range(g.n, r0, r1);
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const double* vi = g.V + (size_t)i * g.ld;
+  double acc[8];
+#pragma unroll
+  for (int c = 0; c < 8; ++c) acc[c] = 0.0;
+  for (int row = r0 + lane; row < r1; row += 32) {
+    const double w = vi[row];
+#pragma unroll
+    for (int c = 0; c < 8; ++c) {
+      const int j = 1 + warp + 8 * c;
+      if (j <= nj) acc[c] = fma(g.V[(size_t)j * g.ld + row], w, acc[c]);
+    }
+  }
+#pragma unroll
+  for (int c = 0; c < 8; ++c) {
+    const int j = 1 + warp + 8 * c;
+    const double t = warp_sum(acc[c]);
+    if (lane == 0 && j <= nj) g.partials[(size_t)(j - 1) * gridDim.x + blockIdx.x] = t;
+  }
+  if (arrive_last(&st->counter)) {
+    const int G = gridDim.x;
+#pragma unroll
+    for (int c = 0; c < 8; ++c) {
+      const int j = 1 + warp + 8 * c;
+      if (j > nj) continue;  // warp-uniform
+      double t = 0.0;
+      for (int bk = lane; bk < G; bk += 32) t += ld_cg(g.partials + (size_t)(j - 1) * G + bk);
+      t = warp_sum(t);
+      if (lane == 0) g.R[j * kRld + i] = t;
+    }
+    if (threadIdx.x == 0) st->counter = 0;
+  }
+}
+
+// K-GM-3: v_i -= sum_{j=1}^{i-1} R_{j,i} v_j (in order j = 1, 2, ...) with the first stage of
+// ||v_i||^2.  Last block: R_{i,i}, lucky-breakdown test (R13).
+__global__ void __launch_bounds__(kBlock) k_gm3(GmArgs g) {
+  DevState* st = g.st;
+  if (!gm_step_live(st)) return;
+  const int i = __ldcg(&st->gm_i);
+  __shared__ double coef[kGmMax];
+  for (int j = threadIdx.x; j < i - 1; j += blockDim.x) coef[j] = ld_cg(g.R + (j + 1) * kRld + i);
+  __syncthreads();
+  int r0, r1;
+  ew_range(g.n, r0, r1);
+  double* vi = g.V + (size_t)i * g.ld;
+  double v[1] = {0.0};
+  for (int row = r0 + threadIdx.x; row < r1; row += blockDim.x) {
+    double w = vi[row];
+    int j = 1;
+    for (; j + 8 <= i; j += 8) {
+      double vj[8];
+#pragma unroll
+      for (int c = 0; c < 8; ++c) vj[c] = g.V[(size_t)(j + c) * g.ld + row];
+#pragma unroll
+      for (int c = 0; c < 8; ++c) w = fma(-coef[j + c - 1], vj[c], w);
+    }
+    for (; j < i; ++j) w = fma(-coef[j - 1], g.V[(size_t)j * g.ld + row], w);
+    vi[row] = w;
+    v[0] = fma(w, w, v[0]);
+  }
+  block_partials<1>(v, g.partials);
+  if (arrive_last(&st->counter)) {
+    double t[1];
+    final_sums<1>(g.partials, t);
+    if (threadIdx.x == 0) {
+      const double nrm2 = t[0];
+      double col2 = nrm2;
+      for (int j = 1; j < i; ++j) col2 += coef[j - 1] * coef[j - 1];
+      const double rii = sqrt(nrm2);
+      if (!isfinite(rii)) {
+        gm_finish(st, PK_ERR_NAN);
+      } else if (rii == 0.0 || rii <= 1e-14 * sqrt(col2)) {
+        st->gm_k = i - 1;  // the cycle ends before step i
+        st->gm_phase = GM_END;
+        cond2_set(st, 0u);
+      } else {
+        g.R[i * kRld + i] = rii;
+      }
+      st->counter = 0;
+    }
+  }
+}
+
+// End-of-step bookkeeping shared by the pipelined and classical forms.
+__device__ __forceinline__ void gm_step_done(DevState* st, GmArgs& g, int i, double xi_i, double rel2) {
+  g.xi[i] = xi_i;
+  st->iter += 1;
+  st->gm_k = i;
+  if (rel2 < 0.0) rel2 = 0.0;
+  const double est = st->s[0] * sqrt(rel2);
+  const int step = st->iter - 1;
+  trace_put(st, step, 0, i >= 2 ? g.R[(i - 1) * kRld + i] : 0.0);
+  trace_put(st, step, 1, g.R[i * kRld + i]);
+  trace_put(st, step, 2, xi_i);
+  trace_put(st, step, 3, est);
+  if (!isfinite(xi_i)) {
+    gm_finish(st, PK_ERR_NAN);
+  } else if (est * est <= st->thr2 || rel2 <= 1e-14 || i >= st->gm_m || st->iter >= st->maxit) {
+    st->gm_phase = GM_END;
+    cond2_set(st, 0u);
+  } else {
+    st->gm_i = i + 1;
+  }
+}
+
+// K-GM-4 (pipelined): v_i /= R_{i,i} with the first stage of xi_i = <v_0, v_i>.
+__global__ void __launch_bounds__(kTileThreads, 2) k_gm4(GmArgs g) {
+  extern __shared__ __align__(128) unsigned char smem[];
+  DevState* st = g.st;
+  const int i = __ldcg(&st->gm_i);
+  double* vi = g.V + (size_t)i * g.ld;
+  int r0, r1;
+  ew_range(g.n, r0, r1);
+  double inv = 0.0;
+  double v[1] = {0.0};
+  StreamIn<2> in{{g.V, vi}};
+  const bool live = stream_tiles<2, 2>(in, r0, r1, smem, st, [&]() {
+    inv = 1.0 / ld_cg(g.R + i * kRld + i);
+    return gm_step_live(st);
+  }, [&](int row, const double2* val, int nv) {
+    double2 w = val[1];
+    w.x *= inv;
+    w.y *= inv;
+    if (nv == 2) {
+      st2(vi + row, w);
+      v[0] = fma(val[0].x, w.x, v[0]);
+      v[0] = fma(val[0].y, w.y, v[0]);
+    } else {
+      vi[row] = w.x;
+      v[0] = fma(val[0].x, w.x, v[0]);
+    }
+  });
+  if (!__syncthreads_or(threadIdx.x < kConsumers && live)) return;
+  tile_block_partials<1>(v, g.partials);
+  if (arrive_last(&st->counter)) {
+    double t[1];
+    final_sums<1>(g.partials, t);
+    if (threadIdx.x == 0) {
+      const double xi_i = t[0];
+      st->s[1] += xi_i * xi_i;
+      if (__ldcg(&st->timeout)) gm_finish(st, PK_TIMEOUT);
+      else gm_step_done(st, g, i, xi_i, 1.0 - st->s[1]);
+      st->counter = 0;
+    }
+  }
+}
+
+// Classical form (Alg. 5): v_i /= R_{i,i} (plain kernel).
+__global__ void __launch_bounds__(kBlock) k_gmc_norm(GmArgs g) {
+  DevState* st = g.st;
+  if (!gm_step_live(st)) return;
+  const int i = __ldcg(&st->gm_i);
+  double* vi = g.V + (size_t)i * g.ld;
+  const double inv = 1.0 / ld_cg(g.R + i * kRld + i);
+  int r0, r1;
+  ew_range(g.n, r0, r1);
+  for (int row = r0 + threadIdx.x; row < r1; row += blockDim.x) vi[row] *= inv;
+}
+
+// Classical form: xi_i = <r, v_i>.
+__global__ void __launch_bounds__(kBlock) k_gmc_xi(GmArgs g) {
+  DevState* st = g.st;
+  if (!gm_step_live(st)) return;
+  const int i = __ldcg(&st->gm_i);
+  const double* vi = g.V + (size_t)i * g.ld;
+  int r0, r1;
+  ew_range(g.n, r0, r1);
+  double v[1] = {0.0};
+  for (int row = r0 + threadIdx.x; row < r1; row += blockDim.x) v[0] = fma(g.r[row], vi[row], v[0]);
+  block_partials<1>(v, g.partials);
+  if (arrive_last(&st->counter)) {
+    double t[1];
+    final_sums<1>(g.partials, t);
+    if (threadIdx.x == 0) {
+      g.xi[i] = t[0];
+      st->counter = 0;
+    }
+  }
+}
+
+// Classical form: r -= xi_i v_i.
+__global__ void __launch_bounds__(kBlock) k_gmc_rupd(GmArgs g) {
+  DevState* st = g.st;
+  if (!gm_step_live(st)) return;
+  const int i = __ldcg(&st->gm_i);
+  const double* vi = g.V + (size_t)i * g.ld;
+  const double xi_i = ld_cg(g.xi + i);
+  int r0, r1;
+  ew_range(g.n, r0, r1);
+  for (int row = r0 + threadIdx.x; row < r1; row += blockDim.x) g.r[row] = fma(-xi_i, vi[row], g.r[row]);
+}
+
+// Classical form: ||r||^2 monitors the residual; end-of-step decision.
+__global__ void __launch_bounds__(kBlock) k_gmc_rnorm(GmArgs g) {
+  DevState* st = g.st;
+  if (!gm_step_live(st)) return;
+  const int i = __ldcg(&st->gm_i);
+  int r0, r1;
+  ew_range(g.n, r0, r1);
+  double v[1] = {0.0};
+  for (int row = r0 + threadIdx.x; row < r1; row += blockDim.x) v[0] = fma(g.r[row], g.r[row], v[0]);
+  block_partials<1>(v, g.partials);
+  if (arrive_last(&st->counter)) {
+    double t[1];
+    final_sums<1>(g.partials, t);
+    if (threadIdx.x == 0) {
+      gm_step_done(st, g, i, g.xi[i], t[0]);
+      st->counter = 0;
+    }
+  }
+}
+
+// END: eta from R eta = xi (warp 0 of every block), x += rho0 sum_i eta_i z_i.
+__global__ void __launch_bounds__(kBlock) k_gm_end(GmArgs g) {
+  DevState* st = g.st;
+  if (state_done(st) || __ldcg(&st->gm_phase) != GM_END) return;
+  const int k = __ldcg(&st->gm_k);
+  const double rho0 = __ldcg(&st->s[0]);
+  __shared__ double eta[kGmMax + 1];
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  if (warp == 0) {
+    for (int ii = k; ii >= 1; --ii) {
+      double s = 0.0;
+      for (int j = ii + 1 + lane; j <= k; j += 32) s = fma(ld_cg(g.R + ii * kRld + j), eta[j], s);
+      s = warp_sum(s);
+      if (lane == 0) eta[ii] = (ld_cg(g.xi + ii) - s) / ld_cg(g.R + ii * kRld + ii);
+      __syncwarp();
+    }
+  }
+  __syncthreads();
+  int r0, r1;
+  ew_range(g.n, r0, r1);
+  if (k > 0) {
+    for (int row = r0 + threadIdx.x; row < r1; row += blockDim.x) {
+      double a = 0.0;
+      for (int ii = 1; ii <= k; ++ii) a = fma(eta[ii], g.V[(size_t)(ii - 1) * g.ld + row], a);
+      g.x[row] = fma(rho0, a, g.x[row]);
+    }
+  }
+  if (arrive_last(&st->counter)) {
+    if (threadIdx.x == 0) {
+      st->gm_phase = GM_START;
+      st->gm_cycle += 1;
+      st->counter = 0;
+    }
+  }
+}
+
+__global__ void k_gm_init(DevState* st, int m) {
+  st->gm_m = m;
+  st->gm_i = 0;
+  st->gm_k = 0;
+  st->gm_cycle = 0;
+  st->gm_phase = GM_START;
+}
+
+static pk_status gm_setup() {
+  static bool done = false;
+  if (!done) {
+    PK_CUDA(cudaFuncSetAttribute(k_gm_start, cudaFuncAttributeMaxDynamicSharedMemorySize, csr_smem_bytes()));
+    PK_CUDA(cudaFuncSetAttribute(k_gm1, cudaFuncAttributeMaxDynamicSharedMemorySize, csr_smem_bytes()));
+    PK_CUDA(cudaFuncSetAttribute(k_gm_scale, cudaFuncAttributeMaxDynamicSharedMemorySize, stream_smem_bytes<1>()));
+    PK_CUDA(cudaFuncSetAttribute(k_gm4, cudaFuncAttributeMaxDynamicSharedMemorySize, stream_smem_bytes<2>()));
+    done = true;
+  }
+  return PK_OK;
+}
+
+pk_status gmres_solve(pk_csr* A, const double* b, double* x, const pk_opts* o, pk_info* info,
+                      cudaStream_t s) {
+  pk_status e = check_opts(A, b, x, o, info);
+  if (e) return e;
+  *info = pk_info{};
+  info->rel_res_true = -1.0;
+  if (A->n == 0) return PK_OK;
+  const int m = o->restart;
+  if (m < 1 || m > kGmMax) { set_error("GMRES restart must be in 1..64"); return PK_ERR_ARG; }
+  if (o->precision != PK_PREC_FP64) { set_error("GMRES runs in FP64 only"); return PK_ERR_ARG; }
+  if (o->variant != PK_VARIANT_PIPELINED && o->variant != PK_VARIANT_CLASSICAL) {
+    set_error("GMRES variants: pipelined or classical");
+    return PK_ERR_ARG;
+  }
+  if (!A->tma_ok) { set_error("GMRES needs the tile engine (rows longer than 4096 nonzeros are not supported)"); return PK_ERR_ARG; }
+  if ((e = gm_setup())) return e;
+  const int n = A->n;
+  const int ld = ((n + 31) & ~31) + 32;
+  if (A->basis_m < m) {
+    if (A->basis) cudaFree(A->basis);
+    A->basis = nullptr;
+    A->basis_m = 0;
+    PK_CUDA(cudaMalloc(&A->basis, sizeof(double) * (size_t)(m + 1) * ld));
+    PK_CUDA(cudaMemset(A->basis, 0, sizeof(double) * (size_t)(m + 1) * ld));
+    A->basis_m = m;
+  }
+  cudaEvent_t e0, e1;
+  PK_CUDA(cudaEventCreate(&e0));
+  PK_CUDA(cudaEventCreate(&e1));
+  PK_CUDA(cudaEventRecord(e0, s));
+  if ((e = state_init(A, o, s))) return e;
+  k_gm_init<<<1, 1, 0, s>>>(A->st, m);
+  VecStage v;
+  if ((e = stage_in(A, b, x, 14, 15, s, &v))) return e;
+  const bool classical = o->variant == PK_VARIANT_CLASSICAL;
+  double* rc = nullptr;
+  if (classical && (e = work_vec(A, 6, &rc))) return e;
+  GmArgs g;
+  g.n = n;
+  g.ld = ld;
+  g.V = A->basis;
+  g.R = A->small;
+  g.xi = A->small + kXiOff;
+  g.r = rc;
+  g.b = v.b_dev;
+  g.x = v.x_dev;
+  g.partials = A->partials;
+  g.st = A->st;
+  const CsrTiles ct = csr_tiles_of(A);
+  const int Gt = A->grid_tma, Gs = A->grid_stream;
+  int Ge = A->grid_ew;
+  if (!Ge) {
+    int sms = 1;
+    PK_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, A->device));
+    Ge = (int)std::max<int64_t>(1, std::min<int64_t>((int64_t)sms * 4, ((int64_t)n + 2 * kBlock - 1) / (2 * kBlock)));
+  }
+  Timer T;
+  T.A = A;
+  T.on = (o->flags & PK_FLAG_TIMING) != 0;
+  T.s = s;
+  int launches = 1;  // k_gm_init
+  auto pre = [&](cudaStream_t cs, Timer* t) {
+    if (t) t->begin(PK_SLOT_OTHER);
+    k_gm_start<<<Gt, kTileThreads, csr_smem_bytes(), cs>>>(ct, g);
+    if (t) { t->end(); t->begin(PK_SLOT_OTHER); }
+    k_gm_scale<<<Gs, kTileThreads, stream_smem_bytes<1>(), cs>>>(g);
+    if (t) t->end();
+  };
+  auto step = [&](cudaStream_t cs, Timer* t) {
+    if (t) t->begin(PK_SLOT_SPMV_DOTS);
+    k_gm1<<<Gt, kTileThreads, csr_smem_bytes(), cs>>>(ct, g);
+    if (t) { t->end(); t->begin(PK_SLOT_MULTIDOT); }
+    k_gm2<<<Ge, kBlock, 0, cs>>>(g);
+    if (t) { t->end(); t->begin(PK_SLOT_ORTHO); }
+    k_gm3<<<Ge, kBlock, 0, cs>>>(g);
+    if (t) t->end();
+    if (!classical) {
+      if (t) t->begin(PK_SLOT_UPDATE);
+      k_gm4<<<Gs, kTileThreads, stream_smem_bytes<2>(), cs>>>(g);
+      if (t) t->end();
+    } else {
+      if (t) t->begin(PK_SLOT_BLAS1);
+      k_gmc_norm<<<Ge, kBlock, 0, cs>>>(g);
+      if (t) { t->end(); t->begin(PK_SLOT_BLAS1); }
+      k_gmc_xi<<<Ge, kBlock, 0, cs>>>(g);
+      if (t) { t->end(); t->begin(PK_SLOT_BLAS1); }
+      k_gmc_rupd<<<Ge, kBlock, 0, cs>>>(g);
+      if (t) { t->end(); t->begin(PK_SLOT_BLAS1); }
+      k_gmc_rnorm<<<Ge, kBlock, 0, cs>>>(g);
+      if (t) t->end();
+    }
+  };
+  auto post = [&](cudaStream_t cs, Timer* t) {
+    if (t) t->begin(PK_SLOT_OTHER);
+    k_gm_end<<<Ge, kBlock, 0, cs>>>(g);
+    if (t) t->end();
+  };
+  const int step_kernels = classical ? 7 : 4;
+  const bool graph = o->loop == PK_LOOP_GRAPH && !T.on;
+  if (graph) {
+    const void* keys[4] = {v.x_dev, v.b_dev, nullptr, nullptr};
+    const int64_t ikeys[4] = {o->variant, m, 0, 0};
+    pk_graph_entry* ge = nullptr;
+    if ((e = build_nested_graph(A, 6 + (classical ? 1 : 0), keys, ikeys,
+                                [&](cudaStream_t cs) { pre(cs, nullptr); },
+                                [&](cudaStream_t cs) { step(cs, nullptr); },
+                                [&](cudaStream_t cs) { post(cs, nullptr); }, &ge)))
+      return e;
+    launch_enable_cond2(A, ge, s);
+    PK_CUDA(cudaGetLastError());
+    PK_CUDA(cudaGraphLaunch(ge->exec, s));
+    launches += 1;
+  } else {
+    for (;;) {
+      pre(s, T.on ? &T : nullptr);
+      launches += 2;
+      for (int i = 0; i < m; ++i) {
+        step(s, T.on ? &T : nullptr);
+        launches += step_kernels;
+        if (T.on) {
+          if ((e = T.flush())) return e;
+          PK_CUDA(cudaMemcpyAsync(&A->st_host->gm_phase, &A->st->gm_phase, sizeof(int), cudaMemcpyDeviceToHost, s));
+          PK_CUDA(cudaStreamSynchronize(s));
+          if (A->st_host->gm_phase != GM_STEP) break;
+        }
+      }
+      post(s, T.on ? &T : nullptr);
+      launches += 1;
+      PK_CUDA(cudaGetLastError());
+      if ((e = T.flush())) return e;
+      PK_CUDA(cudaMemcpyAsync(&A->st_host->done, &A->st->done, sizeof(int), cudaMemcpyDeviceToHost, s));
+      PK_CUDA(cudaStreamSynchronize(s));
+      if (A->st_host->done) break;
+    }
+  }
+  launch_zero_x(A, v.x_dev, s);
+  launches += 1;
+  if ((e = finish_info(A, o, info, s, v, e0, e1, launches))) return e;
+  const DevState* h = A->st_host;
+  info->cycles = h->gm_cycle;
+  if (graph) {
+    const long long steps = passes_of(h);
+    const long long cycles = *reinterpret_cast<const long long*>(&h->s[6]);
+    info->launches += (int)(steps * step_kernels + cycles * 3);
+  }
+  for (int k = 0; k < PK_MAX_KERNEL_SLOTS; ++k) {
+    info->kernel_count[k] = T.count[k];
+    info->kernel_ms[k] = T.count[k] ? T.ms[k] / T.count[k] : 0.0;
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  return (pk_status)info->status;
+}
+
+}  // namespace pk
+
+extern "C" pk_status pk_gmres_solve(pk_csr* A, const double* b, double* x, const pk_opts* opts,
+                                    pk_info* info, void* stream) {
+  return pk::gmres_solve(A, b, x, opts, info, (cudaStream_t)stream);
+}

@@ -38,6 +38,10 @@ struct DevState {
   cudaGraphConditionalHandle cond;
   int32_t timeout;        // a bounded device-side wait ran out
   int32_t early;          // BiCGStab: ||s|| <= tol ||b||, finish with x += alpha p
+  // GMRES(m): step i of the cycle, steps k done in it, restart count, phase, inner loop
+  int32_t gm_i, gm_k, gm_cycle, gm_phase;
+  int32_t gm_m, gm_pad;
+  cudaGraphConditionalHandle cond2;
 };
 
 // Loads that bypass L1 (the value was written by another block or an earlier kernel).
@@ -150,6 +154,7 @@ struct pk_graph_entry {
   cudaGraph_t graph = nullptr;
   cudaGraphExec_t exec = nullptr;
   cudaGraphConditionalHandle cond_handle = 0;
+  cudaGraphConditionalHandle cond2_handle = 0;  // inner loop of a nested graph
   int body_kernels = 0;
 };
 
@@ -329,6 +334,14 @@ struct LoopSpec {
 // Runs the loop until the device sets `done`; adds the launched kernels to *launches.
 pk_status run_loop(pk_csr* A, const pk_opts* o, cudaStream_t s, const LoopSpec& L, Timer* T,
                    int* launches);
+
+// Graph of two nested WHILE loops: outer { pre(); inner { body() }; post(); }.  The kernels
+// clear DevState::cond (outer) and DevState::cond2 (inner); `g` caches the executable.
+pk_status build_nested_graph(pk_csr* A, int kind, const void* const keys[4], const int64_t ikeys[4],
+                             const std::function<void(cudaStream_t)>& pre,
+                             const std::function<void(cudaStream_t)>& body,
+                             const std::function<void(cudaStream_t)>& post, pk_graph_entry** out);
+void launch_enable_cond2(pk_csr* A, const pk_graph_entry* g, cudaStream_t s);
 
 // Counts body passes (first kernel of every body increments st->s[7] as an integer count).
 __device__ __forceinline__ void count_pass(DevState* st) {

@@ -64,6 +64,8 @@ EXPORTS = {
                                       C.c_void_p, C.c_void_p, C.c_void_p]),
     "pk_bicgstab_solve": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.POINTER(Opts),
                                     C.POINTER(Info), C.c_void_p]),
+    "pk_gmres_solve": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.POINTER(Opts),
+                                 C.POINTER(Info), C.c_void_p]),
     "pk_status_string": (C.c_char_p, [C.c_int]),
     "pk_last_error": (C.c_char_p, []),
     "pk_version": (C.c_int32, []),
@@ -222,6 +224,16 @@ def bicgstab_solve(A: CSRMatrix, b, x, stream=None, **kw) -> dict:
     st = lib().pk_bicgstab_solve(A.handle, _ptr(b), _ptr(x), C.byref(o), C.byref(info),
                                  _stream_ptr(stream))
     _check(st, "pk_bicgstab_solve", _SOLVER_OK)
+    return info_dict(info)
+
+
+def gmres_solve(A: CSRMatrix, b, x, stream=None, **kw) -> dict:
+    """pk_gmres_solve (restart length = kw['restart']): x (in: x0, out: solution)."""
+    o = make_opts(**kw)
+    info = Info()
+    st = lib().pk_gmres_solve(A.handle, _ptr(b), _ptr(x), C.byref(o), C.byref(info),
+                              _stream_ptr(stream))
+    _check(st, "pk_gmres_solve", _SOLVER_OK)
     return info_dict(info)
 
 

@@ -1,0 +1,180 @@
+"""GPU parity of restarted GMRES(m) (pipelined Alg. 6, classical Alg. 5) against the oracle.
+
+Per step the solver traces R_{i-1,i}, R_{i,i}, xi_i and the residual estimate; the first
+cycle's values are compared with the oracle's R and xi relative to max |R| (the scalars of
+this method, R14), iterations to tol within +-2, x at the oracle's iteration count within
+1e-9, and the true residual at exit within tol.
+"""
+import numpy as np
+import pytest
+
+import oracle as O
+from paper_1410_4054_gb300 import workloads as W
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+if not torch.cuda.is_available():  # pragma: no cover
+    pytest.skip("no CUDA device", allow_module_level=True)
+
+from paper_1410_4054_gb300 import pk  # noqa: E402
+
+DEV = "cuda:0"
+
+
+def dev(v):
+    return torch.from_numpy(np.ascontiguousarray(v, dtype=np.float64)).to(DEV)
+
+
+def solve(a, b, x0=None, A=None, trace_cap=256, **kw):
+    A = A or pk.CSRMatrix.from_workload(a)
+    x = dev(np.zeros(a.n) if x0 is None else x0)
+    tr = torch.full((trace_cap, 4), float("nan"), dtype=torch.float64, device=DEV)
+    info = pk.gmres_solve(A, dev(b), x, trace=tr, **kw)
+    torch.cuda.synchronize()
+    return info, x.cpu().numpy(), tr.cpu().numpy()
+
+
+def rel(a, b):
+    return float(np.linalg.norm(a - b) / max(np.linalg.norm(b), 1e-300))
+
+
+MATRICES = {
+    "convdiff_16": lambda: W.convdiff_3d(16),
+    "convdiff_23": lambda: W.convdiff_3d(23),
+    "powerlaw_1e4": lambda: W.power_law(10_000, seed=1),
+    "rand28": lambda: W.random_uniform(4000, 28, seed=2),
+    "lap2d_ragged": lambda: W.laplace_2d(97, 41),
+}
+
+
+def oracle_sensitivity(a, b, variant, m, tol, maxit, nsamp=3):
+    """The oracle's own rounding sensitivity: rerun it with b perturbed by about one ulp
+    (relative 2^-52, three seeds); running maxima of the change of R (relative to max |R|)
+    and xi per step of the first cycle, of the iteration count and of x at a fixed count."""
+    base = O.gmres(a, b, tol=tol, maxit=maxit, m=m, variant=variant)
+    fixed = O.gmres(a, b, tol=0.0, maxit=max(base["iters"], 1), m=m, variant=variant)
+    k = min(m, max(base["iters"], 1))
+    sR = np.zeros(k)
+    sX = np.zeros(k)
+    it_spread, x_spread = 0, 0.0
+    scale = np.abs(base["R"][:k, :k]).max()
+    for smp in range(nsamp):
+        bp = b * (1 + 2.0 ** -52 * W.uniform_pm1(100 + smp, a.n))
+        r = O.gmres(a, bp, tol=tol, maxit=maxit, m=m, variant=variant)
+        dR = np.abs(r["R"][:k, :k] - base["R"][:k, :k]).max(axis=0) / scale
+        sR = np.fmax(sR, dR)
+        sX = np.fmax(sX, np.abs(r["xi"][:k] - base["xi"][:k]))
+        it_spread = max(it_spread, abs(r["iters"] - base["iters"]))
+        rf = O.gmres(a, bp, tol=0.0, maxit=max(base["iters"], 1), m=m, variant=variant)
+        x_spread = max(x_spread, rel(rf["x"], fixed["x"]))
+    return base, fixed, np.maximum.accumulate(sR), np.maximum.accumulate(sX), it_spread, x_spread
+
+
+def first_cycle_check(tr, ref, sR, sX, steps):
+    """R_{i-1,i}, R_{i,i} (relative to max |R|) and xi_i (absolute, |xi| <= 1) within
+    max(1e-12, 100 x the oracle's own one-ulp spread) at every step of the first cycle; the
+    steps where the oracle itself is insensitive meet 1e-12 outright."""
+    R, xi = ref["R"], ref["xi"]
+    # first-cycle lengths: the oracle's nonzero R diagonal; on the GPU the trace of a cycle's
+    # first step has R_{0,1} = 0.  The end-of-cycle test compares 1 - sum xi^2 with a floor,
+    # so rounding may move the boundary by one step: compare the steps both took.
+    k_orc = int(np.count_nonzero(np.diag(R)))
+    nxt = [j for j in range(1, steps) if tr[j, 0] == 0.0]
+    k_gpu = nxt[0] if nxt else steps
+    assert abs(k_orc - k_gpu) <= 1, (k_orc, k_gpu)
+    k = min(len(sR), steps, k_orc, k_gpu)
+    scale = np.abs(R[:k, :k]).max()
+    for i in range(1, k + 1):
+        barR = max(1e-12, 100 * sR[i - 1]) * scale
+        barX = max(1e-12, 100 * sX[i - 1])
+        if i >= 2:
+            assert abs(tr[i - 1, 0] - R[i - 2, i - 1]) <= barR, (i, "R_{i-1,i}")
+        assert abs(tr[i - 1, 1] - R[i - 1, i - 1]) <= barR, (i, "R_ii")
+        assert abs(tr[i - 1, 2] - xi[i - 1]) <= barX, (i, "xi")
+    assert (sX[: min(3, k)] < 1e-14).all()
+
+
+@pytest.mark.parametrize("variant", ["pipelined", "classical"])
+@pytest.mark.parametrize("name", sorted(MATRICES))
+def test_gmres_parity(name, variant):
+    a = MATRICES[name]()
+    _, b, _ = W.manufactured(a, seed=0)
+    m = 30
+    ref, fixed, sR, sX, it_spread, x_spread = oracle_sensitivity(a, b, variant, m, 1e-8, 20_000)
+    assert ref["status"] == O.OK
+    info, x, tr = solve(a, b, tol=1e-8, maxit=20_000, restart=m, variant=variant,
+                        flags=pk.FLAG_TRUE_RES, trace_cap=max(256, ref["iters"] + 8))
+    assert info["status"] == pk.PK_OK, info
+    assert abs(info["iters"] - ref["iters"]) <= max(2, 2 * it_spread)
+    first_cycle_check(tr, ref, sR, sX, ref["iters"])
+    assert info["rel_res_true"] <= 1.5e-8
+    info2, x2, _ = solve(a, b, tol=0.0, maxit=ref["iters"], restart=m, variant=variant)
+    assert info2["iters"] == ref["iters"] and info2["cycles"] == fixed["cycles"]
+    assert rel(x2, fixed["x"]) <= max(1e-9, 10 * x_spread)
+
+
+@pytest.mark.parametrize("loop", ["graph", "host"])
+@pytest.mark.parametrize("m", [1, 5, 30, 64])
+def test_gmres_restart_lengths_and_loops(m, loop):
+    a = W.convdiff_3d(12)
+    _, b, _ = W.manufactured(a, seed=3)
+    ref = O.gmres(a, b, tol=1e-9, maxit=5000, m=m)
+    info, x, _ = solve(a, b, tol=1e-9, maxit=5000, restart=m, loop=loop, check_every=1,
+                       flags=pk.FLAG_TRUE_RES)
+    assert info["status"] == pk.PK_OK and abs(info["iters"] - ref["iters"]) <= 2
+    assert abs(info["cycles"] - ref["cycles"]) <= 1
+    assert info["rel_res_true"] <= 1.5e-9
+
+
+def test_gmres_launch_counts():
+    """Sec. 3.3: four kernels per pipelined Arnoldi step (the classical form here: seven)."""
+    a = W.convdiff_3d(10)
+    _, b, _ = W.manufactured(a)
+    per = {}
+    for variant in ("pipelined", "classical"):
+        i10, _, _ = solve(a, b, tol=0.0, maxit=10, restart=30, variant=variant)
+        i20, _, _ = solve(a, b, tol=0.0, maxit=20, restart=30, variant=variant)
+        per[variant] = (i20["launches"] - i10["launches"]) / 10
+    assert per == {"pipelined": 4, "classical": 7}
+
+
+def test_gmres_edge_cases():
+    a = W.convdiff_3d(6)
+    _, b, _ = W.manufactured(a)
+    info, x, _ = solve(a, np.zeros(a.n), x0=np.ones(a.n))
+    assert info["status"] == pk.PK_OK and info["iters"] == 0 and not x.any()
+    info, _, _ = solve(a, b, maxit=0)
+    assert info["status"] == pk.PK_NOT_CONVERGED and info["iters"] == 0
+    ref = O.gmres(a, b, tol=0.0, maxit=13, m=5)
+    info, x, _ = solve(a, b, tol=0.0, maxit=13, restart=5)
+    assert info["status"] == pk.PK_NOT_CONVERGED and info["iters"] == 13 and info["cycles"] == 3
+    assert rel(x, ref["x"]) <= 1e-10
+    # full GMRES on a tiny system: lucky breakdown / precision floor end the cycle
+    t = W.random_uniform(24, 5, seed=2)
+    _, tb, _ = W.manufactured(t, seed=2)
+    ref = O.gmres(t, tb, tol=1e-11, maxit=200, m=30)
+    info, tx, _ = solve(t, tb, tol=1e-11, maxit=200, restart=30)
+    assert info["status"] == pk.PK_OK and abs(info["iters"] - ref["iters"]) <= 2
+    assert rel(tx, np.linalg.solve(t.to_dense(), tb)) < 1e-9
+
+
+def test_gmres_large_convdiff():
+    """128^3 convection-diffusion: the first 10 steps' R and xi against the oracle, then the
+    full GMRES(30) solve checked by its true residual."""
+    a = W.convdiff_3d(128)
+    _, b, _ = W.manufactured(a)
+    ref = O.gmres(a, b, tol=0.0, maxit=10, m=30)
+    A = pk.CSRMatrix.from_workload(a)
+    info, x10, tr = solve(a, b, A=A, tol=0.0, maxit=10, restart=30)
+    bp = b * (1 + 2.0 ** -52 * W.uniform_pm1(100, a.n))
+    pert = O.gmres(a, bp, tol=0.0, maxit=10, m=30)
+    scale = np.abs(ref["R"][:10, :10]).max()
+    sR = np.maximum.accumulate(np.abs(pert["R"][:10, :10] - ref["R"][:10, :10]).max(axis=0) / scale)
+    sX = np.maximum.accumulate(np.abs(pert["xi"][:10] - ref["xi"][:10]))
+    for i in range(1, 11):
+        assert abs(tr[i - 1, 1] - ref["R"][i - 1, i - 1]) <= max(1e-12, 100 * sR[i - 1]) * scale
+        assert abs(tr[i - 1, 2] - ref["xi"][i - 1]) <= max(1e-12, 100 * sX[i - 1])
+    assert rel(x10, ref["x"]) <= 1e-9
+    info, _, _ = solve(a, b, A=A, tol=1e-8, maxit=20_000, restart=30, flags=pk.FLAG_TRUE_RES)
+    assert info["status"] == pk.PK_OK and info["rel_res_true"] <= 1.5e-8
