@@ -73,6 +73,9 @@ enum {
 #define PK_FLAG_TRUE_RES 2u  /* compute ||b - A x|| / ||b|| at exit into pk_info.rel_res_true */
 #define PK_FLAG_NO_TMA 4u    /* use the thread-per-row kernels instead of the warp-specialised
                                 bulk-copy tile kernels (for comparison) */
+#define PK_FLAG_AUTOTUNE 8u  /* pk_batched_solve: time every (block size, blocks per SM)
+                                candidate on the batch first and keep the fastest (cached per
+                                batch shape for the process) */
 
 typedef struct {
   double tol;          /* relative residual tolerance (>= 0) */
@@ -191,12 +194,22 @@ pk_status pk_gmres_solve(pk_csr* A, const double* b, double* x, const pk_opts* o
                          pk_info* info, void* stream);
 
 /*
- * Many independent SPD systems in one persistent launch (pipelined CG per system, with
- * per-system convergence masks).  A[k], b[k], x[k] for k < nsys; b/x device pointers.
- * infos: nsys entries (may be NULL).  opts->precision selects FP64 or MIXED.
+ * Many independent SPD systems in one persistent launch (motivated by the paper's transient
+ * and small-system regime, Sec. 1 and 4.1).  A persistent grid takes systems from a device
+ * work queue, largest first; one thread block runs pipelined CG (Alg. 2) on a system to
+ * completion with block-wide reductions, then takes the next, so a converged system simply
+ * leaves the queue (per-system convergence mask).  A[k], b[k], x[k] for k < nsys; b and x
+ * must be DEVICE pointers.  opts: tol, maxit (per system; MIXED: total inner iterations),
+ * precision PK_PREC_FP64 or PK_PREC_MIXED (FP32 SpMV/vectors inside FP64 iterative
+ * refinement, inner tolerance 1e-4, at most 20 refinement steps), flags PK_FLAG_AUTOTUNE.
+ * infos: nsys entries or NULL (iters, status, cycles = refinement steps, rel_res_est).
+ * Returns PK_OK if every system converged, else the first failing system's status.
  */
 pk_status pk_batched_solve(int32_t nsys, pk_csr* const* A, const double* const* b,
                            double* const* x, const pk_opts* opts, pk_info* infos, void* stream);
+
+/* Block size and blocks per SM used by the last pk_batched_solve call in this process. */
+pk_status pk_batched_last_config(int32_t* block, int32_t* blocks_per_sm);
 
 /*
  * Allocation-free q = A p and *result = <p, q>.  The paper has no counterpart: this entry

@@ -25,6 +25,7 @@ LOOPS = {"graph": 0, "host": 1}
 FLAG_TIMING = 1
 FLAG_TRUE_RES = 2
 FLAG_NO_TMA = 4
+FLAG_AUTOTUNE = 8
 SLOTS = ["spmv_dots", "update", "multidot", "ortho", "spmv", "blas1", "other"]
 MAX_SLOTS = 8
 
@@ -66,6 +67,9 @@ EXPORTS = {
                                     C.POINTER(Info), C.c_void_p]),
     "pk_gmres_solve": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.POINTER(Opts),
                                  C.POINTER(Info), C.c_void_p]),
+    "pk_batched_solve": (C.c_int, [C.c_int32, C.c_void_p, C.c_void_p, C.c_void_p, C.POINTER(Opts),
+                                   C.c_void_p, C.c_void_p]),
+    "pk_batched_last_config": (C.c_int, [C.POINTER(C.c_int32), C.POINTER(C.c_int32)]),
     "pk_status_string": (C.c_char_p, [C.c_int]),
     "pk_last_error": (C.c_char_p, []),
     "pk_version": (C.c_int32, []),
@@ -235,6 +239,25 @@ def gmres_solve(A: CSRMatrix, b, x, stream=None, **kw) -> dict:
                               _stream_ptr(stream))
     _check(st, "pk_gmres_solve", _SOLVER_OK)
     return info_dict(info)
+
+
+def batched_solve(As, bs, xs, stream=None, **kw) -> list:
+    """pk_batched_solve over lists of CSRMatrix handles and device tensors b[k], x[k]."""
+    nsys = len(As)
+    o = make_opts(**kw)
+    ha = (C.c_void_p * nsys)(*[A.handle.value for A in As])
+    hb = (C.c_void_p * nsys)(*[b.data_ptr() for b in bs])
+    hx = (C.c_void_p * nsys)(*[x.data_ptr() for x in xs])
+    infos = (Info * nsys)()
+    st = lib().pk_batched_solve(nsys, ha, hb, hx, C.byref(o), infos, _stream_ptr(stream))
+    _check(st, "pk_batched_solve", _SOLVER_OK)
+    return [info_dict(infos[k]) for k in range(nsys)]
+
+
+def batched_last_config() -> tuple:
+    b, p = C.c_int32(), C.c_int32()
+    _check(lib().pk_batched_last_config(C.byref(b), C.byref(p)), "pk_batched_last_config")
+    return b.value, p.value
 
 
 def spmv(A: CSRMatrix, x, y, stream=None):

@@ -1,0 +1,102 @@
+"""Batched persistent solves (one launch for many uneven SPD systems) against the oracle:
+each system matches its own single-system oracle solve."""
+import numpy as np
+import pytest
+
+import oracle as O
+from paper_1410_4054_gb300 import workloads as W
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+if not torch.cuda.is_available():  # pragma: no cover
+    pytest.skip("no CUDA device", allow_module_level=True)
+
+from paper_1410_4054_gb300 import pk  # noqa: E402
+
+DEV = "cuda:0"
+
+
+def dev(v):
+    return torch.from_numpy(np.ascontiguousarray(v, dtype=np.float64)).to(DEV)
+
+
+def rel(a, b):
+    return float(np.linalg.norm(a - b) / max(np.linalg.norm(b), 1e-300))
+
+
+def make_batch(nsys=40, seed=0, lo=8, hi=64):
+    mats = W.batched_rectangles(nsys, seed=seed, lo=lo, hi=hi)
+    # edge members: a 1 x 1 system and a zero right-hand side
+    mats.append(W.CSR(1, np.array([0, 1], np.int32), np.array([0], np.int32), np.array([3.0])))
+    mats.append(W.laplace_2d(5, 7, shift=0.5))
+    rhs = []
+    for k, a in enumerate(mats):
+        _, b, _ = W.manufactured(a, seed=k)
+        rhs.append(b)
+    rhs[-1] = np.zeros(mats[-1].n)
+    return mats, rhs
+
+
+@pytest.mark.parametrize("autotune", [False, True])
+def test_batched_fp64_matches_single_system_oracle(autotune):
+    mats, rhs = make_batch()
+    As = [pk.CSRMatrix.from_workload(a) for a in mats]
+    bs = [dev(b) for b in rhs]
+    # fixed iteration count: x after 25 iterations equals the oracle's
+    xs = [torch.zeros(a.n, dtype=torch.float64, device=DEV) for a in mats]
+    infos = pk.batched_solve(As, bs, xs, tol=0.0, maxit=25,
+                             flags=pk.FLAG_AUTOTUNE if autotune else 0)
+    torch.cuda.synchronize()
+    for a, b, x, inf in zip(mats, rhs, xs, infos):
+        ref = O.cg(a, b, tol=0.0, maxit=25, variant="pipelined")
+        if ref["status"] == O.NOT_CONVERGED:  # (the 1 x 1 member can reach r = 0 exactly)
+            assert inf["iters"] == ref["iters"], (a.name, inf, ref["iters"])
+        assert rel(x.cpu().numpy(), ref["x"]) <= 1e-9, a.name
+    if autotune:
+        blk, per = pk.batched_last_config()
+        assert blk in (128, 256, 512, 1024) and per in (1, 2, 4, 8)
+    # to tolerance: iterations within 2 of the oracle, true residual within tol
+    xs = [torch.zeros(a.n, dtype=torch.float64, device=DEV) for a in mats]
+    infos = pk.batched_solve(As, bs, xs, tol=1e-10, maxit=5000)
+    torch.cuda.synchronize()
+    for a, b, x, inf in zip(mats, rhs, xs, infos):
+        ref = O.cg(a, b, tol=1e-10, maxit=5000, variant="pipelined")
+        assert inf["status"] == pk.PK_OK
+        assert abs(inf["iters"] - ref["iters"]) <= 2, (a.name, inf["iters"], ref["iters"])
+        xh = x.cpu().numpy()
+        if np.any(b):
+            assert np.linalg.norm(b - a.matvec(xh)) <= 1.5e-10 * np.linalg.norm(b)
+        else:
+            assert not xh.any()
+
+
+def test_batched_mixed_precision_reaches_fp64_accuracy():
+    mats, rhs = make_batch(nsys=24, seed=3)
+    As = [pk.CSRMatrix.from_workload(a) for a in mats]
+    bs = [dev(b) for b in rhs]
+    xs = [torch.zeros(a.n, dtype=torch.float64, device=DEV) for a in mats]
+    infos = pk.batched_solve(As, bs, xs, tol=1e-10, maxit=20_000, precision="mixed")
+    torch.cuda.synchronize()
+    for a, b, x, inf in zip(mats, rhs, xs, infos):
+        assert inf["status"] == pk.PK_OK, (a.name, inf)
+        xh = x.cpu().numpy()
+        if not np.any(b):
+            assert not xh.any()
+            continue
+        assert np.linalg.norm(b - a.matvec(xh)) <= 1.5e-10 * np.linalg.norm(b)
+        ref = O.cg(a, b, tol=1e-12, maxit=20_000, variant="pipelined")
+        assert rel(xh, ref["x"]) <= 1e-8  # error vs the FP64 oracle's solution
+        assert inf["cycles"] >= 1
+
+
+def test_batched_not_spd_member_is_reported():
+    mats, rhs = make_batch(nsys=6, seed=5)
+    neg = W.CSR(mats[0].n, mats[0].row_ptr, mats[0].col, -mats[0].val)
+    mats[0] = neg
+    As = [pk.CSRMatrix.from_workload(a) for a in mats]
+    bs = [dev(b) for b in rhs]
+    xs = [torch.zeros(a.n, dtype=torch.float64, device=DEV) for a in mats]
+    infos = pk.batched_solve(As, bs, xs, tol=1e-10, maxit=2000)
+    assert infos[0]["status"] == pk.PK_NOT_SPD
+    assert all(i["status"] == pk.PK_OK for i in infos[1:])
