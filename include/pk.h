@@ -168,8 +168,12 @@ pk_status pk_spmv_dot(pk_csr* A, const double* p, double* q, double* result, int
  * iteration (update x,r,p + <r,r>; SpMV + <Ap,Ap>, <p,Ap>, with alpha/beta from Eq. (3) in
  * the SpMV kernel's last block; Sec. 3.1); CLASSICAL = Alg. 1 as six kernels per iteration
  * (SpMV, dot, axpy, axpy, dot, xpay); SPLIT = Alg. 2 with SpMV and its dots in separate
- * kernels (three per iteration).  precision MIXED: see pk_cg_solve_mixed semantics in the
- * header notes below.  opts / info may not be NULL.
+ * kernels (three per iteration).  precision MIXED: Alg. 2 in FP32 (values rounded to FP32,
+ * FP32 vectors and SpMV accumulation) on r / ||r||, stopped at a 1e-4 inner reduction, inside
+ * an FP64 iterative-refinement loop (FP64 true residual b - A x, FP64 correction x += ||r|| d,
+ * at most 20 refinement steps; maxit bounds the inner iterations in total; info.cycles =
+ * refinement steps); the inner products that set alpha and beta are accumulated per thread
+ * as float-float pairs and reduced in FP64.  opts / info may not be NULL.
  */
 pk_status pk_cg_solve(pk_csr* A, const double* b, double* x, const pk_opts* opts, pk_info* info,
                       void* stream);

@@ -393,6 +393,9 @@ __global__ void __launch_bounds__(kBlock) k_xpay_beta(RowArgs a, const double* _
   for (int row = r0 + threadIdx.x; row < r1; row += blockDim.x) p[row] = fma(beta, p[row], r[row]);
 }
 
+pk_status cg_mixed(pk_csr* A, const double* b, double* x, const pk_opts* o, pk_info* info,
+                   cudaStream_t s);
+
 pk_status cg_solve(pk_csr* A, const double* b, double* x, const pk_opts* o, pk_info* info,
                    cudaStream_t s) {
   pk_status e = check_opts(A, b, x, o, info);
@@ -400,7 +403,8 @@ pk_status cg_solve(pk_csr* A, const double* b, double* x, const pk_opts* o, pk_i
   *info = pk_info{};
   info->rel_res_true = -1.0;
   if (A->n == 0) return PK_OK;
-  if (o->precision != PK_PREC_FP64) { set_error("precision must be PK_PREC_FP64 here"); return PK_ERR_ARG; }
+  if (o->precision == PK_PREC_MIXED) return cg_mixed(A, b, x, o, info, s);
+  if (o->precision != PK_PREC_FP64) { set_error("precision must be PK_PREC_FP64 or PK_PREC_MIXED"); return PK_ERR_ARG; }
   if (o->variant < 0 || o->variant > 2) { set_error("bad variant"); return PK_ERR_ARG; }
   cudaEvent_t e0, e1;
   PK_CUDA(cudaEventCreate(&e0));
