@@ -55,6 +55,10 @@ def parse():
                     help="kernels: run only --iters fixed pipelined-CG iterations (profiler driver)")
     ap.add_argument("--iters", type=int, default=30)
     ap.add_argument("--variant", default="pipelined")
+    ap.add_argument("--solver", default="cg", choices=["cg", "bicgstab", "gmres"],
+                    help="--mode kernels: cg on the Laplacian, bicgstab / gmres on convection-diffusion")
+    ap.add_argument("--no-forms", action="store_true",
+                    help="skip the BiCGStab / GMRES / batched / mixed-precision lines")
     return ap.parse_args()
 
 
@@ -64,15 +68,16 @@ def run_kernels(args):
     import torch
     from paper_1410_4054_gb300 import pk
 
-    a = W.laplace_3d(args.k)
+    a = W.laplace_3d(args.k) if args.solver == "cg" else W.convdiff_3d(args.k)
     _, b, _ = W.manufactured(a, seed=0)
     A = pk.CSRMatrix.from_workload(a)
     bd = torch.from_numpy(b).cuda()
     xd = torch.zeros(a.n, dtype=torch.float64, device="cuda")
-    info = pk.cg_solve(A, bd, xd, tol=0.0, maxit=args.iters, variant=args.variant, loop="host",
-                       check_every=args.iters)
+    fn = {"cg": pk.cg_solve, "bicgstab": pk.bicgstab_solve, "gmres": pk.gmres_solve}[args.solver]
+    info = fn(A, bd, xd, tol=0.0, maxit=args.iters, variant=args.variant, loop="host",
+              check_every=args.iters)
     torch.cuda.synchronize()
-    print(json.dumps({"mode": "kernels", "k": args.k, "n": a.n, "iters": info["iters"],
+    print(json.dumps({"mode": "kernels", "solver": args.solver, "k": args.k, "n": a.n, "iters": info["iters"],
                       "launches": info["launches"], "solve_ms": info["solve_ms"]}))
     return 0
 
@@ -169,10 +174,14 @@ def measured_peaks():
     return 6800.0, "fallback"
 
 
+KERNEL_SOURCES = ("pk_cg.cu", "pk_tile.cuh", "pk_internal.cuh")
+
+
 def kernel_source_sha() -> str:
+    """Hash of the sources that define the profiled CG kernels."""
     h = hashlib.sha256()
-    for f in sorted((ROOT / "paper_1410_4054_gb300" / "csrc").glob("*")):
-        h.update(f.read_bytes())
+    for name in KERNEL_SOURCES:
+        h.update((ROOT / "paper_1410_4054_gb300" / "csrc" / name).read_bytes())
     return h.hexdigest()[:16]
 
 
@@ -362,6 +371,8 @@ def run_ours(args):
             sweep.append(row)
             M.close()
 
+    forms = {} if args.no_forms else bench_forms(pk, torch, dev, args)
+
     cpu = None
     if not args.no_cpu:
         s, it_cpu = oracle_sample(a, b, 60)
@@ -374,11 +385,113 @@ def run_ours(args):
             "vs_baseline": None, "dtype": "f64", "data": "synthetic", "config": config(args.k, a),
             "time_to_tol_ms": ms, "iters": it, "iters_per_s": it / (ms * 1e-3),
             "gpu_launches": launches, "e2e": e2e, "roofline": roofline, "cpu_baseline": cpu,
-            "clocks": clk, "sweep": sweep}
+            "clocks": clk, "sweep": sweep, "forms": forms}
     print(json.dumps(line), flush=True)
     if pg:
         pg.destroy_process_group()
     return 0
+
+
+def _best(fn, reps=2):
+    best = None
+    for _ in range(reps):
+        info = fn()
+        if best is None or info["solve_ms"] < best["solve_ms"]:
+            best = info
+    return best
+
+
+def bench_forms(pk, torch, dev, args):
+    """The other solvers and forms, each timed after one warm-up run (device time of the call).
+
+    bicgstab / gmres: 3D convection-diffusion 128^3 (cell Peclet 0.5), tol 1e-8, pipelined vs
+    classical on the same GPU, plus per-kernel times over 30 fixed iterations.
+    batched: 512 shifted 2D Laplacians on rectangles with sides log-uniform in [32, 256], tol
+    1e-10, one persistent launch (FP64 and mixed precision) vs 512 sequential plain solves.
+    mixed: the 160^3 Laplacian to 1e-8, mixed precision vs FP64, error of the mixed solution.
+    """
+    out = {}
+    a = W.convdiff_3d(128)
+    _, b, _ = W.manufactured(a, seed=0)
+    A = pk.CSRMatrix.from_workload(a)
+    bd = torch.from_numpy(b).to(dev)
+    x = torch.zeros(a.n, dtype=torch.float64, device=dev)
+    for solver, fn in (("bicgstab", pk.bicgstab_solve), ("gmres", pk.gmres_solve)):
+        row = {"matrix": "convdiff3d_128", "n": a.n, "nnz": a.nnz, "tol": 1e-8}
+        for variant in ("pipelined", "classical"):
+            kw = dict(tol=1e-8, maxit=20_000, variant=variant)
+            if solver == "gmres":
+                kw["restart"] = 30
+            fn(A, bd, x.zero_(), **kw)
+            inf = _best(lambda: fn(A, bd, x.zero_(), **kw))
+            row[f"{variant}_ms"] = inf["solve_ms"]
+            row[f"{variant}_iters"] = inf["iters"]
+            row[f"{variant}_status"] = inf["status_name"]
+        prof = fn(A, bd, x.zero_(), tol=0.0, maxit=30, flags=pk.FLAG_TIMING,
+                  **({"restart": 30} if solver == "gmres" else {}))
+        row["kernel_ms_30_fixed_iterations"] = prof["kernel_ms"]
+        row["speedup_vs_classical"] = row["classical_ms"] / row["pipelined_ms"]
+        out[solver] = row
+    A.close()
+
+    mats = W.batched_rectangles(512, seed=0)
+    rhs = [W.manufactured(m, seed=k)[1] for k, m in enumerate(mats)]
+    As = [pk.CSRMatrix.from_workload(m) for m in mats]
+    bs = [torch.from_numpy(v).to(dev) for v in rhs]
+    xs = [torch.zeros(m.n, dtype=torch.float64, device=dev) for m in mats]
+    brow = {"systems": len(mats), "rows": int(sum(m.n for m in mats)),
+            "nnz": int(sum(m.nnz for m in mats)), "tol": 1e-10}
+    res = {}
+    for prec in ("fp64", "mixed"):
+        kw = dict(tol=1e-10, maxit=20_000, precision=prec, flags=pk.FLAG_AUTOTUNE)
+        pk.batched_solve(As, bs, [v.zero_() for v in xs], **kw)   # tunes, then warm
+        times = []
+        for _ in range(3):
+            infos = pk.batched_solve(As, bs, [v.zero_() for v in xs], **kw)
+            times.append(infos[0]["solve_ms"])
+        ms = min(times)
+        brow[f"{prec}_ms"] = ms
+        brow[f"{prec}_solves_per_s"] = len(mats) / (ms * 1e-3)
+        brow[f"{prec}_all_converged"] = all(i["status"] == pk.PK_OK for i in infos)
+        brow[f"{prec}_config"] = list(pk.batched_last_config())
+        res[prec] = [v.clone() for v in xs]
+    errs = [float(torch.linalg.norm(xm - x64) / torch.linalg.norm(x64))
+            for xm, x64 in zip(res["mixed"], res["fp64"]) if float(torch.linalg.norm(x64)) > 0]
+    brow["mixed_max_rel_error_vs_fp64"] = max(errs)
+    # sequential plain FP64 solves (CUDA-graph loop per system), the same systems
+    for k in range(4):
+        pk.cg_solve(As[k], bs[k], xs[k].zero_(), tol=1e-10, maxit=20_000)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for k in range(len(mats)):
+        pk.cg_solve(As[k], bs[k], xs[k].zero_(), tol=1e-10, maxit=20_000)
+    torch.cuda.synchronize()
+    seq = time.perf_counter() - t0
+    brow["sequential_plain_ms"] = 1e3 * seq
+    brow["sequential_plain_solves_per_s"] = len(mats) / seq
+    brow["speedup_fp64_batched_vs_sequential"] = brow["sequential_plain_ms"] / brow["fp64_ms"]
+    out["batched"] = brow
+    for M in As:
+        M.close()
+
+    a = W.laplace_3d(args.k)
+    _, b, _ = W.manufactured(a, seed=0)
+    A = pk.CSRMatrix.from_workload(a)
+    bd = torch.from_numpy(b).to(dev)
+    x64 = torch.zeros(a.n, dtype=torch.float64, device=dev)
+    xm = torch.zeros(a.n, dtype=torch.float64, device=dev)
+    pk.cg_solve(A, bd, xm.zero_(), tol=1e-8, maxit=50_000, precision="mixed")
+    i64 = _best(lambda: pk.cg_solve(A, bd, x64.zero_(), tol=1e-8, maxit=50_000))
+    im = _best(lambda: pk.cg_solve(A, bd, xm.zero_(), tol=1e-8, maxit=50_000, precision="mixed",
+                                   flags=pk.FLAG_TRUE_RES))
+    out["mixed"] = {"matrix": f"lap3d_{args.k}", "tol": 1e-8, "fp64_ms": i64["solve_ms"],
+                    "mixed_ms": im["solve_ms"], "speedup": i64["solve_ms"] / im["solve_ms"],
+                    "refinement_steps": im["cycles"], "inner_iters": im["iters"],
+                    "fp64_iters": i64["iters"], "mixed_rel_res_true": im["rel_res_true"],
+                    "rel_error_vs_fp64": float(torch.linalg.norm(xm - x64) / torch.linalg.norm(x64)),
+                    "inner_bytes_per_iter": 8 * a.nnz + 40 * a.n}
+    A.close()
+    return out
 
 
 def main():
