@@ -178,7 +178,7 @@ __global__ void __launch_bounds__(kTileThreads, 2) k_gm1(CsrTiles T, GmArgs g) {
 
 // K-GM-2: first stages of <v_j, v_i>, j = 1..i-2.  Warp w owns columns j = 1 + w + 8c; its lanes
 // walk the block's rows, so every basis element is read once, coalesced.
-__global__ void __launch_bounds__(kBlock) k_gm2(GmArgs g) {
+__global__ void __launch_bounds__(kBlock, 2) k_gm2(GmArgs g) {
   DevState* st = g.st;
   if (!gm_step_live(st)) return;
   const int i = __ldcg(&st->gm_i);
@@ -191,12 +191,22 @@ __global__ void __launch_bounds__(kBlock) k_gm2(GmArgs g) {
   double acc[8];
 #pragma unroll
   for (int c = 0; c < 8; ++c) acc[c] = 0.0;
-  for (int row = r0 + lane; row < r1; row += 32) {
-    const double w = vi[row];
+  // four rows per lane per pass, all loads of a column issued before its FMAs
+  for (int row0 = r0 + lane; row0 < r1; row0 += 128) {
+    double w[4];
+#pragma unroll
+    for (int u = 0; u < 4; ++u) w[u] = row0 + 32 * u < r1 ? vi[row0 + 32 * u] : 0.0;
 #pragma unroll
     for (int c = 0; c < 8; ++c) {
       const int j = 1 + warp + 8 * c;
-      if (j <= nj) acc[c] = fma(g.V[(size_t)j * g.ld + row], w, acc[c]);
+      if (j <= nj) {  // warp-uniform
+        const double* vj = g.V + (size_t)j * g.ld;
+        double q[4];
+#pragma unroll
+        for (int u = 0; u < 4; ++u) q[u] = row0 + 32 * u < r1 ? vj[row0 + 32 * u] : 0.0;
+#pragma unroll
+        for (int u = 0; u < 4; ++u) acc[c] = fma(q[u], w[u], acc[c]);
+      }
     }
   }
 #pragma unroll
