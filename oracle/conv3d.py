@@ -1,0 +1,97 @@
+"""CPU oracle of the learned warm start's 3D convolutional network (numpy FP64).
+
+TEST INFRASTRUCTURE ONLY (see the package docstring): imported by the tests and nowhere on
+the product path; it shares no code with the CUDA kernels.
+
+Network: four 3x3x3 convolutions with zero padding 1 on a channels-last grid (D, H, W, C),
+channels padded to 16 (3 -> 16 -> 16 -> 16 -> 1), ReLU after the first three.  Weights are
+indexed w[tap][co][ci] with tap = 9 (dz+1) + 3 (dy+1) + (dx+1).  Every operand the GPU stores
+in BF16 (input, weights, activations, output gradient, hidden-layer gradients) is rounded to
+BF16 here at the same point; all arithmetic is FP64, so the oracle differs from the GPU only
+by the GPU's FP32 accumulation order (and, rarely, a BF16 rounding that flips because of it).
+"""
+from __future__ import annotations
+
+import numpy as np
+
+TAPS = [(dz, dy, dx) for dz in (-1, 0, 1) for dy in (-1, 0, 1) for dx in (-1, 0, 1)]
+
+
+def bf16(a) -> np.ndarray:
+    """Round float values to the nearest bfloat16 (ties to even), returned as float64."""
+    f = np.asarray(a, dtype=np.float32)
+    u = f.view(np.uint32).astype(np.uint64)
+    rounded = (u + 0x7FFF + ((u >> 16) & 1)) >> 16
+    return (rounded.astype(np.uint32) << 16).view(np.float32).astype(np.float64)
+
+
+def conv3d(x: np.ndarray, w: np.ndarray, bias=None) -> np.ndarray:
+    """out[z,y,x,co] = bias[co] + sum_tap sum_ci w[tap,co,ci] x[z+dz, y+dy, x+dx, ci] (zero outside)."""
+    D, H, W, _ = x.shape
+    xp = np.pad(x, ((1, 1), (1, 1), (1, 1), (0, 0)))
+    out = np.zeros((D, H, W, w.shape[1]))
+    for t, (dz, dy, dx) in enumerate(TAPS):
+        sl = xp[1 + dz:1 + dz + D, 1 + dy:1 + dy + H, 1 + dx:1 + dx + W, :]
+        out += np.tensordot(sl, w[t], axes=([3], [1]))
+    if bias is not None:
+        out += bias
+    return out
+
+
+def conv3d_transpose(g: np.ndarray, w: np.ndarray) -> np.ndarray:
+    """Adjoint of conv3d in its input: dx[z,y,x,ci] = sum_tap sum_co w[tap,co,ci] g[z-dz, y-dy, x-dx, co]."""
+    D, H, W, _ = g.shape
+    gp = np.pad(g, ((1, 1), (1, 1), (1, 1), (0, 0)))
+    out = np.zeros((D, H, W, w.shape[2]))
+    for t, (dz, dy, dx) in enumerate(TAPS):
+        sl = gp[1 - dz:1 - dz + D, 1 - dy:1 - dy + H, 1 - dx:1 - dx + W, :]
+        out += np.tensordot(sl, w[t], axes=([3], [0]))
+    return out
+
+
+def conv3d_wgrad(a: np.ndarray, g: np.ndarray) -> np.ndarray:
+    """dW[tap,co,ci] = sum_v g[v,co] a[v + offset(tap), ci] (zero outside)."""
+    D, H, W, _ = a.shape
+    ap = np.pad(a, ((1, 1), (1, 1), (1, 1), (0, 0)))
+    dw = np.zeros((27, g.shape[3], a.shape[3]))
+    for t, (dz, dy, dx) in enumerate(TAPS):
+        sl = ap[1 + dz:1 + dz + D, 1 + dy:1 + dy + H, 1 + dx:1 + dx + W, :]
+        dw[t] = np.tensordot(g, sl, axes=([0, 1, 2], [0, 1, 2]))
+    return dw
+
+
+def forward(params, x16: np.ndarray, rounding: bool = True):
+    """Activations a0..a3 (BF16-rounded after ReLU) and the FP64 output channel 0."""
+    rnd = bf16 if rounding else (lambda v: np.asarray(v, dtype=np.float64))
+    acts = [rnd(x16)]
+    for layer, (w, b) in enumerate(params):
+        z = conv3d(acts[-1], rnd(w), b)
+        if layer < len(params) - 1:
+            acts.append(rnd(np.maximum(z, 0.0)))
+        else:
+            out = z[..., 0]
+    return acts, out
+
+
+def loss_and_grads(params, x16: np.ndarray, target: np.ndarray, rounding: bool = True):
+    """MSE loss mean((out - target)^2) and its gradients dW, db for every layer (chain rule,
+    with the GPU's BF16 rounding of the propagated gradients)."""
+    rnd = bf16 if rounding else (lambda v: np.asarray(v, dtype=np.float64))
+    acts, out = forward(params, x16, rounding)
+    nvox = out.size
+    diff = out - target
+    loss = float(np.mean(diff * diff))
+    g = np.zeros(out.shape + (params[-1][0].shape[1],))
+    g[..., 0] = 2.0 * diff / nvox
+    g = rnd(g)
+    grads = [None] * len(params)
+    for layer in range(len(params) - 1, -1, -1):
+        w, _ = params[layer]
+        a_in = acts[layer]
+        dw = conv3d_wgrad(a_in, g)
+        db = g.sum(axis=(0, 1, 2))
+        grads[layer] = (dw, db)
+        if layer > 0:
+            ga = conv3d_transpose(g, rnd(w))
+            g = rnd(ga * (a_in > 0))
+    return loss, out, grads

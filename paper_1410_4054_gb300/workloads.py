@@ -250,3 +250,97 @@ LAPLACE_3D_SWEEP = (16, 32, 64, 100, 160)
 LAPLACE_2D_SWEEP = (256, 1024, 2048)
 CONVDIFF_SWEEP = (32, 64, 128)
 POWER_LAW_SWEEP = (10_000, 100_000, 1_000_000)
+
+
+# ------------------------------------------------------------------ transient heat equation
+
+@dataclass
+class Transient:
+    """Implicit-Euler heat equation on a k^3 grid: M x_t = x_{t-1} + dt f_t with M = I + dt L."""
+
+    M: CSR
+    dt: float
+    k: int
+    steps: int
+    sigma: float
+    seed: int
+
+    def source(self, t: int) -> np.ndarray:
+        """Gaussian of width sigma cells moving on a circle of radius k/4 around the centre."""
+        k = self.k
+        th = 2.0 * np.pi * t / self.steps
+        c = np.array([k / 2, k / 2 + (k / 4) * np.sin(th), k / 2 + (k / 4) * np.cos(th)])
+        z, y, x = np.meshgrid(np.arange(k), np.arange(k), np.arange(k), indexing="ij")
+        d2 = (z - c[0]) ** 2 + (y - c[1]) ** 2 + (x - c[2]) ** 2
+        return np.exp(-d2 / (2.0 * self.sigma ** 2)).ravel()
+
+    def rhs(self, x_prev: np.ndarray, t: int) -> np.ndarray:
+        return x_prev + self.dt * self.source(t)
+
+
+def _box_filter_3d(a: np.ndarray, w: int) -> np.ndarray:
+    """Mean over the w^3 box of in-domain cells around every cell."""
+    h = w // 2
+    k = a.shape[0]
+    s = np.zeros((k + 1,) * 3)
+    s[1:, 1:, 1:] = a.cumsum(0).cumsum(1).cumsum(2)
+    one = np.zeros((k + 1,) * 3)
+    one[1:, 1:, 1:] = np.ones_like(a).cumsum(0).cumsum(1).cumsum(2)
+    lo = np.clip(np.arange(k) - h, 0, k)
+    hi = np.clip(np.arange(k) + h + 1, 0, k)
+
+    def box(c):
+        z0, y0, x0 = np.ix_(lo, lo, lo)
+        z1, y1, x1 = np.ix_(hi, hi, hi)
+        return (c[z1, y1, x1] - c[z0, y1, x1] - c[z1, y0, x1] - c[z1, y1, x0]
+                + c[z0, y0, x1] + c[z0, y1, x0] + c[z1, y0, x0] - c[z0, y0, x0])
+
+    return box(s) / box(one)
+
+
+def transient_heat(k: int = 64, steps: int = 300, seed: int = 0, sigma: float = 4.0) -> Transient:
+    """Variable-coefficient 7-point operator M = I + dt L on a k^3 grid.
+
+    Conductivity: lognormal (mu 0, sigma 1) per cell, smoothed by a 5^3 box filter over the
+    in-domain cells; face conductivity = harmonic mean of the two cells; Dirichlet boundary
+    faces use the cell's own conductivity.  L_ii = sum of the 6 face conductivities,
+    L_ij = -face conductivity.  dt = 2 / max_i L_ii, so the least diagonally dominant row
+    has |M_ii| / sum_j |M_ij| = 1.5.
+    """
+    rng = np.random.default_rng(seed)
+    kap = _box_filter_3d(np.exp(rng.standard_normal((k, k, k))), 5)
+    n = k ** 3
+    idx = np.arange(n, dtype=np.int64).reshape(k, k, k)
+    diag = np.zeros((k, k, k))
+    rows, cols, vals = [], [], []
+    for ax in range(3):
+        lo = [slice(None)] * 3
+        hi = [slice(None)] * 3
+        lo[ax] = slice(0, -1)
+        hi[ax] = slice(1, None)
+        ka, kb = kap[tuple(lo)], kap[tuple(hi)]
+        kf = 2.0 * ka * kb / (ka + kb)
+        diag[tuple(lo)] += kf
+        diag[tuple(hi)] += kf
+        ia, ib = idx[tuple(lo)].ravel(), idx[tuple(hi)].ravel()
+        rows += [ia, ib]
+        cols += [ib, ia]
+        vals += [-kf.ravel(), -kf.ravel()]
+        # boundary faces (one per side) use the cell's conductivity
+        first = [slice(None)] * 3
+        last = [slice(None)] * 3
+        first[ax] = slice(0, 1)
+        last[ax] = slice(k - 1, k)
+        diag[tuple(first)] += kap[tuple(first)]
+        diag[tuple(last)] += kap[tuple(last)]
+    dt = 2.0 / diag.max()
+    rows.append(idx.ravel())
+    cols.append(idx.ravel())
+    vals.append(np.zeros(n))
+    r = np.concatenate(rows)
+    c = np.concatenate(cols)
+    v = np.concatenate(vals) * dt
+    d = 1.0 + dt * diag.ravel()
+    v[-n:] = d
+    M = _from_coo(n, r, c, v, f"transient_{k}")
+    return Transient(M=M, dt=dt, k=k, steps=steps, sigma=sigma, seed=seed)
