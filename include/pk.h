@@ -239,6 +239,49 @@ pk_status pk_spmv_dot_noalloc(int64_t n, const int32_t* row_ptr, const int32_t* 
                               const double* vals, const double* p, double* q, double* result,
                               void* stream);
 
+/* *out2 = ||b - A x||^2 (device pointers; deterministic reduction). */
+pk_status pk_residual_norm2(pk_csr* A, const double* b, const double* x, double* out2, void* stream);
+
+/*
+ * Learned initial guess for transient problems (an extension; the paper has no counterpart): a 4-layer 3x3x3
+ * convolutional network on a D x H x W grid, BF16 operands with FP32 accumulation on the
+ * tensor cores (m16n8k16 MMA, implicit GEMM).  Activations are channels-last BF16
+ * [D][H][W][16] with channel counts padded to 16 (padded channels are zero); weights are BF16
+ * [27][16 co][16 ci], tap = 9(dz+1) + 3(dy+1) + (dx+1); zero padding 1 at the boundary.
+ * All pointers are device pointers; calls are stream-ordered and return at once.
+ */
+/* Y = conv(X, W) + bias, then ReLU if relu; out_f32: Y is FP32 [D][H][W] holding channel 0
+ * only; mask (nullable, BF16 [D][H][W][16]): Y[v][c] = 0 where mask[v][c] <= 0 (the ReLU
+ * derivative, used by the backward-data pass with flipped weights). */
+pk_status pk_conv3d_fwd(const void* X, const void* Wt, const float* bias, void* Y, int32_t D,
+                        int32_t H, int32_t W, int32_t relu, int32_t out_f32, const void* mask,
+                        void* stream);
+/* dW[tap][co][ci] = sum_v G[v][co] A[v + tap][ci] (FP32), db[co] = sum_v G[v][co]; scratch:
+ * pk_conv3d_wgrad_scratch_floats(D, H, W) floats (deterministic block partials). */
+int64_t pk_conv3d_wgrad_scratch_floats(int32_t D, int32_t H, int32_t W);
+pk_status pk_conv3d_wgrad(const void* A, const void* G, float* scratch, float* dW, float* db,
+                          int32_t D, int32_t H, int32_t W, void* stream);
+/* Wf[26 - t][ci][co] = W[t][co][ci]: weights of the backward-data convolution. */
+pk_status pk_conv3d_flip(const void* W, void* Wf, void* stream);
+/* Network input X16 = bf16(x_{t-1}/s0, (x_{t-1} - x_{t-2})/s1, (b - x_{t-1})/s2, 0...) with
+ * s0..s2 the rms of those three vectors, written to scales[0..2] (3 doubles); scratch:
+ * pk_warmstart_scratch_doubles() doubles. */
+int64_t pk_warmstart_scratch_doubles(void);
+pk_status pk_warmstart_input(int64_t n, const double* xm1, const double* xm2, const double* b,
+                             void* X16, double* scales, double* scratch, void* stream);
+/* Target y = (x_t - 2 x_{t-1} + x_{t-2}) / s1 (the part linear extrapolation misses):
+ * *loss = mean((out - y)^2), G = bf16(2 (out - y) / n) in channel 0 (other channels 0). */
+pk_status pk_warmstart_loss(int64_t n, const float* out, const double* xt, const double* xm1,
+                            const double* xm2, const double* scales, void* G, double* loss,
+                            double* scratch, void* stream);
+/* x_hat = 2 x_{t-1} - x_{t-2} + s1 out; out = NULL gives the linear extrapolation alone. */
+pk_status pk_warmstart_apply(int64_t n, const float* out, const double* xm1, const double* xm2,
+                             const double* scales, double* xhat, void* stream);
+/* Adam (Kingma & Ba) on FP32 parameters, step >= 1; p_bf16 (nullable) receives a BF16 copy. */
+pk_status pk_adam_step(int64_t count, float* p, const float* grad, float* m, float* v, float lr,
+                       float beta1, float beta2, float eps, int32_t step, void* p_bf16,
+                       void* stream);
+
 /* Human-readable name of a status code (static string). */
 const char* pk_status_string(pk_status s);
 

@@ -95,3 +95,12 @@ def loss_and_grads(params, x16: np.ndarray, target: np.ndarray, rounding: bool =
             ga = conv3d_transpose(g, rnd(w))
             g = rnd(ga * (a_in > 0))
     return loss, out, grads
+
+
+def adam_step(p, g, m, v, step, lr=1e-3, beta1=0.9, beta2=0.999, eps=1e-8):
+    """One Adam update (Kingma & Ba, ICLR 2015, Algorithm 1) in FP64; returns (p, m, v)."""
+    m = beta1 * m + (1 - beta1) * g
+    v = beta2 * v + (1 - beta2) * g * g
+    mh = m / (1 - beta1 ** step)
+    vh = v / (1 - beta2 ** step)
+    return p - lr * mh / (np.sqrt(vh) + eps), m, v

@@ -497,6 +497,18 @@ pk_status pk_csr_stats_get(const pk_csr* A, pk_csr_stats* out) {
   return PK_OK;
 }
 
+pk_status pk_residual_norm2(pk_csr* A, const double* b, const double* x, double* out2, void* stream) {
+  if (!A || !out2 || (A->n && (!b || !x))) { set_error("NULL argument"); return PK_ERR_ARG; }
+  cudaStream_t s = (cudaStream_t)stream;
+  if (A->n == 0) {
+    PK_CUDA(cudaMemsetAsync(out2, 0, sizeof(double), s));
+    return PK_OK;
+  }
+  launch_true_residual(A, b, x, nullptr, out2, s);
+  PK_CUDA(cudaGetLastError());
+  return PK_OK;
+}
+
 pk_status pk_spmv(pk_csr* A, const double* x, double* y, void* stream) {
   if (!A || (A->n && (!x || !y))) { set_error("NULL argument"); return PK_ERR_ARG; }
   if (A->n == 0) return PK_OK;

@@ -70,6 +70,22 @@ EXPORTS = {
     "pk_batched_solve": (C.c_int, [C.c_int32, C.c_void_p, C.c_void_p, C.c_void_p, C.POINTER(Opts),
                                    C.c_void_p, C.c_void_p]),
     "pk_batched_last_config": (C.c_int, [C.POINTER(C.c_int32), C.POINTER(C.c_int32)]),
+    "pk_residual_norm2": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p]),
+    "pk_conv3d_fwd": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_int32, C.c_int32,
+                                C.c_int32, C.c_int32, C.c_int32, C.c_void_p, C.c_void_p]),
+    "pk_conv3d_wgrad_scratch_floats": (C.c_int64, [C.c_int32, C.c_int32, C.c_int32]),
+    "pk_conv3d_wgrad": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p,
+                                  C.c_int32, C.c_int32, C.c_int32, C.c_void_p]),
+    "pk_conv3d_flip": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p]),
+    "pk_warmstart_scratch_doubles": (C.c_int64, []),
+    "pk_warmstart_input": (C.c_int, [C.c_int64, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p,
+                                     C.c_void_p, C.c_void_p, C.c_void_p]),
+    "pk_warmstart_loss": (C.c_int, [C.c_int64, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p,
+                                    C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p]),
+    "pk_warmstart_apply": (C.c_int, [C.c_int64, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p,
+                                     C.c_void_p, C.c_void_p]),
+    "pk_adam_step": (C.c_int, [C.c_int64, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_float,
+                               C.c_float, C.c_float, C.c_float, C.c_int32, C.c_void_p, C.c_void_p]),
     "pk_status_string": (C.c_char_p, [C.c_int]),
     "pk_last_error": (C.c_char_p, []),
     "pk_version": (C.c_int32, []),
@@ -284,3 +300,55 @@ def spmv_dot_noalloc(n, row_ptr, col, val, p, q, result, stream=None):
     """pk_spmv_dot_noalloc: q = A p, result = <p, q> from device CSR arrays, no allocation."""
     _check(lib().pk_spmv_dot_noalloc(int(n), _ptr(row_ptr), _ptr(col), _ptr(val), _ptr(p), _ptr(q),
                                      _ptr(result), _stream_ptr(stream)), "pk_spmv_dot_noalloc")
+
+
+def residual_norm2(A: CSRMatrix, b, x, out2, stream=None):
+    """out2[0] = ||b - A x||^2 (device tensors)."""
+    _check(lib().pk_residual_norm2(A.handle, _ptr(b), _ptr(x), _ptr(out2), _stream_ptr(stream)),
+           "pk_residual_norm2")
+
+
+def conv3d_fwd(X, Wt, bias, Y, dims, relu=True, out_f32=False, mask=None, stream=None):
+    D, H, W = dims
+    _check(lib().pk_conv3d_fwd(_ptr(X), _ptr(Wt), _ptr(bias), _ptr(Y), D, H, W, int(relu),
+                               int(out_f32), _ptr(mask), _stream_ptr(stream)), "pk_conv3d_fwd")
+
+
+def conv3d_wgrad_scratch_floats(dims) -> int:
+    return int(lib().pk_conv3d_wgrad_scratch_floats(*dims))
+
+
+def conv3d_wgrad(A, G, scratch, dW, db, dims, stream=None):
+    D, H, W = dims
+    _check(lib().pk_conv3d_wgrad(_ptr(A), _ptr(G), _ptr(scratch), _ptr(dW), _ptr(db), D, H, W,
+                                 _stream_ptr(stream)), "pk_conv3d_wgrad")
+
+
+def conv3d_flip(W, Wf, stream=None):
+    _check(lib().pk_conv3d_flip(_ptr(W), _ptr(Wf), _stream_ptr(stream)), "pk_conv3d_flip")
+
+
+def warmstart_scratch_doubles() -> int:
+    return int(lib().pk_warmstart_scratch_doubles())
+
+
+def warmstart_input(n, xm1, xm2, b, X16, scales, scratch, stream=None):
+    _check(lib().pk_warmstart_input(int(n), _ptr(xm1), _ptr(xm2), _ptr(b), _ptr(X16), _ptr(scales),
+                                    _ptr(scratch), _stream_ptr(stream)), "pk_warmstart_input")
+
+
+def warmstart_loss(n, out, xt, xm1, xm2, scales, G, loss, scratch, stream=None):
+    _check(lib().pk_warmstart_loss(int(n), _ptr(out), _ptr(xt), _ptr(xm1), _ptr(xm2), _ptr(scales),
+                                   _ptr(G), _ptr(loss), _ptr(scratch), _stream_ptr(stream)),
+           "pk_warmstart_loss")
+
+
+def warmstart_apply(n, out, xm1, xm2, scales, xhat, stream=None):
+    """x_hat = 2 x_{t-1} - x_{t-2} + s out (out None: the extrapolation alone)."""
+    _check(lib().pk_warmstart_apply(int(n), _ptr(out), _ptr(xm1), _ptr(xm2), _ptr(scales), _ptr(xhat),
+                                    _stream_ptr(stream)), "pk_warmstart_apply")
+
+
+def adam_step(p, grad, m, v, lr, step, beta1=0.9, beta2=0.999, eps=1e-8, p_bf16=None, stream=None):
+    _check(lib().pk_adam_step(p.numel(), _ptr(p), _ptr(grad), _ptr(m), _ptr(v), lr, beta1, beta2, eps,
+                              int(step), _ptr(p_bf16), _stream_ptr(stream)), "pk_adam_step")

@@ -1,0 +1,211 @@
+"""Learned initial guess for a sequence of implicit time steps (a BF16 convolutional network).
+
+A 4-layer 3x3x3 convolutional network (3 -> 16 -> 16 -> 16 -> 1 channels, ReLU between
+layers, channel counts padded to 16) predicts the next time step from the previous two
+solutions and the new right-hand side.  Every numerical step runs in the library's CUDA
+kernels through the C ABI (BF16 tensor-core implicit-GEMM convolutions with FP32
+accumulation, FP32 Adam); this module only owns the buffers and sequences the calls.
+
+Inputs: x_{t-1}, x_{t-1} - x_{t-2} and b_t - x_{t-1} (the same information as x_{t-1},
+x_{t-2}, b_t), each divided by its own rms s0, s1, s2 so that every BF16 channel is of order
+one.  The network learns what linear extrapolation misses: prediction
+x_hat = 2 x_{t-1} - x_{t-2} + s1 net(inputs), loss = mean((net - (x_t - 2 x_{t-1} + x_{t-2})/s1)^2).
+The solver is always run to the same tolerance: of x_hat and x_{t-1}, the one with the smaller
+residual ||b - A x0|| is the initial guess, so the plain warm start is both fallback and judge.
+The experiment also reports the extrapolation alone (network output taken as zero), so the
+network's own contribution is visible.
+"""
+from __future__ import annotations
+
+import math
+import time
+
+import numpy as np
+
+from . import pk
+
+CH = 16
+LAYERS = ((3, 16), (16, 16), (16, 16), (16, 1))
+
+
+class ConvNet:
+    """Parameters (FP32 master, BF16 copies, flipped BF16 copies, Adam moments) and buffers."""
+
+    def __init__(self, dims, device="cuda", seed=0):
+        import torch
+
+        self.torch = torch
+        self.dims = tuple(int(d) for d in dims)
+        self.n = int(np.prod(self.dims))
+        self.device = device
+        rng = np.random.default_rng(seed)
+        self.W32, self.b32, self.W16, self.Wf16 = [], [], [], []
+        self.mW, self.vW, self.mb, self.vb, self.dW, self.db = [], [], [], [], [], []
+        for li, (cin, cout) in enumerate(LAYERS):
+            w = np.zeros((27, CH, CH), dtype=np.float32)
+            std = math.sqrt(2.0 / (27 * cin)) if li < len(LAYERS) - 1 else 1e-3
+            w[:, :cout, :cin] = rng.standard_normal((27, cout, cin)) * std
+            W32 = torch.from_numpy(w).to(device)
+            self.W32.append(W32)
+            self.b32.append(torch.zeros(CH, dtype=torch.float32, device=device))
+            self.W16.append(W32.to(torch.bfloat16).contiguous())
+            self.Wf16.append(torch.empty_like(self.W16[-1]))
+            for lst, shape in ((self.mW, W32.shape), (self.vW, W32.shape), (self.dW, W32.shape),
+                               (self.mb, (CH,)), (self.vb, (CH,)), (self.db, (CH,))):
+                lst.append(torch.zeros(shape, dtype=torch.float32, device=device))
+        vox = self.dims + (CH,)
+        self.acts = [torch.zeros(vox, dtype=torch.bfloat16, device=device) for _ in range(len(LAYERS))]
+        self.grads = [torch.zeros(vox, dtype=torch.bfloat16, device=device) for _ in range(len(LAYERS))]
+        self.out = torch.zeros(self.dims, dtype=torch.float32, device=device)
+        self.scales = torch.zeros(3, dtype=torch.float64, device=device)
+        self.loss = torch.zeros(1, dtype=torch.float64, device=device)
+        self.scratch = torch.zeros(pk.warmstart_scratch_doubles(), dtype=torch.float64, device=device)
+        self.wscratch = torch.zeros(pk.conv3d_wgrad_scratch_floats(self.dims), dtype=torch.float32,
+                                    device=device)
+        self.step = 0
+        self.refresh_flipped()
+
+    def refresh_flipped(self):
+        for w16, wf in zip(self.W16, self.Wf16):
+            pk.conv3d_flip(w16, wf)
+
+    def pack(self, xm1, xm2, b):
+        """acts[0] = packed network input; scales = (s0, s1, s2)."""
+        pk.warmstart_input(self.n, xm1, xm2, b, self.acts[0], self.scales, self.scratch)
+
+    def forward(self):
+        """out = net(acts[0]) (FP32 channel 0); hidden activations kept for backward."""
+        for li in range(len(LAYERS)):
+            last = li == len(LAYERS) - 1
+            pk.conv3d_fwd(self.acts[li], self.W16[li], self.b32[li],
+                          self.out if last else self.acts[li + 1], self.dims,
+                          relu=not last, out_f32=last)
+        return self.out
+
+    def backward(self):
+        """grads[3] holds dL/d(out) (BF16, channel 0): weight/bias gradients into dW, db."""
+        for li in range(len(LAYERS) - 1, -1, -1):
+            pk.conv3d_wgrad(self.acts[li], self.grads[li], self.wscratch, self.dW[li], self.db[li],
+                            self.dims)
+            if li > 0:
+                # dL/dz_{li-1} = conv(g, flipped W) masked by the ReLU derivative
+                pk.conv3d_fwd(self.grads[li], self.Wf16[li], None, self.grads[li - 1], self.dims,
+                              relu=False, out_f32=False, mask=self.acts[li])
+
+    def adam(self, lr=1e-3):
+        self.step += 1
+        for li in range(len(LAYERS)):
+            pk.adam_step(self.W32[li], self.dW[li], self.mW[li], self.vW[li], lr, self.step,
+                         p_bf16=self.W16[li])
+            pk.adam_step(self.b32[li], self.db[li], self.mb[li], self.vb[li], lr, self.step)
+        self.refresh_flipped()
+
+    def train_sample(self, xm1, xm2, b, xt, lr=1e-3):
+        self.pack(xm1, xm2, b)
+        self.forward()
+        pk.warmstart_loss(self.n, self.out, xt, xm1, xm2, self.scales, self.grads[-1], self.loss,
+                          self.scratch)
+        self.backward()
+        self.adam(lr)
+
+    def predict(self, xm1, xm2, b, xhat):
+        self.pack(xm1, xm2, b)
+        self.forward()
+        pk.warmstart_apply(self.n, self.out, xm1, xm2, self.scales, xhat)
+
+
+def run_transient(k=64, steps=300, train_last=150, epochs=30, lr=1e-3, tol=1e-8, seed=0,
+                  device="cuda", log=None):
+    """The transient experiment: solve the whole sequence with the x_{t-1} warm start, train on
+    steps 2..train_last, then re-solve steps train_last+1..steps from (a) the linear
+    extrapolation 2 x_{t-1} - x_{t-2} and (b) the learned guess, each judged against x_{t-1} by
+    its residual.  Returns per-step iteration counts and times of all three, plus training
+    statistics."""
+    import torch
+
+    from . import workloads as W
+
+    T = W.transient_heat(k, steps=steps, seed=seed)
+    A = pk.CSRMatrix.from_workload(T.M)
+    n = T.M.n
+    dt = T.dt
+    zeros = torch.zeros(n, dtype=torch.float64, device=device)
+    xs = [zeros.clone(), zeros.clone()]  # x_{-1}, x_0
+    bs = [None, None]
+    base_iters, base_ms = [], []
+    for t in range(1, steps + 1):
+        f = torch.from_numpy(T.source(t)).to(device)
+        b = xs[-1] + dt * f
+        x = xs[-1].clone()
+        info = pk.cg_solve(A, b, x, tol=tol, maxit=10_000)
+        assert info["status"] == pk.PK_OK, info
+        base_iters.append(info["iters"])
+        base_ms.append(info["solve_ms"])
+        xs.append(x)
+        bs.append(b)
+    # sample t: x_{t-1} = xs[t], x_{t-2} = xs[t-1], b_t = bs[t+1], target x_t = xs[t+1]
+    net = ConvNet((k, k, k), device=device, seed=seed)
+    train = list(range(2, train_last + 1))
+    rng = np.random.default_rng(seed)
+    t0 = time.perf_counter()
+    final_loss = None
+    for ep in range(epochs):
+        order = rng.permutation(train)
+        acc = 0.0
+        for t in order:
+            net.train_sample(xs[t], xs[t - 1], bs[t + 1], xs[t + 1], lr=lr)
+            if ep == epochs - 1:
+                acc += float(net.loss.item())
+        if ep == epochs - 1:
+            final_loss = acc / len(train)
+        if log:
+            log(f"epoch {ep}")
+    torch.cuda.synchronize()
+    train_s = time.perf_counter() - t0
+
+    xhat = zeros.clone()
+    r2 = torch.zeros(2, dtype=torch.float64, device=device)
+
+    def evaluate(use_net):
+        iters, ms, chosen, ratio = [], [], 0, []
+        for t in range(train_last + 1, steps + 1):
+            b = bs[t + 1]
+            st = torch.cuda.Event(enable_timing=True)
+            en = torch.cuda.Event(enable_timing=True)
+            st.record()
+            if use_net:
+                net.predict(xs[t], xs[t - 1], b, xhat)
+            else:
+                pk.warmstart_apply(n, None, xs[t], xs[t - 1], net.scales, xhat)
+            pk.residual_norm2(A, b, xhat, r2[0:1])
+            pk.residual_norm2(A, b, xs[t], r2[1:2])
+            en.record()
+            torch.cuda.synchronize()
+            ra, rb = float(r2[0]), float(r2[1])
+            ratio.append(np.sqrt(ra / rb) if rb > 0 else 1.0)
+            pick = ra < rb
+            chosen += int(pick)
+            x = (xhat if pick else xs[t]).clone()
+            info = pk.cg_solve(A, b, x, tol=tol, maxit=10_000)
+            assert info["status"] == pk.PK_OK, info
+            iters.append(info["iters"])
+            ms.append(info["solve_ms"] + st.elapsed_time(en))
+        return iters, ms, chosen, float(np.mean(ratio))
+
+    ex_iters, ex_ms, ex_chosen, ex_ratio = evaluate(False)
+    ln_iters, ln_ms, ln_chosen, ln_ratio = evaluate(True)
+    ev = slice(train_last, steps)
+    return {
+        "k": k, "n": n, "steps": steps, "train_samples": len(train), "epochs": epochs,
+        "train_s": train_s, "final_epoch_loss": final_loss,
+        "baseline_iters_eval": base_iters[ev], "extrap_iters_eval": ex_iters,
+        "learned_iters_eval": ln_iters,
+        "baseline_mean_iters": float(np.mean(base_iters[ev])),
+        "extrap_mean_iters": float(np.mean(ex_iters)),
+        "learned_mean_iters": float(np.mean(ln_iters)),
+        "baseline_mean_ms": float(np.mean(base_ms[ev])),
+        "extrap_mean_ms": float(np.mean(ex_ms)),
+        "learned_mean_ms": float(np.mean(ln_ms)),
+        "extrap_residual_ratio": ex_ratio, "learned_residual_ratio": ln_ratio,
+        "extrap_chosen_steps": ex_chosen, "learned_chosen_steps": ln_chosen,
+    }

@@ -102,3 +102,15 @@ def test_network_gradients_match_finite_differences():
         lm, _, _ = C.loss_and_grads(pb, x, target, rounding=False)
         fd = (lp - lm) / (2 * h)
         assert abs(fd - grads[layer][1][co]) <= 1e-6 * max(abs(fd), 1e-3)
+
+
+def test_adam_first_step_is_lr_times_sign():
+    """With m = v = 0, the first Adam step moves every parameter by lr * g / (|g| + eps)."""
+    g = np.array([3.0, -0.5, 1e-3, 0.0])
+    p, m, v = C.adam_step(np.ones(4), g, np.zeros(4), np.zeros(4), 1, lr=0.01)
+    np.testing.assert_allclose(p, 1.0 - 0.01 * g / (np.abs(g) + 1e-8), rtol=0, atol=1e-15)
+    # a constant gradient keeps the bias-corrected step at lr * sign(g)
+    for step in range(2, 6):
+        p2, m, v = C.adam_step(p, g, m, v, step, lr=0.01)
+        np.testing.assert_allclose(p - p2, 0.01 * g / (np.abs(g) + 1e-8), rtol=1e-12, atol=1e-15)
+        p = p2
