@@ -409,6 +409,9 @@ def bench_forms(pk, torch, dev, args):
     batched: 512 shifted 2D Laplacians on rectangles with sides log-uniform in [32, 256], tol
     1e-10, one persistent launch (FP64 and mixed precision) vs 512 sequential plain solves.
     mixed: the 160^3 Laplacian to 1e-8, mixed precision vs FP64, error of the mixed solution.
+    learned_warm_start: the transient heat sequence on 64^3 (300 implicit steps, CG to 1e-8),
+    the network trained on steps 2-150 and evaluated on 151-300 against the x_{t-1} warm start
+    (and the linear extrapolation alone), plus the BF16 convolution kernels' throughput.
     """
     out = {}
     a = W.convdiff_3d(128)
@@ -491,6 +494,53 @@ def bench_forms(pk, torch, dev, args):
                     "rel_error_vs_fp64": float(torch.linalg.norm(xm - x64) / torch.linalg.norm(x64)),
                     "inner_bytes_per_iter": 8 * a.nnz + 40 * a.n}
     A.close()
+
+    from paper_1410_4054_gb300 import warmstart as WS
+
+    res = WS.run_transient(k=64, steps=300, train_last=150, epochs=30)
+    lw = {k: v for k, v in res.items() if not isinstance(v, list)}
+    lw["train_ms_per_sample"] = 1e3 * res["train_s"] / (res["epochs"] * res["train_samples"])
+    lw["iteration_gain_vs_plain_warm_start"] = res["baseline_mean_iters"] - res["learned_mean_iters"]
+    lw["conv"] = conv_throughput(pk, torch, dev, (64, 64, 64))
+    out["learned_warm_start"] = lw
+    return out
+
+
+def conv_throughput(pk, torch, dev, dims, reps=20):
+    """CUDA-event times of the BF16 conv kernels on a 16 -> 16 channel layer: forward (ReLU,
+    BF16 out), backward-data (flipped weights, ReLU mask) and weight gradient.  FLOPs are those
+    of the padded implicit GEMM, 2 x 27 x 16 x 16 per voxel."""
+    nvox = int(np.prod(dims))
+    g = torch.Generator(device=dev).manual_seed(0)
+    X = torch.randn(dims + (16,), generator=g, device=dev).to(torch.bfloat16)
+    Gr = torch.randn(dims + (16,), generator=g, device=dev).to(torch.bfloat16)
+    Wt = (0.1 * torch.randn((27, 16, 16), generator=g, device=dev)).to(torch.bfloat16)
+    Wf = torch.empty_like(Wt)
+    pk.conv3d_flip(Wt, Wf)
+    bias = torch.zeros(16, device=dev)
+    Y = torch.empty_like(X)
+    dX = torch.empty_like(X)
+    scratch = torch.zeros(pk.conv3d_wgrad_scratch_floats(dims), device=dev)
+    dW = torch.zeros((27, 16, 16), device=dev)
+    db = torch.zeros(16, device=dev)
+    calls = {"fwd": lambda: pk.conv3d_fwd(X, Wt, bias, Y, dims, relu=True),
+             "bwd_data": lambda: pk.conv3d_fwd(Gr, Wf, None, dX, dims, relu=False, mask=X),
+             "wgrad": lambda: pk.conv3d_wgrad(X, Gr, scratch, dW, db, dims)}
+    flops = 2 * 27 * 16 * 16 * nvox
+    out = {"dims": list(dims), "gflop_per_call": flops / 1e9}
+    for name, fn in calls.items():
+        for _ in range(3):
+            fn()
+        st, en = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        st.record()
+        for _ in range(reps):
+            fn()
+        en.record()
+        torch.cuda.synchronize()
+        us = 1e3 * st.elapsed_time(en) / reps
+        out[f"{name}_us"] = us
+        out[f"{name}_tflops"] = flops / (us * 1e-6) / 1e12
     return out
 
 

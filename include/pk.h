@@ -263,18 +263,19 @@ pk_status pk_conv3d_wgrad(const void* A, const void* G, float* scratch, float* d
                           int32_t D, int32_t H, int32_t W, void* stream);
 /* Wf[26 - t][ci][co] = W[t][co][ci]: weights of the backward-data convolution. */
 pk_status pk_conv3d_flip(const void* W, void* Wf, void* stream);
-/* Network input X16 = bf16(x_{t-1}/s0, (x_{t-1} - x_{t-2})/s1, (b - x_{t-1})/s2, 0...) with
- * s0..s2 the rms of those three vectors, written to scales[0..2] (3 doubles); scratch:
- * pk_warmstart_scratch_doubles() doubles. */
-int64_t pk_warmstart_scratch_doubles(void);
-pk_status pk_warmstart_input(int64_t n, const double* xm1, const double* xm2, const double* b,
+/* Network input from the residual of the linear extrapolation e = 2 x_{t-1} - x_{t-2} of the
+ * system A x_t = b (A: the n x n matrix of the time step, n = D H W):
+ * r = b - A e, d = diag(A) (1 where a row has no nonzero diagonal entry),
+ * X16 = bf16((r/d)/s0, r/s1, d/s2, 0...) with s0, s1, s2 the rms of r/d, r, d written to
+ * scales[0..2] (1 where zero; 3 doubles); scratch: pk_warmstart_scratch_doubles() doubles. */
+pk_status pk_warmstart_input(pk_csr* A, const double* xm1, const double* xm2, const double* b,
                              void* X16, double* scales, double* scratch, void* stream);
-/* Target y = (x_t - 2 x_{t-1} + x_{t-2}) / s1 (the part linear extrapolation misses):
+/* Target y = (x_t - 2 x_{t-1} + x_{t-2}) / s0 (the part linear extrapolation misses):
  * *loss = mean((out - y)^2), G = bf16(2 (out - y) / n) in channel 0 (other channels 0). */
 pk_status pk_warmstart_loss(int64_t n, const float* out, const double* xt, const double* xm1,
                             const double* xm2, const double* scales, void* G, double* loss,
                             double* scratch, void* stream);
-/* x_hat = 2 x_{t-1} - x_{t-2} + s1 out; out = NULL gives the linear extrapolation alone. */
+/* x_hat = 2 x_{t-1} - x_{t-2} + s0 out; out = NULL gives the linear extrapolation alone. */
 pk_status pk_warmstart_apply(int64_t n, const float* out, const double* xm1, const double* xm2,
                              const double* scales, double* xhat, void* stream);
 /* Adam (Kingma & Ba) on FP32 parameters, step >= 1; p_bf16 (nullable) receives a BF16 copy. */

@@ -97,6 +97,40 @@ def loss_and_grads(params, x16: np.ndarray, target: np.ndarray, rounding: bool =
     return loss, out, grads
 
 
+def warmstart_input(row_ptr, col, val, xm1, xm2, b):
+    """Network input of the learned initial guess before BF16 rounding, and its scales.
+
+    The linear extrapolation e = 2 x_{t-1} - x_{t-2} of the time step A x_t = b leaves the
+    residual r = b - A e; with d = diag(A) (1 where a row has no nonzero diagonal entry) the
+    channels are (r/d)/s0, r/s1, d/s2, zero elsewhere, s0..s2 the rms of r/d, r, d (1 where
+    zero).  Returns (X[n][16], (s0, s1, s2))."""
+    n = len(row_ptr) - 1
+    e = 2.0 * np.asarray(xm1, dtype=np.float64) - np.asarray(xm2, dtype=np.float64)
+    r = np.array(b, dtype=np.float64)
+    d = np.zeros(n)
+    for i in range(n):
+        for j in range(row_ptr[i], row_ptr[i + 1]):
+            r[i] -= val[j] * e[col[j]]
+            if col[j] == i:
+                d[i] = val[j]
+    d[d == 0.0] = 1.0
+    z = r / d
+    scales = []
+    for v in (z, r, d):
+        s = float(np.sqrt(np.mean(v * v)))
+        scales.append(s if s > 0 else 1.0)
+    X = np.zeros((n, 16))
+    X[:, 0] = z / scales[0]
+    X[:, 1] = r / scales[1]
+    X[:, 2] = d / scales[2]
+    return X, tuple(scales)
+
+
+def warmstart_target(xt, xm1, xm2, s0):
+    """What the network is trained to output: (x_t - (2 x_{t-1} - x_{t-2})) / s0."""
+    return (np.asarray(xt) - (2.0 * np.asarray(xm1) - np.asarray(xm2))) / s0
+
+
 def adam_step(p, g, m, v, step, lr=1e-3, beta1=0.9, beta2=0.999, eps=1e-8):
     """One Adam update (Kingma & Ba, ICLR 2015, Algorithm 1) in FP64; returns (p, m, v)."""
     m = beta1 * m + (1 - beta1) * g

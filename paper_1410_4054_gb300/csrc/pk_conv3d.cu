@@ -261,17 +261,38 @@ __device__ __forceinline__ void grid_sums(int n, double* scratch, F&& f, double 
 
 constexpr int kWsGrid = 152;
 
-// scales = rms of (x_{t-1}, x_{t-1} - x_{t-2}, b_t - x_{t-1}) (1 where zero).
-__global__ void __launch_bounds__(kBlock) k_ws_rms(int n, const double* xm1, const double* xm2,
-                                                   const double* b, double* scales,
-                                                   double* scratch) {
+// Residual of the linear extrapolation e = 2 x_{t-1} - x_{t-2} in row i:
+// r = b_i - sum_j a_ij e_j; d = a_ii (1 where the row has no nonzero diagonal entry).
+__device__ __forceinline__ void ws_row(const int32_t* __restrict__ rp, const int32_t* __restrict__ ci,
+                                       const double* __restrict__ va, const double* xm1,
+                                       const double* xm2, const double* b, int i, double& r,
+                                       double& d) {
+  double s = 0.0;
+  d = 0.0;
+  for (int j = rp[i]; j < rp[i + 1]; ++j) {
+    const int c = ci[j];
+    const double e = 2.0 * xm1[c] - xm2[c];
+    s = fma(va[j], e, s);
+    if (c == i) d = va[j];
+  }
+  r = b[i] - s;
+  if (d == 0.0) d = 1.0;
+}
+
+// scales = rms of (r / d, r, d) (1 where zero).
+__global__ void __launch_bounds__(kBlock) k_ws_rms(int n, const int32_t* rp, const int32_t* ci,
+                                                   const double* va, const double* xm1,
+                                                   const double* xm2, const double* b,
+                                                   double* scales, double* scratch) {
   double out[3];
   bool last;
   grid_sums<3>(n, scratch, [&](int i, double (&v)[3]) {
-    const double d = xm1[i] - xm2[i], f = b[i] - xm1[i];
-    v[0] = fma(xm1[i], xm1[i], v[0]);
-    v[1] = fma(d, d, v[1]);
-    v[2] = fma(f, f, v[2]);
+    double r, d;
+    ws_row(rp, ci, va, xm1, xm2, b, i, r, d);
+    const double z = r / d;
+    v[0] = fma(z, z, v[0]);
+    v[1] = fma(r, r, v[1]);
+    v[2] = fma(d, d, v[2]);
   }, out, last);
   if (last && threadIdx.x == 0) {
     for (int k = 0; k < 3; ++k) {
@@ -281,26 +302,29 @@ __global__ void __launch_bounds__(kBlock) k_ws_rms(int n, const double* xm1, con
   }
 }
 
-// X16[v] = bf16(x_{t-1}/s0, (x_{t-1} - x_{t-2})/s1, (b - x_{t-1})/s2, 0, ..., 0): the same
-// information as (x_{t-1}, x_{t-2}, b), each channel of order one so that BF16 resolves it.
-__global__ void k_ws_pack(int n, const double* xm1, const double* xm2, const double* b,
+// X16[v] = bf16((r/d)/s0, r/s1, d/s2, 0, ..., 0): the Jacobi-scaled residual of the
+// extrapolation, the residual itself and the diagonal, each channel of order one.
+__global__ void k_ws_pack(int n, const int32_t* rp, const int32_t* ci, const double* va,
+                          const double* xm1, const double* xm2, const double* b,
                           const double* scales, __nv_bfloat16* X16) {
   const int v = blockIdx.x * blockDim.x + threadIdx.x;
   if (v >= n) return;
+  double r, d;
+  ws_row(rp, ci, va, xm1, xm2, b, v, r, d);
   __nv_bfloat16* o = X16 + (size_t)v * kCh;
-  o[0] = __float2bfloat16_rn((float)(xm1[v] / scales[0]));
-  o[1] = __float2bfloat16_rn((float)((xm1[v] - xm2[v]) / scales[1]));
-  o[2] = __float2bfloat16_rn((float)((b[v] - xm1[v]) / scales[2]));
+  o[0] = __float2bfloat16_rn((float)(r / d / scales[0]));
+  o[1] = __float2bfloat16_rn((float)(r / scales[1]));
+  o[2] = __float2bfloat16_rn((float)(d / scales[2]));
   for (int c = 3; c < kCh; ++c) o[c] = __float2bfloat16_rn(0.f);
 }
 
-// target y = (x_t - 2 x_{t-1} + x_{t-2}) / s1 (what linear extrapolation misses, in units of
-// the last step's change); G[v][0] = bf16(2 (out - y) / n); loss = mean((out - y)^2).
+// target y = (x_t - 2 x_{t-1} + x_{t-2}) / s0 (what linear extrapolation misses, in units of
+// the Jacobi-scaled residual); G[v][0] = bf16(2 (out - y) / n); loss = mean((out - y)^2).
 __global__ void __launch_bounds__(kBlock) k_ws_loss(int n, const float* out, const double* xt,
                                                     const double* xm1, const double* xm2,
                                                     const double* scales, __nv_bfloat16* G,
                                                     double* loss, double* scratch) {
-  const double is = 1.0 / scales[1];
+  const double is = 1.0 / scales[0];
   double sum[1];
   bool last;
   grid_sums<1>(n, scratch, [&](int i, double (&v)[1]) {
@@ -313,13 +337,13 @@ __global__ void __launch_bounds__(kBlock) k_ws_loss(int n, const float* out, con
   if (last && threadIdx.x == 0) *loss = sum[0] / n;
 }
 
-// x_hat = 2 x_{t-1} - x_{t-2} + s1 out (out == nullptr: the extrapolation alone).
+// x_hat = 2 x_{t-1} - x_{t-2} + s0 out (out == nullptr: the extrapolation alone).
 __global__ void k_ws_apply(int n, const float* out, const double* xm1, const double* xm2,
                            const double* scales, double* xhat) {
   const int v = blockIdx.x * blockDim.x + threadIdx.x;
   if (v >= n) return;
   const double e = 2.0 * xm1[v] - xm2[v];
-  xhat[v] = out ? fma(scales[1], (double)out[v], e) : e;
+  xhat[v] = out ? fma(scales[0], (double)out[v], e) : e;
 }
 
 // Adam on FP32 master parameters, optional BF16 copy.
@@ -420,17 +444,18 @@ pk_status pk_conv3d_flip(const void* W, void* Wf, void* stream) {
 
 int64_t pk_warmstart_scratch_doubles(void) { return 3 * kWsGrid + 8; }
 
-pk_status pk_warmstart_input(int64_t n, const double* xm1, const double* xm2, const double* b,
+pk_status pk_warmstart_input(pk_csr* A, const double* xm1, const double* xm2, const double* b,
                              void* X16, double* scales, double* scratch, void* stream) {
-  if (n <= 0 || n >= (int64_t(1) << 31) || !xm1 || !xm2 || !b || !X16 || !scales || !scratch) {
+  if (!A || !xm1 || !xm2 || !b || !X16 || !scales || !scratch) {
     set_error("pk_warmstart_input: bad arguments");
     return PK_ERR_ARG;
   }
+  const int n = A->n;
   cudaStream_t s = (cudaStream_t)stream;
   PK_CUDA(cudaMemsetAsync(scratch + 3 * kWsGrid, 0, sizeof(double), s));
-  k_ws_rms<<<kWsGrid, kBlock, 0, s>>>((int)n, xm1, xm2, b, scales, scratch);
-  k_ws_pack<<<(int)((n + 255) / 256), 256, 0, s>>>((int)n, xm1, xm2, b, scales,
-                                                    static_cast<__nv_bfloat16*>(X16));
+  k_ws_rms<<<kWsGrid, kBlock, 0, s>>>(n, A->rp, A->ci, A->va, xm1, xm2, b, scales, scratch);
+  k_ws_pack<<<(n + 255) / 256, 256, 0, s>>>(n, A->rp, A->ci, A->va, xm1, xm2, b, scales,
+                                             static_cast<__nv_bfloat16*>(X16));
   PK_CUDA(cudaGetLastError());
   return PK_OK;
 }

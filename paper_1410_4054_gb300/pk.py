@@ -78,7 +78,7 @@ EXPORTS = {
                                   C.c_int32, C.c_int32, C.c_int32, C.c_void_p]),
     "pk_conv3d_flip": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p]),
     "pk_warmstart_scratch_doubles": (C.c_int64, []),
-    "pk_warmstart_input": (C.c_int, [C.c_int64, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p,
+    "pk_warmstart_input": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p,
                                      C.c_void_p, C.c_void_p, C.c_void_p]),
     "pk_warmstart_loss": (C.c_int, [C.c_int64, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p,
                                     C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p]),
@@ -332,8 +332,8 @@ def warmstart_scratch_doubles() -> int:
     return int(lib().pk_warmstart_scratch_doubles())
 
 
-def warmstart_input(n, xm1, xm2, b, X16, scales, scratch, stream=None):
-    _check(lib().pk_warmstart_input(int(n), _ptr(xm1), _ptr(xm2), _ptr(b), _ptr(X16), _ptr(scales),
+def warmstart_input(A: CSRMatrix, xm1, xm2, b, X16, scales, scratch, stream=None):
+    _check(lib().pk_warmstart_input(A.handle, _ptr(xm1), _ptr(xm2), _ptr(b), _ptr(X16), _ptr(scales),
                                     _ptr(scratch), _stream_ptr(stream)), "pk_warmstart_input")
 
 

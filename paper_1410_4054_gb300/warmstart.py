@@ -1,15 +1,19 @@
 """Learned initial guess for a sequence of implicit time steps (a BF16 convolutional network).
 
 A 4-layer 3x3x3 convolutional network (3 -> 16 -> 16 -> 16 -> 1 channels, ReLU between
-layers, channel counts padded to 16) predicts the next time step from the previous two
-solutions and the new right-hand side.  Every numerical step runs in the library's CUDA
-kernels through the C ABI (BF16 tensor-core implicit-GEMM convolutions with FP32
-accumulation, FP32 Adam); this module only owns the buffers and sequences the calls.
+layers, channel counts padded to 16) corrects the linear extrapolation of the solution
+sequence.  Every numerical step runs in the library's CUDA kernels through the C ABI (BF16
+tensor-core implicit-GEMM convolutions with FP32 accumulation, FP32 Adam); this module only
+owns the buffers and sequences the calls.
 
-Inputs: x_{t-1}, x_{t-1} - x_{t-2} and b_t - x_{t-1} (the same information as x_{t-1},
-x_{t-2}, b_t), each divided by its own rms s0, s1, s2 so that every BF16 channel is of order
-one.  The network learns what linear extrapolation misses: prediction
-x_hat = 2 x_{t-1} - x_{t-2} + s1 net(inputs), loss = mean((net - (x_t - 2 x_{t-1} + x_{t-2})/s1)^2).
+Input: the residual r = b_t - A e of the extrapolation e = 2 x_{t-1} - x_{t-2}, as r/d (one
+Jacobi step, d = diag(A)), r and d, each divided by its own rms s0, s1, s2 so that every BF16
+channel is of order one.  The exact correction x_t - e = A^{-1} r is a function of r and of
+the coefficients, which the translation-invariant network sees only through d and r, so the
+network is told nothing it would have to memorise position by position.  Prediction
+x_hat = e + s0 net(input), loss = mean((net - (x_t - e)/s0)^2).  The weights start at the
+identity on channel 0 (relu(z) - relu(-z) = z through two hidden channels), i.e. at the Jacobi
+step, and training moves them from there.
 The solver is always run to the same tolerance: of x_hat and x_{t-1}, the one with the smaller
 residual ||b - A x0|| is the initial guess, so the plain warm start is both fallback and judge.
 The experiment also reports the extrapolation alone (network output taken as zero), so the
@@ -28,6 +32,29 @@ CH = 16
 LAYERS = ((3, 16), (16, 16), (16, 16), (16, 1))
 
 
+def initial_weights(seed=0, noise_std=1e-3):
+    """FP32 weights [27][16][16] and biases [16] of the four layers at initialisation: an exact
+    identity on channel 0 through hidden channels 0 (relu(z)) and 1 (relu(-z)) at the centre
+    tap, He-scaled random weights into hidden channels 2..15, and output weights from channels
+    2..15 of standard deviation noise_std."""
+    rng = np.random.default_rng(seed)
+    c = 13  # centre tap (dz, dy, dx) = (0, 0, 0)
+    params = []
+    for li, (cin, cout) in enumerate(LAYERS):
+        w = np.zeros((27, CH, CH), dtype=np.float32)
+        if li < len(LAYERS) - 1:
+            w[:, 2:cout, :cin] = rng.standard_normal((27, cout - 2, cin)) * math.sqrt(2.0 / (27 * cin))
+            if li == 0:
+                w[c, 0, 0], w[c, 1, 0] = 1.0, -1.0
+            else:
+                w[c, 0, 0], w[c, 1, 1] = 1.0, 1.0
+        else:
+            w[:, 0, 2:cin] = rng.standard_normal((27, cin - 2)) * noise_std
+            w[c, 0, 0], w[c, 0, 1] = 1.0, -1.0
+        params.append((w, np.zeros(CH, dtype=np.float32)))
+    return params
+
+
 class ConvNet:
     """Parameters (FP32 master, BF16 copies, flipped BF16 copies, Adam moments) and buffers."""
 
@@ -38,16 +65,12 @@ class ConvNet:
         self.dims = tuple(int(d) for d in dims)
         self.n = int(np.prod(self.dims))
         self.device = device
-        rng = np.random.default_rng(seed)
         self.W32, self.b32, self.W16, self.Wf16 = [], [], [], []
         self.mW, self.vW, self.mb, self.vb, self.dW, self.db = [], [], [], [], [], []
-        for li, (cin, cout) in enumerate(LAYERS):
-            w = np.zeros((27, CH, CH), dtype=np.float32)
-            std = math.sqrt(2.0 / (27 * cin)) if li < len(LAYERS) - 1 else 1e-3
-            w[:, :cout, :cin] = rng.standard_normal((27, cout, cin)) * std
+        for w, bias in initial_weights(seed):
             W32 = torch.from_numpy(w).to(device)
             self.W32.append(W32)
-            self.b32.append(torch.zeros(CH, dtype=torch.float32, device=device))
+            self.b32.append(torch.from_numpy(bias).to(device))
             self.W16.append(W32.to(torch.bfloat16).contiguous())
             self.Wf16.append(torch.empty_like(self.W16[-1]))
             for lst, shape in ((self.mW, W32.shape), (self.vW, W32.shape), (self.dW, W32.shape),
@@ -69,9 +92,9 @@ class ConvNet:
         for w16, wf in zip(self.W16, self.Wf16):
             pk.conv3d_flip(w16, wf)
 
-    def pack(self, xm1, xm2, b):
+    def pack(self, A, xm1, xm2, b):
         """acts[0] = packed network input; scales = (s0, s1, s2)."""
-        pk.warmstart_input(self.n, xm1, xm2, b, self.acts[0], self.scales, self.scratch)
+        pk.warmstart_input(A, xm1, xm2, b, self.acts[0], self.scales, self.scratch)
 
     def forward(self):
         """out = net(acts[0]) (FP32 channel 0); hidden activations kept for backward."""
@@ -100,16 +123,16 @@ class ConvNet:
             pk.adam_step(self.b32[li], self.db[li], self.mb[li], self.vb[li], lr, self.step)
         self.refresh_flipped()
 
-    def train_sample(self, xm1, xm2, b, xt, lr=1e-3):
-        self.pack(xm1, xm2, b)
+    def train_sample(self, A, xm1, xm2, b, xt, lr=1e-3):
+        self.pack(A, xm1, xm2, b)
         self.forward()
         pk.warmstart_loss(self.n, self.out, xt, xm1, xm2, self.scales, self.grads[-1], self.loss,
                           self.scratch)
         self.backward()
         self.adam(lr)
 
-    def predict(self, xm1, xm2, b, xhat):
-        self.pack(xm1, xm2, b)
+    def predict(self, A, xm1, xm2, b, xhat):
+        self.pack(A, xm1, xm2, b)
         self.forward()
         pk.warmstart_apply(self.n, self.out, xm1, xm2, self.scales, xhat)
 
@@ -148,14 +171,16 @@ def run_transient(k=64, steps=300, train_last=150, epochs=30, lr=1e-3, tol=1e-8,
     train = list(range(2, train_last + 1))
     rng = np.random.default_rng(seed)
     t0 = time.perf_counter()
-    final_loss = None
+    first_loss = final_loss = None
     for ep in range(epochs):
         order = rng.permutation(train)
         acc = 0.0
         for t in order:
-            net.train_sample(xs[t], xs[t - 1], bs[t + 1], xs[t + 1], lr=lr)
-            if ep == epochs - 1:
+            net.train_sample(A, xs[t], xs[t - 1], bs[t + 1], xs[t + 1], lr=lr)
+            if ep in (0, epochs - 1):
                 acc += float(net.loss.item())
+        if ep == 0:
+            first_loss = acc / len(train)
         if ep == epochs - 1:
             final_loss = acc / len(train)
         if log:
@@ -167,14 +192,14 @@ def run_transient(k=64, steps=300, train_last=150, epochs=30, lr=1e-3, tol=1e-8,
     r2 = torch.zeros(2, dtype=torch.float64, device=device)
 
     def evaluate(use_net):
-        iters, ms, chosen, ratio = [], [], 0, []
+        iters, ms, chosen, ratio, kept = [], [], 0, [], []
         for t in range(train_last + 1, steps + 1):
             b = bs[t + 1]
             st = torch.cuda.Event(enable_timing=True)
             en = torch.cuda.Event(enable_timing=True)
             st.record()
             if use_net:
-                net.predict(xs[t], xs[t - 1], b, xhat)
+                net.predict(A, xs[t], xs[t - 1], b, xhat)
             else:
                 pk.warmstart_apply(n, None, xs[t], xs[t - 1], net.scales, xhat)
             pk.residual_norm2(A, b, xhat, r2[0:1])
@@ -185,19 +210,20 @@ def run_transient(k=64, steps=300, train_last=150, epochs=30, lr=1e-3, tol=1e-8,
             ratio.append(np.sqrt(ra / rb) if rb > 0 else 1.0)
             pick = ra < rb
             chosen += int(pick)
+            kept.append(np.sqrt(min(ra, rb) / rb) if rb > 0 else 1.0)
             x = (xhat if pick else xs[t]).clone()
             info = pk.cg_solve(A, b, x, tol=tol, maxit=10_000)
             assert info["status"] == pk.PK_OK, info
             iters.append(info["iters"])
             ms.append(info["solve_ms"] + st.elapsed_time(en))
-        return iters, ms, chosen, float(np.mean(ratio))
+        return iters, ms, chosen, float(np.mean(ratio)), float(max(kept))
 
-    ex_iters, ex_ms, ex_chosen, ex_ratio = evaluate(False)
-    ln_iters, ln_ms, ln_chosen, ln_ratio = evaluate(True)
+    ex_iters, ex_ms, ex_chosen, ex_ratio, ex_kept = evaluate(False)
+    ln_iters, ln_ms, ln_chosen, ln_ratio, ln_kept = evaluate(True)
     ev = slice(train_last, steps)
     return {
         "k": k, "n": n, "steps": steps, "train_samples": len(train), "epochs": epochs,
-        "train_s": train_s, "final_epoch_loss": final_loss,
+        "train_s": train_s, "first_epoch_loss": first_loss, "final_epoch_loss": final_loss,
         "baseline_iters_eval": base_iters[ev], "extrap_iters_eval": ex_iters,
         "learned_iters_eval": ln_iters,
         "baseline_mean_iters": float(np.mean(base_iters[ev])),
@@ -208,4 +234,5 @@ def run_transient(k=64, steps=300, train_last=150, epochs=30, lr=1e-3, tol=1e-8,
         "learned_mean_ms": float(np.mean(ln_ms)),
         "extrap_residual_ratio": ex_ratio, "learned_residual_ratio": ln_ratio,
         "extrap_chosen_steps": ex_chosen, "learned_chosen_steps": ln_chosen,
+        "extrap_max_kept_ratio": ex_kept, "learned_max_kept_ratio": ln_kept,
     }

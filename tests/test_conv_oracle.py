@@ -114,3 +114,58 @@ def test_adam_first_step_is_lr_times_sign():
         p2, m, v = C.adam_step(p, g, m, v, step, lr=0.01)
         np.testing.assert_allclose(p - p2, 0.01 * g / (np.abs(g) + 1e-8), rtol=1e-12, atol=1e-15)
         p = p2
+
+
+def _csr(dense):
+    rp, ci, va = [0], [], []
+    for row in dense:
+        nz = np.nonzero(row)[0]
+        ci.extend(nz.tolist())
+        va.extend(row[nz].tolist())
+        rp.append(len(ci))
+    return np.array(rp), np.array(ci), np.array(va)
+
+
+def test_warmstart_input_diagonal_matrix_gives_exact_correction():
+    """For a diagonal A one Jacobi step is exact: e + s0 X[:,0] = A^{-1} b, and the target
+    equals X[:,0]."""
+    r = rng(9)
+    d = 1.0 + r.random(40)
+    xm1, xm2, b = r.standard_normal((3, 40))
+    X, (s0, s1, s2) = C.warmstart_input(*_csr(np.diag(d)), xm1, xm2, b)
+    e = 2.0 * xm1 - xm2
+    np.testing.assert_allclose(e + s0 * X[:, 0], b / d, rtol=1e-14, atol=1e-14)
+    np.testing.assert_allclose(C.warmstart_target(b / d, xm1, xm2, s0), X[:, 0], rtol=1e-12, atol=1e-14)
+    np.testing.assert_allclose(s2 * X[:, 2], d, rtol=1e-15)
+    assert abs(np.sqrt(np.mean(X[:, 0] ** 2)) - 1.0) < 1e-14
+    assert not X[:, 3:].any()
+
+
+def test_warmstart_input_brute_force():
+    r = rng(10)
+    n = 7
+    dense = r.standard_normal((n, n)) * (r.random((n, n)) < 0.5)
+    dense[3, 3] = 0.0                       # no diagonal entry: d = 1
+    np.fill_diagonal(dense[:3, :3], 2.0 + r.random(3))
+    xm1, xm2, b = r.standard_normal((3, n))
+    X, (s0, s1, s2) = C.warmstart_input(*_csr(dense), xm1, xm2, b)
+    for i in range(n):
+        res = b[i] - sum(dense[i, j] * (2 * xm1[j] - xm2[j]) for j in range(n))
+        di = dense[i, i] if dense[i, i] != 0 else 1.0
+        assert abs(X[i, 1] * s1 - res) <= 1e-13 * max(1.0, abs(res))
+        assert abs(X[i, 0] * s0 - res / di) <= 1e-13 * max(1.0, abs(res / di))
+        assert X[i, 2] * s2 == pytest.approx(di, rel=1e-15)
+
+
+def test_warmstart_input_exact_extrapolation_is_zero_residual():
+    """If x_t lies on the line through x_{t-2}, x_{t-1} the residual is zero (integer data, so
+    exactly), the residual channels are zero and their scales fall back to 1."""
+    r = rng(11)
+    dense = np.diag(r.integers(2, 5, 6).astype(float)) + np.eye(6, k=1)
+    xm2, dx = r.integers(-4, 5, (2, 6)).astype(float)
+    xm1 = xm2 + dx
+    b = dense @ (xm1 + dx)
+    X, (s0, s1, s2) = C.warmstart_input(*_csr(dense), xm1, xm2, b)
+    assert (s0, s1) == (1.0, 1.0)
+    assert not X[:, :2].any()
+    np.testing.assert_allclose(X[:, 2] * s2, np.diag(dense), rtol=1e-15)

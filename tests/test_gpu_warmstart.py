@@ -80,24 +80,63 @@ def test_conv_backward_data_and_weights_match_oracle(dims):
     assert rel_l2(host(db), g.sum(axis=(0, 1, 2))) <= 1e-5
 
 
+def test_warmstart_input_matches_oracle():
+    from paper_1410_4054_gb300 import workloads as W
+
+    T = W.transient_heat(16, steps=3, seed=2)
+    A = pk.CSRMatrix.from_workload(T.M)
+    r = np.random.default_rng(6)
+    xm1, xm2, b = r.standard_normal((3, T.M.n))
+    net = WS.ConvNet((16, 16, 16), device=DEV, seed=1)
+    net.pack(A, *(torch.from_numpy(v).to(DEV) for v in (xm1, xm2, b)))
+    torch.cuda.synchronize()
+    X, scales = C.warmstart_input(T.M.row_ptr, T.M.col, T.M.val, xm1, xm2, b)
+    np.testing.assert_allclose(net.scales.cpu().numpy(), scales, rtol=1e-12)
+    got, ref = host(net.acts[0]).reshape(-1, 16), C.bf16(X)
+    # FP64 rows summed in another order can move a value across a BF16 rounding boundary
+    assert np.all(np.abs(got - ref) <= 2.0 ** -8 * np.abs(ref))
+    assert np.mean(got != ref) < 1e-3
+
+
+def _grid_operator(dims, r):
+    """A symmetric 7-point operator on the grid: 1D second differences summed over the three
+    axes with random positive weights, plus 1 on the diagonal (an implicit time step)."""
+    import scipy.sparse as sp
+
+    from paper_1410_4054_gb300 import workloads as W
+
+    eyes = [sp.identity(d, format="csr") for d in dims]
+    M = sp.identity(int(np.prod(dims)), format="csr")
+    for ax, d in enumerate(dims):
+        T = sp.diags([-np.ones(d - 1), 2 * np.ones(d), -np.ones(d - 1)], [-1, 0, 1], format="csr")
+        mats = [T if k == ax else eyes[k] for k in range(3)]
+        M = M + (0.5 + r.random()) * sp.kron(sp.kron(mats[0], mats[1]), mats[2], format="csr")
+    M = M.tocsr()
+    M.sort_indices()
+    return W.CSR(M.shape[0], M.indptr.astype(np.int32), M.indices.astype(np.int32),
+                 M.data.astype(np.float64), "grid7")
+
+
 def test_network_loss_and_gradients_match_oracle():
     dims = (12, 10, 16)
     r = np.random.default_rng(3)
     net = WS.ConvNet(dims, device=DEV, seed=4)
     n = int(np.prod(dims))
+    M = _grid_operator(dims, r)
+    A = pk.CSRMatrix.from_workload(M)
     xm1 = torch.from_numpy(r.standard_normal(n)).to(DEV)
     xm2 = torch.from_numpy(r.standard_normal(n)).to(DEV)
     b = torch.from_numpy(r.standard_normal(n)).to(DEV)
     xt = xm1 + 0.1 * torch.from_numpy(r.standard_normal(n)).to(DEV)
-    net.pack(xm1, xm2, b)
+    net.pack(A, xm1, xm2, b)
     net.forward()
     pk.warmstart_loss(n, net.out, xt, xm1, xm2, net.scales, net.grads[-1], net.loss, net.scratch)
     net.backward()
     torch.cuda.synchronize()
     params = [(host(w), host(bb)) for w, bb in zip(net.W16, net.b32)]
     x16 = host(net.acts[0])
-    s = float(net.scales[1])
-    target = ((xt - 2 * xm1 + xm2) / s).cpu().numpy().reshape(dims)
+    s = float(net.scales[0])
+    target = C.warmstart_target(*(v.cpu().numpy() for v in (xt, xm1, xm2)), s).reshape(dims)
     loss, out, grads = C.loss_and_grads(params, x16, target)
     assert abs(float(net.loss.item()) - loss) <= 1e-5 * loss
     # whole network: hidden BF16 activations can round differently (FP32 vs FP64 sums)
@@ -145,12 +184,14 @@ def test_adam_matches_oracle():
 
 def test_transient_learned_warm_start():
     """Steps 1-150 train the network on the solver's own solutions; steps 151-300 are solved
-    again from the learned guess (with the residual judge).  Every solve reaches the same
-    tolerance; the learned guess may not cost iterations on average."""
+    again from the learned guess with the residual judge.  Every solve reaches the same
+    tolerance.  Whether the network gains is an empirical result, printed here; the test
+    asserts that training lowers the loss, that the judge never starts from a guess with a
+    larger residual than x_{t-1}, and that the learned guess costs no iterations on average."""
     res = WS.run_transient(k=64, steps=300, train_last=150, epochs=30)
     print({k: v for k, v in res.items() if not isinstance(v, list)})
     assert len(res["learned_iters_eval"]) == 150
-    # the judge never lets a guess be worse than x_{t-1} by its residual
-    assert res["learned_residual_ratio"] > 0 and res["extrap_residual_ratio"] > 0
-    assert res["learned_mean_iters"] <= res["baseline_mean_iters"] + 0.5
-    assert res["extrap_mean_iters"] <= res["baseline_mean_iters"] + 0.5
+    assert res["final_epoch_loss"] < 0.5 * res["first_epoch_loss"]
+    assert res["learned_max_kept_ratio"] <= 1.0 and res["extrap_max_kept_ratio"] <= 1.0
+    assert res["learned_mean_iters"] <= res["baseline_mean_iters"]
+    assert res["extrap_mean_iters"] <= res["baseline_mean_iters"]
