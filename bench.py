@@ -358,14 +358,26 @@ def run_ours(args):
             mbd = torch.from_numpy(mb).to(dev)
             mx = torch.zeros(m.n, dtype=torch.float64, device=dev)
             row = {"matrix": f"{kind}_{k}", "n": m.n, "nnz": m.nnz}
-            for variant in ("pipelined", "classical"):
+            for variant, loop in (("pipelined", "graph"), ("pipelined", "persistent"),
+                                  ("classical", "graph")):
+                key = variant if variant == "classical" else f"{variant}_{loop}"
                 best = None
-                for rep in range(2):
-                    mx.zero_()
-                    inf = pk.cg_solve(M, mbd, mx, tol=1e-8, maxit=50_000, variant=variant)
-                    best = inf if best is None or inf["solve_ms"] < best["solve_ms"] else best
-                row[f"{variant}_iters"] = best["iters"]
-                row[f"{variant}_ms"] = best["solve_ms"]
+                try:
+                    for rep in range(2):
+                        mx.zero_()
+                        inf = pk.cg_solve(M, mbd, mx, tol=1e-8, maxit=50_000, variant=variant, loop=loop)
+                        best = inf if best is None or inf["solve_ms"] < best["solve_ms"] else best
+                except pk.PkError:  # the persistent grid does not fit this n
+                    row[f"{key}_iters"] = row[f"{key}_ms"] = None
+                    continue
+                row[f"{key}_iters"] = best["iters"]
+                row[f"{key}_ms"] = best["solve_ms"]
+            # what the default loop (PK_LOOP_AUTO) runs at this n
+            auto = ("persistent" if m.n <= pk.PERSISTENT_AUTO_N and row["pipelined_persistent_ms"]
+                    else "graph")
+            row["pipelined_loop"] = auto
+            row["pipelined_iters"] = row[f"pipelined_{auto}_iters"]
+            row["pipelined_ms"] = row[f"pipelined_{auto}_ms"]
             row["pipelined_gbs"] = bytes_per_solve(m.n, m.nnz, row["pipelined_iters"]) / (row["pipelined_ms"] * 1e-3) / 1e9
             row["speedup_vs_classical"] = row["classical_ms"] / row["pipelined_ms"]
             sweep.append(row)

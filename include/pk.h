@@ -63,9 +63,21 @@ enum {
 enum {
   PK_LOOP_GRAPH = 0, /* CUDA graph with a device-controlled conditional WHILE node:
                         no host round-trip until the solve ends */
-  PK_LOOP_HOST = 1   /* plain launches; the host reads the device "done" flag every
+  PK_LOOP_HOST = 1,  /* plain launches; the host reads the device "done" flag every
                         `check_every` iterations (kernels after convergence return at once) */
+  PK_LOOP_PERSISTENT = 2, /* pipelined FP64 CG only: the whole iteration loop in one launch
+                        on one thread-block cluster (16 CTAs where available, else 8) with
+                        p, x, r, Ap in distributed shared memory, hardware cluster barriers,
+                        every CTA summing the block partials itself in a fixed order; for
+                        n <= PK_PERSISTENT_MAX_N.  Larger n, other solvers, variants or
+                        precisions return PK_ERR_ARG */
+  PK_LOOP_AUTO = 3   /* PK_LOOP_PERSISTENT for pipelined FP64 CG with n <= PK_PERSISTENT_AUTO_N
+                        (and no PK_FLAG_TIMING) when the device can run it, PK_LOOP_GRAPH
+                        otherwise */
 };
+#define PK_PERSISTENT_MAX_N 65536  /* 16 CTAs x 4096 rows (8 x 4096 on devices without
+                                      16-CTA clusters) */
+#define PK_PERSISTENT_AUTO_N 65536
 
 /* pk_opts.flags */
 #define PK_FLAG_TIMING 1u    /* time every kernel launch with CUDA events (host loop) and

@@ -425,6 +425,7 @@ pk_status bicgstab_solve(pk_csr* A, const double* b, double* x, const pk_opts* o
                          cudaStream_t s) {
   pk_status e = check_opts(A, b, x, o, info);
   if (e) return e;
+  if (o->loop == PK_LOOP_PERSISTENT) { set_error("PK_LOOP_PERSISTENT runs pipelined CG only"); return PK_ERR_ARG; }
   *info = pk_info{};
   info->rel_res_true = -1.0;
   if (A->n == 0) return PK_OK;
@@ -523,7 +524,7 @@ pk_status bicgstab_solve(pk_csr* A, const double* b, double* x, const pk_opts* o
   if ((e = T.flush())) return e;
   if (x_copy_back)
     PK_CUDA(cudaMemcpyAsync(x_copy_back, xd, sizeof(double) * A->n, cudaMemcpyDeviceToDevice, s));
-  const bool graph = o->loop == PK_LOOP_GRAPH && !T.on;
+  const bool graph = o->loop != PK_LOOP_HOST && !T.on;
   if ((e = finish_info(A, o, info, s, v, e0, e1, launches))) return e;
   if (graph) info->launches += (int)(passes_of(A->st_host) * L.body_kernels);
   for (int k = 0; k < PK_MAX_KERNEL_SLOTS; ++k) {

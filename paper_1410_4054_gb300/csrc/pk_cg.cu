@@ -395,6 +395,9 @@ __global__ void __launch_bounds__(kBlock) k_xpay_beta(RowArgs a, const double* _
 
 pk_status cg_mixed(pk_csr* A, const double* b, double* x, const pk_opts* o, pk_info* info,
                    cudaStream_t s);
+bool persistent_usable(const pk_csr* A, const pk_opts* o);
+pk_status launch_cg_persistent(pk_csr* A, double* x, double* r, double* p, double* ap,
+                               cudaStream_t s);
 
 pk_status cg_solve(pk_csr* A, const double* b, double* x, const pk_opts* o, pk_info* info,
                    cudaStream_t s) {
@@ -406,6 +409,21 @@ pk_status cg_solve(pk_csr* A, const double* b, double* x, const pk_opts* o, pk_i
   if (o->precision == PK_PREC_MIXED) return cg_mixed(A, b, x, o, info, s);
   if (o->precision != PK_PREC_FP64) { set_error("precision must be PK_PREC_FP64 or PK_PREC_MIXED"); return PK_ERR_ARG; }
   if (o->variant < 0 || o->variant > 2) { set_error("bad variant"); return PK_ERR_ARG; }
+  bool persistent = false;
+  if (o->loop == PK_LOOP_PERSISTENT) {
+    if (o->variant != PK_VARIANT_PIPELINED) {
+      set_error("PK_LOOP_PERSISTENT runs pipelined CG only");
+      return PK_ERR_ARG;
+    }
+    if (!persistent_usable(A, o)) {
+      set_error("PK_LOOP_PERSISTENT: persistent loop needs n <= 16 x 4096 rows (one thread-block cluster) and cluster launch");
+      return PK_ERR_ARG;
+    }
+    persistent = true;
+  } else if (o->loop == PK_LOOP_AUTO) {
+    persistent = o->variant == PK_VARIANT_PIPELINED && A->n <= PK_PERSISTENT_AUTO_N &&
+                 !(o->flags & PK_FLAG_TIMING) && persistent_usable(A, o);
+  }
   cudaEvent_t e0, e1;
   PK_CUDA(cudaEventCreate(&e0));
   PK_CUDA(cudaEventCreate(&e1));
@@ -419,7 +437,7 @@ pk_status cg_solve(pk_csr* A, const double* b, double* x, const pk_opts* o, pk_i
   double* xd = v.x_dev;
   // The bulk-copy kernels read x in 16-byte units: a caller's x that is not 16-byte aligned or
   // has odd length is iterated in a padded library copy.
-  const bool tma_engine = A->tma_ok && !(o->flags & PK_FLAG_NO_TMA);
+  const bool tma_engine = A->tma_ok && !(o->flags & PK_FLAG_NO_TMA) && !persistent;
   double* x_copy_back = nullptr;
   if (tma_engine && (((uintptr_t)xd & 15) || (A->n & 1))) {
     double* xi;
@@ -451,6 +469,23 @@ pk_status cg_solve(pk_csr* A, const double* b, double* x, const pk_opts* o, pk_i
   if ((e = T.end())) return e;
   k_zero_x<<<G, kBlock, 0, s>>>(ra, xd);
   launches += 2;
+  PK_CUDA(cudaGetLastError());
+  if (persistent) {
+    // the whole iteration loop in one cooperative launch
+    if ((e = T.begin(PK_SLOT_OTHER))) return e;
+    if ((e = launch_cg_persistent(A, xd, r, p, ap, s))) return e;
+    if ((e = T.end())) return e;
+    launches += 1;
+    if ((e = T.flush())) return e;
+    if ((e = finish_info(A, o, info, s, v, e0, e1, launches))) return e;
+    for (int k = 0; k < PK_MAX_KERNEL_SLOTS; ++k) {
+      info->kernel_count[k] = T.count[k];
+      info->kernel_ms[k] = T.count[k] ? T.ms[k] / T.count[k] : 0.0;
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    return (pk_status)info->status;
+  }
   const int variant = o->variant;
   const bool tma = tma_engine;
   if (tma && (e = tma_setup())) return e;
@@ -522,7 +557,7 @@ pk_status cg_solve(pk_csr* A, const double* b, double* x, const pk_opts* o, pk_i
   if ((e = T.flush())) return e;
   if (x_copy_back)
     PK_CUDA(cudaMemcpyAsync(x_copy_back, xd, sizeof(double) * A->n, cudaMemcpyDeviceToDevice, s));
-  const bool graph = o->loop == PK_LOOP_GRAPH && !T.on;
+  const bool graph = o->loop != PK_LOOP_HOST && !T.on;
   if ((e = finish_info(A, o, info, s, v, e0, e1, launches))) return e;
   if (graph) info->launches += (int)(passes_of(A->st_host) * L.body_kernels);
   for (int k = 0; k < PK_MAX_KERNEL_SLOTS; ++k) {

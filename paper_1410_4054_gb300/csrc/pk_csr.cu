@@ -247,6 +247,7 @@ pk_status check_opts(const pk_csr* A, const double* b, double* x, const pk_opts*
   if (A->n > 0 && (!b || !x)) { set_error("NULL b or x"); return PK_ERR_ARG; }
   if (!(o->tol >= 0.0) || o->maxit < 0) { set_error("tol must be >= 0 and maxit >= 0"); return PK_ERR_ARG; }
   if (o->trace_cap > 0 && !o->trace) { set_error("trace_cap > 0 needs a trace array"); return PK_ERR_ARG; }
+  if (o->loop < PK_LOOP_GRAPH || o->loop > PK_LOOP_AUTO) { set_error("bad loop mode"); return PK_ERR_ARG; }
   return PK_OK;
 }
 

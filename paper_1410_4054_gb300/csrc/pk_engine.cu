@@ -160,7 +160,7 @@ pk_status build_nested_graph(pk_csr* A, int kind, const void* const keys[4], con
 pk_status run_loop(pk_csr* A, const pk_opts* o, cudaStream_t s, const LoopSpec& L, Timer* T,
                    int* launches) {
   const bool timing = T && T->on;
-  if (o->loop == PK_LOOP_GRAPH && !timing) {
+  if (o->loop != PK_LOOP_HOST && !timing) {
     pk_graph_entry* g = nullptr;
     for (auto& e : A->graphs) {
       if (e.kind == L.kind && e.key[0] == L.keys[0] && e.key[1] == L.keys[1] &&

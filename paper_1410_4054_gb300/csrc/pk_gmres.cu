@@ -469,6 +469,7 @@ pk_status gmres_solve(pk_csr* A, const double* b, double* x, const pk_opts* o, p
                       cudaStream_t s) {
   pk_status e = check_opts(A, b, x, o, info);
   if (e) return e;
+  if (o->loop == PK_LOOP_PERSISTENT) { set_error("PK_LOOP_PERSISTENT runs pipelined CG only"); return PK_ERR_ARG; }
   *info = pk_info{};
   info->rel_res_true = -1.0;
   if (A->n == 0) return PK_OK;
@@ -563,7 +564,7 @@ pk_status gmres_solve(pk_csr* A, const double* b, double* x, const pk_opts* o, p
     if (t) t->end();
   };
   const int step_kernels = classical ? 7 : 4;
-  const bool graph = o->loop == PK_LOOP_GRAPH && !T.on;
+  const bool graph = o->loop != PK_LOOP_HOST && !T.on;
   if (graph) {
     const void* keys[4] = {v.x_dev, v.b_dev, nullptr, nullptr};
     const int64_t ikeys[4] = {o->variant, m, 0, 0};

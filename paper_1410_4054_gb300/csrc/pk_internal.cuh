@@ -42,6 +42,7 @@ struct DevState {
   int32_t gm_i, gm_k, gm_cycle, gm_phase;
   int32_t gm_m, gm_pad;
   cudaGraphConditionalHandle cond2;
+  unsigned int gbar;      // grid-barrier arrivals of the persistent (cooperative) solve
 };
 
 // Loads that bypass L1 (the value was written by another block or an earlier kernel).

@@ -268,6 +268,7 @@ pk_status ensure_fp32_values(pk_csr* A, cudaStream_t s) {
 pk_status cg_mixed(pk_csr* A, const double* b, double* x, const pk_opts* o, pk_info* info,
                    cudaStream_t s) {
   pk_status e;
+  if (o->loop == PK_LOOP_PERSISTENT) { set_error("PK_LOOP_PERSISTENT runs pipelined FP64 CG only"); return PK_ERR_ARG; }
   if ((e = ensure_fp32_values(A, s))) return e;
   cudaEvent_t e0, e1;
   PK_CUDA(cudaEventCreate(&e0));
@@ -328,7 +329,7 @@ pk_status cg_mixed(pk_csr* A, const double* b, double* x, const pk_opts* o, pk_i
     k_mx_correct<<<Ge, kBlock, 0, cs>>>(a);
     if (t) t->end();
   };
-  const bool graph = o->loop == PK_LOOP_GRAPH && !T.on;
+  const bool graph = o->loop != PK_LOOP_HOST && !T.on;
   if (graph) {
     const void* keys[4] = {v.x_dev, v.b_dev, nullptr, nullptr};
     const int64_t ikeys[4] = {PK_PREC_MIXED, 0, 0, 0};

@@ -21,7 +21,8 @@ STATUS_NAMES = ["PK_OK", "PK_ERR_ARG", "PK_ERR_CUDA", "PK_ERR_OOM", "PK_NOT_CONV
                 "PK_BREAKDOWN", "PK_NOT_SPD", "PK_ERR_NAN", "PK_TIMEOUT"]
 VARIANTS = {"pipelined": 0, "classical": 1, "split": 2}
 PRECISIONS = {"fp64": 0, "mixed": 1}
-LOOPS = {"graph": 0, "host": 1}
+LOOPS = {"graph": 0, "host": 1, "persistent": 2, "auto": 3}
+PERSISTENT_AUTO_N = 65536  # PK_PERSISTENT_AUTO_N
 FLAG_TIMING = 1
 FLAG_TRUE_RES = 2
 FLAG_NO_TMA = 4
@@ -196,7 +197,7 @@ class CSRMatrix:
 
 
 def make_opts(tol=1e-8, maxit=1000, restart=30, variant="pipelined", precision="fp64",
-              loop="graph", check_every=0, flags=0, trace=None) -> Opts:
+              loop="auto", check_every=0, flags=0, trace=None) -> Opts:
     o = Opts()
     o.tol = tol
     o.maxit = maxit

@@ -48,14 +48,19 @@ MATRICES = {
 }
 
 
-@pytest.mark.parametrize("variant", ["pipelined", "split", "classical"])
+FORMS = [("pipelined", "graph"), ("pipelined", "persistent"), ("split", "graph"),
+         ("classical", "graph")]
+
+
+@pytest.mark.parametrize("variant,loop", FORMS)
 @pytest.mark.parametrize("name", sorted(MATRICES))
-def test_cg_parity(name, variant):
+def test_cg_parity(name, variant, loop):
     a = MATRICES[name]()
     _, b, _ = W.manufactured(a, seed=0)
     ovar = "classical" if variant == "classical" else "pipelined"
     ref = O.cg(a, b, tol=1e-8, maxit=5000, variant=ovar)
-    info, x, tr = solve(a, b, tol=1e-8, maxit=5000, variant=variant, flags=pk.FLAG_TRUE_RES)
+    info, x, tr = solve(a, b, tol=1e-8, maxit=5000, variant=variant, loop=loop,
+                        flags=pk.FLAG_TRUE_RES)
     assert info["status"] == pk.PK_OK
     assert abs(info["iters"] - ref["iters"]) <= 2
     k = min(20, ref["iters"] - 1)
@@ -64,7 +69,7 @@ def test_cg_parity(name, variant):
     assert info["rel_res_true"] <= 1.5e-8
     # same iteration count: x within 1e-9 of the oracle's
     fixed = ref["iters"]
-    info2, x2, _ = solve(a, b, tol=0.0, maxit=fixed, variant=variant)
+    info2, x2, _ = solve(a, b, tol=0.0, maxit=fixed, variant=variant, loop=loop)
     assert info2["status"] == pk.PK_NOT_CONVERGED and info2["iters"] == fixed
     assert rel(x2, ref["x"]) <= 1e-9
 
@@ -77,6 +82,55 @@ def test_cg_loop_modes_agree_bitwise(loop):
     i2, x2, _ = solve(a, b, loop=loop, check_every=5)
     assert i1["iters"] == i2["iters"]
     assert np.array_equal(x1, x2)  # deterministic reductions: bitwise reproducible
+
+
+def test_cg_persistent_is_repeatable_and_matches_graph():
+    """One cooperative launch runs the whole solve: bitwise repeatable (fixed reduction order),
+    same iterations as the graph loop, x equal up to the reduction order of the partial sums."""
+    for a in (W.laplace_2d(64), W.laplace_3d(40)):
+        _, b, _ = W.manufactured(a)
+        i1, x1, t1 = solve(a, b, loop="persistent")
+        i2, x2, t2 = solve(a, b, loop="persistent")
+        i3, x3, t3 = solve(a, b, loop="graph")
+        assert i1["status"] == i3["status"] == pk.PK_OK
+        assert i1["iters"] == i2["iters"] == i3["iters"]
+        assert np.array_equal(x1, x2) and np.array_equal(t1, t2, equal_nan=True)
+        assert rel(x1, x3) <= 1e-12
+        assert i1["launches"] == 3  # setup, zero-x guard, the persistent loop
+
+
+def test_cg_persistent_largest_cluster_parity():
+    """n = 32,768 fills a cluster's shared memory (2,048 or 4,096 rows per CTA, several rows
+    per thread)."""
+    a = W.laplace_3d(32)
+    _, b, _ = W.manufactured(a, seed=2)
+    ref = O.cg(a, b, tol=1e-8, maxit=5000, variant="pipelined")
+    info, x, tr = solve(a, b, tol=1e-8, maxit=5000, loop="persistent", flags=pk.FLAG_TRUE_RES)
+    assert info["status"] == pk.PK_OK and abs(info["iters"] - ref["iters"]) <= 2
+    np.testing.assert_allclose(tr[:20, 0], ref["alpha"][:20], rtol=1e-12, atol=0)
+    np.testing.assert_allclose(tr[:20, 1], ref["beta"][:20], rtol=1e-12, atol=0)
+    assert info["rel_res_true"] <= 1.5e-8
+    assert rel(x, ref["x"]) <= 1e-9
+
+
+def test_cg_persistent_too_large_falls_back_under_auto():
+    a = W.laplace_3d(64)  # 262,144 rows: more than one cluster's shared memory holds
+    _, b, _ = W.manufactured(a)
+    with pytest.raises(RuntimeError, match="persistent loop needs"):
+        solve(a, b, loop="persistent")
+    i_auto, x_auto, _ = solve(a, b, loop="auto")
+    i_graph, x_graph, _ = solve(a, b, loop="graph")
+    assert i_auto["iters"] == i_graph["iters"] and np.array_equal(x_auto, x_graph)
+
+
+def test_cg_persistent_rejects_other_forms():
+    a = W.laplace_2d(16)
+    _, b, _ = W.manufactured(a)
+    A = pk.CSRMatrix.from_workload(a)
+    for call, kw in ((pk.cg_solve, dict(variant="classical")), (pk.cg_solve, dict(precision="mixed")),
+                     (pk.bicgstab_solve, {}), (pk.gmres_solve, {})):
+        with pytest.raises(RuntimeError, match="PERSISTENT"):
+            call(A, dev(b), dev(np.zeros(a.n)), loop="persistent", **kw)
 
 
 def test_cg_launch_counts_match_the_paper():
@@ -99,9 +153,14 @@ def test_cg_timing_mode_reports_kernels():
     assert all(v > 0 for v in info["kernel_ms"].values())
 
 
-def test_cg_edge_cases():
+@pytest.mark.parametrize("loop", ["graph", "persistent"])
+def test_cg_edge_cases(loop):
     a = W.laplace_2d(8)
     _, b, _ = W.manufactured(a)
+
+    def solve(*args, **kw):
+        return globals()["solve"](*args, loop=loop, **kw)
+
     # b = 0 -> x = 0, no iterations
     info, x, _ = solve(a, np.zeros(a.n), x0=np.ones(a.n))
     assert info["status"] == pk.PK_OK and info["iters"] == 0 and not x.any()
