@@ -176,9 +176,103 @@ __global__ void __launch_bounds__(kTileThreads, 2) k_gm1(CsrTiles T, GmArgs g) {
   }
 }
 
-// K-GM-2: first stages of <v_j, v_i>, j = 1..i-2.  Warp w owns columns j = 1 + w + 8c; its lanes
-// walk the block's rows, so every basis element is read once, coalesced.
-__global__ void __launch_bounds__(kBlock, 2) k_gm2(GmArgs g) {
+// ---------------------------------------------------------------- Gram-Schmidt streaming
+// K-GM-2 and K-GM-3 read i+1 basis columns per step and do one FP64 FMA per element read.
+// On GB300 a warp that waits for its own loads starves both HBM and the narrow FP64 pipe, so
+// both kernels stream the basis through shared memory: one producer warp copies 256-row
+// tiles of up to kBsVecs columns with cp.async.bulk into a kBsStages-deep ring (completion on
+// mbarriers, every wait bounded by 2 s -> PK_TIMEOUT), and eight consumer warps, one row per
+// thread, do the FMAs from shared memory with independent accumulators.
+
+constexpr int kBsRows = kConsumers;  // rows per tile: one per consumer thread
+constexpr int kBsCols = 16;          // basis columns per stage
+constexpr int kBsVecs = kBsCols + 1; // + v_i
+constexpr int kBsStages = 3;
+constexpr int kBsSmem = kBsStages * kBsVecs * kBsRows * 8 + 2 * kBsStages * 8;
+
+struct BasisRing {
+  double* buf;      // [kBsStages][kBsVecs][kBsRows]
+  uint64_t* full;   // [kBsStages]
+  uint64_t* empty;  // [kBsStages]
+  __device__ double* slot(int s, int k) const { return buf + ((size_t)s * kBsVecs + k) * kBsRows; }
+};
+
+__device__ __forceinline__ BasisRing basis_ring(unsigned char* smem) {
+  BasisRing R;
+  R.buf = reinterpret_cast<double*>(smem);
+  R.full = reinterpret_cast<uint64_t*>(smem + (size_t)kBsStages * kBsVecs * kBsRows * 8);
+  R.empty = R.full + kBsStages;
+  if (threadIdx.x == 0) {
+    for (int s = 0; s < kBsStages; ++s) {
+      mbar_init(&R.full[s], 1);
+      mbar_init(&R.empty[s], kConsumerWarps);
+    }
+    mbar_fence_init();
+  }
+  __syncthreads();
+  return R;
+}
+
+// Producer loop (one lane): stage q = 0 .. nq-1 copies the vectors that cols(q, ptrs) lists,
+// rows [row0(q), row0(q) + rows(q)) rounded up to whole 16-byte units (the basis columns are
+// padded, so the rounding stays inside them).  Returns false after a timed-out wait.
+template <class Plan>
+__device__ __forceinline__ bool basis_produce(const BasisRing& R, int nq, DevState* st, Plan&& plan) {
+  int issued = 0;
+  bool ok = true;
+  for (int q = 0; q < nq; ++q) {
+    const int s = q % kBsStages;
+    if (q >= kBsStages && !mbar_wait(&R.empty[s], ((q / kBsStages) - 1) & 1)) { ok = false; break; }
+    const double* src[kBsVecs];
+    int row0, rows, nv;
+    plan(q, src, row0, rows, nv);
+    const uint32_t bytes = (uint32_t)(((rows + 1) & ~1) * 8);
+    int cnt = 0;
+    for (int k = 0; k < kBsVecs; ++k) cnt += src[k] != nullptr;
+    mbar_expect_tx(&R.full[s], bytes * cnt);
+    for (int k = 0; k < kBsVecs; ++k)
+      if (src[k]) bulk_load(R.slot(s, k), src[k] + row0, bytes, &R.full[s]);
+    issued = q + 1;
+    (void)nv;
+  }
+  for (int q = max(0, issued - kBsStages); q < issued; ++q)
+    if (!mbar_wait(&R.full[q % kBsStages], (q / kBsStages) & 1)) { ok = false; break; }
+  if (!ok) report_timeout(st);
+  return ok;
+}
+
+// Named barrier over the consumer warps only (the producer warp does not take part).
+__device__ __forceinline__ void consumers_sync() {
+  asm volatile("bar.sync 1, %0;" ::"r"(kConsumers) : "memory");
+}
+
+// Per-row work of one stage with the column count a compile-time constant: a predicated-off
+// FP64 instruction still occupies GB300's narrow FP64 pipe, so the loops below must not run
+// over the full kBsCols with a guard.
+template <int NC>
+__device__ __forceinline__ void gm2_row(const BasisRing& R, int s, int row, double w,
+                                        double (&acc)[kBsCols]) {
+#pragma unroll
+  for (int c = 0; c < NC; ++c) acc[c] = fma(R.slot(s, 1 + c)[row], w, acc[c]);
+}
+
+template <int NC>
+__device__ __forceinline__ double gm3_row(const BasisRing& R, int s, int row, const double* cf,
+                                          double w) {
+#pragma unroll
+  for (int c = 0; c < NC; ++c) w = fma(-cf[c], R.slot(s, 1 + c)[row], w);
+  return w;
+}
+
+#define PK_GM_CASES(X) X(1) X(2) X(3) X(4) X(5) X(6) X(7) X(8) X(9) X(10) X(11) X(12) X(13) \
+  X(14) X(15) X(16)
+
+// K-GM-2: partial <v_j, v_i> for j = 1 .. i-2 (Sec. 3.3, Alg. 6), column groups of kBsCols
+// streamed one after the other (v_i with every group).  Each consumer thread keeps one
+// accumulator per column of the group; the warp's accumulators are reduced across the lanes
+// by recursive halving (16 shuffle-adds per lane), then over the warps in a fixed order.
+__global__ void __launch_bounds__(kTileThreads, 2) k_gm2(GmArgs g) {
+  extern __shared__ __align__(128) unsigned char smem[];
   DevState* st = g.st;
   if (!gm_step_live(st)) return;
   const int i = __ldcg(&st->gm_i);
@@ -186,41 +280,94 @@ __global__ void __launch_bounds__(kBlock, 2) k_gm2(GmArgs g) {
   if (nj <= 0) return;
   int r0, r1;
   ew_range(g.n, r0, r1);
+  const int ntiles = r1 > r0 ? (r1 - r0 + kBsRows - 1) / kBsRows : 0;
+  const int ngroups = (nj + kBsCols - 1) / kBsCols;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const double* vi = g.V + (size_t)i * g.ld;
-  double acc[8];
+  const BasisRing R = basis_ring(smem);
+  __shared__ double red[kConsumerWarps][kBsCols];
+  if (warp == kConsumerWarps) {
+    if (lane == 0)
+      basis_produce(R, ntiles * ngroups, st, [&](int q, const double** src, int& row0, int& rows, int& nv) {
+        const int grp = q / ntiles, t = q % ntiles;
+        const int j0 = 1 + grp * kBsCols, nc = min(kBsCols, nj - j0 + 1);
+        row0 = r0 + t * kBsRows;
+        rows = min(kBsRows, r1 - row0);
+        nv = nc + 1;
+        src[0] = vi;
+        for (int c = 0; c < kBsCols; ++c) src[1 + c] = c < nc ? g.V + (size_t)(j0 + c) * g.ld : nullptr;
+      });
+  } else {
+    bool ok = true;
+    for (int grp = 0; grp < ngroups; ++grp) {
+      const int j0 = 1 + grp * kBsCols, nc = min(kBsCols, nj - j0 + 1);
+      double acc[kBsCols];
 #pragma unroll
-  for (int c = 0; c < 8; ++c) acc[c] = 0.0;
-  // four rows per lane per pass, all loads of a column issued before its FMAs
-  for (int row0 = r0 + lane; row0 < r1; row0 += 128) {
-    double w[4];
-#pragma unroll
-    for (int u = 0; u < 4; ++u) w[u] = row0 + 32 * u < r1 ? vi[row0 + 32 * u] : 0.0;
-#pragma unroll
-    for (int c = 0; c < 8; ++c) {
-      const int j = 1 + warp + 8 * c;
-      if (j <= nj) {  // warp-uniform
-        const double* vj = g.V + (size_t)j * g.ld;
-        double q[4];
-#pragma unroll
-        for (int u = 0; u < 4; ++u) q[u] = row0 + 32 * u < r1 ? vj[row0 + 32 * u] : 0.0;
-#pragma unroll
-        for (int u = 0; u < 4; ++u) acc[c] = fma(q[u], w[u], acc[c]);
+      for (int c = 0; c < kBsCols; ++c) acc[c] = 0.0;
+      for (int t = 0; t < ntiles && ok; ++t) {
+        const int q = grp * ntiles + t, s = q % kBsStages;
+        if (!mbar_wait(&R.full[s], (q / kBsStages) & 1)) { report_timeout(st); ok = false; break; }
+        const int rows = min(kBsRows, r1 - (r0 + t * kBsRows));
+        if ((int)threadIdx.x < rows) {
+          const double w = R.slot(s, 0)[threadIdx.x];
+          switch (nc) {
+#define PK_GM2_CASE(N) \
+  case N: gm2_row<N>(R, s, threadIdx.x, w, acc); break;
+            PK_GM_CASES(PK_GM2_CASE)
+#undef PK_GM2_CASE
+            default: break;
+          }
+        }
+        __syncwarp();
+        if (lane == 0) mbar_arrive(&R.empty[s]);
       }
-    }
-  }
+      // recursive halving over the lanes: after offsets 16, 8, 4, 2 lane l holds column
+      // (l >> 1) & 15 summed over 16 lanes; offset 1 adds the last pair (a + b == b + a)
+      double h8[8], h4[4], h2[2], h1;
+      {
+        const bool up = lane & 16;
 #pragma unroll
-  for (int c = 0; c < 8; ++c) {
-    const int j = 1 + warp + 8 * c;
-    const double t = warp_sum(acc[c]);
-    if (lane == 0 && j <= nj) g.partials[(size_t)(j - 1) * gridDim.x + blockIdx.x] = t;
+        for (int c = 0; c < 8; ++c) {
+          const double keep = up ? acc[c + 8] : acc[c], send = up ? acc[c] : acc[c + 8];
+          h8[c] = keep + __shfl_xor_sync(0xffffffffu, send, 16);
+        }
+      }
+      {
+        const bool up = lane & 8;
+#pragma unroll
+        for (int c = 0; c < 4; ++c) {
+          const double keep = up ? h8[c + 4] : h8[c], send = up ? h8[c] : h8[c + 4];
+          h4[c] = keep + __shfl_xor_sync(0xffffffffu, send, 8);
+        }
+      }
+      {
+        const bool up = lane & 4;
+#pragma unroll
+        for (int c = 0; c < 2; ++c) {
+          const double keep = up ? h4[c + 2] : h4[c], send = up ? h4[c] : h4[c + 2];
+          h2[c] = keep + __shfl_xor_sync(0xffffffffu, send, 4);
+        }
+      }
+      {
+        const bool up = lane & 2;
+        const double keep = up ? h2[1] : h2[0], send = up ? h2[0] : h2[1];
+        h1 = keep + __shfl_xor_sync(0xffffffffu, send, 2);
+      }
+      h1 += __shfl_xor_sync(0xffffffffu, h1, 1);
+      if ((lane & 1) == 0) red[warp][(lane >> 1) & 15] = h1;
+      consumers_sync();
+      if ((int)threadIdx.x < nc) {
+        double tsum = 0.0;
+#pragma unroll
+        for (int w = 0; w < kConsumerWarps; ++w) tsum += red[w][threadIdx.x];
+        g.partials[(size_t)(j0 + threadIdx.x - 1) * gridDim.x + blockIdx.x] = tsum;
+      }
+      consumers_sync();
+    }
   }
   if (arrive_last(&st->counter)) {
     const int G = gridDim.x;
-#pragma unroll
-    for (int c = 0; c < 8; ++c) {
-      const int j = 1 + warp + 8 * c;
-      if (j > nj) continue;  // warp-uniform
+    for (int j = 1 + warp; j <= nj; j += kTileThreads / 32) {  // one warp per column
       double t = 0.0;
       for (int bk = lane; bk < G; bk += 32) t += ld_cg(g.partials + (size_t)(j - 1) * G + bk);
       t = warp_sum(t);
@@ -231,33 +378,68 @@ __global__ void __launch_bounds__(kBlock, 2) k_gm2(GmArgs g) {
 }
 
 // K-GM-3: v_i -= sum_{j=1}^{i-1} R_{j,i} v_j (in order j = 1, 2, ...) with the first stage of
-// ||v_i||^2.  Last block: R_{i,i}, lucky-breakdown test (R13).
-__global__ void __launch_bounds__(kBlock) k_gm3(GmArgs g) {
+// ||v_i||^2.  Tiles outer, column groups inner: each consumer thread keeps its row of v_i in
+// a register across the groups of the tile, then stores it.  Last block: R_{i,i} and the
+// lucky-breakdown test (R13).
+__global__ void __launch_bounds__(kTileThreads, 2) k_gm3(GmArgs g) {
+  extern __shared__ __align__(128) unsigned char smem[];
   DevState* st = g.st;
   if (!gm_step_live(st)) return;
   const int i = __ldcg(&st->gm_i);
   __shared__ double coef[kGmMax];
   for (int j = threadIdx.x; j < i - 1; j += blockDim.x) coef[j] = ld_cg(g.R + (j + 1) * kRld + i);
-  __syncthreads();
   int r0, r1;
   ew_range(g.n, r0, r1);
+  const int ntiles = r1 > r0 ? (r1 - r0 + kBsRows - 1) / kBsRows : 0;
+  const int ncols = i - 1;                                     // v_1 .. v_{i-1}
+  const int ngroups = max(1, (ncols + kBsCols - 1) / kBsCols);
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   double* vi = g.V + (size_t)i * g.ld;
+  const BasisRing R = basis_ring(smem);  // (its __syncthreads also publishes coef)
   double v[1] = {0.0};
-  for (int row = r0 + threadIdx.x; row < r1; row += blockDim.x) {
-    double w = vi[row];
-    int j = 1;
-    for (; j + 8 <= i; j += 8) {
-      double vj[8];
-#pragma unroll
-      for (int c = 0; c < 8; ++c) vj[c] = g.V[(size_t)(j + c) * g.ld + row];
-#pragma unroll
-      for (int c = 0; c < 8; ++c) w = fma(-coef[j + c - 1], vj[c], w);
+  if (warp == kConsumerWarps) {
+    if (lane == 0)
+      basis_produce(R, ntiles * ngroups, st, [&](int q, const double** src, int& row0, int& rows, int& nv) {
+        const int t = q / ngroups, grp = q % ngroups;
+        const int j0 = 1 + grp * kBsCols, nc = max(0, min(kBsCols, ncols - j0 + 1));
+        row0 = r0 + t * kBsRows;
+        rows = min(kBsRows, r1 - row0);
+        nv = nc + (grp == 0);
+        src[0] = grp == 0 ? vi : nullptr;
+        for (int c = 0; c < kBsCols; ++c) src[1 + c] = c < nc ? g.V + (size_t)(j0 + c) * g.ld : nullptr;
+      });
+  } else {
+    for (int t = 0; t < ntiles; ++t) {
+      const int row0 = r0 + t * kBsRows, rows = min(kBsRows, r1 - row0);
+      const bool mine = (int)threadIdx.x < rows;
+      double w = 0.0;
+      bool ok = true;
+      for (int grp = 0; grp < ngroups; ++grp) {
+        const int q = t * ngroups + grp, s = q % kBsStages;
+        if (!mbar_wait(&R.full[s], (q / kBsStages) & 1)) { report_timeout(st); ok = false; break; }
+        const int j0 = 1 + grp * kBsCols, nc = max(0, min(kBsCols, ncols - j0 + 1));
+        if (mine) {
+          if (grp == 0) w = R.slot(s, 0)[threadIdx.x];
+          const double* cf = coef + (j0 - 1);
+          switch (nc) {
+#define PK_GM3_CASE(N) \
+  case N: w = gm3_row<N>(R, s, threadIdx.x, cf, w); break;
+            PK_GM_CASES(PK_GM3_CASE)
+#undef PK_GM3_CASE
+            default: break;
+          }
+        }
+        __syncwarp();
+        if (lane == 0) mbar_arrive(&R.empty[s]);
+      }
+      if (!ok) break;
+      if (mine) {
+        vi[row0 + threadIdx.x] = w;
+        v[0] = fma(w, w, v[0]);
+      }
     }
-    for (; j < i; ++j) w = fma(-coef[j - 1], g.V[(size_t)j * g.ld + row], w);
-    vi[row] = w;
-    v[0] = fma(w, w, v[0]);
   }
-  block_partials<1>(v, g.partials);
+  tile_block_partials<1>(v, g.partials);
   if (arrive_last(&st->counter)) {
     double t[1];
     final_sums<1>(g.partials, t);
@@ -460,6 +642,8 @@ static pk_status gm_setup() {
     PK_CUDA(cudaFuncSetAttribute(k_gm1, cudaFuncAttributeMaxDynamicSharedMemorySize, csr_smem_bytes()));
     PK_CUDA(cudaFuncSetAttribute(k_gm_scale, cudaFuncAttributeMaxDynamicSharedMemorySize, stream_smem_bytes<1>()));
     PK_CUDA(cudaFuncSetAttribute(k_gm4, cudaFuncAttributeMaxDynamicSharedMemorySize, stream_smem_bytes<2>()));
+    PK_CUDA(cudaFuncSetAttribute(k_gm2, cudaFuncAttributeMaxDynamicSharedMemorySize, kBsSmem));
+    PK_CUDA(cudaFuncSetAttribute(k_gm3, cudaFuncAttributeMaxDynamicSharedMemorySize, kBsSmem));
     done = true;
   }
   return PK_OK;
@@ -538,9 +722,9 @@ pk_status gmres_solve(pk_csr* A, const double* b, double* x, const pk_opts* o, p
     if (t) t->begin(PK_SLOT_SPMV_DOTS);
     k_gm1<<<Gt, kTileThreads, csr_smem_bytes(), cs>>>(ct, g);
     if (t) { t->end(); t->begin(PK_SLOT_MULTIDOT); }
-    k_gm2<<<Ge, kBlock, 0, cs>>>(g);
+    k_gm2<<<Gs, kTileThreads, kBsSmem, cs>>>(g);
     if (t) { t->end(); t->begin(PK_SLOT_ORTHO); }
-    k_gm3<<<Ge, kBlock, 0, cs>>>(g);
+    k_gm3<<<Gs, kTileThreads, kBsSmem, cs>>>(g);
     if (t) t->end();
     if (!classical) {
       if (t) t->begin(PK_SLOT_UPDATE);
