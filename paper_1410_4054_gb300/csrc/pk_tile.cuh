@@ -400,6 +400,33 @@ __device__ __forceinline__ bool csr_tiles(const CsrTiles& T, unsigned char* smem
 // Two row products from a shared-memory window.  Each pass loads up to 8 entries of both
 // rows and issues all their gathers before the FMAs, so a thread keeps up to 16 gathers in
 // flight; each row is still summed left to right.
+// FMAs k < M of one gathered batch, lane-predicated on k < m.  M is the largest batch length
+// among the warp's converged lanes: on GB300 a warp instruction that is predicated off in
+// every lane still takes a slot of the narrow FP64 pipe, so the count issued must not be a
+// fixed 8 (a 7-point stencil row would pay for 8).
+template <int M>
+__device__ __forceinline__ void fma_batch(const double (&v)[8], const double (&xv)[8], int m,
+                                          double& s) {
+#pragma unroll
+  for (int k = 0; k < M; ++k)
+    if (k < m) s = fma(v[k], xv[k], s);
+}
+
+__device__ __forceinline__ void fma_batch_n(int mx, const double (&v)[8], const double (&xv)[8],
+                                            int m, double& s) {
+  switch (mx) {
+    case 1: fma_batch<1>(v, xv, m, s); break;
+    case 2: fma_batch<2>(v, xv, m, s); break;
+    case 3: fma_batch<3>(v, xv, m, s); break;
+    case 4: fma_batch<4>(v, xv, m, s); break;
+    case 5: fma_batch<5>(v, xv, m, s); break;
+    case 6: fma_batch<6>(v, xv, m, s); break;
+    case 7: fma_batch<7>(v, xv, m, s); break;
+    case 8: fma_batch<8>(v, xv, m, s); break;
+    default: break;
+  }
+}
+
 __device__ __forceinline__ void smem_row2(const double* sva, const int32_t* sci, int ja, int ja1,
                                           int jb, int jb1, const double* __restrict__ x,
                                           double& sa, double& sb) {
@@ -422,11 +449,10 @@ __device__ __forceinline__ void smem_row2(const double* sva, const int32_t* sci,
       xa[k] = k < ma ? __ldg(x + ca[k]) : 0.0;
       xb[k] = k < mb ? __ldg(x + cb[k]) : 0.0;
     }
-#pragma unroll
-    for (int k = 0; k < 8; ++k) {
-      if (k < ma) sa = fma(va[k], xa[k], sa);
-      if (k < mb) sb = fma(vb[k], xb[k], sb);
-    }
+    // the same FMAs in the same order as a fixed 8-wide loop, without the dead issue slots
+    const unsigned conv = __activemask();
+    fma_batch_n(__reduce_max_sync(conv, max(ma, 0)), va, xa, ma, sa);
+    fma_batch_n(__reduce_max_sync(conv, max(mb, 0)), vb, xb, mb, sb);
     ja += ma > 0 ? ma : 0;
     jb += mb > 0 ? mb : 0;
   }
