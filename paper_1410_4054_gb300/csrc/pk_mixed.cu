@@ -13,7 +13,7 @@
 #include <cmath>
 #include <vector>
 
-#include "pk_internal.cuh"
+#include "pk_tile.cuh"
 
 namespace pk {
 
@@ -236,6 +236,122 @@ __global__ void __launch_bounds__(kBlock) k_mx_update(MxArgs a) {
   }
 }
 
+// ---------------------------------------------------------------- tile-engine forms
+// The inner loop on the warp-specialised engines: the FP32 CSR copy streamed in bulk-copied
+// tiles (producer warp) for K-CG-S, the four FP32 vectors streamed for K-CG-U, both launched
+// with programmatic dependent launch.  Same per-element arithmetic as the row kernels above.
+
+__device__ __forceinline__ bool mx_inner_live(DevState* st) {
+  return !state_done(st) && __ldcg(&st->gm_phase) == 1;
+}
+
+__global__ void __launch_bounds__(kTileThreads, 2) k_mx_spmv_tma(CsrTilesT<float> T, MxArgs a) {
+  extern __shared__ __align__(128) unsigned char smem[];
+  DevState* st = a.st;
+  FF aa{0.0f, 0.0f}, pa{0.0f, 0.0f};
+  const bool live = csr_tiles(T, smem, st, [&]() { return mx_inner_live(st); },
+                              [&](int ra, int ja0, int ja1, int rb, int jb0, int jb1,
+                                  const float* sva, const int32_t* sci) {
+    const float sa = smem_row_f32(sva, sci, ja0, ja1, a.p);
+    a.ap[ra] = sa;
+    ff_add_prod(aa, sa, sa);
+    ff_add_prod(pa, __ldg(a.p + ra), sa);
+    if (rb >= 0) {
+      const float sb = smem_row_f32(sva, sci, jb0, jb1, a.p);
+      a.ap[rb] = sb;
+      ff_add_prod(aa, sb, sb);
+      ff_add_prod(pa, __ldg(a.p + rb), sb);
+    }
+  });
+  griddep_trigger();
+  if (!__syncthreads_or(threadIdx.x < kConsumers && live)) return;
+  double v[2] = {ff_value(aa), ff_value(pa)};
+  tile_block_partials<2>(v, a.partials);
+  if (arrive_last(&st->counter)) {
+    double t[2];
+    final_sums<2>(a.partials, t);
+    if (threadIdx.x == 0) {
+      const double rr = st->s[2];
+      if (__ldcg(&st->timeout)) mx_finish(st, PK_TIMEOUT);
+      else if (!isfinite(t[0]) || !isfinite(t[1])) mx_finish(st, PK_ERR_NAN);
+      else if (t[1] <= 0.0) mx_finish(st, PK_NOT_SPD);
+      else {
+        st->alpha = rr / t[1];
+        st->beta = st->alpha * st->alpha * t[0] / rr - 1.0;
+      }
+      st->counter = 0;
+    }
+  }
+}
+
+__global__ void __launch_bounds__(kTileThreads, 2) k_mx_update_tma(MxArgs a) {
+  extern __shared__ __align__(128) unsigned char smem[];
+  DevState* st = a.st;
+  count_pass(st);
+  int r0, r1;
+  ew_range(a.n, r0, r1);
+  float af = 0.0f, bf = 0.0f;
+  FF acc{0.0f, 0.0f};
+  // d and r do not depend on the preceding K-CG-S: prefetched before the dependency wait
+  StreamIn<4, float> in{{a.d, a.r, a.p, a.ap}};
+  const bool live = stream_tiles<4, 2>(in, r0, r1, smem, st, [&]() {
+    af = (float)__ldcg(&st->alpha);
+    bf = (float)__ldcg(&st->beta);
+    return mx_inner_live(st);
+  }, [&](int row, const float2* val, int nv) {
+    const float2 dk = val[0], rq = val[1], pk = val[2], ak = val[3];
+    float2 dn, rn, pn;
+    dn.x = fmaf(af, pk.x, dk.x);
+    dn.y = fmaf(af, pk.y, dk.y);
+    rn.x = fmaf(-af, ak.x, rq.x);
+    rn.y = fmaf(-af, ak.y, rq.y);
+    pn.x = fmaf(bf, pk.x, rn.x);
+    pn.y = fmaf(bf, pk.y, rn.y);
+    if (nv == 2) {
+      *reinterpret_cast<float2*>(a.d + row) = dn;
+      *reinterpret_cast<float2*>(a.r + row) = rn;
+      *reinterpret_cast<float2*>(a.p + row) = pn;
+      ff_add_prod(acc, rn.x, rn.x);
+      ff_add_prod(acc, rn.y, rn.y);
+    } else {
+      a.d[row] = dn.x;
+      a.r[row] = rn.x;
+      a.p[row] = pn.x;
+      ff_add_prod(acc, rn.x, rn.x);
+    }
+  });
+  griddep_trigger();
+  if (!__syncthreads_or(threadIdx.x < kConsumers && live)) return;
+  double v[1] = {ff_value(acc)};
+  tile_block_partials<1>(v, a.partials);
+  if (arrive_last(&st->counter)) {
+    double t[1];
+    final_sums<1>(a.partials, t);
+    if (threadIdx.x == 0) {
+      st->s[2] = t[0];
+      st->iter += 1;
+      trace_put(st, st->iter - 1, 0, st->alpha);
+      trace_put(st, st->iter - 1, 1, st->beta);
+      trace_put(st, st->iter - 1, 3, t[0]);
+      if (__ldcg(&st->timeout)) mx_finish(st, PK_TIMEOUT);
+      else if (!isfinite(t[0])) mx_finish(st, PK_ERR_NAN);
+      else if (t[0] <= st->s[3] || st->iter >= st->maxit) mx_stop_inner(st);
+      st->counter = 0;
+    }
+  }
+}
+
+static pk_status mx_tma_setup() {
+  static bool done = false;
+  if (!done) {
+    PK_CUDA(cudaFuncSetAttribute(k_mx_spmv_tma, cudaFuncAttributeMaxDynamicSharedMemorySize, csr_smem_bytes()));
+    PK_CUDA(cudaFuncSetAttribute(k_mx_update_tma, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 stream_smem_bytes<4, float>()));
+    done = true;
+  }
+  return PK_OK;
+}
+
 // Outer correction: x += ||r|| d in FP64.
 __global__ void __launch_bounds__(kBlock) k_mx_correct(MxArgs a) {
   DevState* st = a.st;
@@ -317,11 +433,19 @@ pk_status cg_mixed(pk_csr* A, const double* b, double* x, const pk_opts* o, pk_i
     k_mx_prep<<<Ge, kBlock, 0, cs>>>(a);
     if (t) t->end();
   };
+  // the tile engines need rows of at most 4096 nonzeros and FP32 vectors on 16-byte
+  // boundaries (the work vectors are); PK_FLAG_NO_TMA selects the row kernels
+  const bool tma = A->tma_ok && !(o->flags & PK_FLAG_NO_TMA);
+  if (tma && (e = mx_tma_setup())) return e;
+  const CsrTilesT<float> ct = csr_tiles32_of(A);
+  const int Gt = A->grid_tma, Gs = A->grid_stream;
   auto step = [&](cudaStream_t cs, Timer* t) {
     if (t) t->begin(PK_SLOT_SPMV_DOTS);
-    k_mx_spmv<<<G, kBlock, 0, cs>>>(a);
+    if (tma) launch_pdl(k_mx_spmv_tma, Gt, kTileThreads, csr_smem_bytes(), cs, ct, a);
+    else k_mx_spmv<<<G, kBlock, 0, cs>>>(a);
     if (t) { t->end(); t->begin(PK_SLOT_UPDATE); }
-    k_mx_update<<<Ge, kBlock, 0, cs>>>(a);
+    if (tma) launch_pdl(k_mx_update_tma, Gs, kTileThreads, stream_smem_bytes<4, float>(), cs, a);
+    else k_mx_update<<<Ge, kBlock, 0, cs>>>(a);
     if (t) t->end();
   };
   auto post = [&](cudaStream_t cs, Timer* t) {
@@ -332,10 +456,14 @@ pk_status cg_mixed(pk_csr* A, const double* b, double* x, const pk_opts* o, pk_i
   const bool graph = o->loop != PK_LOOP_HOST && !T.on;
   if (graph) {
     const void* keys[4] = {v.x_dev, v.b_dev, nullptr, nullptr};
-    const int64_t ikeys[4] = {PK_PREC_MIXED, 0, 0, 0};
+    const int64_t ikeys[4] = {PK_PREC_MIXED, tma ? 1 : 0, 0, 0};
     pk_graph_entry* ge = nullptr;
     if ((e = build_nested_graph(A, 8, keys, ikeys, [&](cudaStream_t cs) { pre(cs, nullptr); },
-                                [&](cudaStream_t cs) { step(cs, nullptr); },
+                                [&](cudaStream_t cs) {
+                                  // four inner iterations per graph pass; kernels after the
+                                  // inner stop return at once
+                                  for (int u = 0; u < (tma ? 4 : 1); ++u) step(cs, nullptr);
+                                },
                                 [&](cudaStream_t cs) { post(cs, nullptr); }, &ge)))
       return e;
     launch_enable_cond2(A, ge, s);

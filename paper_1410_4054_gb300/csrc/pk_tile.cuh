@@ -142,23 +142,33 @@ __device__ __forceinline__ void tile_block_partials(double (&v)[NV], double* par
 // Streaming tiles: NIN length-n float64 vectors, TROWS rows per tile, NST stages.
 // Rows of block b: equal chunks of the grid (multiples of 32 rows).
 
-template <int NIN>
+// Element pair read by a consumer thread (two consecutive rows of one input).
+template <class ET>
+struct Pair;
+template <>
+struct Pair<double> { using type = double2; };
+template <>
+struct Pair<float> { using type = float2; };
+
+template <int NIN, class ET = double>
 struct StreamIn {
-  const double* v[NIN];
+  const ET* v[NIN];
 };
 
 constexpr int kStreamRows = 512;  // rows per streaming tile: 2 per consumer thread
 
 // Stages of the streaming ring: as many as fit in ~96 KB (two blocks per SM), 2..8.
-template <int NIN>
+template <int NIN, class ET = double>
 __host__ __device__ constexpr int stream_stages() {
-  return (98304 / (NIN * kStreamRows * 8)) > 8 ? 8
-         : (98304 / (NIN * kStreamRows * 8)) < 2 ? 2 : (98304 / (NIN * kStreamRows * 8));
+  return (98304 / (NIN * kStreamRows * (int)sizeof(ET))) > 8 ? 8
+         : (98304 / (NIN * kStreamRows * (int)sizeof(ET))) < 2
+             ? 2
+             : (98304 / (NIN * kStreamRows * (int)sizeof(ET)));
 }
 
-template <int NIN>
+template <int NIN, class ET = double>
 __host__ __device__ constexpr int stream_smem_bytes() {
-  return stream_stages<NIN>() * NIN * kStreamRows * 8 + 2 * stream_stages<NIN>() * 8;
+  return stream_stages<NIN, ET>() * NIN * kStreamRows * (int)sizeof(ET) + 2 * stream_stages<NIN, ET>() * 8;
 }
 
 // Runs the streaming pipeline.  The first NPRE inputs do not depend on the preceding
@@ -166,17 +176,19 @@ __host__ __device__ constexpr int stream_smem_bytes() {
 // (programmatic dependent launch), the remaining inputs after it.  After the wait the
 // producer and every consumer call `setup()`, which reads the solver state and returns false
 // if this kernel has nothing to do (the block then only drains what was prefetched); it must
-// give the same answer in every thread.  `body(row, vals,
-// nvalid)` is called for row pairs (vals[k] = double2 of input k at rows row, row+1; nvalid =
-// 1 or 2).  Returns, in consumer threads, whether the solve was live (a timed-out wait is
-// recorded in the state and ends the loop early).
-template <int NIN, int NPRE, class Setup, class Body>
-__device__ __forceinline__ bool stream_tiles(const StreamIn<NIN>& in, int r0, int r1,
+// give the same answer in every thread.  `body(row, vals, nvalid)` is called for row pairs
+// (vals[k] = the pair of input k at rows row, row+1; nvalid = 1 or 2).  Returns, in consumer
+// threads, whether the solve was live (a timed-out wait is recorded in the state and ends the
+// loop early).  ET is the element type (double, or float for the mixed-precision inner loop).
+template <int NIN, int NPRE, class ET = double, class Setup, class Body>
+__device__ __forceinline__ bool stream_tiles(const StreamIn<NIN, ET>& in, int r0, int r1,
                                              unsigned char* smem, DevState* st, Setup&& setup,
                                              Body&& body) {
-  constexpr int kStreamStages = stream_stages<NIN>();
-  double* buf = reinterpret_cast<double*>(smem);
-  uint64_t* full = reinterpret_cast<uint64_t*>(smem + kStreamStages * NIN * kStreamRows * 8);
+  using P2 = typename Pair<ET>::type;
+  constexpr int kStreamStages = stream_stages<NIN, ET>();
+  constexpr int kPerUnit = 16 / (int)sizeof(ET);  // elements per 16-byte copy unit
+  ET* buf = reinterpret_cast<ET*>(smem);
+  uint64_t* full = reinterpret_cast<uint64_t*>(smem + (size_t)kStreamStages * NIN * kStreamRows * sizeof(ET));
   uint64_t* empty = full + kStreamStages;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   if (threadIdx.x == 0) {
@@ -191,7 +203,7 @@ __device__ __forceinline__ bool stream_tiles(const StreamIn<NIN>& in, int r0, in
   const int npro = min(kStreamStages, ntiles);
   auto tile_bytes = [&](int t) {
     const int rows = min(kStreamRows, r1 - (r0 + t * kStreamRows));
-    return (uint32_t)(((rows + 1) & ~1) * 8);  // whole 16-byte units
+    return (uint32_t)(((rows + kPerUnit - 1) / kPerUnit) * 16);  // whole 16-byte units
   };
   auto issue = [&](int t, int k0, int k1) {
     const int s = t % kStreamStages;
@@ -247,10 +259,10 @@ __device__ __forceinline__ bool stream_tiles(const StreamIn<NIN>& in, int r0, in
       const int rows = min(kStreamRows, r1 - row0);
       const int i = 2 * threadIdx.x;  // consumer thread -> row pair
       if (i < rows) {
-        double2 vals[NIN];
+        P2 vals[NIN];
 #pragma unroll
         for (int k = 0; k < NIN; ++k)
-          vals[k] = *reinterpret_cast<const double2*>(buf + ((size_t)s * NIN + k) * kStreamRows + i);
+          vals[k] = *reinterpret_cast<const P2*>(buf + ((size_t)s * NIN + k) * kStreamRows + i);
         body(row0 + i, vals, min(2, rows - i));
       }
     }
@@ -274,21 +286,24 @@ constexpr int kStageBytes = ((kRpWords * 4 + 15) & ~15) + kVaWords * 8 + ((kCiWo
 
 constexpr int csr_smem_bytes() { return kCsrStages * kStageBytes + 2 * kCsrStages * 8 + kCsrStages * 8; }
 
-struct CsrTiles {
+template <class VT>
+struct CsrTilesT {
   const int32_t* rp;
   const int32_t* ci;
-  const double* va;
+  const VT* va;             // values: FP64, or the FP32 copy for the mixed-precision inner loop
   const int32_t* tile_row;  // row start of every tile (global tile list), plus n at the end
   const int32_t* blk_tile;  // tiles of block b: [blk_tile[b], blk_tile[b+1])
 };
+using CsrTiles = CsrTilesT<double>;
 
 // Runs the CSR pipeline.  Consumer thread t handles rows R0 + t and R0 + t + 256 of every
 // tile together: `rows_fn(ra, ja0, ja1, rb, jb0, jb1, sva, sci)` receives both rows (rb = -1
 // if the tile has no second row for this thread) and their nonzero windows in shared memory
 // (sva/sci are offset so that entry j is sva[j], sci[j]).
-template <class Setup, class RowFn>
-__device__ __forceinline__ bool csr_tiles(const CsrTiles& T, unsigned char* smem, DevState* st,
+template <class VT, class Setup, class RowFn>
+__device__ __forceinline__ bool csr_tiles(const CsrTilesT<VT>& T, unsigned char* smem, DevState* st,
                                           Setup&& setup, RowFn&& row_fn) {
+  constexpr int kVaUnit = 16 / (int)sizeof(VT);  // values per 16-byte copy unit
   uint64_t* full = reinterpret_cast<uint64_t*>(smem + kCsrStages * kStageBytes);
   uint64_t* empty = full + kCsrStages;
   int2* meta = reinterpret_cast<int2*>(empty + kCsrStages);  // tile rows [R0, R1) per stage
@@ -305,7 +320,7 @@ __device__ __forceinline__ bool csr_tiles(const CsrTiles& T, unsigned char* smem
   const int ntiles = t1 - t0;
   auto stage_rp = [&](int s) { return reinterpret_cast<int32_t*>(smem + (size_t)s * kStageBytes); };
   auto stage_va = [&](int s) {
-    return reinterpret_cast<double*>(smem + (size_t)s * kStageBytes + ((kRpWords * 4 + 15) & ~15));
+    return reinterpret_cast<VT*>(smem + (size_t)s * kStageBytes + ((kRpWords * 4 + 15) & ~15));
   };
   auto stage_ci = [&](int s) {
     return reinterpret_cast<int32_t*>(smem + (size_t)s * kStageBytes + ((kRpWords * 4 + 15) & ~15) +
@@ -340,9 +355,9 @@ __device__ __forceinline__ bool csr_tiles(const CsrTiles& T, unsigned char* smem
           if (use > 0 && !mbar_wait(&empty[s], (use - 1) & 1)) { ok = false; report_timeout(st); }
           if (ok) {
             const int rs = a0 & ~3, re = (a1 + 1 + 3) & ~3;    // row pointers a0..a1
-            const int vs = b0 & ~1, ve = (b1 + 1) & ~1;        // values b0..b1-1
+            const int vs = b0 & ~(kVaUnit - 1), ve = (b1 + kVaUnit - 1) & ~(kVaUnit - 1);  // values
             const int cs = b0 & ~3, ce = (b1 + 3) & ~3;        // columns b0..b1-1
-            const uint32_t nrp = (uint32_t)(re - rs) * 4, nva = (uint32_t)(ve - vs) * 8,
+            const uint32_t nrp = (uint32_t)(re - rs) * 4, nva = (uint32_t)(ve - vs) * (uint32_t)sizeof(VT),
                            nci = (uint32_t)(ce - cs) * 4;
             meta[s] = make_int2(a0, a1);  // published by the arrive below (release)
             mbar_expect_tx(&full[s], nrp + nva + nci);
@@ -385,7 +400,7 @@ __device__ __forceinline__ bool csr_tiles(const CsrTiles& T, unsigned char* smem
     if (ra < R1) {
       const int32_t* srp = stage_rp(s) - (R0 & ~3);
       const int z0 = srp[R0];
-      const int vs = z0 & ~1;  // the window of this tile starts at the first row's nonzeros
+      const int vs = z0 & ~(kVaUnit - 1);  // the window of this tile starts at the first row's nonzeros
       const int cs = z0 & ~3;
       const int rb = ra + kConsumers < R1 ? ra + kConsumers : -1;
       const int jb0 = rb >= 0 ? srp[rb] : 0, jb1 = rb >= 0 ? srp[rb + 1] : 0;
@@ -506,6 +521,39 @@ inline void launch_pdl(void (*kern)(KArgs...), int grid, int block, size_t smem,
   cfg.attrs = attr;
   cfg.numAttrs = 1;
   cudaLaunchKernelEx(&cfg, kern, static_cast<KArgs>(args)...);
+}
+
+// FP32 row product from a shared-memory window: the row's products summed left to right
+// (the order of a plain CSR row loop), gathers of a batch of 8 issued before the FMAs.
+__device__ __forceinline__ float smem_row_f32(const float* sva, const int32_t* sci, int j, int j1,
+                                              const float* __restrict__ x) {
+  float s = 0.0f;
+  for (; j < j1; j += 8) {
+    const int m = min(8, j1 - j);
+    int c[8];
+    float v[8], xv[8];
+#pragma unroll
+    for (int k = 0; k < 8; ++k) {
+      c[k] = k < m ? sci[j + k] : 0;
+      v[k] = k < m ? sva[j + k] : 0.0f;
+    }
+#pragma unroll
+    for (int k = 0; k < 8; ++k) xv[k] = k < m ? __ldg(x + c[k]) : 0.0f;
+#pragma unroll
+    for (int k = 0; k < 8; ++k)
+      if (k < m) s = fmaf(v[k], xv[k], s);
+  }
+  return s;
+}
+
+inline CsrTilesT<float> csr_tiles32_of(const pk_csr* A) {
+  CsrTilesT<float> t;
+  t.rp = A->rp;
+  t.ci = A->ci;
+  t.va = A->va32;
+  t.tile_row = A->tile_row;
+  t.blk_tile = A->blk_tile;
+  return t;
 }
 
 inline CsrTiles csr_tiles_of(const pk_csr* A) {
