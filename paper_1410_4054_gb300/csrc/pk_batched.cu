@@ -38,27 +38,48 @@ struct BatchSys {
   double rel_res;
 };
 
-// Block-wide sums of NV values (fixed order: xor tree in warps, then warps in order); every
-// thread receives the sums.  Ends with a barrier, so the shared array may be reused at once.
+// Block-wide sums of NV values, broadcast to every thread.  GB300 issues about two FP64
+// operations per clock per SM with a 64-cycle latency, so the sum is done by one warp: every
+// thread stages its values in shared memory, each lane of warp 0 adds blockDim/32 of them
+// with four interleaved accumulators (fixed order), and a butterfly finishes (both partners
+// of a pair add the same two values, so every lane ends with the same bits).
 template <int NV>
 __device__ __forceinline__ void cta_sum(double (&v)[NV]) {
-  __shared__ double sm[NV][32];
-  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
+  __shared__ double buf[NV][1024];
+  __shared__ double bc[NV];
+  const int lane = threadIdx.x & 31, per = blockDim.x >> 5;
 #pragma unroll
-  for (int k = 0; k < NV; ++k) v[k] = warp_sum(v[k]);
-  if (lane == 0) {
+  for (int k = 0; k < NV; ++k) buf[k][threadIdx.x] = v[k];
+  __syncthreads();
+  if (threadIdx.x < 32) {
 #pragma unroll
-    for (int k = 0; k < NV; ++k) sm[k][warp] = v[k];
+    for (int k = 0; k < NV; ++k) {
+      double a0 = 0.0, a1 = 0.0, a2 = 0.0, a3 = 0.0;
+      int m = 0;
+      for (; m + 4 <= per; m += 4) {
+        a0 += buf[k][(m + 0) * 32 + lane];
+        a1 += buf[k][(m + 1) * 32 + lane];
+        a2 += buf[k][(m + 2) * 32 + lane];
+        a3 += buf[k][(m + 3) * 32 + lane];
+      }
+      for (; m < per; ++m) a0 += buf[k][m * 32 + lane];
+      double t = (a0 + a1) + (a2 + a3);
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) t += __shfl_xor_sync(0xffffffffu, t, o);
+      if (lane == 0) bc[k] = t;
+    }
   }
   __syncthreads();
 #pragma unroll
-  for (int k = 0; k < NV; ++k) {
-    double t = 0.0;
-    for (int w = 0; w < nw; ++w) t += sm[k][w];
-    v[k] = t;
-  }
-  __syncthreads();
+  for (int k = 0; k < NV; ++k) v[k] = bc[k];
 }
+
+// Scalars of an iteration decided by thread 0 and broadcast (every FP64 instruction issued
+// by all warps of a block, like a division, costs the SM's narrow FP64 pipe).
+struct CtaScalars {
+  double a, b;
+  int status;
+};
 
 __device__ __forceinline__ double row_f64(const BatchSys& S, const double* __restrict__ x, int row) {
   const int j0 = __ldg(S.rp + row), j1 = __ldg(S.rp + row + 1);
@@ -99,6 +120,7 @@ __device__ __forceinline__ float row_f32(const BatchSys& S, const float* __restr
 // Pipelined CG (Alg. 2) on one system by one block, FP64.  Returns the status.
 __device__ int cta_cg64(BatchSys& S, double tol, int maxit) {
   const int n = S.n, t0 = threadIdx.x, bs = blockDim.x;
+  __shared__ CtaScalars sc;
   double v[2] = {0.0, 0.0};
   for (int row = t0; row < n; row += bs) {
     const double bi = S.b[row];
@@ -112,7 +134,7 @@ __device__ int cta_cg64(BatchSys& S, double tol, int maxit) {
   double rr = v[0];
   const double bb = v[1], thr2 = tol * tol * bb;
   S.iters = 0;
-  S.rel_res = bb > 0 ? sqrt(rr / bb) : 0.0;
+  if (t0 == 0) S.rel_res = bb > 0 ? sqrt(rr / bb) : 0.0;
   if (!isfinite(rr) || !isfinite(bb)) return PK_ERR_NAN;
   if (bb == 0.0) {
     for (int row = t0; row < n; row += bs) S.x[row] = 0.0;
@@ -121,7 +143,6 @@ __device__ int cta_cg64(BatchSys& S, double tol, int maxit) {
   }
   if (rr <= thr2) return PK_OK;
   if (maxit <= 0) return PK_NOT_CONVERGED;
-  double alpha = 0.0, beta = 0.0;
   for (int it = 0;; ++it) {
     // A p_it with <Ap,Ap>, <p,Ap> -> alpha, beta (Eq. (3))
     v[0] = v[1] = 0.0;
@@ -132,10 +153,18 @@ __device__ int cta_cg64(BatchSys& S, double tol, int maxit) {
       v[1] = fma(S.p[row], s, v[1]);
     }
     cta_sum<2>(v);
-    if (!isfinite(v[0]) || !isfinite(v[1])) return PK_ERR_NAN;
-    if (v[1] <= 0.0) return PK_NOT_SPD;
-    alpha = rr / v[1];
-    beta = alpha * alpha * v[0] / rr - 1.0;
+    if (t0 == 0) {
+      sc.status = kRunning;
+      if (!isfinite(v[0]) || !isfinite(v[1])) sc.status = PK_ERR_NAN;
+      else if (v[1] <= 0.0) sc.status = PK_NOT_SPD;
+      else {
+        sc.a = rr / v[1];
+        sc.b = sc.a * sc.a * v[0] / rr - 1.0;
+      }
+    }
+    __syncthreads();
+    if (sc.status != kRunning) return sc.status;
+    const double alpha = sc.a, beta = sc.b;
     // x, r, p updates with <r,r>
     double w[1] = {0.0};
     for (int row = t0; row < n; row += bs) {
@@ -148,11 +177,16 @@ __device__ int cta_cg64(BatchSys& S, double tol, int maxit) {
     }
     cta_sum<1>(w);
     rr = w[0];
-    S.iters = it + 1;
-    S.rel_res = sqrt(rr / bb);
-    if (!isfinite(rr)) return PK_ERR_NAN;
-    if (rr <= thr2) return PK_OK;
-    if (it + 1 >= maxit) return PK_NOT_CONVERGED;
+    if (t0 == 0) {
+      S.iters = it + 1;
+      S.rel_res = sqrt(rr / bb);
+      sc.status = kRunning;
+      if (!isfinite(rr)) sc.status = PK_ERR_NAN;
+      else if (rr <= thr2) sc.status = PK_OK;
+      else if (it + 1 >= maxit) sc.status = PK_NOT_CONVERGED;
+    }
+    __syncthreads();
+    if (sc.status != kRunning) return sc.status;
   }
 }
 
@@ -160,6 +194,7 @@ __device__ int cta_cg64(BatchSys& S, double tol, int maxit) {
 // alpha, beta) are accumulated in FP64.  Inner stop: ||r_in|| <= tol_in ||r_outer||.
 __device__ int cta_cg_mixed(BatchSys& S, double tol, int maxit, double tol_in, int max_outer) {
   const int n = S.n, t0 = threadIdx.x, bs = blockDim.x;
+  __shared__ CtaScalars sc;
   S.iters = 0;
   S.outer = 0;
   S.inner_total = 0;
@@ -177,7 +212,7 @@ __device__ int cta_cg_mixed(BatchSys& S, double tol, int maxit, double tol_in, i
     cta_sum<2>(v);
     if (bb < 0) bb = v[1];
     const double rr_out = v[0];
-    S.rel_res = bb > 0 ? sqrt(rr_out / bb) : 0.0;
+    if (t0 == 0) S.rel_res = bb > 0 ? sqrt(rr_out / bb) : 0.0;
     if (!isfinite(rr_out) || !isfinite(bb)) return PK_ERR_NAN;
     if (bb == 0.0) {
       for (int row = t0; row < n; row += bs) S.x[row] = 0.0;
@@ -188,44 +223,57 @@ __device__ int cta_cg_mixed(BatchSys& S, double tol, int maxit, double tol_in, i
     if (outer >= max_outer || S.iters >= maxit) return PK_NOT_CONVERGED;
     S.outer = outer + 1;
     // inner FP32 system A d = r / ||r|| (unit right-hand side keeps FP32 in range)
-    const double scale = sqrt(rr_out);
-    const double inv = 1.0 / scale;
+    if (t0 == 0) {
+      sc.a = sqrt(rr_out);
+      sc.b = 1.0 / sc.a;
+    }
+    __syncthreads();
+    const double scale = sc.a, inv = sc.b;
+    FF acc{0.0f, 0.0f};
     for (int row = t0; row < n; row += bs) {
       const float ri = (float)(S.r[row] * inv);
       S.r32[row] = ri;
       S.p32[row] = ri;
       S.d32[row] = 0.0f;
+      ff_add_prod(acc, ri, ri);
     }
-    __syncthreads();
-    double w[1] = {0.0};
-    for (int row = t0; row < n; row += bs) w[0] = fma((double)S.r32[row], (double)S.r32[row], w[0]);
+    double w[1] = {ff_value(acc)};
     cta_sum<1>(w);
     double rr = w[0];
     const double thr_in = tol_in * tol_in * rr;
     const int budget = maxit - S.iters;
     for (int it = 0; it < budget; ++it) {
-      double u[2] = {0.0, 0.0};
+      FF aa{0.0f, 0.0f}, pa{0.0f, 0.0f};
       for (int row = t0; row < n; row += bs) {
         const float s = row_f32(S, S.p32, row);
         S.ap32[row] = s;
-        u[0] = fma((double)s, (double)s, u[0]);
-        u[1] = fma((double)S.p32[row], (double)s, u[1]);
+        ff_add_prod(aa, s, s);
+        ff_add_prod(pa, S.p32[row], s);
       }
+      double u[2] = {ff_value(aa), ff_value(pa)};
       cta_sum<2>(u);
-      if (!isfinite(u[0]) || !isfinite(u[1])) return PK_ERR_NAN;
-      if (u[1] <= 0.0) return PK_NOT_SPD;
-      const double alpha = rr / u[1];
-      const double beta = alpha * alpha * u[0] / rr - 1.0;
-      const float af = (float)alpha, bf = (float)beta;
-      double q[1] = {0.0};
+      if (t0 == 0) {
+        sc.status = kRunning;
+        if (!isfinite(u[0]) || !isfinite(u[1])) sc.status = PK_ERR_NAN;
+        else if (u[1] <= 0.0) sc.status = PK_NOT_SPD;
+        else {
+          sc.a = rr / u[1];
+          sc.b = sc.a * sc.a * u[0] / rr - 1.0;
+        }
+      }
+      __syncthreads();
+      if (sc.status != kRunning) return sc.status;
+      const float af = (float)sc.a, bf = (float)sc.b;
+      FF racc{0.0f, 0.0f};
       for (int row = t0; row < n; row += bs) {
         const float pk = S.p32[row];
         S.d32[row] = fmaf(af, pk, S.d32[row]);
         const float rk = fmaf(-af, S.ap32[row], S.r32[row]);
         S.r32[row] = rk;
         S.p32[row] = fmaf(bf, pk, rk);
-        q[0] = fma((double)rk, (double)rk, q[0]);
+        ff_add_prod(racc, rk, rk);
       }
+      double q[1] = {ff_value(racc)};
       cta_sum<1>(q);
       rr = q[0];
       S.iters += 1;

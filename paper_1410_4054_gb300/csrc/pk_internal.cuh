@@ -78,6 +78,24 @@ __device__ __forceinline__ void block_partials(double (&v)[NV], double* partials
   }
 }
 
+// Float-float accumulator for FP32 inner products: s.hi + s.lo holds the running sum of the
+// exact float products (error-free product with fmaf, TwoSum), all in the FP32 pipe.
+struct FF {
+  float hi, lo;
+};
+
+__device__ __forceinline__ void ff_add_prod(FF& s, float a, float b) {
+  const float p = a * b;
+  const float e = fmaf(a, b, -p);  // p + e == a * b exactly
+  const float t = s.hi + p;
+  const float bp = t - s.hi;
+  const float err = (s.hi - (t - bp)) + (p - bp);  // s.hi + p == t + err exactly
+  s.hi = t;
+  s.lo += err + e;
+}
+
+__device__ __forceinline__ double ff_value(const FF& s) { return (double)s.hi + (double)s.lo; }
+
 // Arrival on the grid-wide counter; true in every thread of the last block to arrive.
 __device__ __forceinline__ bool arrive_last(unsigned int* counter) {
   __shared__ unsigned int ticket;

@@ -35,23 +35,6 @@ struct MxArgs {
   DevState* st;
 };
 
-// float-float accumulator: s.hi + s.lo holds the running sum of exact float products
-struct FF {
-  float hi, lo;
-};
-
-__device__ __forceinline__ void ff_add_prod(FF& s, float a, float b) {
-  const float p = a * b;
-  const float e = fmaf(a, b, -p);  // p + e == a * b exactly
-  const float t = s.hi + p;
-  const float bp = t - s.hi;
-  const float err = (s.hi - (t - bp)) + (p - bp);  // s.hi + p == t + err exactly
-  s.hi = t;
-  s.lo += err + e;
-}
-
-__device__ __forceinline__ double ff_value(const FF& s) { return (double)s.hi + (double)s.lo; }
-
 __device__ __forceinline__ float row32(const MxArgs& a, const float* __restrict__ x, int row) {
   int j = __ldg(a.rp + row);
   const int j1 = __ldg(a.rp + row + 1);
