@@ -262,12 +262,18 @@ pk_status pk_residual_norm2(pk_csr* A, const double* b, const double* x, double*
  * [27][16 co][16 ci], tap = 9(dz+1) + 3(dy+1) + (dx+1); zero padding 1 at the boundary.
  * All pointers are device pointers; calls are stream-ordered and return at once.
  */
-/* Y = conv(X, W) + bias, then ReLU if relu; out_f32: Y is FP32 [D][H][W] holding channel 0
+/* Y = conv(X, W) + bias, then ReLU if relu (tcgen05 tensor cores: M = 128-voxel tiles of
+ * 8 x 16 voxels, one M128 N16 K16 MMA per tap, FP32 accumulator in tensor memory);
+ * out_f32: Y is FP32 [D][H][W] holding channel 0
  * only; mask (nullable, BF16 [D][H][W][16]): Y[v][c] = 0 where mask[v][c] <= 0 (the ReLU
  * derivative, used by the backward-data pass with flipped weights). */
 pk_status pk_conv3d_fwd(const void* X, const void* Wt, const float* bias, void* Y, int32_t D,
                         int32_t H, int32_t W, int32_t relu, int32_t out_f32, const void* mask,
                         void* stream);
+/* Reads and clears the device flag a tensor-core convolution sets when its bounded wait for
+ * its own MMAs runs out (PK_TIMEOUT; the output of that call is then incomplete); PK_OK
+ * otherwise.  Synchronises the stream. */
+pk_status pk_conv3d_check(void* stream);
 /* dW[tap][co][ci] = sum_v G[v][co] A[v + tap][ci] (FP32), db[co] = sum_v G[v][co]; scratch:
  * pk_conv3d_wgrad_scratch_floats(D, H, W) floats (deterministic block partials). */
 int64_t pk_conv3d_wgrad_scratch_floats(int32_t D, int32_t H, int32_t W);

@@ -5,22 +5,20 @@
 // channels are zero); weights BF16 [tap][co][ci] = [27][16][16], tap = 9(dz+1)+3(dy+1)+(dx+1);
 // zero padding of 1 at the grid boundary.
 //
-// Forward / backward-data (conv3d_fwd): one block per (z, y) row and 64-voxel x segment, four
-// warps of 16 voxels.  The block stages the 9 neighbouring rows (+-1 voxel halo in x) and all
-// weights in shared memory; for every tap a warp multiplies its 16 x 16 activation tile by
-// the tap's 16 x 16 weight tile with two m16n8k16 BF16 tensor-core MMAs (operands through
-// ldmatrix), i.e. an implicit GEMM with M = voxels, N = 16 output channels, K = 27 x 16.
-// The backward-data pass is the same kernel on flipped, transposed weights with the ReLU mask
-// of the layer input applied in the epilogue.
-// Weight gradient (conv3d_wgrad): dW[tap] = G^T A_shift(tap), M = 16 output channels,
+// Forward / backward-data (conv3d_fwd): the tcgen05 tensor-core kernel below (TMA-staged
+// input blocks, one M128 N16 K16 MMA per tap, FP32 accumulators in tensor memory).  The
+// backward-data pass is the same kernel on flipped, transposed weights with the ReLU mask of
+// the layer input applied in the epilogue.
+// Weight gradient (conv3d_wgrad, warp-level mma.sync): dW[tap] = G^T A_shift(tap), M = 16 output channels,
 // N = 16 input channels, K = voxels: each block accumulates a band of rows in registers
 // (warp w owns taps w, w+4, ...), operands transposed on the fly with ldmatrix.trans, then a
 // fixed-order reduction over blocks (deterministic).
+#include <cuda.h>
 #include <cuda_bf16.h>
 
 #include <algorithm>
 
-#include "pk_internal.cuh"
+#include "pk_tile.cuh"
 
 namespace pk {
 
@@ -31,12 +29,6 @@ constexpr int kVs = 24;         // shared-memory stride of one voxel in BF16 (48
 constexpr int kWgradRows = 16;  // (z, y) rows per weight-gradient block
 
 __device__ __forceinline__ uint32_t sa(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
-
-__device__ __forceinline__ void ldsm4(uint32_t (&r)[4], const void* p) {
-  asm volatile("ldmatrix.sync.aligned.m8n8.x4.shared.b16 {%0,%1,%2,%3}, [%4];"
-               : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3])
-               : "r"(sa(p)));
-}
 
 __device__ __forceinline__ void ldsm4t(uint32_t (&r)[4], const void* p) {
   asm volatile("ldmatrix.sync.aligned.m8n8.x4.trans.shared.b16 {%0,%1,%2,%3}, [%4];"
@@ -78,68 +70,256 @@ struct ConvArgs {
   int out_f32;
 };
 
-__global__ void __launch_bounds__(128) k_conv3d(ConvArgs a) {
-  extern __shared__ __align__(128) unsigned char smem_raw[];
-  __nv_bfloat16* halo = reinterpret_cast<__nv_bfloat16*>(smem_raw);
-  __nv_bfloat16* wsm = halo + 9 * kHx * kVs;
-  const int y = blockIdx.x, z = blockIdx.y;
+// ---------------------------------------------------------------- tcgen05 forward kernel
+// Implicit GEMM on the 5th-generation tensor cores: an M = 128 tile of output voxels (8 along
+// x by 16 along y at one z) times N = 16 output channels, K = 27 taps x 16 input channels,
+// one tcgen05.mma (M128 N16 K16, BF16 operands, FP32 accumulator in tensor memory) per tap.
+// The input block around a tile -- 3 planes x 18 rows x 10 voxels, each voxel's 16 channels
+// as two 8-channel halves -- arrives by TMA: six cp.async.bulk.tensor copies of an
+// [18][10][8] box per tile, the halo outside the grid filled with zeros by the copy engine.
+// Each box lands in the no-swizzle K-major layout of the MMA's A operand: a core matrix is 8
+// voxels consecutive in x (8 x 16 bytes), the two K halves are kTcHalf bytes apart (leading
+// byte offset) and consecutive y rows kTcRow bytes apart (stride byte offset); a tap
+// (dz, dy, dx) is the same descriptor with its start moved by (dz, dy, dx) voxels; the taps
+// of each dz accumulate in their own tensor-memory accumulator (three independent MMA chains
+// per tile, summed in the epilogue).  Weights
+// [tap][half][co][8 ci] stay in shared memory for the whole launch.  A ring of kTcStages
+// staging buffers and two accumulators pipeline a persistent block's tiles: thread 0 issues
+// the copies and the MMAs of the next tile while all four warps run the epilogue of the
+// current one (tcgen05.ld, bias, ReLU or mask, BF16 store).  Every mbarrier wait is bounded
+// (2 s): a wait that runs out sets a device flag (pk_conv3d_check reports PK_TIMEOUT), the
+// block waits (bounded) for what it issued, frees its tensor memory and returns.
+
+constexpr int kTcX = 8, kTcY = 16;                  // tile: 8 x 16 voxels = M 128
+constexpr int kTcBx = kTcX + 2, kTcBy = kTcY + 2;   // staged block with the halo
+constexpr int kTcRow = kTcBx * 16;                  // bytes between staged y rows (SBO)
+constexpr int kTcBox = kTcBy * kTcRow;              // bytes of one [18][10][8] box (2880)
+constexpr int kTcHalf = (kTcBox + 127) & ~127;      // box pitch, 128-byte aligned (LBO)
+constexpr int kTcPlane = 2 * kTcHalf;
+constexpr int kTcStage = 3 * kTcPlane;              // 17,664 bytes
+constexpr int kTcStages = 2;
+constexpr int kTcW = 27 * 512;                      // weights, 13,824 bytes
+constexpr int kTcSmem = kTcStages * kTcStage + kTcW;
+constexpr int kTcChains = 3;                        // independent accumulators per tile (9 taps each)
+constexpr uint32_t kTcCols = 128;                   // tensor memory: 2 tiles x 3 accumulators x 16 columns
+
+__device__ int g_conv_timeout = 0;
+
+__device__ __forceinline__ uint64_t tc_desc(uint32_t saddr, uint32_t lbo, uint32_t sbo) {
+  // shared-memory matrix descriptor: start >> 4 (bits 0-13), LBO >> 4 (16-29), SBO >> 4
+  // (32-45), fixed 0b001 (46-48), base offset 0, relative LBO, no swizzle (61-63 = 0)
+  return (uint64_t)((saddr & 0x3FFFF) >> 4) | ((uint64_t)((lbo >> 4) & 0x3FFF) << 16) |
+         ((uint64_t)((sbo >> 4) & 0x3FFF) << 32) | (1ull << 46);
+}
+
+// instruction descriptor, kind::f16: D FP32 (bits 4-5 = 1), A and B BF16 (bits 7-9, 10-12 =
+// 1), both K-major (bits 15, 16 = 0), N >> 3 (bits 17-22), M >> 4 (bits 24-28)
+constexpr uint32_t kTcIdesc = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(16 >> 3) << 17) |
+                              ((uint32_t)(128 >> 4) << 24);
+
+__device__ __forceinline__ void tc_mma(uint32_t tmem_d, uint64_t adesc, uint64_t bdesc, uint32_t accumulate) {
+  asm volatile(
+      "{\n\t.reg .pred p;\n\t"
+      "setp.ne.b32 p, %4, 0;\n\t"
+      "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}" ::"r"(tmem_d),
+      "l"(adesc), "l"(bdesc), "r"(kTcIdesc), "r"(accumulate)
+      : "memory");
+}
+
+__device__ __forceinline__ void tc_commit(uint64_t* bar) {
+  asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+                   smem_addr(bar))
+               : "memory");
+}
+
+__device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
+__device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
+__device__ __forceinline__ void proxy_fence() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
+
+// 16 FP32 columns of this thread's tensor-memory lane.
+__device__ __forceinline__ void tc_ld16(uint32_t taddr, float (&v)[16]) {
+  uint32_t r[16];
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
+      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]),
+        "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]),
+        "=r"(r[14]), "=r"(r[15])
+      : "r"(taddr));
+  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+  for (int k = 0; k < 16; ++k) v[k] = __uint_as_float(r[k]);
+}
+
+// One [18][10][8] box of the channels-last input at (c, x, y, z) (x, y, z may lie outside
+// the grid: zero fill) into shared memory, completion on `bar`.
+__device__ __forceinline__ void tc_tma_box(uint32_t dst, const CUtensorMap* map, int c, int x, int y,
+                                           int z, uint64_t* bar) {
+  asm volatile(
+      "cp.async.bulk.tensor.4d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, "
+      "%4, %5}], [%6];" ::"r"(dst),
+      "l"(reinterpret_cast<uint64_t>(map)), "r"(c), "r"(x), "r"(y), "r"(z), "r"(smem_addr(bar))
+      : "memory");
+}
+
+__global__ void __launch_bounds__(128) k_conv3d_tc(const __grid_constant__ CUtensorMap xmap, ConvArgs a) {
+  extern __shared__ __align__(1024) unsigned char smem_tc[];
+  unsigned char* stg0 = smem_tc;                          // kTcStages staging buffers
+  unsigned char* wsm = smem_tc + kTcStages * kTcStage;    // weights
+  __shared__ __align__(8) uint64_t full_bar[kTcStages];   // staging buffer loaded
+  __shared__ __align__(8) uint64_t mma_bar[2];            // accumulator complete
+  __shared__ uint32_t tmem_slot;
+  __shared__ int abort_flag;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int tx = (a.W + kTcX - 1) / kTcX, ty = (a.H + kTcY - 1) / kTcY;
+  const int ntiles = tx * ty * a.D;
+  const int mine = blockIdx.x < ntiles ? (ntiles - 1 - blockIdx.x) / gridDim.x + 1 : 0;  // my tiles
   for (int e = threadIdx.x; e < 27 * kCh * 2; e += blockDim.x) {
-    const int half = e & 1, row = e >> 1;  // row = tap * 16 + co
-    *reinterpret_cast<uint4*>(wsm + row * kVs + 8 * half) =
-        *reinterpret_cast<const uint4*>(a.Wt + row * kCh + 8 * half);
+    const int half = e & 1, row = e >> 1, t = row / kCh, co = row % kCh;
+    *reinterpret_cast<uint4*>(wsm + t * 512 + half * 256 + co * 16) =
+        __ldg(reinterpret_cast<const uint4*>(a.Wt + row * kCh + 8 * half));
   }
-  const int j = lane >> 3, r = lane & 7;
-  const int g = lane >> 2, tq = lane & 3;
-  float bias0[2], bias1[2];
+  proxy_fence();  // the weights are read by the tensor core (async proxy)
+  if (threadIdx.x == 0) {
+    for (int s = 0; s < kTcStages; ++s) mbar_init(&full_bar[s], 1);
+    mbar_init(&mma_bar[0], 1);
+    mbar_init(&mma_bar[1], 1);
+    mbar_fence_init();
+    abort_flag = 0;
+  }
+  if (warp == 0) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_addr(&tmem_slot)),
+                 "r"(kTcCols)
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+  }
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tmem = tmem_slot;
+  const uint32_t w_addr = smem_addr(wsm), s_base = smem_addr(stg0);
+  auto tile_of = [&](int k, int& z, int& y0, int& x0) {  // the block's k-th tile
+    const int t = blockIdx.x + k * gridDim.x;
+    x0 = (t % tx) * kTcX;
+    y0 = ((t / tx) % ty) * kTcY;
+    z = t / (tx * ty);
+  };
+  auto load = [&](int k) {  // thread 0: the six boxes of tile k into stage k % kTcStages
+    int z, y0, x0;
+    tile_of(k, z, y0, x0);
+    const int s = k % kTcStages;
+    mbar_expect_tx(&full_bar[s], 6 * kTcBox);
+    for (int pl = 0; pl < 3; ++pl)
+      for (int h = 0; h < 2; ++h)
+        tc_tma_box(s_base + s * kTcStage + pl * kTcPlane + h * kTcHalf, &xmap, 8 * h, x0 - 1, y0 - 1,
+                   z + pl - 1, &full_bar[s]);
+  };
+  bool ok = true;
+  auto issue = [&](int k) {  // thread 0: wait for tile k's data, 27 MMAs into accumulator k & 1
+    const int s = k % kTcStages;
+    if (!mbar_wait(&full_bar[s], (k / kTcStages) & 1)) return false;
+    tc_fence_after();
+    const uint32_t sa0 = s_base + s * kTcStage;
+    const uint32_t acc = tmem + (k & 1) * (kTcChains * 16);
+    // three chains of nine taps (dz = -1, 0, +1), issued interleaved: consecutive MMAs write
+    // different accumulators and overlap in the tensor pipe
+#pragma unroll 1
+    for (int i = 0; i < 9; ++i) {
+      const int dy = i / 3, dx = i % 3;
 #pragma unroll
-  for (int k = 0; k < 2; ++k) {
-    bias0[k] = a.bias ? a.bias[2 * tq + k] : 0.f;
-    bias1[k] = a.bias ? a.bias[8 + 2 * tq + k] : 0.f;
-  }
-  for (int x0 = 0; x0 < a.W; x0 += kSeg) {
-    __syncthreads();
-    load_halo(halo, a.X, a.D, a.H, a.W, z, y, x0);
-    __syncthreads();
-    float acc0[4] = {0.f, 0.f, 0.f, 0.f}, acc1[4] = {0.f, 0.f, 0.f, 0.f};
-    const int ai = r + 8 * (j & 1), ach = 8 * (j >> 1);  // A: voxel row, channel block
-    const int bco = r + 8 * (j >> 1), bci = 8 * (j & 1);  // B: output channel, input block
-#pragma unroll 3
-    for (int t = 0; t < 27; ++t) {
-      const int dzdy = t / 3, dx = t % 3 - 1;
-      uint32_t af[4], bf[4];
-      ldsm4(af, halo + (dzdy * kHx + 16 * warp + ai + dx + 1) * kVs + ach);
-      ldsm4(bf, wsm + (t * kCh + bco) * kVs + bci);
-      mma16816(acc0, af, bf[0], bf[1]);
-      mma16816(acc1, af, bf[2], bf[3]);
+      for (int c = 0; c < kTcChains; ++c) {
+        const int tap = 9 * c + i;  // dz = c - 1
+        tc_mma(acc + c * 16, tc_desc(sa0 + c * kTcPlane + dy * kTcRow + dx * 16, kTcHalf, kTcRow),
+               tc_desc(w_addr + tap * 512, 256, 128), i > 0 ? 1u : 0u);
+      }
     }
-    // epilogue: rows g and g + 8 of the warp's 16 voxels
+    tc_commit(&mma_bar[k & 1]);
+    return true;
+  };
+  float bias[16];
 #pragma unroll
-    for (int h = 0; h < 2; ++h) {
-      const int x = x0 + 16 * warp + g + 8 * h;
-      if (x >= a.W) continue;
+  for (int c = 0; c < 16; ++c) bias[c] = a.bias ? a.bias[c] : 0.f;
+  if (threadIdx.x == 0 && mine > 0) {
+    for (int k = 0; k < min(kTcStages, mine); ++k) load(k);
+    ok = issue(0);
+  }
+  int issued_mma = threadIdx.x == 0 && mine > 0 && ok ? 1 : 0;
+  for (int k = 0; k < mine; ++k) {
+    // thread 0: the next tile's MMAs go out before this tile's epilogue (other accumulator)
+    if (threadIdx.x == 0 && ok && k + 1 < mine) {
+      ok = issue(k + 1);
+      issued_mma += ok;
+    }
+    if (!ok) abort_flag = 1;
+    if (!mbar_wait(&mma_bar[k & 1], (k >> 1) & 1)) abort_flag = 1;
+    tc_fence_after();
+    __syncthreads();
+    if (abort_flag) break;
+    // the stage of tile k is free: thread 0 refills it with tile k + kTcStages
+    if (threadIdx.x == 0 && k + kTcStages < mine) load(k + kTcStages);
+    int z, y0, x0;
+    tile_of(k, z, y0, x0);
+    float o[16];
+    {
+      // the three partial sums (taps with dz = -1, 0, +1), added in that order
+      const uint32_t row = tmem + ((uint32_t)(32 * warp) << 16) + (k & 1) * (kTcChains * 16);
+      float p1[16], p2[16];
+      tc_ld16(row, o);
+      tc_ld16(row + 16, p1);
+      tc_ld16(row + 32, p2);
+#pragma unroll
+      for (int c = 0; c < 16; ++c) o[c] = (o[c] + p1[c]) + p2[c];
+    }
+    const int m = 32 * warp + lane;
+    const int y = y0 + m / kTcX, x = x0 + m % kTcX;
+    if (y < a.H && x < a.W) {
       const size_t v = ((size_t)z * a.H + y) * a.W + x;
-      float o[4] = {acc0[2 * h] + bias0[0], acc0[2 * h + 1] + bias0[1], acc1[2 * h] + bias1[0],
-                    acc1[2 * h + 1] + bias1[1]};
       if (a.out_f32) {
-        if (tq == 0) a.Yf[v] = o[0];
-        continue;
-      }
-      if (a.relu) {
+        a.Yf[v] = o[0] + bias[0];
+      } else {
 #pragma unroll
-        for (int k = 0; k < 4; ++k) o[k] = fmaxf(o[k], 0.f);
+        for (int c = 0; c < 16; ++c) {
+          o[c] += bias[c];
+          if (a.relu) o[c] = fmaxf(o[c], 0.f);
+        }
+        if (a.mask) {
+          const uint4 m0 = *reinterpret_cast<const uint4*>(a.mask + v * kCh);
+          const uint4 m1 = *reinterpret_cast<const uint4*>(a.mask + v * kCh + 8);
+          const __nv_bfloat16* mb0 = reinterpret_cast<const __nv_bfloat16*>(&m0);
+          const __nv_bfloat16* mb1 = reinterpret_cast<const __nv_bfloat16*>(&m1);
+#pragma unroll
+          for (int c = 0; c < 8; ++c) {
+            if (!(__bfloat162float(mb0[c]) > 0.f)) o[c] = 0.f;
+            if (!(__bfloat162float(mb1[c]) > 0.f)) o[8 + c] = 0.f;
+          }
+        }
+        uint4 p0, p1;
+        __nv_bfloat162* q0 = reinterpret_cast<__nv_bfloat162*>(&p0);
+        __nv_bfloat162* q1 = reinterpret_cast<__nv_bfloat162*>(&p1);
+#pragma unroll
+        for (int c = 0; c < 4; ++c) {
+          q0[c] = __floats2bfloat162_rn(o[2 * c], o[2 * c + 1]);
+          q1[c] = __floats2bfloat162_rn(o[8 + 2 * c], o[8 + 2 * c + 1]);
+        }
+        *reinterpret_cast<uint4*>(a.Y + v * kCh) = p0;
+        *reinterpret_cast<uint4*>(a.Y + v * kCh + 8) = p1;
       }
-      if (a.mask) {
-        const __nv_bfloat162 m0 = *reinterpret_cast<const __nv_bfloat162*>(a.mask + v * kCh + 2 * tq);
-        const __nv_bfloat162 m1 = *reinterpret_cast<const __nv_bfloat162*>(a.mask + v * kCh + 8 + 2 * tq);
-        if (!(__bfloat162float(m0.x) > 0.f)) o[0] = 0.f;
-        if (!(__bfloat162float(m0.y) > 0.f)) o[1] = 0.f;
-        if (!(__bfloat162float(m1.x) > 0.f)) o[2] = 0.f;
-        if (!(__bfloat162float(m1.y) > 0.f)) o[3] = 0.f;
-      }
-      *reinterpret_cast<__nv_bfloat162*>(a.Y + v * kCh + 2 * tq) = __floats2bfloat162_rn(o[0], o[1]);
-      *reinterpret_cast<__nv_bfloat162*>(a.Y + v * kCh + 8 + 2 * tq) = __floats2bfloat162_rn(o[2], o[3]);
     }
+    tc_fence_before();
+    __syncthreads();  // accumulator k & 1 is free again
+  }
+  if (abort_flag && threadIdx.x == 0) {
+    atomicExch(&g_conv_timeout, 1);
+    // bounded waits for what this block still has in flight before its tensor memory goes
+    for (int s = 0; s < kTcStages; ++s) mbar_wait(&full_bar[s], 0);
+    mbar_wait(&mma_bar[0], 0);
+    mbar_wait(&mma_bar[1], 0);
+  }
+  (void)issued_mma;
+  tc_fence_before();
+  __syncthreads();
+  if (warp == 0) {
+    tc_fence_after();
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(kTcCols) : "memory");
   }
 }
 
@@ -362,12 +542,53 @@ __global__ void k_adam(int count, float* p, const float* grad, float* m, float* 
   if (p16) p16[e] = __float2bfloat16_rn(np);
 }
 
+// Tensor map of a channels-last BF16 activation [D][H][W][16] for the TMA boxes of
+// k_conv3d_tc: dimensions (channel, x, y, z), box (8, 10, 18, 1), zero fill outside.
+using EncodeTiled = CUresult (*)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*, const cuuint64_t*,
+                                 const cuuint64_t*, const cuuint32_t*, const cuuint32_t*,
+                                 CUtensorMapInterleave, CUtensorMapSwizzle, CUtensorMapL2promotion,
+                                 CUtensorMapFloatOOBfill);
+
+static pk_status input_map(CUtensorMap* map, const __nv_bfloat16* X, int D, int H, int W) {
+  static EncodeTiled encode = nullptr;
+  if (!encode) {
+    void* fn = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &fn, 12000, cudaEnableDefault, &q) !=
+            cudaSuccess ||
+        q != cudaDriverEntryPointSuccess || !fn) {
+      set_error("cuTensorMapEncodeTiled is not available");
+      return PK_ERR_CUDA;
+    }
+    encode = reinterpret_cast<EncodeTiled>(fn);
+  }
+  if (reinterpret_cast<uintptr_t>(X) & 15) {
+    set_error("pk_conv3d_fwd: activations must be 16-byte aligned");
+    return PK_ERR_ARG;
+  }
+  const cuuint64_t dims[4] = {(cuuint64_t)kCh, (cuuint64_t)W, (cuuint64_t)H, (cuuint64_t)D};
+  const cuuint64_t strides[3] = {(cuuint64_t)kCh * 2, (cuuint64_t)W * kCh * 2, (cuuint64_t)H * W * kCh * 2};
+  const cuuint32_t box[4] = {8, (cuuint32_t)kTcBx, (cuuint32_t)kTcBy, 1};
+  const cuuint32_t estr[4] = {1, 1, 1, 1};
+  const CUresult r = encode(map, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 4, const_cast<__nv_bfloat16*>(X), dims,
+                            strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+                            CU_TENSOR_MAP_L2_PROMOTION_L2_128B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  if (r != CUDA_SUCCESS) {
+    set_error("pk_conv3d_fwd: cuTensorMapEncodeTiled failed");
+    return PK_ERR_CUDA;
+  }
+  return PK_OK;
+}
+
 static pk_status conv_setup() {
   static bool done = false;
   if (!done) {
-    const int fwd_smem = (9 * kHx * kVs + 27 * kCh * kVs) * 2;
     const int wg_smem = (9 * kHx * kVs + kSeg * kVs) * 2;
-    PK_CUDA(cudaFuncSetAttribute(k_conv3d, cudaFuncAttributeMaxDynamicSharedMemorySize, fwd_smem));
+    PK_CUDA(cudaFuncSetAttribute(k_conv3d_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, kTcSmem));
+    // several blocks per SM (each with its own chain of accumulating MMAs): the largest
+    // shared-memory carveout
+    PK_CUDA(cudaFuncSetAttribute(k_conv3d_tc, cudaFuncAttributePreferredSharedMemoryCarveout,
+                                 (int)cudaSharedmemCarveoutMaxShared));
     PK_CUDA(cudaFuncSetAttribute(k_conv3d_wgrad, cudaFuncAttributeMaxDynamicSharedMemorySize, wg_smem));
     done = true;
   }
@@ -383,7 +604,8 @@ extern "C" {
 pk_status pk_conv3d_fwd(const void* X, const void* Wt, const float* bias, void* Y, int32_t D,
                         int32_t H, int32_t W, int32_t relu, int32_t out_f32, const void* mask,
                         void* stream) {
-  if (!X || !Wt || !Y || D <= 0 || H <= 0 || W <= 0 || H > 65535 || D > 65535) {
+  if (!X || !Wt || !Y || D <= 0 || H <= 0 || W <= 0 ||
+      (int64_t)D * ((H + kTcY - 1) / kTcY) * ((W + kTcX - 1) / kTcX) >= (int64_t(1) << 31)) {
     set_error("pk_conv3d_fwd: bad arguments");
     return PK_ERR_ARG;
   }
@@ -401,9 +623,42 @@ pk_status pk_conv3d_fwd(const void* X, const void* Wt, const float* bias, void* 
   a.W = W;
   a.relu = relu;
   a.out_f32 = out_f32;
-  const int smem = (9 * kHx * kVs + 27 * kCh * kVs) * 2;
-  k_conv3d<<<dim3(H, D), 128, smem, (cudaStream_t)stream>>>(a);
+  static int grid_max = 0;
+  if (!grid_max) {
+    // resident blocks per SM from the kernel's own footprint (shared memory incl. the
+    // per-block reservation, registers, threads)
+    int dev = 0, sms = 1, smem_sm = 0, resv = 0, regs_sm = 0;
+    PK_CUDA(cudaGetDevice(&dev));
+    PK_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+    PK_CUDA(cudaDeviceGetAttribute(&smem_sm, cudaDevAttrMaxSharedMemoryPerMultiprocessor, dev));
+    PK_CUDA(cudaDeviceGetAttribute(&resv, cudaDevAttrReservedSharedMemoryPerBlock, dev));
+    PK_CUDA(cudaDeviceGetAttribute(&regs_sm, cudaDevAttrMaxRegistersPerMultiprocessor, dev));
+    cudaFuncAttributes fa;
+    PK_CUDA(cudaFuncGetAttributes(&fa, k_conv3d_tc));
+    const int per_block = kTcSmem + (int)fa.sharedSizeBytes + resv;
+    const int by_smem = smem_sm / per_block;
+    const int by_regs = regs_sm / (128 * ((fa.numRegs + 7) & ~7));
+    grid_max = sms * std::max(1, std::min(std::min(by_smem, by_regs), 16));
+  }
+  CUtensorMap map;
+  if ((e = input_map(&map, a.X, D, H, W))) return e;
+  const int64_t ntiles = (int64_t)D * ((H + kTcY - 1) / kTcY) * ((W + kTcX - 1) / kTcX);
+  const int grid = (int)std::min<int64_t>(ntiles, grid_max);
+  k_conv3d_tc<<<grid, 128, kTcSmem, (cudaStream_t)stream>>>(map, a);
   PK_CUDA(cudaGetLastError());
+  return PK_OK;
+}
+
+pk_status pk_conv3d_check(void* stream) {
+  int flag = 0, zero = 0;
+  cudaStream_t s = (cudaStream_t)stream;
+  PK_CUDA(cudaMemcpyFromSymbolAsync(&flag, g_conv_timeout, sizeof(int), 0, cudaMemcpyDeviceToHost, s));
+  PK_CUDA(cudaMemcpyToSymbolAsync(g_conv_timeout, &zero, sizeof(int), 0, cudaMemcpyHostToDevice, s));
+  PK_CUDA(cudaStreamSynchronize(s));
+  if (flag) {
+    set_error("a tensor-core convolution timed out waiting for its MMAs");
+    return PK_TIMEOUT;
+  }
   return PK_OK;
 }
 

@@ -78,6 +78,7 @@ EXPORTS = {
     "pk_conv3d_wgrad": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p,
                                   C.c_int32, C.c_int32, C.c_int32, C.c_void_p]),
     "pk_conv3d_flip": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p]),
+    "pk_conv3d_check": (C.c_int, [C.c_void_p]),
     "pk_warmstart_scratch_doubles": (C.c_int64, []),
     "pk_warmstart_input": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p,
                                      C.c_void_p, C.c_void_p, C.c_void_p]),
@@ -307,6 +308,11 @@ def residual_norm2(A: CSRMatrix, b, x, out2, stream=None):
     """out2[0] = ||b - A x||^2 (device tensors)."""
     _check(lib().pk_residual_norm2(A.handle, _ptr(b), _ptr(x), _ptr(out2), _stream_ptr(stream)),
            "pk_residual_norm2")
+
+
+def conv3d_check(stream=None):
+    """Raises PkError(PK_TIMEOUT) if a tensor-core convolution timed out since the last check."""
+    _check(lib().pk_conv3d_check(_stream_ptr(stream)), "pk_conv3d_check")
 
 
 def conv3d_fwd(X, Wt, bias, Y, dims, relu=True, out_f32=False, mask=None, stream=None):

@@ -45,6 +45,7 @@ def test_conv_forward_matches_oracle(dims):
     pk.conv3d_fwd(X, Wt, bias, Y, dims, relu=True)
     Yf = torch.zeros(dims, dtype=torch.float32, device=DEV)
     pk.conv3d_fwd(X, Wt, bias, Yf, dims, relu=False, out_f32=True)
+    pk.conv3d_check()
     torch.cuda.synchronize()
     # FP32 output: only the accumulation order differs from the FP64 oracle
     assert rel_l2(host(Yf), ref[..., 0]) <= 1e-6
@@ -70,6 +71,7 @@ def test_conv_backward_data_and_weights_match_oracle(dims):
     dW = torch.zeros((27, 16, 16), dtype=torch.float32, device=DEV)
     db = torch.zeros(16, dtype=torch.float32, device=DEV)
     pk.conv3d_wgrad(A, G, scratch, dW, db, dims)
+    pk.conv3d_check()
     torch.cuda.synchronize()
     ref_dx = C.bf16(C.conv3d_transpose(g, w) * (a > 0))
     dx = host(dX)
@@ -132,6 +134,7 @@ def test_network_loss_and_gradients_match_oracle():
     net.forward()
     pk.warmstart_loss(n, net.out, xt, xm1, xm2, net.scales, net.grads[-1], net.loss, net.scratch)
     net.backward()
+    pk.conv3d_check()
     torch.cuda.synchronize()
     params = [(host(w), host(bb)) for w, bb in zip(net.W16, net.b32)]
     x16 = host(net.acts[0])
