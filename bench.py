@@ -51,8 +51,9 @@ def parse():
     ap.add_argument("--k", type=int, default=K3D, help="3D grid side of the timed workload")
     ap.add_argument("--no-sweep", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
-    ap.add_argument("--mode", default="bench", choices=["bench", "kernels"],
-                    help="kernels: run only --iters fixed pipelined-CG iterations (profiler driver)")
+    ap.add_argument("--mode", default="bench", choices=["bench", "kernels", "conv"],
+                    help="kernels: run only --iters fixed pipelined-CG iterations (profiler driver); "
+                         "conv: time the BF16 conv kernels on one 64^3 layer")
     ap.add_argument("--iters", type=int, default=30)
     ap.add_argument("--variant", default="pipelined")
     ap.add_argument("--solver", default="cg", choices=["cg", "bicgstab", "gmres"],
@@ -567,6 +568,13 @@ def main():
     args = parse()
     if args.mode == "kernels":
         return run_kernels(args)
+    if args.mode == "conv":
+        import torch
+        from paper_1410_4054_gb300 import pk
+
+        print(json.dumps({"mode": "conv", **conv_throughput(pk, torch, "cuda", (64, 64, 64))}))
+        pk.conv3d_check()
+        return 0
     if args.impl == "reference":
         return run_reference(args)
     return run_ours(args)
