@@ -429,6 +429,10 @@ def bench_forms(pk, torch, dev, args):
     batched: 512 shifted 2D Laplacians on rectangles with sides log-uniform in [32, 256], tol
     1e-10, one persistent launch (FP64 and mixed precision) vs 512 sequential plain solves.
     mixed: the 160^3 Laplacian to 1e-8, mixed precision vs FP64, error of the mixed solution.
+    nonsymmetric_sweep: BiCGStab and GMRES(30) to 1e-8, pipelined vs classical, on the
+    convection-diffusion matrices 32^3, 64^3, 128^3 and the power-law matrices n = 1e4, 1e5, 1e6.
+    fused_spmv_dot: q = A p with <p, q> fused into the SpMV (one launch) against SpMV then an
+    inner-product kernel (Sec. 2.2), random matrices with 4 and 28 nonzeros per row.
     learned_warm_start: the transient heat sequence on 64^3 (300 implicit steps, CG to 1e-8),
     the network trained on steps 2-150 and evaluated on 151-300 against the x_{t-1} warm start
     (and the linear extrapolation alone), plus the BF16 convolution kernels' throughput.
@@ -515,6 +519,9 @@ def bench_forms(pk, torch, dev, args):
                     "inner_bytes_per_iter": 8 * a.nnz + 40 * a.n}
     A.close()
 
+    out["nonsymmetric_sweep"] = nonsymmetric_sweep(pk, torch, dev)
+    out["fused_spmv_dot"] = fused_spmv_dot(pk, torch, dev)
+
     from paper_1410_4054_gb300 import warmstart as WS
 
     res = WS.run_transient(k=64, steps=300, train_last=150, epochs=30)
@@ -523,6 +530,68 @@ def bench_forms(pk, torch, dev, args):
     lw["iteration_gain_vs_plain_warm_start"] = res["baseline_mean_iters"] - res["learned_mean_iters"]
     lw["conv"] = conv_throughput(pk, torch, dev, (64, 64, 64))
     out["learned_warm_start"] = lw
+    return out
+
+
+def nonsymmetric_sweep(pk, torch, dev):
+    """BiCGStab and GMRES(30) solve times (best of two after a warm-up) on the paper's
+    nonsymmetric workload shapes."""
+    rows = []
+    mats = [("convdiff3d", k, lambda k=k: W.convdiff_3d(k)) for k in (32, 64, 128)] + \
+           [("powerlaw", n, lambda n=n: W.power_law(n, seed=0)) for n in (10_000, 100_000, 1_000_000)]
+    for kind, size, make in mats:
+        a = make()
+        _, b, _ = W.manufactured(a, seed=0)
+        A = pk.CSRMatrix.from_workload(a)
+        bd = torch.from_numpy(b).to(dev)
+        x = torch.zeros(a.n, dtype=torch.float64, device=dev)
+        row = {"matrix": f"{kind}_{size}", "n": a.n, "nnz": a.nnz}
+        for solver, fn in (("bicgstab", pk.bicgstab_solve), ("gmres", pk.gmres_solve)):
+            for variant in ("pipelined", "classical"):
+                kw = dict(tol=1e-8, maxit=20_000, variant=variant)
+                if solver == "gmres":
+                    kw["restart"] = 30
+                fn(A, bd, x.zero_(), **kw)
+                inf = _best(lambda: fn(A, bd, x.zero_(), **kw))
+                row[f"{solver}_{variant}_ms"] = inf["solve_ms"]
+                row[f"{solver}_{variant}_iters"] = inf["iters"]
+                row[f"{solver}_{variant}_status"] = inf["status_name"]
+            row[f"{solver}_speedup"] = row[f"{solver}_classical_ms"] / row[f"{solver}_pipelined_ms"]
+        rows.append(row)
+        A.close()
+    return rows
+
+
+def fused_spmv_dot(pk, torch, dev, reps=20):
+    """Sec. 2.2 experiment: fused q = A p, <p, q> (one kernel) against the unfused pair, CUDA
+    events over `reps` calls after a warm-up.  Bytes per call: 12 nnz + 4 (n + 1) + 16 n."""
+    out = []
+    for per_row, sizes in ((4, (1_000, 10_000, 100_000, 1_000_000, 10_000_000)),
+                           (28, (1_000, 10_000, 100_000, 1_000_000))):
+        for n in sizes:
+            a = W.random_uniform(n, per_row, seed=1)
+            A = pk.CSRMatrix.from_workload(a)
+            p = torch.from_numpy(np.random.default_rng(2).uniform(-1, 1, a.n)).to(dev)
+            q = torch.empty_like(p)
+            res = torch.zeros(1, dtype=torch.float64, device=dev)
+            row = {"per_row": per_row, "n": n, "nnz": a.nnz}
+            for fused in (True, False):
+                for _ in range(3):
+                    pk.spmv_dot(A, p, q, res, fused=fused)
+                st, en = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                torch.cuda.synchronize()
+                st.record()
+                for _ in range(reps):
+                    pk.spmv_dot(A, p, q, res, fused=fused)
+                en.record()
+                torch.cuda.synchronize()
+                us = 1e3 * st.elapsed_time(en) / reps
+                key = "fused" if fused else "unfused"
+                row[f"{key}_us"] = us
+                row[f"{key}_gbs"] = (12 * a.nnz + 4 * (a.n + 1) + 16 * a.n) / (us * 1e-6) / 1e9
+            row["speedup"] = row["unfused_us"] / row["fused_us"]
+            out.append(row)
+            A.close()
     return out
 
 

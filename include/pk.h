@@ -142,6 +142,9 @@ typedef struct {
   int32_t block;             /* threads per block */
   int32_t kernel;            /* SpMV engine: 0 thread-per-row loads, 2 warp-specialised bulk-copy tiles */
   int32_t values_fp32_exact; /* 1 if every value is exactly representable in float32 */
+  /* bulk-copy tiles by row schedule: every row one thread (all rows <= 32 nonzeros), or
+   * short rows one thread and longer rows a whole warp each */
+  int32_t tiles_thread, tiles_long;
 } pk_csr_stats;
 
 /*

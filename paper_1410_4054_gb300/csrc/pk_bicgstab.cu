@@ -27,17 +27,10 @@ __global__ void __launch_bounds__(kTileThreads, 2) k_bi1_tma(CsrTiles T, const d
   extern __shared__ __align__(128) unsigned char smem[];
   count_pass(st);
   double v[1] = {0.0};
-  const bool live = csr_tiles(T, smem, st, [&]() { return !state_done(st); },
-                              [&](int ra, int ja0, int ja1, int rb, int jb0, int jb1,
-                                  const double* sva, const int32_t* sci) {
-    double sa, sb;
-    smem_row2(sva, sci, ja0, ja1, jb0, jb1, p, sa, sb);
-    ap[ra] = sa;
-    v[0] = fma(sa, __ldg(r0s + ra), v[0]);
-    if (rb >= 0) {
-      ap[rb] = sb;
-      v[0] = fma(sb, __ldg(r0s + rb), v[0]);
-    }
+  const bool live = csr_tiles(T, smem, st, [&]() { return !state_done(st); }, p,
+                              [&](int row, double y) {
+    ap[row] = y;
+    v[0] = fma(y, __ldg(r0s + row), v[0]);
   });
   griddep_trigger();
   if (!__syncthreads_or(threadIdx.x < kConsumers && live)) {
@@ -111,21 +104,12 @@ __global__ void __launch_bounds__(kTileThreads, 2) k_bi3_tma(CsrTiles T, const d
                                                              double* partials, DevState* st) {
   extern __shared__ __align__(128) unsigned char smem[];
   double v[3] = {0.0, 0.0, 0.0};
-  const bool live = csr_tiles(T, smem, st, [&]() { return !state_done(st) && !__ldcg(&st->early); },
-                              [&](int ra, int ja0, int ja1, int rb, int jb0, int jb1,
-                                  const double* sva, const int32_t* sci) {
-    double sa, sb;
-    smem_row2(sva, sci, ja0, ja1, jb0, jb1, s, sa, sb);
-    as[ra] = sa;
-    v[0] = fma(sa, __ldg(s + ra), v[0]);
-    v[1] = fma(sa, sa, v[1]);
-    v[2] = fma(sa, __ldg(r0s + ra), v[2]);
-    if (rb >= 0) {
-      as[rb] = sb;
-      v[0] = fma(sb, __ldg(s + rb), v[0]);
-      v[1] = fma(sb, sb, v[1]);
-      v[2] = fma(sb, __ldg(r0s + rb), v[2]);
-    }
+  const bool live = csr_tiles(T, smem, st, [&]() { return !state_done(st) && !__ldcg(&st->early); }, s,
+                              [&](int row, double y) {
+    as[row] = y;
+    v[0] = fma(y, __ldg(s + row), v[0]);
+    v[1] = fma(y, y, v[1]);
+    v[2] = fma(y, __ldg(r0s + row), v[2]);
   });
   griddep_trigger();
   if (!__syncthreads_or(threadIdx.x < kConsumers && live)) return;

@@ -275,19 +275,11 @@ __global__ void __launch_bounds__(kTileThreads, 2) k_cg_spmv_dots_tma(CsrTiles T
                                                                       double* partials, DevState* st) {
   extern __shared__ __align__(128) unsigned char smem[];
   double v[2] = {0.0, 0.0};
-  const bool live = csr_tiles(T, smem, st, [&]() { return !state_done(st); },
-                              [&](int ra, int ja0, int ja1, int rb, int jb0, int jb1,
-                                  const double* sva, const int32_t* sci) {
-    double sa, sb;
-    smem_row2(sva, sci, ja0, ja1, jb0, jb1, p, sa, sb);
-    ap[ra] = sa;
-    v[0] = fma(sa, sa, v[0]);
-    v[1] = fma(__ldg(p + ra), sa, v[1]);
-    if (rb >= 0) {
-      ap[rb] = sb;
-      v[0] = fma(sb, sb, v[0]);
-      v[1] = fma(__ldg(p + rb), sb, v[1]);
-    }
+  const bool live = csr_tiles(T, smem, st, [&]() { return !state_done(st); }, p,
+                              [&](int row, double y) {
+    ap[row] = y;
+    v[0] = fma(y, y, v[0]);
+    v[1] = fma(__ldg(p + row), y, v[1]);
   });
   griddep_trigger();
   if (!__syncthreads_or(threadIdx.x < kConsumers && live)) return;

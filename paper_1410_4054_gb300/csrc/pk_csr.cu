@@ -422,6 +422,15 @@ pk_status pk_csr_create(int64_t n, int64_t nnz, const int32_t* row_ptr, const in
     tile_row.push_back((int32_t)n);
     A->ntiles = (int)tile_row.size() - 1;
   }
+  // per tile: 1 if every row has at most 32 nonzeros (one thread per row throughout), 32 if
+  // the tile holds longer rows (those go to whole warps); see csr_tiles
+  std::vector<int8_t> tile_grp(A->tma_ok ? A->ntiles : 0);
+  for (int t = 0; t < (int)tile_grp.size(); ++t) {
+    int64_t lmax = 0;
+    for (int64_t r = tile_row[t]; r < tile_row[t + 1]; ++r) lmax = std::max<int64_t>(lmax, rp[r + 1] - rp[r]);
+    tile_grp[t] = lmax <= 32 ? 1 : 32;
+    (tile_grp[t] == 1 ? A->stats.tiles_thread : A->stats.tiles_long) += 1;
+  }
   A->grid_stream = (int)std::max<int64_t>(1, std::min<int64_t>((int64_t)sms * 2, (n + 511) / 512));
 
   auto fail = [&](pk_status e) { pk_csr_destroy(A); return e; };
@@ -447,6 +456,10 @@ pk_status pk_csr_create(int64_t n, int64_t nnz, const int32_t* row_ptr, const in
     if ((e = cudaMalloc(&A->blk_tile, sizeof(int32_t) * blk_tile.size())) != cudaSuccess) return fail(cuda_fail(e, "cudaMalloc(tiles)"));
     if ((e = cudaMemcpyAsync(A->tile_row, tile_row.data(), sizeof(int32_t) * tile_row.size(), cudaMemcpyHostToDevice, s)) != cudaSuccess) return fail(cuda_fail(e, "copy tiles"));
     if ((e = cudaMemcpyAsync(A->blk_tile, blk_tile.data(), sizeof(int32_t) * blk_tile.size(), cudaMemcpyHostToDevice, s)) != cudaSuccess) return fail(cuda_fail(e, "copy tiles"));
+    if ((e = cudaMalloc(&A->tile_grp, std::max<size_t>(1, tile_grp.size()))) != cudaSuccess) return fail(cuda_fail(e, "cudaMalloc(tiles)"));
+    if (!tile_grp.empty() &&
+        (e = cudaMemcpyAsync(A->tile_grp, tile_grp.data(), tile_grp.size(), cudaMemcpyHostToDevice, s)) != cudaSuccess)
+      return fail(cuda_fail(e, "copy tiles"));
   }
   if ((e = cudaStreamSynchronize(s)) != cudaSuccess) return fail(cuda_fail(e, "sync"));
 
@@ -487,6 +500,7 @@ pk_status pk_csr_destroy(pk_csr* A) {
   if (A->rowblk) cudaFree(A->rowblk);
   if (A->tile_row) cudaFree(A->tile_row);
   if (A->blk_tile) cudaFree(A->blk_tile);
+  if (A->tile_grp) cudaFree(A->tile_grp);
   if (A->cap_stream) cudaStreamDestroy(A->cap_stream);
   delete A;
   return PK_OK;

@@ -63,21 +63,12 @@ __global__ void __launch_bounds__(kTileThreads, 2) k_gm_start(CsrTiles T, GmArgs
   }
   double* r = g.V;
   double v[2] = {0.0, 0.0};
-  const bool live = csr_tiles(T, smem, st, [&]() { return !state_done(st); },
-                              [&](int ra, int ja0, int ja1, int rb, int jb0, int jb1,
-                                  const double* sva, const int32_t* sci) {
-    double sa, sb;
-    smem_row2(sva, sci, ja0, ja1, jb0, jb1, g.x, sa, sb);
-    const double ba = __ldg(g.b + ra), qa = ba - sa;
-    r[ra] = qa;
-    v[0] = fma(qa, qa, v[0]);
-    v[1] = fma(ba, ba, v[1]);
-    if (rb >= 0) {
-      const double bb = __ldg(g.b + rb), qb = bb - sb;
-      r[rb] = qb;
-      v[0] = fma(qb, qb, v[0]);
-      v[1] = fma(bb, bb, v[1]);
-    }
+  const bool live = csr_tiles(T, smem, st, [&]() { return !state_done(st); }, (const double*)g.x,
+                              [&](int row, double y) {
+    const double bi = __ldg(g.b + row), q = bi - y;
+    r[row] = q;
+    v[0] = fma(q, q, v[0]);
+    v[1] = fma(bi, bi, v[1]);
   });
   if (!__syncthreads_or(threadIdx.x < kConsumers && live)) {
     if (blockIdx.x == 0 && threadIdx.x == 0 && st->use_cond) {
@@ -152,17 +143,10 @@ __global__ void __launch_bounds__(kTileThreads, 2) k_gm1(CsrTiles T, GmArgs g) {
   const double* vp = g.V + (size_t)(i - 1) * g.ld;
   double* vi = g.V + (size_t)i * g.ld;
   double v[1] = {0.0};
-  const bool live = csr_tiles(T, smem, st, [&]() { return gm_step_live(st); },
-                              [&](int ra, int ja0, int ja1, int rb, int jb0, int jb1,
-                                  const double* sva, const int32_t* sci) {
-    double sa, sb;
-    smem_row2(sva, sci, ja0, ja1, jb0, jb1, vp, sa, sb);
-    vi[ra] = sa;
-    v[0] = fma(__ldg(vp + ra), sa, v[0]);
-    if (rb >= 0) {
-      vi[rb] = sb;
-      v[0] = fma(__ldg(vp + rb), sb, v[0]);
-    }
+  const bool live = csr_tiles(T, smem, st, [&]() { return gm_step_live(st); }, vp,
+                              [&](int row, double y) {
+    vi[row] = y;
+    v[0] = fma(__ldg(vp + row), y, v[0]);
   });
   if (!__syncthreads_or(threadIdx.x < kConsumers && live)) return;
   tile_block_partials<1>(v, g.partials);

@@ -192,6 +192,7 @@ struct pk_csr {
   int grid_tma = 0;
   int32_t* tile_row = nullptr;  // ntiles + 1
   int32_t* blk_tile = nullptr;  // grid_tma + 1
+  int8_t* tile_grp = nullptr;   // ntiles: lanes per row in the tile (1, 8 or 32)
   int ntiles = 0;
   int grid_stream = 0;          // grid of the streaming (vector-only) tile kernels
   int partial_cap = 0;         // blocks the partials buffer can hold

@@ -232,19 +232,11 @@ __global__ void __launch_bounds__(kTileThreads, 2) k_mx_spmv_tma(CsrTilesT<float
   extern __shared__ __align__(128) unsigned char smem[];
   DevState* st = a.st;
   FF aa{0.0f, 0.0f}, pa{0.0f, 0.0f};
-  const bool live = csr_tiles(T, smem, st, [&]() { return mx_inner_live(st); },
-                              [&](int ra, int ja0, int ja1, int rb, int jb0, int jb1,
-                                  const float* sva, const int32_t* sci) {
-    const float sa = smem_row_f32(sva, sci, ja0, ja1, a.p);
-    a.ap[ra] = sa;
-    ff_add_prod(aa, sa, sa);
-    ff_add_prod(pa, __ldg(a.p + ra), sa);
-    if (rb >= 0) {
-      const float sb = smem_row_f32(sva, sci, jb0, jb1, a.p);
-      a.ap[rb] = sb;
-      ff_add_prod(aa, sb, sb);
-      ff_add_prod(pa, __ldg(a.p + rb), sb);
-    }
+  const bool live = csr_tiles(T, smem, st, [&]() { return mx_inner_live(st); }, (const float*)a.p,
+                              [&](int row, float y) {
+    a.ap[row] = y;
+    ff_add_prod(aa, y, y);
+    ff_add_prod(pa, __ldg(a.p + row), y);
   });
   griddep_trigger();
   if (!__syncthreads_or(threadIdx.x < kConsumers && live)) return;

@@ -22,6 +22,9 @@ __device__ __forceinline__ uint32_t smem_addr(const void* p) {
   return (uint32_t)__cvta_generic_to_shared(p);
 }
 
+__device__ __forceinline__ double fma_t(double a, double b, double c) { return fma(a, b, c); }
+__device__ __forceinline__ float fma_t(float a, float b, float c) { return fmaf(a, b, c); }
+
 __device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count) {
   asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_addr(bar)), "r"(count) : "memory");
 }
@@ -284,7 +287,7 @@ constexpr int kVaWords = kTileNnz + 2;        // doubles
 constexpr int kCiWords = kTileNnz + 8;        // ints (window rounded out to 16 bytes on both ends)
 constexpr int kStageBytes = ((kRpWords * 4 + 15) & ~15) + kVaWords * 8 + ((kCiWords * 4 + 15) & ~15);
 
-constexpr int csr_smem_bytes() { return kCsrStages * kStageBytes + 2 * kCsrStages * 8 + kCsrStages * 8; }
+constexpr int csr_smem_bytes() { return kCsrStages * kStageBytes + 2 * kCsrStages * 8 + kCsrStages * 16; }
 
 template <class VT>
 struct CsrTilesT {
@@ -293,20 +296,33 @@ struct CsrTilesT {
   const VT* va;             // values: FP64, or the FP32 copy for the mixed-precision inner loop
   const int32_t* tile_row;  // row start of every tile (global tile list), plus n at the end
   const int32_t* blk_tile;  // tiles of block b: [blk_tile[b], blk_tile[b+1])
+  const int8_t* tile_grp;   // lanes per row of every tile: 1, 8 or 32
 };
 using CsrTiles = CsrTilesT<double>;
 
-// Runs the CSR pipeline.  Consumer thread t handles rows R0 + t and R0 + t + 256 of every
-// tile together: `rows_fn(ra, ja0, ja1, rb, jb0, jb1, sva, sci)` receives both rows (rb = -1
-// if the tile has no second row for this thread) and their nonzero windows in shared memory
-// (sva/sci are offset so that entry j is sva[j], sci[j]).
-template <class VT, class Setup, class RowFn>
+// Two row products from a shared-memory window (defined below): FP64 and FP32.
+__device__ __forceinline__ void row_pair(const double* sva, const int32_t* sci, int ja, int ja1, int jb,
+                                         int jb1, const double* __restrict__ x, double& sa, double& sb);
+__device__ __forceinline__ void row_pair(const float* sva, const int32_t* sci, int ja, int ja1, int jb,
+                                         int jb1, const float* __restrict__ x, float& sa, float& sb);
+
+// Runs the CSR pipeline and the row products y_row = sum_j A[row][j] x[col j]; every finished
+// row goes to `row_done(row, y_row)`, called by the one consumer thread that owns the row.
+// Consumer thread t computes rows R0 + t and R0 + t + 256 of every tile itself (summed left
+// to right, the order of a plain CSR loop).  In tiles that hold rows longer than kLongRow
+// nonzeros (T.tile_grp != 1, set at pk_csr_create) a thread skips its long rows, and each
+// warp then takes its lanes' long rows one at a time with all 32 lanes (lane l sums entries
+// l, l + 32, ... left to right, then a butterfly), so that no thread walks a long row alone;
+// no synchronisation beyond the warp is involved.
+constexpr int kLongRow = 32;
+
+template <class VT, class Setup, class RowDone>
 __device__ __forceinline__ bool csr_tiles(const CsrTilesT<VT>& T, unsigned char* smem, DevState* st,
-                                          Setup&& setup, RowFn&& row_fn) {
+                                          Setup&& setup, const VT* __restrict__ x, RowDone&& row_done) {
   constexpr int kVaUnit = 16 / (int)sizeof(VT);  // values per 16-byte copy unit
   uint64_t* full = reinterpret_cast<uint64_t*>(smem + kCsrStages * kStageBytes);
   uint64_t* empty = full + kCsrStages;
-  int2* meta = reinterpret_cast<int2*>(empty + kCsrStages);  // tile rows [R0, R1) per stage
+  int4* meta = reinterpret_cast<int4*>(empty + kCsrStages);  // tile rows [R0, R1), lanes per row
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   if (threadIdx.x == 0) {
     for (int s = 0; s < kCsrStages; ++s) {
@@ -337,17 +353,19 @@ __device__ __forceinline__ bool csr_tiles(const CsrTilesT<VT>& T, unsigned char*
     const uint64_t pol = l2_evict_first();
     for (int base = 0; base < ntiles && ok && live; base += 32) {
       const int tt = t0 + base + lane;
-      int R0 = 0, R1 = 0, z0 = 0, z1 = 0;
+      int R0 = 0, R1 = 0, z0 = 0, z1 = 0, gr = 1;
       if (tt < t1) {
         R0 = __ldg(T.tile_row + tt);
         R1 = __ldg(T.tile_row + tt + 1);
         z0 = __ldg(T.rp + R0);
         z1 = __ldg(T.rp + R1);
+        gr = T.tile_grp ? (int)__ldg(T.tile_grp + tt) : 1;
       }
       const int cnt = min(32, ntiles - base);
       for (int q = 0; q < cnt; ++q) {
         const int a0 = __shfl_sync(0xffffffffu, R0, q), a1 = __shfl_sync(0xffffffffu, R1, q);
         const int b0 = __shfl_sync(0xffffffffu, z0, q), b1 = __shfl_sync(0xffffffffu, z1, q);
+        const int g0 = __shfl_sync(0xffffffffu, gr, q);
         if (lane == 0) {
           const int t = base + q;
           const int s = t % kCsrStages;
@@ -359,7 +377,7 @@ __device__ __forceinline__ bool csr_tiles(const CsrTilesT<VT>& T, unsigned char*
             const int cs = b0 & ~3, ce = (b1 + 3) & ~3;        // columns b0..b1-1
             const uint32_t nrp = (uint32_t)(re - rs) * 4, nva = (uint32_t)(ve - vs) * (uint32_t)sizeof(VT),
                            nci = (uint32_t)(ce - cs) * 4;
-            meta[s] = make_int2(a0, a1);  // published by the arrive below (release)
+            meta[s] = make_int4(a0, a1, g0, 0);  // published by the arrive below (release)
             mbar_expect_tx(&full[s], nrp + nva + nci);
             bulk_load_hint(stage_rp(s), T.rp + rs, nrp, &full[s], pol);
             if (nva) bulk_load_hint(stage_va(s), T.va + vs, nva, &full[s], pol);
@@ -394,17 +412,49 @@ __device__ __forceinline__ bool csr_tiles(const CsrTilesT<VT>& T, unsigned char*
       if (lane == 0) mbar_arrive(&empty[s]);
       continue;
     }
-    const int2 m = meta[s];
-    const int R0 = m.x, R1 = m.y;
+    const int4 m = meta[s];
+    const int R0 = m.x, R1 = m.y, G = m.z;
+    const int32_t* srp = stage_rp(s) - (R0 & ~3);
+    const int z0 = srp[R0];
+    const VT* sva = stage_va(s) - (z0 & ~(kVaUnit - 1));  // windows start at the first row's nonzeros
+    const int32_t* sci = stage_ci(s) - (z0 & ~3);
     const int ra = R0 + (int)threadIdx.x;
-    if (ra < R1) {
-      const int32_t* srp = stage_rp(s) - (R0 & ~3);
-      const int z0 = srp[R0];
-      const int vs = z0 & ~(kVaUnit - 1);  // the window of this tile starts at the first row's nonzeros
-      const int cs = z0 & ~3;
-      const int rb = ra + kConsumers < R1 ? ra + kConsumers : -1;
-      const int jb0 = rb >= 0 ? srp[rb] : 0, jb1 = rb >= 0 ? srp[rb + 1] : 0;
-      row_fn(ra, srp[ra], srp[ra + 1], rb, jb0, jb1, stage_va(s) - vs, stage_ci(s) - cs);
+    if (G == 1) {
+      if (ra < R1) {
+        const int rb = ra + kConsumers < R1 ? ra + kConsumers : -1;
+        VT sa, sb;
+        row_pair(sva, sci, srp[ra], srp[ra + 1], rb >= 0 ? srp[rb] : 0, rb >= 0 ? srp[rb + 1] : 0, x, sa, sb);
+        row_done(ra, sa);
+        if (rb >= 0) row_done(rb, sb);
+      }
+    } else {
+      // every lane takes part (the ballots below need the whole warp)
+      const bool has_a = ra < R1;
+      const int rb = has_a && ra + kConsumers < R1 ? ra + kConsumers : -1;
+      int ja0 = has_a ? srp[ra] : 0, ja1 = has_a ? srp[ra + 1] : 0;
+      int jb0 = rb >= 0 ? srp[rb] : 0, jb1 = rb >= 0 ? srp[rb + 1] : 0;
+      const bool la = ja1 - ja0 > kLongRow, lb = jb1 - jb0 > kLongRow;
+      if (has_a) {
+        VT sa, sb;
+        row_pair(sva, sci, ja0, la ? ja0 : ja1, jb0, lb ? jb0 : jb1, x, sa, sb);
+        if (!la) row_done(ra, sa);
+        if (rb >= 0 && !lb) row_done(rb, sb);
+      }
+#pragma unroll
+      for (int h = 0; h < 2; ++h) {
+        unsigned pending = __ballot_sync(0xffffffffu, h == 0 ? la : lb);
+        while (pending) {
+          const int src = __ffs(pending) - 1;
+          pending &= pending - 1;
+          const int r = __shfl_sync(0xffffffffu, h == 0 ? ra : rb, src);
+          const int j0 = srp[r], j1 = srp[r + 1];
+          VT acc = (VT)0;
+          for (int j = j0 + lane; j < j1; j += 32) acc = fma_t(sva[j], __ldg(x + sci[j]), acc);
+#pragma unroll
+          for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+          if (lane == src) row_done(r, acc);
+        }
+      }
     }
     __syncwarp();
     if (lane == 0) mbar_arrive(&empty[s]);
@@ -546,6 +596,17 @@ __device__ __forceinline__ float smem_row_f32(const float* sva, const int32_t* s
   return s;
 }
 
+__device__ __forceinline__ void row_pair(const double* sva, const int32_t* sci, int ja, int ja1, int jb,
+                                         int jb1, const double* __restrict__ x, double& sa, double& sb) {
+  smem_row2(sva, sci, ja, ja1, jb, jb1, x, sa, sb);
+}
+
+__device__ __forceinline__ void row_pair(const float* sva, const int32_t* sci, int ja, int ja1, int jb,
+                                         int jb1, const float* __restrict__ x, float& sa, float& sb) {
+  sa = smem_row_f32(sva, sci, ja, ja1, x);
+  sb = jb1 > jb ? smem_row_f32(sva, sci, jb, jb1, x) : 0.0f;
+}
+
 inline CsrTilesT<float> csr_tiles32_of(const pk_csr* A) {
   CsrTilesT<float> t;
   t.rp = A->rp;
@@ -553,6 +614,7 @@ inline CsrTilesT<float> csr_tiles32_of(const pk_csr* A) {
   t.va = A->va32;
   t.tile_row = A->tile_row;
   t.blk_tile = A->blk_tile;
+  t.tile_grp = A->tile_grp;
   return t;
 }
 
@@ -563,6 +625,7 @@ inline CsrTiles csr_tiles_of(const pk_csr* A) {
   t.va = A->va;
   t.tile_row = A->tile_row;
   t.blk_tile = A->blk_tile;
+  t.tile_grp = A->tile_grp;
   return t;
 }
 

@@ -48,7 +48,8 @@ class Info(C.Structure):
 class Stats(C.Structure):
     _fields_ = [("n", C.c_int64), ("nnz", C.c_int64), ("row_min", C.c_int32),
                 ("row_max", C.c_int32), ("row_mean", C.c_double), ("grid", C.c_int32),
-                ("block", C.c_int32), ("kernel", C.c_int32), ("values_fp32_exact", C.c_int32)]
+                ("block", C.c_int32), ("kernel", C.c_int32), ("values_fp32_exact", C.c_int32),
+                ("tiles_thread", C.c_int32), ("tiles_long", C.c_int32)]
 
 
 EXPORTS = {
