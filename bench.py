@@ -58,6 +58,9 @@ def parse():
     ap.add_argument("--variant", default="pipelined")
     ap.add_argument("--solver", default="cg", choices=["cg", "bicgstab", "gmres"],
                     help="--mode kernels: cg on the Laplacian, bicgstab / gmres on convection-diffusion")
+    ap.add_argument("--matrix", default="stencil", choices=["stencil", "powerlaw"],
+                    help="--mode kernels: the stencil of --k, or a power-law matrix with --n rows")
+    ap.add_argument("--n", type=int, default=1_000_000)
     ap.add_argument("--no-forms", action="store_true",
                     help="skip the BiCGStab / GMRES / batched / mixed-precision lines")
     return ap.parse_args()
@@ -69,7 +72,10 @@ def run_kernels(args):
     import torch
     from paper_1410_4054_gb300 import pk
 
-    a = W.laplace_3d(args.k) if args.solver == "cg" else W.convdiff_3d(args.k)
+    if args.matrix == "powerlaw":
+        a = W.power_law(args.n, seed=0)
+    else:
+        a = W.laplace_3d(args.k) if args.solver == "cg" else W.convdiff_3d(args.k)
     _, b, _ = W.manufactured(a, seed=0)
     A = pk.CSRMatrix.from_workload(a)
     bd = torch.from_numpy(b).cuda()

@@ -430,6 +430,8 @@ pk_status bicgstab_solve(pk_csr* A, const double* b, double* x, const pk_opts* o
       (e = work_vec(A, 3, &sv)) || (e = work_vec(A, 4, &as)) || (e = work_vec(A, 5, &r0s)))
     return e;
   const bool tma = A->tma_ok && !(o->flags & PK_FLAG_NO_TMA) && o->variant == PK_VARIANT_PIPELINED;
+  // the classical form's SpMV runs on the same tile engine (only the fusion differs)
+  const bool tma_spmv = A->tma_ok && !(o->flags & PK_FLAG_NO_TMA);
   double* xd = v.x_dev;
   double* x_copy_back = nullptr;
   if (tma && (((uintptr_t)xd & 15) || (A->n & 1))) {
@@ -491,11 +493,17 @@ pk_status bicgstab_solve(pk_csr* A, const double* b, double* x, const pk_opts* o
     L.body = [=](cudaStream_t cs, Timer* t) {
       auto k = [&](int slot) { if (t) t->begin(slot); };
       auto kend = [&]() { if (t) t->end(); };
-      k(PK_SLOT_SPMV); k_bc_spmv<<<G, kBlock, 0, cs>>>(ra, p, ap, 1); kend();
+      k(PK_SLOT_SPMV);
+      if (tma_spmv) launch_spmv_tma(A, p, ap, 1, 1, cs);
+      else k_bc_spmv<<<G, kBlock, 0, cs>>>(ra, p, ap, 1);
+      kend();
       k(PK_SLOT_BLAS1); k_bc_alpha<<<G, kBlock, 0, cs>>>(ra, ap, r0s); kend();
       k(PK_SLOT_BLAS1); k_bc_s<<<G, kBlock, 0, cs>>>(ra, r, ap, sv); kend();
       k(PK_SLOT_BLAS1); k_bc_ss<<<G, kBlock, 0, cs>>>(ra, sv); kend();
-      k(PK_SLOT_SPMV); k_bc_spmv<<<G, kBlock, 0, cs>>>(ra, sv, as, 0); kend();
+      k(PK_SLOT_SPMV);
+      if (tma_spmv) launch_spmv_tma(A, sv, as, 0, 1, cs);
+      else k_bc_spmv<<<G, kBlock, 0, cs>>>(ra, sv, as, 0);
+      kend();
       k(PK_SLOT_BLAS1); k_bc_omega<<<G, kBlock, 0, cs>>>(ra, as, sv); kend();
       k(PK_SLOT_BLAS1); k_bc_x<<<G, kBlock, 0, cs>>>(ra, xd, p, sv); kend();
       k(PK_SLOT_BLAS1); k_bc_r<<<G, kBlock, 0, cs>>>(ra, r, sv, as); kend();

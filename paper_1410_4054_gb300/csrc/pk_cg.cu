@@ -295,6 +295,19 @@ __global__ void __launch_bounds__(kTileThreads, 2) k_cg_spmv_dots_tma(CsrTiles T
   }
 }
 
+// Plain y = A x on the CSR tile engine, no inner products: the SpMV of the unfused forms
+// (classical and split CG, classical BiCGStab), so that fused and unfused solvers differ only
+// in the fusion.  `first` counts a loop pass; `skip_early`: BiCGStab's early-exit flag also
+// ends the solve.
+__global__ void __launch_bounds__(kTileThreads, 2) k_spmv_tma(CsrTiles T, const double* __restrict__ x,
+                                                              double* __restrict__ y, DevState* st,
+                                                              int first, int skip_early) {
+  extern __shared__ __align__(128) unsigned char smem[];
+  if (first) count_pass(st);
+  csr_tiles(T, smem, st, [&]() { return !state_done(st) && !(skip_early && __ldcg(&st->early)); }, x,
+            [&](int row, double v) { y[row] = v; });
+}
+
 static pk_status tma_setup() {
   static bool done = false;
   if (!done) {
@@ -302,6 +315,7 @@ static pk_status tma_setup() {
                                  stream_smem_bytes<4>()));
     PK_CUDA(cudaFuncSetAttribute(k_cg_spmv_dots_tma, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                  csr_smem_bytes()));
+    PK_CUDA(cudaFuncSetAttribute(k_spmv_tma, cudaFuncAttributeMaxDynamicSharedMemorySize, csr_smem_bytes()));
     done = true;
   }
   return PK_OK;
@@ -521,7 +535,8 @@ pk_status cg_solve(pk_csr* A, const double* b, double* x, const pk_opts* o, pk_i
       if (t) t->begin(PK_SLOT_UPDATE);
       k_cg_update<<<Gu, kBlock, 0, cs>>>(ra, xd, r, p, ap);
       if (t) { t->end(); t->begin(PK_SLOT_SPMV); }
-      k_spmv_live<<<G, kBlock, 0, cs>>>(ra, p, ap, 0);
+      if (tma) k_spmv_tma<<<Gt, kTileThreads, csr_smem_bytes(), cs>>>(ct, p, ap, dst, 0, 0);
+      else k_spmv_live<<<G, kBlock, 0, cs>>>(ra, p, ap, 0);
       if (t) { t->end(); t->begin(PK_SLOT_BLAS1); }
       k_cg_dots<<<G, kBlock, 0, cs>>>(ra, p, ap);
       if (t) t->end();
@@ -531,7 +546,8 @@ pk_status cg_solve(pk_csr* A, const double* b, double* x, const pk_opts* o, pk_i
     L.body_kernels = 6;
     L.body = [=](cudaStream_t cs, Timer* t) {
       if (t) t->begin(PK_SLOT_SPMV);
-      k_spmv_live<<<G, kBlock, 0, cs>>>(ra, p, ap, 1);
+      if (tma) k_spmv_tma<<<Gt, kTileThreads, csr_smem_bytes(), cs>>>(ct, p, ap, dst, 1, 0);
+      else k_spmv_live<<<G, kBlock, 0, cs>>>(ra, p, ap, 1);
       if (t) { t->end(); t->begin(PK_SLOT_BLAS1); }
       k_cls_alpha<<<G, kBlock, 0, cs>>>(ra, p, ap);
       if (t) { t->end(); t->begin(PK_SLOT_BLAS1); }
@@ -559,6 +575,13 @@ pk_status cg_solve(pk_csr* A, const double* b, double* x, const pk_opts* o, pk_i
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);
   return (pk_status)info->status;
+}
+
+pk_status launch_spmv_tma(pk_csr* A, const double* x, double* y, int first, int skip_early, cudaStream_t s) {
+  pk_status e = tma_setup();
+  if (e) return e;
+  k_spmv_tma<<<A->grid_tma, kTileThreads, csr_smem_bytes(), s>>>(csr_tiles_of(A), x, y, A->st, first, skip_early);
+  return PK_OK;
 }
 
 void launch_residual_init(const pk_csr* A, const double* b, const double* x, double* r,

@@ -431,6 +431,31 @@ pk_status pk_csr_create(int64_t n, int64_t nnz, const int32_t* row_ptr, const in
     tile_grp[t] = lmax <= 32 ? 1 : 32;
     (tile_grp[t] == 1 ? A->stats.tiles_thread : A->stats.tiles_long) += 1;
   }
+  // row order of every irregular tile: rows sorted by length (longest first), dealt
+  // round-robin over the 8 consumer warps -- slot (warp w, lane l) takes sorted rows
+  // 8 l + w and 256 + 8 l + w -- so that each warp holds rows of similar length and the
+  // long rows spread over all warps; -1 marks an empty slot
+  std::vector<int16_t> tile_perm;
+  if (A->stats.tiles_long > 0) {
+    tile_perm.assign((size_t)A->ntiles * kTileRows, (int16_t)-1);
+    std::vector<int32_t> order;
+    for (int t = 0; t < A->ntiles; ++t) {
+      if (tile_grp[t] == 1) continue;
+      const int32_t R0 = tile_row[t], m = tile_row[t + 1] - R0;
+      order.resize(m);
+      for (int k = 0; k < m; ++k) order[k] = k;
+      std::stable_sort(order.begin(), order.end(), [&](int32_t a, int32_t b) {
+        return rp[R0 + a + 1] - rp[R0 + a] > rp[R0 + b + 1] - rp[R0 + b];
+      });
+      int16_t* P = tile_perm.data() + (size_t)t * kTileRows;
+      for (int tid = 0; tid < kTileRows / 2; ++tid) {
+        const int w = tid / 32, l = tid % 32;
+        const int k1 = 8 * l + w, k2 = kTileRows / 2 + 8 * l + w;
+        P[tid] = k1 < m ? (int16_t)order[k1] : (int16_t)-1;
+        P[kTileRows / 2 + tid] = k2 < m ? (int16_t)order[k2] : (int16_t)-1;
+      }
+    }
+  }
   A->grid_stream = (int)std::max<int64_t>(1, std::min<int64_t>((int64_t)sms * 2, (n + 511) / 512));
 
   auto fail = [&](pk_status e) { pk_csr_destroy(A); return e; };
@@ -457,6 +482,11 @@ pk_status pk_csr_create(int64_t n, int64_t nnz, const int32_t* row_ptr, const in
     if ((e = cudaMemcpyAsync(A->tile_row, tile_row.data(), sizeof(int32_t) * tile_row.size(), cudaMemcpyHostToDevice, s)) != cudaSuccess) return fail(cuda_fail(e, "copy tiles"));
     if ((e = cudaMemcpyAsync(A->blk_tile, blk_tile.data(), sizeof(int32_t) * blk_tile.size(), cudaMemcpyHostToDevice, s)) != cudaSuccess) return fail(cuda_fail(e, "copy tiles"));
     if ((e = cudaMalloc(&A->tile_grp, std::max<size_t>(1, tile_grp.size()))) != cudaSuccess) return fail(cuda_fail(e, "cudaMalloc(tiles)"));
+    if (!tile_perm.empty()) {
+      if ((e = cudaMalloc(&A->tile_perm, sizeof(int16_t) * tile_perm.size())) != cudaSuccess) return fail(cuda_fail(e, "cudaMalloc(tiles)"));
+      if ((e = cudaMemcpyAsync(A->tile_perm, tile_perm.data(), sizeof(int16_t) * tile_perm.size(), cudaMemcpyHostToDevice, s)) != cudaSuccess)
+        return fail(cuda_fail(e, "copy tiles"));
+    }
     if (!tile_grp.empty() &&
         (e = cudaMemcpyAsync(A->tile_grp, tile_grp.data(), tile_grp.size(), cudaMemcpyHostToDevice, s)) != cudaSuccess)
       return fail(cuda_fail(e, "copy tiles"));
@@ -501,6 +531,7 @@ pk_status pk_csr_destroy(pk_csr* A) {
   if (A->tile_row) cudaFree(A->tile_row);
   if (A->blk_tile) cudaFree(A->blk_tile);
   if (A->tile_grp) cudaFree(A->tile_grp);
+  if (A->tile_perm) cudaFree(A->tile_perm);
   if (A->cap_stream) cudaStreamDestroy(A->cap_stream);
   delete A;
   return PK_OK;

@@ -192,7 +192,8 @@ struct pk_csr {
   int grid_tma = 0;
   int32_t* tile_row = nullptr;  // ntiles + 1
   int32_t* blk_tile = nullptr;  // grid_tma + 1
-  int8_t* tile_grp = nullptr;   // ntiles: lanes per row in the tile (1, 8 or 32)
+  int8_t* tile_grp = nullptr;   // ntiles: 1 if the tile has no row longer than 32 nonzeros
+  int16_t* tile_perm = nullptr; // ntiles x 512: row order of the irregular tiles (or null)
   int ntiles = 0;
   int grid_stream = 0;          // grid of the streaming (vector-only) tile kernels
   int partial_cap = 0;         // blocks the partials buffer can hold
@@ -362,6 +363,8 @@ pk_status build_nested_graph(pk_csr* A, int kind, const void* const keys[4], con
                              const std::function<void(cudaStream_t)>& body,
                              const std::function<void(cudaStream_t)>& post, pk_graph_entry** out);
 void launch_enable_cond2(pk_csr* A, const pk_graph_entry* g, cudaStream_t s);
+// y = A x on the CSR tile engine (the unfused forms' SpMV); needs A->tma_ok.
+pk_status launch_spmv_tma(pk_csr* A, const double* x, double* y, int first, int skip_early, cudaStream_t s);
 
 // Counts body passes (first kernel of every body increments st->s[7] as an integer count).
 __device__ __forceinline__ void count_pass(DevState* st) {

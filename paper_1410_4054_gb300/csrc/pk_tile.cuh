@@ -285,7 +285,8 @@ constexpr int kCsrStages = 2;
 constexpr int kRpWords = kTileRows + 8;       // ints, incl. alignment slack
 constexpr int kVaWords = kTileNnz + 2;        // doubles
 constexpr int kCiWords = kTileNnz + 8;        // ints (window rounded out to 16 bytes on both ends)
-constexpr int kStageBytes = ((kRpWords * 4 + 15) & ~15) + kVaWords * 8 + ((kCiWords * 4 + 15) & ~15);
+constexpr int kCiBytes = (kCiWords * 4 + 15) & ~15;
+constexpr int kStageBytes = ((kRpWords * 4 + 15) & ~15) + kVaWords * 8 + kCiBytes + kTileRows * 2;  // + row order
 
 constexpr int csr_smem_bytes() { return kCsrStages * kStageBytes + 2 * kCsrStages * 8 + kCsrStages * 16; }
 
@@ -296,7 +297,8 @@ struct CsrTilesT {
   const VT* va;             // values: FP64, or the FP32 copy for the mixed-precision inner loop
   const int32_t* tile_row;  // row start of every tile (global tile list), plus n at the end
   const int32_t* blk_tile;  // tiles of block b: [blk_tile[b], blk_tile[b+1])
-  const int8_t* tile_grp;   // lanes per row of every tile: 1, 8 or 32
+  const int8_t* tile_grp;   // 1: every row of the tile has at most kLongRow nonzeros
+  const int16_t* tile_perm; // [tile][512]: row (offset in the tile) of every consumer slot, or -1
 };
 using CsrTiles = CsrTilesT<double>;
 
@@ -342,6 +344,10 @@ __device__ __forceinline__ bool csr_tiles(const CsrTilesT<VT>& T, unsigned char*
     return reinterpret_cast<int32_t*>(smem + (size_t)s * kStageBytes + ((kRpWords * 4 + 15) & ~15) +
                                       kVaWords * 8);
   };
+  auto stage_perm = [&](int s) {
+    return reinterpret_cast<int16_t*>(smem + (size_t)s * kStageBytes + ((kRpWords * 4 + 15) & ~15) +
+                                      kVaWords * 8 + kCiBytes);
+  };
   const int npro = min(kCsrStages, ntiles);
   bool ok = true;
   if (warp == kConsumerWarps) {
@@ -377,11 +383,13 @@ __device__ __forceinline__ bool csr_tiles(const CsrTilesT<VT>& T, unsigned char*
             const int cs = b0 & ~3, ce = (b1 + 3) & ~3;        // columns b0..b1-1
             const uint32_t nrp = (uint32_t)(re - rs) * 4, nva = (uint32_t)(ve - vs) * (uint32_t)sizeof(VT),
                            nci = (uint32_t)(ce - cs) * 4;
-            meta[s] = make_int4(a0, a1, g0, 0);  // published by the arrive below (release)
-            mbar_expect_tx(&full[s], nrp + nva + nci);
+            const bool perm = g0 != 1 && T.tile_perm;  // irregular tile: its row order too
+            meta[s] = make_int4(a0, a1, g0, perm ? 1 : 0);  // published by the arrive below (release)
+            mbar_expect_tx(&full[s], nrp + nva + nci + (perm ? kTileRows * 2 : 0));
             bulk_load_hint(stage_rp(s), T.rp + rs, nrp, &full[s], pol);
             if (nva) bulk_load_hint(stage_va(s), T.va + vs, nva, &full[s], pol);
             if (nci) bulk_load_hint(stage_ci(s), T.ci + cs, nci, &full[s], pol);
+            if (perm) bulk_load_hint(stage_perm(s), T.tile_perm + (size_t)(t0 + t) * kTileRows, kTileRows * 2, &full[s], pol);
             issued = t + 1;
           }
         }
@@ -418,8 +426,8 @@ __device__ __forceinline__ bool csr_tiles(const CsrTilesT<VT>& T, unsigned char*
     const int z0 = srp[R0];
     const VT* sva = stage_va(s) - (z0 & ~(kVaUnit - 1));  // windows start at the first row's nonzeros
     const int32_t* sci = stage_ci(s) - (z0 & ~3);
-    const int ra = R0 + (int)threadIdx.x;
     if (G == 1) {
+      const int ra = R0 + (int)threadIdx.x;
       if (ra < R1) {
         const int rb = ra + kConsumers < R1 ? ra + kConsumers : -1;
         VT sa, sb;
@@ -428,16 +436,21 @@ __device__ __forceinline__ bool csr_tiles(const CsrTilesT<VT>& T, unsigned char*
         if (rb >= 0) row_done(rb, sb);
       }
     } else {
-      // every lane takes part (the ballots below need the whole warp)
-      const bool has_a = ra < R1;
-      const int rb = has_a && ra + kConsumers < R1 ? ra + kConsumers : -1;
-      int ja0 = has_a ? srp[ra] : 0, ja1 = has_a ? srp[ra + 1] : 0;
+      // every lane takes part (the ballots below need the whole warp).  With a row order
+      // (sorted by length, dealt round-robin over the warps) each warp holds rows of similar
+      // length, so its FMA batches carry few idle lanes.
+      const int16_t* sperm = m.w ? stage_perm(s) : nullptr;
+      const int ka = sperm ? sperm[threadIdx.x] : (int)threadIdx.x;
+      const int kb = sperm ? sperm[threadIdx.x + kConsumers] : (int)threadIdx.x + kConsumers;
+      const int ra = ka >= 0 && R0 + ka < R1 ? R0 + ka : -1;
+      const int rb = kb >= 0 && R0 + kb < R1 ? R0 + kb : -1;
+      int ja0 = ra >= 0 ? srp[ra] : 0, ja1 = ra >= 0 ? srp[ra + 1] : 0;
       int jb0 = rb >= 0 ? srp[rb] : 0, jb1 = rb >= 0 ? srp[rb + 1] : 0;
       const bool la = ja1 - ja0 > kLongRow, lb = jb1 - jb0 > kLongRow;
-      if (has_a) {
+      if (ra >= 0 || rb >= 0) {
         VT sa, sb;
         row_pair(sva, sci, ja0, la ? ja0 : ja1, jb0, lb ? jb0 : jb1, x, sa, sb);
-        if (!la) row_done(ra, sa);
+        if (ra >= 0 && !la) row_done(ra, sa);
         if (rb >= 0 && !lb) row_done(rb, sb);
       }
 #pragma unroll
@@ -615,6 +628,7 @@ inline CsrTilesT<float> csr_tiles32_of(const pk_csr* A) {
   t.tile_row = A->tile_row;
   t.blk_tile = A->blk_tile;
   t.tile_grp = A->tile_grp;
+  t.tile_perm = A->tile_perm;
   return t;
 }
 
@@ -626,6 +640,7 @@ inline CsrTiles csr_tiles_of(const pk_csr* A) {
   t.tile_row = A->tile_row;
   t.blk_tile = A->blk_tile;
   t.tile_grp = A->tile_grp;
+  t.tile_perm = A->tile_perm;
   return t;
 }
 
