@@ -463,6 +463,7 @@ def bench_forms(pk, torch, dev, args):
         prof = fn(A, bd, x.zero_(), tol=0.0, maxit=30, flags=pk.FLAG_TIMING,
                   **({"restart": 30} if solver == "gmres" else {}))
         row["kernel_ms_30_fixed_iterations"] = prof["kernel_ms"]
+        row["roofline"] = solver_rooflines(solver, a.n, a.nnz, prof["kernel_ms"])
         row["speedup_vs_classical"] = row["classical_ms"] / row["pipelined_ms"]
         out[solver] = row
     A.close()
@@ -487,6 +488,14 @@ def bench_forms(pk, torch, dev, args):
         brow[f"{prec}_solves_per_s"] = len(mats) / (ms * 1e-3)
         brow[f"{prec}_all_converged"] = all(i["status"] == pk.PK_OK for i in infos)
         brow[f"{prec}_config"] = list(pk.batched_last_config())
+        # algorithmic bytes of every system's iterations (FP64: 12 nnz + 76 n per iteration;
+        # mixed: the FP32 inner iteration, 8 nnz + 40 n) over the launch time
+        per_it = [(12 * m.nnz + 76 * m.n) if prec == "fp64" else (8 * m.nnz + 40 * m.n) for m in mats]
+        moved = sum(i["iters"] * b_ for i, b_ in zip(infos, per_it))
+        gbs = moved / (ms * 1e-3) / 1e9
+        brow[f"{prec}_roofline"] = {"bound": "hbm", "achieved": gbs, "peak": measured_peaks()[0],
+                                    "unit": "GB/s", "frac": gbs / measured_peaks()[0],
+                                    "note": "sum over systems of iterations x algorithmic bytes per iteration"}
         res[prec] = [v.clone() for v in xs]
     errs = [float(torch.linalg.norm(xm - x64) / torch.linalg.norm(x64))
             for xm, x64 in zip(res["mixed"], res["fp64"]) if float(torch.linalg.norm(x64)) > 0]
@@ -523,6 +532,11 @@ def bench_forms(pk, torch, dev, args):
                     "fp64_iters": i64["iters"], "mixed_rel_res_true": im["rel_res_true"],
                     "rel_error_vs_fp64": float(torch.linalg.norm(xm - x64) / torch.linalg.norm(x64)),
                     "inner_bytes_per_iter": 8 * a.nnz + 40 * a.n}
+    mixed_bytes = im["iters"] * (8 * a.nnz + 40 * a.n) + (im["cycles"] + 1) * (12 * a.nnz + 4 * (a.n + 1) + 16 * a.n)
+    gbs = mixed_bytes / (im["solve_ms"] * 1e-3) / 1e9
+    out["mixed"]["roofline"] = {"bound": "hbm", "achieved": gbs, "peak": measured_peaks()[0], "unit": "GB/s",
+                                "frac": gbs / measured_peaks()[0],
+                                "note": "inner FP32 iterations x (8 nnz + 40 n) + FP64 residuals, over the solve"}
     A.close()
 
     out["nonsymmetric_sweep"] = nonsymmetric_sweep(pk, torch, dev)
@@ -535,7 +549,60 @@ def bench_forms(pk, torch, dev, args):
     lw["train_ms_per_sample"] = 1e3 * res["train_s"] / (res["epochs"] * res["train_samples"])
     lw["iteration_gain_vs_plain_warm_start"] = res["baseline_mean_iters"] - res["learned_mean_iters"]
     lw["conv"] = conv_throughput(pk, torch, dev, (64, 64, 64))
+    bf16_peak = bf16_peak_tflops()
+    lw["conv"]["roofline"] = {"bound": "tensor", "peak": bf16_peak, "unit": "TFLOP/s",
+                              "peak_source": "measured (MEASURED_PEAKS.json bf16_tflops)",
+                              **{f"{k}_frac": lw["conv"][f"{k}_tflops"] / bf16_peak
+                                 for k in ("fwd", "bwd_data", "wgrad")}}
     out["learned_warm_start"] = lw
+    return out
+
+
+FP64_NOMINAL_TFLOPS = 1.25  # GB300 FP64 (vector and tensor), nominal
+
+
+def bf16_peak_tflops():
+    p = ROOT / "MEASURED_PEAKS.json"
+    if p.exists():
+        return float(json.loads(p.read_text())["bf16_tflops"])
+    return 1900.0
+
+
+def solver_rooflines(solver, n, nnz, km):
+    """Per-kernel achieved GB/s (algorithmic bytes per launch / mean launch time of 30 fixed
+    iterations) against the measured HBM copy bandwidth; the Gram-Schmidt kernels also
+    against the nominal FP64 rate, which bounds them on GB300."""
+    peak = measured_peaks()[0]
+    spmv = 12 * nnz + 4 * (n + 1) + 24 * n
+    out = {}
+
+    def hbm(name, bytes_, ms):
+        if ms:
+            gbs = bytes_ / (ms * 1e-3) / 1e9
+            out[name] = {"bound": "hbm", "bytes_per_launch": bytes_, "launch_ms": ms, "achieved_gbs": gbs,
+                         "peak_gbs": peak, "frac": gbs / peak}
+
+    if solver == "bicgstab":
+        hbm("K-BI-1/3 (SpMV + dots)", spmv, km.get("spmv_dots"))
+        hbm("K-BI-2/4 (updates + dots), mean of 24n and 72n", 48 * n, km.get("update"))
+    else:
+        hbm("K-GM-1 (SpMV + <v_{i-1}, v_i>)", spmv, km.get("spmv_dots"))
+        hbm("K-GM-4 (normalise + xi)", 24 * n, km.get("update"))
+        steps = range(1, 31)
+        for name, slot, vecs, fmas in (("K-GM-2 (inner products)", "multidot",
+                                        lambda i: i - 1 if i >= 3 else 0, lambda i: max(i - 2, 0)),
+                                       ("K-GM-3 (CGS update + norm)", "ortho",
+                                        lambda i: i + 1, lambda i: i)):
+            ms = km.get(slot)
+            if not ms:
+                continue
+            b_ = 8 * n * sum(vecs(i) for i in steps) / 30
+            f_ = 2 * n * sum(fmas(i) for i in steps) / 30
+            gbs = b_ / (ms * 1e-3) / 1e9
+            tf = f_ / (ms * 1e-3) / 1e12
+            out[name] = {"bound": "fp64", "bytes_per_launch_mean": b_, "launch_ms": ms, "achieved_gbs": gbs,
+                         "frac_hbm": gbs / peak, "fp64_tflops": tf, "fp64_peak_tflops": FP64_NOMINAL_TFLOPS,
+                         "frac": tf / FP64_NOMINAL_TFLOPS, "peak_source": "nominal FP64"}
     return out
 
 

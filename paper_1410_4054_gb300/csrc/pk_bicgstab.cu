@@ -20,6 +20,7 @@ namespace pk {
 
 // ---------------------------------------------------------------- pipelined, tile engine
 
+template <bool IRR>
 __global__ void __launch_bounds__(kTileThreads, 2) k_bi1_tma(CsrTiles T, const double* __restrict__ p,
                                                              double* __restrict__ ap,
                                                              const double* __restrict__ r0s,
@@ -27,7 +28,7 @@ __global__ void __launch_bounds__(kTileThreads, 2) k_bi1_tma(CsrTiles T, const d
   extern __shared__ __align__(128) unsigned char smem[];
   count_pass(st);
   double v[1] = {0.0};
-  const bool live = csr_tiles(T, smem, st, [&]() { return !state_done(st); }, p,
+  const bool live = csr_tiles<IRR>(T, smem, st, [&]() { return !state_done(st); }, p,
                               [&](int row, double y) {
     ap[row] = y;
     v[0] = fma(y, __ldg(r0s + row), v[0]);
@@ -98,13 +99,14 @@ __global__ void __launch_bounds__(kTileThreads, 2) k_bi2_tma(int n, const double
   }
 }
 
+template <bool IRR>
 __global__ void __launch_bounds__(kTileThreads, 2) k_bi3_tma(CsrTiles T, const double* __restrict__ s,
                                                              double* __restrict__ as,
                                                              const double* __restrict__ r0s,
                                                              double* partials, DevState* st) {
   extern __shared__ __align__(128) unsigned char smem[];
   double v[3] = {0.0, 0.0, 0.0};
-  const bool live = csr_tiles(T, smem, st, [&]() { return !state_done(st) && !__ldcg(&st->early); }, s,
+  const bool live = csr_tiles<IRR>(T, smem, st, [&]() { return !state_done(st) && !__ldcg(&st->early); }, s,
                               [&](int row, double y) {
     as[row] = y;
     v[0] = fma(y, __ldg(s + row), v[0]);
@@ -396,8 +398,8 @@ __global__ void __launch_bounds__(kBlock) k_bc_rr(RowArgs a, const double* __res
 static pk_status bi_tma_setup() {
   static bool done = false;
   if (!done) {
-    PK_CUDA(cudaFuncSetAttribute(k_bi1_tma, cudaFuncAttributeMaxDynamicSharedMemorySize, csr_smem_bytes()));
-    PK_CUDA(cudaFuncSetAttribute(k_bi3_tma, cudaFuncAttributeMaxDynamicSharedMemorySize, csr_smem_bytes()));
+    for (auto k : {k_bi1_tma<false>, k_bi1_tma<true>, k_bi3_tma<false>, k_bi3_tma<true>})
+      PK_CUDA(cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, csr_smem_bytes()));
     PK_CUDA(cudaFuncSetAttribute(k_bi2_tma, cudaFuncAttributeMaxDynamicSharedMemorySize, stream_smem_bytes<2>()));
     PK_CUDA(cudaFuncSetAttribute(k_bi4_tma, cudaFuncAttributeMaxDynamicSharedMemorySize, stream_smem_bytes<6>()));
     done = true;
@@ -449,6 +451,7 @@ pk_status bicgstab_solve(pk_csr* A, const double* b, double* x, const pk_opts* o
   int launches = 0;
   const RowArgs ra = row_args(A);
   const CsrTiles ct = csr_tiles_of(A);
+  const bool irr = A->stats.tiles_long > 0;  // rows longer than 32 nonzeros somewhere
   const int G = A->grid, Gt = A->grid_tma, Gs = A->grid_stream, n = A->n;
   double* part = A->partials;
   DevState* dst = A->st;
@@ -472,11 +475,11 @@ pk_status bicgstab_solve(pk_csr* A, const double* b, double* x, const pk_opts* o
     L.body = [=](cudaStream_t cs, Timer* t) {
       if (tma) {
         if (t) t->begin(PK_SLOT_SPMV_DOTS);
-        launch_pdl(k_bi1_tma, Gt, kTileThreads, csr_smem_bytes(), cs, ct, (const double*)p, ap, (const double*)r0s, part, dst);
+        launch_pdl(irr ? k_bi1_tma<true> : k_bi1_tma<false>, Gt, kTileThreads, csr_smem_bytes(), cs, ct, (const double*)p, ap, (const double*)r0s, part, dst);
         if (t) { t->end(); t->begin(PK_SLOT_UPDATE); }
         launch_pdl(k_bi2_tma, Gs, kTileThreads, stream_smem_bytes<2>(), cs, n, (const double*)r, (const double*)ap, sv, part, dst);
         if (t) { t->end(); t->begin(PK_SLOT_SPMV_DOTS); }
-        launch_pdl(k_bi3_tma, Gt, kTileThreads, csr_smem_bytes(), cs, ct, (const double*)sv, as, (const double*)r0s, part, dst);
+        launch_pdl(irr ? k_bi3_tma<true> : k_bi3_tma<false>, Gt, kTileThreads, csr_smem_bytes(), cs, ct, (const double*)sv, as, (const double*)r0s, part, dst);
         if (t) { t->end(); t->begin(PK_SLOT_UPDATE); }
         launch_pdl(k_bi4_tma, Gs, kTileThreads, stream_smem_bytes<6>(), cs, n, xd, p, (const double*)sv,
                    (const double*)ap, (const double*)r0s, (const double*)as, r, part, dst);

@@ -269,13 +269,14 @@ __global__ void __launch_bounds__(kTileThreads, 2) k_cg_update_tma(int n, double
 }
 
 // K-CG-S on the CSR tile engine.
+template <bool IRR>
 __global__ void __launch_bounds__(kTileThreads, 2) k_cg_spmv_dots_tma(CsrTiles T,
                                                                       const double* __restrict__ p,
                                                                       double* __restrict__ ap,
                                                                       double* partials, DevState* st) {
   extern __shared__ __align__(128) unsigned char smem[];
   double v[2] = {0.0, 0.0};
-  const bool live = csr_tiles(T, smem, st, [&]() { return !state_done(st); }, p,
+  const bool live = csr_tiles<IRR>(T, smem, st, [&]() { return !state_done(st); }, p,
                               [&](int row, double y) {
     ap[row] = y;
     v[0] = fma(y, y, v[0]);
@@ -299,12 +300,13 @@ __global__ void __launch_bounds__(kTileThreads, 2) k_cg_spmv_dots_tma(CsrTiles T
 // (classical and split CG, classical BiCGStab), so that fused and unfused solvers differ only
 // in the fusion.  `first` counts a loop pass; `skip_early`: BiCGStab's early-exit flag also
 // ends the solve.
+template <bool IRR>
 __global__ void __launch_bounds__(kTileThreads, 2) k_spmv_tma(CsrTiles T, const double* __restrict__ x,
                                                               double* __restrict__ y, DevState* st,
                                                               int first, int skip_early) {
   extern __shared__ __align__(128) unsigned char smem[];
   if (first) count_pass(st);
-  csr_tiles(T, smem, st, [&]() { return !state_done(st) && !(skip_early && __ldcg(&st->early)); }, x,
+  csr_tiles<IRR>(T, smem, st, [&]() { return !state_done(st) && !(skip_early && __ldcg(&st->early)); }, x,
             [&](int row, double v) { y[row] = v; });
 }
 
@@ -313,9 +315,10 @@ static pk_status tma_setup() {
   if (!done) {
     PK_CUDA(cudaFuncSetAttribute(k_cg_update_tma, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                  stream_smem_bytes<4>()));
-    PK_CUDA(cudaFuncSetAttribute(k_cg_spmv_dots_tma, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                 csr_smem_bytes()));
-    PK_CUDA(cudaFuncSetAttribute(k_spmv_tma, cudaFuncAttributeMaxDynamicSharedMemorySize, csr_smem_bytes()));
+    for (auto k : {k_cg_spmv_dots_tma<false>, k_cg_spmv_dots_tma<true>})
+      PK_CUDA(cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, csr_smem_bytes()));
+    for (auto k : {k_spmv_tma<false>, k_spmv_tma<true>})
+      PK_CUDA(cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, csr_smem_bytes()));
     done = true;
   }
   return PK_OK;
@@ -496,6 +499,7 @@ pk_status cg_solve(pk_csr* A, const double* b, double* x, const pk_opts* o, pk_i
   const bool tma = tma_engine;
   if (tma && (e = tma_setup())) return e;
   const CsrTiles ct = csr_tiles_of(A);
+  const bool irr = A->stats.tiles_long > 0;  // rows longer than 32 nonzeros somewhere
   const int Gt = A->grid_tma, Gs = A->grid_stream;
   double* part = A->partials;
   DevState* dst = A->st;
@@ -503,7 +507,7 @@ pk_status cg_solve(pk_csr* A, const double* b, double* x, const pk_opts* o, pk_i
   if (variant == PK_VARIANT_PIPELINED || variant == PK_VARIANT_SPLIT) {
     // A p0, alpha_0, beta_0
     if ((e = T.begin(PK_SLOT_SPMV_DOTS))) return e;
-    if (tma) k_cg_spmv_dots_tma<<<Gt, kTileThreads, csr_smem_bytes(), s>>>(ct, p, ap, part, dst);
+    if (tma) (irr ? k_cg_spmv_dots_tma<true> : k_cg_spmv_dots_tma<false>)<<<Gt, kTileThreads, csr_smem_bytes(), s>>>(ct, p, ap, part, dst);
     else k_cg_spmv_dots<<<G, kBlock, 0, s>>>(ra, p, ap);
     if ((e = T.end())) return e;
     launches += 1;
@@ -524,7 +528,7 @@ pk_status cg_solve(pk_csr* A, const double* b, double* x, const pk_opts* o, pk_i
       if (tma) launch_pdl(k_cg_update_tma, Gs, kTileThreads, stream_smem_bytes<4>(), cs, n, xd, r, p, ap, part, dst);
       else k_cg_update<<<Gu, kBlock, 0, cs>>>(ra, xd, r, p, ap);
       if (t) { t->end(); t->begin(PK_SLOT_SPMV_DOTS); }
-      if (tma) launch_pdl(k_cg_spmv_dots_tma, Gt, kTileThreads, csr_smem_bytes(), cs, ct, (const double*)p, ap, part, dst);
+      if (tma) launch_pdl(irr ? k_cg_spmv_dots_tma<true> : k_cg_spmv_dots_tma<false>, Gt, kTileThreads, csr_smem_bytes(), cs, ct, (const double*)p, ap, part, dst);
       else k_cg_spmv_dots<<<G, kBlock, 0, cs>>>(ra, p, ap);
       if (t) t->end();
     };
@@ -535,7 +539,7 @@ pk_status cg_solve(pk_csr* A, const double* b, double* x, const pk_opts* o, pk_i
       if (t) t->begin(PK_SLOT_UPDATE);
       k_cg_update<<<Gu, kBlock, 0, cs>>>(ra, xd, r, p, ap);
       if (t) { t->end(); t->begin(PK_SLOT_SPMV); }
-      if (tma) k_spmv_tma<<<Gt, kTileThreads, csr_smem_bytes(), cs>>>(ct, p, ap, dst, 0, 0);
+      if (tma) (irr ? k_spmv_tma<true> : k_spmv_tma<false>)<<<Gt, kTileThreads, csr_smem_bytes(), cs>>>(ct, p, ap, dst, 0, 0);
       else k_spmv_live<<<G, kBlock, 0, cs>>>(ra, p, ap, 0);
       if (t) { t->end(); t->begin(PK_SLOT_BLAS1); }
       k_cg_dots<<<G, kBlock, 0, cs>>>(ra, p, ap);
@@ -546,7 +550,7 @@ pk_status cg_solve(pk_csr* A, const double* b, double* x, const pk_opts* o, pk_i
     L.body_kernels = 6;
     L.body = [=](cudaStream_t cs, Timer* t) {
       if (t) t->begin(PK_SLOT_SPMV);
-      if (tma) k_spmv_tma<<<Gt, kTileThreads, csr_smem_bytes(), cs>>>(ct, p, ap, dst, 1, 0);
+      if (tma) (irr ? k_spmv_tma<true> : k_spmv_tma<false>)<<<Gt, kTileThreads, csr_smem_bytes(), cs>>>(ct, p, ap, dst, 1, 0);
       else k_spmv_live<<<G, kBlock, 0, cs>>>(ra, p, ap, 1);
       if (t) { t->end(); t->begin(PK_SLOT_BLAS1); }
       k_cls_alpha<<<G, kBlock, 0, cs>>>(ra, p, ap);
@@ -580,7 +584,8 @@ pk_status cg_solve(pk_csr* A, const double* b, double* x, const pk_opts* o, pk_i
 pk_status launch_spmv_tma(pk_csr* A, const double* x, double* y, int first, int skip_early, cudaStream_t s) {
   pk_status e = tma_setup();
   if (e) return e;
-  k_spmv_tma<<<A->grid_tma, kTileThreads, csr_smem_bytes(), s>>>(csr_tiles_of(A), x, y, A->st, first, skip_early);
+  (A->stats.tiles_long > 0 ? k_spmv_tma<true> : k_spmv_tma<false>)<<<A->grid_tma, kTileThreads, csr_smem_bytes(), s>>>(
+      csr_tiles_of(A), x, y, A->st, first, skip_early);
   return PK_OK;
 }
 

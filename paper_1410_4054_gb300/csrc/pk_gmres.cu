@@ -54,6 +54,7 @@ __device__ __forceinline__ bool gm_step_live(const DevState* st) {
 }
 
 // START: r = b - A x into v_0, <r,r>, <b,b>; cycle-boundary tests.
+template <bool IRR>
 __global__ void __launch_bounds__(kTileThreads, 2) k_gm_start(CsrTiles T, GmArgs g) {
   extern __shared__ __align__(128) unsigned char smem[];
   DevState* st = g.st;
@@ -63,7 +64,7 @@ __global__ void __launch_bounds__(kTileThreads, 2) k_gm_start(CsrTiles T, GmArgs
   }
   double* r = g.V;
   double v[2] = {0.0, 0.0};
-  const bool live = csr_tiles(T, smem, st, [&]() { return !state_done(st); }, (const double*)g.x,
+  const bool live = csr_tiles<IRR>(T, smem, st, [&]() { return !state_done(st); }, (const double*)g.x,
                               [&](int row, double y) {
     const double bi = __ldg(g.b + row), q = bi - y;
     r[row] = q;
@@ -135,6 +136,7 @@ __global__ void __launch_bounds__(kTileThreads, 2) k_gm_scale(GmArgs g) {
 }
 
 // K-GM-1: v_i = A v_{i-1} and the first stage of <v_{i-1}, v_i> (i >= 2).
+template <bool IRR>
 __global__ void __launch_bounds__(kTileThreads, 2) k_gm1(CsrTiles T, GmArgs g) {
   extern __shared__ __align__(128) unsigned char smem[];
   DevState* st = g.st;
@@ -143,7 +145,7 @@ __global__ void __launch_bounds__(kTileThreads, 2) k_gm1(CsrTiles T, GmArgs g) {
   const double* vp = g.V + (size_t)(i - 1) * g.ld;
   double* vi = g.V + (size_t)i * g.ld;
   double v[1] = {0.0};
-  const bool live = csr_tiles(T, smem, st, [&]() { return gm_step_live(st); }, vp,
+  const bool live = csr_tiles<IRR>(T, smem, st, [&]() { return gm_step_live(st); }, vp,
                               [&](int row, double y) {
     vi[row] = y;
     v[0] = fma(__ldg(vp + row), y, v[0]);
@@ -622,8 +624,8 @@ __global__ void k_gm_init(DevState* st, int m) {
 static pk_status gm_setup() {
   static bool done = false;
   if (!done) {
-    PK_CUDA(cudaFuncSetAttribute(k_gm_start, cudaFuncAttributeMaxDynamicSharedMemorySize, csr_smem_bytes()));
-    PK_CUDA(cudaFuncSetAttribute(k_gm1, cudaFuncAttributeMaxDynamicSharedMemorySize, csr_smem_bytes()));
+    for (auto k : {k_gm_start<false>, k_gm_start<true>, k_gm1<false>, k_gm1<true>})
+      PK_CUDA(cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, csr_smem_bytes()));
     PK_CUDA(cudaFuncSetAttribute(k_gm_scale, cudaFuncAttributeMaxDynamicSharedMemorySize, stream_smem_bytes<1>()));
     PK_CUDA(cudaFuncSetAttribute(k_gm4, cudaFuncAttributeMaxDynamicSharedMemorySize, stream_smem_bytes<2>()));
     PK_CUDA(cudaFuncSetAttribute(k_gm2, cudaFuncAttributeMaxDynamicSharedMemorySize, kBsSmem));
@@ -683,6 +685,7 @@ pk_status gmres_solve(pk_csr* A, const double* b, double* x, const pk_opts* o, p
   g.partials = A->partials;
   g.st = A->st;
   const CsrTiles ct = csr_tiles_of(A);
+  const bool irr = A->stats.tiles_long > 0;  // rows longer than 32 nonzeros somewhere
   const int Gt = A->grid_tma, Gs = A->grid_stream;
   int Ge = A->grid_ew;
   if (!Ge) {
@@ -697,14 +700,14 @@ pk_status gmres_solve(pk_csr* A, const double* b, double* x, const pk_opts* o, p
   int launches = 1;  // k_gm_init
   auto pre = [&](cudaStream_t cs, Timer* t) {
     if (t) t->begin(PK_SLOT_OTHER);
-    k_gm_start<<<Gt, kTileThreads, csr_smem_bytes(), cs>>>(ct, g);
+    (irr ? k_gm_start<true> : k_gm_start<false>)<<<Gt, kTileThreads, csr_smem_bytes(), cs>>>(ct, g);
     if (t) { t->end(); t->begin(PK_SLOT_OTHER); }
     k_gm_scale<<<Gs, kTileThreads, stream_smem_bytes<1>(), cs>>>(g);
     if (t) t->end();
   };
   auto step = [&](cudaStream_t cs, Timer* t) {
     if (t) t->begin(PK_SLOT_SPMV_DOTS);
-    k_gm1<<<Gt, kTileThreads, csr_smem_bytes(), cs>>>(ct, g);
+    (irr ? k_gm1<true> : k_gm1<false>)<<<Gt, kTileThreads, csr_smem_bytes(), cs>>>(ct, g);
     if (t) { t->end(); t->begin(PK_SLOT_MULTIDOT); }
     k_gm2<<<Gs, kTileThreads, kBsSmem, cs>>>(g);
     if (t) { t->end(); t->begin(PK_SLOT_ORTHO); }

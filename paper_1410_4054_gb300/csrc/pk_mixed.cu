@@ -228,11 +228,12 @@ __device__ __forceinline__ bool mx_inner_live(DevState* st) {
   return !state_done(st) && __ldcg(&st->gm_phase) == 1;
 }
 
+template <bool IRR>
 __global__ void __launch_bounds__(kTileThreads, 2) k_mx_spmv_tma(CsrTilesT<float> T, MxArgs a) {
   extern __shared__ __align__(128) unsigned char smem[];
   DevState* st = a.st;
   FF aa{0.0f, 0.0f}, pa{0.0f, 0.0f};
-  const bool live = csr_tiles(T, smem, st, [&]() { return mx_inner_live(st); }, (const float*)a.p,
+  const bool live = csr_tiles<IRR>(T, smem, st, [&]() { return mx_inner_live(st); }, (const float*)a.p,
                               [&](int row, float y) {
     a.ap[row] = y;
     ff_add_prod(aa, y, y);
@@ -319,7 +320,8 @@ __global__ void __launch_bounds__(kTileThreads, 2) k_mx_update_tma(MxArgs a) {
 static pk_status mx_tma_setup() {
   static bool done = false;
   if (!done) {
-    PK_CUDA(cudaFuncSetAttribute(k_mx_spmv_tma, cudaFuncAttributeMaxDynamicSharedMemorySize, csr_smem_bytes()));
+    for (auto k : {k_mx_spmv_tma<false>, k_mx_spmv_tma<true>})
+      PK_CUDA(cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, csr_smem_bytes()));
     PK_CUDA(cudaFuncSetAttribute(k_mx_update_tma, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                  stream_smem_bytes<4, float>()));
     done = true;
@@ -413,10 +415,11 @@ pk_status cg_mixed(pk_csr* A, const double* b, double* x, const pk_opts* o, pk_i
   const bool tma = A->tma_ok && !(o->flags & PK_FLAG_NO_TMA);
   if (tma && (e = mx_tma_setup())) return e;
   const CsrTilesT<float> ct = csr_tiles32_of(A);
+  const bool irr = A->stats.tiles_long > 0;  // rows longer than 32 nonzeros somewhere
   const int Gt = A->grid_tma, Gs = A->grid_stream;
   auto step = [&](cudaStream_t cs, Timer* t) {
     if (t) t->begin(PK_SLOT_SPMV_DOTS);
-    if (tma) launch_pdl(k_mx_spmv_tma, Gt, kTileThreads, csr_smem_bytes(), cs, ct, a);
+    if (tma) launch_pdl(irr ? k_mx_spmv_tma<true> : k_mx_spmv_tma<false>, Gt, kTileThreads, csr_smem_bytes(), cs, ct, a);
     else k_mx_spmv<<<G, kBlock, 0, cs>>>(a);
     if (t) { t->end(); t->begin(PK_SLOT_UPDATE); }
     if (tma) launch_pdl(k_mx_update_tma, Gs, kTileThreads, stream_smem_bytes<4, float>(), cs, a);

@@ -318,7 +318,8 @@ __device__ __forceinline__ void row_pair(const float* sva, const int32_t* sci, i
 // no synchronisation beyond the warp is involved.
 constexpr int kLongRow = 32;
 
-template <class VT, class Setup, class RowDone>
+// IRR = false compiles the thread-per-row path only (matrices without long rows).
+template <bool IRR, class VT, class Setup, class RowDone>
 __device__ __forceinline__ bool csr_tiles(const CsrTilesT<VT>& T, unsigned char* smem, DevState* st,
                                           Setup&& setup, const VT* __restrict__ x, RowDone&& row_done) {
   constexpr int kVaUnit = 16 / (int)sizeof(VT);  // values per 16-byte copy unit
@@ -426,7 +427,7 @@ __device__ __forceinline__ bool csr_tiles(const CsrTilesT<VT>& T, unsigned char*
     const int z0 = srp[R0];
     const VT* sva = stage_va(s) - (z0 & ~(kVaUnit - 1));  // windows start at the first row's nonzeros
     const int32_t* sci = stage_ci(s) - (z0 & ~3);
-    if (G == 1) {
+    if (!IRR || G == 1) {
       const int ra = R0 + (int)threadIdx.x;
       if (ra < R1) {
         const int rb = ra + kConsumers < R1 ? ra + kConsumers : -1;
