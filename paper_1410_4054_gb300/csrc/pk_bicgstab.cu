@@ -67,7 +67,7 @@ __global__ void __launch_bounds__(kTileThreads, 2) k_bi2_tma(int n, const double
   double v[1] = {0.0};
   double alpha = 0.0;
   StreamIn<2> in{{r, ap}};
-  const bool live = stream_tiles<2, 1>(in, r0, r1, smem, st, [&]() {
+  const bool live = stream_tiles<2, 1, double, 4>(in, r0, r1, smem, st, [&]() {
     alpha = __ldcg(&st->alpha);
     return !state_done(st);
   }, [&](int row, const double2* val, int nv) {
@@ -153,7 +153,7 @@ __global__ void __launch_bounds__(kTileThreads, 2) k_bi4_tma(int n, double* __re
   bool early = false;
   // everything but As (written by K-BI-3) is prefetched before the dependency wait
   StreamIn<6> in{{x, p, s, ap, r0s, as}};
-  const bool live = stream_tiles<6, 5>(in, r0, r1, smem, st, [&]() {
+  const bool live = stream_tiles<6, 5, double, 2>(in, r0, r1, smem, st, [&]() {
     alpha = __ldcg(&st->alpha);
     omega = __ldcg(&st->omega);
     beta = __ldcg(&st->beta);
@@ -161,19 +161,35 @@ __global__ void __launch_bounds__(kTileThreads, 2) k_bi4_tma(int n, double* __re
     return !state_done(st);
   }, [&](int row, const double2* val, int nv) {
     const double2 xk = val[0], pk = val[1], sk = val[2], ak = val[3], zk = val[4], bk = val[5];
-    double xs[2] = {xk.x, xk.y}, ps[2] = {pk.x, pk.y}, ss[2] = {sk.x, sk.y};
-    double aps[2] = {ak.x, ak.y}, zs[2] = {zk.x, zk.y}, ass[2] = {bk.x, bk.y};
-    for (int k = 0; k < nv; ++k) {
-      if (early) {
-        x[row + k] = fma(alpha, ps[k], xs[k]);
-        continue;
-      }
-      x[row + k] = xs[k] + fma(alpha, ps[k], omega * ss[k]);
-      const double rn = fma(-omega, ass[k], ss[k]);
-      r[row + k] = rn;
-      p[row + k] = fma(beta, fma(-omega, aps[k], ps[k]), rn);
-      v[0] = fma(rn, zs[k], v[0]);
-      v[1] = fma(rn, rn, v[1]);
+    double2 xn, rn, pn;
+    if (early) {  // ||s|| small: x += alpha p only
+      xn.x = fma(alpha, pk.x, xk.x);
+      xn.y = fma(alpha, pk.y, xk.y);
+      if (nv == 2) st2(x + row, xn);
+      else x[row] = xn.x;
+      return;
+    }
+    // x + alpha p + omega s, r = s - omega As, p = r + beta (p - omega Ap): 6 FMA per row
+    xn.x = fma(omega, sk.x, fma(alpha, pk.x, xk.x));
+    xn.y = fma(omega, sk.y, fma(alpha, pk.y, xk.y));
+    rn.x = fma(-omega, bk.x, sk.x);
+    rn.y = fma(-omega, bk.y, sk.y);
+    pn.x = fma(beta, fma(-omega, ak.x, pk.x), rn.x);
+    pn.y = fma(beta, fma(-omega, ak.y, pk.y), rn.y);
+    if (nv == 2) {
+      st2(x + row, xn);
+      st2(r + row, rn);
+      st2(p + row, pn);
+      v[0] = fma(rn.x, zk.x, v[0]);
+      v[1] = fma(rn.x, rn.x, v[1]);
+      v[0] = fma(rn.y, zk.y, v[0]);
+      v[1] = fma(rn.y, rn.y, v[1]);
+    } else {
+      x[row] = xn.x;
+      r[row] = rn.x;
+      p[row] = pn.x;
+      v[0] = fma(rn.x, zk.x, v[0]);
+      v[1] = fma(rn.x, rn.x, v[1]);
     }
   });
   griddep_trigger();
@@ -400,8 +416,8 @@ static pk_status bi_tma_setup() {
   if (!done) {
     for (auto k : {k_bi1_tma<false>, k_bi1_tma<true>, k_bi3_tma<false>, k_bi3_tma<true>})
       PK_CUDA(cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, csr_smem_bytes()));
-    PK_CUDA(cudaFuncSetAttribute(k_bi2_tma, cudaFuncAttributeMaxDynamicSharedMemorySize, stream_smem_bytes<2>()));
-    PK_CUDA(cudaFuncSetAttribute(k_bi4_tma, cudaFuncAttributeMaxDynamicSharedMemorySize, stream_smem_bytes<6>()));
+    PK_CUDA(cudaFuncSetAttribute(k_bi2_tma, cudaFuncAttributeMaxDynamicSharedMemorySize, stream_smem_bytes<2, double, 4>()));
+    PK_CUDA(cudaFuncSetAttribute(k_bi4_tma, cudaFuncAttributeMaxDynamicSharedMemorySize, stream_smem_bytes<6, double, 2>()));
     done = true;
   }
   return PK_OK;
@@ -477,11 +493,11 @@ pk_status bicgstab_solve(pk_csr* A, const double* b, double* x, const pk_opts* o
         if (t) t->begin(PK_SLOT_SPMV_DOTS);
         launch_pdl(irr ? k_bi1_tma<true> : k_bi1_tma<false>, Gt, kTileThreads, csr_smem_bytes(), cs, ct, (const double*)p, ap, (const double*)r0s, part, dst);
         if (t) { t->end(); t->begin(PK_SLOT_UPDATE); }
-        launch_pdl(k_bi2_tma, Gs, kTileThreads, stream_smem_bytes<2>(), cs, n, (const double*)r, (const double*)ap, sv, part, dst);
+        launch_pdl(k_bi2_tma, Gs, kTileThreads, stream_smem_bytes<2, double, 4>(), cs, n, (const double*)r, (const double*)ap, sv, part, dst);
         if (t) { t->end(); t->begin(PK_SLOT_SPMV_DOTS); }
         launch_pdl(irr ? k_bi3_tma<true> : k_bi3_tma<false>, Gt, kTileThreads, csr_smem_bytes(), cs, ct, (const double*)sv, as, (const double*)r0s, part, dst);
         if (t) { t->end(); t->begin(PK_SLOT_UPDATE); }
-        launch_pdl(k_bi4_tma, Gs, kTileThreads, stream_smem_bytes<6>(), cs, n, xd, p, (const double*)sv,
+        launch_pdl(k_bi4_tma, Gs, kTileThreads, stream_smem_bytes<6, double, 2>(), cs, n, xd, p, (const double*)sv,
                    (const double*)ap, (const double*)r0s, (const double*)as, r, part, dst);
         if (t) t->end();
       }

@@ -218,7 +218,7 @@ __global__ void __launch_bounds__(kTileThreads, 2) k_cg_update_tma(int n, double
   double alpha = 0.0, beta = 0.0;
   // x and r do not depend on the preceding K-CG-S: prefetched before the dependency wait
   StreamIn<4> in{{x, r, p, ap}};
-  const bool live = stream_tiles<4, 2>(in, r0, r1, smem, st, [&]() {
+  const bool live = stream_tiles<4, 2, double, 2>(in, r0, r1, smem, st, [&]() {
     alpha = __ldcg(&st->alpha);
     beta = __ldcg(&st->beta);
     return !state_done(st);
@@ -314,7 +314,7 @@ static pk_status tma_setup() {
   static bool done = false;
   if (!done) {
     PK_CUDA(cudaFuncSetAttribute(k_cg_update_tma, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                 stream_smem_bytes<4>()));
+                                 stream_smem_bytes<4, double, 2>()));
     for (auto k : {k_cg_spmv_dots_tma<false>, k_cg_spmv_dots_tma<true>})
       PK_CUDA(cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, csr_smem_bytes()));
     for (auto k : {k_spmv_tma<false>, k_spmv_tma<true>})
@@ -525,7 +525,7 @@ pk_status cg_solve(pk_csr* A, const double* b, double* x, const pk_opts* o, pk_i
     L.ikeys[1] = tma;
     L.body = [=](cudaStream_t cs, Timer* t) {
       if (t) t->begin(PK_SLOT_UPDATE);
-      if (tma) launch_pdl(k_cg_update_tma, Gs, kTileThreads, stream_smem_bytes<4>(), cs, n, xd, r, p, ap, part, dst);
+      if (tma) launch_pdl(k_cg_update_tma, Gs, kTileThreads, stream_smem_bytes<4, double, 2>(), cs, n, xd, r, p, ap, part, dst);
       else k_cg_update<<<Gu, kBlock, 0, cs>>>(ra, xd, r, p, ap);
       if (t) { t->end(); t->begin(PK_SLOT_SPMV_DOTS); }
       if (tma) launch_pdl(irr ? k_cg_spmv_dots_tma<true> : k_cg_spmv_dots_tma<false>, Gt, kTileThreads, csr_smem_bytes(), cs, ct, (const double*)p, ap, part, dst);

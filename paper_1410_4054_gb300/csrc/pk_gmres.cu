@@ -97,6 +97,7 @@ __global__ void __launch_bounds__(kTileThreads, 2) k_gm_start(CsrTiles T, GmArgs
       else if (st->gm_cycle > 0 && st->gm_k == 0) gm_finish(st, PK_BREAKDOWN);
       else {
         st->s[0] = sqrt(t[0]);  // rho0
+        st->s[3] = 1.0 / st->s[0];  // once here, not in every thread of the scaling kernel
         st->s[1] = 0.0;         // sum of xi^2
         st->gm_i = 1;
         st->gm_k = 0;
@@ -119,7 +120,7 @@ __global__ void __launch_bounds__(kTileThreads, 2) k_gm_scale(GmArgs g) {
   double* rc = g.r;
   StreamIn<1> in{{v0}};
   stream_tiles<1, 1>(in, r0, r1, smem, st, [&]() {
-    inv = 1.0 / __ldcg(&st->s[0]);
+    inv = __ldcg(&st->s[3]);
     return gm_step_live(st);
   }, [&](int row, const double2* val, int nv) {
     double2 w = val[0];
@@ -442,6 +443,7 @@ __global__ void __launch_bounds__(kTileThreads, 2) k_gm3(GmArgs g) {
         cond2_set(st, 0u);
       } else {
         g.R[i * kRld + i] = rii;
+        st->s[4] = 1.0 / rii;  // once here, not in every thread of the normalising kernel
       }
       st->counter = 0;
     }
@@ -481,8 +483,8 @@ __global__ void __launch_bounds__(kTileThreads, 2) k_gm4(GmArgs g) {
   double inv = 0.0;
   double v[1] = {0.0};
   StreamIn<2> in{{g.V, vi}};
-  const bool live = stream_tiles<2, 2>(in, r0, r1, smem, st, [&]() {
-    inv = 1.0 / ld_cg(g.R + i * kRld + i);
+  const bool live = stream_tiles<2, 2, double, 4>(in, r0, r1, smem, st, [&]() {
+    inv = __ldcg(&st->s[4]);
     return gm_step_live(st);
   }, [&](int row, const double2* val, int nv) {
     double2 w = val[1];
@@ -518,7 +520,7 @@ __global__ void __launch_bounds__(kBlock) k_gmc_norm(GmArgs g) {
   if (!gm_step_live(st)) return;
   const int i = __ldcg(&st->gm_i);
   double* vi = g.V + (size_t)i * g.ld;
-  const double inv = 1.0 / ld_cg(g.R + i * kRld + i);
+  const double inv = __ldcg(&st->s[4]);
   int r0, r1;
   ew_range(g.n, r0, r1);
   for (int row = r0 + threadIdx.x; row < r1; row += blockDim.x) vi[row] *= inv;
@@ -627,7 +629,7 @@ static pk_status gm_setup() {
     for (auto k : {k_gm_start<false>, k_gm_start<true>, k_gm1<false>, k_gm1<true>})
       PK_CUDA(cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, csr_smem_bytes()));
     PK_CUDA(cudaFuncSetAttribute(k_gm_scale, cudaFuncAttributeMaxDynamicSharedMemorySize, stream_smem_bytes<1>()));
-    PK_CUDA(cudaFuncSetAttribute(k_gm4, cudaFuncAttributeMaxDynamicSharedMemorySize, stream_smem_bytes<2>()));
+    PK_CUDA(cudaFuncSetAttribute(k_gm4, cudaFuncAttributeMaxDynamicSharedMemorySize, stream_smem_bytes<2, double, 4>()));
     PK_CUDA(cudaFuncSetAttribute(k_gm2, cudaFuncAttributeMaxDynamicSharedMemorySize, kBsSmem));
     PK_CUDA(cudaFuncSetAttribute(k_gm3, cudaFuncAttributeMaxDynamicSharedMemorySize, kBsSmem));
     done = true;
@@ -715,7 +717,7 @@ pk_status gmres_solve(pk_csr* A, const double* b, double* x, const pk_opts* o, p
     if (t) t->end();
     if (!classical) {
       if (t) t->begin(PK_SLOT_UPDATE);
-      k_gm4<<<Gs, kTileThreads, stream_smem_bytes<2>(), cs>>>(g);
+      k_gm4<<<Gs, kTileThreads, stream_smem_bytes<2, double, 4>(), cs>>>(g);
       if (t) t->end();
     } else {
       if (t) t->begin(PK_SLOT_BLAS1);

@@ -111,32 +111,34 @@ __device__ __forceinline__ bool arrive_last(unsigned int* counter) {
 }
 
 // Second reduction stage in the last block: out[k] = sum over blocks of partials[k][.], in a
-// fixed order (strided per thread, then the xor tree), broadcast to every thread.
+// fixed order, broadcast to every thread.  One warp does it (two interleaved accumulators
+// per lane, then a butterfly): on GB300 every FP64 instruction that all warps of the block
+// would issue costs the SM's narrow FP64 pipe, and this runs on the critical path.
 template <int NV>
 __device__ __forceinline__ void final_sums(const double* partials, double (&out)[NV]) {
-  __shared__ double sm[NV][32];
+  __shared__ double sm[NV];
   const int G = gridDim.x;
-  double v[NV];
+  if (threadIdx.x < 32) {
+    const int lane = threadIdx.x;
 #pragma unroll
-  for (int k = 0; k < NV; ++k) v[k] = 0.0;
-  for (int i = threadIdx.x; i < G; i += blockDim.x) {
+    for (int k = 0; k < NV; ++k) {
+      const double* pk = partials + (size_t)k * G;
+      double a0 = 0.0, a1 = 0.0;
+      int i = lane;
+      for (; i + 32 < G; i += 64) {
+        a0 += ld_cg(pk + i);
+        a1 += ld_cg(pk + i + 32);
+      }
+      if (i < G) a0 += ld_cg(pk + i);
+      double t = a0 + a1;
 #pragma unroll
-    for (int k = 0; k < NV; ++k) v[k] += ld_cg(partials + (size_t)k * G + i);
-  }
-  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-#pragma unroll
-  for (int k = 0; k < NV; ++k) v[k] = warp_sum(v[k]);
-  if (lane == 0) {
-#pragma unroll
-    for (int k = 0; k < NV; ++k) sm[k][warp] = v[k];
+      for (int o = 16; o > 0; o >>= 1) t += __shfl_xor_sync(0xffffffffu, t, o);
+      if (lane == 0) sm[k] = t;
+    }
   }
   __syncthreads();
 #pragma unroll
-  for (int k = 0; k < NV; ++k) {
-    double t = 0.0;
-    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) t += sm[k][w];
-    out[k] = t;
-  }
+  for (int k = 0; k < NV; ++k) out[k] = sm[k];
 }
 
 __device__ __forceinline__ void trace_put(DevState* st, int i, int slot, double v) {

@@ -117,6 +117,7 @@ __global__ void __launch_bounds__(kBlock) k_mx_residual(MxArgs a) {
       else if (st->gm_cycle >= kMaxOuter || st->iter >= st->maxit) mx_finish(st, PK_NOT_CONVERGED);
       else {
         st->s[0] = sqrt(t[0]);  // ||r||: the inner right-hand side is r / ||r||
+        st->s[5] = 1.0 / st->s[0];
         st->gm_cycle += 1;
         st->gm_phase = 1;
         if (st->use_cond) cudaGraphSetConditional(st->cond2, 1u);
@@ -130,7 +131,7 @@ __global__ void __launch_bounds__(kBlock) k_mx_residual(MxArgs a) {
 __global__ void __launch_bounds__(kBlock) k_mx_prep(MxArgs a) {
   DevState* st = a.st;
   if (state_done(st)) return;
-  const double inv = 1.0 / __ldcg(&st->s[0]);
+  const double inv = __ldcg(&st->s[5]);
   int r0, r1;
   ew_range(a.n, r0, r1);
   FF acc{0.0f, 0.0f};
@@ -270,7 +271,7 @@ __global__ void __launch_bounds__(kTileThreads, 2) k_mx_update_tma(MxArgs a) {
   FF acc{0.0f, 0.0f};
   // d and r do not depend on the preceding K-CG-S: prefetched before the dependency wait
   StreamIn<4, float> in{{a.d, a.r, a.p, a.ap}};
-  const bool live = stream_tiles<4, 2>(in, r0, r1, smem, st, [&]() {
+  const bool live = stream_tiles<4, 2, float, 2>(in, r0, r1, smem, st, [&]() {
     af = (float)__ldcg(&st->alpha);
     bf = (float)__ldcg(&st->beta);
     return mx_inner_live(st);
@@ -323,7 +324,7 @@ static pk_status mx_tma_setup() {
     for (auto k : {k_mx_spmv_tma<false>, k_mx_spmv_tma<true>})
       PK_CUDA(cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, csr_smem_bytes()));
     PK_CUDA(cudaFuncSetAttribute(k_mx_update_tma, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                 stream_smem_bytes<4, float>()));
+                                 stream_smem_bytes<4, float, 2>()));
     done = true;
   }
   return PK_OK;
@@ -422,7 +423,7 @@ pk_status cg_mixed(pk_csr* A, const double* b, double* x, const pk_opts* o, pk_i
     if (tma) launch_pdl(irr ? k_mx_spmv_tma<true> : k_mx_spmv_tma<false>, Gt, kTileThreads, csr_smem_bytes(), cs, ct, a);
     else k_mx_spmv<<<G, kBlock, 0, cs>>>(a);
     if (t) { t->end(); t->begin(PK_SLOT_UPDATE); }
-    if (tma) launch_pdl(k_mx_update_tma, Gs, kTileThreads, stream_smem_bytes<4, float>(), cs, a);
+    if (tma) launch_pdl(k_mx_update_tma, Gs, kTileThreads, stream_smem_bytes<4, float, 2>(), cs, a);
     else k_mx_update<<<Ge, kBlock, 0, cs>>>(a);
     if (t) t->end();
   };

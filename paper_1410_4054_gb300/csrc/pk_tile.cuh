@@ -160,18 +160,20 @@ struct StreamIn {
 
 constexpr int kStreamRows = 512;  // rows per streaming tile: 2 per consumer thread
 
-// Stages of the streaming ring: as many as fit in ~96 KB (two blocks per SM), 2..8.
-template <int NIN, class ET = double>
+// Stages of the streaming ring: as many as fit in ~96 KB (two blocks per SM), 2..8.  U row
+// pairs per consumer thread per stage (kStreamRows * U rows): light kernels take several so
+// that the per-stage barrier traffic is amortised over more work.
+template <int NIN, class ET = double, int U = 1>
 __host__ __device__ constexpr int stream_stages() {
-  return (98304 / (NIN * kStreamRows * (int)sizeof(ET))) > 8 ? 8
-         : (98304 / (NIN * kStreamRows * (int)sizeof(ET))) < 2
+  return (98304 / (NIN * kStreamRows * U * (int)sizeof(ET))) > 8 ? 8
+         : (98304 / (NIN * kStreamRows * U * (int)sizeof(ET))) < 2
              ? 2
-             : (98304 / (NIN * kStreamRows * (int)sizeof(ET)));
+             : (98304 / (NIN * kStreamRows * U * (int)sizeof(ET)));
 }
 
-template <int NIN, class ET = double>
+template <int NIN, class ET = double, int U = 1>
 __host__ __device__ constexpr int stream_smem_bytes() {
-  return stream_stages<NIN, ET>() * NIN * kStreamRows * (int)sizeof(ET) + 2 * stream_stages<NIN, ET>() * 8;
+  return stream_stages<NIN, ET, U>() * NIN * kStreamRows * U * (int)sizeof(ET) + 2 * stream_stages<NIN, ET, U>() * 8;
 }
 
 // Runs the streaming pipeline.  The first NPRE inputs do not depend on the preceding
@@ -183,15 +185,16 @@ __host__ __device__ constexpr int stream_smem_bytes() {
 // (vals[k] = the pair of input k at rows row, row+1; nvalid = 1 or 2).  Returns, in consumer
 // threads, whether the solve was live (a timed-out wait is recorded in the state and ends the
 // loop early).  ET is the element type (double, or float for the mixed-precision inner loop).
-template <int NIN, int NPRE, class ET = double, class Setup, class Body>
+template <int NIN, int NPRE, class ET = double, int U = 1, class Setup, class Body>
 __device__ __forceinline__ bool stream_tiles(const StreamIn<NIN, ET>& in, int r0, int r1,
                                              unsigned char* smem, DevState* st, Setup&& setup,
                                              Body&& body) {
   using P2 = typename Pair<ET>::type;
-  constexpr int kStreamStages = stream_stages<NIN, ET>();
+  constexpr int kStreamStages = stream_stages<NIN, ET, U>();
+  constexpr int kRows = kStreamRows * U;  // rows per stage
   constexpr int kPerUnit = 16 / (int)sizeof(ET);  // elements per 16-byte copy unit
   ET* buf = reinterpret_cast<ET*>(smem);
-  uint64_t* full = reinterpret_cast<uint64_t*>(smem + (size_t)kStreamStages * NIN * kStreamRows * sizeof(ET));
+  uint64_t* full = reinterpret_cast<uint64_t*>(smem + (size_t)kStreamStages * NIN * kRows * sizeof(ET));
   uint64_t* empty = full + kStreamStages;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   if (threadIdx.x == 0) {
@@ -202,20 +205,20 @@ __device__ __forceinline__ bool stream_tiles(const StreamIn<NIN, ET>& in, int r0
     mbar_fence_init();
   }
   __syncthreads();
-  const int ntiles = r1 > r0 ? (r1 - r0 + kStreamRows - 1) / kStreamRows : 0;
+  const int ntiles = r1 > r0 ? (r1 - r0 + kRows - 1) / kRows : 0;
   const int npro = min(kStreamStages, ntiles);
   auto tile_bytes = [&](int t) {
-    const int rows = min(kStreamRows, r1 - (r0 + t * kStreamRows));
+    const int rows = min(kRows, r1 - (r0 + t * kRows));
     return (uint32_t)(((rows + kPerUnit - 1) / kPerUnit) * 16);  // whole 16-byte units
   };
   auto issue = [&](int t, int k0, int k1) {
     const int s = t % kStreamStages;
-    const int row0 = r0 + t * kStreamRows;
+    const int row0 = r0 + t * kRows;
     const uint32_t bytes = tile_bytes(t);
 #pragma unroll
     for (int k = 0; k < NIN; ++k)
       if (k >= k0 && k < k1)
-        bulk_load(buf + ((size_t)s * NIN + k) * kStreamRows, in.v[k] + row0, bytes, &full[s]);
+        bulk_load(buf + ((size_t)s * NIN + k) * kRows, in.v[k] + row0, bytes, &full[s]);
   };
   bool ok = true;
   if (warp == kConsumerWarps) {
@@ -258,15 +261,18 @@ __device__ __forceinline__ bool stream_tiles(const StreamIn<NIN, ET>& in, int r0
     const int s = t % kStreamStages;
     if (!mbar_wait(&full[s], (t / kStreamStages) & 1)) { report_timeout(st); break; }
     if (live) {
-      const int row0 = r0 + t * kStreamRows;
-      const int rows = min(kStreamRows, r1 - row0);
-      const int i = 2 * threadIdx.x;  // consumer thread -> row pair
-      if (i < rows) {
-        P2 vals[NIN];
+      const int row0 = r0 + t * kRows;
+      const int rows = min(kRows, r1 - row0);
 #pragma unroll
-        for (int k = 0; k < NIN; ++k)
-          vals[k] = *reinterpret_cast<const P2*>(buf + ((size_t)s * NIN + k) * kStreamRows + i);
-        body(row0 + i, vals, min(2, rows - i));
+      for (int u = 0; u < U; ++u) {
+        const int i = 2 * ((int)threadIdx.x + u * kConsumers);  // consumer thread -> row pairs
+        if (i < rows) {
+          P2 vals[NIN];
+#pragma unroll
+          for (int k = 0; k < NIN; ++k)
+            vals[k] = *reinterpret_cast<const P2*>(buf + ((size_t)s * NIN + k) * kRows + i);
+          body(row0 + i, vals, min(2, rows - i));
+        }
       }
     }
     __syncwarp();
