@@ -217,6 +217,23 @@ def dist():
     return ws, rank, local
 
 
+def max_over_ranks(x: float, pg, device) -> float:
+    """The job's time is the slowest replica's: all-reduce MAX over the process group (the
+    replicas share nothing else; there is no data-path collective)."""
+    if pg is None:
+        return x
+    import torch
+
+    t = torch.tensor([x], dtype=torch.float64, device=device)
+    pg.all_reduce(t, op=pg.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_value(ws: int, bytes_per_replica: float, seconds: float) -> float:
+    """Whole-job GB/s: every replica moves the same algorithmic bytes in the job's time."""
+    return ws * bytes_per_replica / seconds / 1e9
+
+
 # ------------------------------------------------------------------ CPU oracle arm
 
 def oracle_sample(a, b, iters: int) -> tuple[float, float]:
@@ -307,15 +324,12 @@ def run_ours(args):
     e1.record(stream)
     torch.cuda.synchronize()
     clk = clocks.stop()
-    ms = e0.elapsed_time(e1) / args.steps
+    ms = max_over_ranks(e0.elapsed_time(e1) / args.steps, pg, dev)
     if pg:
-        t = torch.tensor([ms], device=dev)
-        pg.all_reduce(t, op=pg.ReduceOp.MAX)
-        ms = float(t.item())
         pg.barrier()
     it = iters[-1]
     bps = bytes_per_solve(a.n, a.nnz, it)
-    value = ws * bps / (ms * 1e-3) / 1e9
+    value = job_value(ws, bps, ms * 1e-3)
 
     # end to end through the C ABI with pinned host buffers
     bh = torch.from_numpy(b).pin_memory()
@@ -331,12 +345,8 @@ def run_ours(args):
         xh.zero_()
         pk.cg_solve(A, bh, xh, **kw)
     torch.cuda.synchronize()
-    e2e_s = (time.perf_counter() - t0) / args.steps
-    if pg:
-        t = torch.tensor([e2e_s], device=dev)
-        pg.all_reduce(t, op=pg.ReduceOp.MAX)
-        e2e_s = float(t.item())
-    e2e = {"value": ws * bps / e2e_s / 1e9, "unit": UNIT, "h2d_bytes_per_step": 16 * a.n,
+    e2e_s = max_over_ranks((time.perf_counter() - t0) / args.steps, pg, dev)
+    e2e = {"value": job_value(ws, bps, e2e_s), "unit": UNIT, "h2d_bytes_per_step": 16 * a.n,
            "d2h_bytes_per_step": 8 * a.n, "ms_per_step": 1e3 * e2e_s}
 
     if rank != 0:
