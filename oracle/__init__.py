@@ -44,6 +44,9 @@ def lib():
             f = getattr(L, name)
             f.argtypes = common + [_dp, _dp, _dp, C.POINTER(C.c_int32)]
             f.restype = C.c_int
+        L.orc_pcg_jacobi.argtypes = [C.c_int32, _i32p, _i32p, _f64p, _f64p, _f64p, C.c_double, C.c_int32,
+                                     C.c_int32, C.c_int32, _dp, _dp, _dp, C.POINTER(C.c_int32)]
+        L.orc_pcg_jacobi.restype = C.c_int
         L.orc_bicgstab_classical.argtypes = common + [_dp, _dp, _dp, _dp, C.POINTER(C.c_int32)]
         L.orc_bicgstab_classical.restype = C.c_int
         L.orc_bicgstab_pipelined.argtypes = common + [_dp, _dp, _dp, _dp, _dp, C.POINTER(C.c_int32)]
@@ -90,6 +93,20 @@ def cg(a, b, x0=None, tol=1e-8, maxit=1000, variant="pipelined", cap=None):
     f = lib().orc_cg_pipelined if variant == "pipelined" else lib().orc_cg_classical
     st = f(n, rp, ci, va, b, x, tol, maxit, cap, _ptr(tr["alpha"]), _ptr(tr["beta"]),
            _ptr(tr["res2"]), C.byref(it))
+    return dict(x=x, iters=it.value, status=st, **tr)
+
+
+def pcg_jacobi(a, b, x0=None, tol=1e-8, maxit=1000, variant="pipelined", cap=None):
+    """CG with the Jacobi preconditioner diag(A): standard (variant='classical') or in the
+    pipelined structure of Algorithm 2 (variant='pipelined')."""
+    n, rp, ci, va = _csr(a)
+    cap = maxit + 1 if cap is None else cap
+    b = np.ascontiguousarray(b, dtype=np.float64)
+    x = np.zeros(n) if x0 is None else np.array(x0, dtype=np.float64, copy=True)
+    tr = {k: np.full(cap, np.nan) for k in ("alpha", "beta", "res2")}
+    it = C.c_int32(0)
+    st = lib().orc_pcg_jacobi(n, rp, ci, va, b, x, tol, maxit, 1 if variant == "pipelined" else 0, cap,
+                              _ptr(tr["alpha"]), _ptr(tr["beta"]), _ptr(tr["res2"]), C.byref(it))
     return dict(x=x, iters=it.value, status=st, **tr)
 
 

@@ -17,6 +17,11 @@
  *   orc_gmres               Algorithms 5 and 6 (restarted simpler GMRES with classical
  *                           Gram-Schmidt; classical form updates the residual, pipelined
  *                           form uses xi_i = <v_0, v_i>)
+ *   orc_pcg_jacobi          CG with the Jacobi preconditioner M = diag(A) (Sec. 5 names
+ *                           preconditioner fusion as the natural extension): the standard
+ *                           preconditioned CG, and the pipelined form of Algorithm 2 with
+ *                           the preconditioned inner products, beta from the analogue of
+ *                           Eq. (3): beta = alpha^2 <Ap, M^-1 Ap> / <r, M^-1 r> - 1.
  *
  * Readings of points the paper leaves open (they are listed with reasons in the design
  * notes of the repository):
@@ -179,6 +184,115 @@ int orc_cg_pipelined(int32_t n, const int32_t* rp, const int32_t* ci, const doub
   }
 done:
   free(r); free(p); free(ap);
+  return status;
+}
+
+/* ---------------------------------------------------------------- Jacobi-preconditioned CG */
+
+/* M^-1 = diag(A)^-1, applied as a product with the reciprocal of every diagonal entry
+ * (entries of a row in column i summed).  A zero or negative diagonal entry cannot belong to
+ * an SPD matrix: NOT_SPD. */
+static int jacobi_inverse(int32_t n, const int32_t* rp, const int32_t* ci, const double* va,
+                          double* dinv) {
+  for (int32_t i = 0; i < n; ++i) {
+    double d = 0.0;
+    for (int32_t j = rp[i]; j < rp[i + 1]; ++j)
+      if (ci[j] == i) d += va[j];
+    if (!(d > 0.0)) return ORC_NOT_SPD;
+    dinv[i] = 1.0 / d;
+  }
+  return ORC_OK;
+}
+
+/* Preconditioned CG with M = diag(A).  Classical (pipelined = 0): z = M^-1 r, gamma = <r, z>,
+ * alpha = gamma / <p, Ap>, beta = gamma_{i+1} / gamma_i, p = z + beta p.  Pipelined
+ * (pipelined = 1): the structure of Algorithm 2 -- the update step forms x, r and
+ * p = M^-1 r + beta p with <r, M^-1 r> and <r, r>; the SpMV step forms Ap with <p, Ap> and
+ * <Ap, M^-1 Ap>, and alpha = <r, M^-1 r>/<p, Ap>, beta = alpha^2 <Ap, M^-1 Ap>/<r, M^-1 r> - 1.
+ * The stopping test is on the unpreconditioned ||r||.  The traces record alpha_i, beta_i and
+ * <r_i, r_i>. */
+int orc_pcg_jacobi(int32_t n, const int32_t* rp, const int32_t* ci, const double* va,
+                   const double* b, double* x, double tol, int32_t maxit, int32_t pipelined,
+                   int32_t cap, double* tr_alpha, double* tr_beta, double* tr_res2,
+                   int32_t* iters_out) {
+  *iters_out = 0;
+  if (n <= 0) return ORC_OK;
+  double bb = orc_dot(n, b, b);
+  if (bb == 0.0) { memset(x, 0, sizeof(double) * (size_t)n); return ORC_OK; }
+  double thr2 = tol * tol * bb;
+  size_t sz = sizeof(double) * (size_t)n;
+  double *r = malloc(sz), *p = malloc(sz), *ap = malloc(sz), *z = malloc(sz), *dinv = malloc(sz);
+  if (!r || !p || !ap || !z || !dinv) { free(r); free(p); free(ap); free(z); free(dinv); return ORC_ERR_OOM; }
+  int status = jacobi_inverse(n, rp, ci, va, dinv);
+  if (status != ORC_OK) goto done;
+  status = ORC_NOT_CONVERGED;
+  /* r0 = b - A x0, z0 = M^-1 r0, p0 = z0 */
+  orc_spmv(n, rp, ci, va, x, ap);
+  for (int32_t k = 0; k < n; ++k) { r[k] = b[k] - ap[k]; z[k] = r[k] * dinv[k]; p[k] = z[k]; }
+  double rr = orc_dot(n, r, r);
+  double gamma = orc_dot(n, r, z);
+  if (!isfinite(rr) || !isfinite(gamma)) { status = ORC_NAN; goto done; }
+  if (rr <= thr2) { status = ORC_OK; goto done; }
+  if (!pipelined) {
+    for (int32_t i = 0; i < maxit; ++i) {
+      orc_spmv(n, rp, ci, va, p, ap);
+      const double pap = orc_dot(n, p, ap);
+      if (!finite3(pap, gamma, rr)) { status = ORC_NAN; break; }
+      if (pap <= 0.0) { status = ORC_NOT_SPD; break; }
+      const double alpha = gamma / pap;
+      record(tr_alpha, cap, i, alpha);
+      for (int32_t k = 0; k < n; ++k) x[k] += alpha * p[k];
+      for (int32_t k = 0; k < n; ++k) r[k] -= alpha * ap[k];
+      rr = orc_dot(n, r, r);
+      record(tr_res2, cap, i, rr);
+      *iters_out = i + 1;
+      if (!isfinite(rr)) { status = ORC_NAN; break; }
+      if (rr <= thr2) { status = ORC_OK; break; }
+      for (int32_t k = 0; k < n; ++k) z[k] = r[k] * dinv[k];
+      const double gnew = orc_dot(n, r, z);
+      const double beta = gnew / gamma;
+      record(tr_beta, cap, i, beta);
+      gamma = gnew;
+      for (int32_t k = 0; k < n; ++k) p[k] = z[k] + beta * p[k];
+    }
+    goto done;
+  }
+  /* pipelined: A p0, alpha_0, beta_0 */
+  orc_spmv(n, rp, ci, va, p, ap);
+  for (int32_t k = 0; k < n; ++k) z[k] = ap[k] * dinv[k];
+  double qdq = orc_dot(n, ap, z);                 /* <Ap, M^-1 Ap> */
+  double pap = orc_dot(n, p, ap);
+  if (!finite3(qdq, pap, gamma)) { status = ORC_NAN; goto done; }
+  if (pap <= 0.0) { status = ORC_NOT_SPD; goto done; }
+  double alpha = gamma / pap;
+  double beta = alpha * alpha * qdq / gamma - 1.0;
+  record(tr_alpha, cap, 0, alpha);
+  record(tr_beta, cap, 0, beta);
+  for (int32_t i = 1; i <= maxit; ++i) {
+    for (int32_t k = 0; k < n; ++k) x[k] += alpha * p[k];
+    for (int32_t k = 0; k < n; ++k) r[k] -= alpha * ap[k];
+    for (int32_t k = 0; k < n; ++k) p[k] = r[k] * dinv[k] + beta * p[k];
+    for (int32_t k = 0; k < n; ++k) z[k] = r[k] * dinv[k];
+    gamma = orc_dot(n, r, z);                     /* <r_i, M^-1 r_i> */
+    rr = orc_dot(n, r, r);                        /* <r_i, r_i> */
+    record(tr_res2, cap, i - 1, rr);
+    *iters_out = i;
+    if (!isfinite(rr) || !isfinite(gamma)) { status = ORC_NAN; break; }
+    if (rr <= thr2) { status = ORC_OK; break; }
+    if (i == maxit) break;
+    orc_spmv(n, rp, ci, va, p, ap);
+    for (int32_t k = 0; k < n; ++k) z[k] = ap[k] * dinv[k];
+    qdq = orc_dot(n, ap, z);
+    pap = orc_dot(n, p, ap);
+    if (!finite3(qdq, pap, gamma)) { status = ORC_NAN; break; }
+    if (pap <= 0.0) { status = ORC_NOT_SPD; break; }
+    alpha = gamma / pap;
+    beta = alpha * alpha * qdq / gamma - 1.0;
+    record(tr_alpha, cap, i, alpha);
+    record(tr_beta, cap, i, beta);
+  }
+done:
+  free(r); free(p); free(ap); free(z); free(dinv);
   return status;
 }
 
