@@ -102,7 +102,16 @@ typedef struct {
   double* trace;       /* optional DEVICE array [trace_cap][4]: per iteration i the solver
                           writes {alpha_i, beta_i, omega_i, res2_i} (unused slots untouched);
                           GMRES writes {R_{i-1,i}, R_{i,i}, xi_i, estimate_i} */
+  int32_t precond;     /* PK_PRECOND_*: CG only (0 = none) */
 } pk_opts;
+
+/* pk_opts.precond.  JACOBI: M = diag(A), pipelined FP64 CG (Alg. 2 with the preconditioned
+ * inner products <r, M^-1 r> and <Ap, M^-1 Ap>; beta = alpha^2 <Ap, M^-1 Ap>/<r, M^-1 r> - 1)
+ * on the graph or host loop; the fused SpMV kernel forms Ap, <p, Ap>, <Ap, M^-1 Ap>, the
+ * update kernel x, r, p = M^-1 r + beta p, <r, M^-1 r> and <r, r>.  The stopping test stays
+ * ||r|| <= tol ||b||.  A diagonal entry <= 0 returns PK_NOT_SPD.  Other variants, precisions
+ * and the persistent loop return PK_ERR_ARG (PK_LOOP_AUTO uses the graph loop). */
+enum { PK_PRECOND_NONE = 0, PK_PRECOND_JACOBI = 1 };
 
 /* Per-kernel timing slots in pk_info (PK_FLAG_TIMING). */
 #define PK_MAX_KERNEL_SLOTS 8

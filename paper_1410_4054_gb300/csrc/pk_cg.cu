@@ -405,6 +405,8 @@ __global__ void __launch_bounds__(kBlock) k_xpay_beta(RowArgs a, const double* _
 pk_status cg_mixed(pk_csr* A, const double* b, double* x, const pk_opts* o, pk_info* info,
                    cudaStream_t s);
 bool persistent_usable(const pk_csr* A, const pk_opts* o);
+pk_status pcg_jacobi_solve(pk_csr* A, const double* b, double* x, const pk_opts* o, pk_info* info,
+                           cudaStream_t s);
 pk_status launch_cg_persistent(pk_csr* A, double* x, double* r, double* p, double* ap,
                                cudaStream_t s);
 
@@ -415,6 +417,8 @@ pk_status cg_solve(pk_csr* A, const double* b, double* x, const pk_opts* o, pk_i
   *info = pk_info{};
   info->rel_res_true = -1.0;
   if (A->n == 0) return PK_OK;
+  if (o->precond == PK_PRECOND_JACOBI) return pcg_jacobi_solve(A, b, x, o, info, s);
+  if (o->precond != PK_PRECOND_NONE) { set_error("bad precond"); return PK_ERR_ARG; }
   if (o->precision == PK_PREC_MIXED) return cg_mixed(A, b, x, o, info, s);
   if (o->precision != PK_PREC_FP64) { set_error("precision must be PK_PREC_FP64 or PK_PREC_MIXED"); return PK_ERR_ARG; }
   if (o->variant < 0 || o->variant > 2) { set_error("bad variant"); return PK_ERR_ARG; }

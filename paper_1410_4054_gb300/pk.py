@@ -35,7 +35,7 @@ class Opts(C.Structure):
     _fields_ = [("tol", C.c_double), ("maxit", C.c_int32), ("restart", C.c_int32),
                 ("variant", C.c_int32), ("precision", C.c_int32), ("loop", C.c_int32),
                 ("check_every", C.c_int32), ("flags", C.c_uint32), ("trace_cap", C.c_int32),
-                ("trace", C.c_void_p)]
+                ("trace", C.c_void_p), ("precond", C.c_int32)]
 
 
 class Info(C.Structure):
@@ -198,9 +198,13 @@ class CSRMatrix:
             pass
 
 
+PRECONDS = {"none": 0, "jacobi": 1}
+
+
 def make_opts(tol=1e-8, maxit=1000, restart=30, variant="pipelined", precision="fp64",
-              loop="auto", check_every=0, flags=0, trace=None) -> Opts:
+              loop="auto", check_every=0, flags=0, trace=None, precond="none") -> Opts:
     o = Opts()
+    o.precond = PRECONDS[precond] if isinstance(precond, str) else int(precond)
     o.tol = tol
     o.maxit = maxit
     o.restart = restart

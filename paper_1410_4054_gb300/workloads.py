@@ -190,6 +190,41 @@ def power_law(n: int, seed: int = 0, lmin: int = 3, lmax: int = 256, mean: float
     )
 
 
+def spd_power_law(n: int, seed: int = 0, lmin: int = 3, lmax: int = 256, mean: float = 12.0) -> CSR:
+    """Symmetric positive definite matrix with power-law row lengths.
+
+    The off-diagonal part of ``power_law(n, seed, ...)`` plus its transpose (coincident
+    entries summed); the diagonal is 1.1 times the row's absolute off-diagonal sum plus 1
+    (strict diagonal dominance, so SPD).  Rows average about 2 * (mean - 1) + 1 entries and the
+    longest reach past ``lmax``.
+    """
+    p = power_law(n, seed, lmin, lmax, mean)
+    rows = np.repeat(np.arange(n, dtype=np.int64), np.diff(p.row_ptr))
+    cols = p.col.astype(np.int64)
+    off = cols != rows
+    r, c, v = rows[off], cols[off], p.val[off]
+    key, inv = np.unique(np.concatenate([r * n + c, c * n + r]), return_inverse=True)
+    vals = np.bincount(inv, weights=np.concatenate([v, v]))
+    ur, uc = key // n, key % n
+    absum = np.bincount(ur, weights=np.abs(vals), minlength=n)
+    d = np.arange(n, dtype=np.int64)
+    return _from_coo(n, np.concatenate([ur, d]), np.concatenate([uc, d]),
+                     np.concatenate([vals, 1.1 * absum + 1.0]), f"spdpowerlaw_{n}")
+
+
+def diag_scaled(a: CSR, seed: int = 0, spread: float = 100.0) -> CSR:
+    """D A D with D = diag(d), ln d uniform on [0, ln spread) from splitmix64(seed).
+
+    Keeps A's sparsity and definiteness while its diagonal spans a factor spread^2: the
+    badly scaled systems (cell coefficients that vary over orders of magnitude) on which the
+    Jacobi preconditioner diag(A) pays.
+    """
+    d = np.exp(0.5 * (uniform_pm1(seed, a.n) + 1.0) * np.log(spread))
+    rows = np.repeat(np.arange(a.n, dtype=np.int64), np.diff(a.row_ptr))
+    return CSR(a.n, a.row_ptr.copy(), a.col.copy(), a.val * d[rows] * d[a.col],
+               f"{a.name}_scaled{spread:g}")
+
+
 def random_uniform(n: int, per_row: int, seed: int = 0) -> CSR:
     """``per_row`` distinct uniformly random columns per row, diagonal included, values N(0,1)
     and a dominant diagonal (the random matrices of the fused SpMV + dot experiment)."""
