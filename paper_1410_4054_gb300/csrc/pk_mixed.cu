@@ -325,6 +325,9 @@ static pk_status mx_tma_setup() {
       PK_CUDA(cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, csr_smem_bytes()));
     PK_CUDA(cudaFuncSetAttribute(k_mx_update_tma, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                  stream_smem_bytes<4, float, 2>()));
+    // two blocks of up to 113 KB each need the largest shared-memory carveout
+    PK_CUDA(cudaFuncSetAttribute(k_mx_update_tma, cudaFuncAttributePreferredSharedMemoryCarveout,
+                                 (int)cudaSharedmemCarveoutMaxShared));
     done = true;
   }
   return PK_OK;

@@ -16,6 +16,8 @@ namespace pk {
 
 namespace {
 
+constexpr int kPcgRowPairs = 1;  // row pairs per consumer thread per stage of K-PCG-U
+
 // dinv = 1 / diag(A); a diagonal entry that is not > 0 ends the solve with PK_NOT_SPD.
 __global__ void __launch_bounds__(kBlock) k_jacobi_inverse(RowArgs a, double* __restrict__ dinv) {
   const int r0 = a.rowblk[blockIdx.x], r1 = a.rowblk[blockIdx.x + 1];
@@ -128,7 +130,7 @@ __global__ void __launch_bounds__(kTileThreads, 2) k_pcg_update_tma(int n, doubl
   double v[2] = {0.0, 0.0};
   double alpha = 0.0, beta = 0.0;
   StreamIn<5> in{{x, r, dinv, p, ap}};
-  const bool live = stream_tiles<5, 3, double, 1>(in, r0, r1, smem, st, [&]() {
+  const bool live = stream_tiles<5, 3, double, kPcgRowPairs>(in, r0, r1, smem, st, [&]() {
     alpha = __ldcg(&st->alpha);
     beta = __ldcg(&st->beta);
     return !state_done(st);
@@ -189,7 +191,10 @@ pk_status pcg_setup() {
     for (auto k : {k_pcg_spmv_dots_tma<false>, k_pcg_spmv_dots_tma<true>})
       PK_CUDA(cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, csr_smem_bytes()));
     PK_CUDA(cudaFuncSetAttribute(k_pcg_update_tma, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                 stream_smem_bytes<5>()));
+                                 stream_smem_bytes<5, double, kPcgRowPairs>()));
+    // two blocks of up to 113 KB each need the largest shared-memory carveout
+    PK_CUDA(cudaFuncSetAttribute(k_pcg_update_tma, cudaFuncAttributePreferredSharedMemoryCarveout,
+                                 (int)cudaSharedmemCarveoutMaxShared));
     done = true;
   }
   return PK_OK;
@@ -264,7 +269,7 @@ pk_status pcg_jacobi_solve(pk_csr* A, const double* b, double* x, const pk_opts*
   L.unroll = 4;
   L.body = [=](cudaStream_t cs, Timer* t) {
     if (t) t->begin(PK_SLOT_UPDATE);
-    launch_pdl(k_pcg_update_tma, Gs, kTileThreads, stream_smem_bytes<5>(), cs, n, xd, r, p, (const double*)ap,
+    launch_pdl(k_pcg_update_tma, Gs, kTileThreads, stream_smem_bytes<5, double, kPcgRowPairs>(), cs, n, xd, r, p, (const double*)ap,
                (const double*)dinv, part, dst);
     if (t) { t->end(); t->begin(PK_SLOT_SPMV_DOTS); }
     launch_pdl(irr ? k_pcg_spmv_dots_tma<true> : k_pcg_spmv_dots_tma<false>, Gt, kTileThreads, csr_smem_bytes(),

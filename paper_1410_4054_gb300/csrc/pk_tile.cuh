@@ -160,15 +160,19 @@ struct StreamIn {
 
 constexpr int kStreamRows = 512;  // rows per streaming tile: 2 per consumer thread
 
-// Stages of the streaming ring: as many as fit in ~96 KB (two blocks per SM), 2..8.  U row
-// pairs per consumer thread per stage (kStreamRows * U rows): light kernels take several so
-// that the per-stage barrier traffic is amortised over more work.
+// Stages of the streaming ring: as many as fit in kStreamBudget bytes, 2..8.  U row pairs
+// per consumer thread per stage (kStreamRows * U rows): light kernels take several so that the
+// per-stage barrier traffic is amortised over more work.  96 KB keeps two blocks per SM; a
+// 112 KB ring measured no faster on GB300 (the 5-input update kernel is bound by FP64 issue
+// as much as by HBM).
+constexpr int kStreamBudget = 98304;
+
 template <int NIN, class ET = double, int U = 1>
 __host__ __device__ constexpr int stream_stages() {
-  return (98304 / (NIN * kStreamRows * U * (int)sizeof(ET))) > 8 ? 8
-         : (98304 / (NIN * kStreamRows * U * (int)sizeof(ET))) < 2
+  return (kStreamBudget / (NIN * kStreamRows * U * (int)sizeof(ET))) > 8 ? 8
+         : (kStreamBudget / (NIN * kStreamRows * U * (int)sizeof(ET))) < 2
              ? 2
-             : (98304 / (NIN * kStreamRows * U * (int)sizeof(ET)));
+             : (kStreamBudget / (NIN * kStreamRows * U * (int)sizeof(ET)));
 }
 
 template <int NIN, class ET = double, int U = 1>
