@@ -55,6 +55,10 @@ def lib():
                                 C.c_int32, C.c_int32, C.c_int32, C.c_int32, _dp, _dp, _dp, _dp,
                                 C.POINTER(C.c_int32), C.POINTER(C.c_int32)]
         L.orc_gmres.restype = C.c_int
+        L.orc_jacobi_right_begin.argtypes = [C.c_int32, _i32p, _i32p, _f64p, _f64p, _f64p, _f64p]
+        L.orc_jacobi_right_begin.restype = C.c_int
+        L.orc_jacobi_right_end.argtypes = [C.c_int32, _f64p, _f64p]
+        L.orc_jacobi_right_end.restype = None
         _lib = L
     return _lib
 
@@ -110,12 +114,26 @@ def pcg_jacobi(a, b, x0=None, tol=1e-8, maxit=1000, variant="pipelined", cap=Non
     return dict(x=x, iters=it.value, status=st, **tr)
 
 
-def bicgstab(a, b, x0=None, tol=1e-8, maxit=1000, variant="pipelined", cap=None):
-    """Algorithm 3 (variant='classical') or Algorithm 4 (variant='pipelined')."""
+def _right_jacobi(n, rp, ci, va, x, precond):
+    """precond='jacobi': the values of A M^-1 and M^-1 (M = diag(A)), x <- M x; else as given."""
+    if precond == "none":
+        return va, None
+    if precond != "jacobi":
+        raise ValueError(f"precond {precond!r}")
+    va_r, dinv = np.empty_like(va), np.empty(n)
+    if lib().orc_jacobi_right_begin(n, rp, ci, va, x, va_r, dinv) != OK:
+        raise ValueError("the Jacobi preconditioner needs a nonzero finite diagonal")
+    return va_r, dinv
+
+
+def bicgstab(a, b, x0=None, tol=1e-8, maxit=1000, variant="pipelined", cap=None, precond="none"):
+    """Algorithm 3 (variant='classical') or Algorithm 4 (variant='pipelined');
+    precond='jacobi': right-preconditioned with M = diag(A) (run on A M^-1, x = M^-1 y)."""
     n, rp, ci, va = _csr(a)
     cap = maxit + 1 if cap is None else cap
     b = np.ascontiguousarray(b, dtype=np.float64)
     x = np.zeros(n) if x0 is None else np.array(x0, dtype=np.float64, copy=True)
+    va, dinv = _right_jacobi(n, rp, ci, va, x, precond)
     tr = {k: np.full(cap, np.nan) for k in ("alpha", "beta", "omega", "res2", "res2_est")}
     it = C.c_int32(0)
     if variant == "pipelined":
@@ -126,15 +144,19 @@ def bicgstab(a, b, x0=None, tol=1e-8, maxit=1000, variant="pipelined", cap=None)
         st = lib().orc_bicgstab_classical(n, rp, ci, va, b, x, tol, maxit, cap, _ptr(tr["alpha"]),
                                           _ptr(tr["beta"]), _ptr(tr["omega"]), _ptr(tr["res2"]),
                                           C.byref(it))
+    if dinv is not None:
+        lib().orc_jacobi_right_end(n, dinv, x)
     return dict(x=x, iters=it.value, status=st, **tr)
 
 
-def gmres(a, b, x0=None, tol=1e-8, maxit=1000, m=30, variant="pipelined", cap=None):
-    """Algorithm 6 (variant='pipelined') or Algorithm 5 (variant='classical'), restarted."""
+def gmres(a, b, x0=None, tol=1e-8, maxit=1000, m=30, variant="pipelined", cap=None, precond="none"):
+    """Algorithm 6 (variant='pipelined') or Algorithm 5 (variant='classical'), restarted;
+    precond='jacobi': right-preconditioned with M = diag(A) (run on A M^-1, x = M^-1 y)."""
     n, rp, ci, va = _csr(a)
     cap = maxit + 2 if cap is None else cap
     b = np.ascontiguousarray(b, dtype=np.float64)
     x = np.zeros(n) if x0 is None else np.array(x0, dtype=np.float64, copy=True)
+    va, dinv = _right_jacobi(n, rp, ci, va, x, precond)
     R = np.zeros((m, m))
     xi = np.zeros(m)
     est = np.full(cap, np.nan)
@@ -142,4 +164,6 @@ def gmres(a, b, x0=None, tol=1e-8, maxit=1000, m=30, variant="pipelined", cap=No
     it, cyc = C.c_int32(0), C.c_int32(0)
     st = lib().orc_gmres(n, rp, ci, va, b, x, tol, maxit, m, 1 if variant == "pipelined" else 0,
                          cap, _ptr(R), _ptr(xi), _ptr(est), _ptr(res), C.byref(it), C.byref(cyc))
+    if dinv is not None:
+        lib().orc_jacobi_right_end(n, dinv, x)
     return dict(x=x, iters=it.value, cycles=cyc.value, status=st, R=R, xi=xi, est=est, res=res)

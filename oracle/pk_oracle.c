@@ -17,6 +17,8 @@
  *   orc_gmres               Algorithms 5 and 6 (restarted simpler GMRES with classical
  *                           Gram-Schmidt; classical form updates the residual, pipelined
  *                           form uses xi_i = <v_0, v_i>)
+ *   orc_jacobi_right_begin  right preconditioning with M = diag(A) for BiCGStab and GMRES:
+ *   orc_jacobi_right_end    the solver runs on A M^-1 y = b, and x = M^-1 y
  *   orc_pcg_jacobi          CG with the Jacobi preconditioner M = diag(A) (Sec. 5 names
  *                           preconditioner fusion as the natural extension): the standard
  *                           preconditioned CG, and the pipelined form of Algorithm 2 with
@@ -294,6 +296,39 @@ int orc_pcg_jacobi(int32_t n, const int32_t* rp, const int32_t* ci, const double
 done:
   free(r); free(p); free(ap); free(z); free(dinv);
   return status;
+}
+
+/* ---------------------------------------------------------------- right Jacobi preconditioning */
+
+/* Right preconditioning with M = diag(A) (entries of row i in column i summed): a Krylov
+ * solver applied to A M^-1 y = b has the residual b - A M^-1 y = b - A x of x = M^-1 y, so
+ * its iterates, stopping test and iteration count are those of the preconditioned solve.
+ * begin: va_out = the values of A M^-1 (every entry times the reciprocal diagonal entry of
+ * its column), dinv_out = M^-1, x <- M x (y0 from x0).  A zero or non-finite diagonal entry
+ * leaves everything untouched and returns ERR_ARG. */
+int orc_jacobi_right_begin(int32_t n, const int32_t* rp, const int32_t* ci, const double* va,
+                           double* x, double* va_out, double* dinv_out) {
+  for (int32_t i = 0; i < n; ++i) {
+    double d = 0.0;
+    for (int32_t j = rp[i]; j < rp[i + 1]; ++j)
+      if (ci[j] == i) d += va[j];
+    if (d == 0.0 || !isfinite(d)) return ORC_ERR_ARG;
+    dinv_out[i] = 1.0 / d;
+  }
+  for (int32_t i = 0; i < n; ++i)
+    for (int32_t j = rp[i]; j < rp[i + 1]; ++j) va_out[j] = va[j] * dinv_out[ci[j]];
+  for (int32_t i = 0; i < n; ++i) {
+    double d = 0.0;
+    for (int32_t j = rp[i]; j < rp[i + 1]; ++j)
+      if (ci[j] == i) d += va[j];
+    x[i] = x[i] * d;
+  }
+  return ORC_OK;
+}
+
+/* end: x = M^-1 y. */
+void orc_jacobi_right_end(int32_t n, const double* dinv, double* x) {
+  for (int32_t i = 0; i < n; ++i) x[i] = dinv[i] * x[i];
 }
 
 /* ---------------------------------------------------------------- BiCGStab, Algorithm 3 */

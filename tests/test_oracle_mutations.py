@@ -35,10 +35,26 @@ MUTANTS = {
     "spmv_transposed_gather": ("s += va[j] * x[ci[j]];", "s += va[j] * x[i];"),
 }
 
+# mutants of the preconditioned solvers, checked against their own pin files
+PRECOND_MUTANTS = {
+    "pcg_beta_sign": ([("beta = alpha * alpha * qdq / gamma - 1.0;", "beta = alpha * alpha * qdq / gamma + 1.0;")],
+                      "test_oracle_pcg.py"),
+    "pcg_qdq_unpreconditioned": ([("z[k] = ap[k] * dinv[k];", "z[k] = ap[k];")], "test_oracle_pcg.py"),
+    "pcg_p_update_unpreconditioned": ([("p[k] = r[k] * dinv[k] + beta * p[k];", "p[k] = r[k] + beta * p[k];")],
+                                      "test_oracle_pcg.py"),
+    "jacobi_right_scales_rows": ([("va_out[j] = va[j] * dinv_out[ci[j]];", "va_out[j] = va[j] * dinv_out[i];")],
+                                 "test_oracle_jacobi_right.py"),
+    "jacobi_right_y0_unscaled": ([("x[i] = x[i] * d;", "x[i] = x[i];")], "test_oracle_jacobi_right.py"),
+    "jacobi_right_end_skipped": ([("x[i] = dinv[i] * x[i];", "x[i] = x[i];")], "test_oracle_jacobi_right.py"),
+}
 
-@pytest.mark.parametrize("name", sorted(MUTANTS))
+
+@pytest.mark.parametrize("name", sorted(MUTANTS) + sorted(PRECOND_MUTANTS))
 def test_pins_catch_mutant(name, tmp_path):
-    edits = MUTANTS[name]
+    if name in MUTANTS:
+        edits, pins = MUTANTS[name], "test_oracle_pins.py"
+    else:
+        edits, pins = PRECOND_MUTANTS[name]
     edits = edits if isinstance(edits, list) else [edits]
     text = SRC
     for old, new in edits:
@@ -51,6 +67,6 @@ def test_pins_catch_mutant(name, tmp_path):
                     str(so), str(src), "-lm"], check=True)
     env = dict(os.environ, PK_ORACLE_LIB=str(so))
     res = subprocess.run([sys.executable, "-m", "pytest", "-x", "-q", "-p", "no:cacheprovider",
-                          str(ROOT / "tests" / "test_oracle_pins.py")],
+                          str(ROOT / "tests" / pins)],
                          cwd=ROOT, env=env, capture_output=True, text=True, timeout=300)
     assert res.returncode != 0, f"mutant {name} survived the pins:\n{res.stdout[-2000:]}"
