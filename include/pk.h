@@ -102,15 +102,24 @@ typedef struct {
   double* trace;       /* optional DEVICE array [trace_cap][4]: per iteration i the solver
                           writes {alpha_i, beta_i, omega_i, res2_i} (unused slots untouched);
                           GMRES writes {R_{i-1,i}, R_{i,i}, xi_i, estimate_i} */
-  int32_t precond;     /* PK_PRECOND_*: CG only (0 = none) */
+  int32_t precond;     /* PK_PRECOND_*: CG, BiCGStab, GMRES (0 = none; the batched solver
+                          takes none) */
 } pk_opts;
 
-/* pk_opts.precond.  JACOBI: M = diag(A), pipelined FP64 CG (Alg. 2 with the preconditioned
+/* pk_opts.precond.  JACOBI, M = diag(A) (entries of row i in column i summed; Sec. 5 names
+ * preconditioner fusion as the method's extension).
+ * CG: pipelined FP64 CG (Alg. 2 with the preconditioned
  * inner products <r, M^-1 r> and <Ap, M^-1 Ap>; beta = alpha^2 <Ap, M^-1 Ap>/<r, M^-1 r> - 1)
  * on the graph or host loop; the fused SpMV kernel forms Ap, <p, Ap>, <Ap, M^-1 Ap>, the
  * update kernel x, r, p = M^-1 r + beta p, <r, M^-1 r> and <r, r>.  The stopping test stays
  * ||r|| <= tol ||b||.  A diagonal entry <= 0 returns PK_NOT_SPD.  Other variants, precisions
- * and the persistent loop return PK_ERR_ARG (PK_LOOP_AUTO uses the graph loop). */
+ * and the persistent loop return PK_ERR_ARG (PK_LOOP_AUTO uses the graph loop).
+ * BiCGStab and GMRES (both variants): right preconditioning.  The solver runs unchanged on
+ * A M^-1 y = b, whose residual is b - A x for x = M^-1 y, so the stopping test and the trace
+ * are those of the plain solver on A M^-1; the values of A M^-1 (columns scaled by the
+ * reciprocal diagonal) are built on first use and kept with the handle (8 nnz + 16 n bytes),
+ * x enters as y0 = M x0 and leaves as M^-1 y.  A zero or non-finite diagonal entry returns
+ * PK_ERR_ARG before any iteration. */
 enum { PK_PRECOND_NONE = 0, PK_PRECOND_JACOBI = 1 };
 
 /* Per-kernel timing slots in pk_info (PK_FLAG_TIMING). */

@@ -40,7 +40,7 @@
  *     x <- x0 + rho0 (eta_1 v_0 + sum_{i=2..k} eta_i v_{i-1}) with R eta = xi.
  *     Within a cycle the residual estimate rho0 sqrt(max(0, 1 - sum xi_j^2)) (pipelined)
  *     or rho0 ||r|| (classical) ends the cycle when <= tol ||b||, when the squared relative
- *     estimate is <= 1e-14, at k = m, or when the iteration budget is spent.  Convergence is
+ *     estimate is <= 1e-12, at k = m, or when the iteration budget is spent.  Convergence is
  *     declared only from the true residual b - A x at a cycle boundary.  maxit counts
  *     Arnoldi steps over all cycles.  R_{i,i} <= 1e-14 ||A v_{i-1}|| ends the cycle before
  *     step i (lucky breakdown).
@@ -554,7 +554,7 @@ int orc_gmres(int32_t n, const int32_t* rp, const int32_t* ci, const double* va,
       if (rel2 < 0.0) rel2 = 0.0;
       double est = rho0 * sqrt(rel2);
       record(tr_est, cap, est_k++, est);
-      if (est <= tol * bnorm || rel2 <= 1e-14) break;
+      if (est <= tol * bnorm || rel2 <= 1e-12) break;
     }
     if (cycle == 0) {
       if (tr_R)

@@ -436,6 +436,7 @@ pk_status bicgstab_solve(pk_csr* A, const double* b, double* x, const pk_opts* o
     set_error("BiCGStab variants: pipelined or classical");
     return PK_ERR_ARG;
   }
+  if (o->precond != PK_PRECOND_NONE && o->precond != PK_PRECOND_JACOBI) { set_error("bad precond"); return PK_ERR_ARG; }
   cudaEvent_t e0, e1;
   PK_CUDA(cudaEventCreate(&e0));
   PK_CUDA(cudaEventCreate(&e1));
@@ -460,6 +461,9 @@ pk_status bicgstab_solve(pk_csr* A, const double* b, double* x, const pk_opts* o
     xd = xi;
   }
   if (tma && (e = bi_tma_setup())) return e;
+  // right Jacobi preconditioning: iterate on A M^-1 with y = M x (values swapped until leave)
+  JacobiRight jac;
+  if (o->precond == PK_PRECOND_JACOBI && (e = jacobi_right_enter(A, xd, s, &jac))) return e;
   Timer T;
   T.A = A;
   T.on = (o->flags & PK_FLAG_TIMING) != 0;
@@ -484,6 +488,7 @@ pk_status bicgstab_solve(pk_csr* A, const double* b, double* x, const pk_opts* o
   L.keys[0] = xd;
   L.ikeys[0] = o->variant;
   L.ikeys[1] = tma;
+  L.ikeys[2] = o->precond;  // the graph holds the value pointer of A or of A M^-1
   if (o->variant == PK_VARIANT_PIPELINED) {
     L.kind = 4;
     L.body_kernels = 4;
@@ -533,6 +538,10 @@ pk_status bicgstab_solve(pk_csr* A, const double* b, double* x, const pk_opts* o
   }
   if ((e = run_loop(A, o, s, L, &T, &launches))) return e;
   if ((e = T.flush())) return e;
+  if (jac.A) {
+    if ((e = jacobi_right_leave(&jac, xd, s))) return e;
+    launches += 2;  // y0 = M x0 and x = M^-1 y
+  }
   if (x_copy_back)
     PK_CUDA(cudaMemcpyAsync(x_copy_back, xd, sizeof(double) * A->n, cudaMemcpyDeviceToDevice, s));
   const bool graph = o->loop != PK_LOOP_HOST && !T.on;

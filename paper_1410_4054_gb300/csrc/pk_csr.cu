@@ -519,6 +519,9 @@ pk_status pk_csr_destroy(pk_csr* A) {
   for (int k = 0; k < A->ev_count; ++k) cudaEventDestroy(A->ev_pool[k]);
   for (auto* v : A->vec) if (v) cudaFree(v);
   if (A->basis) cudaFree(A->basis);
+  if (A->jac_va) cudaFree(A->jac_va);
+  if (A->jac_d) cudaFree(A->jac_d);
+  if (A->jac_dinv) cudaFree(A->jac_dinv);
   if (A->small) cudaFree(A->small);
   if (A->partials) cudaFree(A->partials);
   if (A->st) cudaFree(A->st);

@@ -27,6 +27,11 @@ enum { GM_START = 0, GM_STEP = 1, GM_END = 2 };
 constexpr int kGmMax = 64;           // largest restart length
 constexpr int kRld = kGmMax + 1;     // leading dimension of R in device scratch
 constexpr int kXiOff = kRld * kRld;  // xi after R
+// A cycle ends once the squared relative residual estimate 1 - sum xi^2 (pipelined) or
+// ||r~||^2 (classical) is <= this floor: below it the estimate is rounding (a difference of
+// O(1) terms accumulated over up to 64 steps, with classical Gram-Schmidt's loss of
+// orthogonality on top), and the true residual at the restart decides.
+constexpr double kGmEstFloor = 1e-12;
 
 struct GmArgs {
   int n, ld;
@@ -464,7 +469,7 @@ __device__ __forceinline__ void gm_step_done(DevState* st, GmArgs& g, int i, dou
   trace_put(st, step, 3, est);
   if (!isfinite(xi_i)) {
     gm_finish(st, PK_ERR_NAN);
-  } else if (est * est <= st->thr2 || rel2 <= 1e-14 || i >= st->gm_m || st->iter >= st->maxit) {
+  } else if (est * est <= st->thr2 || rel2 <= kGmEstFloor || i >= st->gm_m || st->iter >= st->maxit) {
     st->gm_phase = GM_END;
     cond2_set(st, 0u);
   } else {
@@ -652,6 +657,7 @@ pk_status gmres_solve(pk_csr* A, const double* b, double* x, const pk_opts* o, p
     set_error("GMRES variants: pipelined or classical");
     return PK_ERR_ARG;
   }
+  if (o->precond != PK_PRECOND_NONE && o->precond != PK_PRECOND_JACOBI) { set_error("bad precond"); return PK_ERR_ARG; }
   if (!A->tma_ok) { set_error("GMRES needs the tile engine (rows longer than 4096 nonzeros are not supported)"); return PK_ERR_ARG; }
   if ((e = gm_setup())) return e;
   const int n = A->n;
@@ -672,6 +678,9 @@ pk_status gmres_solve(pk_csr* A, const double* b, double* x, const pk_opts* o, p
   k_gm_init<<<1, 1, 0, s>>>(A->st, m);
   VecStage v;
   if ((e = stage_in(A, b, x, 14, 15, s, &v))) return e;
+  // right Jacobi preconditioning: iterate on A M^-1 with y = M x (values swapped until leave)
+  JacobiRight jac;
+  if (o->precond == PK_PRECOND_JACOBI && (e = jacobi_right_enter(A, v.x_dev, s, &jac))) return e;
   const bool classical = o->variant == PK_VARIANT_CLASSICAL;
   double* rc = nullptr;
   if (classical && (e = work_vec(A, 6, &rc))) return e;
@@ -740,7 +749,7 @@ pk_status gmres_solve(pk_csr* A, const double* b, double* x, const pk_opts* o, p
   const bool graph = o->loop != PK_LOOP_HOST && !T.on;
   if (graph) {
     const void* keys[4] = {v.x_dev, v.b_dev, nullptr, nullptr};
-    const int64_t ikeys[4] = {o->variant, m, 0, 0};
+    const int64_t ikeys[4] = {o->variant, m, o->precond, 0};  // precond: values of A or of A M^-1
     pk_graph_entry* ge = nullptr;
     if ((e = build_nested_graph(A, 6 + (classical ? 1 : 0), keys, ikeys,
                                 [&](cudaStream_t cs) { pre(cs, nullptr); },
@@ -776,6 +785,10 @@ pk_status gmres_solve(pk_csr* A, const double* b, double* x, const pk_opts* o, p
   }
   launch_zero_x(A, v.x_dev, s);
   launches += 1;
+  if (jac.A) {
+    if ((e = jacobi_right_leave(&jac, v.x_dev, s))) return e;
+    launches += 2;  // y0 = M x0 and x = M^-1 y
+  }
   if ((e = finish_info(A, o, info, s, v, e0, e1, launches))) return e;
   const DevState* h = A->st_host;
   info->cycles = h->gm_cycle;

@@ -210,6 +210,12 @@ struct pk_csr {
   double* basis = nullptr;            // GMRES Krylov basis, (m+1) x n column-contiguous
   int basis_m = 0;
   double* small = nullptr;            // small device scratch (R, xi, eta ...): 8192 doubles
+  // right Jacobi preconditioning (built on first use): values of A diag(A)^-1, diag(A) and its
+  // reciprocal; jac_state 0 = not built, 1 = built, -1 = a zero or non-finite diagonal entry
+  double* jac_va = nullptr;
+  double* jac_d = nullptr;
+  double* jac_dinv = nullptr;
+  int jac_state = 0;
   pk_graph_entry graphs[4];
   cudaEvent_t ev_pool[64] = {nullptr};
   int ev_count = 0;
@@ -273,6 +279,18 @@ void launch_residual_init(const pk_csr* A, const double* b, const double* x, dou
 void launch_zero_x(const pk_csr* A, double* x, cudaStream_t s);
 pk_status check_opts(const pk_csr* A, const double* b, double* x, const pk_opts* o,
                      pk_info* info);
+
+// Right preconditioning with M = diag(A) for BiCGStab and GMRES: while a JacobiRight is
+// entered, A's values are those of A M^-1 and x holds y = M x; leave() restores both.
+struct JacobiRight {
+  pk_csr* A = nullptr;
+  double* saved_va = nullptr;
+  ~JacobiRight() {
+    if (A) A->va = saved_va;  // error paths: values restored, x left in y form
+  }
+};
+pk_status jacobi_right_enter(pk_csr* A, double* x, cudaStream_t s, JacobiRight* g);
+pk_status jacobi_right_leave(JacobiRight* g, double* x, cudaStream_t s);
 
 inline long long passes_of(const DevState* h) {
   return *reinterpret_cast<const long long*>(&h->s[7]);

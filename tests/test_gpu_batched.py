@@ -100,3 +100,12 @@ def test_batched_not_spd_member_is_reported():
     infos = pk.batched_solve(As, bs, xs, tol=1e-10, maxit=2000)
     assert infos[0]["status"] == pk.PK_NOT_SPD
     assert all(i["status"] == pk.PK_OK for i in infos[1:])
+
+
+def test_batched_rejects_a_preconditioner():
+    mats, rhs = make_batch(nsys=2, seed=1)
+    As = [pk.CSRMatrix.from_workload(a) for a in mats]
+    bs = [dev(b) for b in rhs]
+    xs = [torch.zeros(a.n, dtype=torch.float64, device=DEV) for a in mats]
+    with pytest.raises(RuntimeError, match="no preconditioner"):
+        pk.batched_solve(As, bs, xs, tol=1e-10, maxit=2000, precond="jacobi")

@@ -44,38 +44,49 @@ MATRICES = {
 }
 
 
-def oracle_sensitivity(a, b, variant, tol=1e-8, maxit=5000, nsamp=3):
+def oracle_sensitivity(a, b, variant, tol=1e-8, maxit=5000, nsamp=3, precond="none"):
     """The oracle's own rounding sensitivity: rerun it with b perturbed by about one ulp
     (relative 2^-52, three seeds) and record how far alpha, omega, beta (running maximum of
     the relative change per iteration), the iteration count and x at a fixed count move."""
-    base = O.bicgstab(a, b, tol=tol, maxit=maxit, variant=variant)
-    fixed = O.bicgstab(a, b, tol=0.0, maxit=max(base["iters"], 1), variant=variant)
+    base = O.bicgstab(a, b, tol=tol, maxit=maxit, variant=variant, precond=precond)
+    fixed = O.bicgstab(a, b, tol=0.0, maxit=max(base["iters"], 1), variant=variant, precond=precond)
     k = 20
     spread = np.zeros(k)
     it_spread, x_spread = 0, 0.0
     for smp in range(nsamp):
         bp = b * (1 + 2.0 ** -52 * W.uniform_pm1(100 + smp, a.n))
-        r = O.bicgstab(a, bp, tol=tol, maxit=maxit, variant=variant)
+        r = O.bicgstab(a, bp, tol=tol, maxit=maxit, variant=variant, precond=precond)
         for key in ("alpha", "omega", "beta"):
             d = np.abs(r[key][:k] - base[key][:k]) / np.abs(base[key][:k])
             spread = np.fmax(spread, np.nan_to_num(d, nan=0.0))
         it_spread = max(it_spread, abs(r["iters"] - base["iters"]))
-        rf = O.bicgstab(a, bp, tol=0.0, maxit=max(base["iters"], 1), variant=variant)
+        rf = O.bicgstab(a, bp, tol=0.0, maxit=max(base["iters"], 1), variant=variant, precond=precond)
         x_spread = max(x_spread, rel(rf["x"], fixed["x"]))
     return base, fixed, np.maximum.accumulate(spread), it_spread, x_spread
 
 
+JACOBI_MATRICES = {
+    "convdiff_16_scaled": lambda: W.diag_scaled(W.convdiff_3d(16), seed=1, spread=100.0),
+    "powerlaw_1e4_scaled": lambda: W.diag_scaled(W.power_law(10_000, seed=1), seed=2, spread=100.0),
+    "rand28_scaled": lambda: W.diag_scaled(W.random_uniform(4000, 28, seed=2), seed=3, spread=10.0),
+    "lap2d_ragged_scaled": lambda: W.diag_scaled(W.laplace_2d(97, 41), seed=4, spread=10.0),
+}
+
+
 @pytest.mark.parametrize("variant", ["pipelined", "classical"])
-@pytest.mark.parametrize("name", sorted(MATRICES))
+@pytest.mark.parametrize("name", sorted(MATRICES) + [f"jacobi:{k}" for k in sorted(JACOBI_MATRICES)])
 def test_bicgstab_parity(name, variant):
     """Bars: alpha/omega/beta within max(1e-12, 100 x the oracle's own one-ulp spread) per
     iteration; iterations within max(2, 2 x the oracle's own spread); x at the oracle's
-    iteration count within max(1e-9, 10 x the oracle's own spread); true residual <= tol."""
-    a = MATRICES[name]()
+    iteration count within max(1e-9, 10 x the oracle's own spread); true residual <= tol.
+    'jacobi:' cases: right preconditioning with M = diag(A) on both sides."""
+    precond = "jacobi" if name.startswith("jacobi:") else "none"
+    a = JACOBI_MATRICES[name[7:]]() if precond == "jacobi" else MATRICES[name]()
     _, b, _ = W.manufactured(a, seed=0)
-    ref, fixed, spread, it_spread, x_spread = oracle_sensitivity(a, b, variant)
+    ref, fixed, spread, it_spread, x_spread = oracle_sensitivity(a, b, variant, precond=precond)
     assert ref["status"] == O.OK
-    info, x, tr = solve(a, b, tol=1e-8, maxit=5000, variant=variant, flags=pk.FLAG_TRUE_RES)
+    info, x, tr = solve(a, b, tol=1e-8, maxit=5000, variant=variant, flags=pk.FLAG_TRUE_RES,
+                        precond=precond)
     assert info["status"] == pk.PK_OK, info
     assert abs(info["iters"] - ref["iters"]) <= max(2, 2 * it_spread)
     k = min(20, ref["iters"] - 1)
@@ -87,9 +98,42 @@ def test_bicgstab_parity(name, variant):
     calm = spread[:k] < 1e-14
     assert calm[:3].all()
     assert info["rel_res_true"] <= 1.5e-8
-    info2, x2, _ = solve(a, b, tol=0.0, maxit=ref["iters"], variant=variant)
+    info2, x2, _ = solve(a, b, tol=0.0, maxit=ref["iters"], variant=variant, precond=precond)
     assert info2["iters"] == ref["iters"]
     assert rel(x2, fixed["x"]) <= max(1e-9, 10 * x_spread)
+
+
+def test_bicgstab_jacobi_unit_diagonal_is_plain_and_handle_stays_clean():
+    """diag(A) = I: the preconditioned solve is the plain one bitwise; plain solves on the same
+    handle before and after a preconditioned one agree bitwise (values restored, separate
+    cached graphs)."""
+    a = W.convdiff_3d(12)
+    u = W.CSR(a.n, a.row_ptr, a.col, a.val / 9.0, "convdiff_unit_diag")
+    _, b, _ = W.manufactured(u, seed=1)
+    for variant in ("pipelined", "classical"):
+        A = pk.CSRMatrix.from_workload(u)
+        i1, x1, t1 = solve(u, b, A=A, variant=variant)
+        i2, x2, t2 = solve(u, b, A=A, variant=variant, precond="jacobi")
+        assert i1["iters"] == i2["iters"] and np.array_equal(x1, x2)
+        assert np.array_equal(t1, t2, equal_nan=True)
+    s = W.diag_scaled(a, seed=5, spread=100.0)
+    _, b, _ = W.manufactured(s, seed=2)
+    A = pk.CSRMatrix.from_workload(s)
+    i1, x1, _ = solve(s, b, A=A, tol=1e-8, maxit=5000)
+    ij, xj, _ = solve(s, b, A=A, tol=1e-8, maxit=5000, precond="jacobi", flags=pk.FLAG_TRUE_RES)
+    i3, x3, _ = solve(s, b, A=A, tol=1e-8, maxit=5000)
+    assert i1["iters"] == i3["iters"] and np.array_equal(x1, x3)
+    assert ij["status"] == pk.PK_OK and ij["rel_res_true"] <= 1.5e-8 and ij["iters"] < i1["iters"]
+
+
+def test_bicgstab_jacobi_zero_diagonal_rejected():
+    a = W.convdiff_3d(8)
+    z = W.CSR(a.n, a.row_ptr, a.col, a.val.copy(), "zero_diag")
+    rows = np.repeat(np.arange(a.n), np.diff(a.row_ptr))
+    z.val[np.nonzero((rows == 100) & (a.col == 100))[0]] = 0.0
+    _, b, _ = W.manufactured(a)
+    with pytest.raises(RuntimeError, match="nonzero finite diagonal"):
+        solve(z, b, precond="jacobi")
 
 
 def test_bicgstab_launch_counts():
