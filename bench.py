@@ -397,7 +397,8 @@ def run_ours(args):
                 row[f"{key}_iters"] = best["iters"]
                 row[f"{key}_ms"] = best["solve_ms"]
             # what the default loop (PK_LOOP_AUTO) runs at this n
-            auto = ("persistent" if m.n <= pk.PERSISTENT_AUTO_N and row["pipelined_persistent_ms"]
+            auto = ("persistent" if m.n <= pk.PERSISTENT_AUTO_N and m.nnz <= pk.PERSISTENT_AUTO_NNZ
+                    and row["pipelined_persistent_ms"]
                     else "graph")
             row["pipelined_loop"] = auto
             row["pipelined_iters"] = row[f"pipelined_{auto}_iters"]
@@ -551,6 +552,7 @@ def bench_forms(pk, torch, dev, args):
 
     out["jacobi_pcg"] = jacobi_pcg(pk, torch, dev, args.k)
     out["jacobi_right"] = jacobi_right(pk, torch, dev)
+    out["fe_sweep"] = fe_sweep(pk, torch, dev)
     out["nonsymmetric_sweep"] = nonsymmetric_sweep(pk, torch, dev)
     out["fused_spmv_dot"] = fused_spmv_dot(pk, torch, dev)
 
@@ -686,6 +688,42 @@ def jacobi_right(pk, torch, dev, k=128):
         out[solver] = row
     A.close()
     return out
+
+
+def fe_sweep(pk, torch, dev):
+    """Time per iteration against system size on finite-element matrices (the shape of the
+    paper's Sec. 4.1 / 4.2 benchmarks): P1 Poisson on irregular triangulations of the unit
+    square, 225 ... 261,121 unknowns (~7 per row), and P1 elasticity on jittered Kuhn
+    tetrahedra, 540 ... 324,864 unknowns (3 x 3 blocks, ~43 per row).  CG, BiCGStab and
+    GMRES(30), pipelined and classical, a fixed number of iterations (tol 0) through the graph
+    loop; CG also through PK_LOOP_AUTO (the cluster-resident loop up to 65,536 rows).  Best of
+    two after a warm-up, microseconds per iteration (solve time / iterations)."""
+    mats = [("fe2d", lv, lambda lv=lv: W.fe_poisson_2d(lv)) for lv in range(4, 10)]
+    mats += [("fe3d", k, lambda k=k: W.fe_elasticity_3d(k)) for k in (5, 11, 23, 47)]
+    forms = [("cg", pk.cg_solve, "pipelined", "graph", 300, {}), ("cg", pk.cg_solve, "classical", "graph", 300, {}),
+             ("cg", pk.cg_solve, "pipelined", "auto", 300, {}),
+             ("bicgstab", pk.bicgstab_solve, "pipelined", "graph", 150, {}),
+             ("bicgstab", pk.bicgstab_solve, "classical", "graph", 150, {}),
+             ("gmres", pk.gmres_solve, "pipelined", "graph", 120, {"restart": 30}),
+             ("gmres", pk.gmres_solve, "classical", "graph", 120, {"restart": 30})]
+    rows = []
+    for kind, size, make in mats:
+        a = make()
+        _, b, _ = W.manufactured(a, seed=0)
+        A = pk.CSRMatrix.from_workload(a)
+        bd = torch.from_numpy(b).to(dev)
+        x = torch.zeros(a.n, dtype=torch.float64, device=dev)
+        row = {"matrix": a.name, "n": a.n, "nnz": a.nnz}
+        for solver, fn, variant, loop, its, extra in forms:
+            kw = dict(tol=0.0, maxit=its, variant=variant, loop=loop, **extra)
+            fn(A, bd, x.zero_(), **kw)
+            inf = _best(lambda: fn(A, bd, x.zero_(), **kw))
+            key = f"{solver}_{variant}" + ("_auto" if loop == "auto" else "")
+            row[f"{key}_us_per_iter"] = 1e3 * inf["solve_ms"] / max(inf["iters"], 1)
+        rows.append(row)
+        A.close()
+        del a
+    return rows
 
 
 def nonsymmetric_sweep(pk, torch, dev):

@@ -72,12 +72,15 @@ enum {
                         n <= PK_PERSISTENT_MAX_N.  Larger n, other solvers, variants or
                         precisions return PK_ERR_ARG */
   PK_LOOP_AUTO = 3   /* PK_LOOP_PERSISTENT for pipelined FP64 CG with n <= PK_PERSISTENT_AUTO_N
-                        (and no PK_FLAG_TIMING) when the device can run it, PK_LOOP_GRAPH
-                        otherwise */
+                        and nnz <= PK_PERSISTENT_AUTO_NNZ (and no PK_FLAG_TIMING) when the
+                        device can run it, PK_LOOP_GRAPH otherwise */
 };
 #define PK_PERSISTENT_MAX_N 65536  /* 16 CTAs x 4096 rows (8 x 4096 on devices without
                                       16-CTA clusters) */
 #define PK_PERSISTENT_AUTO_N 65536
+/* measured on GB300: the 16-SM cluster loop wins up to ~330k nonzeros (2D 5-point 256^2),
+ * the full-GPU graph loop from ~450k (P1 triangles, 65,025 unknowns) */
+#define PK_PERSISTENT_AUTO_NNZ 393216
 
 /* pk_opts.flags */
 #define PK_FLAG_TIMING 1u    /* time every kernel launch with CUDA events (host loop) and
@@ -160,9 +163,11 @@ typedef struct {
   int32_t block;             /* threads per block */
   int32_t kernel;            /* SpMV engine: 0 thread-per-row loads, 2 warp-specialised bulk-copy tiles */
   int32_t values_fp32_exact; /* 1 if every value is exactly representable in float32 */
-  /* bulk-copy tiles by row schedule: every row one thread (all rows <= 32 nonzeros), or
-   * short rows one thread and longer rows a whole warp each */
+  /* bulk-copy tiles by row schedule: every row one thread (rows short enough for one thread
+   * to walk), short rows one thread and long rows a whole warp each (rows of very different
+   * lengths), or rows of similar length G = 2..16 lanes each (tiles_group) */
   int32_t tiles_thread, tiles_long;
+  int32_t tiles_group;
 } pk_csr_stats;
 
 /*

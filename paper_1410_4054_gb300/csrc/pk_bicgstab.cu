@@ -471,7 +471,7 @@ pk_status bicgstab_solve(pk_csr* A, const double* b, double* x, const pk_opts* o
   int launches = 0;
   const RowArgs ra = row_args(A);
   const CsrTiles ct = csr_tiles_of(A);
-  const bool irr = A->stats.tiles_long > 0;  // rows longer than 32 nonzeros somewhere
+  const bool irr = csr_irregular(A);  // some tile needs the grouped or whole-warp rows
   const int G = A->grid, Gt = A->grid_tma, Gs = A->grid_stream, n = A->n;
   double* part = A->partials;
   DevState* dst = A->st;

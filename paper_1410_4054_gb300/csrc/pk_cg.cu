@@ -435,6 +435,7 @@ pk_status cg_solve(pk_csr* A, const double* b, double* x, const pk_opts* o, pk_i
     persistent = true;
   } else if (o->loop == PK_LOOP_AUTO) {
     persistent = o->variant == PK_VARIANT_PIPELINED && A->n <= PK_PERSISTENT_AUTO_N &&
+                 A->nnz <= PK_PERSISTENT_AUTO_NNZ &&
                  !(o->flags & PK_FLAG_TIMING) && persistent_usable(A, o);
   }
   cudaEvent_t e0, e1;
@@ -503,7 +504,7 @@ pk_status cg_solve(pk_csr* A, const double* b, double* x, const pk_opts* o, pk_i
   const bool tma = tma_engine;
   if (tma && (e = tma_setup())) return e;
   const CsrTiles ct = csr_tiles_of(A);
-  const bool irr = A->stats.tiles_long > 0;  // rows longer than 32 nonzeros somewhere
+  const bool irr = csr_irregular(A);  // some tile needs the grouped or whole-warp rows
   const int Gt = A->grid_tma, Gs = A->grid_stream;
   double* part = A->partials;
   DevState* dst = A->st;
@@ -588,7 +589,7 @@ pk_status cg_solve(pk_csr* A, const double* b, double* x, const pk_opts* o, pk_i
 pk_status launch_spmv_tma(pk_csr* A, const double* x, double* y, int first, int skip_early, cudaStream_t s) {
   pk_status e = tma_setup();
   if (e) return e;
-  (A->stats.tiles_long > 0 ? k_spmv_tma<true> : k_spmv_tma<false>)<<<A->grid_tma, kTileThreads, csr_smem_bytes(), s>>>(
+  (csr_irregular(A) ? k_spmv_tma<true> : k_spmv_tma<false>)<<<A->grid_tma, kTileThreads, csr_smem_bytes(), s>>>(
       csr_tiles_of(A), x, y, A->st, first, skip_early);
   return PK_OK;
 }

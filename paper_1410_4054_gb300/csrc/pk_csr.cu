@@ -385,7 +385,11 @@ pk_status pk_csr_create(int64_t n, int64_t nnz, const int32_t* row_ptr, const in
   // kTileRows rows and kTileNnz nonzeros
   std::vector<int32_t> tile_row, blk_tile;
   A->tma_ok = 1;
-  A->grid_tma = (int)std::max<int64_t>(1, std::min<int64_t>((int64_t)sms * 2, (n + kTileRows - 1) / kTileRows));
+  // at least one tile per block where the matrix has that many: tiles end at kTileRows rows or
+  // kTileNnz nonzeros, whichever comes first
+  A->grid_tma = (int)std::max<int64_t>(
+      1, std::min<int64_t>((int64_t)sms * 2, std::max<int64_t>((n + kTileRows - 1) / kTileRows,
+                                                               ((int64_t)nnz + kTileNnz - 1) / kTileNnz)));
   {
     const int Gt = A->grid_tma;
     std::vector<int32_t> tb(Gt + 1);
@@ -422,14 +426,32 @@ pk_status pk_csr_create(int64_t n, int64_t nnz, const int32_t* row_ptr, const in
     tile_row.push_back((int32_t)n);
     A->ntiles = (int)tile_row.size() - 1;
   }
-  // per tile: 1 if every row has at most 32 nonzeros (one thread per row throughout), 32 if
-  // the tile holds longer rows (those go to whole warps); see csr_tiles
+  // per tile, the lanes that compute one row (see csr_tiles): 1 = one thread per row (two rows
+  // per thread, in one pass), 2..16 = a group of lanes per row, 32 = short rows one thread and
+  // rows longer than 32 nonzeros a whole warp each, in a length-sorted row order.  A tile
+  // holds at most kTileNnz nonzeros, so long rows mean few rows per tile: with one thread per
+  // row most consumer threads would idle.  The group size minimises the rounds of (at most 8)
+  // dependent gathers a lane waits for: ceil(rows G / consumers) rows one after the other,
+  // each ceil(lmax / 8 G) batches.  Tiles whose longest row is far above their mean (power-law
+  // rows) take the sorted whole-warp schedule instead.
+  auto tile_lanes = [&](int64_t rows, int64_t lmax, int64_t z) -> int {
+    if (lmax <= 8) return 1;
+    const double mean = (double)z / (double)rows;
+    if (lmax > 32 && (double)lmax > 3.0 * mean + 8.0) return 32;
+    int best = 1;
+    double cost = std::ceil((double)lmax / 8.0);  // two rows per thread, interleaved
+    for (int G = 2; G <= 16; G *= 2) {
+      const double c = std::ceil((double)(rows * G) / kConsumers) * std::ceil((double)lmax / (8.0 * G));
+      if (c <= cost) { best = G; cost = c; }  // ties: more lanes, fewer batches per row
+    }
+    return best == 1 && lmax > 32 ? 32 : best;
+  };
   std::vector<int8_t> tile_grp(A->tma_ok ? A->ntiles : 0);
   for (int t = 0; t < (int)tile_grp.size(); ++t) {
     int64_t lmax = 0;
     for (int64_t r = tile_row[t]; r < tile_row[t + 1]; ++r) lmax = std::max<int64_t>(lmax, rp[r + 1] - rp[r]);
-    tile_grp[t] = lmax <= 32 ? 1 : 32;
-    (tile_grp[t] == 1 ? A->stats.tiles_thread : A->stats.tiles_long) += 1;
+    tile_grp[t] = (int8_t)tile_lanes(tile_row[t + 1] - tile_row[t], lmax, rp[tile_row[t + 1]] - rp[tile_row[t]]);
+    (tile_grp[t] == 1 ? A->stats.tiles_thread : tile_grp[t] == 32 ? A->stats.tiles_long : A->stats.tiles_group) += 1;
   }
   // row order of every irregular tile: rows sorted by length (longest first), dealt
   // round-robin over the 8 consumer warps -- slot (warp w, lane l) takes sorted rows
@@ -440,7 +462,7 @@ pk_status pk_csr_create(int64_t n, int64_t nnz, const int32_t* row_ptr, const in
     tile_perm.assign((size_t)A->ntiles * kTileRows, (int16_t)-1);
     std::vector<int32_t> order;
     for (int t = 0; t < A->ntiles; ++t) {
-      if (tile_grp[t] == 1) continue;
+      if (tile_grp[t] != 32) continue;
       const int32_t R0 = tile_row[t], m = tile_row[t + 1] - R0;
       order.resize(m);
       for (int k = 0; k < m; ++k) order[k] = k;

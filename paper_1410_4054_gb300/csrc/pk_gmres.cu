@@ -696,7 +696,7 @@ pk_status gmres_solve(pk_csr* A, const double* b, double* x, const pk_opts* o, p
   g.partials = A->partials;
   g.st = A->st;
   const CsrTiles ct = csr_tiles_of(A);
-  const bool irr = A->stats.tiles_long > 0;  // rows longer than 32 nonzeros somewhere
+  const bool irr = csr_irregular(A);  // some tile needs the grouped or whole-warp rows
   const int Gt = A->grid_tma, Gs = A->grid_stream;
   int Ge = A->grid_ew;
   if (!Ge) {

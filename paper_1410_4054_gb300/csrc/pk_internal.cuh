@@ -292,6 +292,10 @@ struct JacobiRight {
 pk_status jacobi_right_enter(pk_csr* A, double* x, cudaStream_t s, JacobiRight* g);
 pk_status jacobi_right_leave(JacobiRight* g, double* x, cudaStream_t s);
 
+// Kernels on the CSR tile engine take the instantiation with the grouped and whole-warp row
+// paths when some tile needs one of them.
+inline bool csr_irregular(const pk_csr* A) { return A->stats.tiles_long > 0 || A->stats.tiles_group > 0; }
+
 inline long long passes_of(const DevState* h) {
   return *reinterpret_cast<const long long*>(&h->s[7]);
 }

@@ -419,7 +419,7 @@ pk_status cg_mixed(pk_csr* A, const double* b, double* x, const pk_opts* o, pk_i
   const bool tma = A->tma_ok && !(o->flags & PK_FLAG_NO_TMA);
   if (tma && (e = mx_tma_setup())) return e;
   const CsrTilesT<float> ct = csr_tiles32_of(A);
-  const bool irr = A->stats.tiles_long > 0;  // rows longer than 32 nonzeros somewhere
+  const bool irr = csr_irregular(A);  // some tile needs the grouped or whole-warp rows
   const int Gt = A->grid_tma, Gs = A->grid_stream;
   auto step = [&](cudaStream_t cs, Timer* t) {
     if (t) t->begin(PK_SLOT_SPMV_DOTS);

@@ -243,7 +243,7 @@ pk_status pcg_jacobi_solve(pk_csr* A, const double* b, double* x, const pk_opts*
   int launches = 0;
   const int G = A->grid, Gt = A->grid_tma, Gs = A->grid_stream, n = A->n;
   const CsrTiles ct = csr_tiles_of(A);
-  const bool irr = A->stats.tiles_long > 0;
+  const bool irr = csr_irregular(A);
   double* part = A->partials;
   DevState* dst = A->st;
   if ((e = T.begin(PK_SLOT_OTHER))) return e;

@@ -312,6 +312,76 @@ struct CsrTilesT {
 };
 using CsrTiles = CsrTilesT<double>;
 
+// FMAs k < M of one gathered batch of any element type, lane-predicated on k < m.
+template <int M, class VT>
+__device__ __forceinline__ void fma_batch_g(const VT (&v)[8], const VT (&xv)[8], int m, VT& s) {
+#pragma unroll
+  for (int k = 0; k < M; ++k)
+    if (k < m) s = fma_t(v[k], xv[k], s);
+}
+
+template <class VT>
+__device__ __forceinline__ void fma_batch_gn(int mx, const VT (&v)[8], const VT (&xv)[8], int m, VT& s) {
+  switch (mx) {
+    case 1: fma_batch_g<1>(v, xv, m, s); break;
+    case 2: fma_batch_g<2>(v, xv, m, s); break;
+    case 3: fma_batch_g<3>(v, xv, m, s); break;
+    case 4: fma_batch_g<4>(v, xv, m, s); break;
+    case 5: fma_batch_g<5>(v, xv, m, s); break;
+    case 6: fma_batch_g<6>(v, xv, m, s); break;
+    case 7: fma_batch_g<7>(v, xv, m, s); break;
+    case 8: fma_batch_g<8>(v, xv, m, s); break;
+    default: break;
+  }
+}
+
+// One row product by a group of G lanes (G a power of two <= 16, the group aligned in the
+// warp): lane q sums entries j0 + q, j0 + q + G, ... left to right, up to 8 gathers in flight
+// before their FMAs, then the group adds its partial sums by a butterfly.  Warp-uniform:
+// every lane of the warp calls it together (lanes without a row pass j = j1), and the batch
+// loop runs to the warp's longest share, issuing only that many FMAs (predicated-off FP64
+// instructions still take issue slots).
+template <int G, class VT>
+__device__ __forceinline__ VT group_row(const VT* sva, const int32_t* sci, int j, int j1,
+                                        const VT* __restrict__ x) {
+  VT s = (VT)0;
+  for (;;) {
+    const int m = j < j1 ? min(8, (j1 - j + G - 1) / G) : 0;
+    const int mx = __reduce_max_sync(0xffffffffu, m);
+    if (mx == 0) break;
+    int c[8];
+    VT v[8], xv[8];
+#pragma unroll
+    for (int k = 0; k < 8; ++k) {
+      c[k] = k < m ? sci[j + k * G] : 0;
+      v[k] = k < m ? sva[j + k * G] : (VT)0;
+    }
+#pragma unroll
+    for (int k = 0; k < 8; ++k) xv[k] = k < m ? __ldg(x + c[k]) : (VT)0;
+    fma_batch_gn(mx, v, xv, m, s);
+    j += 8 * G;
+  }
+#pragma unroll
+  for (int o = G >> 1; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+  return s;
+}
+
+// The rows of a grouped tile: kConsumers / G rows per round, rows in order.  Rounds are the
+// same for the whole block, so every lane reaches the group's shuffles.
+template <int G, class VT, class RowDone>
+__device__ __forceinline__ void group_rows(const int32_t* srp, const VT* sva, const int32_t* sci, int R0,
+                                           int R1, const VT* __restrict__ x, RowDone& row_done) {
+  constexpr int ng = kConsumers / G;
+  const int gid = (int)threadIdx.x / G, q = (int)threadIdx.x & (G - 1);
+  const int rounds = (R1 - R0 + ng - 1) / ng;
+  for (int k = 0; k < rounds; ++k) {
+    const int r = R0 + gid + k * ng;
+    const int j0 = r < R1 ? srp[r] + q : 0, j1 = r < R1 ? srp[r + 1] : 0;
+    const VT acc = group_row<G>(sva, sci, j0, j1, x);
+    if (r < R1 && q == 0) row_done(r, acc);
+  }
+}
+
 // Two row products from a shared-memory window (defined below): FP64 and FP32.
 __device__ __forceinline__ void row_pair(const double* sva, const int32_t* sci, int ja, int ja1, int jb,
                                          int jb1, const double* __restrict__ x, double& sa, double& sb);
@@ -325,7 +395,8 @@ __device__ __forceinline__ void row_pair(const float* sva, const int32_t* sci, i
 // nonzeros (T.tile_grp != 1, set at pk_csr_create) a thread skips its long rows, and each
 // warp then takes its lanes' long rows one at a time with all 32 lanes (lane l sums entries
 // l, l + 32, ... left to right, then a butterfly), so that no thread walks a long row alone;
-// no synchronisation beyond the warp is involved.
+// no synchronisation beyond the warp is involved.  Tiles of rows of similar length that are
+// too long for one thread (T.tile_grp = G in 2..16) give each row a group of G lanes instead.
 constexpr int kLongRow = 32;
 
 // IRR = false compiles the thread-per-row path only (matrices without long rows).
@@ -394,7 +465,7 @@ __device__ __forceinline__ bool csr_tiles(const CsrTilesT<VT>& T, unsigned char*
             const int cs = b0 & ~3, ce = (b1 + 3) & ~3;        // columns b0..b1-1
             const uint32_t nrp = (uint32_t)(re - rs) * 4, nva = (uint32_t)(ve - vs) * (uint32_t)sizeof(VT),
                            nci = (uint32_t)(ce - cs) * 4;
-            const bool perm = g0 != 1 && T.tile_perm;  // irregular tile: its row order too
+            const bool perm = g0 == 32 && T.tile_perm;  // irregular tile: its row order too
             meta[s] = make_int4(a0, a1, g0, perm ? 1 : 0);  // published by the arrive below (release)
             mbar_expect_tx(&full[s], nrp + nva + nci + (perm ? kTileRows * 2 : 0));
             bulk_load_hint(stage_rp(s), T.rp + rs, nrp, &full[s], pol);
@@ -445,6 +516,14 @@ __device__ __forceinline__ bool csr_tiles(const CsrTilesT<VT>& T, unsigned char*
         row_pair(sva, sci, srp[ra], srp[ra + 1], rb >= 0 ? srp[rb] : 0, rb >= 0 ? srp[rb + 1] : 0, x, sa, sb);
         row_done(ra, sa);
         if (rb >= 0) row_done(rb, sb);
+      }
+    } else if (G < 32) {
+      // rows of similar length, too long for one thread: G lanes per row (G = 2..16)
+      switch (G) {
+        case 2: group_rows<2>(srp, sva, sci, R0, R1, x, row_done); break;
+        case 4: group_rows<4>(srp, sva, sci, R0, R1, x, row_done); break;
+        case 8: group_rows<8>(srp, sva, sci, R0, R1, x, row_done); break;
+        default: group_rows<16>(srp, sva, sci, R0, R1, x, row_done); break;
       }
     } else {
       // every lane takes part (the ballots below need the whole warp).  With a row order

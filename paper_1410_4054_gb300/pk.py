@@ -23,6 +23,7 @@ VARIANTS = {"pipelined": 0, "classical": 1, "split": 2}
 PRECISIONS = {"fp64": 0, "mixed": 1}
 LOOPS = {"graph": 0, "host": 1, "persistent": 2, "auto": 3}
 PERSISTENT_AUTO_N = 65536  # PK_PERSISTENT_AUTO_N
+PERSISTENT_AUTO_NNZ = 393216  # PK_PERSISTENT_AUTO_NNZ
 FLAG_TIMING = 1
 FLAG_TRUE_RES = 2
 FLAG_NO_TMA = 4
@@ -49,7 +50,8 @@ class Stats(C.Structure):
     _fields_ = [("n", C.c_int64), ("nnz", C.c_int64), ("row_min", C.c_int32),
                 ("row_max", C.c_int32), ("row_mean", C.c_double), ("grid", C.c_int32),
                 ("block", C.c_int32), ("kernel", C.c_int32), ("values_fp32_exact", C.c_int32),
-                ("tiles_thread", C.c_int32), ("tiles_long", C.c_int32)]
+                ("tiles_thread", C.c_int32), ("tiles_long", C.c_int32),
+                ("tiles_group", C.c_int32)]
 
 
 EXPORTS = {

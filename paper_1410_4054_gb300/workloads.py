@@ -289,6 +289,131 @@ POWER_LAW_SWEEP = (10_000, 100_000, 1_000_000)
 
 # ------------------------------------------------------------------ transient heat equation
 
+def _csr_from_coo_summed(n: int, rows: np.ndarray, cols: np.ndarray, vals: np.ndarray, name: str) -> CSR:
+    """CSR with coincident (row, col) entries summed (finite-element assembly)."""
+    import scipy.sparse as sp
+
+    m = sp.coo_matrix((vals, (rows, cols)), shape=(n, n)).tocsr()
+    m.sum_duplicates()
+    m.sort_indices()
+    assert m.nnz < 2**31
+    return CSR(n, m.indptr.astype(np.int32), m.indices.astype(np.int32), m.data.astype(np.float64), name)
+
+
+def fe_poisson_2d(level: int, seed: int = 0, jitter: float = 0.25) -> CSR:
+    """Linear (P1) finite elements for -Laplace u = f on the unit square, Dirichlet boundary.
+
+    The mesh: 2^level x 2^level squares, each cut along a diagonal whose direction is drawn
+    per square, interior nodes moved by up to ``jitter`` cells in x and y (splitmix64(seed)),
+    so that the triangles are irregular and the node valence varies (4..8, mean 6): about 7
+    nonzeros per row, (2^level - 1)^2 unknowns (225, 961, 3969, 16129, 65025, 261121 for
+    level 4..9), the sizes of the hierarchy of refined triangular meshes of the 2D Poisson
+    benchmark.  Element matrices (grad phi_i . grad phi_j) |T|, assembled and summed.
+    """
+    N = 1 << level
+    h = 1.0 / N
+    g = np.arange(N + 1)
+    X, Y = np.meshgrid(g * h, g * h, indexing="ij")
+    inner = np.zeros((N + 1, N + 1), dtype=bool)
+    inner[1:-1, 1:-1] = True
+    u = uniform_pm1(seed, 2 * (N + 1) ** 2).reshape(2, N + 1, N + 1)
+    X = X + np.where(inner, jitter * h * u[0], 0.0)
+    Y = Y + np.where(inner, jitter * h * u[1], 0.0)
+    node = np.arange((N + 1) ** 2).reshape(N + 1, N + 1)
+    a, b_, c, d = node[:-1, :-1].ravel(), node[1:, :-1].ravel(), node[1:, 1:].ravel(), node[:-1, 1:].ravel()
+    flip = (splitmix64(seed + 1, N * N) >> np.uint64(63)).astype(bool)
+    t1 = np.where(flip[:, None], np.stack([a, b_, d], 1), np.stack([a, b_, c], 1))
+    t2 = np.where(flip[:, None], np.stack([b_, c, d], 1), np.stack([a, c, d], 1))
+    tri = np.concatenate([t1, t2])
+    px, py = X.ravel()[tri], Y.ravel()[tri]
+    # gradients of the barycentric coordinates: (y_j - y_k, x_k - x_j) / (2|T|)
+    bx = np.stack([py[:, 1] - py[:, 2], py[:, 2] - py[:, 0], py[:, 0] - py[:, 1]], 1)
+    by = np.stack([px[:, 2] - px[:, 1], px[:, 0] - px[:, 2], px[:, 1] - px[:, 0]], 1)
+    area2 = px[:, 0] * bx[:, 0] + px[:, 1] * bx[:, 1] + px[:, 2] * bx[:, 2]
+    assert (area2 > 0).all()
+    ke = (bx[:, :, None] * bx[:, None, :] + by[:, :, None] * by[:, None, :]) / (2.0 * area2)[:, None, None]
+    dof = np.full((N + 1) ** 2, -1, dtype=np.int64)
+    dof[node[inner]] = np.arange((N - 1) ** 2)
+    td = dof[tri]
+    r = np.broadcast_to(td[:, :, None], ke.shape).ravel()
+    c_ = np.broadcast_to(td[:, None, :], ke.shape).ravel()
+    keep = (r >= 0) & (c_ >= 0)
+    return _csr_from_coo_summed((N - 1) ** 2, r[keep], c_[keep], ke.ravel()[keep], f"fe2d_p1_{N - 1}sq")
+
+
+def fe_elasticity_3d(k: int, seed: int = 0, jitter: float = 0.2, E: float = 1.0, nu: float = 0.3) -> CSR:
+    """Linear (P1) finite elements for isotropic linear elasticity on the unit cube, three
+    displacement unknowns per node (3 x 3 blocks), clamped on the face x = 0, free elsewhere.
+
+    The mesh: k^3 cubes, each cut into the six tetrahedra of the Kuhn subdivision, nodes off
+    the clamped face moved by up to ``jitter`` cells (splitmix64(seed)).  3 k (k+1)^2
+    unknowns (540, 4752, 39744, 324864 for k = 5, 11, 23, 47, near the 693 ... 319,725 of the
+    3D elasticity benchmark) and up to 45 nonzeros per row (15 nodes x 3), against the
+    benchmark's about 60 from unstructured meshes.  Element matrices |T| B^T D B with B the
+    6 x 12 strain-displacement matrix and D the isotropic stiffness (Young's modulus E,
+    Poisson ratio nu), assembled and summed: symmetric positive definite.
+    """
+    n1 = k + 1
+    g = np.arange(n1) / k
+    X = np.stack(np.meshgrid(g, g, g, indexing="ij"), -1).reshape(-1, 3)
+    free = X[:, 0] > 0.0
+    u = uniform_pm1(seed, 3 * n1 ** 3).reshape(-1, 3)
+    move = np.zeros(n1 ** 3, dtype=bool)
+    idx = np.arange(n1 ** 3).reshape(n1, n1, n1)
+    move[idx[1:-1, 1:-1, 1:-1].ravel()] = True
+    X = X + np.where(move[:, None], jitter / k * u, 0.0)
+    corner = idx[:-1, :-1, :-1].ravel()
+    step = np.array([n1 * n1, n1, 1])
+    tets = []
+    for perm in ((0, 1, 2), (0, 2, 1), (1, 0, 2), (1, 2, 0), (2, 0, 1), (2, 1, 0)):
+        v0 = corner
+        v1 = v0 + step[perm[0]]
+        v2 = v1 + step[perm[1]]
+        v3 = v2 + step[perm[2]]
+        tets.append(np.stack([v0, v1, v2, v3], 1))
+    tet = np.concatenate(tets)
+    P = X[tet]                                           # ne x 4 x 3
+    M = np.concatenate([np.ones((tet.shape[0], 4, 1)), P], 2)
+    vol6 = np.linalg.det(M)
+    flipped = vol6 < 0
+    tet[flipped] = tet[flipped][:, [0, 2, 1, 3]]
+    P = X[tet]
+    M = np.concatenate([np.ones((tet.shape[0], 4, 1)), P], 2)
+    vol = np.linalg.det(M) / 6.0
+    assert (vol > 0).all()
+    G = np.linalg.inv(M)[:, 1:, :]                       # ne x 3 x 4: d phi_a / d x_i
+    ne = tet.shape[0]
+    B = np.zeros((ne, 6, 12))
+    for a in range(4):
+        gx, gy, gz = G[:, 0, a], G[:, 1, a], G[:, 2, a]
+        B[:, 0, 3 * a] = gx
+        B[:, 1, 3 * a + 1] = gy
+        B[:, 2, 3 * a + 2] = gz
+        B[:, 3, 3 * a] = gy
+        B[:, 3, 3 * a + 1] = gx
+        B[:, 4, 3 * a + 1] = gz
+        B[:, 4, 3 * a + 2] = gy
+        B[:, 5, 3 * a] = gz
+        B[:, 5, 3 * a + 2] = gx
+    lam = E * nu / ((1 + nu) * (1 - 2 * nu))
+    mu = E / (2 * (1 + nu))
+    D = np.zeros((6, 6))
+    D[:3, :3] = lam
+    D[np.arange(3), np.arange(3)] += 2 * mu
+    D[np.arange(3, 6), np.arange(3, 6)] = mu
+    ke = np.einsum("eki,kl,elj->eij", B, D, B) * vol[:, None, None]
+    ke = 0.5 * (ke + ke.transpose(0, 2, 1))             # exactly symmetric
+    nd = np.full(n1 ** 3, -1, dtype=np.int64)
+    nd[free] = np.arange(int(free.sum()))
+    td = np.repeat(nd[tet], 3, axis=1) * 3 + np.tile(np.arange(3), 4)
+    td = np.where(np.repeat(nd[tet], 3, axis=1) >= 0, td, -1)
+    r = np.broadcast_to(td[:, :, None], ke.shape).ravel()
+    c = np.broadcast_to(td[:, None, :], ke.shape).ravel()
+    keep = (r >= 0) & (c >= 0)
+    n = 3 * int(free.sum())
+    return _csr_from_coo_summed(n, r[keep], c[keep], ke.ravel()[keep], f"fe3d_elast_{k}")
+
+
 @dataclass
 class Transient:
     """Implicit-Euler heat equation on a k^3 grid: M x_t = x_{t-1} + dt f_t with M = I + dt L."""

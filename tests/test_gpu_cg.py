@@ -39,6 +39,8 @@ def rel(a, b):
 
 
 MATRICES = {
+    "fe2d_p1_961": lambda: W.fe_poisson_2d(5),              # P1 triangles, ~7 per row
+    "fe3d_elast_4752": lambda: W.fe_elasticity_3d(11),      # P1 elasticity, 3x3 blocks, <= 45 per row
     "lap2d_64": lambda: W.laplace_2d(64),                   # the 64 x 64 configuration
     "lap2d_ragged": lambda: W.laplace_2d(97, 41),           # several blocks, ragged tail
     "lap3d_16": lambda: W.laplace_3d(16),
@@ -67,11 +69,22 @@ def test_cg_parity(name, variant, loop):
     np.testing.assert_allclose(tr[:k, 0], ref["alpha"][:k], rtol=1e-12, atol=0)
     np.testing.assert_allclose(tr[:k, 1], ref["beta"][:k], rtol=1e-12, atol=0)
     assert info["rel_res_true"] <= 1.5e-8
-    # same iteration count: x within 1e-9 of the oracle's
+    # same iteration count: x within max(1e-9, 10 x the oracle's own one-ulp spread)
     fixed = ref["iters"]
     info2, x2, _ = solve(a, b, tol=0.0, maxit=fixed, variant=variant, loop=loop)
     assert info2["status"] == pk.PK_NOT_CONVERGED and info2["iters"] == fixed
-    assert rel(x2, ref["x"]) <= 1e-9
+    assert rel(x2, ref["x"]) <= max(1e-9, 10 * oracle_x_spread(a, b, ovar, fixed, ref["x"]))
+
+
+def oracle_x_spread(a, b, variant, iters, x_ref, nsamp=3):
+    """How far the oracle's own x after `iters` iterations moves when b is perturbed by about
+    one ulp (relative 2^-52, three seeds): 6e-16 on the Laplacians, 3.5e-9 on the irregular
+    P1 triangulation with 961 unknowns after 104 iterations."""
+    sp = 0.0
+    for smp in range(nsamp):
+        bp = b * (1 + 2.0 ** -52 * W.uniform_pm1(100 + smp, a.n))
+        sp = max(sp, rel(O.cg(a, bp, tol=0.0, maxit=iters, variant=variant)["x"], x_ref))
+    return sp
 
 
 @pytest.mark.parametrize("loop", ["graph", "host"])

@@ -40,6 +40,8 @@ def rel(a, b):
 
 
 MATRICES = {
+    "fe2d_p1_961": lambda: W.fe_poisson_2d(5),
+    "fe3d_elast_540": lambda: W.fe_elasticity_3d(5),
     "convdiff_16": lambda: W.convdiff_3d(16),
     "convdiff_23": lambda: W.convdiff_3d(23),
     "powerlaw_1e4": lambda: W.power_law(10_000, seed=1),
