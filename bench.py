@@ -553,6 +553,7 @@ def bench_forms(pk, torch, dev, args):
     out["jacobi_pcg"] = jacobi_pcg(pk, torch, dev, args.k)
     out["jacobi_right"] = jacobi_right(pk, torch, dev)
     out["fe_sweep"] = fe_sweep(pk, torch, dev)
+    out["sell"] = sell_compare(pk, torch, dev, args.k)
     out["nonsymmetric_sweep"] = nonsymmetric_sweep(pk, torch, dev)
     out["fused_spmv_dot"] = fused_spmv_dot(pk, torch, dev)
 
@@ -687,6 +688,51 @@ def jacobi_right(pk, torch, dev, k=128):
         row["speedup_vs_plain"] = row["none_ms"] / row["jacobi_ms"]
         out[solver] = row
     A.close()
+    return out
+
+
+def sell_compare(pk, torch, dev, k, reps=20):
+    """Fused SpMV + inner products on the SELL-C-sigma copy against the CSR kernels.
+    spmv_dot: q = A p, <p, q> as one launch, CSR thread-per-row (the paper's design) and
+    SELL-C-sigma (warp per 32-row slice), CUDA events over `reps` calls; bytes 12 nnz + 4 (n+1)
+    + 16 n (the SELL copy reads its padding and no row pointers: its own bytes are reported too).
+    CG (SPD matrices): K-CG-S on the CSR tiles and on SELL, mean launch time over 30 fixed
+    iterations (PK_FLAG_TIMING)."""
+    out = []
+    for a, spd in ((W.laplace_3d(k), True), (W.fe_elasticity_3d(47), True),
+                   (W.spd_power_law(1_000_000, seed=1), True), (W.random_uniform(1_000_000, 28, seed=1), False)):
+        A = pk.CSRMatrix.from_workload(a)
+        p = torch.from_numpy(W.uniform_pm1(3, a.n)).to(dev)
+        q = torch.empty_like(p)
+        res = torch.zeros(1, dtype=torch.float64, device=dev)
+        row = {"matrix": a.name, "n": a.n, "nnz": a.nnz, "csr_bytes": 12 * a.nnz + 4 * (a.n + 1) + 16 * a.n}
+        for key, kw in (("csr_thread", {"fused": True}), ("sell", {"sell": True})):
+            for _ in range(3):
+                pk.spmv_dot(A, p, q, res, **kw)
+            st, en = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            torch.cuda.synchronize()
+            st.record()
+            for _ in range(reps):
+                pk.spmv_dot(A, p, q, res, **kw)
+            en.record()
+            torch.cuda.synchronize()
+            us = 1e3 * st.elapsed_time(en) / reps
+            row[f"spmv_dot_{key}_us"] = us
+            row[f"spmv_dot_{key}_gbs"] = row["csr_bytes"] / (us * 1e-6) / 1e9
+        if spd:
+            _, b, _ = W.manufactured(a, seed=0)
+            bd = torch.from_numpy(b).to(dev)
+            x = torch.zeros(a.n, dtype=torch.float64, device=dev)
+            for key, fl in (("tiles", 0), ("sell", pk.FLAG_SELL)):
+                best = None
+                for _ in range(2):
+                    inf = pk.cg_solve(A, bd, x.zero_(), tol=0.0, maxit=30, flags=pk.FLAG_TIMING | fl)
+                    ms = inf["kernel_ms"]["spmv_dots"]
+                    best = ms if best is None else min(best, ms)
+                row[f"k_cg_s_{key}_us"] = 1e3 * best
+                row[f"k_cg_s_{key}_gbs"] = (12 * a.nnz + 4 * (a.n + 1) + 16 * a.n) / (best * 1e-3) / 1e9
+        out.append(row)
+        A.close()
     return out
 
 

@@ -91,6 +91,11 @@ enum {
 #define PK_FLAG_AUTOTUNE 8u  /* pk_batched_solve: time every (block size, blocks per SM)
                                 candidate on the batch first and keep the fastest (cached per
                                 batch shape for the process) */
+#define PK_FLAG_SELL 16u     /* pipelined FP64 CG: the fused SpMV kernel (Ap, <Ap,Ap>, <p,Ap>, alpha,
+                                beta) reads a SELL-C-sigma copy of A (C = 32, sigma = 1024; built on
+                                first use, kept with the handle) instead of the CSR tiles.  Other
+                                solvers, variants, precisions, PK_LOOP_PERSISTENT and
+                                preconditioners return PK_ERR_ARG */
 
 typedef struct {
   double tol;          /* relative residual tolerance (>= 0) */
@@ -195,7 +200,10 @@ pk_status pk_spmv(pk_csr* A, const double* x, double* y, void* stream);
 /*
  * q = A p and *result = <p, q> (Sec. 2.2, Eq. (1)-(2)).  fused = 1 computes the first
  * reduction stage inside the SpMV kernel and the second in its last block (one launch);
- * fused = 0 runs the SpMV, then a separate inner-product kernel (two launches).
+ * fused = 0 runs the SpMV, then a separate inner-product kernel (two launches); fused = 2 is
+ * the fused kernel on a SELL-C-sigma copy of A (sliced ELLPACK, 32 rows per slice sorted by
+ * length within windows of 1024 rows; built on first use and kept with the handle, padded
+ * entries skipped; every row summed left to right as in the CSR loop).
  * p, q: device, length n.  result: device pointer to one double.
  */
 pk_status pk_spmv_dot(pk_csr* A, const double* p, double* q, double* result, int32_t fused,

@@ -296,6 +296,39 @@ __global__ void __launch_bounds__(kTileThreads, 2) k_cg_spmv_dots_tma(CsrTiles T
   }
 }
 
+// K-CG-S on the SELL-C-sigma copy (PK_FLAG_SELL): warp per slice, lane per row, Ap with the
+// first stage of <Ap, Ap> and <p, Ap>; alpha, beta in the last block.  Launched with
+// programmatic dependent launch after K-CG-U: nothing is read before the dependency wait.
+__global__ void __launch_bounds__(kBlock) k_cg_sell_spmv_dots(SellArgs s, const double* __restrict__ p,
+                                                              double* __restrict__ ap, double* partials,
+                                                              DevState* st) {
+  griddep_wait();
+  if (state_done(st)) return;  // uniform in the grid
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  double v[2] = {0.0, 0.0};
+  for (int sl = blockIdx.x * kSellWarps + warp; sl < s.nslices; sl += gridDim.x * kSellWarps) {
+    const int64_t base = s.ptr[sl];
+    const int w = (int)((s.ptr[sl + 1] - base) / kSellC);
+    const int row = s.perm[(size_t)sl * kSellC + lane];
+    const double y = sell_row(s, base + lane, w, p);
+    if (row >= 0) {
+      ap[row] = y;
+      v[0] = fma(y, y, v[0]);
+      v[1] = fma(__ldg(p + row), y, v[1]);
+    }
+  }
+  griddep_trigger();
+  block_partials<2>(v, partials);
+  if (arrive_last(&st->counter)) {
+    double t[2];
+    final_sums<2>(partials, t);
+    if (threadIdx.x == 0) {
+      cg_alpha_beta(st, t[0], t[1]);
+      st->counter = 0;
+    }
+  }
+}
+
 // Plain y = A x on the CSR tile engine, no inner products: the SpMV of the unfused forms
 // (classical and split CG, classical BiCGStab), so that fused and unfused solvers differ only
 // in the fusion.  `first` counts a loop pass; `skip_early`: BiCGStab's early-exit flag also
@@ -417,6 +450,12 @@ pk_status cg_solve(pk_csr* A, const double* b, double* x, const pk_opts* o, pk_i
   *info = pk_info{};
   info->rel_res_true = -1.0;
   if (A->n == 0) return PK_OK;
+  const bool sell = (o->flags & PK_FLAG_SELL) != 0;
+  if (sell && (o->precond != PK_PRECOND_NONE || o->precision != PK_PREC_FP64 ||
+               o->variant != PK_VARIANT_PIPELINED || o->loop == PK_LOOP_PERSISTENT)) {
+    set_error("PK_FLAG_SELL runs pipelined FP64 CG without preconditioner on the graph or host loop");
+    return PK_ERR_ARG;
+  }
   if (o->precond == PK_PRECOND_JACOBI) return pcg_jacobi_solve(A, b, x, o, info, s);
   if (o->precond != PK_PRECOND_NONE) { set_error("bad precond"); return PK_ERR_ARG; }
   if (o->precision == PK_PREC_MIXED) return cg_mixed(A, b, x, o, info, s);
@@ -433,7 +472,7 @@ pk_status cg_solve(pk_csr* A, const double* b, double* x, const pk_opts* o, pk_i
       return PK_ERR_ARG;
     }
     persistent = true;
-  } else if (o->loop == PK_LOOP_AUTO) {
+  } else if (o->loop == PK_LOOP_AUTO && !sell) {
     persistent = o->variant == PK_VARIANT_PIPELINED && A->n <= PK_PERSISTENT_AUTO_N &&
                  A->nnz <= PK_PERSISTENT_AUTO_NNZ &&
                  !(o->flags & PK_FLAG_TIMING) && persistent_usable(A, o);
@@ -509,10 +548,14 @@ pk_status cg_solve(pk_csr* A, const double* b, double* x, const pk_opts* o, pk_i
   double* part = A->partials;
   DevState* dst = A->st;
   const int n = A->n;
+  if (sell && (e = sell_build(A, s))) return e;
+  const SellArgs sa = sell ? sell_args(A) : SellArgs{};
+  const int Gsell = A->sell_grid;
   if (variant == PK_VARIANT_PIPELINED || variant == PK_VARIANT_SPLIT) {
     // A p0, alpha_0, beta_0
     if ((e = T.begin(PK_SLOT_SPMV_DOTS))) return e;
-    if (tma) (irr ? k_cg_spmv_dots_tma<true> : k_cg_spmv_dots_tma<false>)<<<Gt, kTileThreads, csr_smem_bytes(), s>>>(ct, p, ap, part, dst);
+    if (sell) k_cg_sell_spmv_dots<<<Gsell, kBlock, 0, s>>>(sa, p, ap, part, dst);
+    else if (tma) (irr ? k_cg_spmv_dots_tma<true> : k_cg_spmv_dots_tma<false>)<<<Gt, kTileThreads, csr_smem_bytes(), s>>>(ct, p, ap, part, dst);
     else k_cg_spmv_dots<<<G, kBlock, 0, s>>>(ra, p, ap);
     if ((e = T.end())) return e;
     launches += 1;
@@ -528,12 +571,14 @@ pk_status cg_solve(pk_csr* A, const double* b, double* x, const pk_opts* o, pk_i
     L.body_kernels = 2;
     L.unroll = tma ? 4 : 1;  // more back-to-back programmatic launches per graph body pass
     L.ikeys[1] = tma;
+    L.ikeys[2] = sell;  // the SpMV kernel in the graph body
     L.body = [=](cudaStream_t cs, Timer* t) {
       if (t) t->begin(PK_SLOT_UPDATE);
       if (tma) launch_pdl(k_cg_update_tma, Gs, kTileThreads, stream_smem_bytes<4, double, 2>(), cs, n, xd, r, p, ap, part, dst);
       else k_cg_update<<<Gu, kBlock, 0, cs>>>(ra, xd, r, p, ap);
       if (t) { t->end(); t->begin(PK_SLOT_SPMV_DOTS); }
-      if (tma) launch_pdl(irr ? k_cg_spmv_dots_tma<true> : k_cg_spmv_dots_tma<false>, Gt, kTileThreads, csr_smem_bytes(), cs, ct, (const double*)p, ap, part, dst);
+      if (sell) launch_pdl(k_cg_sell_spmv_dots, Gsell, kBlock, 0, cs, sa, (const double*)p, ap, part, dst);
+      else if (tma) launch_pdl(irr ? k_cg_spmv_dots_tma<true> : k_cg_spmv_dots_tma<false>, Gt, kTileThreads, csr_smem_bytes(), cs, ct, (const double*)p, ap, part, dst);
       else k_cg_spmv_dots<<<G, kBlock, 0, cs>>>(ra, p, ap);
       if (t) t->end();
     };

@@ -542,6 +542,10 @@ pk_status pk_csr_destroy(pk_csr* A) {
   for (auto* v : A->vec) if (v) cudaFree(v);
   if (A->basis) cudaFree(A->basis);
   if (A->jac_va) cudaFree(A->jac_va);
+  if (A->sell_ptr) cudaFree(A->sell_ptr);
+  if (A->sell_perm) cudaFree(A->sell_perm);
+  if (A->sell_col) cudaFree(A->sell_col);
+  if (A->sell_val) cudaFree(A->sell_val);
   if (A->jac_d) cudaFree(A->jac_d);
   if (A->jac_dinv) cudaFree(A->jac_dinv);
   if (A->small) cudaFree(A->small);
@@ -596,7 +600,10 @@ pk_status pk_spmv_dot(pk_csr* A, const double* p, double* q, double* result, int
     PK_CUDA(cudaMemsetAsync(result, 0, sizeof(double), s));
     return PK_OK;
   }
-  if (fused) {
+  if (fused == 2) {
+    pk_status e = launch_sell_spmv_dot(A, p, q, result, s);
+    if (e) return e;
+  } else if (fused) {
     k_spmv_dot<<<A->grid, kBlock, 0, s>>>(row_args(A), p, q, result);
   } else {
     launch_spmv(A, p, q, s);

@@ -212,6 +212,14 @@ struct pk_csr {
   double* small = nullptr;            // small device scratch (R, xi, eta ...): 8192 doubles
   // right Jacobi preconditioning (built on first use): values of A diag(A)^-1, diag(A) and its
   // reciprocal; jac_state 0 = not built, 1 = built, -1 = a zero or non-finite diagonal entry
+  // SELL-C-sigma copy (built on first use; sell_nslices -1 = not built)
+  int32_t sell_nslices = -1;
+  int64_t sell_padded = 0;
+  int sell_grid = 1;
+  int64_t* sell_ptr = nullptr;
+  int32_t* sell_perm = nullptr;
+  int32_t* sell_col = nullptr;
+  double* sell_val = nullptr;
   double* jac_va = nullptr;
   double* jac_d = nullptr;
   double* jac_dinv = nullptr;
@@ -291,6 +299,49 @@ struct JacobiRight {
 };
 pk_status jacobi_right_enter(pk_csr* A, double* x, cudaStream_t s, JacobiRight* g);
 pk_status jacobi_right_leave(JacobiRight* g, double* x, cudaStream_t s);
+
+// SELL-C-sigma copy of a matrix (pk_sell.cu): slices of kSellC sorted rows, column-major.
+constexpr int kSellC = 32;
+constexpr int kSellWarps = kBlock / 32;
+struct SellArgs {
+  int32_t nslices;
+  const int64_t* ptr;    // slice starts (entries), nslices + 1
+  const int32_t* perm;   // row of every slice lane, -1 for padding lanes
+  const int32_t* col;    // -1 for padding entries
+  const double* val;
+};
+pk_status sell_build(pk_csr* A, cudaStream_t s);
+SellArgs sell_args(const pk_csr* A);
+pk_status launch_sell_spmv_dot(pk_csr* A, const double* p, double* q, double* out, cudaStream_t s);
+
+// Row product of lane `lane` of a slice: entries k < w at stride 32, four loads in flight
+// before their gathers and FMAs.
+__device__ __forceinline__ double sell_row(const SellArgs& s, int64_t base, int w,
+                                         const double* __restrict__ x) {
+  const int32_t* __restrict__ cc = s.col + base;
+  const double* __restrict__ vv = s.val + base;
+  double acc = 0.0;
+  int k = 0;
+  for (; k + 4 <= w; k += 4) {
+    int c[4];
+    double v[4], xv[4];
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+      c[u] = __ldg(cc + (size_t)(k + u) * kSellC);
+      v[u] = __ldg(vv + (size_t)(k + u) * kSellC);
+    }
+#pragma unroll
+    for (int u = 0; u < 4; ++u) xv[u] = c[u] >= 0 ? __ldg(x + c[u]) : 0.0;
+#pragma unroll
+    for (int u = 0; u < 4; ++u)
+      if (c[u] >= 0) acc = fma(v[u], xv[u], acc);
+  }
+  for (; k < w; ++k) {
+    const int c = __ldg(cc + (size_t)k * kSellC);
+    if (c >= 0) acc = fma(__ldg(vv + (size_t)k * kSellC), __ldg(x + c), acc);
+  }
+  return acc;
+}
 
 // Kernels on the CSR tile engine take the instantiation with the grouped and whole-warp row
 // paths when some tile needs one of them.

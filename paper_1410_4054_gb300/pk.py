@@ -28,6 +28,7 @@ FLAG_TIMING = 1
 FLAG_TRUE_RES = 2
 FLAG_NO_TMA = 4
 FLAG_AUTOTUNE = 8
+FLAG_SELL = 16
 SLOTS = ["spmv_dots", "update", "multidot", "ortho", "spmv", "blas1", "other"]
 MAX_SLOTS = 8
 
@@ -289,9 +290,12 @@ def spmv(A: CSRMatrix, x, y, stream=None):
     _check(lib().pk_spmv(A.handle, _ptr(x), _ptr(y), _stream_ptr(stream)), "pk_spmv")
 
 
-def spmv_dot(A: CSRMatrix, p, q, result, fused=True, stream=None):
-    _check(lib().pk_spmv_dot(A.handle, _ptr(p), _ptr(q), _ptr(result), 1 if fused else 0,
-                             _stream_ptr(stream)), "pk_spmv_dot")
+def spmv_dot(A: CSRMatrix, p, q, result, fused=True, stream=None, sell=False):
+    """pk_spmv_dot: q = A p, result[0] = <p, q>; fused (one launch) or not; sell: the fused
+    kernel on the SELL-C-sigma copy."""
+    mode = 2 if sell else (1 if fused else 0)
+    _check(lib().pk_spmv_dot(A.handle, _ptr(p), _ptr(q), _ptr(result), mode, _stream_ptr(stream)),
+           "pk_spmv_dot")
 
 
 def status_string(s: int) -> str:
