@@ -55,6 +55,8 @@ def lib():
                                 C.c_int32, C.c_int32, C.c_int32, C.c_int32, _dp, _dp, _dp, _dp,
                                 C.POINTER(C.c_int32), C.POINTER(C.c_int32)]
         L.orc_gmres.restype = C.c_int
+        L.orc_gmres_cgs2.argtypes = L.orc_gmres.argtypes + [_dp]
+        L.orc_gmres_cgs2.restype = C.c_int
         L.orc_jacobi_right_begin.argtypes = [C.c_int32, _i32p, _i32p, _f64p, _f64p, _f64p, _f64p]
         L.orc_jacobi_right_begin.restype = C.c_int
         L.orc_jacobi_right_end.argtypes = [C.c_int32, _f64p, _f64p]
@@ -149,9 +151,11 @@ def bicgstab(a, b, x0=None, tol=1e-8, maxit=1000, variant="pipelined", cap=None,
     return dict(x=x, iters=it.value, status=st, **tr)
 
 
-def gmres(a, b, x0=None, tol=1e-8, maxit=1000, m=30, variant="pipelined", cap=None, precond="none"):
+def gmres(a, b, x0=None, tol=1e-8, maxit=1000, m=30, variant="pipelined", cap=None, precond="none",
+          cgs2=False):
     """Algorithm 6 (variant='pipelined') or Algorithm 5 (variant='classical'), restarted;
-    precond='jacobi': right-preconditioned with M = diag(A) (run on A M^-1, x = M^-1 y)."""
+    precond='jacobi': right-preconditioned with M = diag(A) (run on A M^-1, x = M^-1 y);
+    cgs2: Gram-Schmidt applied twice per step."""
     n, rp, ci, va = _csr(a)
     cap = maxit + 2 if cap is None else cap
     b = np.ascontiguousarray(b, dtype=np.float64)
@@ -162,8 +166,17 @@ def gmres(a, b, x0=None, tol=1e-8, maxit=1000, m=30, variant="pipelined", cap=No
     est = np.full(cap, np.nan)
     res = np.full(cap, np.nan)
     it, cyc = C.c_int32(0), C.c_int32(0)
-    st = lib().orc_gmres(n, rp, ci, va, b, x, tol, maxit, m, 1 if variant == "pipelined" else 0,
-                         cap, _ptr(R), _ptr(xi), _ptr(est), _ptr(res), C.byref(it), C.byref(cyc))
+    args = (n, rp, ci, va, b, x, tol, maxit, m, 1 if variant == "pipelined" else 0,
+            cap, _ptr(R), _ptr(xi), _ptr(est), _ptr(res), C.byref(it), C.byref(cyc))
+    V = None
+    if cgs2:
+        V = np.full((m + 1, n), np.nan)
+        st = lib().orc_gmres_cgs2(*args, _ptr(V))
+    else:
+        st = lib().orc_gmres(*args)
     if dinv is not None:
         lib().orc_jacobi_right_end(n, dinv, x)
-    return dict(x=x, iters=it.value, cycles=cyc.value, status=st, R=R, xi=xi, est=est, res=res)
+    out = dict(x=x, iters=it.value, cycles=cyc.value, status=st, R=R, xi=xi, est=est, res=res)
+    if V is not None:
+        out["V"] = V   # first cycle's basis v_0 .. v_k (rows beyond k: NaN)
+    return out

@@ -17,6 +17,7 @@
  *   orc_gmres               Algorithms 5 and 6 (restarted simpler GMRES with classical
  *                           Gram-Schmidt; classical form updates the residual, pipelined
  *                           form uses xi_i = <v_0, v_i>)
+ *   orc_gmres_cgs2          the same with Gram-Schmidt applied twice per step (CGS2)
  *   orc_jacobi_right_begin  right preconditioning with M = diag(A) for BiCGStab and GMRES:
  *   orc_jacobi_right_end    the solver runs on A M^-1 y = b, and x = M^-1 y
  *   orc_pcg_jacobi          CG with the Jacobi preconditioner M = diag(A) (Sec. 5 names
@@ -476,10 +477,37 @@ done:
  * tr_est (cap) the per-step residual estimate; tr_res (cap) the true residual norm at
  * every cycle boundary (index = cycle).
  */
+static int gmres_run(int32_t n, const int32_t* rp, const int32_t* ci, const double* va,
+                     const double* b, double* x, double tol, int32_t maxit, int32_t m, int32_t pipelined,
+                     int32_t cgs2, int32_t cap, double* tr_R, double* tr_xi, double* tr_est,
+                     double* tr_res, double* tr_V, int32_t* iters_out, int32_t* cycles_out);
+
 int orc_gmres(int32_t n, const int32_t* rp, const int32_t* ci, const double* va,
               const double* b, double* x, double tol, int32_t maxit, int32_t m, int32_t pipelined,
               int32_t cap, double* tr_R, double* tr_xi, double* tr_est, double* tr_res,
               int32_t* iters_out, int32_t* cycles_out) {
+  return gmres_run(n, rp, ci, va, b, x, tol, maxit, m, pipelined, 0, cap, tr_R, tr_xi, tr_est, tr_res,
+                   NULL, iters_out, cycles_out);
+}
+
+/* The same GMRES with classical Gram-Schmidt applied twice per step (CGS2, "twice is
+ * enough": Giraud, Langou, Rozloznik, Comput. Math. Appl. 50, 2005): after v_i -= sum_j
+ * R_{j,i} v_j, the coefficients c_j = <v_j, v_i> (j = 1 .. i-1) are computed again, v_i -=
+ * sum_j c_j v_j, and R_{j,i} += c_j; the norm, R_{i,i} and the breakdown test follow the
+ * second pass.  tr_V (optional, n x (m+1), vector after vector) receives the first cycle's
+ * basis v_0 .. v_m. */
+int orc_gmres_cgs2(int32_t n, const int32_t* rp, const int32_t* ci, const double* va,
+                   const double* b, double* x, double tol, int32_t maxit, int32_t m, int32_t pipelined,
+                   int32_t cap, double* tr_R, double* tr_xi, double* tr_est, double* tr_res,
+                   int32_t* iters_out, int32_t* cycles_out, double* tr_V) {
+  return gmres_run(n, rp, ci, va, b, x, tol, maxit, m, pipelined, 1, cap, tr_R, tr_xi, tr_est, tr_res,
+                   tr_V, iters_out, cycles_out);
+}
+
+static int gmres_run(int32_t n, const int32_t* rp, const int32_t* ci, const double* va,
+                     const double* b, double* x, double tol, int32_t maxit, int32_t m, int32_t pipelined,
+                     int32_t cgs2, int32_t cap, double* tr_R, double* tr_xi, double* tr_est,
+                     double* tr_res, double* tr_V, int32_t* iters_out, int32_t* cycles_out) {
   *iters_out = 0;
   if (cycles_out) *cycles_out = 0;
   if (n <= 0) return ORC_OK;
@@ -494,8 +522,9 @@ int orc_gmres(int32_t n, const int32_t* rp, const int32_t* ci, const double* va,
   double* R = calloc((size_t)(m + 1) * (size_t)(m + 1), sizeof(double)); /* R[j][i], 1-based */
   double* xi = calloc((size_t)(m + 1), sizeof(double));
   double* eta = calloc((size_t)(m + 1), sizeof(double));
-  if (!V || !r || !acc || !R || !xi || !eta) {
-    free(V); free(r); free(acc); free(R); free(xi); free(eta); return ORC_ERR_OOM;
+  double* c2 = calloc((size_t)(m + 1), sizeof(double));
+  if (!V || !r || !acc || !R || !xi || !eta || !c2) {
+    free(V); free(r); free(acc); free(R); free(xi); free(eta); free(c2); return ORC_ERR_OOM;
   }
 #define VEC(i) (V + (size_t)(i) * (size_t)n)
 #define RR(j, i) R[(size_t)(j) * (size_t)(m + 1) + (size_t)(i)]
@@ -525,6 +554,14 @@ int orc_gmres(int32_t n, const int32_t* rp, const int32_t* ci, const double* va,
         double rji = RR(j, i);
         const double* vj = VEC(j);
         for (int32_t k = 0; k < n; ++k) vi[k] -= rji * vj[k];
+      }
+      if (cgs2) {                                       /* second pass (CGS2) */
+        for (int32_t j = 1; j <= i - 1; ++j) c2[j] = orc_dot(n, VEC(j), vi);
+        for (int32_t j = 1; j <= i - 1; ++j) {
+          const double* vj = VEC(j);
+          for (int32_t k = 0; k < n; ++k) vi[k] -= c2[j] * vj[k];
+        }
+        for (int32_t j = 1; j <= i - 1; ++j) RR(j, i) += c2[j];
       }
       double nrm2 = orc_dot(n, vi, vi);
       double rii = sqrt(nrm2);
@@ -562,6 +599,7 @@ int orc_gmres(int32_t n, const int32_t* rp, const int32_t* ci, const double* va,
           for (int32_t i = 1; i <= m; ++i) tr_R[(size_t)(j - 1) * m + (i - 1)] = RR(j, i);
       if (tr_xi)
         for (int32_t i = 1; i <= m; ++i) tr_xi[i - 1] = xi[i];
+      if (tr_V) memcpy(tr_V, V, sz * (size_t)(kdone + 1));
     }
     if (broke == 2) break;
     if (kdone == 0) { status = ORC_BREAKDOWN; break; }
@@ -584,6 +622,6 @@ int orc_gmres(int32_t n, const int32_t* rp, const int32_t* ci, const double* va,
 #undef RR
   *iters_out = total;
   if (cycles_out) *cycles_out = cycle;
-  free(V); free(r); free(acc); free(R); free(xi); free(eta);
+  free(V); free(r); free(acc); free(R); free(xi); free(eta); free(c2);
   return status;
 }

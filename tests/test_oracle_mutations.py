@@ -35,8 +35,8 @@ MUTANTS = {
     "spmv_transposed_gather": ("s += va[j] * x[ci[j]];", "s += va[j] * x[i];"),
 }
 
-# mutants of the preconditioned solvers, checked against their own pin files
-PRECOND_MUTANTS = {
+# mutants of the preconditioned solvers and of CGS2, checked against their own pin files
+EXTRA_MUTANTS = {
     "pcg_beta_sign": ([("beta = alpha * alpha * qdq / gamma - 1.0;", "beta = alpha * alpha * qdq / gamma + 1.0;")],
                       "test_oracle_pcg.py"),
     "pcg_qdq_unpreconditioned": ([("z[k] = ap[k] * dinv[k];", "z[k] = ap[k];")], "test_oracle_pcg.py"),
@@ -46,15 +46,21 @@ PRECOND_MUTANTS = {
                                  "test_oracle_jacobi_right.py"),
     "jacobi_right_y0_unscaled": ([("x[i] = x[i] * d;", "x[i] = x[i];")], "test_oracle_jacobi_right.py"),
     "jacobi_right_end_skipped": ([("x[i] = dinv[i] * x[i];", "x[i] = x[i];")], "test_oracle_jacobi_right.py"),
+    # (the second pass's coefficients are O(eps ||A v_{i-1}||): leaving them out of R is not
+    # observable above rounding, so that edit is not a mutant; the second pass acts through v_i)
+    "cgs2_second_pass_not_subtracted": ([("for (int32_t k = 0; k < n; ++k) vi[k] -= c2[j] * vj[k];", "")],
+                                        "test_oracle_cgs2.py"),
+    "cgs2_second_pass_sign": ([("for (int32_t k = 0; k < n; ++k) vi[k] -= c2[j] * vj[k];",
+                                "for (int32_t k = 0; k < n; ++k) vi[k] += c2[j] * vj[k];")], "test_oracle_cgs2.py"),
 }
 
 
-@pytest.mark.parametrize("name", sorted(MUTANTS) + sorted(PRECOND_MUTANTS))
+@pytest.mark.parametrize("name", sorted(MUTANTS) + sorted(EXTRA_MUTANTS))
 def test_pins_catch_mutant(name, tmp_path):
     if name in MUTANTS:
         edits, pins = MUTANTS[name], "test_oracle_pins.py"
     else:
-        edits, pins = PRECOND_MUTANTS[name]
+        edits, pins = EXTRA_MUTANTS[name]
     edits = edits if isinstance(edits, list) else [edits]
     text = SRC
     for old, new in edits:
