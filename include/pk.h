@@ -96,6 +96,12 @@ enum {
                                 first use, kept with the handle) instead of the CSR tiles.  Other
                                 solvers, variants, precisions, PK_LOOP_PERSISTENT and
                                 preconditioners return PK_ERR_ARG */
+#define PK_FLAG_CGS2 32u     /* GMRES: classical Gram-Schmidt applied twice per Arnoldi step
+                                (c_j = <v_j, v_i> again after the first projection, v_i -=
+                                sum c_j v_j, R_{j,i} += c_j; two more launches per step), which
+                                keeps the basis orthonormal and the in-cycle residual estimate
+                                exact on badly conditioned systems.  Other solvers return
+                                PK_ERR_ARG */
 
 typedef struct {
   double tol;          /* relative residual tolerance (>= 0) */

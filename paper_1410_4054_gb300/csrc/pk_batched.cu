@@ -345,6 +345,7 @@ pk_status batched_solve(int32_t nsys, pk_csr* const* A, const double* const* b, 
   if (!(o->tol >= 0.0) || o->maxit < 0) { set_error("tol must be >= 0 and maxit >= 0"); return PK_ERR_ARG; }
   if (o->precond != PK_PRECOND_NONE) { set_error("the batched solver has no preconditioner"); return PK_ERR_ARG; }
   if (o->flags & PK_FLAG_SELL) { set_error("PK_FLAG_SELL applies to pipelined FP64 CG"); return PK_ERR_ARG; }
+  if (o->flags & PK_FLAG_CGS2) { set_error("PK_FLAG_CGS2 applies to GMRES"); return PK_ERR_ARG; }
   if (nsys == 0) return PK_OK;
   const int mixed = o->precision == PK_PREC_MIXED;
   pk_status e;

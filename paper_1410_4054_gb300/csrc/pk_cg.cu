@@ -450,6 +450,7 @@ pk_status cg_solve(pk_csr* A, const double* b, double* x, const pk_opts* o, pk_i
   *info = pk_info{};
   info->rel_res_true = -1.0;
   if (A->n == 0) return PK_OK;
+  if (o->flags & PK_FLAG_CGS2) { set_error("PK_FLAG_CGS2 applies to GMRES"); return PK_ERR_ARG; }
   const bool sell = (o->flags & PK_FLAG_SELL) != 0;
   if (sell && (o->precond != PK_PRECOND_NONE || o->precision != PK_PREC_FP64 ||
                o->variant != PK_VARIANT_PIPELINED || o->loop == PK_LOOP_PERSISTENT)) {

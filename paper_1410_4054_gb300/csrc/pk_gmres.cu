@@ -15,6 +15,9 @@
 //          x += rho0 (eta_1 v_0 + sum_{i>=2} eta_i v_{i-1}).
 // The classical form replaces K-GM-4 by a normalisation kernel, xi_i = <r, v_i>, the residual
 // update r -= xi_i v_i and ||r|| as separate kernels (r is only monitored, R12).
+// PK_FLAG_CGS2 applies Gram-Schmidt twice per step: K-GM-3 without the norm, then K-GM-2
+// for c_j = <v_j, v_i>, j = 1 .. i-1, and K-GM-3 again with v_i -= sum c_j v_j,
+// R_{j,i} += c_j and ||v_i|| (two more launches per step).
 // The graph is an outer WHILE loop over cycles around an inner WHILE loop over steps.
 #include <algorithm>
 #include <cmath>
@@ -38,6 +41,7 @@ struct GmArgs {
   double* V;         // basis v_0..v_m, column j at V + j * ld
   double* R;         // R[j * kRld + i]
   double* xi;        // xi[i]
+  double* C;         // CGS2: second-pass coefficients c_j, j = 1 .. i-1
   double* r;         // classical form: the monitored residual
   const double* b;
   double* x;
@@ -263,12 +267,13 @@ __device__ __forceinline__ double gm3_row(const BasisRing& R, int s, int row, co
 // streamed one after the other (v_i with every group).  Each consumer thread keeps one
 // accumulator per column of the group; the warp's accumulators are reduced across the lanes
 // by recursive halving (16 shuffle-adds per lane), then over the warps in a fixed order.
-__global__ void __launch_bounds__(kTileThreads, 2) k_gm2(GmArgs g) {
+// pass = 1 (CGS2): j = 1 .. i-1 into C.
+__global__ void __launch_bounds__(kTileThreads, 2) k_gm2(GmArgs g, int pass) {
   extern __shared__ __align__(128) unsigned char smem[];
   DevState* st = g.st;
   if (!gm_step_live(st)) return;
   const int i = __ldcg(&st->gm_i);
-  const int nj = i - 2;
+  const int nj = pass ? i - 1 : i - 2;
   if (nj <= 0) return;
   int r0, r1;
   ew_range(g.n, r0, r1);
@@ -363,7 +368,10 @@ __global__ void __launch_bounds__(kTileThreads, 2) k_gm2(GmArgs g) {
       double t = 0.0;
       for (int bk = lane; bk < G; bk += 32) t += ld_cg(g.partials + (size_t)(j - 1) * G + bk);
       t = warp_sum(t);
-      if (lane == 0) g.R[j * kRld + i] = t;
+      if (lane == 0) {
+        if (pass) g.C[j] = t;
+        else g.R[j * kRld + i] = t;
+      }
     }
     if (threadIdx.x == 0) st->counter = 0;
   }
@@ -372,14 +380,16 @@ __global__ void __launch_bounds__(kTileThreads, 2) k_gm2(GmArgs g) {
 // K-GM-3: v_i -= sum_{j=1}^{i-1} R_{j,i} v_j (in order j = 1, 2, ...) with the first stage of
 // ||v_i||^2.  Tiles outer, column groups inner: each consumer thread keeps its row of v_i in
 // a register across the groups of the tile, then stores it.  Last block: R_{i,i} and the
-// lucky-breakdown test (R13).
-__global__ void __launch_bounds__(kTileThreads, 2) k_gm3(GmArgs g) {
+// lucky-breakdown test (R13).  mode 1 (CGS2, first pass): no norm, no epilogue; mode 2 (CGS2,
+// second pass): coefficients c_j from C, then R_{j,i} += c_j before R_{i,i} and the test.
+__global__ void __launch_bounds__(kTileThreads, 2) k_gm3(GmArgs g, int mode) {
   extern __shared__ __align__(128) unsigned char smem[];
   DevState* st = g.st;
   if (!gm_step_live(st)) return;
   const int i = __ldcg(&st->gm_i);
   __shared__ double coef[kGmMax];
-  for (int j = threadIdx.x; j < i - 1; j += blockDim.x) coef[j] = ld_cg(g.R + (j + 1) * kRld + i);
+  for (int j = threadIdx.x; j < i - 1; j += blockDim.x)
+    coef[j] = mode == 2 ? ld_cg(g.C + j + 1) : ld_cg(g.R + (j + 1) * kRld + i);
   int r0, r1;
   ew_range(g.n, r0, r1);
   const int ntiles = r1 > r0 ? (r1 - r0 + kBsRows - 1) / kBsRows : 0;
@@ -427,10 +437,11 @@ __global__ void __launch_bounds__(kTileThreads, 2) k_gm3(GmArgs g) {
       if (!ok) break;
       if (mine) {
         vi[row0 + threadIdx.x] = w;
-        v[0] = fma(w, w, v[0]);
+        if (mode != 1) v[0] = fma(w, w, v[0]);
       }
     }
   }
+  if (mode == 1) return;
   tile_block_partials<1>(v, g.partials);
   if (arrive_last(&st->counter)) {
     double t[1];
@@ -438,7 +449,12 @@ __global__ void __launch_bounds__(kTileThreads, 2) k_gm3(GmArgs g) {
     if (threadIdx.x == 0) {
       const double nrm2 = t[0];
       double col2 = nrm2;
-      for (int j = 1; j < i; ++j) col2 += coef[j - 1] * coef[j - 1];
+      if (mode == 2)
+        for (int j = 1; j < i; ++j) g.R[j * kRld + i] += coef[j - 1];
+      for (int j = 1; j < i; ++j) {
+        const double rji = mode == 2 ? g.R[j * kRld + i] : coef[j - 1];
+        col2 += rji * rji;
+      }
       const double rii = sqrt(nrm2);
       if (!isfinite(rii)) {
         gm_finish(st, PK_ERR_NAN);
@@ -659,6 +675,7 @@ pk_status gmres_solve(pk_csr* A, const double* b, double* x, const pk_opts* o, p
   }
   if (o->precond != PK_PRECOND_NONE && o->precond != PK_PRECOND_JACOBI) { set_error("bad precond"); return PK_ERR_ARG; }
   if (o->flags & PK_FLAG_SELL) { set_error("PK_FLAG_SELL applies to pipelined FP64 CG"); return PK_ERR_ARG; }
+  const bool cgs2 = (o->flags & PK_FLAG_CGS2) != 0;
   if (!A->tma_ok) { set_error("GMRES needs the tile engine (rows longer than 4096 nonzeros are not supported)"); return PK_ERR_ARG; }
   if ((e = gm_setup())) return e;
   const int n = A->n;
@@ -691,6 +708,7 @@ pk_status gmres_solve(pk_csr* A, const double* b, double* x, const pk_opts* o, p
   g.V = A->basis;
   g.R = A->small;
   g.xi = A->small + kXiOff;
+  g.C = A->small + kXiOff + kRld;
   g.r = rc;
   g.b = v.b_dev;
   g.x = v.x_dev;
@@ -721,10 +739,17 @@ pk_status gmres_solve(pk_csr* A, const double* b, double* x, const pk_opts* o, p
     if (t) t->begin(PK_SLOT_SPMV_DOTS);
     (irr ? k_gm1<true> : k_gm1<false>)<<<Gt, kTileThreads, csr_smem_bytes(), cs>>>(ct, g);
     if (t) { t->end(); t->begin(PK_SLOT_MULTIDOT); }
-    k_gm2<<<Gs, kTileThreads, kBsSmem, cs>>>(g);
+    k_gm2<<<Gs, kTileThreads, kBsSmem, cs>>>(g, 0);
     if (t) { t->end(); t->begin(PK_SLOT_ORTHO); }
-    k_gm3<<<Gs, kTileThreads, kBsSmem, cs>>>(g);
+    k_gm3<<<Gs, kTileThreads, kBsSmem, cs>>>(g, cgs2 ? 1 : 0);
     if (t) t->end();
+    if (cgs2) {  // second Gram-Schmidt pass
+      if (t) t->begin(PK_SLOT_MULTIDOT);
+      k_gm2<<<Gs, kTileThreads, kBsSmem, cs>>>(g, 1);
+      if (t) { t->end(); t->begin(PK_SLOT_ORTHO); }
+      k_gm3<<<Gs, kTileThreads, kBsSmem, cs>>>(g, 2);
+      if (t) t->end();
+    }
     if (!classical) {
       if (t) t->begin(PK_SLOT_UPDATE);
       k_gm4<<<Gs, kTileThreads, stream_smem_bytes<2, double, 4>(), cs>>>(g);
@@ -746,11 +771,11 @@ pk_status gmres_solve(pk_csr* A, const double* b, double* x, const pk_opts* o, p
     k_gm_end<<<Ge, kBlock, 0, cs>>>(g);
     if (t) t->end();
   };
-  const int step_kernels = classical ? 7 : 4;
+  const int step_kernels = (classical ? 7 : 4) + (cgs2 ? 2 : 0);
   const bool graph = o->loop != PK_LOOP_HOST && !T.on;
   if (graph) {
     const void* keys[4] = {v.x_dev, v.b_dev, nullptr, nullptr};
-    const int64_t ikeys[4] = {o->variant, m, o->precond, 0};  // precond: values of A or of A M^-1
+    const int64_t ikeys[4] = {o->variant, m, o->precond, cgs2};  // precond: values of A or of A M^-1
     pk_graph_entry* ge = nullptr;
     if ((e = build_nested_graph(A, 6 + (classical ? 1 : 0), keys, ikeys,
                                 [&](cudaStream_t cs) { pre(cs, nullptr); },

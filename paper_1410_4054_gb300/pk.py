@@ -29,6 +29,7 @@ FLAG_TRUE_RES = 2
 FLAG_NO_TMA = 4
 FLAG_AUTOTUNE = 8
 FLAG_SELL = 16
+FLAG_CGS2 = 32
 SLOTS = ["spmv_dots", "update", "multidot", "ortho", "spmv", "blas1", "other"]
 MAX_SLOTS = 8
 

@@ -50,12 +50,12 @@ MATRICES = {
 }
 
 
-def oracle_sensitivity(a, b, variant, m, tol, maxit, nsamp=3, precond="none"):
+def oracle_sensitivity(a, b, variant, m, tol, maxit, nsamp=3, precond="none", cgs2=False):
     """The oracle's own rounding sensitivity: rerun it with b perturbed by about one ulp
     (relative 2^-52, three seeds); running maxima of the change of R (relative to max |R|)
     and xi per step of the first cycle, of the iteration count and of x at a fixed count."""
-    base = O.gmres(a, b, tol=tol, maxit=maxit, m=m, variant=variant, precond=precond)
-    fixed = O.gmres(a, b, tol=0.0, maxit=max(base["iters"], 1), m=m, variant=variant, precond=precond)
+    base = O.gmres(a, b, tol=tol, maxit=maxit, m=m, variant=variant, precond=precond, cgs2=cgs2)
+    fixed = O.gmres(a, b, tol=0.0, maxit=max(base["iters"], 1), m=m, variant=variant, precond=precond, cgs2=cgs2)
     k = min(m, max(base["iters"], 1))
     sR = np.zeros(k)
     sX = np.zeros(k)
@@ -63,12 +63,12 @@ def oracle_sensitivity(a, b, variant, m, tol, maxit, nsamp=3, precond="none"):
     scale = np.abs(base["R"][:k, :k]).max()
     for smp in range(nsamp):
         bp = b * (1 + 2.0 ** -52 * W.uniform_pm1(100 + smp, a.n))
-        r = O.gmres(a, bp, tol=tol, maxit=maxit, m=m, variant=variant, precond=precond)
+        r = O.gmres(a, bp, tol=tol, maxit=maxit, m=m, variant=variant, precond=precond, cgs2=cgs2)
         dR = np.abs(r["R"][:k, :k] - base["R"][:k, :k]).max(axis=0) / scale
         sR = np.fmax(sR, dR)
         sX = np.fmax(sX, np.abs(r["xi"][:k] - base["xi"][:k]))
         it_spread = max(it_spread, abs(r["iters"] - base["iters"]))
-        rf = O.gmres(a, bp, tol=0.0, maxit=max(base["iters"], 1), m=m, variant=variant, precond=precond)
+        rf = O.gmres(a, bp, tol=0.0, maxit=max(base["iters"], 1), m=m, variant=variant, precond=precond, cgs2=cgs2)
         x_spread = max(x_spread, rel(rf["x"], fixed["x"]))
     return base, fixed, np.maximum.accumulate(sR), np.maximum.accumulate(sX), it_spread, x_spread
 
@@ -109,26 +109,44 @@ JACOBI_MATRICES = {
 }
 
 
+CGS2_MATRICES = {
+    "convdiff_16": lambda: W.convdiff_3d(16),
+    "powerlaw_1e4": lambda: W.power_law(10_000, seed=1),
+    "fe3d_elast_540": lambda: W.fe_elasticity_3d(5),
+    "convdiff10_scaled": lambda: W.diag_scaled(W.convdiff_3d(10), seed=3, spread=100.0),
+}
+
+
 @pytest.mark.parametrize("variant", ["pipelined", "classical"])
-@pytest.mark.parametrize("name", sorted(MATRICES) + [f"jacobi:{k}" for k in sorted(JACOBI_MATRICES)])
+@pytest.mark.parametrize("name", sorted(MATRICES) + [f"jacobi:{k}" for k in sorted(JACOBI_MATRICES)]
+                         + [f"cgs2:{k}" for k in sorted(CGS2_MATRICES)])
 def test_gmres_parity(name, variant):
-    """'jacobi:' cases: right preconditioning with M = diag(A) on both sides."""
+    """'jacobi:' cases: right preconditioning with M = diag(A) on both sides; 'cgs2:' cases:
+    Gram-Schmidt applied twice per step on both sides."""
     precond = "jacobi" if name.startswith("jacobi:") else "none"
-    a = JACOBI_MATRICES[name[7:]]() if precond == "jacobi" else MATRICES[name]()
+    cgs2 = name.startswith("cgs2:")
+    if precond == "jacobi":
+        a = JACOBI_MATRICES[name[7:]]()
+    elif cgs2:
+        a = CGS2_MATRICES[name[5:]]()
+    else:
+        a = MATRICES[name]()
     _, b, _ = W.manufactured(a, seed=0)
     m = 30
     ref, fixed, sR, sX, it_spread, x_spread = oracle_sensitivity(a, b, variant, m, 1e-8, 20_000,
-                                                                 precond=precond)
+                                                                 precond=precond, cgs2=cgs2)
     assert ref["status"] == O.OK
+    fl = pk.FLAG_CGS2 if cgs2 else 0
     info, x, tr = solve(a, b, tol=1e-8, maxit=20_000, restart=m, variant=variant,
-                        flags=pk.FLAG_TRUE_RES, trace_cap=max(256, ref["iters"] + 8), precond=precond)
+                        flags=pk.FLAG_TRUE_RES | fl, trace_cap=max(256, ref["iters"] + 8), precond=precond)
     assert info["status"] == pk.PK_OK, info
     assert info["rel_res_true"] <= 1.5e-8
     first_cycle_check(tr, ref, sR, sX, ref["iters"])
     k_orc, k_gpu = first_cycle_lengths(tr, ref, ref["iters"])
     if k_orc == k_gpu or ref["iters"] <= min(k_orc, k_gpu):
         assert abs(info["iters"] - ref["iters"]) <= max(2, 2 * it_spread)
-        info2, x2, _ = solve(a, b, tol=0.0, maxit=ref["iters"], restart=m, variant=variant, precond=precond)
+        info2, x2, _ = solve(a, b, tol=0.0, maxit=ref["iters"], restart=m, variant=variant, precond=precond,
+                             flags=fl)
         assert info2["iters"] == ref["iters"] and info2["cycles"] == fixed["cycles"]
         assert rel(x2, fixed["x"]) <= max(1e-9, 10 * x_spread)
     else:
@@ -137,8 +155,8 @@ def test_gmres_parity(name, variant):
         # both took (a fixed count that ends the first cycle on both sides)
         assert info["iters"] <= ref["iters"] + m
         k = min(k_orc, k_gpu)
-        _, fixed_k, _, _, _, xs_k = oracle_sensitivity(a, b, variant, m, 0.0, k, precond=precond)
-        info2, x2, _ = solve(a, b, tol=0.0, maxit=k, restart=m, variant=variant, precond=precond)
+        _, fixed_k, _, _, _, xs_k = oracle_sensitivity(a, b, variant, m, 0.0, k, precond=precond, cgs2=cgs2)
+        info2, x2, _ = solve(a, b, tol=0.0, maxit=k, restart=m, variant=variant, precond=precond, flags=fl)
         assert info2["iters"] == k and info2["cycles"] == fixed_k["cycles"]
         assert rel(x2, fixed_k["x"]) <= max(1e-9, 10 * xs_k)
 
@@ -177,15 +195,40 @@ def test_gmres_restart_lengths_and_loops(m, loop):
 
 
 def test_gmres_launch_counts():
-    """Sec. 3.3: four kernels per pipelined Arnoldi step (the classical form here: seven)."""
+    """Sec. 3.3: four kernels per pipelined Arnoldi step (the classical form here: seven);
+    CGS2 adds a second K-GM-2 / K-GM-3 pair."""
     a = W.convdiff_3d(10)
     _, b, _ = W.manufactured(a)
     per = {}
     for variant in ("pipelined", "classical"):
-        i10, _, _ = solve(a, b, tol=0.0, maxit=10, restart=30, variant=variant)
-        i20, _, _ = solve(a, b, tol=0.0, maxit=20, restart=30, variant=variant)
-        per[variant] = (i20["launches"] - i10["launches"]) / 10
-    assert per == {"pipelined": 4, "classical": 7}
+        for fl, tag in ((0, ""), (pk.FLAG_CGS2, "+cgs2")):
+            i10, _, _ = solve(a, b, tol=0.0, maxit=10, restart=30, variant=variant, flags=fl)
+            i20, _, _ = solve(a, b, tol=0.0, maxit=20, restart=30, variant=variant, flags=fl)
+            per[variant + tag] = (i20["launches"] - i10["launches"]) / 10
+    assert per == {"pipelined": 4, "classical": 7, "pipelined+cgs2": 6, "classical+cgs2": 9}
+
+
+@pytest.mark.parametrize("make", [lambda: W.diag_scaled(W.laplace_2d(40), seed=3, spread=1e3),
+                                  lambda: W.diag_scaled(W.fe_elasticity_3d(5), seed=6, spread=1e3)])
+def test_gmres_cgs2_estimate_matches_true_residual(make):
+    """After a full cycle of 30 pipelined steps the in-cycle estimate rho0 sqrt(1 - sum xi^2)
+    equals ||b - A x|| to 1e-9 with CGS2 (the basis stays orthonormal), on the GPU as in the
+    oracle."""
+    a = make()
+    _, b, _ = W.manufactured(a, seed=1)
+    info, x, tr = solve(a, b, tol=0.0, maxit=30, restart=30, flags=pk.FLAG_CGS2 | pk.FLAG_TRUE_RES)
+    assert info["iters"] == 30
+    true = info["rel_res_true"] * np.linalg.norm(b)
+    assert abs(tr[29, 3] - true) <= 1e-9 * true
+
+
+def test_cgs2_flag_rejected_elsewhere():
+    a = W.laplace_2d(20)
+    _, b, _ = W.manufactured(a)
+    A = pk.CSRMatrix.from_workload(a)
+    for fn in (pk.cg_solve, pk.bicgstab_solve):
+        with pytest.raises(RuntimeError, match="PK_FLAG_CGS2"):
+            fn(A, dev(b), dev(np.zeros(a.n)), flags=pk.FLAG_CGS2)
 
 
 def test_gmres_edge_cases():
