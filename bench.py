@@ -58,8 +58,10 @@ def parse():
     ap.add_argument("--variant", default="pipelined")
     ap.add_argument("--solver", default="cg", choices=["cg", "bicgstab", "gmres"],
                     help="--mode kernels: cg on the Laplacian, bicgstab / gmres on convection-diffusion")
-    ap.add_argument("--matrix", default="stencil", choices=["stencil", "powerlaw"],
-                    help="--mode kernels: the stencil of --k, or a power-law matrix with --n rows")
+    ap.add_argument("--matrix", default="stencil", choices=["stencil", "powerlaw", "fe3d"],
+                    help="--mode kernels: the stencil of --k, a power-law matrix with --n rows, or P1 "
+                         "elasticity on --k^3 cubes")
+    ap.add_argument("--sell", action="store_true", help="--mode kernels, cg: K-CG-S on the SELL-C-sigma copy")
     ap.add_argument("--n", type=int, default=1_000_000)
     ap.add_argument("--no-forms", action="store_true",
                     help="skip the BiCGStab / GMRES / batched / mixed-precision lines")
@@ -74,6 +76,8 @@ def run_kernels(args):
 
     if args.matrix == "powerlaw":
         a = W.power_law(args.n, seed=0)
+    elif args.matrix == "fe3d":
+        a = W.fe_elasticity_3d(args.k)
     else:
         a = W.laplace_3d(args.k) if args.solver == "cg" else W.convdiff_3d(args.k)
     _, b, _ = W.manufactured(a, seed=0)
@@ -82,7 +86,7 @@ def run_kernels(args):
     xd = torch.zeros(a.n, dtype=torch.float64, device="cuda")
     fn = {"cg": pk.cg_solve, "bicgstab": pk.bicgstab_solve, "gmres": pk.gmres_solve}[args.solver]
     info = fn(A, bd, xd, tol=0.0, maxit=args.iters, variant=args.variant, loop="host",
-              check_every=args.iters)
+              check_every=args.iters, flags=pk.FLAG_SELL if args.sell else 0)
     torch.cuda.synchronize()
     print(json.dumps({"mode": "kernels", "solver": args.solver, "k": args.k, "n": a.n, "iters": info["iters"],
                       "launches": info["launches"], "solve_ms": info["solve_ms"]}))
