@@ -15,7 +15,7 @@ x_hat = e + s0 net(input), loss = mean((net - (x_t - e)/s0)^2).  The weights sta
 identity on channel 0 (relu(z) - relu(-z) = z through two hidden channels), i.e. at the Jacobi
 step, and training moves them from there.
 The solver is always run to the same tolerance: of x_hat and x_{t-1}, the one with the smaller
-residual ||b - A x0|| is the initial guess, so the plain warm start is both fallback and judge.
+residual ||b - A x0|| is the initial guess, so the plain warm start is both fallback and yardstick.
 The experiment also reports the extrapolation alone (network output taken as zero), so the
 network's own contribution is visible.
 """
@@ -141,7 +141,7 @@ def run_transient(k=64, steps=300, train_last=150, epochs=30, lr=1e-3, tol=1e-8,
                   device="cuda", log=None):
     """The transient experiment: solve the whole sequence with the x_{t-1} warm start, train on
     steps 2..train_last, then re-solve steps train_last+1..steps from (a) the linear
-    extrapolation 2 x_{t-1} - x_{t-2} and (b) the learned guess, each judged against x_{t-1} by
+    extrapolation 2 x_{t-1} - x_{t-2} and (b) the learned guess, each measured against x_{t-1} by
     its residual.  Returns per-step iteration counts and times of all three, plus training
     statistics."""
     import torch
