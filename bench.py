@@ -530,6 +530,7 @@ def bench_forms(pk, torch, dev, args):
     out["batched"] = brow
     for M in As:
         M.close()
+    out["batched_fe"] = batched_fe(pk, torch, dev)
 
     a = W.laplace_3d(args.k)
     _, b, _ = W.manufactured(a, seed=0)
@@ -624,6 +625,32 @@ def solver_rooflines(solver, n, nnz, km):
                          "frac_hbm": gbs / peak, "fp64_tflops": tf, "fp64_peak_tflops": FP64_NOMINAL_TFLOPS,
                          "frac": tf / FP64_NOMINAL_TFLOPS, "peak_source": "nominal FP64"}
     return out
+
+
+def batched_fe(pk, torch, dev, nsys=256):
+    """Batched FP64 pipelined CG on 256 uneven P1 elasticity systems (k = 3..7 cubes: 144 to
+    1,536 rows, up to 45 nonzeros per row) to 1e-10: solves/s with the autotuned block shape
+    and lanes per row, against one thread per row (lanes = 1, its best block shape)."""
+    ks = 3 + (W.splitmix64(7, nsys) % np.uint64(5)).astype(int)
+    mats = [W.fe_elasticity_3d(int(k), seed=i) for i, k in enumerate(ks)]
+    rhs = [W.manufactured(m, seed=i)[1] for i, m in enumerate(mats)]
+    As = [pk.CSRMatrix.from_workload(m) for m in mats]
+    bs = [torch.from_numpy(v).to(dev) for v in rhs]
+    xs = [torch.zeros(m.n, dtype=torch.float64, device=dev) for m in mats]
+    row = {"systems": nsys, "rows": int(sum(m.n for m in mats)), "nnz": int(sum(m.nnz for m in mats)), "tol": 1e-10}
+    for key, lanes in (("tuned", 0), ("one_lane", 1)):
+        kw = dict(tol=1e-10, maxit=20_000, flags=pk.FLAG_AUTOTUNE, lanes=lanes)
+        pk.batched_solve(As, bs, [v.zero_() for v in xs], **kw)
+        ms = min(pk.batched_solve(As, bs, [v.zero_() for v in xs], **kw)[0]["solve_ms"] for _ in range(3))
+        infos = pk.batched_solve(As, bs, [v.zero_() for v in xs], **kw)
+        row[f"{key}_ms"] = ms
+        row[f"{key}_solves_per_s"] = nsys / (ms * 1e-3)
+        row[f"{key}_all_converged"] = all(i["status"] == pk.PK_OK for i in infos)
+        row[f"{key}_config"] = list(pk.batched_last_config()) + [pk.batched_last_lanes()]
+    row["speedup_tuned_vs_one_lane"] = row["one_lane_ms"] / row["tuned_ms"]
+    for M in As:
+        M.close()
+    return row
 
 
 def jacobi_pcg(pk, torch, dev, k):

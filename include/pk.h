@@ -118,6 +118,9 @@ typedef struct {
                           GMRES writes {R_{i-1,i}, R_{i,i}, xi_i, estimate_i} */
   int32_t precond;     /* PK_PRECOND_*: CG, BiCGStab, GMRES (0 = none; the batched solver
                           takes none) */
+  int32_t lanes;       /* pk_batched_solve: lanes per matrix row in the row products (1, 2, 4
+                          or 8; 0 = automatic: from the batch's mean row length, or tuned with
+                          the block shape under PK_FLAG_AUTOTUNE).  Other solvers ignore it */
 } pk_opts;
 
 /* pk_opts.precond.  JACOBI, M = diag(A) (entries of row i in column i summed; Sec. 5 names
@@ -266,6 +269,9 @@ pk_status pk_batched_solve(int32_t nsys, pk_csr* const* A, const double* const* 
 
 /* Block size and blocks per SM used by the last pk_batched_solve call in this process. */
 pk_status pk_batched_last_config(int32_t* block, int32_t* blocks_per_sm);
+
+/* Lanes per row (1, 2, 4 or 8) that the last pk_batched_solve call ran with. */
+pk_status pk_batched_last_lanes(int32_t* lanes);
 
 /*
  * Allocation-free q = A p and *result = <p, q>.  The paper has no counterpart: this entry

@@ -117,19 +117,91 @@ __device__ __forceinline__ float row_f32(const BatchSys& S, const float* __restr
   return s;
 }
 
-// Pipelined CG (Alg. 2) on one system by one block, FP64.  Returns the status.
-__device__ int cta_cg64(BatchSys& S, double tol, int maxit) {
+// Rows computed by groups of G lanes (G = 2, 4 or 8, aligned in the warp; the autotuned
+// lanes per row): lane q sums entries j0 + q, j0 + q + G, ... left to right, then the group
+// adds by a butterfly over its own lanes.  Every lane of a group walks the same rows, so the
+// group is converged at the shuffles.
+struct RowGroup {
+  int G, q, g0, gs;
+  unsigned mask;
+};
+
+__device__ __forceinline__ RowGroup row_group(int G) {
+  RowGroup g;
+  g.G = G;
+  g.q = (int)threadIdx.x & (G - 1);
+  g.g0 = (int)threadIdx.x / G;
+  g.gs = (int)blockDim.x / G;
+  g.mask = G >= 32 ? 0xffffffffu : (((1u << G) - 1u) << (((int)threadIdx.x & 31) & ~(G - 1)));
+  return g;
+}
+
+__device__ __forceinline__ double fma_b(double a, double b, double c) { return fma(a, b, c); }
+__device__ __forceinline__ float fma_b(float a, float b, float c) { return fmaf(a, b, c); }
+
+template <class T>
+__device__ __forceinline__ T row_grouped(const int32_t* __restrict__ rp, const int32_t* __restrict__ ci,
+                                         const T* __restrict__ va, const T* __restrict__ x, int row,
+                                         const RowGroup& g) {
+  const int j1 = __ldg(rp + row + 1);
+  T s = (T)0;
+  int j = __ldg(rp + row) + g.q;
+  for (; j + 3 * g.G < j1; j += 4 * g.G) {
+    int c[4];
+    T v[4], xv[4];
+#pragma unroll
+    for (int k = 0; k < 4; ++k) { c[k] = __ldg(ci + j + k * g.G); v[k] = __ldg(va + j + k * g.G); }
+#pragma unroll
+    for (int k = 0; k < 4; ++k) xv[k] = x[c[k]];
+#pragma unroll
+    for (int k = 0; k < 4; ++k) s = fma_b(v[k], xv[k], s);
+  }
+  for (; j < j1; j += g.G) s = fma_b(__ldg(va + j), x[__ldg(ci + j)], s);
+  for (int o = g.G >> 1; o > 0; o >>= 1) s += __shfl_xor_sync(g.mask, s, o);
+  return s;
+}
+
+// Row products of the block's system: one thread per row (G = 1, the plain loop) or a group
+// of G lanes per row; f(row, y) runs in the row's first lane.
+template <class F>
+__device__ __forceinline__ void rows_f64(const BatchSys& S, const double* __restrict__ x, int G, F&& f) {
+  if (G == 1) {
+    for (int row = threadIdx.x; row < S.n; row += blockDim.x) f(row, row_f64(S, x, row));
+  } else {
+    const RowGroup g = row_group(G);
+    for (int row = g.g0; row < S.n; row += g.gs) {
+      const double y = row_grouped(S.rp, S.ci, S.va, x, row, g);
+      if (g.q == 0) f(row, y);
+    }
+  }
+}
+
+template <class F>
+__device__ __forceinline__ void rows_f32(const BatchSys& S, const float* __restrict__ x, int G, F&& f) {
+  if (G == 1) {
+    for (int row = threadIdx.x; row < S.n; row += blockDim.x) f(row, row_f32(S, x, row));
+  } else {
+    const RowGroup g = row_group(G);
+    for (int row = g.g0; row < S.n; row += g.gs) {
+      const float y = row_grouped(S.rp, S.ci, S.va32, x, row, g);
+      if (g.q == 0) f(row, y);
+    }
+  }
+}
+
+// Pipelined CG (Alg. 2) on one system by one block, FP64, G lanes per row.  Returns the status.
+__device__ int cta_cg64(BatchSys& S, double tol, int maxit, int G) {
   const int n = S.n, t0 = threadIdx.x, bs = blockDim.x;
   __shared__ CtaScalars sc;
   double v[2] = {0.0, 0.0};
-  for (int row = t0; row < n; row += bs) {
+  rows_f64(S, S.x, G, [&](int row, double y) {
     const double bi = S.b[row];
-    const double ri = bi - row_f64(S, S.x, row);
+    const double ri = bi - y;
     S.r[row] = ri;
     S.p[row] = ri;
     v[0] = fma(ri, ri, v[0]);
     v[1] = fma(bi, bi, v[1]);
-  }
+  });
   cta_sum<2>(v);
   double rr = v[0];
   const double bb = v[1], thr2 = tol * tol * bb;
@@ -146,12 +218,11 @@ __device__ int cta_cg64(BatchSys& S, double tol, int maxit) {
   for (int it = 0;; ++it) {
     // A p_it with <Ap,Ap>, <p,Ap> -> alpha, beta (Eq. (3))
     v[0] = v[1] = 0.0;
-    for (int row = t0; row < n; row += bs) {
-      const double s = row_f64(S, S.p, row);
+    rows_f64(S, S.p, G, [&](int row, double s) {
       S.ap[row] = s;
       v[0] = fma(s, s, v[0]);
       v[1] = fma(S.p[row], s, v[1]);
-    }
+    });
     cta_sum<2>(v);
     if (t0 == 0) {
       sc.status = kRunning;
@@ -192,7 +263,7 @@ __device__ int cta_cg64(BatchSys& S, double tol, int maxit) {
 
 // Mixed precision: FP64 refinement around an FP32 pipelined CG whose inner products (and so
 // alpha, beta) are accumulated in FP64.  Inner stop: ||r_in|| <= tol_in ||r_outer||.
-__device__ int cta_cg_mixed(BatchSys& S, double tol, int maxit, double tol_in, int max_outer) {
+__device__ int cta_cg_mixed(BatchSys& S, double tol, int maxit, double tol_in, int max_outer, int G) {
   const int n = S.n, t0 = threadIdx.x, bs = blockDim.x;
   __shared__ CtaScalars sc;
   S.iters = 0;
@@ -202,13 +273,13 @@ __device__ int cta_cg_mixed(BatchSys& S, double tol, int maxit, double tol_in, i
   for (int outer = 0;; ++outer) {
     // FP64 true residual r = b - A x
     double v[2] = {0.0, 0.0};
-    for (int row = t0; row < n; row += bs) {
+    rows_f64(S, S.x, G, [&](int row, double y) {
       const double bi = S.b[row];
-      const double ri = bi - row_f64(S, S.x, row);
+      const double ri = bi - y;
       S.r[row] = ri;
       v[0] = fma(ri, ri, v[0]);
       v[1] = fma(bi, bi, v[1]);
-    }
+    });
     cta_sum<2>(v);
     if (bb < 0) bb = v[1];
     const double rr_out = v[0];
@@ -244,12 +315,11 @@ __device__ int cta_cg_mixed(BatchSys& S, double tol, int maxit, double tol_in, i
     const int budget = maxit - S.iters;
     for (int it = 0; it < budget; ++it) {
       FF aa{0.0f, 0.0f}, pa{0.0f, 0.0f};
-      for (int row = t0; row < n; row += bs) {
-        const float s = row_f32(S, S.p32, row);
+      rows_f32(S, S.p32, G, [&](int row, float s) {
         S.ap32[row] = s;
         ff_add_prod(aa, s, s);
         ff_add_prod(pa, S.p32[row], s);
-      }
+      });
       double u[2] = {ff_value(aa), ff_value(pa)};
       cta_sum<2>(u);
       if (t0 == 0) {
@@ -288,7 +358,7 @@ __device__ int cta_cg_mixed(BatchSys& S, double tol, int maxit, double tol_in, i
 }
 
 __global__ void __launch_bounds__(1024, 1) k_batched(BatchSys* sys, int nsys, int* queue, double tol, int maxit, int mixed,
-                          double tol_in, int max_outer) {
+                          double tol_in, int max_outer, int lanes) {
   __shared__ int cur;
   for (;;) {
     __syncthreads();
@@ -297,7 +367,7 @@ __global__ void __launch_bounds__(1024, 1) k_batched(BatchSys* sys, int nsys, in
     const int k = cur;
     if (k >= nsys) return;
     BatchSys S = sys[k];
-    const int st = mixed ? cta_cg_mixed(S, tol, maxit, tol_in, max_outer) : cta_cg64(S, tol, maxit);
+    const int st = mixed ? cta_cg_mixed(S, tol, maxit, tol_in, max_outer, lanes) : cta_cg64(S, tol, maxit, lanes);
     if (threadIdx.x == 0) {
       sys[k].iters = S.iters;
       sys[k].status = st;
@@ -319,13 +389,13 @@ struct TuneKey {
   }
 };
 struct TuneVal {
-  int block, per_sm;
+  int block, per_sm, lanes;
 };
 static std::mutex g_tune_mutex;
 static std::map<TuneKey, TuneVal> g_tune;
-static TuneVal g_last{512, 2};
+static TuneVal g_last{512, 2, 1};
 
-static pk_status run_batch(BatchSys* dsys, int* dqueue, int nsys, int block, int per_sm,
+static pk_status run_batch(BatchSys* dsys, int* dqueue, int nsys, int block, int per_sm, int lanes,
                            double tol, int maxit, int mixed, cudaStream_t s) {
   int sms = 1, dev = 0;
   PK_CUDA(cudaGetDevice(&dev));
@@ -334,7 +404,7 @@ static pk_status run_batch(BatchSys* dsys, int* dqueue, int nsys, int block, int
   PK_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_batched, block, 0));
   const int grid = std::max(1, std::min(nsys, sms * std::max(1, std::min(per_sm, occ))));
   PK_CUDA(cudaMemsetAsync(dqueue, 0, sizeof(int), s));
-  k_batched<<<grid, block, 0, s>>>(dsys, nsys, dqueue, tol, maxit, mixed, 1e-4, 20);
+  k_batched<<<grid, block, 0, s>>>(dsys, nsys, dqueue, tol, maxit, mixed, 1e-4, 20, lanes);
   PK_CUDA(cudaGetLastError());
   return PK_OK;
 }
@@ -401,17 +471,27 @@ pk_status batched_solve(int32_t nsys, pk_csr* const* A, const double* const* b, 
   int* dqueue = reinterpret_cast<int*>(reinterpret_cast<char*>(dsys) + sizeof(BatchSys) * nsys);
   PK_CUDA(cudaMemcpyAsync(dsys, hs.data(), sizeof(BatchSys) * nsys, cudaMemcpyHostToDevice, s));
 
-  TuneVal cfg{512, 2};
+  // lanes per row: given, else from the batch's mean row length (one thread up to 12
+  // nonzeros per row, then 2, 4, 8 lanes), else tuned
+  if (o->lanes != 0 && o->lanes != 1 && o->lanes != 2 && o->lanes != 4 && o->lanes != 8) {
+    set_error("lanes per row must be 0 (automatic), 1, 2, 4 or 8");
+    return PK_ERR_ARG;
+  }
+  const double mean_len = rows > 0 ? (double)nnz / (double)rows : 0.0;
+  const int lanes_auto = mean_len <= 12 ? 1 : mean_len <= 24 ? 2 : mean_len <= 48 ? 4 : 8;
+  TuneVal cfg{512, 2, o->lanes ? o->lanes : lanes_auto};
   const TuneKey key{nsys, rows, nnz, mixed};
   bool have = false;
-  {
+  if (o->lanes == 0) {
     std::lock_guard<std::mutex> lock(g_tune_mutex);
     auto it = g_tune.find(key);
     if (it != g_tune.end()) { cfg = it->second; have = true; }
   }
   if (!have && (o->flags & PK_FLAG_AUTOTUNE)) {
-    // autotuner: time every (block size, blocks per SM) candidate on the whole batch for a
-    // few fixed iterations, from x as given (restored afterwards)
+    // autotuner: time every (block size, blocks per SM, lanes per row) candidate on the whole
+    // batch for a few fixed iterations, from x as given (restored afterwards); lanes per row
+    // beyond one only for rows of more than 8 nonzeros on average, and only the given
+    // number when the caller fixes it
     std::vector<double*> xsave(nsys, nullptr);
     for (int k = 0; k < nsys; ++k) {
       if (!h[k].n) continue;
@@ -424,34 +504,42 @@ pk_status batched_solve(int32_t nsys, pk_csr* const* A, const double* const* b, 
     float best = 1e30f;
     const int blocks[] = {128, 256, 512, 1024};
     const int per[] = {1, 2, 4, 8};
-    for (int bsz : blocks) {
-      for (int ps : per) {
-        if (bsz * ps > 2048) continue;
-        for (int rep = 0; rep < 2; ++rep) {
-          PK_CUDA(cudaEventRecord(a0, s));
-          if ((e = run_batch(dsys, dqueue, nsys, bsz, ps, 0.0, 6, mixed, s))) return e;
-          PK_CUDA(cudaEventRecord(a1, s));
-          PK_CUDA(cudaEventSynchronize(a1));
-          float ms = 0;
-          PK_CUDA(cudaEventElapsedTime(&ms, a0, a1));
-          if (rep == 1 && ms < best) { best = ms; cfg = TuneVal{bsz, ps}; }
+    std::vector<int> lane_set;
+    if (o->lanes) lane_set.push_back(o->lanes);
+    else if (mean_len > 8) lane_set = {1, 2, 4, 8};
+    else lane_set.push_back(1);
+    for (int ln : lane_set) {
+      for (int bsz : blocks) {
+        for (int ps : per) {
+          if (bsz * ps > 2048) continue;
+          for (int rep = 0; rep < 2; ++rep) {
+            PK_CUDA(cudaEventRecord(a0, s));
+            if ((e = run_batch(dsys, dqueue, nsys, bsz, ps, ln, 0.0, 6, mixed, s))) return e;
+            PK_CUDA(cudaEventRecord(a1, s));
+            PK_CUDA(cudaEventSynchronize(a1));
+            float ms = 0;
+            PK_CUDA(cudaEventElapsedTime(&ms, a0, a1));
+            if (rep == 1 && ms < best) { best = ms; cfg = TuneVal{bsz, ps, ln}; }
+          }
+          for (int k = 0; k < nsys; ++k)
+            if (xsave[k]) PK_CUDA(cudaMemcpyAsync(h[k].x, xsave[k], sizeof(double) * h[k].n, cudaMemcpyDeviceToDevice, s));
         }
-        for (int k = 0; k < nsys; ++k)
-          if (xsave[k]) PK_CUDA(cudaMemcpyAsync(h[k].x, xsave[k], sizeof(double) * h[k].n, cudaMemcpyDeviceToDevice, s));
       }
     }
     for (int k = 0; k < nsys; ++k) if (xsave[k]) PK_CUDA(cudaFreeAsync(xsave[k], s));
     cudaEventDestroy(a0);
     cudaEventDestroy(a1);
-    std::lock_guard<std::mutex> lock(g_tune_mutex);
-    g_tune[key] = cfg;
+    if (o->lanes == 0) {
+      std::lock_guard<std::mutex> lock(g_tune_mutex);
+      g_tune[key] = cfg;
+    }
   }
   g_last = cfg;
   cudaEvent_t e0, e1;
   PK_CUDA(cudaEventCreate(&e0));
   PK_CUDA(cudaEventCreate(&e1));
   PK_CUDA(cudaEventRecord(e0, s));
-  if ((e = run_batch(dsys, dqueue, nsys, cfg.block, cfg.per_sm, o->tol, o->maxit, mixed, s))) return e;
+  if ((e = run_batch(dsys, dqueue, nsys, cfg.block, cfg.per_sm, cfg.lanes, o->tol, o->maxit, mixed, s))) return e;
   PK_CUDA(cudaEventRecord(e1, s));
   PK_CUDA(cudaMemcpyAsync(hs.data(), dsys, sizeof(BatchSys) * nsys, cudaMemcpyDeviceToHost, s));
   PK_CUDA(cudaFreeAsync(dsys, s));
@@ -492,5 +580,11 @@ extern "C" pk_status pk_batched_last_config(int32_t* block, int32_t* blocks_per_
   if (!block || !blocks_per_sm) return PK_ERR_ARG;
   *block = pk::g_last.block;
   *blocks_per_sm = pk::g_last.per_sm;
+  return PK_OK;
+}
+
+extern "C" pk_status pk_batched_last_lanes(int32_t* lanes) {
+  if (!lanes) return PK_ERR_ARG;
+  *lanes = pk::g_last.lanes;
   return PK_OK;
 }

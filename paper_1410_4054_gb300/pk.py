@@ -38,7 +38,7 @@ class Opts(C.Structure):
     _fields_ = [("tol", C.c_double), ("maxit", C.c_int32), ("restart", C.c_int32),
                 ("variant", C.c_int32), ("precision", C.c_int32), ("loop", C.c_int32),
                 ("check_every", C.c_int32), ("flags", C.c_uint32), ("trace_cap", C.c_int32),
-                ("trace", C.c_void_p), ("precond", C.c_int32)]
+                ("trace", C.c_void_p), ("precond", C.c_int32), ("lanes", C.c_int32)]
 
 
 class Info(C.Structure):
@@ -76,6 +76,7 @@ EXPORTS = {
     "pk_batched_solve": (C.c_int, [C.c_int32, C.c_void_p, C.c_void_p, C.c_void_p, C.POINTER(Opts),
                                    C.c_void_p, C.c_void_p]),
     "pk_batched_last_config": (C.c_int, [C.POINTER(C.c_int32), C.POINTER(C.c_int32)]),
+    "pk_batched_last_lanes": (C.c_int, [C.POINTER(C.c_int32)]),
     "pk_residual_norm2": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p]),
     "pk_conv3d_fwd": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_int32, C.c_int32,
                                 C.c_int32, C.c_int32, C.c_int32, C.c_void_p, C.c_void_p]),
@@ -206,9 +207,10 @@ PRECONDS = {"none": 0, "jacobi": 1}
 
 
 def make_opts(tol=1e-8, maxit=1000, restart=30, variant="pipelined", precision="fp64",
-              loop="auto", check_every=0, flags=0, trace=None, precond="none") -> Opts:
+              loop="auto", check_every=0, flags=0, trace=None, precond="none", lanes=0) -> Opts:
     o = Opts()
     o.precond = PRECONDS[precond] if isinstance(precond, str) else int(precond)
+    o.lanes = int(lanes)
     o.tol = tol
     o.maxit = maxit
     o.restart = restart
@@ -279,6 +281,13 @@ def batched_solve(As, bs, xs, stream=None, **kw) -> list:
     st = lib().pk_batched_solve(nsys, ha, hb, hx, C.byref(o), infos, _stream_ptr(stream))
     _check(st, "pk_batched_solve", _SOLVER_OK)
     return [info_dict(infos[k]) for k in range(nsys)]
+
+
+def batched_last_lanes() -> int:
+    """Lanes per row of the last pk_batched_solve call."""
+    v = C.c_int32()
+    _check(lib().pk_batched_last_lanes(C.byref(v)), "pk_batched_last_lanes")
+    return v.value
 
 
 def batched_last_config() -> tuple:

@@ -109,3 +109,63 @@ def test_batched_rejects_a_preconditioner():
     xs = [torch.zeros(a.n, dtype=torch.float64, device=DEV) for a in mats]
     with pytest.raises(RuntimeError, match="no preconditioner"):
         pk.batched_solve(As, bs, xs, tol=1e-10, maxit=2000, precond="jacobi")
+
+
+def make_fe_batch(nsys=24, seed=0):
+    """Uneven batch of P1 elasticity systems (3 x 3 blocks, up to 45 nonzeros per row)."""
+    ks = 2 + (W.splitmix64(seed, nsys) % np.uint64(4)).astype(int)   # k = 2..5: 54 .. 540 rows
+    mats = [W.fe_elasticity_3d(int(k), seed=i) for i, k in enumerate(ks)]
+    rhs = [W.manufactured(a, seed=i)[1] for i, a in enumerate(mats)]
+    return mats, rhs
+
+
+def oracle_x_spread(a, b, iters, x_ref, nsamp=3):
+    """The oracle's own one-ulp spread of x after `iters` pipelined-CG iterations: up to 1e-7 on
+    the 54-unknown members, which reach the rounding floor before 20 iterations."""
+    sp = 0.0
+    for smp in range(nsamp):
+        bp = b * (1 + 2.0 ** -52 * W.uniform_pm1(100 + smp, a.n))
+        sp = max(sp, rel(O.cg(a, bp, tol=0.0, maxit=iters, variant="pipelined")["x"], x_ref))
+    return sp
+
+
+@pytest.mark.parametrize("lanes", [1, 2, 4, 8])
+def test_batched_lanes_per_row_match_the_oracle(lanes):
+    """Rows computed by 1, 2, 4 or 8 lanes: x after a fixed count matches each system's oracle
+    solve within max(1e-9, 10 x the oracle's own one-ulp spread); to tolerance, every system
+    converges with the oracle's iteration count (+-2)."""
+    mats, rhs = make_fe_batch()
+    As = [pk.CSRMatrix.from_workload(a) for a in mats]
+    bs = [dev(b) for b in rhs]
+    xs = [torch.zeros(a.n, dtype=torch.float64, device=DEV) for a in mats]
+    pk.batched_solve(As, bs, xs, tol=0.0, maxit=20, lanes=lanes)
+    torch.cuda.synchronize()
+    assert pk.batched_last_lanes() == lanes
+    for a, b, x in zip(mats, rhs, xs):
+        ref = O.cg(a, b, tol=0.0, maxit=20, variant="pipelined")
+        bar = max(1e-9, 10 * oracle_x_spread(a, b, 20, ref["x"]))
+        assert rel(x.cpu().numpy(), ref["x"]) <= bar, a.name
+    xs = [torch.zeros(a.n, dtype=torch.float64, device=DEV) for a in mats]
+    infos = pk.batched_solve(As, bs, xs, tol=1e-10, maxit=5000, lanes=lanes)
+    torch.cuda.synchronize()
+    for a, b, x, inf in zip(mats, rhs, xs, infos):
+        ref = O.cg(a, b, tol=1e-10, maxit=5000, variant="pipelined")
+        assert inf["status"] == pk.PK_OK and abs(inf["iters"] - ref["iters"]) <= 2
+        assert np.linalg.norm(b - a.matvec(x.cpu().numpy())) <= 1.5e-10 * np.linalg.norm(b)
+
+
+def test_batched_autotuner_covers_lanes_per_row():
+    mats, rhs = make_fe_batch(nsys=32, seed=4)
+    As = [pk.CSRMatrix.from_workload(a) for a in mats]
+    bs = [dev(b) for b in rhs]
+    xs = [torch.zeros(a.n, dtype=torch.float64, device=DEV) for a in mats]
+    for prec in ("fp64", "mixed"):
+        infos = pk.batched_solve(As, bs, [x.zero_() for x in xs], tol=1e-10, maxit=5000, precision=prec,
+                                 flags=pk.FLAG_AUTOTUNE)
+        torch.cuda.synchronize()
+        assert all(i["status"] == pk.PK_OK for i in infos)
+        assert pk.batched_last_lanes() in (1, 2, 4, 8)
+        for a, b, x in zip(mats, rhs, xs):
+            assert np.linalg.norm(b - a.matvec(x.cpu().numpy())) <= 1.5e-10 * np.linalg.norm(b)
+    with pytest.raises(RuntimeError, match="lanes per row"):
+        pk.batched_solve(As, bs, xs, tol=1e-10, maxit=10, lanes=3)
