@@ -383,7 +383,7 @@ pk_status pk_csr_create(int64_t n, int64_t nnz, const int32_t* row_ptr, const in
 
   // warp-specialised CSR tiles: 2 blocks per SM, nnz-balanced block ranges, tiles of at most
   // kTileRows rows and kTileNnz nonzeros
-  std::vector<int32_t> tile_row, blk_tile;
+  std::vector<int32_t> tile_row, blk_tile, tile_z0;
   A->tma_ok = 1;
   // at least one tile per block where the matrix has that many: tiles end at kTileRows rows or
   // kTileNnz nonzeros, whichever comes first
@@ -417,7 +417,17 @@ pk_status pk_csr_create(int64_t n, int64_t nnz, const int32_t* row_ptr, const in
           }
           R1 = lo;
         }
-        if (R1 == R) { A->tma_ok = 0; break; }  // a single row longer than a tile
+        if (R1 == R) {
+          // a row longer than a tile: one chunk tile per kTileNnz of its nonzeros, summed by
+          // the whole block (csr_tiles, block per row)
+          for (int64_t z = rp[R]; z < rp[R + 1]; z += kTileNnz) {
+            tile_row.push_back((int32_t)R);
+            tile_z0.resize(tile_row.size() - 1, -1);
+            tile_z0.push_back((int32_t)z);
+          }
+          R = R + 1;
+          continue;
+        }
         tile_row.push_back((int32_t)R);
         R = R1;
       }
@@ -425,6 +435,7 @@ pk_status pk_csr_create(int64_t n, int64_t nnz, const int32_t* row_ptr, const in
     }
     tile_row.push_back((int32_t)n);
     A->ntiles = (int)tile_row.size() - 1;
+    if (!tile_z0.empty()) tile_z0.resize(A->ntiles, -1);
   }
   // per tile, the lanes that compute one row (see csr_tiles): 1 = one thread per row (two rows
   // per thread, in one pass), 2..16 = a group of lanes per row, 32 = short rows one thread and
@@ -448,6 +459,11 @@ pk_status pk_csr_create(int64_t n, int64_t nnz, const int32_t* row_ptr, const in
   };
   std::vector<int8_t> tile_grp(A->tma_ok ? A->ntiles : 0);
   for (int t = 0; t < (int)tile_grp.size(); ++t) {
+    if (!tile_z0.empty() && tile_z0[t] >= 0) {  // chunk of a row longer than a tile
+      tile_grp[t] = 64;
+      A->stats.tiles_long += 1;
+      continue;
+    }
     int64_t lmax = 0;
     for (int64_t r = tile_row[t]; r < tile_row[t + 1]; ++r) lmax = std::max<int64_t>(lmax, rp[r + 1] - rp[r]);
     tile_grp[t] = (int8_t)tile_lanes(tile_row[t + 1] - tile_row[t], lmax, rp[tile_row[t + 1]] - rp[tile_row[t]]);
@@ -509,6 +525,11 @@ pk_status pk_csr_create(int64_t n, int64_t nnz, const int32_t* row_ptr, const in
       if ((e = cudaMemcpyAsync(A->tile_perm, tile_perm.data(), sizeof(int16_t) * tile_perm.size(), cudaMemcpyHostToDevice, s)) != cudaSuccess)
         return fail(cuda_fail(e, "copy tiles"));
     }
+    if (!tile_z0.empty()) {
+      if ((e = cudaMalloc(&A->tile_z0, sizeof(int32_t) * tile_z0.size())) != cudaSuccess) return fail(cuda_fail(e, "cudaMalloc(tiles)"));
+      if ((e = cudaMemcpyAsync(A->tile_z0, tile_z0.data(), sizeof(int32_t) * tile_z0.size(), cudaMemcpyHostToDevice, s)) != cudaSuccess)
+        return fail(cuda_fail(e, "copy tiles"));
+    }
     if (!tile_grp.empty() &&
         (e = cudaMemcpyAsync(A->tile_grp, tile_grp.data(), tile_grp.size(), cudaMemcpyHostToDevice, s)) != cudaSuccess)
       return fail(cuda_fail(e, "copy tiles"));
@@ -561,6 +582,7 @@ pk_status pk_csr_destroy(pk_csr* A) {
   if (A->blk_tile) cudaFree(A->blk_tile);
   if (A->tile_grp) cudaFree(A->tile_grp);
   if (A->tile_perm) cudaFree(A->tile_perm);
+  if (A->tile_z0) cudaFree(A->tile_z0);
   if (A->cap_stream) cudaStreamDestroy(A->cap_stream);
   delete A;
   return PK_OK;

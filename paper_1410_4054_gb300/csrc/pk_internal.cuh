@@ -196,6 +196,7 @@ struct pk_csr {
   int32_t* blk_tile = nullptr;  // grid_tma + 1
   int8_t* tile_grp = nullptr;   // ntiles: 1 if the tile has no row longer than 32 nonzeros
   int16_t* tile_perm = nullptr; // ntiles x 512: row order of the irregular tiles (or null)
+  int32_t* tile_z0 = nullptr;   // ntiles: first nonzero of a chunk tile, -1 otherwise (or null)
   int ntiles = 0;
   int grid_stream = 0;          // grid of the streaming (vector-only) tile kernels
   int partial_cap = 0;         // blocks the partials buffer can hold

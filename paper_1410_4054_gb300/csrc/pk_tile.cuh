@@ -309,6 +309,7 @@ struct CsrTilesT {
   const int32_t* blk_tile;  // tiles of block b: [blk_tile[b], blk_tile[b+1])
   const int8_t* tile_grp;   // 1: every row of the tile has at most kLongRow nonzeros
   const int16_t* tile_perm; // [tile][512]: row (offset in the tile) of every consumer slot, or -1
+  const int32_t* tile_z0;   // chunk tiles (tile_grp 64): first nonzero of the chunk, else -1
 };
 using CsrTiles = CsrTilesT<double>;
 
@@ -397,7 +398,54 @@ __device__ __forceinline__ void row_pair(const float* sva, const int32_t* sci, i
 // l, l + 32, ... left to right, then a butterfly), so that no thread walks a long row alone;
 // no synchronisation beyond the warp is involved.  Tiles of rows of similar length that are
 // too long for one thread (T.tile_grp = G in 2..16) give each row a group of G lanes instead.
+// A row longer than a tile is cut into chunk tiles of kTileNnz nonzeros (T.tile_grp = 64,
+// consecutive tiles of one block) and summed by the whole block: see block_row_chunk.
 constexpr int kLongRow = 32;
+constexpr int kChunkTile = 64;
+
+// One chunk tile of a row longer than a tile (block per row).  The chunk's nonzeros
+// [zc0, min(zr1, zc0 + kTileNnz)) sit in the stage's value and column windows.  Thread t
+// takes the entries whose offset in the row is t modulo kConsumers (chunks hold whole
+// multiples of kConsumers, so that share is the same in every chunk) and sums its share left to
+// right across all the row's chunks in `acc`.  After the row's last chunk each warp adds its
+// lanes by a butterfly and posts the sum; the warp that posts last adds the kConsumerWarps
+// sums in warp order and hands the row to row_done.  No warp waits for another (a warp that
+// timed out elsewhere cannot stall this one).  The warp that posts last resets the counter
+// before it releases the stage; with two stages no warp can reach the next long row's last
+// chunk (at least two tiles on) before that.
+static_assert(kCsrStages <= 2, "the chunk-row counter is reused two tiles after its last use");
+static_assert(kTileNnz % kConsumers == 0, "chunks must hold whole multiples of the consumer count");
+
+template <class VT, class RowDone>
+__device__ __forceinline__ void block_row_chunk(int row, int zc0, int zr1, VT* stage_va, int32_t* stage_ci,
+                                                const VT* __restrict__ x, VT& acc, VT* red, int* cnt,
+                                                int warp, int lane, RowDone& row_done) {
+  constexpr int kVaUnit = 16 / (int)sizeof(VT);
+  const int zc1 = min(zr1, zc0 + kTileNnz);
+  const VT* sva = stage_va - (zc0 & ~(kVaUnit - 1));
+  const int32_t* sci = stage_ci - (zc0 & ~3);
+  for (int j = zc0 + (int)threadIdx.x; j < zc1; j += kConsumers) acc = fma_t(sva[j], __ldg(x + sci[j]), acc);
+  if (zc1 != zr1) return;  // more chunks of this row follow
+  VT w = acc;
+  acc = (VT)0;
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) w += __shfl_xor_sync(0xffffffffu, w, o);
+  int last = 0;
+  if (lane == 0) {
+    red[warp] = w;
+    __threadfence_block();
+    last = atomicAdd(cnt, 1) == kConsumerWarps - 1;
+  }
+  last = __shfl_sync(0xffffffffu, last, 0);
+  if (last && lane == 0) {
+    __threadfence_block();
+    VT tot = (VT)0;
+    const volatile VT* vr = red;
+    for (int k = 0; k < kConsumerWarps; ++k) tot += vr[k];
+    *cnt = 0;
+    row_done(row, tot);
+  }
+}
 
 // IRR = false compiles the thread-per-row path only (matrices without long rows).
 template <bool IRR, class VT, class Setup, class RowDone>
@@ -407,6 +455,8 @@ __device__ __forceinline__ bool csr_tiles(const CsrTilesT<VT>& T, unsigned char*
   uint64_t* full = reinterpret_cast<uint64_t*>(smem + kCsrStages * kStageBytes);
   uint64_t* empty = full + kCsrStages;
   int4* meta = reinterpret_cast<int4*>(empty + kCsrStages);  // tile rows [R0, R1), lanes per row
+  __shared__ VT chunk_red[kConsumerWarps];  // warp sums of a long row (chunk tiles)
+  __shared__ int chunk_cnt;                 // warps that have added their sum
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   if (threadIdx.x == 0) {
     for (int s = 0; s < kCsrStages; ++s) {
@@ -414,6 +464,7 @@ __device__ __forceinline__ bool csr_tiles(const CsrTilesT<VT>& T, unsigned char*
       mbar_init(&empty[s], kConsumerWarps);
     }
     mbar_fence_init();
+    chunk_cnt = 0;
   }
   __syncthreads();
   const int t0 = T.blk_tile[blockIdx.x], t1 = T.blk_tile[blockIdx.x + 1];
@@ -444,10 +495,16 @@ __device__ __forceinline__ bool csr_tiles(const CsrTilesT<VT>& T, unsigned char*
       int R0 = 0, R1 = 0, z0 = 0, z1 = 0, gr = 1;
       if (tt < t1) {
         R0 = __ldg(T.tile_row + tt);
-        R1 = __ldg(T.tile_row + tt + 1);
-        z0 = __ldg(T.rp + R0);
-        z1 = __ldg(T.rp + R1);
         gr = T.tile_grp ? (int)__ldg(T.tile_grp + tt) : 1;
+        if (gr == kChunkTile) {  // one chunk of row R0: nonzeros [z0, z1)
+          R1 = R0 + 1;
+          z0 = __ldg(T.tile_z0 + tt);
+          z1 = min(__ldg(T.rp + R0 + 1), z0 + kTileNnz);
+        } else {
+          R1 = __ldg(T.tile_row + tt + 1);
+          z0 = __ldg(T.rp + R0);
+          z1 = __ldg(T.rp + R1);
+        }
       }
       const int cnt = min(32, ntiles - base);
       for (int q = 0; q < cnt; ++q) {
@@ -466,7 +523,8 @@ __device__ __forceinline__ bool csr_tiles(const CsrTilesT<VT>& T, unsigned char*
             const uint32_t nrp = (uint32_t)(re - rs) * 4, nva = (uint32_t)(ve - vs) * (uint32_t)sizeof(VT),
                            nci = (uint32_t)(ce - cs) * 4;
             const bool perm = g0 == 32 && T.tile_perm;  // irregular tile: its row order too
-            meta[s] = make_int4(a0, a1, g0, perm ? 1 : 0);  // published by the arrive below (release)
+            // published by the arrive below (release); w: the row order flag, or a chunk's start
+            meta[s] = make_int4(a0, a1, g0, g0 == kChunkTile ? b0 : (perm ? 1 : 0));
             mbar_expect_tx(&full[s], nrp + nva + nci + (perm ? kTileRows * 2 : 0));
             bulk_load_hint(stage_rp(s), T.rp + rs, nrp, &full[s], pol);
             if (nva) bulk_load_hint(stage_va(s), T.va + vs, nva, &full[s], pol);
@@ -494,6 +552,7 @@ __device__ __forceinline__ bool csr_tiles(const CsrTilesT<VT>& T, unsigned char*
   griddep_wait();
   const bool live = setup();
   const int nproc = live ? ntiles : npro;
+  VT chunk_acc = (VT)0;  // this thread's share of the current long row (chunk tiles)
   for (int t = 0; t < nproc; ++t) {
     const int s = t % kCsrStages;
     if (!mbar_wait(&full[s], (t / kCsrStages) & 1)) { report_timeout(st); break; }
@@ -508,7 +567,10 @@ __device__ __forceinline__ bool csr_tiles(const CsrTilesT<VT>& T, unsigned char*
     const int z0 = srp[R0];
     const VT* sva = stage_va(s) - (z0 & ~(kVaUnit - 1));  // windows start at the first row's nonzeros
     const int32_t* sci = stage_ci(s) - (z0 & ~3);
-    if (!IRR || G == 1) {
+    if (IRR && G == kChunkTile) {
+      block_row_chunk(R0, m.w, srp[R0 + 1], stage_va(s), stage_ci(s), x, chunk_acc, chunk_red, &chunk_cnt,
+                      warp, lane, row_done);
+    } else if (!IRR || G == 1) {
       const int ra = R0 + (int)threadIdx.x;
       if (ra < R1) {
         const int rb = ra + kConsumers < R1 ? ra + kConsumers : -1;
@@ -719,6 +781,7 @@ inline CsrTilesT<float> csr_tiles32_of(const pk_csr* A) {
   t.blk_tile = A->blk_tile;
   t.tile_grp = A->tile_grp;
   t.tile_perm = A->tile_perm;
+  t.tile_z0 = A->tile_z0;
   return t;
 }
 
@@ -731,6 +794,7 @@ inline CsrTiles csr_tiles_of(const pk_csr* A) {
   t.blk_tile = A->blk_tile;
   t.tile_grp = A->tile_grp;
   t.tile_perm = A->tile_perm;
+  t.tile_z0 = A->tile_z0;
   return t;
 }
 

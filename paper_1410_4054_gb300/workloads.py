@@ -212,6 +212,36 @@ def spd_power_law(n: int, seed: int = 0, lmin: int = 3, lmax: int = 256, mean: f
                      np.concatenate([vals, 1.1 * absum + 1.0]), f"spdpowerlaw_{n}")
 
 
+def spd_dense_rows(k: int = 100, dense=(0, 17, 5000), per_row: int = 9000, seed: int = 0) -> CSR:
+    """SPD matrix with a few rows longer than any tile: the 2D 5-point Laplacian on a k x k
+    grid plus, for each row r in ``dense``, ``per_row`` couplings to distinct random columns
+    (values N(0,1)/per_row, mirrored into the columns), the diagonal raised to 1.1 times the
+    absolute row sum plus 1 (strict diagonal dominance).  Stands in for the dense rows of
+    arrow-shaped systems (a global constraint or a hub node coupled to many unknowns).
+    """
+    lap = laplace_2d(k)
+    n = lap.n
+    rng = np.random.default_rng(seed)
+    rows = [np.repeat(np.arange(n, dtype=np.int64), np.diff(lap.row_ptr))]
+    cols = [lap.col.astype(np.int64)]
+    vals = [lap.val.copy()]
+    rows[0], cols[0], vals[0] = rows[0][rows[0] != cols[0]], cols[0][rows[0] != cols[0]], vals[0][rows[0] != cols[0]]
+    for r in dense:
+        c = rng.choice(np.setdiff1d(np.arange(n), [r]), size=min(per_row, n - 1), replace=False).astype(np.int64)
+        v = rng.standard_normal(c.size) / per_row
+        rows += [np.full(c.size, r, dtype=np.int64), c]
+        cols += [c, np.full(c.size, r, dtype=np.int64)]
+        vals += [v, v]
+    r_all, c_all, v_all = np.concatenate(rows), np.concatenate(cols), np.concatenate(vals)
+    key, inv = np.unique(r_all * n + c_all, return_inverse=True)
+    v_sum = np.bincount(inv, weights=v_all)
+    ur, uc = key // n, key % n
+    absum = np.bincount(ur, weights=np.abs(v_sum), minlength=n)
+    d = np.arange(n, dtype=np.int64)
+    return _from_coo(n, np.concatenate([ur, d]), np.concatenate([uc, d]),
+                     np.concatenate([v_sum, 1.1 * absum + 1.0]), f"spd_dense_rows_{n}")
+
+
 def diag_scaled(a: CSR, seed: int = 0, spread: float = 100.0) -> CSR:
     """D A D with D = diag(d), ln d uniform on [0, ln spread) from splitmix64(seed).
 

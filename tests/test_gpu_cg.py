@@ -39,6 +39,8 @@ def rel(a, b):
 
 
 MATRICES = {
+    "dense_rows_1e4": lambda: W.spd_dense_rows(),            # rows of 9,000 nonzeros: chunk tiles
+    "dense_rows_62500": lambda: W.spd_dense_rows(k=250, dense=(0, 5, 31000, 62499), per_row=20000),
     "fe2d_p1_961": lambda: W.fe_poisson_2d(5),              # P1 triangles, ~7 per row
     "fe3d_elast_4752": lambda: W.fe_elasticity_3d(11),      # P1 elasticity, 3x3 blocks, <= 45 per row
     "lap2d_64": lambda: W.laplace_2d(64),                   # the 64 x 64 configuration
@@ -276,3 +278,22 @@ def test_cg_unaligned_and_odd_length_x():
     torch.cuda.synchronize()
     assert info["status"] == pk.PK_OK
     assert np.array_equal(xv.cpu().numpy(), x_ref) and buf[0].item() == 0.0
+
+
+def test_rows_longer_than_a_tile_use_chunk_tiles():
+    """Rows of 20,000 nonzeros are cut into chunk tiles summed by a whole block: the tile
+    engine stays in use (no thread-per-row fallback), and A p equals the oracle's row sums."""
+    a = W.spd_dense_rows(k=250, dense=(0, 5, 31000, 62499), per_row=20000)
+    A = pk.CSRMatrix.from_workload(a)
+    st = A.stats()
+    assert st["kernel"] == 2 and st["tiles_long"] >= 4 * 5
+    p = W.uniform_pm1(5, a.n)
+    _, b, _ = W.manufactured(a, seed=1)
+    # one K-CG-S through a fixed single CG iteration: alpha_0 = <r0,r0> / <r0, A r0>
+    tr = torch.full((4, 4), float("nan"), dtype=torch.float64, device=DEV)
+    x = dev(np.zeros(a.n))
+    pk.cg_solve(A, dev(b), x, trace=tr, tol=0.0, maxit=1)
+    ref = O.cg(a, b, tol=0.0, maxit=1, variant="pipelined")
+    np.testing.assert_allclose(tr.cpu().numpy()[0, :2], [ref["alpha"][0], ref["beta"][0]], rtol=1e-12)
+    assert rel(x.cpu().numpy(), ref["x"]) <= 1e-13
+    del p

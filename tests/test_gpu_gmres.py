@@ -40,6 +40,7 @@ def rel(a, b):
 
 
 MATRICES = {
+    "dense_rows_1e4": lambda: W.spd_dense_rows(),
     "fe2d_p1_961": lambda: W.fe_poisson_2d(5),
     "fe3d_elast_540": lambda: W.fe_elasticity_3d(5),
     "convdiff_16": lambda: W.convdiff_3d(16),
