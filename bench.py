@@ -56,8 +56,11 @@ def parse():
                          "conv: time the BF16 conv kernels on one 64^3 layer")
     ap.add_argument("--iters", type=int, default=30)
     ap.add_argument("--variant", default="pipelined")
-    ap.add_argument("--solver", default="cg", choices=["cg", "bicgstab", "gmres"],
-                    help="--mode kernels: cg on the Laplacian, bicgstab / gmres on convection-diffusion")
+    ap.add_argument("--solver", default="cg", choices=["cg", "bicgstab", "gmres", "batched"],
+                    help="--mode kernels: cg on the Laplacian, bicgstab / gmres on convection-diffusion, "
+                         "batched on the 512 shifted rectangles")
+    ap.add_argument("--precision", default="fp64", choices=["fp64", "mixed"],
+                    help="--mode kernels, cg / batched: FP64 or FP32-inner mixed precision")
     ap.add_argument("--matrix", default="stencil", choices=["stencil", "powerlaw", "fe3d"],
                     help="--mode kernels: the stencil of --k, a power-law matrix with --n rows, or P1 "
                          "elasticity on --k^3 cubes")
@@ -74,6 +77,16 @@ def run_kernels(args):
     import torch
     from paper_1410_4054_gb300 import pk
 
+    if args.solver == "batched":
+        mats = W.batched_rectangles(512, seed=0)
+        As = [pk.CSRMatrix.from_workload(m) for m in mats]
+        bs = [torch.from_numpy(W.manufactured(m, seed=k)[1]).cuda() for k, m in enumerate(mats)]
+        xs = [torch.zeros(m.n, dtype=torch.float64, device="cuda") for m in mats]
+        infos = pk.batched_solve(As, bs, xs, tol=0.0, maxit=args.iters, precision=args.precision)
+        torch.cuda.synchronize()
+        print(json.dumps({"mode": "kernels", "solver": "batched", "systems": len(mats),
+                          "iters": infos[0]["iters"], "solve_ms": infos[0]["solve_ms"]}))
+        return 0
     if args.matrix == "powerlaw":
         a = W.power_law(args.n, seed=0)
     elif args.matrix == "fe3d":
@@ -86,7 +99,8 @@ def run_kernels(args):
     xd = torch.zeros(a.n, dtype=torch.float64, device="cuda")
     fn = {"cg": pk.cg_solve, "bicgstab": pk.bicgstab_solve, "gmres": pk.gmres_solve}[args.solver]
     info = fn(A, bd, xd, tol=0.0, maxit=args.iters, variant=args.variant, loop="host",
-              check_every=args.iters, flags=pk.FLAG_SELL if args.sell else 0)
+              check_every=args.iters, flags=pk.FLAG_SELL if args.sell else 0,
+              **({"precision": args.precision} if args.solver == "cg" else {}))
     torch.cuda.synchronize()
     print(json.dumps({"mode": "kernels", "solver": args.solver, "k": args.k, "n": a.n, "iters": info["iters"],
                       "launches": info["launches"], "solve_ms": info["solve_ms"]}))
