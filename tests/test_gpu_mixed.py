@@ -29,7 +29,8 @@ def rel(a, b):
 @pytest.mark.parametrize("make", [lambda: W.laplace_2d(64), lambda: W.laplace_3d(32),
                                   lambda: W.laplace_2d(130, 77, shift=0.3),
                                   lambda: W.spd_random(500, seed=2, density=0.02),
-                                  lambda: W.spd_dense_rows()])   # rows longer than a tile
+                                  lambda: W.spd_dense_rows(),   # rows longer than a tile
+                                  lambda: W.fe_elasticity_3d(8)])  # grouped-lane tiles (FP32 path)
 @pytest.mark.parametrize("loop", ["graph", "host"])
 def test_mixed_reaches_fp64_tolerance(make, loop):
     a = make()

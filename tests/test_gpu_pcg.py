@@ -47,6 +47,8 @@ MATRICES = {
     "spd_rand_scaled": lambda: W.diag_scaled(W.spd_random(300, seed=5, density=0.05), seed=4),
     "spd_powerlaw_scaled": lambda: W.diag_scaled(W.spd_power_law(20_000, seed=3), seed=5),  # rows > 32
     "lap2d_64": lambda: W.laplace_2d(64),  # constant diagonal: Jacobi is a scalar multiple of I
+    "fe3d_elast_4752": lambda: W.fe_elasticity_3d(11),       # grouped-lane tiles
+    "dense_rows_1e4": lambda: W.spd_dense_rows(),             # rows longer than a tile: chunk tiles
 }
 
 
