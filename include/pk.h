@@ -23,6 +23,10 @@
  *     PK_NOT_CONVERGED with x valid.  pk_last_error() gives a message for the last failure
  *     on the calling thread.
  *   - The library uses one GPU: the device current on the calling thread.
+ *   - A pk_csr handle carries its solves' work memory, cached graphs and state, and (during a
+ *     right-Jacobi BiCGStab / GMRES solve) points its values at the scaled copy: calls on one
+ *     handle must not overlap (one solve at a time per handle, from one host thread at a
+ *     time, and in stream order when streams differ).  Different handles are independent.
  */
 #ifndef PK_H_
 #define PK_H_
