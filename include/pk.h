@@ -186,6 +186,9 @@ typedef struct {
    * lengths), or rows of similar length G = 2..16 lanes each (tiles_group) */
   int32_t tiles_thread, tiles_long;
   int32_t tiles_group;
+  /* row-length histogram: rows with 0-8, 9-16, 17-32, 33-64, 65-256, 257-4096 and more than
+   * 4096 nonzeros (one thread, small groups, a warp, long warp rows, chunk tiles) */
+  int64_t row_hist[7];
 } pk_csr_stats;
 
 /*

@@ -546,6 +546,11 @@ pk_status pk_csr_create(int64_t n, int64_t nnz, const int32_t* row_ptr, const in
   st.block = kBlock;
   st.kernel = A->tma_ok ? 2 : 0;
   st.values_fp32_exact = fp32_exact;
+  for (int k = 0; k < 7; ++k) st.row_hist[k] = 0;
+  for (int64_t r = 0; r < n; ++r) {
+    const int64_t L = rp[r + 1] - rp[r];
+    st.row_hist[L <= 8 ? 0 : L <= 16 ? 1 : L <= 32 ? 2 : L <= 64 ? 3 : L <= 256 ? 4 : L <= 4096 ? 5 : 6] += 1;
+  }
   pk_status ps = ensure_state(A);
   if (ps) return fail(ps);
   *out = A;

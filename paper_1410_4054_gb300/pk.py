@@ -53,7 +53,7 @@ class Stats(C.Structure):
                 ("row_max", C.c_int32), ("row_mean", C.c_double), ("grid", C.c_int32),
                 ("block", C.c_int32), ("kernel", C.c_int32), ("values_fp32_exact", C.c_int32),
                 ("tiles_thread", C.c_int32), ("tiles_long", C.c_int32),
-                ("tiles_group", C.c_int32)]
+                ("tiles_group", C.c_int32), ("row_hist", C.c_int64 * 7)]
 
 
 EXPORTS = {
@@ -189,7 +189,9 @@ class CSRMatrix:
     def stats(self) -> dict:
         s = Stats()
         _check(lib().pk_csr_stats_get(self.handle, C.byref(s)), "pk_csr_stats_get")
-        return {k: getattr(s, k) for k, _ in Stats._fields_}
+        d = {k: getattr(s, k) for k, _ in Stats._fields_}
+        d["row_hist"] = list(d["row_hist"])  # rows with 0-8, 9-16, 17-32, 33-64, 65-256, 257-4096, > 4096 nonzeros
+        return d
 
     def close(self):
         if getattr(self, "handle", None):

@@ -287,6 +287,11 @@ def test_rows_longer_than_a_tile_use_chunk_tiles():
     A = pk.CSRMatrix.from_workload(a)
     st = A.stats()
     assert st["kernel"] == 2 and st["tiles_long"] >= 4 * 5
+    lens = np.diff(a.row_ptr)
+    edges = [0, 8, 16, 32, 64, 256, 4096, np.inf]
+    assert st["row_hist"] == [int(((lens > lo) & (lens <= hi)).sum()) if lo else int((lens <= hi).sum())
+                              for lo, hi in zip(edges[:-1], edges[1:])]
+    assert st["row_hist"][6] == 4
     p = W.uniform_pm1(5, a.n)
     _, b, _ = W.manufactured(a, seed=1)
     # one K-CG-S through a fixed single CG iteration: alpha_0 = <r0,r0> / <r0, A r0>
