@@ -106,6 +106,10 @@ enum {
                                 keeps the basis orthonormal and the in-cycle residual estimate
                                 exact on badly conditioned systems.  Other solvers return
                                 PK_ERR_ARG */
+#define PK_FLAG_TEST_STALL 64u  /* testing the failure path: the CSR tile engine's producer
+                                   issues no copies, so the first wait of every consumer runs
+                                   out after pk_opts.wait_ns and the solve returns PK_TIMEOUT
+                                   (nothing is in flight; the context stays usable) */
 
 typedef struct {
   double tol;          /* relative residual tolerance (>= 0) */
@@ -125,6 +129,10 @@ typedef struct {
   int32_t lanes;       /* pk_batched_solve: lanes per matrix row in the row products (1, 2, 4
                           or 8; 0 = automatic: from the batch's mean row length, or tuned with
                           the block shape under PK_FLAG_AUTOTUNE).  Other solvers ignore it */
+  int64_t wait_ns;     /* bound, in ns, on every device-side pipeline wait that should make
+                          progress (0 = 2 s).  A wait that runs out ends the solve with
+                          PK_TIMEOUT after the kernel has drained its own copies; the context
+                          stays usable.  Small values exercise that path in tests */
 } pk_opts;
 
 /* pk_opts.precond.  JACOBI, M = diag(A) (entries of row i in column i summed; Sec. 5 names

@@ -100,6 +100,8 @@ pk_status state_init(pk_csr* A, const pk_opts* o, cudaStream_t s) {
   h->trace = o->trace_cap > 0 ? o->trace : nullptr;
   h->trace_cap = o->trace_cap > 0 ? o->trace_cap : 0;
   h->thr2 = o->tol;  // the setup kernel turns tol into tol^2 <b,b>
+  h->wait_ns = o->wait_ns > 0 ? (unsigned long long)o->wait_ns : 2000000000ull;
+  h->stall_test = (o->flags & PK_FLAG_TEST_STALL) ? 1 : 0;
   PK_CUDA(cudaMemcpyAsync(A->st, h, sizeof(DevState), cudaMemcpyHostToDevice, s));
   return PK_OK;
 }
@@ -248,6 +250,7 @@ pk_status check_opts(const pk_csr* A, const double* b, double* x, const pk_opts*
   if (!(o->tol >= 0.0) || o->maxit < 0) { set_error("tol must be >= 0 and maxit >= 0"); return PK_ERR_ARG; }
   if (o->trace_cap > 0 && !o->trace) { set_error("trace_cap > 0 needs a trace array"); return PK_ERR_ARG; }
   if (o->loop < PK_LOOP_GRAPH || o->loop > PK_LOOP_AUTO) { set_error("bad loop mode"); return PK_ERR_ARG; }
+  if (o->wait_ns < 0) { set_error("wait_ns must be >= 0"); return PK_ERR_ARG; }
   return PK_OK;
 }
 

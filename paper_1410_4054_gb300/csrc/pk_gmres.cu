@@ -218,7 +218,7 @@ __device__ __forceinline__ bool basis_produce(const BasisRing& R, int nq, DevSta
   bool ok = true;
   for (int q = 0; q < nq; ++q) {
     const int s = q % kBsStages;
-    if (q >= kBsStages && !mbar_wait(&R.empty[s], ((q / kBsStages) - 1) & 1)) { ok = false; break; }
+    if (q >= kBsStages && !mbar_wait_st(&R.empty[s], ((q / kBsStages) - 1) & 1, st)) { ok = false; break; }
     const double* src[kBsVecs];
     int row0, rows, nv;
     plan(q, src, row0, rows, nv);
@@ -303,7 +303,7 @@ __global__ void __launch_bounds__(kTileThreads, 2) k_gm2(GmArgs g, int pass) {
       for (int c = 0; c < kBsCols; ++c) acc[c] = 0.0;
       for (int t = 0; t < ntiles && ok; ++t) {
         const int q = grp * ntiles + t, s = q % kBsStages;
-        if (!mbar_wait(&R.full[s], (q / kBsStages) & 1)) { report_timeout(st); ok = false; break; }
+        if (!mbar_wait_st(&R.full[s], (q / kBsStages) & 1, st)) { report_timeout(st); ok = false; break; }
         const int rows = min(kBsRows, r1 - (r0 + t * kBsRows));
         if ((int)threadIdx.x < rows) {
           const double w = R.slot(s, 0)[threadIdx.x];
@@ -418,7 +418,7 @@ __global__ void __launch_bounds__(kTileThreads, 2) k_gm3(GmArgs g, int mode) {
       bool ok = true;
       for (int grp = 0; grp < ngroups; ++grp) {
         const int q = t * ngroups + grp, s = q % kBsStages;
-        if (!mbar_wait(&R.full[s], (q / kBsStages) & 1)) { report_timeout(st); ok = false; break; }
+        if (!mbar_wait_st(&R.full[s], (q / kBsStages) & 1, st)) { report_timeout(st); ok = false; break; }
         const int j0 = 1 + grp * kBsCols, nc = max(0, min(kBsCols, ncols - j0 + 1));
         if (mine) {
           if (grp == 0) w = R.slot(s, 0)[threadIdx.x];

@@ -43,6 +43,9 @@ struct DevState {
   int32_t gm_m, gm_pad;
   cudaGraphConditionalHandle cond2;
   unsigned int gbar;      // grid-barrier arrivals of the persistent (cooperative) solve
+  unsigned long long wait_ns;  // bound on a pipeline wait that should make progress
+  int32_t stall_test;          // PK_FLAG_TEST_STALL: the CSR tile producer issues no copies
+  int32_t stall_pad;
 };
 
 // Loads that bypass L1 (the value was written by another block or an earlier kernel).

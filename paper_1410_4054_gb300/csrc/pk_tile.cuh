@@ -61,14 +61,26 @@ __device__ __forceinline__ uint64_t global_ns() {
   return t;
 }
 
-// Bounded wait on phase `parity`: false once about kWaitNs nanoseconds have passed.
-__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity) {
+// Bounded wait on phase `parity`: false once about `budget_ns` nanoseconds have passed.
+// Pipeline waits that should make progress take the solve's budget (pk_opts.wait_ns, 2 s by
+// default); the drain of a block's own copies before it exits always takes kWaitNs.
+__device__ __forceinline__ bool mbar_wait_for(uint64_t* bar, uint32_t parity, uint64_t budget_ns) {
   if (mbar_try_wait(bar, parity)) return true;
   const uint64_t t0 = global_ns();
   for (;;) {
     if (mbar_try_wait(bar, parity)) return true;
-    if (global_ns() - t0 > kWaitNs) return false;
+    if (global_ns() - t0 > budget_ns) return false;
   }
+}
+
+__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity) {
+  return mbar_wait_for(bar, parity, kWaitNs);
+}
+
+// A progress wait bounded by the solve's budget, read only once the first try has failed.
+__device__ __forceinline__ bool mbar_wait_st(uint64_t* bar, uint32_t parity, const DevState* st) {
+  if (mbar_try_wait(bar, parity)) return true;
+  return mbar_wait_for(bar, parity, st->wait_ns);
 }
 
 // Bulk copy global -> shared (16-byte aligned addresses, size a multiple of 16), completion
@@ -246,7 +258,7 @@ __device__ __forceinline__ bool stream_tiles(const StreamIn<NIN, ET>& in, int r0
       if (live) {
         for (int t = npro; t < ntiles; ++t) {
           const int s = t % kStreamStages;
-          if (!mbar_wait(&empty[s], ((t / kStreamStages) - 1) & 1)) { ok = false; report_timeout(st); break; }
+          if (!mbar_wait_st(&empty[s], ((t / kStreamStages) - 1) & 1, st)) { ok = false; report_timeout(st); break; }
           mbar_expect_tx(&full[s], tile_bytes(t) * NIN);
           issue(t, 0, NIN);
           issued = t + 1;
@@ -263,7 +275,7 @@ __device__ __forceinline__ bool stream_tiles(const StreamIn<NIN, ET>& in, int r0
   const int nproc = live ? ntiles : npro;
   for (int t = 0; t < nproc; ++t) {
     const int s = t % kStreamStages;
-    if (!mbar_wait(&full[s], (t / kStreamStages) & 1)) { report_timeout(st); break; }
+    if (!mbar_wait_st(&full[s], (t / kStreamStages) & 1, st)) { report_timeout(st); break; }
     if (live) {
       const int row0 = r0 + t * kRows;
       const int rows = min(kRows, r1 - row0);
@@ -484,6 +496,12 @@ __device__ __forceinline__ bool csr_tiles(const CsrTilesT<VT>& T, unsigned char*
   const int npro = min(kCsrStages, ntiles);
   bool ok = true;
   if (warp == kConsumerWarps) {
+    // PK_FLAG_TEST_STALL: no copy is issued, so every consumer's first wait runs out after the
+    // solve's wait bound (the timeout path, tested without a fault: nothing is in flight)
+    if (st->stall_test) {
+      griddep_wait();
+      return false;
+    }
     // producer warp: lanes prefetch tile bounds 32 tiles at a time, lane 0 issues copies.
     // The matrix does not depend on the preceding kernel: the first stages are issued before
     // the grid-dependency wait; after it the producer stops if the solve has finished.
@@ -515,7 +533,7 @@ __device__ __forceinline__ bool csr_tiles(const CsrTilesT<VT>& T, unsigned char*
           const int t = base + q;
           const int s = t % kCsrStages;
           const int use = t / kCsrStages;
-          if (use > 0 && !mbar_wait(&empty[s], (use - 1) & 1)) { ok = false; report_timeout(st); }
+          if (use > 0 && !mbar_wait_st(&empty[s], (use - 1) & 1, st)) { ok = false; report_timeout(st); }
           if (ok) {
             const int rs = a0 & ~3, re = (a1 + 1 + 3) & ~3;    // row pointers a0..a1
             const int vs = b0 & ~(kVaUnit - 1), ve = (b1 + kVaUnit - 1) & ~(kVaUnit - 1);  // values
@@ -555,7 +573,7 @@ __device__ __forceinline__ bool csr_tiles(const CsrTilesT<VT>& T, unsigned char*
   VT chunk_acc = (VT)0;  // this thread's share of the current long row (chunk tiles)
   for (int t = 0; t < nproc; ++t) {
     const int s = t % kCsrStages;
-    if (!mbar_wait(&full[s], (t / kCsrStages) & 1)) { report_timeout(st); break; }
+    if (!mbar_wait_st(&full[s], (t / kCsrStages) & 1, st)) { report_timeout(st); break; }
     if (!live) {
       __syncwarp();
       if (lane == 0) mbar_arrive(&empty[s]);

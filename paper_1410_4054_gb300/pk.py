@@ -30,6 +30,7 @@ FLAG_NO_TMA = 4
 FLAG_AUTOTUNE = 8
 FLAG_SELL = 16
 FLAG_CGS2 = 32
+FLAG_TEST_STALL = 64
 SLOTS = ["spmv_dots", "update", "multidot", "ortho", "spmv", "blas1", "other"]
 MAX_SLOTS = 8
 
@@ -38,7 +39,8 @@ class Opts(C.Structure):
     _fields_ = [("tol", C.c_double), ("maxit", C.c_int32), ("restart", C.c_int32),
                 ("variant", C.c_int32), ("precision", C.c_int32), ("loop", C.c_int32),
                 ("check_every", C.c_int32), ("flags", C.c_uint32), ("trace_cap", C.c_int32),
-                ("trace", C.c_void_p), ("precond", C.c_int32), ("lanes", C.c_int32)]
+                ("trace", C.c_void_p), ("precond", C.c_int32), ("lanes", C.c_int32),
+                ("wait_ns", C.c_int64)]
 
 
 class Info(C.Structure):
@@ -209,10 +211,12 @@ PRECONDS = {"none": 0, "jacobi": 1}
 
 
 def make_opts(tol=1e-8, maxit=1000, restart=30, variant="pipelined", precision="fp64",
-              loop="auto", check_every=0, flags=0, trace=None, precond="none", lanes=0) -> Opts:
+              loop="auto", check_every=0, flags=0, trace=None, precond="none", lanes=0,
+              wait_ns=0) -> Opts:
     o = Opts()
     o.precond = PRECONDS[precond] if isinstance(precond, str) else int(precond)
     o.lanes = int(lanes)
+    o.wait_ns = int(wait_ns)
     o.tol = tol
     o.maxit = maxit
     o.restart = restart

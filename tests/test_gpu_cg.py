@@ -302,3 +302,26 @@ def test_rows_longer_than_a_tile_use_chunk_tiles():
     np.testing.assert_allclose(tr.cpu().numpy()[0, :2], [ref["alpha"][0], ref["beta"][0]], rtol=1e-12)
     assert rel(x.cpu().numpy(), ref["x"]) <= 1e-13
     del p
+
+
+@pytest.mark.parametrize("solver", ["cg", "cg_jacobi", "cg_mixed", "bicgstab", "gmres"])
+def test_bounded_waits_time_out_and_the_context_stays_usable(solver):
+    """Failure detection without a GPU fault: with PK_FLAG_TEST_STALL the CSR tile engine's
+    producer issues no copies, so every consumer's first wait (a barrier phase that nothing
+    completes) runs out after the 1 ms bound; the kernel records it and returns, the solve
+    ends with PK_TIMEOUT, and the next solve on the same handle, with the default bound and
+    no flag, is exact."""
+    a = W.laplace_3d(48)  # 110,592 rows: the graph loop with the tile engines
+    _, b, _ = W.manufactured(a, seed=3)
+    A = pk.CSRMatrix.from_workload(a)
+    fn = pk.gmres_solve if solver == "gmres" else pk.bicgstab_solve if solver == "bicgstab" else pk.cg_solve
+    kw = {"cg_jacobi": {"precond": "jacobi"}, "cg_mixed": {"precision": "mixed"}}.get(solver, {})
+    x = dev(np.zeros(a.n))
+    with pytest.raises(pk.PkError) as err:
+        fn(A, dev(b), x, tol=1e-8, maxit=40, wait_ns=1_000_000, flags=pk.FLAG_TEST_STALL, **kw)
+    assert err.value.status == pk.PK_TIMEOUT
+    torch.cuda.synchronize()
+    info = fn(A, dev(b), x.zero_(), tol=1e-8, maxit=5000, flags=pk.FLAG_TRUE_RES, **kw)
+    assert info["status"] == pk.PK_OK and info["rel_res_true"] <= 1.5e-8
+    with pytest.raises(RuntimeError, match="wait_ns"):
+        fn(A, dev(b), x, wait_ns=-1)
