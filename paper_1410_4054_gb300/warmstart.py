@@ -92,6 +92,31 @@ class ConvNet:
         for w16, wf in zip(self.W16, self.Wf16):
             pk.conv3d_flip(w16, wf)
 
+    # -------------------------------------------------------------- checkpoints
+    def state_dict(self) -> dict:
+        """FP32 master weights and biases, Adam moments and step (host tensors); the BF16
+        copies are derived from the masters on load."""
+        cpu = lambda lst: [t.detach().cpu().clone() for t in lst]  # noqa: E731
+        return {"dims": self.dims, "step": self.step, "W32": cpu(self.W32), "b32": cpu(self.b32),
+                "mW": cpu(self.mW), "vW": cpu(self.vW), "mb": cpu(self.mb), "vb": cpu(self.vb)}
+
+    def load_state_dict(self, d: dict):
+        if tuple(d["dims"]) != self.dims:
+            raise ValueError(f"checkpoint for grid {tuple(d['dims'])}, network built for {self.dims}")
+        for key in ("W32", "b32", "mW", "vW", "mb", "vb"):
+            for dst, src in zip(getattr(self, key), d[key]):
+                dst.copy_(src.to(dst.device))
+        for w32, w16 in zip(self.W32, self.W16):
+            w16.copy_(w32.to(self.torch.bfloat16))
+        self.step = int(d["step"])
+        self.refresh_flipped()
+
+    def save(self, path):
+        self.torch.save(self.state_dict(), path)
+
+    def load(self, path):
+        self.load_state_dict(self.torch.load(path, map_location="cpu"))
+
     def pack(self, A, xm1, xm2, b):
         """acts[0] = packed network input; scales = (s0, s1, s2)."""
         pk.warmstart_input(A, xm1, xm2, b, self.acts[0], self.scales, self.scratch)
@@ -138,12 +163,19 @@ class ConvNet:
 
 
 def run_transient(k=64, steps=300, train_last=150, epochs=30, lr=1e-3, tol=1e-8, seed=0,
-                  device="cuda", log=None):
+                  device="cuda", log=None, checkpoint=None, resume=False):
     """The transient experiment: solve the whole sequence with the x_{t-1} warm start, train on
     steps 2..train_last, then re-solve steps train_last+1..steps from (a) the linear
     extrapolation 2 x_{t-1} - x_{t-2} and (b) the learned guess, each measured against x_{t-1} by
     its residual.  Returns per-step iteration counts and times of all three, plus training
-    statistics."""
+    statistics.
+
+    checkpoint: a file for the solved sequence (x_t, b_t, plain warm-start iterations and
+    times) and the network (weights, Adam state), written after training.  resume=True loads
+    it, skips solving the sequence and continues training for `epochs` more epochs (0:
+    evaluate the saved network as it is)."""
+    import os
+
     import torch
 
     from . import workloads as W
@@ -153,21 +185,30 @@ def run_transient(k=64, steps=300, train_last=150, epochs=30, lr=1e-3, tol=1e-8,
     n = T.M.n
     dt = T.dt
     zeros = torch.zeros(n, dtype=torch.float64, device=device)
-    xs = [zeros.clone(), zeros.clone()]  # x_{-1}, x_0
-    bs = [None, None]
-    base_iters, base_ms = [], []
-    for t in range(1, steps + 1):
-        f = torch.from_numpy(T.source(t)).to(device)
-        b = xs[-1] + dt * f
-        x = xs[-1].clone()
-        info = pk.cg_solve(A, b, x, tol=tol, maxit=10_000)
-        assert info["status"] == pk.PK_OK, info
-        base_iters.append(info["iters"])
-        base_ms.append(info["solve_ms"])
-        xs.append(x)
-        bs.append(b)
-    # sample t: x_{t-1} = xs[t], x_{t-2} = xs[t-1], b_t = bs[t+1], target x_t = xs[t+1]
     net = ConvNet((k, k, k), device=device, seed=seed)
+    if resume and checkpoint and os.path.exists(checkpoint):
+        ck = torch.load(checkpoint, map_location="cpu")
+        if (ck["k"], ck["steps"], ck["seed"]) != (k, steps, seed):
+            raise ValueError("checkpoint of a different transient sequence")
+        xs = [v.to(device) for v in ck["xs"]]
+        bs = [None, None] + [v.to(device) for v in ck["bs"][2:]]
+        base_iters, base_ms = list(ck["base_iters"]), list(ck["base_ms"])
+        net.load_state_dict(ck["net"])
+    else:
+        xs = [zeros.clone(), zeros.clone()]  # x_{-1}, x_0
+        bs = [None, None]
+        base_iters, base_ms = [], []
+        for t in range(1, steps + 1):
+            f = torch.from_numpy(T.source(t)).to(device)
+            b = xs[-1] + dt * f
+            x = xs[-1].clone()
+            info = pk.cg_solve(A, b, x, tol=tol, maxit=10_000)
+            assert info["status"] == pk.PK_OK, info
+            base_iters.append(info["iters"])
+            base_ms.append(info["solve_ms"])
+            xs.append(x)
+            bs.append(b)
+    # sample t: x_{t-1} = xs[t], x_{t-2} = xs[t-1], b_t = bs[t+1], target x_t = xs[t+1]
     train = list(range(2, train_last + 1))
     rng = np.random.default_rng(seed)
     t0 = time.perf_counter()
@@ -187,6 +228,10 @@ def run_transient(k=64, steps=300, train_last=150, epochs=30, lr=1e-3, tol=1e-8,
             log(f"epoch {ep}")
     torch.cuda.synchronize()
     train_s = time.perf_counter() - t0
+    if checkpoint:
+        torch.save({"k": k, "steps": steps, "seed": seed, "xs": [v.cpu() for v in xs],
+                    "bs": [None, None] + [v.cpu() for v in bs[2:]], "base_iters": base_iters,
+                    "base_ms": base_ms, "net": net.state_dict()}, checkpoint)
 
     xhat = zeros.clone()
     r2 = torch.zeros(2, dtype=torch.float64, device=device)

@@ -198,3 +198,39 @@ def test_transient_learned_warm_start():
     assert res["learned_max_kept_ratio"] <= 1.0 and res["extrap_max_kept_ratio"] <= 1.0
     assert res["learned_mean_iters"] <= res["baseline_mean_iters"]
     assert res["extrap_mean_iters"] <= res["baseline_mean_iters"]
+
+
+def test_checkpoint_round_trip_and_resume(tmp_path):
+    """A network restored from a checkpoint predicts bitwise like the saved one and takes the
+    same Adam steps (moments and step count restored); run_transient resumes from its
+    checkpoint without re-solving the sequence."""
+    from paper_1410_4054_gb300 import workloads as W
+
+    T = W.transient_heat(16, steps=4, seed=3)
+    A = pk.CSRMatrix.from_workload(T.M)
+    r = np.random.default_rng(8)
+    xm1, xm2, b, xt = (torch.from_numpy(v).to(DEV) for v in r.standard_normal((4, T.M.n)))
+    net = WS.ConvNet((16, 16, 16), device=DEV, seed=2)
+    for _ in range(3):
+        net.train_sample(A, xm1, xm2, b, xt)
+    path = tmp_path / "net.pt"
+    net.save(path)
+    other = WS.ConvNet((16, 16, 16), device=DEV, seed=9)
+    other.load(path)
+    y1, y2 = torch.empty_like(xt), torch.empty_like(xt)
+    net.predict(A, xm1, xm2, b, y1)
+    other.predict(A, xm1, xm2, b, y2)
+    torch.cuda.synchronize()
+    assert torch.equal(y1, y2)
+    net.train_sample(A, xm1, xm2, b, xt)
+    other.train_sample(A, xm1, xm2, b, xt)
+    torch.cuda.synchronize()
+    assert other.step == net.step
+    assert all(torch.equal(a, c) for a, c in zip(net.W32, other.W32))
+    with pytest.raises(ValueError, match="grid"):
+        WS.ConvNet((8, 8, 8), device=DEV).load(path)
+    ck = tmp_path / "transient.pt"
+    first = WS.run_transient(k=16, steps=12, train_last=6, epochs=2, checkpoint=str(ck))
+    again = WS.run_transient(k=16, steps=12, train_last=6, epochs=0, checkpoint=str(ck), resume=True)
+    assert again["baseline_iters_eval"] == first["baseline_iters_eval"]
+    assert again["learned_iters_eval"] == first["learned_iters_eval"]
