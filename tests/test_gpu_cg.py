@@ -325,3 +325,17 @@ def test_bounded_waits_time_out_and_the_context_stays_usable(solver):
     assert info["status"] == pk.PK_OK and info["rel_res_true"] <= 1.5e-8
     with pytest.raises(RuntimeError, match="wait_ns"):
         fn(A, dev(b), x, wait_ns=-1)
+
+
+@pytest.mark.parametrize("solver", ["bicgstab", "gmres", "cg_jacobi", "cg_mixed", "bicgstab_jacobi"])
+def test_nan_in_b_is_reported(solver):
+    """A NaN in b reaches <b, b> in the setup kernel's last block: PK_ERR_NAN, no iteration."""
+    a = W.convdiff_3d(10) if solver.startswith(("bicgstab", "gmres")) else W.laplace_3d(10)
+    _, b, _ = W.manufactured(a)
+    b[17] = np.nan
+    A = pk.CSRMatrix.from_workload(a)
+    fn = pk.gmres_solve if solver == "gmres" else pk.bicgstab_solve if solver.startswith("bicgstab") else pk.cg_solve
+    kw = {"cg_jacobi": {"precond": "jacobi"}, "bicgstab_jacobi": {"precond": "jacobi"},
+          "cg_mixed": {"precision": "mixed"}}.get(solver, {})
+    info = fn(A, dev(b), dev(np.zeros(a.n)), tol=1e-8, maxit=100, **kw)
+    assert info["status"] == pk.PK_ERR_NAN and info["iters"] == 0
