@@ -218,6 +218,12 @@ pk_status pk_csr_destroy(pk_csr* A);
 /* Row statistics and the schedule chosen for A. */
 pk_status pk_csr_stats_get(const pk_csr* A, pk_csr_stats* out);
 
+/* The statistics and schedule pk_csr_create would choose for a matrix with these row pointers
+ * on a device with `sms` multiprocessors, computed on the host alone (no GPU, nothing kept):
+ * row_ptr is a HOST int32 array of n + 1 entries; values_fp32_exact is -1 (no values given).
+ * An invalid row_ptr returns PK_ERR_ARG. */
+pk_status pk_csr_plan(int64_t n, int64_t nnz, const int32_t* row_ptr, int32_t sms, pk_csr_stats* out);
+
 /* y = A x (device pointers, length n) -- the plain CSR product of Sec. 2.2. */
 pk_status pk_spmv(pk_csr* A, const double* x, double* y, void* stream);
 

@@ -288,6 +288,166 @@ pk_status finish_info(pk_csr* A, const pk_opts* o, pk_info* info, cudaStream_t s
 
 using namespace pk;
 
+// The launch schedule of a CSR matrix, host only (pk_csr_create and pk_csr_plan): the row
+// ranges of the persistent grid, the tile list of the bulk-copy engine with each tile's row
+// schedule, and the tile counts by schedule.
+struct CsrPlan {
+  int grid = 1, grid_tma = 1, grid_stream = 1, ntiles = 0, tma_ok = 1;
+  std::vector<int32_t> rb, tile_row, blk_tile, tile_z0;
+  std::vector<int8_t> tile_grp;
+  std::vector<int16_t> tile_perm;
+  int32_t tiles_thread = 0, tiles_long = 0, tiles_group = 0;
+};
+
+static void build_plan(int64_t n, int64_t nnz, const std::vector<int32_t>& rp, int sms, CsrPlan& P) {
+  // persistent grid: up to kMaxGridPerSm blocks per SM, at least kBlock rows per block
+  const int64_t gmax = (int64_t)sms * kMaxGridPerSm;
+  P.grid = (int)std::max<int64_t>(1, std::min<int64_t>(gmax, (n + kBlock - 1) / kBlock));
+  // nnz-balanced contiguous row ranges: weight of a row = its nonzeros + 2
+  P.rb.assign(P.grid + 1, 0);
+  auto& rb = P.rb;
+  const double wtot = (double)nnz + 2.0 * (double)n;
+  rb[0] = 0;
+  for (int b = 1; b < P.grid; ++b) {
+    const double target = wtot * b / P.grid;
+    int64_t lo = rb[b - 1], hi = n;  // first row with rp[row] + 2 row >= target
+    while (lo < hi) {
+      const int64_t mid = (lo + hi) / 2;
+      if ((double)rp[mid] + 2.0 * (double)mid < target) lo = mid + 1; else hi = mid;
+    }
+    int64_t r = (lo / 32) * 32;  // warp-aligned boundaries
+    rb[b] = (int32_t)std::max<int64_t>(r, rb[b - 1]);
+  }
+  rb[P.grid] = (int32_t)n;
+
+  // warp-specialised CSR tiles: 2 blocks per SM, nnz-balanced block ranges, tiles of at most
+  // kTileRows rows and kTileNnz nonzeros
+  auto& tile_row = P.tile_row;
+  auto& blk_tile = P.blk_tile;
+  auto& tile_z0 = P.tile_z0;
+  P.tma_ok = 1;
+  // at least one tile per block where the matrix has that many: tiles end at kTileRows rows or
+  // kTileNnz nonzeros, whichever comes first
+  P.grid_tma = (int)std::max<int64_t>(
+      1, std::min<int64_t>((int64_t)sms * 2, std::max<int64_t>((n + kTileRows - 1) / kTileRows,
+                                                               ((int64_t)nnz + kTileNnz - 1) / kTileNnz)));
+  {
+    const int Gt = P.grid_tma;
+    std::vector<int32_t> tb(Gt + 1);
+    tb[0] = 0;
+    for (int b = 1; b < Gt; ++b) {
+      const double target = wtot * b / Gt;
+      int64_t lo = tb[b - 1], hi = n;
+      while (lo < hi) {
+        const int64_t mid = (lo + hi) / 2;
+        if ((double)rp[mid] + 2.0 * (double)mid < target) lo = mid + 1; else hi = mid;
+      }
+      tb[b] = (int32_t)std::max<int64_t>((lo / 32) * 32, tb[b - 1]);
+    }
+    tb[Gt] = (int32_t)n;
+    blk_tile.push_back(0);
+    for (int b = 0; b < Gt && P.tma_ok; ++b) {
+      int64_t R = tb[b];
+      while (R < tb[b + 1]) {
+        int64_t R1 = std::min<int64_t>(R + kTileRows, tb[b + 1]);
+        if (rp[R1] - rp[R] > kTileNnz) {
+          int64_t lo = R, hi = R1;  // largest R1 with rp[R1] - rp[R] <= kTileNnz
+          while (lo < hi) {
+            const int64_t mid = (lo + hi + 1) / 2;
+            if (rp[mid] - rp[R] <= kTileNnz) lo = mid; else hi = mid - 1;
+          }
+          R1 = lo;
+        }
+        if (R1 == R) {
+          // a row longer than a tile: one chunk tile per kTileNnz of its nonzeros, summed by
+          // the whole block (csr_tiles, block per row)
+          for (int64_t z = rp[R]; z < rp[R + 1]; z += kTileNnz) {
+            tile_row.push_back((int32_t)R);
+            tile_z0.resize(tile_row.size() - 1, -1);
+            tile_z0.push_back((int32_t)z);
+          }
+          R = R + 1;
+          continue;
+        }
+        tile_row.push_back((int32_t)R);
+        R = R1;
+      }
+      blk_tile.push_back((int32_t)tile_row.size());
+    }
+    tile_row.push_back((int32_t)n);
+    P.ntiles = (int)tile_row.size() - 1;
+    if (!tile_z0.empty()) tile_z0.resize(P.ntiles, -1);
+  }
+  // per tile, the lanes that compute one row (see csr_tiles): 1 = one thread per row (two rows
+  // per thread, in one pass), 2..16 = a group of lanes per row, 32 = short rows one thread and
+  // rows longer than 32 nonzeros a whole warp each, in a length-sorted row order.  A tile
+  // holds at most kTileNnz nonzeros, so long rows mean few rows per tile: with one thread per
+  // row most consumer threads would idle.  The group size minimises the rounds of (at most 8)
+  // dependent gathers a lane waits for: ceil(rows G / consumers) rows one after the other,
+  // each ceil(lmax / 8 G) batches.  Tiles whose longest row is far above their mean (power-law
+  // rows) take the sorted whole-warp schedule instead.
+  auto tile_lanes = [&](int64_t rows, int64_t lmax, int64_t z) -> int {
+    if (lmax <= 8) return 1;
+    const double mean = (double)z / (double)rows;
+    if (lmax > 32 && (double)lmax > 3.0 * mean + 8.0) return 32;
+    int best = 1;
+    double cost = std::ceil((double)lmax / 8.0);  // two rows per thread, interleaved
+    for (int G = 2; G <= 16; G *= 2) {
+      const double c = std::ceil((double)(rows * G) / kConsumers) * std::ceil((double)lmax / (8.0 * G));
+      if (c <= cost) { best = G; cost = c; }  // ties: more lanes, fewer batches per row
+    }
+    return best == 1 && lmax > 32 ? 32 : best;
+  };
+  P.tile_grp.assign(P.tma_ok ? P.ntiles : 0, 1);
+  auto& tile_grp = P.tile_grp;
+  for (int t = 0; t < (int)tile_grp.size(); ++t) {
+    if (!tile_z0.empty() && tile_z0[t] >= 0) {  // chunk of a row longer than a tile
+      tile_grp[t] = 64;
+      P.tiles_long += 1;
+      continue;
+    }
+    int64_t lmax = 0;
+    for (int64_t r = tile_row[t]; r < tile_row[t + 1]; ++r) lmax = std::max<int64_t>(lmax, rp[r + 1] - rp[r]);
+    tile_grp[t] = (int8_t)tile_lanes(tile_row[t + 1] - tile_row[t], lmax, rp[tile_row[t + 1]] - rp[tile_row[t]]);
+    (tile_grp[t] == 1 ? P.tiles_thread : tile_grp[t] == 32 ? P.tiles_long : P.tiles_group) += 1;
+  }
+  // row order of every irregular tile: rows sorted by length (longest first), dealt
+  // round-robin over the 8 consumer warps -- slot (warp w, lane l) takes sorted rows
+  // 8 l + w and 256 + 8 l + w -- so that each warp holds rows of similar length and the
+  // long rows spread over all warps; -1 marks an empty slot
+  auto& tile_perm = P.tile_perm;
+  if (P.tiles_long > 0) {
+    tile_perm.assign((size_t)P.ntiles * kTileRows, (int16_t)-1);
+    std::vector<int32_t> order;
+    for (int t = 0; t < P.ntiles; ++t) {
+      if (tile_grp[t] != 32) continue;
+      const int32_t R0 = tile_row[t], m = tile_row[t + 1] - R0;
+      order.resize(m);
+      for (int k = 0; k < m; ++k) order[k] = k;
+      std::stable_sort(order.begin(), order.end(), [&](int32_t a, int32_t b) {
+        return rp[R0 + a + 1] - rp[R0 + a] > rp[R0 + b + 1] - rp[R0 + b];
+      });
+      int16_t* P = tile_perm.data() + (size_t)t * kTileRows;
+      for (int tid = 0; tid < kTileRows / 2; ++tid) {
+        const int w = tid / 32, l = tid % 32;
+        const int k1 = 8 * l + w, k2 = kTileRows / 2 + 8 * l + w;
+        P[tid] = k1 < m ? (int16_t)order[k1] : (int16_t)-1;
+        P[kTileRows / 2 + tid] = k2 < m ? (int16_t)order[k2] : (int16_t)-1;
+      }
+    }
+  }
+  P.grid_stream = (int)std::max<int64_t>(1, std::min<int64_t>((int64_t)sms * 2, (n + 511) / 512));
+}
+
+// Row-length histogram: 0-8, 9-16, 17-32, 33-64, 65-256, 257-4096, > 4096 nonzeros.
+static void row_histogram(int64_t n, const std::vector<int32_t>& rp, int64_t (&hist)[7]) {
+  for (int k = 0; k < 7; ++k) hist[k] = 0;
+  for (int64_t r = 0; r < n; ++r) {
+    const int64_t L = rp[r + 1] - rp[r];
+    hist[L <= 8 ? 0 : L <= 16 ? 1 : L <= 32 ? 2 : L <= 64 ? 3 : L <= 256 ? 4 : L <= 4096 ? 5 : 6] += 1;
+  }
+}
+
 extern "C" {
 
 const char* pk_status_string(pk_status s) {
@@ -365,139 +525,22 @@ pk_status pk_csr_create(int64_t n, int64_t nnz, const int32_t* row_ptr, const in
   cudaGetDevice(&A->device);
   int sms = 148;
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, A->device);
-  // persistent grid: up to kMaxGridPerSm blocks per SM, at least kBlock rows per block
-  const int64_t gmax = (int64_t)sms * kMaxGridPerSm;
-  A->grid = (int)std::max<int64_t>(1, std::min<int64_t>(gmax, (n + kBlock - 1) / kBlock));
-  // nnz-balanced contiguous row ranges: weight of a row = its nonzeros + 2
-  std::vector<int32_t> rb(A->grid + 1);
-  const double wtot = (double)nnz + 2.0 * (double)n;
-  rb[0] = 0;
-  for (int b = 1; b < A->grid; ++b) {
-    const double target = wtot * b / A->grid;
-    int64_t lo = rb[b - 1], hi = n;  // first row with rp[row] + 2 row >= target
-    while (lo < hi) {
-      const int64_t mid = (lo + hi) / 2;
-      if ((double)rp[mid] + 2.0 * (double)mid < target) lo = mid + 1; else hi = mid;
-    }
-    int64_t r = (lo / 32) * 32;  // warp-aligned boundaries
-    rb[b] = (int32_t)std::max<int64_t>(r, rb[b - 1]);
-  }
-  rb[A->grid] = (int32_t)n;
-
-  // warp-specialised CSR tiles: 2 blocks per SM, nnz-balanced block ranges, tiles of at most
-  // kTileRows rows and kTileNnz nonzeros
-  std::vector<int32_t> tile_row, blk_tile, tile_z0;
-  A->tma_ok = 1;
-  // at least one tile per block where the matrix has that many: tiles end at kTileRows rows or
-  // kTileNnz nonzeros, whichever comes first
-  A->grid_tma = (int)std::max<int64_t>(
-      1, std::min<int64_t>((int64_t)sms * 2, std::max<int64_t>((n + kTileRows - 1) / kTileRows,
-                                                               ((int64_t)nnz + kTileNnz - 1) / kTileNnz)));
-  {
-    const int Gt = A->grid_tma;
-    std::vector<int32_t> tb(Gt + 1);
-    tb[0] = 0;
-    for (int b = 1; b < Gt; ++b) {
-      const double target = wtot * b / Gt;
-      int64_t lo = tb[b - 1], hi = n;
-      while (lo < hi) {
-        const int64_t mid = (lo + hi) / 2;
-        if ((double)rp[mid] + 2.0 * (double)mid < target) lo = mid + 1; else hi = mid;
-      }
-      tb[b] = (int32_t)std::max<int64_t>((lo / 32) * 32, tb[b - 1]);
-    }
-    tb[Gt] = (int32_t)n;
-    blk_tile.push_back(0);
-    for (int b = 0; b < Gt && A->tma_ok; ++b) {
-      int64_t R = tb[b];
-      while (R < tb[b + 1]) {
-        int64_t R1 = std::min<int64_t>(R + kTileRows, tb[b + 1]);
-        if (rp[R1] - rp[R] > kTileNnz) {
-          int64_t lo = R, hi = R1;  // largest R1 with rp[R1] - rp[R] <= kTileNnz
-          while (lo < hi) {
-            const int64_t mid = (lo + hi + 1) / 2;
-            if (rp[mid] - rp[R] <= kTileNnz) lo = mid; else hi = mid - 1;
-          }
-          R1 = lo;
-        }
-        if (R1 == R) {
-          // a row longer than a tile: one chunk tile per kTileNnz of its nonzeros, summed by
-          // the whole block (csr_tiles, block per row)
-          for (int64_t z = rp[R]; z < rp[R + 1]; z += kTileNnz) {
-            tile_row.push_back((int32_t)R);
-            tile_z0.resize(tile_row.size() - 1, -1);
-            tile_z0.push_back((int32_t)z);
-          }
-          R = R + 1;
-          continue;
-        }
-        tile_row.push_back((int32_t)R);
-        R = R1;
-      }
-      blk_tile.push_back((int32_t)tile_row.size());
-    }
-    tile_row.push_back((int32_t)n);
-    A->ntiles = (int)tile_row.size() - 1;
-    if (!tile_z0.empty()) tile_z0.resize(A->ntiles, -1);
-  }
-  // per tile, the lanes that compute one row (see csr_tiles): 1 = one thread per row (two rows
-  // per thread, in one pass), 2..16 = a group of lanes per row, 32 = short rows one thread and
-  // rows longer than 32 nonzeros a whole warp each, in a length-sorted row order.  A tile
-  // holds at most kTileNnz nonzeros, so long rows mean few rows per tile: with one thread per
-  // row most consumer threads would idle.  The group size minimises the rounds of (at most 8)
-  // dependent gathers a lane waits for: ceil(rows G / consumers) rows one after the other,
-  // each ceil(lmax / 8 G) batches.  Tiles whose longest row is far above their mean (power-law
-  // rows) take the sorted whole-warp schedule instead.
-  auto tile_lanes = [&](int64_t rows, int64_t lmax, int64_t z) -> int {
-    if (lmax <= 8) return 1;
-    const double mean = (double)z / (double)rows;
-    if (lmax > 32 && (double)lmax > 3.0 * mean + 8.0) return 32;
-    int best = 1;
-    double cost = std::ceil((double)lmax / 8.0);  // two rows per thread, interleaved
-    for (int G = 2; G <= 16; G *= 2) {
-      const double c = std::ceil((double)(rows * G) / kConsumers) * std::ceil((double)lmax / (8.0 * G));
-      if (c <= cost) { best = G; cost = c; }  // ties: more lanes, fewer batches per row
-    }
-    return best == 1 && lmax > 32 ? 32 : best;
-  };
-  std::vector<int8_t> tile_grp(A->tma_ok ? A->ntiles : 0);
-  for (int t = 0; t < (int)tile_grp.size(); ++t) {
-    if (!tile_z0.empty() && tile_z0[t] >= 0) {  // chunk of a row longer than a tile
-      tile_grp[t] = 64;
-      A->stats.tiles_long += 1;
-      continue;
-    }
-    int64_t lmax = 0;
-    for (int64_t r = tile_row[t]; r < tile_row[t + 1]; ++r) lmax = std::max<int64_t>(lmax, rp[r + 1] - rp[r]);
-    tile_grp[t] = (int8_t)tile_lanes(tile_row[t + 1] - tile_row[t], lmax, rp[tile_row[t + 1]] - rp[tile_row[t]]);
-    (tile_grp[t] == 1 ? A->stats.tiles_thread : tile_grp[t] == 32 ? A->stats.tiles_long : A->stats.tiles_group) += 1;
-  }
-  // row order of every irregular tile: rows sorted by length (longest first), dealt
-  // round-robin over the 8 consumer warps -- slot (warp w, lane l) takes sorted rows
-  // 8 l + w and 256 + 8 l + w -- so that each warp holds rows of similar length and the
-  // long rows spread over all warps; -1 marks an empty slot
-  std::vector<int16_t> tile_perm;
-  if (A->stats.tiles_long > 0) {
-    tile_perm.assign((size_t)A->ntiles * kTileRows, (int16_t)-1);
-    std::vector<int32_t> order;
-    for (int t = 0; t < A->ntiles; ++t) {
-      if (tile_grp[t] != 32) continue;
-      const int32_t R0 = tile_row[t], m = tile_row[t + 1] - R0;
-      order.resize(m);
-      for (int k = 0; k < m; ++k) order[k] = k;
-      std::stable_sort(order.begin(), order.end(), [&](int32_t a, int32_t b) {
-        return rp[R0 + a + 1] - rp[R0 + a] > rp[R0 + b + 1] - rp[R0 + b];
-      });
-      int16_t* P = tile_perm.data() + (size_t)t * kTileRows;
-      for (int tid = 0; tid < kTileRows / 2; ++tid) {
-        const int w = tid / 32, l = tid % 32;
-        const int k1 = 8 * l + w, k2 = kTileRows / 2 + 8 * l + w;
-        P[tid] = k1 < m ? (int16_t)order[k1] : (int16_t)-1;
-        P[kTileRows / 2 + tid] = k2 < m ? (int16_t)order[k2] : (int16_t)-1;
-      }
-    }
-  }
-  A->grid_stream = (int)std::max<int64_t>(1, std::min<int64_t>((int64_t)sms * 2, (n + 511) / 512));
+  CsrPlan P;
+  build_plan(n, nnz, rp, sms, P);
+  A->grid = P.grid;
+  A->grid_tma = P.grid_tma;
+  A->grid_stream = P.grid_stream;
+  A->ntiles = P.ntiles;
+  A->tma_ok = P.tma_ok;
+  A->stats.tiles_thread = P.tiles_thread;
+  A->stats.tiles_long = P.tiles_long;
+  A->stats.tiles_group = P.tiles_group;
+  auto& rb = P.rb;
+  auto& tile_row = P.tile_row;
+  auto& blk_tile = P.blk_tile;
+  auto& tile_z0 = P.tile_z0;
+  auto& tile_grp = P.tile_grp;
+  auto& tile_perm = P.tile_perm;
 
   auto fail = [&](pk_status e) { pk_csr_destroy(A); return e; };
   cudaError_t e;
@@ -549,11 +592,7 @@ pk_status pk_csr_create(int64_t n, int64_t nnz, const int32_t* row_ptr, const in
   st.block = kBlock;
   st.kernel = A->tma_ok ? 2 : 0;
   st.values_fp32_exact = fp32_exact;
-  for (int k = 0; k < 7; ++k) st.row_hist[k] = 0;
-  for (int64_t r = 0; r < n; ++r) {
-    const int64_t L = rp[r + 1] - rp[r];
-    st.row_hist[L <= 8 ? 0 : L <= 16 ? 1 : L <= 32 ? 2 : L <= 64 ? 3 : L <= 256 ? 4 : L <= 4096 ? 5 : 6] += 1;
-  }
+  row_histogram(n, rp, st.row_hist);
   pk_status ps = ensure_state(A);
   if (ps) return fail(ps);
   *out = A;
@@ -593,6 +632,43 @@ pk_status pk_csr_destroy(pk_csr* A) {
   if (A->tile_z0) cudaFree(A->tile_z0);
   if (A->cap_stream) cudaStreamDestroy(A->cap_stream);
   delete A;
+  return PK_OK;
+}
+
+pk_status pk_csr_plan(int64_t n, int64_t nnz, const int32_t* row_ptr, int32_t sms, pk_csr_stats* out) {
+  if (!out || n < 0 || nnz < 0 || n >= (int64_t(1) << 31) - 64 || nnz >= (int64_t(1) << 31) || sms < 1 ||
+      (n > 0 && !row_ptr)) {
+    set_error("pk_csr_plan: bad arguments");
+    return PK_ERR_ARG;
+  }
+  std::vector<int32_t> rp(n + 1, 0);
+  if (n > 0) memcpy(rp.data(), row_ptr, sizeof(int32_t) * (n + 1));
+  if (rp[0] != 0 || rp[n] != nnz) {
+    set_error("row_ptr[0] must be 0 and row_ptr[n] must equal nnz");
+    return PK_ERR_ARG;
+  }
+  pk_csr_stats st{};
+  st.row_min = n ? INT32_MAX : 0;
+  for (int64_t i = 0; i < n; ++i) {
+    const int32_t len = rp[i + 1] - rp[i];
+    if (len < 0) { set_error("row_ptr must be nondecreasing"); return PK_ERR_ARG; }
+    st.row_min = std::min(st.row_min, len);
+    st.row_max = std::max(st.row_max, len);
+  }
+  CsrPlan P;
+  build_plan(n, nnz, rp, sms, P);
+  st.n = n;
+  st.nnz = nnz;
+  st.row_mean = n ? (double)nnz / (double)n : 0.0;
+  st.grid = P.grid;
+  st.block = kBlock;
+  st.kernel = P.tma_ok ? 2 : 0;
+  st.values_fp32_exact = -1;  // no values here
+  st.tiles_thread = P.tiles_thread;
+  st.tiles_long = P.tiles_long;
+  st.tiles_group = P.tiles_group;
+  row_histogram(n, rp, st.row_hist);
+  *out = st;
   return PK_OK;
 }
 

@@ -79,6 +79,7 @@ EXPORTS = {
                                    C.c_void_p, C.c_void_p]),
     "pk_batched_last_config": (C.c_int, [C.POINTER(C.c_int32), C.POINTER(C.c_int32)]),
     "pk_batched_last_lanes": (C.c_int, [C.POINTER(C.c_int32)]),
+    "pk_csr_plan": (C.c_int, [C.c_int64, C.c_int64, C.c_void_p, C.c_int32, C.POINTER(Stats)]),
     "pk_residual_norm2": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p]),
     "pk_conv3d_fwd": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_int32, C.c_int32,
                                 C.c_int32, C.c_int32, C.c_int32, C.c_void_p, C.c_void_p]),
@@ -287,6 +288,18 @@ def batched_solve(As, bs, xs, stream=None, **kw) -> list:
     st = lib().pk_batched_solve(nsys, ha, hb, hx, C.byref(o), infos, _stream_ptr(stream))
     _check(st, "pk_batched_solve", _SOLVER_OK)
     return [info_dict(infos[k]) for k in range(nsys)]
+
+
+def csr_plan(row_ptr, sms=152) -> dict:
+    """pk_csr_plan: the statistics and tile schedule pk_csr_create would choose, computed on
+    the host (no GPU needed)."""
+    rp = np.ascontiguousarray(row_ptr, dtype=np.int32)
+    s = Stats()
+    _check(lib().pk_csr_plan(len(rp) - 1, int(rp[-1]) if len(rp) else 0, _ptr(rp), int(sms), C.byref(s)),
+           "pk_csr_plan")
+    d = {k: getattr(s, k) for k, _ in Stats._fields_}
+    d["row_hist"] = list(d["row_hist"])
+    return d
 
 
 def batched_last_lanes() -> int:
