@@ -510,7 +510,7 @@ pk_status bicgstab_solve(pk_csr* A, const double* b, double* x, const pk_opts* o
       }
     };
     if (!tma) {
-      set_error("pipelined BiCGStab needs the tile engine (rows longer than 4096 nonzeros are not supported)");
+      set_error("pipelined BiCGStab needs the tile engine (PK_FLAG_NO_TMA: only the classical form has thread-per-row kernels)");
       return PK_ERR_ARG;
     }
   } else {

@@ -676,7 +676,7 @@ pk_status gmres_solve(pk_csr* A, const double* b, double* x, const pk_opts* o, p
   if (o->precond != PK_PRECOND_NONE && o->precond != PK_PRECOND_JACOBI) { set_error("bad precond"); return PK_ERR_ARG; }
   if (o->flags & PK_FLAG_SELL) { set_error("PK_FLAG_SELL applies to pipelined FP64 CG"); return PK_ERR_ARG; }
   const bool cgs2 = (o->flags & PK_FLAG_CGS2) != 0;
-  if (!A->tma_ok) { set_error("GMRES needs the tile engine (rows longer than 4096 nonzeros are not supported)"); return PK_ERR_ARG; }
+  if (!A->tma_ok) { set_error("GMRES needs the tile engine"); return PK_ERR_ARG; }
   if ((e = gm_setup())) return e;
   const int n = A->n;
   const int ld = ((n + 31) & ~31) + 32;
