@@ -1,0 +1,42 @@
+"""The algorithmic byte counts behind bench.py's rooflines (CPU only), rebuilt here from the
+arrays each kernel reads and writes: CSR values (8 B) and column indices (4 B) per nonzero,
+row pointers (4 B per row + 1), and 8 B per FP64 vector element."""
+import sys
+from pathlib import Path
+
+import pytest
+
+sys.path.insert(0, str(Path(__file__).resolve().parents[1]))
+import bench  # noqa: E402
+
+from paper_1410_4054_gb300 import workloads as W  # noqa: E402
+
+
+def csr(n, nnz):
+    return 8 * nnz + 4 * nnz + 4 * (n + 1)
+
+
+@pytest.mark.parametrize("n,nnz", [(4_096_000, 28_518_400), (2_097_152, 14_581_760), (1, 1)])
+def test_cg_kernel_bytes(n, nnz):
+    vec = 8 * n
+    # K-CG-S: the matrix, p gathered once, Ap written
+    assert bench.spmv_dots_bytes(n, nnz) == csr(n, nnz) + vec + vec
+    # K-CG-U: read x, r, p, Ap; write x, r, p
+    assert bench.update_bytes(n) == 4 * vec + 3 * vec
+    # one iteration = one K-CG-U + one K-CG-S = 12 nnz + 76 n + 4
+    per_it = bench.bytes_per_solve(n, nnz, 11) - bench.bytes_per_solve(n, nnz, 10)
+    assert per_it == bench.spmv_dots_bytes(n, nnz) + bench.update_bytes(n) == 12 * nnz + 76 * n + 4
+    # setup: r0 = b - A x0 (matrix, read b, x; write r, p) and the first K-CG-S
+    assert bench.bytes_per_solve(n, nnz, 0) == csr(n, nnz) + 4 * vec
+
+
+def test_headline_workload_bytes():
+    a = W.laplace_3d(160)
+    assert (a.n, a.nnz) == (4_096_000, 28_518_400)
+    assert bench.spmv_dots_bytes(a.n, a.nnz) == 424_140_804
+    assert bench.bytes_per_solve(a.n, a.nnz, 1) - bench.bytes_per_solve(a.n, a.nnz, 0) == 653_516_804
+
+
+def test_job_value_sums_replicas():
+    assert bench.job_value(1, 5e9, 1.0) == pytest.approx(5.0)
+    assert bench.job_value(4, 5e9, 2.0) == pytest.approx(10.0)
