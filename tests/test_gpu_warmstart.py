@@ -187,10 +187,11 @@ def test_adam_matches_oracle():
 
 def test_transient_learned_warm_start():
     """Steps 1-150 train the network on the solver's own solutions; steps 151-300 are solved
-    again from the learned guess with the residual judge.  Every solve reaches the same
-    tolerance.  Whether the network gains is an empirical result, printed here; the test
-    asserts that training lowers the loss, that the judge never starts from a guess with a
-    larger residual than x_{t-1}, and that the learned guess costs no iterations on average."""
+    again from the learned guess, kept only where its residual is not larger than that of
+    x_{t-1}.  Every solve reaches the same tolerance.  Whether the network gains is an
+    empirical result, printed here; the test asserts that training lowers the loss, that no
+    solve starts from a guess with a larger residual than x_{t-1}, and that the learned guess
+    costs no iterations on average."""
     res = WS.run_transient(k=64, steps=300, train_last=150, epochs=30)
     print({k: v for k, v in res.items() if not isinstance(v, list)})
     assert len(res["learned_iters_eval"]) == 150
