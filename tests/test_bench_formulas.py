@@ -40,3 +40,12 @@ def test_headline_workload_bytes():
 def test_job_value_sums_replicas():
     assert bench.job_value(1, 5e9, 1.0) == pytest.approx(5.0)
     assert bench.job_value(4, 5e9, 2.0) == pytest.approx(10.0)
+
+
+def test_working_set_and_l2_label():
+    a = W.laplace_3d(160)
+    assert bench.working_set_bytes(a.n, a.nnz) == 12 * a.nnz + 4 * (a.n + 1) + 5 * 8 * a.n
+    assert bench.config(160, a)["l2"].startswith("inputs larger than L2 (working set ~522 MB")
+    small = W.laplace_3d(64)
+    assert bench.working_set_bytes(small.n, small.nnz) <= bench.L2_BYTES
+    assert bench.config(64, small)["l2"].startswith("working set ~33 MB <= 129 MB L2")
