@@ -1,6 +1,9 @@
-"""The algorithmic byte counts behind bench.py's rooflines (CPU only), rebuilt here from the
-arrays each kernel reads and writes: CSR values (8 B) and column indices (4 B) per nonzero,
-row pointers (4 B per row + 1), and 8 B per FP64 vector element."""
+"""bench.py host logic (CPU only).
+
+The algorithmic byte counts behind its rooflines are rebuilt here from the arrays each kernel
+reads and writes: CSR values (8 B) and column indices (4 B) per nonzero, row pointers (4 B per
+row + 1), and 8 B per FP64 vector element.  Also the working-set label and the summary of the
+clock samples taken during the timed region."""
 import sys
 from pathlib import Path
 
@@ -49,3 +52,31 @@ def test_working_set_and_l2_label():
     small = W.laplace_3d(64)
     assert bench.working_set_bytes(small.n, small.nnz) <= bench.L2_BYTES
     assert bench.config(64, small)["l2"].startswith("working set ~33 MB <= 129 MB L2")
+
+
+class _DoneProc:
+    def terminate(self):
+        pass
+
+    def wait(self, timeout=None):
+        return 0
+
+
+def test_clock_samples_are_summarised(tmp_path):
+    """The nvidia-smi sampler's CSV (sm, max sm, active mask, four throttle reasons) becomes
+    the median SM clock, the max clock and the set of throttle reasons seen."""
+    csv = tmp_path / "clocks.csv"
+    csv.write_text("2070, 2070, 0x0, Not Active, Not Active, Not Active, Not Active\n"
+                   "1980, 2070, 0x4, Not Active, Not Active, Not Active, Active\n"
+                   "2070, 2070, 0x0, Not Active, Not Active, Not Active, Not Active\n"
+                   "[N/A], 2070, 0x0, Not Active, Not Active, Not Active, Not Active\n"
+                   "truncated line\n")
+    c = bench.Clocks(0)
+    c.proc, c.path = _DoneProc(), str(csv)
+    out = c.stop()
+    assert out == {"sm_mhz": 2070.0, "sm_max_mhz": 2070.0, "reasons": ["sw_power_cap"], "samples": 3}
+    assert not csv.exists()
+
+
+def test_clock_sampler_absent_gives_none():
+    assert bench.Clocks(0).stop() is None
