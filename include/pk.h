@@ -20,8 +20,9 @@
  *   - Stopping rule: ||r||_2 <= tol * ||b||_2.  b = 0 returns x = 0 after 0 iterations.
  *     tol = 0 runs exactly maxit iterations (fixed-iteration timing, Sec. 4).
  *   - Errors are returned as pk_status values, never by aborting.  Reaching maxit returns
- *     PK_NOT_CONVERGED with x valid.  pk_last_error() gives a message for the last failure
- *     on the calling thread.
+ *     PK_NOT_CONVERGED with x valid.  A host allocation that fails inside the library (the
+ *     CSR analysis, the SELL-C-sigma and FP32 copies, the batch tables) returns PK_ERR_OOM.
+ *     pk_last_error() gives a message for the last failure on the calling thread.
  *   - The library uses one GPU: the device current on the calling thread.
  *   - A pk_csr handle carries its solves' work memory, cached graphs and state, and (during a
  *     right-Jacobi BiCGStab / GMRES solve) points its values at the scaled copy: calls on one

@@ -19,6 +19,7 @@
 #include <mutex>
 #include <vector>
 
+#include "pk_guard.cuh"
 #include "pk_internal.cuh"
 
 namespace pk {
@@ -409,6 +410,8 @@ static pk_status run_batch(BatchSys* dsys, int* dqueue, int nsys, int block, int
   return PK_OK;
 }
 
+pk_status ensure_fp32_values(pk_csr* A, cudaStream_t s);  // pk_mixed.cu
+
 pk_status batched_solve(int32_t nsys, pk_csr* const* A, const double* const* b, double* const* x,
                         const pk_opts* o, pk_info* infos, cudaStream_t s) {
   if (nsys < 0 || (nsys > 0 && (!A || !b || !x)) || !o) { set_error("bad batched arguments"); return PK_ERR_ARG; }
@@ -436,14 +439,7 @@ pk_status batched_solve(int32_t nsys, pk_csr* const* A, const double* const* b, 
     if (M->n > 0) {
       if ((e = work_vec(M, 0, &S.r)) || (e = work_vec(M, 1, &S.p)) || (e = work_vec(M, 2, &S.ap))) return e;
       if (mixed) {
-        if (!M->va32) {
-          PK_CUDA(cudaMalloc(&M->va32, sizeof(float) * ((size_t)M->nnz + 64)));
-          std::vector<double> hv(M->nnz);
-          std::vector<float> hf(M->nnz);
-          PK_CUDA(cudaMemcpy(hv.data(), M->va, sizeof(double) * M->nnz, cudaMemcpyDeviceToHost));
-          for (int j = 0; j < M->nnz; ++j) hf[j] = (float)hv[j];
-          PK_CUDA(cudaMemcpy(M->va32, hf.data(), sizeof(float) * M->nnz, cudaMemcpyHostToDevice));
-        }
+        if ((e = ensure_fp32_values(M, s))) return e;
         S.va32 = M->va32;
         // FP32 vectors live in the FP64 work slots 3..6 (each holds 2n floats)
         double *w3, *w4, *w5, *w6;
@@ -573,7 +569,7 @@ pk_status batched_solve(int32_t nsys, pk_csr* const* A, const double* const* b, 
 extern "C" pk_status pk_batched_solve(int32_t nsys, pk_csr* const* A, const double* const* b,
                                       double* const* x, const pk_opts* opts, pk_info* infos,
                                       void* stream) {
-  return pk::batched_solve(nsys, A, b, x, opts, infos, (cudaStream_t)stream);
+  return pk::guarded([&] { return pk::batched_solve(nsys, A, b, x, opts, infos, (cudaStream_t)stream); });
 }
 
 extern "C" pk_status pk_batched_last_config(int32_t* block, int32_t* blocks_per_sm) {

@@ -14,6 +14,7 @@
 #include <algorithm>
 #include <cmath>
 
+#include "pk_guard.cuh"
 #include "pk_tile.cuh"
 
 namespace pk {
@@ -562,5 +563,5 @@ pk_status bicgstab_solve(pk_csr* A, const double* b, double* x, const pk_opts* o
 
 extern "C" pk_status pk_bicgstab_solve(pk_csr* A, const double* b, double* x, const pk_opts* opts,
                                        pk_info* info, void* stream) {
-  return pk::bicgstab_solve(A, b, x, opts, info, (cudaStream_t)stream);
+  return pk::guarded([&] { return pk::bicgstab_solve(A, b, x, opts, info, (cudaStream_t)stream); });
 }

@@ -8,6 +8,7 @@
 #include <cstring>
 #include <vector>
 
+#include "pk_guard.cuh"
 #include "pk_tile.cuh"
 
 namespace pk {
@@ -15,6 +16,14 @@ namespace pk {
 static thread_local std::string g_last_error;
 
 void set_error(const std::string& msg) { g_last_error = msg; }
+
+pk_status host_failure(bool oom) noexcept {
+  try {
+    g_last_error = oom ? "host memory allocation failed" : "unexpected host-side exception";
+  } catch (...) {  // no memory even for the message: keep the previous one
+  }
+  return oom ? PK_ERR_OOM : PK_ERR_ARG;
+}
 
 pk_status cuda_fail(cudaError_t e, const char* what) {
   set_error(std::string(what) + ": " + cudaGetErrorString(e));
@@ -469,10 +478,8 @@ const char* pk_last_error(void) { return g_last_error.c_str(); }
 
 int32_t pk_version(void) { return 100; }
 
-pk_status pk_csr_create(int64_t n, int64_t nnz, const int32_t* row_ptr, const int32_t* col_idx,
-                        const double* vals, int32_t on_device, void* stream, pk_csr** out) {
-  if (!out) { set_error("out is NULL"); return PK_ERR_ARG; }
-  *out = nullptr;
+static pk_status csr_create(int64_t n, int64_t nnz, const int32_t* row_ptr, const int32_t* col_idx,
+                            const double* vals, int32_t on_device, void* stream, pk_csr** out) {
   if (n < 0 || nnz < 0 || n >= (int64_t(1) << 31) - 64 || nnz >= (int64_t(1) << 31)) {
     set_error("n and nnz must be in [0, 2^31)");
     return PK_ERR_ARG;
@@ -519,14 +526,16 @@ pk_status pk_csr_create(int64_t n, int64_t nnz, const int32_t* row_ptr, const in
     if ((double)(float)va[j] != va[j]) fp32_exact = 0;
   }
 
+  // every host allocation happens before the handle exists, so a failed one leaks nothing
+  int device = 0, sms = 148;
+  cudaGetDevice(&device);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, device);
+  CsrPlan P;
+  build_plan(n, nnz, rp, sms, P);
   pk_csr* A = new pk_csr();
   A->n = (int32_t)n;
   A->nnz = (int32_t)nnz;
-  cudaGetDevice(&A->device);
-  int sms = 148;
-  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, A->device);
-  CsrPlan P;
-  build_plan(n, nnz, rp, sms, P);
+  A->device = device;
   A->grid = P.grid;
   A->grid_tma = P.grid_tma;
   A->grid_stream = P.grid_stream;
@@ -599,6 +608,13 @@ pk_status pk_csr_create(int64_t n, int64_t nnz, const int32_t* row_ptr, const in
   return PK_OK;
 }
 
+pk_status pk_csr_create(int64_t n, int64_t nnz, const int32_t* row_ptr, const int32_t* col_idx,
+                        const double* vals, int32_t on_device, void* stream, pk_csr** out) {
+  if (!out) { set_error("out is NULL"); return PK_ERR_ARG; }
+  *out = nullptr;
+  return guarded([&] { return csr_create(n, nnz, row_ptr, col_idx, vals, on_device, stream, out); });
+}
+
 pk_status pk_csr_destroy(pk_csr* A) {
   if (!A) return PK_OK;
   cudaDeviceSynchronize();
@@ -635,12 +651,7 @@ pk_status pk_csr_destroy(pk_csr* A) {
   return PK_OK;
 }
 
-pk_status pk_csr_plan(int64_t n, int64_t nnz, const int32_t* row_ptr, int32_t sms, pk_csr_stats* out) {
-  if (!out || n < 0 || nnz < 0 || n >= (int64_t(1) << 31) - 64 || nnz >= (int64_t(1) << 31) || sms < 1 ||
-      (n > 0 && !row_ptr)) {
-    set_error("pk_csr_plan: bad arguments");
-    return PK_ERR_ARG;
-  }
+static pk_status csr_plan(int64_t n, int64_t nnz, const int32_t* row_ptr, int32_t sms, pk_csr_stats* out) {
   std::vector<int32_t> rp(n + 1, 0);
   if (n > 0) memcpy(rp.data(), row_ptr, sizeof(int32_t) * (n + 1));
   if (rp[0] != 0 || rp[n] != nnz) {
@@ -670,6 +681,15 @@ pk_status pk_csr_plan(int64_t n, int64_t nnz, const int32_t* row_ptr, int32_t sm
   row_histogram(n, rp, st.row_hist);
   *out = st;
   return PK_OK;
+}
+
+pk_status pk_csr_plan(int64_t n, int64_t nnz, const int32_t* row_ptr, int32_t sms, pk_csr_stats* out) {
+  if (!out || n < 0 || nnz < 0 || n >= (int64_t(1) << 31) - 64 || nnz >= (int64_t(1) << 31) || sms < 1 ||
+      (n > 0 && !row_ptr)) {
+    set_error("pk_csr_plan: bad arguments");
+    return PK_ERR_ARG;
+  }
+  return guarded([&] { return csr_plan(n, nnz, row_ptr, sms, out); });
 }
 
 pk_status pk_csr_stats_get(const pk_csr* A, pk_csr_stats* out) {

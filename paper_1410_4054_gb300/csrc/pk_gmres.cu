@@ -22,6 +22,7 @@
 #include <algorithm>
 #include <cmath>
 
+#include "pk_guard.cuh"
 #include "pk_tile.cuh"
 
 namespace pk {
@@ -836,5 +837,5 @@ pk_status gmres_solve(pk_csr* A, const double* b, double* x, const pk_opts* o, p
 
 extern "C" pk_status pk_gmres_solve(pk_csr* A, const double* b, double* x, const pk_opts* opts,
                                     pk_info* info, void* stream) {
-  return pk::gmres_solve(A, b, x, opts, info, (cudaStream_t)stream);
+  return pk::guarded([&] { return pk::gmres_solve(A, b, x, opts, info, (cudaStream_t)stream); });
 }

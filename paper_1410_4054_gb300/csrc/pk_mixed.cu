@@ -13,6 +13,7 @@
 #include <cmath>
 #include <vector>
 
+#include "pk_guard.cuh"
 #include "pk_tile.cuh"
 
 namespace pk {
@@ -349,16 +350,29 @@ __global__ void k_mx_init(DevState* st) {
   st->gm_phase = 0;
 }
 
+// FP32 copy of A's values for the mixed-precision kernels (single and batched), made once per
+// handle.  A->va32 is set only once the copy is complete: a failed attempt leaves nothing
+// half-made for the next solve to pick up.
 pk_status ensure_fp32_values(pk_csr* A, cudaStream_t s) {
   if (A->va32 || A->nnz == 0) return PK_OK;
-  PK_CUDA(cudaMalloc(&A->va32, sizeof(float) * ((size_t)A->nnz + 64)));
-  std::vector<double> hv(A->nnz);
-  std::vector<float> hf(A->nnz);
-  PK_CUDA(cudaMemcpyAsync(hv.data(), A->va, sizeof(double) * A->nnz, cudaMemcpyDeviceToHost, s));
-  PK_CUDA(cudaStreamSynchronize(s));
-  for (int j = 0; j < A->nnz; ++j) hf[j] = (float)hv[j];
-  PK_CUDA(cudaMemcpyAsync(A->va32, hf.data(), sizeof(float) * A->nnz, cudaMemcpyHostToDevice, s));
-  PK_CUDA(cudaStreamSynchronize(s));
+  float* d = nullptr;
+  const pk_status e = guarded([&]() -> pk_status {
+    std::vector<double> hv(A->nnz);
+    std::vector<float> hf(A->nnz);
+    PK_CUDA(cudaMalloc(&d, sizeof(float) * ((size_t)A->nnz + 64)));
+    PK_CUDA(cudaMemsetAsync(d + A->nnz, 0, sizeof(float) * 64, s));
+    PK_CUDA(cudaMemcpyAsync(hv.data(), A->va, sizeof(double) * A->nnz, cudaMemcpyDeviceToHost, s));
+    PK_CUDA(cudaStreamSynchronize(s));
+    for (int j = 0; j < A->nnz; ++j) hf[j] = (float)hv[j];
+    PK_CUDA(cudaMemcpyAsync(d, hf.data(), sizeof(float) * A->nnz, cudaMemcpyHostToDevice, s));
+    PK_CUDA(cudaStreamSynchronize(s));
+    return PK_OK;
+  });
+  if (e) {
+    if (d) cudaFree(d);
+    return e;
+  }
+  A->va32 = d;
   return PK_OK;
 }
 
