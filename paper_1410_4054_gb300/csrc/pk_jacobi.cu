@@ -57,9 +57,10 @@ int grid_for(int64_t items) {
 
 pk_status build_cache(pk_csr* A, cudaStream_t s) {
   const size_t nv = (size_t)A->n + 64, nz = (size_t)A->nnz + 64;
-  PK_CUDA(cudaMalloc(&A->jac_va, sizeof(double) * nz));
-  PK_CUDA(cudaMalloc(&A->jac_d, sizeof(double) * nv));
-  PK_CUDA(cudaMalloc(&A->jac_dinv, sizeof(double) * nv));
+  // a retry after a failed allocation reuses what the earlier attempt got
+  if (!A->jac_va) PK_CUDA(cudaMalloc(&A->jac_va, sizeof(double) * nz));
+  if (!A->jac_d) PK_CUDA(cudaMalloc(&A->jac_d, sizeof(double) * nv));
+  if (!A->jac_dinv) PK_CUDA(cudaMalloc(&A->jac_dinv, sizeof(double) * nv));
   PK_CUDA(cudaMemsetAsync(A->jac_va, 0, sizeof(double) * nz, s));
   int* bad = reinterpret_cast<int*>(A->small + 8100);
   PK_CUDA(cudaMemsetAsync(bad, 0, sizeof(int), s));

@@ -428,8 +428,8 @@ pk_status cg_mixed(pk_csr* A, const double* b, double* x, const pk_opts* o, pk_i
     k_mx_prep<<<Ge, kBlock, 0, cs>>>(a);
     if (t) t->end();
   };
-  // the tile engines need rows of at most 4096 nonzeros and FP32 vectors on 16-byte
-  // boundaries (the work vectors are); PK_FLAG_NO_TMA selects the row kernels
+  // the tile engines need FP32 vectors on 16-byte boundaries (the work vectors are);
+  // PK_FLAG_NO_TMA selects the thread-per-row kernels
   const bool tma = A->tma_ok && !(o->flags & PK_FLAG_NO_TMA);
   if (tma && (e = mx_tma_setup())) return e;
   const CsrTilesT<float> ct = csr_tiles32_of(A);

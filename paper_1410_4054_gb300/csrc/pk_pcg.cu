@@ -209,7 +209,7 @@ pk_status pcg_jacobi_solve(pk_csr* A, const double* b, double* x, const pk_opts*
     return PK_ERR_ARG;
   }
   if (!A->tma_ok || (o->flags & PK_FLAG_NO_TMA)) {
-    set_error("PK_PRECOND_JACOBI needs the tile engine (rows of at most 4096 nonzeros)");
+    set_error("PK_PRECOND_JACOBI needs the tile engine (PK_FLAG_NO_TMA is not supported)");
     return PK_ERR_ARG;
   }
   pk_status e;
