@@ -80,3 +80,21 @@ def test_clock_samples_are_summarised(tmp_path):
 
 def test_clock_sampler_absent_gives_none():
     assert bench.Clocks(0).stop() is None
+
+
+def test_traffic_counters_are_reported_only_for_the_profiled_source(monkeypatch):
+    """The roofline's DRAM traffic comes from a committed ncu capture and is dropped as soon
+    as the kernel sources differ from the ones that capture ran."""
+    t = bench.ncu_traffic("k_cg_spmv_dots", "lap3d_160")
+    assert t is not None and 0.5 * 424_140_804 < t < 1.5 * 424_140_804
+    assert bench.ncu_traffic("k_cg_spmv_dots", "lap3d_999") is None
+    monkeypatch.setattr(bench, "kernel_source_sha", lambda: "0" * 16)
+    assert bench.ncu_traffic("k_cg_spmv_dots", "lap3d_160") is None
+
+
+def test_peak_comes_from_the_measured_file():
+    peak, kind = bench.measured_peaks()
+    if (Path(bench.ROOT) / "MEASURED_PEAKS.json").exists():
+        assert kind == "measured" and 5000 < peak < 8000
+    else:  # pragma: no cover
+        assert (peak, kind) == (6800.0, "fallback")
