@@ -42,7 +42,7 @@ typedef enum {
   PK_OK = 0,
   PK_ERR_ARG = 1,        /* invalid argument (bad CSR, NULL pointer, size limits) */
   PK_ERR_CUDA = 2,       /* a CUDA runtime call failed; see pk_last_error() */
-  PK_ERR_OOM = 3,        /* device allocation failed */
+  PK_ERR_OOM = 3,        /* a device or host allocation failed */
   PK_NOT_CONVERGED = 4,  /* maxit reached; x holds the last iterate */
   PK_BREAKDOWN = 5,      /* BiCGStab / GMRES breakdown (zero denominator, no progress) */
   PK_NOT_SPD = 6,        /* CG found <p, Ap> <= 0 */
@@ -93,9 +93,9 @@ enum {
 #define PK_FLAG_TRUE_RES 2u  /* compute ||b - A x|| / ||b|| at exit into pk_info.rel_res_true */
 #define PK_FLAG_NO_TMA 4u    /* use the thread-per-row kernels instead of the warp-specialised
                                 bulk-copy tile kernels (for comparison) */
-#define PK_FLAG_AUTOTUNE 8u  /* pk_batched_solve: time every (block size, blocks per SM)
-                                candidate on the batch first and keep the fastest (cached per
-                                batch shape for the process) */
+#define PK_FLAG_AUTOTUNE 8u  /* pk_batched_solve: time every (block size, blocks per SM,
+                                lanes per row) candidate on the batch first and keep the
+                                fastest (cached per batch shape for the process) */
 #define PK_FLAG_SELL 16u     /* pipelined FP64 CG: the fused SpMV kernel (Ap, <Ap,Ap>, <p,Ap>, alpha,
                                 beta) reads a SELL-C-sigma copy of A (C = 32, sigma = 1024; built on
                                 first use, kept with the handle) instead of the CSR tiles.  Other
