@@ -190,9 +190,11 @@ typedef struct {
   int32_t block;             /* threads per block */
   int32_t kernel;            /* SpMV engine: 0 thread-per-row loads, 2 warp-specialised bulk-copy tiles */
   int32_t values_fp32_exact; /* 1 if every value is exactly representable in float32 */
-  /* bulk-copy tiles by row schedule: every row one thread (rows short enough for one thread
-   * to walk), short rows one thread and long rows a whole warp each (rows of very different
-   * lengths), or rows of similar length G = 2..16 lanes each (tiles_group) */
+  /* bulk-copy tiles by row schedule: every row one thread (tiles_thread: rows short enough
+   * for one thread to walk); short rows one thread and long rows a whole warp each
+   * (tiles_long: rows of very different lengths); rows of similar length G = 2..16 lanes each
+   * (tiles_group).  The chunk tiles of a row longer than a tile (4096 nonzeros), summed by
+   * the whole block, count in tiles_long too: ceil(length / 4096) per such row */
   int32_t tiles_thread, tiles_long;
   int32_t tiles_group;
   /* row-length histogram: rows with 0-8, 9-16, 17-32, 33-64, 65-256, 257-4096 and more than
