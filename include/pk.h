@@ -284,7 +284,9 @@ pk_status pk_gmres_solve(pk_csr* A, const double* b, double* x, const pk_opts* o
  * leaves the queue (per-system convergence mask).  A[k], b[k], x[k] for k < nsys; b and x
  * must be DEVICE pointers.  opts: tol, maxit (per system; MIXED: total inner iterations),
  * precision PK_PREC_FP64 or PK_PREC_MIXED (FP32 SpMV/vectors inside FP64 iterative
- * refinement, inner tolerance 1e-4, at most 20 refinement steps), flags PK_FLAG_AUTOTUNE.
+ * refinement, inner tolerance 1e-4, at most 20 refinement steps), lanes (per matrix row),
+ * flags PK_FLAG_AUTOTUNE.  PK_FLAG_SELL, PK_FLAG_CGS2 and a preconditioner return
+ * PK_ERR_ARG; variant, loop and the other flags are ignored (always pipelined CG).
  * infos: nsys entries or NULL (iters, status, cycles = refinement steps, rel_res_est).
  * Returns PK_OK if every system converged, else the first failing system's status.
  */
@@ -327,7 +329,8 @@ pk_status pk_residual_norm2(pk_csr* A, const double* b, const double* x, double*
 /*
  * Learned initial guess for transient problems (an extension; the paper has no counterpart): a 4-layer 3x3x3
  * convolutional network on a D x H x W grid, BF16 operands with FP32 accumulation on the
- * tensor cores (m16n8k16 MMA, implicit GEMM).  Activations are channels-last BF16
+ * tensor cores as implicit GEMMs (tcgen05 for the forward and backward-data passes, the
+ * warp-level m16n8k16 MMA for the weight gradient).  Activations are channels-last BF16
  * [D][H][W][16] with channel counts padded to 16 (padded channels are zero); weights are BF16
  * [27][16 co][16 ci], tap = 9(dz+1) + 3(dy+1) + (dx+1); zero padding 1 at the boundary.
  * All pointers are device pointers; calls are stream-ordered and return at once.
