@@ -10,8 +10,7 @@
  *   - Matrices are CSR with int32 row pointers / column indices and float64 values
  *     (Sec. 2.2).  pk_csr_create COPIES the matrix into library-owned device memory; the
  *     caller keeps ownership of its arrays.  Solver work vectors are allocated on first use
- *     (cudaMallocAsync on the given stream) and cached in the pk_csr handle until
- *     pk_csr_destroy.
+ *     (cudaMalloc) and cached in the pk_csr handle until pk_csr_destroy.
  *   - Vectors b (input) and x (in: initial guess x0, out: solution) are caller-owned,
  *     float64, length n.  They may be device pointers (no copies) or host pointers (the
  *     library copies them in and out inside the call; used for end-to-end timing).
