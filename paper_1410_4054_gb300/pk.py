@@ -1,7 +1,8 @@
 """Thin ctypes binding of the pk C ABI (include/pk.h): argument marshalling only.
 
 Every numerical step runs in the CUDA library ``_build/libpk.so``; there is no CPU fallback.
-If the library cannot be loaded the import-time call ``lib()`` raises.  Vectors may be torch
+``lib()`` loads it on first use (building it first if it is missing or stale); if it cannot
+be built or loaded, that call and every call through it raise.  Vectors may be torch
 CUDA tensors (passed by device pointer, on the current torch stream unless ``stream`` is
 given) or numpy arrays / torch CPU tensors (host pointers: the library copies them in and out
 inside the call).
