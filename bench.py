@@ -264,6 +264,10 @@ def job_value(ws: int, bytes_per_replica: float, seconds: float) -> float:
 
 # ------------------------------------------------------------------ CPU oracle arm
 
+def host_cores() -> int:
+    return len(os.sched_getaffinity(0))
+
+
 def oracle_sample(a, b, iters: int) -> tuple[float, float]:
     """Seconds for `iters` oracle pipelined-CG iterations (tol = 0) on the same system."""
     import oracle as O
@@ -273,32 +277,77 @@ def oracle_sample(a, b, iters: int) -> tuple[float, float]:
     return time.perf_counter() - t0, iters
 
 
+def oracle_omp_sample(a, b, iters: int):
+    """Seconds for `iters` pipelined-CG iterations of the OpenMP copy of the oracle on every
+    core this process may use (static schedule), or None without OpenMP."""
+    import oracle as O
+    if O.omp_lib() is None:
+        return None
+    t0 = time.perf_counter()
+    O.cg_omp(a, b, tol=0.0, maxit=iters, threads=host_cores())
+    return time.perf_counter() - t0
+
+
 def oracle_gbs(a, seconds: float, iters: int) -> float:
     per_iter = 56 * a.n + 12 * a.nnz + 4 * (a.n + 1) + 16 * a.n
     return per_iter * iters / seconds / 1e9
 
 
+def cpu_legs(a, b, k: int, it1: int, itp: int) -> dict:
+    """The CPU baseline: (i) the sequential parity oracle on one core, (ii) its OpenMP copy on
+    every core of the host (static schedule, cores from sched_getaffinity); the faster one is
+    reported, as the paper's Sec. 4 reports the best of 1/2/4/8 CPU processes."""
+    s1, _ = oracle_sample(a, b, it1)
+    legs = {"one_core": {"value": oracle_gbs(a, s1, it1), "cores": 1, "iters": it1, "s": s1}}
+    cores = host_cores()
+    sp = oracle_omp_sample(a, b, itp)
+    if sp is not None:
+        legs["all_cores"] = {"value": oracle_gbs(a, sp, itp), "cores": cores, "iters": itp, "s": sp}
+    best = max(legs.values(), key=lambda v: v["value"])
+    return {"value": best["value"], "unit": UNIT, "cores": best["cores"], "kind": "oracle",
+            "sample": f"pipelined-CG iterations (tol=0) of the same {k}^3 system: "
+                      + "; ".join(f"{v['iters']} its on {v['cores']} core(s) in {v['s']:.2f} s "
+                                  f"= {v['value']:.1f} GB/s" for v in legs.values())
+                      + "; faster leg reported",
+            "legs": {name: round(v["value"], 2) for name, v in legs.items()}}
+
+
 def run_reference(args):
+    """The oracle arm: each step runs a bounded sample of the same workload (12 pipelined-CG
+    iterations of the --k^3 system) on one core and on every core (OpenMP copy); the faster
+    leg's median step time is the value."""
     ws, rank, _ = dist()
     if rank != 0:
         return 0
+    import oracle as O
+
     a = W.laplace_3d(args.k)
     _, b, _ = W.manufactured(a, seed=0)
     it = 12
+    cores = host_cores()
+    have_omp = O.omp_lib() is not None
     for _ in range(args.warmup):
         oracle_sample(a, b, 2)
-    times = []
+        if have_omp:
+            oracle_omp_sample(a, b, 2)
+    t1, tp = [], []
     for _ in range(args.steps):
-        s, _ = oracle_sample(a, b, it)
-        times.append(s)
-    ms = 1e3 * statistics.median(times)
-    val = oracle_gbs(a, statistics.median(times), it)
+        t1.append(oracle_sample(a, b, it)[0])
+        if have_omp:
+            tp.append(oracle_omp_sample(a, b, it))
+    legs = {"one_core": (statistics.median(t1), 1)}
+    if tp:
+        legs["all_cores"] = (statistics.median(tp), cores)
+    name, (sec, used) = min(legs.items(), key=lambda kv: kv[1][0])
+    val = oracle_gbs(a, sec, it)
     line = {"metric": METRIC, "value": val, "unit": UNIT, "n_gpus": args.gpus, "steps": args.steps,
-            "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
+            "warmup": args.warmup, "ms_per_step": 1e3 * sec, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f64", "data": "synthetic", "impl": "reference",
             "config": config(args.k, a),
-            "cpu_baseline": {"value": val, "unit": UNIT, "cores": 1, "kind": "oracle",
-                             "sample": f"{it} pipelined-CG iterations of the {args.k}^3 system per step"},
+            "cpu_baseline": {"value": val, "unit": UNIT, "cores": used, "kind": "oracle",
+                             "sample": f"{it} pipelined-CG iterations of the {args.k}^3 system per step, "
+                                       f"on 1 core and on {cores} cores (OpenMP copy); {name} reported",
+                             "legs": {k: round(oracle_gbs(a, v[0], it), 2) for k, v in legs.items()}},
             "e2e": {"value": val, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
     return 0
@@ -390,74 +439,104 @@ def run_ours(args):
     ach = spmv_dots_bytes(a.n, a.nnz) / t_s / 1e9
     roofline = {"bound": "hbm", "achieved": ach, "peak": peak, "unit": "GB/s", "frac": ach / peak,
                 "traffic": ncu_traffic("k_cg_spmv_dots", workload_name(args.k)),
-                "kernel": "k_cg_spmv_dots (K-CG-S: SpMV + <Ap,Ap>, <p,Ap>, last-block alpha/beta)",
-                "peak_source": f"{peak_kind} (MEASURED_PEAKS.json hbm_gbs)" if peak_kind == "measured" else "fallback",
-                "algorithmic_bytes_per_launch": spmv_dots_bytes(a.n, a.nnz),
-                "launch_ms": 1e3 * t_s,
-                "fp64_flops_per_launch": 2 * a.nnz + 4 * a.n,
-                "fp64_tflops": (2 * a.nnz + 4 * a.n) / t_s / 1e12,
-                "other_kernels": {"k_cg_update": {"launch_ms": 1e3 * t_u,
-                                                  "gbs": update_bytes(a.n) / t_u / 1e9,
-                                                  "frac": update_bytes(a.n) / t_u / 1e9 / peak}}}
+                "kernel": "k_cg_spmv_dots_tma (K-CG-S)",
+                "peak_source": "of measured (MEASURED_PEAKS.json hbm_gbs)" if peak_kind == "measured"
+                               else "of fallback",
+                "algorithmic_bytes_per_launch": spmv_dots_bytes(a.n, a.nnz), "launch_ms": 1e3 * t_s}
+    update_roofline = {"kernel": "k_cg_update_tma (K-CG-U)", "launch_ms": 1e3 * t_u,
+                       "algorithmic_bytes_per_launch": update_bytes(a.n),
+                       "achieved": update_bytes(a.n) / t_u / 1e9, "peak": peak,
+                       "frac": update_bytes(a.n) / t_u / 1e9 / peak,
+                       "fp64_tflops_k_cg_s": (2 * a.nnz + 4 * a.n) / t_s / 1e12}
+    emit_detail("roofline_kernels", update_roofline)
 
-    sweep = []
     if not args.no_sweep:
-        cases = [("lap3d", k) for k in W.LAPLACE_3D_SWEEP] + [("lap2d", k) for k in W.LAPLACE_2D_SWEEP]
-        for kind, k in cases:
-            m = W.laplace_3d(k) if kind == "lap3d" else W.laplace_2d(k)
-            _, mb, _ = W.manufactured(m, seed=0)
-            M = pk.CSRMatrix.from_workload(m)
-            mbd = torch.from_numpy(mb).to(dev)
-            mx = torch.zeros(m.n, dtype=torch.float64, device=dev)
-            ws_b = working_set_bytes(m.n, m.nnz)
-            # below the L2 size, algorithmic GB/s may exceed HBM speed (L2 bandwidth)
-            row = {"matrix": f"{kind}_{k}", "n": m.n, "nnz": m.nnz, "working_set_mb": ws_b / 1e6,
-                   "below_l2_size": ws_b <= L2_BYTES}
-            for variant, loop in (("pipelined", "graph"), ("pipelined", "persistent"),
-                                  ("classical", "graph")):
-                key = variant if variant == "classical" else f"{variant}_{loop}"
-                best = None
-                try:
-                    for rep in range(2):
-                        mx.zero_()
-                        inf = pk.cg_solve(M, mbd, mx, tol=1e-8, maxit=50_000, variant=variant, loop=loop)
-                        best = inf if best is None or inf["solve_ms"] < best["solve_ms"] else best
-                except pk.PkError:  # the persistent grid does not fit this n
-                    row[f"{key}_iters"] = row[f"{key}_ms"] = None
-                    continue
-                row[f"{key}_iters"] = best["iters"]
-                row[f"{key}_ms"] = best["solve_ms"]
-            # what the default loop (PK_LOOP_AUTO) runs at this n
-            auto = ("persistent" if m.n <= pk.PERSISTENT_AUTO_N and m.nnz <= pk.PERSISTENT_AUTO_NNZ
-                    and row["pipelined_persistent_ms"]
-                    else "graph")
-            row["pipelined_loop"] = auto
-            row["pipelined_iters"] = row[f"pipelined_{auto}_iters"]
-            row["pipelined_ms"] = row[f"pipelined_{auto}_ms"]
-            row["pipelined_gbs"] = bytes_per_solve(m.n, m.nnz, row["pipelined_iters"]) / (row["pipelined_ms"] * 1e-3) / 1e9
-            row["speedup_vs_classical"] = row["classical_ms"] / row["pipelined_ms"]
-            sweep.append(row)
-            M.close()
+        for row in size_sweep(pk, torch, dev):
+            emit_detail("sweep", row)
 
-    forms = {} if args.no_forms else bench_forms(pk, torch, dev, args)
+    if not args.no_forms:
+        bench_forms(pk, torch, dev, args, emit=lambda name, val: emit_detail("form:" + name, val))
 
     cpu = None
     if not args.no_cpu:
-        s, it_cpu = oracle_sample(a, b, 60)
-        cpu = {"value": oracle_gbs(a, s, it_cpu), "unit": UNIT, "cores": 1, "kind": "oracle",
-               "sample": f"{it_cpu} pipelined-CG iterations (tol=0) of the same {args.k}^3 system, "
-                         f"{s:.1f} s, single-threaded FP64 C"}
+        cpu = cpu_legs(a, b, args.k, it1=60, itp=240)
 
-    line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
-            "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
-            "vs_baseline": None, "dtype": "f64", "data": "synthetic", "config": config(args.k, a),
-            "time_to_tol_ms": ms, "iters": it, "iters_per_s": it / (ms * 1e-3),
-            "gpu_launches": launches, "e2e": e2e, "roofline": roofline, "cpu_baseline": cpu,
-            "clocks": clk, "sweep": sweep, "forms": forms}
-    print(json.dumps(line), flush=True)
+    line = headline(value=value, ws=ws, args=args, ms=ms, cfg=config(args.k, a), it=it, launches=launches,
+                    e2e=e2e, roofline=roofline, cpu=cpu, clk=clk)
+    print(line, flush=True)
     if pg:
         pg.destroy_process_group()
     return 0
+
+
+HEADLINE_MAX = 2048
+
+
+def emit_detail(name: str, data) -> None:
+    """One JSON line per sweep row / form, printed BEFORE the headline (the last line)."""
+    print(json.dumps({"detail": name, "data": data}), flush=True)
+
+
+def headline(*, value, ws, args, ms, cfg, it, launches, e2e, roofline, cpu, clk) -> str:
+    """The benchmark's result line: printed last, one line, under HEADLINE_MAX bytes."""
+    r = lambda v, d=4: None if v is None else round(float(v), d)  # noqa: E731
+    line = {"metric": METRIC, "value": r(value, 2), "unit": UNIT, "n_gpus": ws, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": r(ms), "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64", "data": "synthetic", "config": cfg,
+            "time_to_tol_ms": r(ms), "iters": it, "iters_per_s": r(it / (ms * 1e-3), 1),
+            "gpu_launches": launches,
+            "e2e": {k: (r(v, 3) if isinstance(v, float) else v) for k, v in e2e.items()},
+            "roofline": {k: (r(v) if isinstance(v, float) else v) for k, v in roofline.items()},
+            "cpu_baseline": cpu, "clocks": clk}
+    if cpu is not None:
+        line["cpu_baseline"] = dict(cpu, value=r(cpu["value"], 3))
+    s = json.dumps(line)
+    if len(s) >= HEADLINE_MAX:
+        raise RuntimeError(f"bench.py: headline line is {len(s)} bytes (limit {HEADLINE_MAX})")
+    return s
+
+
+def size_sweep(pk, torch, dev):
+    """Pipelined CG to 1e-8 against the unfused classical CG on the same GPU, both from x0 = 0,
+    best of two solves, over the 3D k^3 and 2D k^2 Laplacians of the size sweep."""
+    sweep = []
+    cases = [("lap3d", k) for k in W.LAPLACE_3D_SWEEP] + [("lap2d", k) for k in W.LAPLACE_2D_SWEEP]
+    for kind, k in cases:
+        m = W.laplace_3d(k) if kind == "lap3d" else W.laplace_2d(k)
+        _, mb, _ = W.manufactured(m, seed=0)
+        M = pk.CSRMatrix.from_workload(m)
+        mbd = torch.from_numpy(mb).to(dev)
+        mx = torch.zeros(m.n, dtype=torch.float64, device=dev)
+        ws_b = working_set_bytes(m.n, m.nnz)
+        # below the L2 size, algorithmic GB/s may exceed HBM speed (L2 bandwidth)
+        row = {"matrix": f"{kind}_{k}", "n": m.n, "nnz": m.nnz, "working_set_mb": ws_b / 1e6,
+               "below_l2_size": ws_b <= L2_BYTES}
+        for variant, loop in (("pipelined", "graph"), ("pipelined", "persistent"),
+                              ("classical", "graph")):
+            key = variant if variant == "classical" else f"{variant}_{loop}"
+            best = None
+            try:
+                for rep in range(2):
+                    mx.zero_()
+                    inf = pk.cg_solve(M, mbd, mx, tol=1e-8, maxit=50_000, variant=variant, loop=loop)
+                    best = inf if best is None or inf["solve_ms"] < best["solve_ms"] else best
+            except pk.PkError:  # the persistent grid does not fit this n
+                row[f"{key}_iters"] = row[f"{key}_ms"] = None
+                continue
+            row[f"{key}_iters"] = best["iters"]
+            row[f"{key}_ms"] = best["solve_ms"]
+        # what the default loop (PK_LOOP_AUTO) runs at this n
+        auto = ("persistent" if m.n <= pk.PERSISTENT_AUTO_N and m.nnz <= pk.PERSISTENT_AUTO_NNZ
+                and row["pipelined_persistent_ms"]
+                else "graph")
+        row["pipelined_loop"] = auto
+        row["pipelined_iters"] = row[f"pipelined_{auto}_iters"]
+        row["pipelined_ms"] = row[f"pipelined_{auto}_ms"]
+        row["pipelined_gbs"] = bytes_per_solve(m.n, m.nnz, row["pipelined_iters"]) / (row["pipelined_ms"] * 1e-3) / 1e9
+        row["speedup_vs_classical"] = row["classical_ms"] / row["pipelined_ms"]
+        sweep.append(row)
+        M.close()
+    return sweep
 
 
 def _best(fn, reps=2):
@@ -469,7 +548,7 @@ def _best(fn, reps=2):
     return best
 
 
-def bench_forms(pk, torch, dev, args):
+def bench_forms(pk, torch, dev, args, emit=None):
     """The other solvers and forms, each timed after one warm-up run (device time of the call).
 
     bicgstab / gmres: 3D convection-diffusion 128^3 (cell Peclet 0.5), tol 1e-8, pipelined vs
@@ -484,8 +563,14 @@ def bench_forms(pk, torch, dev, args):
     learned_warm_start: the transient heat sequence on 64^3 (300 implicit steps, CG to 1e-8),
     the network trained on steps 2-150 and evaluated on 151-300 against the x_{t-1} warm start
     (and the linear extrapolation alone), plus the BF16 convolution kernels' throughput.
+    Each form is handed to `emit(name, value)` as soon as it is measured.
     """
     out = {}
+
+    def put(name, val):
+        out[name] = val
+        if emit:
+            emit(name, val)
     a = W.convdiff_3d(128)
     _, b, _ = W.manufactured(a, seed=0)
     A = pk.CSRMatrix.from_workload(a)
@@ -507,7 +592,7 @@ def bench_forms(pk, torch, dev, args):
         row["kernel_ms_30_fixed_iterations"] = prof["kernel_ms"]
         row["roofline"] = solver_rooflines(solver, a.n, a.nnz, prof["kernel_ms"])
         row["speedup_vs_classical"] = row["classical_ms"] / row["pipelined_ms"]
-        out[solver] = row
+        put(solver, row)
     A.close()
 
     mats = W.batched_rectangles(512, seed=0)
@@ -554,10 +639,10 @@ def bench_forms(pk, torch, dev, args):
     brow["sequential_plain_ms"] = 1e3 * seq
     brow["sequential_plain_solves_per_s"] = len(mats) / seq
     brow["speedup_fp64_batched_vs_sequential"] = brow["sequential_plain_ms"] / brow["fp64_ms"]
-    out["batched"] = brow
+    put("batched", brow)
     for M in As:
         M.close()
-    out["batched_fe"] = batched_fe(pk, torch, dev)
+    put("batched_fe", batched_fe(pk, torch, dev))
 
     a = W.laplace_3d(args.k)
     _, b, _ = W.manufactured(a, seed=0)
@@ -569,7 +654,7 @@ def bench_forms(pk, torch, dev, args):
     i64 = _best(lambda: pk.cg_solve(A, bd, x64.zero_(), tol=1e-8, maxit=50_000))
     im = _best(lambda: pk.cg_solve(A, bd, xm.zero_(), tol=1e-8, maxit=50_000, precision="mixed",
                                    flags=pk.FLAG_TRUE_RES))
-    out["mixed"] = {"matrix": f"lap3d_{args.k}", "tol": 1e-8, "fp64_ms": i64["solve_ms"],
+    mixed = {"matrix": f"lap3d_{args.k}", "tol": 1e-8, "fp64_ms": i64["solve_ms"],
                     "mixed_ms": im["solve_ms"], "speedup": i64["solve_ms"] / im["solve_ms"],
                     "refinement_steps": im["cycles"], "inner_iters": im["iters"],
                     "fp64_iters": i64["iters"], "mixed_rel_res_true": im["rel_res_true"],
@@ -577,18 +662,19 @@ def bench_forms(pk, torch, dev, args):
                     "inner_bytes_per_iter": 8 * a.nnz + 40 * a.n}
     mixed_bytes = im["iters"] * (8 * a.nnz + 40 * a.n) + (im["cycles"] + 1) * (12 * a.nnz + 4 * (a.n + 1) + 16 * a.n)
     gbs = mixed_bytes / (im["solve_ms"] * 1e-3) / 1e9
-    out["mixed"]["roofline"] = {"bound": "hbm", "achieved": gbs, "peak": measured_peaks()[0], "unit": "GB/s",
-                                "frac": gbs / measured_peaks()[0],
-                                "note": "inner FP32 iterations x (8 nnz + 40 n) + FP64 residuals, over the solve"}
+    mixed["roofline"] = {"bound": "hbm", "achieved": gbs, "peak": measured_peaks()[0], "unit": "GB/s",
+                         "frac": gbs / measured_peaks()[0],
+                         "note": "inner FP32 iterations x (8 nnz + 40 n) + FP64 residuals, over the solve"}
+    put("mixed", mixed)
     A.close()
 
-    out["jacobi_pcg"] = jacobi_pcg(pk, torch, dev, args.k)
-    out["jacobi_right"] = jacobi_right(pk, torch, dev)
-    out["gmres_cgs2"] = gmres_cgs2(pk, torch, dev)
-    out["fe_sweep"] = fe_sweep(pk, torch, dev)
-    out["sell"] = sell_compare(pk, torch, dev, args.k)
-    out["nonsymmetric_sweep"] = nonsymmetric_sweep(pk, torch, dev)
-    out["fused_spmv_dot"] = fused_spmv_dot(pk, torch, dev)
+    put("jacobi_pcg", jacobi_pcg(pk, torch, dev, args.k))
+    put("jacobi_right", jacobi_right(pk, torch, dev))
+    put("gmres_cgs2", gmres_cgs2(pk, torch, dev))
+    put("fe_sweep", fe_sweep(pk, torch, dev))
+    put("sell", sell_compare(pk, torch, dev, args.k))
+    put("nonsymmetric_sweep", nonsymmetric_sweep(pk, torch, dev))
+    put("fused_spmv_dot", fused_spmv_dot(pk, torch, dev))
 
     from paper_1410_4054_gb300 import warmstart as WS
 
@@ -602,7 +688,7 @@ def bench_forms(pk, torch, dev, args):
                               "peak_source": "measured (MEASURED_PEAKS.json bf16_tflops)",
                               **{f"{k}_frac": lw["conv"][f"{k}_tflops"] / bf16_peak
                                  for k in ("fwd", "bwd_data", "wgrad")}}
-    out["learned_warm_start"] = lw
+    put("learned_warm_start", lw)
     return out
 
 

@@ -180,3 +180,43 @@ def gmres(a, b, x0=None, tol=1e-8, maxit=1000, m=30, variant="pipelined", cap=No
     if V is not None:
         out["V"] = V   # first cycle's basis v_0 .. v_k (rows beyond k: NaN)
     return out
+
+
+_omp = None
+
+
+def omp_lib():
+    """The OpenMP timing copy of the pipelined CG oracle (libpk_oracle_omp.so), or None when
+    the compiler has no OpenMP.  Used only for the CPU baseline's multi-threaded leg."""
+    global _omp
+    if _omp is None:
+        try:
+            path = _build.build_omp()
+        except Exception:  # noqa: BLE001 - no OpenMP on this host: single-threaded leg only
+            return None
+        L = C.CDLL(str(path))
+        L.orc_omp_threads.argtypes = []
+        L.orc_omp_threads.restype = C.c_int32
+        L.orc_omp_set_threads.argtypes = [C.c_int32]
+        L.orc_omp_set_threads.restype = None
+        L.orc_cg_pipelined_omp.argtypes = [C.c_int32, _i32p, _i32p, _f64p, _f64p, _f64p, C.c_double,
+                                           C.c_int32, C.POINTER(C.c_int32)]
+        L.orc_cg_pipelined_omp.restype = C.c_int
+        _omp = L
+    return _omp
+
+
+def cg_omp(a, b, x0=None, tol=1e-8, maxit=1000, threads=None):
+    """Algorithm 2 with every row loop split statically over `threads` OpenMP threads (default:
+    the cores this process may run on).  Timing only: the parity oracle is cg()."""
+    L = omp_lib()
+    if L is None:
+        raise RuntimeError("the OpenMP oracle is not available (gcc without -fopenmp)")
+    n, rp, ci, va = _csr(a)
+    threads = threads or len(os.sched_getaffinity(0))
+    L.orc_omp_set_threads(int(threads))
+    b = np.ascontiguousarray(b, dtype=np.float64)
+    x = np.zeros(n) if x0 is None else np.array(x0, dtype=np.float64, copy=True)
+    it = C.c_int32(0)
+    st = L.orc_cg_pipelined_omp(n, rp, ci, va, b, x, tol, maxit, C.byref(it))
+    return dict(x=x, iters=it.value, status=st, threads=int(L.orc_omp_threads()))
