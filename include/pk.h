@@ -75,9 +75,19 @@ enum {
                         every CTA summing the block partials itself in a fixed order; for
                         n <= PK_PERSISTENT_MAX_N.  Larger n, other solvers, variants or
                         precisions return PK_ERR_ARG */
-  PK_LOOP_AUTO = 3   /* PK_LOOP_PERSISTENT for pipelined FP64 CG with n <= PK_PERSISTENT_AUTO_N
+  PK_LOOP_AUTO = 3,  /* PK_LOOP_PERSISTENT for pipelined FP64 CG with n <= PK_PERSISTENT_AUTO_N
                         and nnz <= PK_PERSISTENT_AUTO_NNZ (and no PK_FLAG_TIMING) when the
                         device can run it, PK_LOOP_GRAPH otherwise */
+  PK_LOOP_RESIDENT = 4 /* pipelined FP64 CG only: the whole iteration loop in one cooperative
+                        launch of one block per SM.  Each iteration's update (x, r, p) and fused
+                        SpMV run back to back in the launch; the SpMV of a block waits only for
+                        the blocks owning the columns it reads, and the one grid-wide step is
+                        the deterministic reduction that forms alpha and beta (Eq. (3)).  Needs
+                        the tile grid to cover two blocks per SM (n >= 1024 x SMs rows or
+                        nnz >= 8192 x SMs) and cooperative launch; otherwise, or with
+                        PK_FLAG_SELL or PK_FLAG_NO_TMA, PK_ERR_ARG.  PK_FLAG_TIMING times the
+                        launch (PK_SLOT_RESIDENT).  Every wait is bounded by pk_opts.wait_ns
+                        (PK_TIMEOUT) */
 };
 #define PK_PERSISTENT_MAX_N 65536  /* 16 CTAs x 4096 rows (8 x 4096 on devices without
                                       16-CTA clusters) */
@@ -174,7 +184,8 @@ enum {
   PK_SLOT_ORTHO = 3,     /* GMRES update + norm, normalisation + xi */
   PK_SLOT_SPMV = 4,      /* plain SpMV (classical / split forms) */
   PK_SLOT_BLAS1 = 5,     /* plain BLAS-1 kernels (classical / split forms) */
-  PK_SLOT_OTHER = 6      /* setup, cycle end, refinement */
+  PK_SLOT_OTHER = 6,     /* setup, cycle end, refinement */
+  PK_SLOT_RESIDENT = 7   /* the single launch of PK_LOOP_RESIDENT (the whole iteration loop) */
 };
 
 typedef struct pk_csr pk_csr;
@@ -276,6 +287,17 @@ pk_status pk_gmres_solve(pk_csr* A, const double* b, double* x, const pk_opts* o
                          pk_info* info, void* stream);
 
 /*
+ * The R factor and xi = (<v_0, v_1>, ..., <v_0, v_m>) of the most recent GMRES cycle run on A
+ * (Alg. 5 / 6, Sec. 3.3: the upper-triangular R of the Arnoldi relation and the right-hand
+ * side of R eta = xi), for inspection and testing.  R and xi are HOST arrays of m * m and m
+ * doubles; R[(j-1) * m + (i-1)] receives R_{j,i} for 1 <= j <= i <= m (zero below the
+ * diagonal), xi[i-1] receives xi_i.  Columns past the steps that cycle took hold values of an
+ * earlier cycle (or zero).  m in 1..64; PK_ERR_ARG if no GMRES solve has run on A.
+ * Synchronises `stream`.
+ */
+pk_status pk_gmres_cycle_factors(const pk_csr* A, int32_t m, double* R, double* xi, void* stream);
+
+/*
  * Many independent SPD systems in one persistent launch (motivated by the paper's transient
  * and small-system regime, Sec. 1 and 4.1).  A persistent grid takes systems from a device
  * work queue, largest first; one thread block runs pipelined CG (Alg. 2) on a system to
@@ -300,17 +322,20 @@ pk_status pk_batched_last_lanes(int32_t* lanes);
 
 /*
  * Allocation-free q = A p and *result = <p, q>.  The paper has no counterpart: this entry
- * point exists for callers that cannot allocate device memory where they need the product
- * -- code running inside CUDA stream capture (cudaMalloc is not permitted there), loops with
- * a memory budget fixed in advance, or hosts that must not go through a caching allocator.
+ * point exists for callers that cannot allocate device memory where they need the product --
+ * loops with a memory budget fixed in advance (an allocation could fail or stall mid-loop),
+ * or hosts that must not go through a caching allocator they do not own.
  * Unlike pk_spmv_dot it needs no pk_csr handle: the caller passes its own DEVICE CSR arrays
  * (same layout as pk_csr_create, not validated here), p, q (length n) and result (one
  * double), and the call allocates nothing.  Its scratch (per-block partial sums and the
  * last-block arrival counter) lives in a fixed device array of PK_NOALLOC_SCRATCH_BYTES
  * that every GPU loading the library holds until the process exits.
  *   - n must be in [0, PK_NOALLOC_MAX_N]; larger n returns PK_ERR_ARG with a message.
+ *   - q must not overlap p, row_ptr, col_idx, vals or result (q == p returns PK_ERR_ARG;
+ *     other overlaps give wrong results).
  *   - The first call on a device looks up the array's device address (cudaGetSymbolAddress)
- *     with that device current; make that first call before any stream capture.
+ *     with that device current and keeps it for the process; make that first call before
+ *     any stream capture.  Calls after a cudaDeviceReset of that device are not supported.
  *   - All calls on a device share the array (each call zeroes the counter first): calls that
  *     overlap on the GPU, e.g. on two streams at once, race and give wrong results.
  * Stream-ordered on `stream`; returns without synchronising.
@@ -368,6 +393,16 @@ pk_status pk_warmstart_loss(int64_t n, const float* out, const double* xt, const
 /* x_hat = 2 x_{t-1} - x_{t-2} + s0 out; out = NULL gives the linear extrapolation alone. */
 pk_status pk_warmstart_apply(int64_t n, const float* out, const double* xm1, const double* xm2,
                              const double* scales, double* xhat, void* stream);
+/* The energy step along the network's correction d = s0 out from the extrapolation
+ * e = 2 x_{t-1} - x_{t-2} (A SPD): gamma = <b - A e, d> / <d, A d>, the step length that
+ * minimises the A-norm of the error of e + gamma d (A (x_t - e) = b - A e), written to
+ * gamma[0] (device, one double; 0 if <d, A d> <= 0 or the quotient is not finite), and
+ * x_hat = e + gamma d.  Unlike pk_warmstart_apply (gamma = 1), the start it gives is never
+ * farther from the solution in the A-norm than e.  One pass over A plus one over the vectors;
+ * scratch: pk_warmstart_scratch_doubles() doubles.  (An extension; the paper has no learned part.) */
+pk_status pk_warmstart_apply_energy(pk_csr* A, const float* out, const double* xm1, const double* xm2,
+                                    const double* b, const double* scales, double* xhat, double* gamma,
+                                    double* scratch, void* stream);
 /* Adam (Kingma & Ba) on FP32 parameters, step >= 1; p_bf16 (nullable) receives a BF16 copy. */
 pk_status pk_adam_step(int64_t count, float* p, const float* grad, float* m, float* v, float lr,
                        float beta1, float beta2, float eps, int32_t step, void* p_bf16,

@@ -131,6 +131,25 @@ def warmstart_target(xt, xm1, xm2, s0):
     return (np.asarray(xt) - (2.0 * np.asarray(xm1) - np.asarray(xm2))) / s0
 
 
+def warmstart_energy_step(row_ptr, col, val, xm1, xm2, b, out, s0):
+    """The energy step along the network's correction: e = 2 x_{t-1} - x_{t-2}, r = b - A e,
+    d = s0 out, gamma = <r, d> / <d, A d> (0 if <d, A d> <= 0), x_hat = e + gamma d.  For SPD A,
+    gamma minimises ||x_t - e - gamma d||_A over gamma, since A (x_t - e) = r.  Returns
+    (x_hat, gamma); rows summed left to right in FP64."""
+    n = len(row_ptr) - 1
+    e = 2.0 * np.asarray(xm1, dtype=np.float64) - np.asarray(xm2, dtype=np.float64)
+    d = float(s0) * np.asarray(out, dtype=np.float64)
+    r = np.array(b, dtype=np.float64)
+    ad = np.zeros(n)
+    for i in range(n):
+        for j in range(row_ptr[i], row_ptr[i + 1]):
+            r[i] -= val[j] * e[col[j]]
+            ad[i] += val[j] * d[col[j]]
+    num, den = float(np.dot(r, d)), float(np.dot(d, ad))
+    gamma = num / den if den > 0 and np.isfinite(num / den) else 0.0
+    return e + gamma * d, gamma
+
+
 def adam_step(p, g, m, v, step, lr=1e-3, beta1=0.9, beta2=0.999, eps=1e-8):
     """One Adam update (Kingma & Ba, ICLR 2015, Algorithm 1) in FP64; returns (p, m, v)."""
     m = beta1 * m + (1 - beta1) * g

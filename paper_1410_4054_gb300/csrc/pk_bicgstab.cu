@@ -428,7 +428,7 @@ pk_status bicgstab_solve(pk_csr* A, const double* b, double* x, const pk_opts* o
                          cudaStream_t s) {
   pk_status e = check_opts(A, b, x, o, info);
   if (e) return e;
-  if (o->loop == PK_LOOP_PERSISTENT) { set_error("PK_LOOP_PERSISTENT runs pipelined CG only"); return PK_ERR_ARG; }
+  if (o->loop == PK_LOOP_PERSISTENT || o->loop == PK_LOOP_RESIDENT) { set_error("PK_LOOP_PERSISTENT / PK_LOOP_RESIDENT run pipelined CG only"); return PK_ERR_ARG; }
   *info = pk_info{};
   info->rel_res_true = -1.0;
   if (A->n == 0) return PK_OK;

@@ -442,6 +442,8 @@ pk_status pcg_jacobi_solve(pk_csr* A, const double* b, double* x, const pk_opts*
                            cudaStream_t s);
 pk_status launch_cg_persistent(pk_csr* A, double* x, double* r, double* p, double* ap,
                                cudaStream_t s);
+pk_status resident_prepare(pk_csr* A, cudaStream_t s, bool* usable);
+pk_status launch_cg_resident(pk_csr* A, double* x, double* r, double* p, double* ap, cudaStream_t s);
 
 pk_status cg_solve(pk_csr* A, const double* b, double* x, const pk_opts* o, pk_info* info,
                    cudaStream_t s) {
@@ -478,6 +480,19 @@ pk_status cg_solve(pk_csr* A, const double* b, double* x, const pk_opts* o, pk_i
                  A->nnz <= PK_PERSISTENT_AUTO_NNZ &&
                  !(o->flags & PK_FLAG_TIMING) && persistent_usable(A, o);
   }
+  bool resident = false;
+  if (o->loop == PK_LOOP_RESIDENT) {
+    if (o->variant != PK_VARIANT_PIPELINED || sell || (o->flags & PK_FLAG_NO_TMA)) {
+      set_error("PK_LOOP_RESIDENT runs pipelined CG on the CSR tiles (no PK_FLAG_SELL, PK_FLAG_NO_TMA)");
+      return PK_ERR_ARG;
+    }
+    if ((e = resident_prepare(A, s, &resident))) return e;
+    if (!resident) {
+      set_error("PK_LOOP_RESIDENT: the resident loop needs a tile grid of two blocks per SM "
+                "(n >= 512 x 2 x SMs rows or nnz >= 4096 x 2 x SMs) and cooperative launch");
+      return PK_ERR_ARG;
+    }
+  }
   cudaEvent_t e0, e1;
   PK_CUDA(cudaEventCreate(&e0));
   PK_CUDA(cudaEventCreate(&e1));
@@ -506,6 +521,29 @@ pk_status cg_solve(pk_csr* A, const double* b, double* x, const pk_opts* o, pk_i
   T.on = (o->flags & PK_FLAG_TIMING) != 0;
   T.s = s;
   int launches = 0;
+  if (resident) {
+    // r0, p0, <r0,r0>, <b,b>; then the whole iteration loop in one cooperative launch
+    if ((e = T.begin(PK_SLOT_OTHER))) return e;
+    k_residual_init<<<A->grid, kBlock, 0, s>>>(row_args(A), bd, xd, r, p, nullptr);
+    if ((e = T.end())) return e;
+    k_zero_x<<<A->grid, kBlock, 0, s>>>(row_args(A), xd);
+    PK_CUDA(cudaGetLastError());
+    if ((e = T.begin(PK_SLOT_RESIDENT))) return e;
+    if ((e = launch_cg_resident(A, xd, r, p, ap, s))) return e;
+    if ((e = T.end())) return e;
+    launches += 3;
+    if ((e = T.flush())) return e;
+    if (x_copy_back)
+      PK_CUDA(cudaMemcpyAsync(x_copy_back, xd, sizeof(double) * A->n, cudaMemcpyDeviceToDevice, s));
+    if ((e = finish_info(A, o, info, s, v, e0, e1, launches))) return e;
+    for (int k = 0; k < PK_MAX_KERNEL_SLOTS; ++k) {
+      info->kernel_count[k] = T.count[k];
+      info->kernel_ms[k] = T.count[k] ? T.ms[k] / T.count[k] : 0.0;
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    return (pk_status)info->status;
+  }
   const int G = A->grid;
   if (!A->grid_ew) {
     // elementwise kernels run as many resident blocks as their register use allows

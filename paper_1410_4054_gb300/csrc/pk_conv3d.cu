@@ -526,6 +526,45 @@ __global__ void k_ws_apply(int n, const float* out, const double* xm1, const dou
   xhat[v] = out ? fma(scales[0], (double)out[v], e) : e;
 }
 
+// The energy step along the network's correction: d = s0 out, r = b - A e,
+// gamma = <r, d> / <d, A d> -- the step from e along d that minimises the A-norm of the error
+// (<x_t - e - gamma d, A (x_t - e - gamma d)> is a parabola in gamma with its minimum there,
+// because A (x_t - e) = r).  Row i adds r_i d_i and d_i (A d)_i; d is formed at every gathered
+// column from out.  gamma = 0 when <d, A d> <= 0 or is not finite (the extrapolation alone).
+__global__ void __launch_bounds__(kBlock) k_ws_energy(int n, const int32_t* rp, const int32_t* ci,
+                                                      const double* va, const float* out,
+                                                      const double* xm1, const double* xm2,
+                                                      const double* b, const double* scales,
+                                                      double* gamma, double* scratch) {
+  const double s0 = scales[0];
+  double sums[2];
+  bool last;
+  grid_sums<2>(n, scratch, [&](int i, double (&v)[2]) {
+    double se = 0.0, sd = 0.0;
+    for (int j = rp[i]; j < rp[i + 1]; ++j) {
+      const int c = ci[j];
+      se = fma(va[j], 2.0 * xm1[c] - xm2[c], se);
+      sd = fma(va[j], s0 * (double)out[c], sd);
+    }
+    const double r = b[i] - se, d = s0 * (double)out[i];
+    v[0] = fma(r, d, v[0]);
+    v[1] = fma(d, sd, v[1]);
+  }, sums, last);
+  if (last && threadIdx.x == 0) {
+    const double g = sums[0] / sums[1];
+    gamma[0] = sums[1] > 0.0 && isfinite(g) ? g : 0.0;
+  }
+}
+
+// x_hat = 2 x_{t-1} - x_{t-2} + gamma s0 out.
+__global__ void k_ws_apply_gamma(int n, const float* out, const double* xm1, const double* xm2,
+                                 const double* scales, const double* gamma, double* xhat) {
+  const int v = blockIdx.x * blockDim.x + threadIdx.x;
+  if (v >= n) return;
+  const double e = 2.0 * xm1[v] - xm2[v];
+  xhat[v] = fma(gamma[0], scales[0] * (double)out[v], e);
+}
+
 // Adam on FP32 master parameters, optional BF16 copy.
 __global__ void k_adam(int count, float* p, const float* grad, float* m, float* v, float lr,
                        float b1, float b2, float eps, float c1, float c2, __nv_bfloat16* p16) {
@@ -739,6 +778,23 @@ pk_status pk_warmstart_apply(int64_t n, const float* out, const double* xm1, con
   }
   k_ws_apply<<<(int)((n + 255) / 256), 256, 0, (cudaStream_t)stream>>>((int)n, out, xm1, xm2,
                                                                        scales, xhat);
+  PK_CUDA(cudaGetLastError());
+  return PK_OK;
+}
+
+pk_status pk_warmstart_apply_energy(pk_csr* A, const float* out, const double* xm1, const double* xm2,
+                                    const double* b, const double* scales, double* xhat, double* gamma,
+                                    double* scratch, void* stream) {
+  if (!A || !out || !xm1 || !xm2 || !b || !scales || !xhat || !gamma || !scratch) {
+    set_error("pk_warmstart_apply_energy: bad arguments");
+    return PK_ERR_ARG;
+  }
+  const int n = A->n;
+  if (n == 0) return PK_OK;
+  cudaStream_t s = (cudaStream_t)stream;
+  PK_CUDA(cudaMemsetAsync(scratch + 3 * kWsGrid, 0, sizeof(double), s));
+  k_ws_energy<<<kWsGrid, kBlock, 0, s>>>(n, A->rp, A->ci, A->va, out, xm1, xm2, b, scales, gamma, scratch);
+  k_ws_apply_gamma<<<(n + 255) / 256, 256, 0, s>>>(n, out, xm1, xm2, scales, gamma, xhat);
   PK_CUDA(cudaGetLastError());
   return PK_OK;
 }

@@ -258,7 +258,7 @@ pk_status check_opts(const pk_csr* A, const double* b, double* x, const pk_opts*
   if (A->n > 0 && (!b || !x)) { set_error("NULL b or x"); return PK_ERR_ARG; }
   if (!(o->tol >= 0.0) || o->maxit < 0) { set_error("tol must be >= 0 and maxit >= 0"); return PK_ERR_ARG; }
   if (o->trace_cap > 0 && !o->trace) { set_error("trace_cap > 0 needs a trace array"); return PK_ERR_ARG; }
-  if (o->loop < PK_LOOP_GRAPH || o->loop > PK_LOOP_AUTO) { set_error("bad loop mode"); return PK_ERR_ARG; }
+  if (o->loop < PK_LOOP_GRAPH || o->loop > PK_LOOP_RESIDENT) { set_error("bad loop mode"); return PK_ERR_ARG; }
   if (o->wait_ns < 0) { set_error("wait_ns must be >= 0"); return PK_ERR_ARG; }
   return PK_OK;
 }
@@ -632,6 +632,9 @@ pk_status pk_csr_destroy(pk_csr* A) {
   if (A->sell_val) cudaFree(A->sell_val);
   if (A->jac_d) cudaFree(A->jac_d);
   if (A->jac_dinv) cudaFree(A->jac_dinv);
+  if (A->res_rows) cudaFree(A->res_rows);
+  if (A->res_nbr) cudaFree(A->res_nbr);
+  if (A->res_flag) cudaFree(A->res_flag);
   if (A->small) cudaFree(A->small);
   if (A->partials) cudaFree(A->partials);
   if (A->st) cudaFree(A->st);

@@ -21,6 +21,7 @@
 // The graph is an outer WHILE loop over cycles around an inner WHILE loop over steps.
 #include <algorithm>
 #include <cmath>
+#include <vector>
 
 #include "pk_guard.cuh"
 #include "pk_tile.cuh"
@@ -366,8 +367,18 @@ __global__ void __launch_bounds__(kTileThreads, 2) k_gm2(GmArgs g, int pass) {
   if (arrive_last(&st->counter)) {
     const int G = gridDim.x;
     for (int j = 1 + warp; j <= nj; j += kTileThreads / 32) {  // one warp per column
+      // the slots lane, lane + 32, ... added in order; loads issued 8 at a time (one L2 round
+      // trip per batch instead of one per slot)
+      const double* pj = g.partials + (size_t)(j - 1) * G;
       double t = 0.0;
-      for (int bk = lane; bk < G; bk += 32) t += ld_cg(g.partials + (size_t)(j - 1) * G + bk);
+      for (int base = lane; base < G; base += 32 * 8) {
+        double v[8];
+#pragma unroll
+        for (int q = 0; q < 8; ++q) v[q] = base + 32 * q < G ? ld_cg(pj + base + 32 * q) : 0.0;
+#pragma unroll
+        for (int q = 0; q < 8; ++q)
+          if (base + 32 * q < G) t += v[q];
+      }
       t = warp_sum(t);
       if (lane == 0) {
         if (pass) g.C[j] = t;
@@ -663,7 +674,7 @@ pk_status gmres_solve(pk_csr* A, const double* b, double* x, const pk_opts* o, p
                       cudaStream_t s) {
   pk_status e = check_opts(A, b, x, o, info);
   if (e) return e;
-  if (o->loop == PK_LOOP_PERSISTENT) { set_error("PK_LOOP_PERSISTENT runs pipelined CG only"); return PK_ERR_ARG; }
+  if (o->loop == PK_LOOP_PERSISTENT || o->loop == PK_LOOP_RESIDENT) { set_error("PK_LOOP_PERSISTENT / PK_LOOP_RESIDENT run pipelined CG only"); return PK_ERR_ARG; }
   *info = pk_info{};
   info->rel_res_true = -1.0;
   if (A->n == 0) return PK_OK;
@@ -838,4 +849,23 @@ pk_status gmres_solve(pk_csr* A, const double* b, double* x, const pk_opts* o, p
 extern "C" pk_status pk_gmres_solve(pk_csr* A, const double* b, double* x, const pk_opts* opts,
                                     pk_info* info, void* stream) {
   return pk::guarded([&] { return pk::gmres_solve(A, b, x, opts, info, (cudaStream_t)stream); });
+}
+
+// The R factor and xi of the most recent GMRES cycle on the handle (device scratch -> host).
+extern "C" pk_status pk_gmres_cycle_factors(const pk_csr* A, int32_t m, double* R, double* xi,
+                                            void* stream) {
+  return pk::guarded([&]() -> pk_status {
+    using namespace pk;
+    if (!A || !R || !xi) { set_error("pk_gmres_cycle_factors: NULL argument"); return PK_ERR_ARG; }
+    if (m < 1 || m > kGmMax) { set_error("pk_gmres_cycle_factors: m must be in 1..64"); return PK_ERR_ARG; }
+    if (!A->small) { set_error("pk_gmres_cycle_factors: no GMRES solve has run on this handle"); return PK_ERR_ARG; }
+    cudaStream_t s = (cudaStream_t)stream;
+    std::vector<double> h((size_t)kXiOff + kRld);
+    PK_CUDA(cudaMemcpyAsync(h.data(), A->small, sizeof(double) * h.size(), cudaMemcpyDeviceToHost, s));
+    PK_CUDA(cudaStreamSynchronize(s));
+    for (int j = 1; j <= m; ++j)
+      for (int i = 1; i <= m; ++i) R[(size_t)(j - 1) * m + (i - 1)] = j <= i ? h[(size_t)j * kRld + i] : 0.0;
+    for (int i = 1; i <= m; ++i) xi[i - 1] = h[(size_t)kXiOff + i];
+    return PK_OK;
+  });
 }

@@ -46,6 +46,10 @@ struct DevState {
   unsigned long long wait_ns;  // bound on a pipeline wait that should make progress
   int32_t stall_test;          // PK_FLAG_TEST_STALL: the CSR tile producer issues no copies
   int32_t stall_pad;
+  // grid-resident CG loop: the last block of iteration i's reduction publishes epoch = i + 1
+  // once alpha_i, beta_i and the exit decision are in place
+  int32_t epoch;
+  int32_t epoch_pad;
 };
 
 // Loads that bypass L1 (the value was written by another block or an earlier kernel).
@@ -113,30 +117,60 @@ __device__ __forceinline__ bool arrive_last(unsigned int* counter) {
   return last;
 }
 
+// A lane's share of a fixed-order second stage over G block slots: for every k < NV, the
+// slots c = lane, lane + 32, lane + 64, ... of partials[k * G + c], added in that order
+// alternately into two accumulators (even steps a0, odd steps a1), t[k] = a0 + a1.  The loads
+// of B steps of all NV sums are issued before their adds: a warp issues in order, so a loop
+// that adds each load before issuing the next waits one L2 round trip per step (measured on
+// GB300 with 304 slots: about 10 us for two sums, on the critical path of every iteration).
+// The adds are the same, in the same order, as in that loop.
+template <int NV, int B>
+__device__ __forceinline__ void lane_slot_sums(const double* partials, int G, int lane, double (&t)[NV]) {
+  static_assert(B % 2 == 0, "batches keep the even / odd step parity");
+  double a0[NV], a1[NV];
+#pragma unroll
+  for (int k = 0; k < NV; ++k) a0[k] = a1[k] = 0.0;
+  for (int base = lane; base < G; base += 32 * B) {
+    double v[NV][B];
+#pragma unroll
+    for (int k = 0; k < NV; ++k)
+#pragma unroll
+      for (int q = 0; q < B; ++q) {
+        const int c = base + 32 * q;
+        v[k][q] = c < G ? ld_cg(partials + (size_t)k * G + c) : 0.0;
+      }
+#pragma unroll
+    for (int k = 0; k < NV; ++k)
+#pragma unroll
+      for (int q = 0; q < B; ++q)
+        if (base + 32 * q < G) {
+          if (q & 1) a1[k] += v[k][q];
+          else a0[k] += v[k][q];
+        }
+  }
+#pragma unroll
+  for (int k = 0; k < NV; ++k) t[k] = a0[k] + a1[k];
+}
+
 // Second reduction stage in the last block: out[k] = sum over blocks of partials[k][.], in a
 // fixed order, broadcast to every thread.  One warp does it (two interleaved accumulators
-// per lane, then a butterfly): on GB300 every FP64 instruction that all warps of the block
-// would issue costs the SM's narrow FP64 pipe, and this runs on the critical path.
+// per lane, loads issued in batches, then a butterfly): on GB300 every FP64 instruction that
+// all warps of the block would issue costs the SM's narrow FP64 pipe, and this runs on the
+// critical path.
 template <int NV>
 __device__ __forceinline__ void final_sums(const double* partials, double (&out)[NV]) {
   __shared__ double sm[NV];
   const int G = gridDim.x;
   if (threadIdx.x < 32) {
     const int lane = threadIdx.x;
+    double t[NV];
+    lane_slot_sums<NV, (NV <= 2 ? 6 : 4)>(partials, G, lane, t);
 #pragma unroll
     for (int k = 0; k < NV; ++k) {
-      const double* pk = partials + (size_t)k * G;
-      double a0 = 0.0, a1 = 0.0;
-      int i = lane;
-      for (; i + 32 < G; i += 64) {
-        a0 += ld_cg(pk + i);
-        a1 += ld_cg(pk + i + 32);
-      }
-      if (i < G) a0 += ld_cg(pk + i);
-      double t = a0 + a1;
+      double u = t[k];
 #pragma unroll
-      for (int o = 16; o > 0; o >>= 1) t += __shfl_xor_sync(0xffffffffu, t, o);
-      if (lane == 0) sm[k] = t;
+      for (int o = 16; o > 0; o >>= 1) u += __shfl_xor_sync(0xffffffffu, u, o);
+      if (lane == 0) sm[k] = u;
     }
   }
   __syncthreads();
@@ -228,6 +262,12 @@ struct pk_csr {
   double* jac_d = nullptr;
   double* jac_dinv = nullptr;
   int jac_state = 0;
+  // grid-resident CG loop (built on first use): blocks, their rows, the range of
+  // blocks whose p each block's SpMV reads, the per-block "p written" flags
+  int res_grid = 0;                 // 0 = not built, -1 = not usable on this matrix / device
+  int32_t* res_rows = nullptr;      // res_grid + 1
+  int32_t* res_nbr = nullptr;       // 2 per block: first and last neighbour block
+  int32_t* res_flag = nullptr;      // res_grid
   pk_graph_entry graphs[4];
   cudaEvent_t ev_pool[64] = {nullptr};
   int ev_count = 0;

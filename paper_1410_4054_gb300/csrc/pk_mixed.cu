@@ -379,7 +379,7 @@ pk_status ensure_fp32_values(pk_csr* A, cudaStream_t s) {
 pk_status cg_mixed(pk_csr* A, const double* b, double* x, const pk_opts* o, pk_info* info,
                    cudaStream_t s) {
   pk_status e;
-  if (o->loop == PK_LOOP_PERSISTENT) { set_error("PK_LOOP_PERSISTENT runs pipelined FP64 CG only"); return PK_ERR_ARG; }
+  if (o->loop == PK_LOOP_PERSISTENT || o->loop == PK_LOOP_RESIDENT) { set_error("PK_LOOP_PERSISTENT / PK_LOOP_RESIDENT run pipelined FP64 CG only"); return PK_ERR_ARG; }
   if ((e = ensure_fp32_values(A, s))) return e;
   cudaEvent_t e0, e1;
   PK_CUDA(cudaEventCreate(&e0));

@@ -1,9 +1,9 @@
 // Allocation-free variant of the fused SpMV + inner product (q = A p, <p, q>).
 //
 // Some callers cannot allocate device memory at the point where they need this product:
-// code that runs while a CUDA graph is being captured (cudaMalloc is not allowed there),
-// real-time or embedded loops whose memory budget is fixed up front, and host code that must
-// not touch a caching allocator it does not own.  pk_spmv_dot needs a pk_csr handle, whose
+// real-time or embedded loops whose memory budget is fixed up front (an allocation could fail
+// or stall mid-loop), and host code that must not touch a caching allocator it does not own
+// (a second allocator in the process fragments or double-books device memory).  pk_spmv_dot needs a pk_csr handle, whose
 // creation allocates; this entry point takes the caller's own device CSR arrays and keeps its
 // scratch -- one partial sum per thread block plus the arrival counter of the last-block
 // reduction -- in a fixed, file-scope device array instead.
@@ -30,7 +30,9 @@ static_assert(256 + 8 * kNaBlocks <= kNaScratchBytes, "scratch layout");
 static __device__ __align__(256) unsigned char g_noalloc_scratch[kNaScratchBytes];
 
 // Host-side addresses of g_noalloc_scratch, one per device (the symbol itself is only a
-// host stand-in and must never be passed to a kernel).
+// host stand-in and must never be passed to a kernel).  Looked up once per device for the
+// life of the process: after a cudaDeviceReset the library's module, and with it the array,
+// may be loaded at another address, so calls after a reset are not supported.
 static std::mutex g_noalloc_mutex;
 static void* g_noalloc_ptr[64] = {nullptr};
 
@@ -93,6 +95,10 @@ extern "C" pk_status pk_spmv_dot_noalloc(int64_t n, const int32_t* row_ptr, cons
   }
   if (!result || (n > 0 && (!row_ptr || !col_idx || !vals || !p || !q))) {
     set_error("pk_spmv_dot_noalloc: NULL argument");
+    return PK_ERR_ARG;
+  }
+  if (n > 0 && (const void*)q == (const void*)p) {  // rows read p[col] while others write q
+    set_error("pk_spmv_dot_noalloc: q must not be p");
     return PK_ERR_ARG;
   }
   cudaStream_t s = (cudaStream_t)stream;

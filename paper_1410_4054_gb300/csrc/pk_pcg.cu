@@ -204,7 +204,7 @@ pk_status pcg_setup() {
 
 pk_status pcg_jacobi_solve(pk_csr* A, const double* b, double* x, const pk_opts* o, pk_info* info,
                            cudaStream_t s) {
-  if (o->variant != PK_VARIANT_PIPELINED || o->precision != PK_PREC_FP64 || o->loop == PK_LOOP_PERSISTENT) {
+  if (o->variant != PK_VARIANT_PIPELINED || o->precision != PK_PREC_FP64 || o->loop == PK_LOOP_PERSISTENT || o->loop == PK_LOOP_RESIDENT) {
     set_error("PK_PRECOND_JACOBI runs pipelined FP64 CG on the graph or host loop");
     return PK_ERR_ARG;
   }

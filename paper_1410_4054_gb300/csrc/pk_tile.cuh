@@ -312,6 +312,19 @@ constexpr int kStageBytes = ((kRpWords * 4 + 15) & ~15) + kVaWords * 8 + kCiByte
 
 constexpr int csr_smem_bytes() { return kCsrStages * kStageBytes + 2 * kCsrStages * 8 + kCsrStages * 16; }
 
+// Gathers of the SpMV's input vector.  A plain pointer reads through the non-coherent path
+// (the vector is read-only while the kernel runs); CohVec reads through L2 only, for the
+// grid-resident CG loop, in which other blocks rewrite the vector between the phases of one
+// launch and a non-coherent copy could be stale.
+template <class VT>
+struct CohVec {
+  const VT* p;
+};
+__device__ __forceinline__ double gather(const double* __restrict__ x, int c) { return __ldg(x + c); }
+__device__ __forceinline__ float gather(const float* __restrict__ x, int c) { return __ldg(x + c); }
+template <class VT>
+__device__ __forceinline__ VT gather(CohVec<VT> x, int c) { return __ldcg(x.p + c); }
+
 template <class VT>
 struct CsrTilesT {
   const int32_t* rp;
@@ -354,9 +367,8 @@ __device__ __forceinline__ void fma_batch_gn(int mx, const VT (&v)[8], const VT 
 // every lane of the warp calls it together (lanes without a row pass j = j1), and the batch
 // loop runs to the warp's longest share, issuing only that many FMAs (predicated-off FP64
 // instructions still take issue slots).
-template <int G, class VT>
-__device__ __forceinline__ VT group_row(const VT* sva, const int32_t* sci, int j, int j1,
-                                        const VT* __restrict__ x) {
+template <int G, class VT, class XP>
+__device__ __forceinline__ VT group_row(const VT* sva, const int32_t* sci, int j, int j1, XP x) {
   VT s = (VT)0;
   for (;;) {
     const int m = j < j1 ? min(8, (j1 - j + G - 1) / G) : 0;
@@ -370,7 +382,7 @@ __device__ __forceinline__ VT group_row(const VT* sva, const int32_t* sci, int j
       v[k] = k < m ? sva[j + k * G] : (VT)0;
     }
 #pragma unroll
-    for (int k = 0; k < 8; ++k) xv[k] = k < m ? __ldg(x + c[k]) : (VT)0;
+    for (int k = 0; k < 8; ++k) xv[k] = k < m ? gather(x, c[k]) : (VT)0;
     fma_batch_gn(mx, v, xv, m, s);
     j += 8 * G;
   }
@@ -381,9 +393,9 @@ __device__ __forceinline__ VT group_row(const VT* sva, const int32_t* sci, int j
 
 // The rows of a grouped tile: kConsumers / G rows per round, rows in order.  Rounds are the
 // same for the whole block, so every lane reaches the group's shuffles.
-template <int G, class VT, class RowDone>
+template <int G, class VT, class XP, class RowDone>
 __device__ __forceinline__ void group_rows(const int32_t* srp, const VT* sva, const int32_t* sci, int R0,
-                                           int R1, const VT* __restrict__ x, RowDone& row_done) {
+                                           int R1, XP x, RowDone& row_done) {
   constexpr int ng = kConsumers / G;
   const int gid = (int)threadIdx.x / G, q = (int)threadIdx.x & (G - 1);
   const int rounds = (R1 - R0 + ng - 1) / ng;
@@ -396,10 +408,12 @@ __device__ __forceinline__ void group_rows(const int32_t* srp, const VT* sva, co
 }
 
 // Two row products from a shared-memory window (defined below): FP64 and FP32.
+template <class XP>
 __device__ __forceinline__ void row_pair(const double* sva, const int32_t* sci, int ja, int ja1, int jb,
-                                         int jb1, const double* __restrict__ x, double& sa, double& sb);
+                                         int jb1, XP x, double& sa, double& sb);
+template <class XP>
 __device__ __forceinline__ void row_pair(const float* sva, const int32_t* sci, int ja, int ja1, int jb,
-                                         int jb1, const float* __restrict__ x, float& sa, float& sb);
+                                         int jb1, XP x, float& sa, float& sb);
 
 // Runs the CSR pipeline and the row products y_row = sum_j A[row][j] x[col j]; every finished
 // row goes to `row_done(row, y_row)`, called by the one consumer thread that owns the row.
@@ -428,15 +442,15 @@ constexpr int kChunkTile = 64;
 static_assert(kCsrStages <= 2, "the chunk-row counter is reused two tiles after its last use");
 static_assert(kTileNnz % kConsumers == 0, "chunks must hold whole multiples of the consumer count");
 
-template <class VT, class RowDone>
+template <class VT, class XP, class RowDone>
 __device__ __forceinline__ void block_row_chunk(int row, int zc0, int zr1, VT* stage_va, int32_t* stage_ci,
-                                                const VT* __restrict__ x, VT& acc, VT* red, int* cnt,
+                                                XP x, VT& acc, VT* red, int* cnt,
                                                 int warp, int lane, RowDone& row_done) {
   constexpr int kVaUnit = 16 / (int)sizeof(VT);
   const int zc1 = min(zr1, zc0 + kTileNnz);
   const VT* sva = stage_va - (zc0 & ~(kVaUnit - 1));
   const int32_t* sci = stage_ci - (zc0 & ~3);
-  for (int j = zc0 + (int)threadIdx.x; j < zc1; j += kConsumers) acc = fma_t(sva[j], __ldg(x + sci[j]), acc);
+  for (int j = zc0 + (int)threadIdx.x; j < zc1; j += kConsumers) acc = fma_t(sva[j], gather(x, sci[j]), acc);
   if (zc1 != zr1) return;  // more chunks of this row follow
   VT w = acc;
   acc = (VT)0;
@@ -460,9 +474,9 @@ __device__ __forceinline__ void block_row_chunk(int row, int zc0, int zr1, VT* s
 }
 
 // IRR = false compiles the thread-per-row path only (matrices without long rows).
-template <bool IRR, class VT, class Setup, class RowDone>
+template <bool IRR, class VT, class XP, class Setup, class RowDone>
 __device__ __forceinline__ bool csr_tiles(const CsrTilesT<VT>& T, unsigned char* smem, DevState* st,
-                                          Setup&& setup, const VT* __restrict__ x, RowDone&& row_done) {
+                                          Setup&& setup, XP x, RowDone&& row_done) {
   constexpr int kVaUnit = 16 / (int)sizeof(VT);  // values per 16-byte copy unit
   uint64_t* full = reinterpret_cast<uint64_t*>(smem + kCsrStages * kStageBytes);
   uint64_t* empty = full + kCsrStages;
@@ -632,7 +646,7 @@ __device__ __forceinline__ bool csr_tiles(const CsrTilesT<VT>& T, unsigned char*
           const int r = __shfl_sync(0xffffffffu, h == 0 ? ra : rb, src);
           const int j0 = srp[r], j1 = srp[r + 1];
           VT acc = (VT)0;
-          for (int j = j0 + lane; j < j1; j += 32) acc = fma_t(sva[j], __ldg(x + sci[j]), acc);
+          for (int j = j0 + lane; j < j1; j += 32) acc = fma_t(sva[j], gather(x, sci[j]), acc);
 #pragma unroll
           for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
           if (lane == src) row_done(r, acc);
@@ -675,9 +689,9 @@ __device__ __forceinline__ void fma_batch_n(int mx, const double (&v)[8], const 
   }
 }
 
+template <class XP>
 __device__ __forceinline__ void smem_row2(const double* sva, const int32_t* sci, int ja, int ja1,
-                                          int jb, int jb1, const double* __restrict__ x,
-                                          double& sa, double& sb) {
+                                          int jb, int jb1, XP x, double& sa, double& sb) {
   sa = 0.0;
   sb = 0.0;
   for (;;) {
@@ -694,8 +708,8 @@ __device__ __forceinline__ void smem_row2(const double* sva, const int32_t* sci,
     }
 #pragma unroll
     for (int k = 0; k < 8; ++k) {
-      xa[k] = k < ma ? __ldg(x + ca[k]) : 0.0;
-      xb[k] = k < mb ? __ldg(x + cb[k]) : 0.0;
+      xa[k] = k < ma ? gather(x, ca[k]) : 0.0;
+      xb[k] = k < mb ? gather(x, cb[k]) : 0.0;
     }
     // the same FMAs in the same order as a fixed 8-wide loop, without the dead issue slots
     const unsigned conv = __activemask();
@@ -758,8 +772,8 @@ inline void launch_pdl(void (*kern)(KArgs...), int grid, int block, size_t smem,
 
 // FP32 row product from a shared-memory window: the row's products summed left to right
 // (the order of a plain CSR row loop), gathers of a batch of 8 issued before the FMAs.
-__device__ __forceinline__ float smem_row_f32(const float* sva, const int32_t* sci, int j, int j1,
-                                              const float* __restrict__ x) {
+template <class XP>
+__device__ __forceinline__ float smem_row_f32(const float* sva, const int32_t* sci, int j, int j1, XP x) {
   float s = 0.0f;
   for (; j < j1; j += 8) {
     const int m = min(8, j1 - j);
@@ -771,7 +785,7 @@ __device__ __forceinline__ float smem_row_f32(const float* sva, const int32_t* s
       v[k] = k < m ? sva[j + k] : 0.0f;
     }
 #pragma unroll
-    for (int k = 0; k < 8; ++k) xv[k] = k < m ? __ldg(x + c[k]) : 0.0f;
+    for (int k = 0; k < 8; ++k) xv[k] = k < m ? gather(x, c[k]) : 0.0f;
 #pragma unroll
     for (int k = 0; k < 8; ++k)
       if (k < m) s = fmaf(v[k], xv[k], s);
@@ -779,13 +793,15 @@ __device__ __forceinline__ float smem_row_f32(const float* sva, const int32_t* s
   return s;
 }
 
+template <class XP>
 __device__ __forceinline__ void row_pair(const double* sva, const int32_t* sci, int ja, int ja1, int jb,
-                                         int jb1, const double* __restrict__ x, double& sa, double& sb) {
+                                         int jb1, XP x, double& sa, double& sb) {
   smem_row2(sva, sci, ja, ja1, jb, jb1, x, sa, sb);
 }
 
+template <class XP>
 __device__ __forceinline__ void row_pair(const float* sva, const int32_t* sci, int ja, int ja1, int jb,
-                                         int jb1, const float* __restrict__ x, float& sa, float& sb) {
+                                         int jb1, XP x, float& sa, float& sb) {
   sa = smem_row_f32(sva, sci, ja, ja1, x);
   sb = jb1 > jb ? smem_row_f32(sva, sci, jb, jb1, x) : 0.0f;
 }

@@ -22,7 +22,7 @@ STATUS_NAMES = ["PK_OK", "PK_ERR_ARG", "PK_ERR_CUDA", "PK_ERR_OOM", "PK_NOT_CONV
                 "PK_BREAKDOWN", "PK_NOT_SPD", "PK_ERR_NAN", "PK_TIMEOUT"]
 VARIANTS = {"pipelined": 0, "classical": 1, "split": 2}
 PRECISIONS = {"fp64": 0, "mixed": 1}
-LOOPS = {"graph": 0, "host": 1, "persistent": 2, "auto": 3}
+LOOPS = {"graph": 0, "host": 1, "persistent": 2, "auto": 3, "resident": 4}
 PERSISTENT_AUTO_N = 65536  # PK_PERSISTENT_AUTO_N
 PERSISTENT_AUTO_NNZ = 393216  # PK_PERSISTENT_AUTO_NNZ
 FLAG_TIMING = 1
@@ -32,7 +32,7 @@ FLAG_AUTOTUNE = 8
 FLAG_SELL = 16
 FLAG_CGS2 = 32
 FLAG_TEST_STALL = 64
-SLOTS = ["spmv_dots", "update", "multidot", "ortho", "spmv", "blas1", "other"]
+SLOTS = ["spmv_dots", "update", "multidot", "ortho", "spmv", "blas1", "other", "resident"]
 MAX_SLOTS = 8
 
 
@@ -76,6 +76,7 @@ EXPORTS = {
                                     C.POINTER(Info), C.c_void_p]),
     "pk_gmres_solve": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.POINTER(Opts),
                                  C.POINTER(Info), C.c_void_p]),
+    "pk_gmres_cycle_factors": (C.c_int, [C.c_void_p, C.c_int32, C.c_void_p, C.c_void_p, C.c_void_p]),
     "pk_batched_solve": (C.c_int, [C.c_int32, C.c_void_p, C.c_void_p, C.c_void_p, C.POINTER(Opts),
                                    C.c_void_p, C.c_void_p]),
     "pk_batched_last_config": (C.c_int, [C.POINTER(C.c_int32), C.POINTER(C.c_int32)]),
@@ -96,6 +97,8 @@ EXPORTS = {
                                     C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p]),
     "pk_warmstart_apply": (C.c_int, [C.c_int64, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p,
                                      C.c_void_p, C.c_void_p]),
+    "pk_warmstart_apply_energy": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p,
+                                            C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p]),
     "pk_adam_step": (C.c_int, [C.c_int64, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_float,
                                C.c_float, C.c_float, C.c_float, C.c_int32, C.c_void_p, C.c_void_p]),
     "pk_status_string": (C.c_char_p, [C.c_int]),
@@ -278,6 +281,15 @@ def gmres_solve(A: CSRMatrix, b, x, stream=None, **kw) -> dict:
     return info_dict(info)
 
 
+def gmres_cycle_factors(A: CSRMatrix, m: int, stream=None):
+    """pk_gmres_cycle_factors: (R, xi) of the last GMRES cycle on A, R[j-1, i-1] = R_{j,i}."""
+    R = np.zeros((m, m))
+    xi = np.zeros(m)
+    _check(lib().pk_gmres_cycle_factors(A.handle, int(m), _ptr(R), _ptr(xi), _stream_ptr(stream)),
+           "pk_gmres_cycle_factors")
+    return R, xi
+
+
 def batched_solve(As, bs, xs, stream=None, **kw) -> list:
     """pk_batched_solve over lists of CSRMatrix handles and device tensors b[k], x[k]."""
     nsys = len(As)
@@ -395,6 +407,13 @@ def warmstart_apply(n, out, xm1, xm2, scales, xhat, stream=None):
     """x_hat = 2 x_{t-1} - x_{t-2} + s out (out None: the extrapolation alone)."""
     _check(lib().pk_warmstart_apply(int(n), _ptr(out), _ptr(xm1), _ptr(xm2), _ptr(scales), _ptr(xhat),
                                     _stream_ptr(stream)), "pk_warmstart_apply")
+
+
+def warmstart_apply_energy(A: CSRMatrix, out, xm1, xm2, b, scales, xhat, gamma, scratch, stream=None):
+    """x_hat = e + gamma s0 out with the A-norm-optimal gamma (written to gamma[0])."""
+    _check(lib().pk_warmstart_apply_energy(A.handle, _ptr(out), _ptr(xm1), _ptr(xm2), _ptr(b), _ptr(scales),
+                                           _ptr(xhat), _ptr(gamma), _ptr(scratch), _stream_ptr(stream)),
+           "pk_warmstart_apply_energy")
 
 
 def adam_step(p, grad, m, v, lr, step, beta1=0.9, beta2=0.999, eps=1e-8, p_bf16=None, stream=None):

@@ -17,7 +17,9 @@ step, and training moves them from there.
 The solver is always run to the same tolerance: of x_hat and x_{t-1}, the one with the smaller
 residual ||b - A x0|| is the initial guess, so the plain warm start is both fallback and yardstick.
 The experiment also reports the extrapolation alone (network output taken as zero), so the
-network's own contribution is visible.
+network's own contribution is visible, and the energy step: the network's correction d taken as
+a search direction from e, x0 = e + gamma d with the gamma that minimises the A-norm of the
+error along d (one more pass over A), so that the start is never worse than e in that norm.
 """
 from __future__ import annotations
 
@@ -161,6 +163,13 @@ class ConvNet:
         self.forward()
         pk.warmstart_apply(self.n, self.out, xm1, xm2, self.scales, xhat)
 
+    def predict_energy(self, A, xm1, xm2, b, xhat, gamma):
+        """x_hat = e + gamma s0 net with gamma minimising the A-norm error along the network's
+        correction: never farther from x_t (A-norm) than the extrapolation e."""
+        self.pack(A, xm1, xm2, b)
+        self.forward()
+        pk.warmstart_apply_energy(A, self.out, xm1, xm2, b, self.scales, xhat, gamma, self.scratch)
+
 
 def run_transient(k=64, steps=300, train_last=150, epochs=30, lr=1e-3, tol=1e-8, seed=0,
                   device="cuda", log=None, checkpoint=None, resume=False):
@@ -236,15 +245,20 @@ def run_transient(k=64, steps=300, train_last=150, epochs=30, lr=1e-3, tol=1e-8,
     xhat = zeros.clone()
     r2 = torch.zeros(2, dtype=torch.float64, device=device)
 
-    def evaluate(use_net):
+    gamma = torch.zeros(1, dtype=torch.float64, device=device)
+    gammas = []
+
+    def evaluate(mode):
         iters, ms, chosen, ratio, kept = [], [], 0, [], []
         for t in range(train_last + 1, steps + 1):
             b = bs[t + 1]
             st = torch.cuda.Event(enable_timing=True)
             en = torch.cuda.Event(enable_timing=True)
             st.record()
-            if use_net:
+            if mode == "learned":
                 net.predict(A, xs[t], xs[t - 1], b, xhat)
+            elif mode == "energy":
+                net.predict_energy(A, xs[t], xs[t - 1], b, xhat, gamma)
             else:
                 pk.warmstart_apply(n, None, xs[t], xs[t - 1], net.scales, xhat)
             pk.residual_norm2(A, b, xhat, r2[0:1])
@@ -261,10 +275,13 @@ def run_transient(k=64, steps=300, train_last=150, epochs=30, lr=1e-3, tol=1e-8,
             assert info["status"] == pk.PK_OK, info
             iters.append(info["iters"])
             ms.append(info["solve_ms"] + st.elapsed_time(en))
+            if mode == "energy":
+                gammas.append(float(gamma.item()))
         return iters, ms, chosen, float(np.mean(ratio)), float(max(kept))
 
-    ex_iters, ex_ms, ex_chosen, ex_ratio, ex_kept = evaluate(False)
-    ln_iters, ln_ms, ln_chosen, ln_ratio, ln_kept = evaluate(True)
+    ex_iters, ex_ms, ex_chosen, ex_ratio, ex_kept = evaluate("extrap")
+    ln_iters, ln_ms, ln_chosen, ln_ratio, ln_kept = evaluate("learned")
+    en_iters, en_ms, en_chosen, en_ratio, en_kept = evaluate("energy")
     ev = slice(train_last, steps)
     return {
         "k": k, "n": n, "steps": steps, "train_samples": len(train), "epochs": epochs,
@@ -280,4 +297,9 @@ def run_transient(k=64, steps=300, train_last=150, epochs=30, lr=1e-3, tol=1e-8,
         "extrap_residual_ratio": ex_ratio, "learned_residual_ratio": ln_ratio,
         "extrap_chosen_steps": ex_chosen, "learned_chosen_steps": ln_chosen,
         "extrap_max_kept_ratio": ex_kept, "learned_max_kept_ratio": ln_kept,
+        "energy_iters_eval": en_iters, "energy_mean_iters": float(np.mean(en_iters)),
+        "energy_mean_ms": float(np.mean(en_ms)), "energy_residual_ratio": en_ratio,
+        "energy_chosen_steps": en_chosen, "energy_max_kept_ratio": en_kept,
+        "energy_gamma_mean": float(np.mean(gammas)), "energy_gamma_min": float(np.min(gammas)),
+        "energy_gamma_max": float(np.max(gammas)),
     }

@@ -291,10 +291,30 @@ def spd_random(n: int, seed: int = 0, density: float = 0.3, cond_shift: float = 
     return _from_coo(n, r, c, s[r, c], f"spd_{n}")
 
 
+def csr_product(a: CSR, x: np.ndarray) -> np.ndarray:
+    """y = A x with every product rounded on its own and each row's products added left to
+    right, as separate numpy multiply and add operations: the same bits on every host (a
+    compiled CSR loop may fuse the multiply-add on one architecture and not on another)."""
+    x = np.asarray(x, dtype=np.float64)
+    prod = a.val * x[a.col]
+    lens = np.diff(a.row_ptr).astype(np.int64)
+    order = np.argsort(-lens, kind="stable")  # longest rows first: pass k touches a prefix
+    starts = a.row_ptr[:-1].astype(np.int64)[order]
+    ys = np.zeros(a.n)
+    active = np.searchsorted(-lens[order], 0, side="left")  # rows with at least one entry
+    for k in range(int(lens.max()) if a.n else 0):
+        while active > 0 and lens[order[active - 1]] <= k:
+            active -= 1
+        ys[:active] += prod[starts[:active] + k]
+    y = np.empty(a.n)
+    y[order] = ys
+    return y
+
+
 def manufactured(a: CSR, seed: int = 0):
-    """x* uniform[-1,1) from splitmix64(seed), b = A x*, x0 = 0."""
+    """x* uniform[-1,1) from splitmix64(seed), b = A x* (csr_product), x0 = 0."""
     xs = uniform_pm1(seed, a.n)
-    b = a.matvec(xs)
+    b = csr_product(a, xs)
     return xs, b, np.zeros(a.n)
 
 

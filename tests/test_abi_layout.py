@@ -25,11 +25,11 @@ TABLES = {
                  "split": "PK_VARIANT_SPLIT"},
     "PRECISIONS": {"fp64": "PK_PREC_FP64", "mixed": "PK_PREC_MIXED"},
     "LOOPS": {"graph": "PK_LOOP_GRAPH", "host": "PK_LOOP_HOST", "persistent": "PK_LOOP_PERSISTENT",
-              "auto": "PK_LOOP_AUTO"},
+              "auto": "PK_LOOP_AUTO", "resident": "PK_LOOP_RESIDENT"},
     "PRECONDS": {"none": "PK_PRECOND_NONE", "jacobi": "PK_PRECOND_JACOBI"},
 }
 SLOTS = ["PK_SLOT_SPMV_DOTS", "PK_SLOT_UPDATE", "PK_SLOT_MULTIDOT", "PK_SLOT_ORTHO", "PK_SLOT_SPMV",
-         "PK_SLOT_BLAS1", "PK_SLOT_OTHER"]
+         "PK_SLOT_BLAS1", "PK_SLOT_OTHER", "PK_SLOT_RESIDENT"]
 
 
 @pytest.fixture(scope="module")

@@ -169,3 +169,38 @@ def test_warmstart_input_exact_extrapolation_is_zero_residual():
     assert (s0, s1) == (1.0, 1.0)
     assert not X[:, :2].any()
     np.testing.assert_allclose(X[:, 2] * s2, np.diag(dense), rtol=1e-15)
+
+
+def test_warmstart_energy_step_minimises_the_energy_error():
+    """On a random SPD system: the oracle's gamma is the minimiser of the A-norm error
+    E(g) = (x* - e - g d)^T A (x* - e - g d), found here from three samples of the parabola
+    (dense products, no residual formula); E(gamma) <= E(0) and <= E(1); the exact correction
+    direction gives gamma = 1 and x_hat = x*; a zero correction gives gamma = 0."""
+    r = rng(12)
+    n = 9
+    m = r.standard_normal((n, n))
+    dense = m @ m.T + n * np.eye(n)
+    dense[np.abs(dense) < 0.3] = 0.0
+    dense = (dense + dense.T) / 2 + n * np.eye(n)
+    xs, xm1, xm2 = r.standard_normal((3, n))
+    b = dense @ xs
+    out = r.standard_normal(n).astype(np.float32)
+    s0 = 0.7
+    xh, gamma = C.warmstart_energy_step(*_csr(dense), xm1, xm2, b, out, s0)
+    e, d = 2 * xm1 - xm2, s0 * out.astype(np.float64)
+
+    def E(g):
+        err = xs - e - g * d
+        return float(err @ dense @ err)
+
+    e0, e1, e2 = E(0.0), E(1.0), E(2.0)
+    g_star = (e0 - e1) / (e0 - 2 * e1 + e2) + 0.5   # vertex of the parabola through g = 0, 1, 2
+    assert gamma == pytest.approx(g_star, rel=1e-9)
+    assert E(gamma) <= min(e0, e1) + 1e-12 * e0
+    np.testing.assert_allclose(xh, e + gamma * d, rtol=0, atol=1e-14)
+    # the exact correction (as FP32 output of a unit scale) is taken whole
+    exact = (xs - e).astype(np.float32)
+    xh2, g2 = C.warmstart_energy_step(*_csr(dense), xm1, xm2, dense @ (e + exact.astype(np.float64)), exact, 1.0)
+    assert g2 == pytest.approx(1.0, rel=1e-12)
+    _, g3 = C.warmstart_energy_step(*_csr(dense), xm1, xm2, b, np.zeros(n, np.float32), s0)
+    assert g3 == 0.0

@@ -169,3 +169,40 @@ def test_batched_autotuner_covers_lanes_per_row():
             assert np.linalg.norm(b - a.matvec(x.cpu().numpy())) <= 1.5e-10 * np.linalg.norm(b)
     with pytest.raises(RuntimeError, match="lanes per row"):
         pk.batched_solve(As, bs, xs, tol=1e-10, maxit=10, lanes=3)
+
+
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+def test_batched_config_512_rectangles(precision):
+    """The benchmark's batch itself: 512 shifted 2D Laplacians on rectangles with sides drawn
+    log-uniform from 32 to 256 (up to 65,536 rows each), one launch to 1e-10.  Every system's
+    true residual meets the tolerance; a sample of 16 systems (the largest, the smallest and 14
+    seeded picks) is checked against its own oracle solve: FP64 iterations within +-2 and x
+    after 30 fixed iterations within 1e-9; mixed precision: the error against the FP64
+    oracle's solution."""
+    mats = W.batched_rectangles(512, seed=0)
+    rhs = [W.manufactured(a, seed=k)[1] for k, a in enumerate(mats)]
+    As = [pk.CSRMatrix.from_workload(a) for a in mats]
+    bs = [dev(b) for b in rhs]
+    xs = [torch.zeros(a.n, dtype=torch.float64, device=DEV) for a in mats]
+    ns = np.array([a.n for a in mats])
+    pick = sorted({int(ns.argmax()), int(ns.argmin())}
+                  | set(np.random.default_rng(5).choice(len(mats), 14, replace=False).tolist()))
+    infos = pk.batched_solve(As, bs, xs, tol=1e-10, maxit=20_000, precision=precision)
+    torch.cuda.synchronize()
+    for a, b, x, inf in zip(mats, rhs, xs, infos):
+        assert inf["status"] == pk.PK_OK, (a.name, inf)
+        assert np.linalg.norm(b - a.matvec(x.cpu().numpy())) <= 1.5e-10 * np.linalg.norm(b), a.name
+    for k in pick:
+        ref = O.cg(mats[k], rhs[k], tol=1e-10, maxit=20_000, variant="pipelined")
+        if precision == "fp64":
+            assert abs(infos[k]["iters"] - ref["iters"]) <= 2, (k, infos[k]["iters"], ref["iters"])
+        else:
+            assert rel(xs[k].cpu().numpy(), ref["x"]) <= 1e-8, k
+    if precision == "fp64":
+        pk.batched_solve(As, bs, [x.zero_() for x in xs], tol=0.0, maxit=30)
+        torch.cuda.synchronize()
+        for k in pick:
+            ref = O.cg(mats[k], rhs[k], tol=0.0, maxit=30, variant="pipelined")
+            assert rel(xs[k].cpu().numpy(), ref["x"]) <= 1e-9, k
+    for A in As:
+        A.close()

@@ -8,6 +8,7 @@ import numpy as np
 import pytest
 
 import oracle as O
+from _parity import record
 from paper_1410_4054_gb300 import workloads as W
 
 pytestmark = pytest.mark.gpu
@@ -75,7 +76,11 @@ def test_cg_parity(name, variant, loop):
     fixed = ref["iters"]
     info2, x2, _ = solve(a, b, tol=0.0, maxit=fixed, variant=variant, loop=loop)
     assert info2["status"] == pk.PK_NOT_CONVERGED and info2["iters"] == fixed
-    assert rel(x2, ref["x"]) <= max(1e-9, 10 * oracle_x_spread(a, b, ovar, fixed, ref["x"]))
+    d_x = rel(x2, ref["x"])
+    spread = oracle_x_spread(a, b, ovar, fixed, ref["x"])
+    record("cg_parity", f"{name} {variant} {loop}", "x at the oracle's count", d_x, 1e-9, max(1e-9, 10 * spread),
+           oracle_spread=spread)
+    assert d_x <= max(1e-9, 10 * spread)
 
 
 def oracle_x_spread(a, b, variant, iters, x_ref, nsamp=3):
@@ -339,3 +344,92 @@ def test_nan_in_b_is_reported(solver):
           "cg_mixed": {"precision": "mixed"}}.get(solver, {})
     info = fn(A, dev(b), dev(np.zeros(a.n)), tol=1e-8, maxit=100, **kw)
     assert info["status"] == pk.PK_ERR_NAN and info["iters"] == 0
+
+
+RESIDENT_MATRICES = {
+    "lap3d_64": lambda: W.laplace_3d(64),                     # 262,144 rows, thread-per-row tiles
+    "lap2d_513x400": lambda: W.laplace_2d(513, 400),          # 205,200 rows, ragged blocks, odd n
+    "fe3d_elast_47": lambda: W.fe_elasticity_3d(47),          # 324,864 rows, G-lane tiles
+    "spd_powerlaw_2e5": lambda: W.spd_power_law(200_000, seed=3),  # whole-warp rows, wide columns
+    "dense_rows_3e5": lambda: W.spd_dense_rows(k=550, dense=(0, 7, 150_000, 302_499), per_row=20000),
+}
+
+
+@pytest.mark.parametrize("name", sorted(RESIDENT_MATRICES))
+def test_cg_resident_parity(name):
+    """The grid-resident loop (one cooperative launch, one block per SM): alpha/beta at 1e-12
+    for 20 iterations, iterations +-2, x after the oracle's count at 1e-9 (or 10 x the
+    oracle's own one-ulp spread), true residual; bitwise repeatable."""
+    a = RESIDENT_MATRICES[name]()
+    _, b, _ = W.manufactured(a, seed=0)
+    ref = O.cg(a, b, tol=1e-8, maxit=20_000, variant="pipelined")
+    A = pk.CSRMatrix.from_workload(a)
+    info, x, tr = solve(a, b, A=A, tol=1e-8, maxit=20_000, loop="resident", flags=pk.FLAG_TRUE_RES)
+    assert info["status"] == pk.PK_OK, info
+    assert abs(info["iters"] - ref["iters"]) <= 2, (info["iters"], ref["iters"])
+    assert info["launches"] <= 4  # setup, zero-x guard, the resident loop (+ true residual)
+    k = min(20, ref["iters"] - 1)
+    np.testing.assert_allclose(tr[:k, 0], ref["alpha"][:k], rtol=1e-12, atol=0)
+    np.testing.assert_allclose(tr[:k, 1], ref["beta"][:k], rtol=1e-12, atol=0)
+    np.testing.assert_allclose(tr[:k, 3], ref["res2"][:k], rtol=1e-11, atol=0)
+    assert info["rel_res_true"] <= 1.5e-8
+    fixed = ref["iters"]
+    info2, x2, _ = solve(a, b, A=A, tol=0.0, maxit=fixed, loop="resident")
+    assert info2["status"] == pk.PK_NOT_CONVERGED and info2["iters"] == fixed
+    d_x = rel(x2, ref["x"])
+    spread = oracle_x_spread(a, b, "pipelined", fixed, ref["x"]) if d_x > 1e-9 else 0.0
+    record("cg_resident", name, "x at the oracle's count", d_x, 1e-9, max(1e-9, 10 * spread), oracle_spread=spread)
+    assert d_x <= max(1e-9, 10 * spread)
+    info3, x3, tr3 = solve(a, b, A=A, tol=1e-8, maxit=20_000, loop="resident")
+    assert info3["iters"] == info["iters"] and np.array_equal(x3, x)
+    assert np.array_equal(tr3, tr, equal_nan=True)
+
+
+def test_cg_resident_edge_cases_and_rejections():
+    a = W.laplace_3d(64)
+    _, b, _ = W.manufactured(a, seed=1)
+    A = pk.CSRMatrix.from_workload(a)
+    # b = 0, exact x0, maxit = 0, maxit = 1, not SPD, NaN
+    info, x, _ = solve(a, np.zeros(a.n), A=A, x0=np.ones(a.n), loop="resident")
+    assert info["status"] == pk.PK_OK and info["iters"] == 0 and not x.any()
+    info, _, _ = solve(a, b, A=A, maxit=0, loop="resident")
+    assert info["status"] == pk.PK_NOT_CONVERGED and info["iters"] == 0
+    ref = O.cg(a, b, tol=0.0, maxit=1, variant="pipelined")
+    info, x, _ = solve(a, b, A=A, tol=0.0, maxit=1, loop="resident")
+    assert info["status"] == pk.PK_NOT_CONVERGED and info["iters"] == 1 and rel(x, ref["x"]) <= 1e-13
+    neg = W.CSR(a.n, a.row_ptr, a.col, -a.val)
+    info, _, _ = solve(neg, b, loop="resident")
+    assert info["status"] == pk.PK_NOT_SPD
+    nb = b.copy()
+    nb[77] = np.nan
+    info, _, _ = solve(a, nb, A=A, loop="resident")
+    assert info["status"] == pk.PK_ERR_NAN
+    # the same handle afterwards: exact
+    info, x, _ = solve(a, b, A=A, tol=1e-8, maxit=5000, loop="resident", flags=pk.FLAG_TRUE_RES)
+    assert info["status"] == pk.PK_OK and info["rel_res_true"] <= 1.5e-8
+    # too small for one block per SM taking two tile blocks; other forms rejected
+    small = W.laplace_3d(20)
+    _, sb, _ = W.manufactured(small)
+    with pytest.raises(RuntimeError, match="resident loop needs"):
+        solve(small, sb, loop="resident")
+    for kw in (dict(variant="classical"), dict(flags=pk.FLAG_SELL), dict(flags=pk.FLAG_NO_TMA)):
+        with pytest.raises(RuntimeError, match="PK_LOOP_RESIDENT"):
+            solve(a, b, A=A, loop="resident", **kw)
+    for call, kw in ((pk.cg_solve, dict(precision="mixed")), (pk.cg_solve, dict(precond="jacobi")),
+                     (pk.bicgstab_solve, {}), (pk.gmres_solve, {})):
+        with pytest.raises(RuntimeError, match="RESIDENT|graph or host loop"):
+            call(A, dev(b), dev(np.zeros(a.n)), loop="resident", **kw)
+
+
+def test_cg_resident_bounded_wait_times_out_and_context_stays_usable():
+    """With PK_FLAG_TEST_STALL the CSR producer issues no copies: every consumer's first wait
+    runs out after 1 ms, the blocks record PK_TIMEOUT and leave the loop, the launch ends, and
+    the next solve on the handle is exact."""
+    a = W.laplace_3d(64)
+    _, b, _ = W.manufactured(a, seed=3)
+    A = pk.CSRMatrix.from_workload(a)
+    with pytest.raises(pk.PkError) as err:
+        solve(a, b, A=A, tol=1e-8, maxit=40, loop="resident", wait_ns=1_000_000, flags=pk.FLAG_TEST_STALL)
+    assert err.value.status == pk.PK_TIMEOUT
+    info, _, _ = solve(a, b, A=A, tol=1e-8, maxit=5000, loop="resident", flags=pk.FLAG_TRUE_RES)
+    assert info["status"] == pk.PK_OK and info["rel_res_true"] <= 1.5e-8

@@ -9,6 +9,7 @@ import numpy as np
 import pytest
 
 import oracle as O
+from _parity import record
 from paper_1410_4054_gb300 import workloads as W
 
 pytestmark = pytest.mark.gpu
@@ -82,7 +83,30 @@ def first_cycle_lengths(tr, ref, steps):
     return k_orc, (nxt[0] if nxt else steps)
 
 
-def first_cycle_check(tr, ref, sR, sX, steps):
+def full_R_check(A, a, b, ref, sR, sX, k, case, m=30, **kw):
+    """Every entry R_{j,i}, j <= i <= k, of the first cycle (K-GM-2 forms R_{j,i} for
+    j <= i - 2, K-GM-1 R_{i-1,i}, K-GM-3 R_{i,i}) and xi_1..xi_k, read back after a solve of
+    exactly k steps, against the oracle's first cycle: column i within max(1e-12, 100 x the
+    oracle's own one-ulp spread of that column) relative to max |R|, xi as in the trace."""
+    info, _, _ = solve(a, b, A=A, tol=0.0, maxit=k, restart=m, **kw)
+    assert info["iters"] == k and info["cycles"] == 1
+    R, xi = pk.gmres_cycle_factors(A, m)
+    Ro = ref["R"][:k, :k]
+    scale = np.abs(Ro).max()
+    dcol = np.abs(np.triu(R[:k, :k]) - np.triu(Ro)).max(axis=0) / scale
+    bars = np.maximum(1e-12, 100 * sR[:k])
+    record("gmres_full_R", case, f"R_(j,i), i <= {k} (rel. max|R|)", float(dcol.max()), 1e-12, float(bars.max()),
+           oracle_spread=float(sR[:k].max()))
+    assert np.all(dcol <= bars), (dcol, bars)
+    dxi = np.abs(xi[:k] - ref["xi"][:k])
+    barx = np.maximum(1e-12, 100 * sX[:k])
+    record("gmres_full_R", case, f"xi_i, i <= {k}", float(dxi.max()), 1e-12, float(barx.max()),
+           oracle_spread=float(sX[:k].max()))
+    assert np.all(dxi <= barx), (dxi, barx)
+    assert np.all(np.tril(R[:k, :k], -1) == 0.0)
+
+
+def first_cycle_check(tr, ref, sR, sX, steps, case=""):
     """R_{i-1,i}, R_{i,i} (relative to max |R|) and xi_i (absolute, |xi| <= 1) within
     max(1e-12, 100 x the oracle's own one-ulp spread) at every step of the first cycle; the
     steps where the oracle itself is insensitive meet 1e-12 outright."""
@@ -93,6 +117,12 @@ def first_cycle_check(tr, ref, sR, sX, steps):
     assert abs(k_orc - k_gpu) <= 1, (k_orc, k_gpu)
     k = min(len(sR), steps, k_orc, k_gpu)
     scale = np.abs(R[:k, :k]).max()
+    dR = max(abs(tr[i - 1, 1] - R[i - 1, i - 1]) for i in range(1, k + 1)) / scale
+    dX = max(abs(tr[i - 1, 2] - xi[i - 1]) for i in range(1, k + 1))
+    record("gmres_trace", f"{case} k={k}", "R_(i-1,i), R_(i,i) (rel. max|R|)", dR, 1e-12,
+           float(max(1e-12, 100 * sR[k - 1])), oracle_spread=float(sR[k - 1]))
+    record("gmres_trace", f"{case} k={k}", "xi_i", dX, 1e-12, float(max(1e-12, 100 * sX[k - 1])),
+           oracle_spread=float(sX[k - 1]))
     for i in range(1, k + 1):
         barR = max(1e-12, 100 * sR[i - 1]) * scale
         barX = max(1e-12, 100 * sX[i - 1])
@@ -138,22 +168,33 @@ def test_gmres_parity(name, variant):
                                                                  precond=precond, cgs2=cgs2)
     assert ref["status"] == O.OK
     fl = pk.FLAG_CGS2 if cgs2 else 0
-    info, x, tr = solve(a, b, tol=1e-8, maxit=20_000, restart=m, variant=variant,
+    A = pk.CSRMatrix.from_workload(a)
+    info, x, tr = solve(a, b, A=A, tol=1e-8, maxit=20_000, restart=m, variant=variant,
                         flags=pk.FLAG_TRUE_RES | fl, trace_cap=max(256, ref["iters"] + 8), precond=precond)
     assert info["status"] == pk.PK_OK, info
     assert info["rel_res_true"] <= 1.5e-8
-    first_cycle_check(tr, ref, sR, sX, ref["iters"])
+    case = f"{name} {variant}"
+    first_cycle_check(tr, ref, sR, sX, ref["iters"], case)
     k_orc, k_gpu = first_cycle_lengths(tr, ref, ref["iters"])
+    full_R_check(A, a, b, ref, sR, sX, min(k_orc, k_gpu, len(sR)), case, m=m, variant=variant,
+                 precond=precond, flags=fl)
     if k_orc == k_gpu or ref["iters"] <= min(k_orc, k_gpu):
-        assert abs(info["iters"] - ref["iters"]) <= max(2, 2 * it_spread)
+        d_it = abs(info["iters"] - ref["iters"])
+        record("gmres_parity", case, "iterations", d_it, 2, max(2, 2 * it_spread), oracle_spread=it_spread)
+        assert d_it <= max(2, 2 * it_spread)
         info2, x2, _ = solve(a, b, tol=0.0, maxit=ref["iters"], restart=m, variant=variant, precond=precond,
                              flags=fl)
         assert info2["iters"] == ref["iters"] and info2["cycles"] == fixed["cycles"]
-        assert rel(x2, fixed["x"]) <= max(1e-9, 10 * x_spread)
+        d_x = rel(x2, fixed["x"])
+        record("gmres_parity", case, "x at the oracle's count", d_x, 1e-9, max(1e-9, 10 * x_spread),
+               oracle_spread=x_spread)
+        assert d_x <= max(1e-9, 10 * x_spread)
     else:
         # rounding moved the end of the first cycle by one step (R17): the restart points
         # differ, so the totals may differ by up to one cycle; x is compared over the steps
         # both took (a fixed count that ends the first cycle on both sides)
+        record("gmres_parity", case, "iterations (first cycle ended one step apart)",
+               abs(info["iters"] - ref["iters"]), 2, m, oracle_spread=it_spread)
         assert info["iters"] <= ref["iters"] + m
         k = min(k_orc, k_gpu)
         _, fixed_k, _, _, _, xs_k = oracle_sensitivity(a, b, variant, m, 0.0, k, precond=precond, cgs2=cgs2)
@@ -253,21 +294,28 @@ def test_gmres_edge_cases():
 
 
 def test_gmres_large_convdiff():
-    """128^3 convection-diffusion: the first 10 steps' R and xi against the oracle, then the
-    full GMRES(30) solve checked by its true residual."""
+    """128^3 convection-diffusion: the first 20 steps' full R column and xi (read back after a
+    20-step solve) and the traced R_ii, xi against the oracle, x after 20 steps, then the full
+    GMRES(30) solve checked by its true residual (its step count is compared with the stored
+    oracle solve in test_gpu_fullsize.py)."""
     a = W.convdiff_3d(128)
     _, b, _ = W.manufactured(a)
-    ref = O.gmres(a, b, tol=0.0, maxit=10, m=30)
+    k = 20
+    ref = O.gmres(a, b, tol=0.0, maxit=k, m=30)
     A = pk.CSRMatrix.from_workload(a)
-    info, x10, tr = solve(a, b, A=A, tol=0.0, maxit=10, restart=30)
-    bp = b * (1 + 2.0 ** -52 * W.uniform_pm1(100, a.n))
-    pert = O.gmres(a, bp, tol=0.0, maxit=10, m=30)
-    scale = np.abs(ref["R"][:10, :10]).max()
-    sR = np.maximum.accumulate(np.abs(pert["R"][:10, :10] - ref["R"][:10, :10]).max(axis=0) / scale)
-    sX = np.maximum.accumulate(np.abs(pert["xi"][:10] - ref["xi"][:10]))
-    for i in range(1, 11):
+    info, xk, tr = solve(a, b, A=A, tol=0.0, maxit=k, restart=30)
+    scale = np.abs(ref["R"][:k, :k]).max()
+    sR, sX = np.zeros(k), np.zeros(k)
+    for smp in range(2):
+        bp = b * (1 + 2.0 ** -52 * W.uniform_pm1(100 + smp, a.n))
+        pert = O.gmres(a, bp, tol=0.0, maxit=k, m=30)
+        sR = np.fmax(sR, np.abs(pert["R"][:k, :k] - ref["R"][:k, :k]).max(axis=0) / scale)
+        sX = np.fmax(sX, np.abs(pert["xi"][:k] - ref["xi"][:k]))
+    sR, sX = np.maximum.accumulate(sR), np.maximum.accumulate(sX)
+    for i in range(1, k + 1):
         assert abs(tr[i - 1, 1] - ref["R"][i - 1, i - 1]) <= max(1e-12, 100 * sR[i - 1]) * scale
         assert abs(tr[i - 1, 2] - ref["xi"][i - 1]) <= max(1e-12, 100 * sX[i - 1])
-    assert rel(x10, ref["x"]) <= 1e-9
+    full_R_check(A, a, b, ref, sR, sX, k, "convdiff_128")
+    assert rel(xk, ref["x"]) <= 1e-9
     info, _, _ = solve(a, b, A=A, tol=1e-8, maxit=20_000, restart=30, flags=pk.FLAG_TRUE_RES)
     assert info["status"] == pk.PK_OK and info["rel_res_true"] <= 1.5e-8

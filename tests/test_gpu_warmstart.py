@@ -100,6 +100,30 @@ def test_warmstart_input_matches_oracle():
     assert np.mean(got != ref) < 1e-3
 
 
+def test_warmstart_energy_step_matches_oracle():
+    """pk_warmstart_apply_energy against the oracle on the transient operator: gamma to 1e-12
+    relative, x_hat to 1e-13 relative (same FP32 correction, FP64 sums in another order)."""
+    from paper_1410_4054_gb300 import workloads as W
+
+    T = W.transient_heat(16, steps=3, seed=2)
+    A = pk.CSRMatrix.from_workload(T.M)
+    r = np.random.default_rng(7)
+    xm1, xm2 = r.standard_normal((2, T.M.n))
+    b = T.M.matvec(xm1 + 0.01 * r.standard_normal(T.M.n))
+    out = (0.01 * r.standard_normal(T.M.n)).astype(np.float32)
+    scales = torch.tensor([0.3, 1.0, 1.0], dtype=torch.float64, device=DEV)
+    xh = torch.zeros(T.M.n, dtype=torch.float64, device=DEV)
+    gamma = torch.zeros(1, dtype=torch.float64, device=DEV)
+    scratch = torch.zeros(pk.warmstart_scratch_doubles(), dtype=torch.float64, device=DEV)
+    dv = lambda v: torch.from_numpy(np.ascontiguousarray(v)).to(DEV)  # noqa: E731
+    for _ in range(2):  # twice in a row: the scratch counter is reset by each call
+        pk.warmstart_apply_energy(A, dv(out), dv(xm1), dv(xm2), dv(b), scales, xh, gamma, scratch)
+        torch.cuda.synchronize()
+        ref, g = C.warmstart_energy_step(T.M.row_ptr, T.M.col, T.M.val, xm1, xm2, b, out, 0.3)
+        assert gamma.item() == pytest.approx(g, rel=1e-12)
+        assert rel_l2(xh.cpu().numpy(), ref) <= 1e-13
+
+
 def _grid_operator(dims, r):
     """A symmetric 7-point operator on the grid: 1D second differences summed over the three
     axes with random positive weights, plus 1 on the diagonal (an implicit time step)."""
@@ -199,6 +223,8 @@ def test_transient_learned_warm_start():
     assert res["learned_max_kept_ratio"] <= 1.0 and res["extrap_max_kept_ratio"] <= 1.0
     assert res["learned_mean_iters"] <= res["baseline_mean_iters"]
     assert res["extrap_mean_iters"] <= res["baseline_mean_iters"]
+    assert res["energy_max_kept_ratio"] <= 1.0
+    assert res["energy_mean_iters"] <= res["baseline_mean_iters"]
 
 
 def test_checkpoint_round_trip_and_resume(tmp_path):

@@ -156,6 +156,34 @@ def test_cg_table2_bound_classical_vs_pipelined():
         assert abs(rc - rp) / rc < 1e-10
 
 
+def test_nonsymmetric_table2_bounds_classical_vs_pipelined():
+    """Table 2 / Sec. 4.3, nonsymmetric rows: after 30 iterations the relative difference of
+    the classical and pipelined residual norms.  The table's GMRES column reaches 5.3e-8
+    (rma10), although the text puts CG and GMRES below 1e-10; the pin takes the table's own
+    maximum.  BiCGStab differs by up to 0.41 there, and the text bounds it by 1.  On synthetic
+    nonsymmetric matrices of the same shapes (upwind convection-diffusion, power-law rows,
+    P1 triangles, a badly scaled copy) the oracle's two forms stay within those bounds.  The
+    measure compares unconverged residuals: every case is still above 1e-6 relative after 30
+    steps (a solve that reaches the rounding floor compares noise)."""
+    paper = np.loadtxt("tests/golden/table2_residual_diffs_nonsym.txt", usecols=(1, 2), comments="#")
+    assert paper.shape == (7, 2)
+    bicg_max, gmres_max = paper[:, 0].max(), paper[:, 1].max()
+    assert bicg_max == 0.41 and gmres_max == 5.3e-8
+    for a in (W.convdiff_3d(20), W.power_law(5000, seed=3), W.fe_poisson_2d(6),
+              W.diag_scaled(W.convdiff_3d(12), seed=1, spread=100.0)):
+        _, b, _ = W.manufactured(a, seed=1)
+
+        def res(x):
+            return np.linalg.norm(b - O.spmv(a, x))
+
+        g = [res(O.gmres(a, b, tol=0.0, maxit=30, m=30, variant=v)["x"]) for v in ("classical", "pipelined")]
+        assert g[0] > 1e-6 * np.linalg.norm(b), a.name
+        assert abs(g[0] - g[1]) / g[0] < gmres_max, a.name
+        s = [res(O.bicgstab(a, b, tol=0.0, maxit=30, variant=v)["x"]) for v in ("classical", "pipelined")]
+        assert s[0] > 1e-6 * np.linalg.norm(b), a.name
+        assert np.isfinite(s).all() and abs(s[0] - s[1]) / s[0] < 1.0, a.name
+
+
 # ------------------------------------------------------------------------------- BiCGStab
 
 NONSYM = [lambda: W.convdiff_3d(4), lambda: W.power_law(60, seed=2, lmax=12, mean=6),

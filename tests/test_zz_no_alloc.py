@@ -1,16 +1,18 @@
 """The allocation-free fused SpMV + inner product (pk_spmv_dot_noalloc).
 
-It is for callers that cannot allocate device memory where they need the product (inside
-stream capture, with a fixed memory budget): it takes the caller's device CSR arrays and
-keeps its scratch in a fixed device array.  Checked through the C ABI against the existing
-entry point (pk_spmv_dot on a pk_csr handle) on two calls in a row.  This file sorts last so
-that a run stopping at the first failure has run everything else first.
+It is for callers that cannot allocate device memory where they need the product (a memory
+budget fixed in advance, no access to the process's caching allocator): it takes the caller's
+device CSR arrays and keeps its scratch in a fixed device array.  Checked through the C ABI
+against the existing entry point (pk_spmv_dot on a pk_csr handle) and against the oracle's
+product and inner product, on two calls in a row.  This file sorts last so that a run
+stopping at the first failure has run everything else first.
 """
 import ctypes as C
 
 import numpy as np
 import pytest
 
+import oracle as O
 from paper_1410_4054_gb300 import workloads as W
 
 pytestmark = pytest.mark.gpu
@@ -47,6 +49,12 @@ def test_noalloc_matches_existing_entry_point(make):
         assert torch.equal(q, ref_q)  # same row products, same order
         scale = float(torch.dot(p.abs(), ref_q.abs()))
         assert abs(r.item() - ref_r.item()) <= 1e-12 * scale
+        # and the oracle's A p (rows summed left to right) and <p, A p>
+        ph = p.cpu().numpy()
+        qo = O.spmv(a, ph)
+        absrow = W.CSR(a.n, a.row_ptr, a.col, np.abs(a.val)).matvec(np.abs(ph))
+        assert np.all(np.abs(q.cpu().numpy() - qo) <= 1e-14 * absrow + 1e-300)
+        assert abs(r.item() - O.dot(ph, qo)) <= 1e-12 * float(np.dot(np.abs(ph), absrow))
     A.close()
 
 
@@ -56,6 +64,13 @@ def test_noalloc_rejects_sizes_beyond_the_limit():
                                       C.c_void_p(r.data_ptr()), None)
     assert st == pk.PK_ERR_ARG
     assert "PK_NOALLOC_MAX_N" in pk.lib().pk_last_error().decode()
+    # q must not be p (rows read p at other rows' columns while q is written)
+    p = torch.zeros(8, dtype=torch.float64, device=DEV)
+    rp = _dev(np.arange(9), np.int32)
+    st = pk.lib().pk_spmv_dot_noalloc(8, C.c_void_p(rp.data_ptr()), C.c_void_p(rp.data_ptr()),
+                                      C.c_void_p(p.data_ptr()), C.c_void_p(p.data_ptr()),
+                                      C.c_void_p(p.data_ptr()), C.c_void_p(r.data_ptr()), None)
+    assert st == pk.PK_ERR_ARG and "q must not be p" in pk.lib().pk_last_error().decode()
     # n = 0: result 0, nothing else touched
     r.fill_(5.0)
     pk.spmv_dot_noalloc(0, None, None, None, None, None, r)
