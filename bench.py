@@ -66,6 +66,9 @@ def parse():
                          "elasticity on --k^3 cubes")
     ap.add_argument("--sell", action="store_true", help="--mode kernels, cg: K-CG-S on the SELL-C-sigma copy")
     ap.add_argument("--n", type=int, default=1_000_000)
+    ap.add_argument("--lanes", type=int, default=0,
+                    help="--mode kernels, batched: the engine (0 row engine automatic, 1/2/4/8 lanes per "
+                         "row, -1 tile engine, -2 cluster engine)")
     ap.add_argument("--no-forms", action="store_true",
                     help="skip the BiCGStab / GMRES / batched / mixed-precision lines")
     return ap.parse_args()
@@ -82,7 +85,8 @@ def run_kernels(args):
         As = [pk.CSRMatrix.from_workload(m) for m in mats]
         bs = [torch.from_numpy(W.manufactured(m, seed=k)[1]).cuda() for k, m in enumerate(mats)]
         xs = [torch.zeros(m.n, dtype=torch.float64, device="cuda") for m in mats]
-        infos = pk.batched_solve(As, bs, xs, tol=0.0, maxit=args.iters, precision=args.precision)
+        infos = pk.batched_solve(As, bs, xs, tol=0.0, maxit=args.iters, precision=args.precision,
+                                 lanes=args.lanes)
         torch.cuda.synchronize()
         print(json.dumps({"mode": "kernels", "solver": "batched", "systems": len(mats),
                           "iters": infos[0]["iters"], "solve_ms": infos[0]["solve_ms"]}))
@@ -614,7 +618,7 @@ def bench_forms(pk, torch, dev, args, emit=None):
         brow[f"{prec}_ms"] = ms
         brow[f"{prec}_solves_per_s"] = len(mats) / (ms * 1e-3)
         brow[f"{prec}_all_converged"] = all(i["status"] == pk.PK_OK for i in infos)
-        brow[f"{prec}_config"] = list(pk.batched_last_config())
+        brow[f"{prec}_config"] = list(pk.batched_last_config()) + [pk.batched_last_lanes()]
         # algorithmic bytes of every system's iterations (FP64: 12 nnz + 76 n per iteration;
         # mixed: the FP32 inner iteration, 8 nnz + 40 n) over the launch time
         per_it = [(12 * m.nnz + 76 * m.n) if prec == "fp64" else (8 * m.nnz + 40 * m.n) for m in mats]

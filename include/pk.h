@@ -138,7 +138,9 @@ typedef struct {
                           takes none) */
   int32_t lanes;       /* pk_batched_solve: lanes per matrix row in the row products (1, 2, 4
                           or 8; 0 = automatic: from the batch's mean row length, or tuned with
-                          the block shape under PK_FLAG_AUTOTUNE).  Other solvers ignore it */
+                          the block shape under PK_FLAG_AUTOTUNE; -1 = the tile engine, -2 = the
+                          cluster engine).
+                          Other solvers ignore it */
   int64_t wait_ns;     /* bound, in ns, on every device-side pipeline wait that should make
                           progress (0 = 2 s).  A wait that runs out ends the solve with
                           PK_TIMEOUT after the kernel has drained its own copies; the context
@@ -305,19 +307,43 @@ pk_status pk_gmres_cycle_factors(const pk_csr* A, int32_t m, double* R, double* 
  * leaves the queue (per-system convergence mask).  A[k], b[k], x[k] for k < nsys; b and x
  * must be DEVICE pointers.  opts: tol, maxit (per system; MIXED: total inner iterations),
  * precision PK_PREC_FP64 or PK_PREC_MIXED (FP32 SpMV/vectors inside FP64 iterative
- * refinement, inner tolerance 1e-4, at most 20 refinement steps), lanes (per matrix row),
- * flags PK_FLAG_AUTOTUNE.  PK_FLAG_SELL, PK_FLAG_CGS2 and a preconditioner return
- * PK_ERR_ARG; variant, loop and the other flags are ignored (always pipelined CG).
- * infos: nsys entries or NULL (iters, status, cycles = refinement steps, rel_res_est).
- * Returns PK_OK if every system converged, else the first failing system's status.
+ * refinement, inner tolerance 1e-4, at most 20 refinement steps), lanes, wait_ns, flags
+ * PK_FLAG_AUTOTUNE.  Two engines:
+ *   - the row engine (default): plain row loops, lanes = 1, 2, 4 or 8 lanes per row (0 = from
+ *     the batch's mean row length), FP64 or MIXED;
+ *   - lanes = -1, FP64, every system with CSR tiles: the tile engine -- each block (288
+ *     threads, 2 per SM) streams its system's CSR tiles and vectors through shared memory with
+ *     bulk copies, as the single-system kernels do (bounded waits: PK_TIMEOUT).  Measured
+ *     slower than the row engine on small systems (18 resident warps per SM against 64 hide
+ *     less of the gather latency), so it is an option and a candidate of the tuner;
+ *   - lanes = -2, FP64, every system of at most 65536 rows: the cluster engine -- a system of
+ *     n rows is solved by a thread-block cluster of C = 1, 2, 4, 8 or 16 CTAs holding p, x, r
+ *     and Ap in the CTAs' shared memory, the SpMV gathering p across the cluster (distributed
+ *     shared memory), so that per iteration only the matrix is read from global memory.  CTA
+ *     shapes: 256 threads and up to 2048 rows (2 per SM), the smallest C with C * 2048 >= n;
+ *     systems of more than 32768 rows on CTAs of 512 threads and up to 4096 rows (1 per SM).
+ *     One persistent cluster launch per (shape, C) class, the launches on streams of their
+ *     own that join the caller's stream.
+ * PK_FLAG_AUTOTUNE (lanes 0) times the tile engine and the cluster engine (FP64, the cluster
+ * engine aiming at 1024, 2048 and 4096 rows per CTA: CTAs of 128, 256, 512 threads) and every
+ * (block size, blocks per SM, lanes per row) of the row engine on the batch and keeps the
+ * fastest.  PK_FLAG_SELL, PK_FLAG_CGS2 and a
+ * preconditioner return PK_ERR_ARG; variant, loop and the other flags are ignored (always
+ * pipelined CG).  infos: nsys entries or NULL (iters, status, cycles = refinement steps,
+ * rel_res_est).  Returns PK_OK if every system converged, else the first failing system's
+ * status.
  */
 pk_status pk_batched_solve(int32_t nsys, pk_csr* const* A, const double* const* b,
                            double* const* x, const pk_opts* opts, pk_info* infos, void* stream);
 
-/* Block size and blocks per SM used by the last pk_batched_solve call in this process. */
+/* Block size and blocks per SM used by the last pk_batched_solve call in this process
+ * (the cluster engine: the CTA shape of its default or tuned rows per CTA, e.g. 256 threads and
+ * 2 blocks per SM for 2048 rows). */
 pk_status pk_batched_last_config(int32_t* block, int32_t* blocks_per_sm);
 
-/* Lanes per row (1, 2, 4 or 8) that the last pk_batched_solve call ran with. */
+/* Lanes per row (1, 2, 4 or 8) that the last pk_batched_solve call ran with; -1 = the tile
+ * engine (pk_batched_last_config then gives 288 threads, 2 blocks per SM), -2 = the cluster
+ * engine. */
 pk_status pk_batched_last_lanes(int32_t* lanes);
 
 /*

@@ -191,6 +191,27 @@ __device__ __forceinline__ void finish(DevState* st, int status) {
 
 // Host-side maxima of the tile engine (defined in pk_tile.cuh).
 // Common kernel arguments of the row-parallel kernels.
+// One system of a batch as the cluster engine of the batched solver sees it: the CSR copy of
+// its handle, b, x, and the results written back by the cluster that solved it.
+struct BatchClSys {
+  int32_t n;
+  const int32_t* rp;
+  const int32_t* ci;
+  const double* va;
+  const double* b;
+  double* x;
+  int32_t iters, status;
+  double rel_res;
+};
+
+// The batched solver's cluster engine (pk_batched_cluster.cu): shapes 0, 1, 2 are CTAs of
+// 512 threads and up to 4096 rows, 256 and 2048, 128 and 1024.
+constexpr int kBcShapeCount = 3;
+int batched_cluster_max_rows(int shape);
+int batched_cluster_capacity(int shape, int C);
+pk_status launch_batched_cluster(int shape, BatchClSys* sys, int first, int end, int* queue, int C, double tol,
+                                 int maxit, cudaStream_t s);
+
 struct RowArgs {
   int32_t n;
   const int32_t* rp;      // row pointers

@@ -324,6 +324,15 @@ __device__ __forceinline__ double gather(const double* __restrict__ x, int c) { 
 __device__ __forceinline__ float gather(const float* __restrict__ x, int c) { return __ldg(x + c); }
 template <class VT>
 __device__ __forceinline__ VT gather(CohVec<VT> x, int c) { return __ldcg(x.p + c); }
+// BlockVec: a vector that only the reading block writes (the batched solver: one block owns a
+// system's vectors).  Plain L1-cached loads see the block's own earlier stores after a block
+// barrier; the non-coherent path might not.
+template <class VT>
+struct BlockVec {
+  const VT* p;
+};
+template <class VT>
+__device__ __forceinline__ VT gather(BlockVec<VT> x, int c) { return __ldca(x.p + c); }
 
 template <class VT>
 struct CsrTilesT {
@@ -474,9 +483,11 @@ __device__ __forceinline__ void block_row_chunk(int row, int zc0, int zr1, VT* s
 }
 
 // IRR = false compiles the thread-per-row path only (matrices without long rows).
+// csr_tiles_range runs the tiles [t0, t1) of T in this block; csr_tiles runs the block's own
+// range [T.blk_tile[blockIdx.x], T.blk_tile[blockIdx.x + 1]).
 template <bool IRR, class VT, class XP, class Setup, class RowDone>
-__device__ __forceinline__ bool csr_tiles(const CsrTilesT<VT>& T, unsigned char* smem, DevState* st,
-                                          Setup&& setup, XP x, RowDone&& row_done) {
+__device__ __forceinline__ bool csr_tiles_range(const CsrTilesT<VT>& T, int t0, int t1, unsigned char* smem,
+                                                DevState* st, Setup&& setup, XP x, RowDone&& row_done) {
   constexpr int kVaUnit = 16 / (int)sizeof(VT);  // values per 16-byte copy unit
   uint64_t* full = reinterpret_cast<uint64_t*>(smem + kCsrStages * kStageBytes);
   uint64_t* empty = full + kCsrStages;
@@ -493,7 +504,6 @@ __device__ __forceinline__ bool csr_tiles(const CsrTilesT<VT>& T, unsigned char*
     chunk_cnt = 0;
   }
   __syncthreads();
-  const int t0 = T.blk_tile[blockIdx.x], t1 = T.blk_tile[blockIdx.x + 1];
   const int ntiles = t1 - t0;
   auto stage_rp = [&](int s) { return reinterpret_cast<int32_t*>(smem + (size_t)s * kStageBytes); };
   auto stage_va = [&](int s) {
@@ -657,6 +667,13 @@ __device__ __forceinline__ bool csr_tiles(const CsrTilesT<VT>& T, unsigned char*
     if (lane == 0) mbar_arrive(&empty[s]);
   }
   return live;
+}
+
+template <bool IRR, class VT, class XP, class Setup, class RowDone>
+__device__ __forceinline__ bool csr_tiles(const CsrTilesT<VT>& T, unsigned char* smem, DevState* st,
+                                          Setup&& setup, XP x, RowDone&& row_done) {
+  return csr_tiles_range<IRR>(T, T.blk_tile[blockIdx.x], T.blk_tile[blockIdx.x + 1], smem, st,
+                              static_cast<Setup&&>(setup), x, static_cast<RowDone&&>(row_done));
 }
 
 // Two row products from a shared-memory window.  Each pass loads up to 8 entries of both

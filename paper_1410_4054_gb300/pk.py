@@ -316,7 +316,8 @@ def csr_plan(row_ptr, sms=152) -> dict:
 
 
 def batched_last_lanes() -> int:
-    """Lanes per row of the last pk_batched_solve call."""
+    """Lanes per row of the last pk_batched_solve call (-1: the tile engine, -2: the cluster
+    engine)."""
     v = C.c_int32()
     _check(lib().pk_batched_last_lanes(C.byref(v)), "pk_batched_last_lanes")
     return v.value

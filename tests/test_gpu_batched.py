@@ -55,7 +55,17 @@ def test_batched_fp64_matches_single_system_oracle(autotune):
         assert rel(x.cpu().numpy(), ref["x"]) <= 1e-9, a.name
     if autotune:
         blk, per = pk.batched_last_config()
-        assert blk in (128, 256, 512, 1024) and per in (1, 2, 4, 8)
+        assert (blk, per) == (288, 2) or (blk in (128, 256, 512, 1024) and per in (1, 2, 4, 8))
+    # the tile engine (lanes = -1) on the same batch: the same oracle bars
+    xs = [torch.zeros(a.n, dtype=torch.float64, device=DEV) for a in mats]
+    infos = pk.batched_solve(As, bs, xs, tol=0.0, maxit=25, lanes=-1)
+    torch.cuda.synchronize()
+    assert pk.batched_last_lanes() == -1 and pk.batched_last_config() == (288, 2)
+    for a, b, x, inf in zip(mats, rhs, xs, infos):
+        ref = O.cg(a, b, tol=0.0, maxit=25, variant="pipelined")
+        if ref["status"] == O.NOT_CONVERGED:
+            assert inf["iters"] == ref["iters"], (a.name, inf, ref["iters"])
+        assert rel(x.cpu().numpy(), ref["x"]) <= 1e-9, a.name
     # to tolerance: iterations within 2 of the oracle, true residual within tol
     xs = [torch.zeros(a.n, dtype=torch.float64, device=DEV) for a in mats]
     infos = pk.batched_solve(As, bs, xs, tol=1e-10, maxit=5000)
@@ -164,21 +174,23 @@ def test_batched_autotuner_covers_lanes_per_row():
                                  flags=pk.FLAG_AUTOTUNE)
         torch.cuda.synchronize()
         assert all(i["status"] == pk.PK_OK for i in infos)
-        assert pk.batched_last_lanes() in (1, 2, 4, 8)
+        assert pk.batched_last_lanes() in ((-2, -1, 1, 2, 4, 8) if prec == "fp64" else (1, 2, 4, 8))  # -1 tiles, -2 clusters
         for a, b, x in zip(mats, rhs, xs):
             assert np.linalg.norm(b - a.matvec(x.cpu().numpy())) <= 1.5e-10 * np.linalg.norm(b)
     with pytest.raises(RuntimeError, match="lanes per row"):
         pk.batched_solve(As, bs, xs, tol=1e-10, maxit=10, lanes=3)
+    with pytest.raises(RuntimeError, match="tile engine"):
+        pk.batched_solve(As, bs, xs, tol=1e-10, maxit=10, lanes=-1, precision="mixed")
 
 
-@pytest.mark.parametrize("precision", ["fp64", "mixed"])
-def test_batched_config_512_rectangles(precision):
+@pytest.mark.parametrize("precision,lanes", [("fp64", 0), ("fp64", -2), ("mixed", 0)])
+def test_batched_config_512_rectangles(precision, lanes):
     """The benchmark's batch itself: 512 shifted 2D Laplacians on rectangles with sides drawn
-    log-uniform from 32 to 256 (up to 65,536 rows each), one launch to 1e-10.  Every system's
-    true residual meets the tolerance; a sample of 16 systems (the largest, the smallest and 14
-    seeded picks) is checked against its own oracle solve: FP64 iterations within +-2 and x
-    after 30 fixed iterations within 1e-9; mixed precision: the error against the FP64
-    oracle's solution."""
+    log-uniform from 32 to 256 (up to 65,536 rows each), one launch to 1e-10 (FP64: the row
+    engine and the cluster engine).  Every system's true residual meets the tolerance; a
+    sample of 16 systems (the largest, the smallest and 14 seeded picks) is checked against its
+    own oracle solve: FP64 iterations within +-2 and x after 30 fixed iterations within 1e-9;
+    mixed precision: the error against the FP64 oracle's solution."""
     mats = W.batched_rectangles(512, seed=0)
     rhs = [W.manufactured(a, seed=k)[1] for k, a in enumerate(mats)]
     As = [pk.CSRMatrix.from_workload(a) for a in mats]
@@ -187,8 +199,10 @@ def test_batched_config_512_rectangles(precision):
     ns = np.array([a.n for a in mats])
     pick = sorted({int(ns.argmax()), int(ns.argmin())}
                   | set(np.random.default_rng(5).choice(len(mats), 14, replace=False).tolist()))
-    infos = pk.batched_solve(As, bs, xs, tol=1e-10, maxit=20_000, precision=precision)
+    infos = pk.batched_solve(As, bs, xs, tol=1e-10, maxit=20_000, precision=precision, lanes=lanes)
     torch.cuda.synchronize()
+    if lanes:
+        assert pk.batched_last_lanes() == lanes
     for a, b, x, inf in zip(mats, rhs, xs, infos):
         assert inf["status"] == pk.PK_OK, (a.name, inf)
         assert np.linalg.norm(b - a.matvec(x.cpu().numpy())) <= 1.5e-10 * np.linalg.norm(b), a.name
@@ -199,10 +213,138 @@ def test_batched_config_512_rectangles(precision):
         else:
             assert rel(xs[k].cpu().numpy(), ref["x"]) <= 1e-8, k
     if precision == "fp64":
-        pk.batched_solve(As, bs, [x.zero_() for x in xs], tol=0.0, maxit=30)
+        pk.batched_solve(As, bs, [x.zero_() for x in xs], tol=0.0, maxit=30, lanes=lanes)
         torch.cuda.synchronize()
         for k in pick:
             ref = O.cg(mats[k], rhs[k], tol=0.0, maxit=30, variant="pipelined")
             assert rel(xs[k].cpu().numpy(), ref["x"]) <= 1e-9, k
     for A in As:
         A.close()
+
+
+def test_batched_tile_engine_irregular_rows_and_unaligned_x():
+    """The tile engine on P1 elasticity systems (G-lane tiles) and power-law SPD systems
+    (whole-warp rows), with every other x 8 bytes off a 16-byte boundary (its update then
+    runs without bulk copies of x): x after 20 fixed iterations matches each system's oracle
+    solve within max(1e-9, 10 x the oracle's one-ulp spread), and to tolerance every system
+    converges with the oracle's iteration count (+-2)."""
+    mats, rhs = make_fe_batch(nsys=12, seed=2)
+    mats += [W.spd_power_law(3000 + 1000 * k, seed=k) for k in range(4)]
+    rhs += [W.manufactured(a, seed=40 + k)[1] for k, a in enumerate(mats[12:])]
+    As = [pk.CSRMatrix.from_workload(a) for a in mats]
+    bs = [dev(b) for b in rhs]
+    bufs = [torch.zeros(a.n + 1, dtype=torch.float64, device=DEV) for a in mats]
+    xs = [buf[k % 2:k % 2 + a.n] for k, (buf, a) in enumerate(zip(bufs, mats))]
+    pk.batched_solve(As, bs, xs, tol=0.0, maxit=20, lanes=-1)
+    torch.cuda.synchronize()
+    assert pk.batched_last_lanes() == -1
+    for a, b, x in zip(mats, rhs, xs):
+        ref = O.cg(a, b, tol=0.0, maxit=20, variant="pipelined")
+        bar = max(1e-9, 10 * oracle_x_spread(a, b, 20, ref["x"]))
+        assert rel(x.cpu().numpy(), ref["x"]) <= bar, a.name
+    for x in xs:
+        x.zero_()
+    infos = pk.batched_solve(As, bs, xs, tol=1e-10, maxit=5000, lanes=-1)
+    torch.cuda.synchronize()
+    for a, b, x, inf in zip(mats, rhs, xs, infos):
+        ref = O.cg(a, b, tol=1e-10, maxit=5000, variant="pipelined")
+        assert inf["status"] == pk.PK_OK and abs(inf["iters"] - ref["iters"]) <= 2, (a.name, inf["iters"], ref["iters"])
+        assert np.linalg.norm(b - a.matvec(x.cpu().numpy())) <= 1.5e-10 * np.linalg.norm(b)
+    for buf, k in zip(bufs, range(len(bufs))):
+        assert buf[0 if k % 2 else -1].item() == 0.0  # nothing written outside x
+
+
+def test_batched_tile_engine_bounded_wait_times_out():
+    """PK_FLAG_TEST_STALL: the CSR producer issues no copies, every system's first wait runs
+    out after 1 ms, the systems report PK_TIMEOUT, and the next batch on the same handles is
+    exact."""
+    mats, rhs = make_batch(nsys=6, seed=7)
+    As = [pk.CSRMatrix.from_workload(a) for a in mats]
+    bs = [dev(b) for b in rhs]
+    xs = [torch.zeros(a.n, dtype=torch.float64, device=DEV) for a in mats]
+    with pytest.raises(pk.PkError) as err:
+        pk.batched_solve(As, bs, xs, tol=1e-10, maxit=100, wait_ns=1_000_000, flags=pk.FLAG_TEST_STALL, lanes=-1)
+    assert err.value.status == pk.PK_TIMEOUT
+    torch.cuda.synchronize()
+    infos = pk.batched_solve(As, bs, [x.zero_() for x in xs], tol=1e-10, maxit=5000, lanes=-1)
+    for a, b, x, inf in zip(mats, rhs, xs, infos):
+        assert inf["status"] == pk.PK_OK
+        if np.any(b):
+            assert np.linalg.norm(b - a.matvec(x.cpu().numpy())) <= 1.5e-10 * np.linalg.norm(b)
+
+
+def make_cluster_batch():
+    """Members for every cluster size of the cluster engine (1 to 16 CTAs of up to 4096 rows):
+    the small batch (with its 1 x 1 and zero right-hand-side members), P1 elasticity systems
+    (rows of up to 45 nonzeros), power-law SPD systems and shifted Laplacians of 5,000 to
+    65,536 rows (up to 4,096 rows on each of 16 CTAs)."""
+    mats, rhs = make_batch(nsys=10, seed=11)
+    fe, fe_rhs = make_fe_batch(nsys=4, seed=6)
+    mats += fe
+    rhs += fe_rhs
+    extra = [W.spd_power_law(5000, seed=3), W.spd_power_law(9000, seed=4),
+             W.laplace_2d(130, 130, shift=0.05), W.laplace_2d(181, 181, shift=0.02),
+             W.laplace_2d(256, 256, shift=0.01)]
+    mats += extra
+    rhs += [W.manufactured(a, seed=60 + k)[1] for k, a in enumerate(extra)]
+    return mats, rhs
+
+
+def test_batched_cluster_engine_matches_the_oracle():
+    """The cluster engine (lanes = -2): x after 25 fixed iterations matches each system's
+    oracle solve within max(1e-9, 10 x the oracle's one-ulp spread); to tolerance every system
+    converges with the oracle's iteration count (+-2) and meets the tolerance in its true
+    residual; the zero right-hand side gives x = 0."""
+    mats, rhs = make_cluster_batch()
+    As = [pk.CSRMatrix.from_workload(a) for a in mats]
+    bs = [dev(b) for b in rhs]
+    xs = [torch.zeros(a.n, dtype=torch.float64, device=DEV) for a in mats]
+    infos = pk.batched_solve(As, bs, xs, tol=0.0, maxit=25, lanes=-2)
+    torch.cuda.synchronize()
+    assert pk.batched_last_lanes() == -2 and pk.batched_last_config() == (256, 2)
+    for a, b, x, inf in zip(mats, rhs, xs, infos):
+        ref = O.cg(a, b, tol=0.0, maxit=25, variant="pipelined")
+        if ref["status"] == O.NOT_CONVERGED:
+            assert inf["iters"] == ref["iters"], (a.name, inf, ref["iters"])
+        bar = max(1e-9, 10 * oracle_x_spread(a, b, 25, ref["x"])) if np.any(b) else 0.0
+        assert rel(x.cpu().numpy(), ref["x"]) <= bar, a.name
+    xs = [torch.zeros(a.n, dtype=torch.float64, device=DEV) for a in mats]
+    infos = pk.batched_solve(As, bs, xs, tol=1e-10, maxit=5000, lanes=-2)
+    torch.cuda.synchronize()
+    for a, b, x, inf in zip(mats, rhs, xs, infos):
+        ref = O.cg(a, b, tol=1e-10, maxit=5000, variant="pipelined")
+        assert inf["status"] == pk.PK_OK, (a.name, inf)
+        assert abs(inf["iters"] - ref["iters"]) <= 2, (a.name, inf["iters"], ref["iters"])
+        xh = x.cpu().numpy()
+        if np.any(b):
+            assert np.linalg.norm(b - a.matvec(xh)) <= 1.5e-10 * np.linalg.norm(b)
+        else:
+            assert not xh.any()
+    for A in As:
+        A.close()
+
+
+def test_batched_cluster_engine_reports_members_and_rejects():
+    """A negated (negative definite) member reports PK_NOT_SPD while the others converge;
+    mixed precision and a system of more than 65,536 rows are rejected; maxit = 0 leaves x."""
+    mats, rhs = make_batch(nsys=6, seed=5)
+    mats[0] = W.CSR(mats[0].n, mats[0].row_ptr, mats[0].col, -mats[0].val)
+    As = [pk.CSRMatrix.from_workload(a) for a in mats]
+    bs = [dev(b) for b in rhs]
+    xs = [torch.zeros(a.n, dtype=torch.float64, device=DEV) for a in mats]
+    infos = pk.batched_solve(As, bs, xs, tol=1e-10, maxit=2000, lanes=-2)
+    assert infos[0]["status"] == pk.PK_NOT_SPD
+    assert all(i["status"] == pk.PK_OK for i in infos[1:])
+    with pytest.raises(RuntimeError, match="cluster engine"):
+        pk.batched_solve(As, bs, xs, tol=1e-10, maxit=10, lanes=-2, precision="mixed")
+    big = W.laplace_2d(257, 256, shift=0.1)
+    Ab = pk.CSRMatrix.from_workload(big)
+    bb = dev(W.manufactured(big, seed=1)[1])
+    xb = torch.zeros(big.n, dtype=torch.float64, device=DEV)
+    with pytest.raises(RuntimeError, match="65536 rows"):
+        pk.batched_solve([Ab], [bb], [xb], tol=1e-10, maxit=10, lanes=-2)
+    # maxit = 0: x stays as given, except x = 0 for the zero right-hand side (the last member)
+    x0 = [torch.full((a.n,), 0.5, dtype=torch.float64, device=DEV) for a in mats[1:]]
+    infos = pk.batched_solve(As[1:], bs[1:], x0, tol=1e-10, maxit=0, lanes=-2)
+    assert all(bool((x == 0.5).all()) for x in x0[:-1]) and not x0[-1].any()
+    assert infos[-1]["status"] == pk.PK_OK and all(i["status"] == pk.PK_NOT_CONVERGED for i in infos[:-1])
