@@ -102,9 +102,9 @@ enum {
 #define PK_FLAG_TRUE_RES 2u  /* compute ||b - A x|| / ||b|| at exit into pk_info.rel_res_true */
 #define PK_FLAG_NO_TMA 4u    /* use the thread-per-row kernels instead of the warp-specialised
                                 bulk-copy tile kernels (for comparison) */
-#define PK_FLAG_AUTOTUNE 8u  /* pk_batched_solve: time every (block size, blocks per SM,
-                                lanes per row) candidate on the batch first and keep the
-                                fastest (cached per batch shape for the process) */
+#define PK_FLAG_AUTOTUNE 8u  /* pk_batched_solve: time every engine and (block size, blocks
+                                per SM, lanes per row) candidate on the batch first and keep
+                                the fastest (cached per batch shape for the process) */
 #define PK_FLAG_SELL 16u     /* pipelined FP64 CG: the fused SpMV kernel (Ap, <Ap,Ap>, <p,Ap>, alpha,
                                 beta) reads a SELL-C-sigma copy of A (C = 32, sigma = 1024; built on
                                 first use, kept with the handle) instead of the CSR tiles.  Other
@@ -326,8 +326,9 @@ pk_status pk_gmres_cycle_factors(const pk_csr* A, int32_t m, double* R, double* 
  *     own that join the caller's stream.
  * PK_FLAG_AUTOTUNE (lanes 0) times the tile engine and the cluster engine (FP64, the cluster
  * engine aiming at 1024, 2048 and 4096 rows per CTA: CTAs of 128, 256, 512 threads) and every
- * (block size, blocks per SM, lanes per row) of the row engine on the batch and keeps the
- * fastest.  PK_FLAG_SELL, PK_FLAG_CGS2 and a
+ * (block size, blocks per SM, lanes per row) of the row engine on the batch, each solving the
+ * whole batch to tol / maxit from x as given (x is restored after each), and keeps the
+ * fastest (cached per batch shape and precision for the process).  PK_FLAG_SELL, PK_FLAG_CGS2 and a
  * preconditioner return PK_ERR_ARG; variant, loop and the other flags are ignored (always
  * pipelined CG).  infos: nsys entries or NULL (iters, status, cycles = refinement steps,
  * rel_res_est).  Returns PK_OK if every system converged, else the first failing system's

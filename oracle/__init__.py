@@ -57,6 +57,10 @@ def lib():
         L.orc_gmres.restype = C.c_int
         L.orc_gmres_cgs2.argtypes = L.orc_gmres.argtypes + [_dp]
         L.orc_gmres_cgs2.restype = C.c_int
+        L.orc_gmres_shift3.argtypes = [C.c_int32, _i32p, _i32p, _f64p, _f64p, _f64p, C.c_double,
+                                       C.c_int32, C.c_int32, C.c_int32, _dp, _dp, _dp, _dp, _dp,
+                                       C.POINTER(C.c_int32), C.POINTER(C.c_int32)]
+        L.orc_gmres_shift3.restype = C.c_int
         L.orc_jacobi_right_begin.argtypes = [C.c_int32, _i32p, _i32p, _f64p, _f64p, _f64p, _f64p]
         L.orc_jacobi_right_begin.restype = C.c_int
         L.orc_jacobi_right_end.argtypes = [C.c_int32, _f64p, _f64p]
@@ -152,10 +156,11 @@ def bicgstab(a, b, x0=None, tol=1e-8, maxit=1000, variant="pipelined", cap=None,
 
 
 def gmres(a, b, x0=None, tol=1e-8, maxit=1000, m=30, variant="pipelined", cap=None, precond="none",
-          cgs2=False):
+          cgs2=False, shift3=False):
     """Algorithm 6 (variant='pipelined') or Algorithm 5 (variant='classical'), restarted;
     precond='jacobi': right-preconditioned with M = diag(A) (run on A M^-1, x = M^-1 y);
-    cgs2: Gram-Schmidt applied twice per step."""
+    cgs2: Gram-Schmidt applied twice per step; shift3: the shift-invariant three-kernel form
+    of the pipelined method (Sec. 3.3), with the per-step shifts in 'sigma'."""
     n, rp, ci, va = _csr(a)
     cap = maxit + 2 if cap is None else cap
     b = np.ascontiguousarray(b, dtype=np.float64)
@@ -166,6 +171,16 @@ def gmres(a, b, x0=None, tol=1e-8, maxit=1000, m=30, variant="pipelined", cap=No
     est = np.full(cap, np.nan)
     res = np.full(cap, np.nan)
     it, cyc = C.c_int32(0), C.c_int32(0)
+    if shift3:
+        if variant != "pipelined" or cgs2:
+            raise ValueError("the three-kernel form is a form of the pipelined method with one Gram-Schmidt pass")
+        sigma = np.full(cap, np.nan)
+        st = lib().orc_gmres_shift3(n, rp, ci, va, b, x, tol, maxit, m, cap, _ptr(R), _ptr(xi), _ptr(est),
+                                    _ptr(res), _ptr(sigma), C.byref(it), C.byref(cyc))
+        if dinv is not None:
+            lib().orc_jacobi_right_end(n, dinv, x)
+        return dict(x=x, iters=it.value, cycles=cyc.value, status=st, R=R, xi=xi, est=est, res=res,
+                    sigma=sigma)
     args = (n, rp, ci, va, b, x, tol, maxit, m, 1 if variant == "pipelined" else 0,
             cap, _ptr(R), _ptr(xi), _ptr(est), _ptr(res), C.byref(it), C.byref(cyc))
     V = None

@@ -18,6 +18,8 @@
  *                           Gram-Schmidt; classical form updates the residual, pipelined
  *                           form uses xi_i = <v_0, v_i>)
  *   orc_gmres_cgs2          the same with Gram-Schmidt applied twice per step (CGS2)
+ *   orc_gmres_shift3        the shift-invariant three-kernel form of Sec. 3.3 (shifted
+ *                           basis vectors, ||v_i|| from the Gram-Schmidt inner products)
  *   orc_jacobi_right_begin  right preconditioning with M = diag(A) for BiCGStab and GMRES:
  *   orc_jacobi_right_end    the solver runs on A M^-1 y = b, and x = M^-1 y
  *   orc_pcg_jacobi          CG with the Jacobi preconditioner M = diag(A) (Sec. 5 names
@@ -623,5 +625,128 @@ static int gmres_run(int32_t n, const int32_t* rp, const int32_t* ci, const doub
   *iters_out = total;
   if (cycles_out) *cycles_out = cycle;
   free(V); free(r); free(acc); free(R); free(xi); free(eta); free(c2);
+  return status;
+}
+
+/* ---------------------------------------------------------------- GMRES(m), three-kernel form */
+
+/*
+ * The shift-invariant variant of the pipelined GMRES(m) that Sec. 3.3 names as the way to
+ * drop the normalisation kernel: span{v_0, (A - s I) v_0, ...} is the Krylov space of A for
+ * every shift s, so step i may orthogonalise w = (A - sigma_i I) v_{i-1} instead of A v_{i-1},
+ * and ||v_i|| then comes from the inner products that the orthogonalisation already forms
+ * (v_1 .. v_{i-1} orthonormal, Pythagoras):
+ *     R'_{j,i} = <v_j, w>  (j = 1 .. i-1),   nu = <w, w>,
+ *     R_{i,i}^2 = nu - sum_j R'_{j,i}^2,     v_i = (w - sum_j R'_{j,i} v_j) / R_{i,i}.
+ * Since v_{i-1} is v_{i-1} of the basis, A v_{i-1} = w + sigma_i v_{i-1} has the same
+ * coefficients except R_{i-1,i} = R'_{i-1,i} + sigma_i (i >= 2), so the R of Algorithm 6, and
+ * with it xi, eta and x, are unchanged in exact arithmetic.  The shift (the paper gives none;
+ * this is the reading that needs no extra inner product): sigma_1 = 0 and
+ * sigma_{i+1} = <v_{i-1}, A v_{i-1}> = <v_{i-1}, w> + sigma_i, the Rayleigh quotient of the
+ * previous basis vector, which removes the largest term of the difference nu - sum R'^2.
+ * The difference is only trusted while R_{i,i}^2 > 1e-8 nu (below, its rounding error is a
+ * visible fraction of it): otherwise the cycle ends before step i, as in a lucky breakdown.
+ * Everything else (xi_i = <v_0, v_i>, the estimate, the end of a cycle, the update, the
+ * restart from the true residual) is Algorithm 6 as in orc_gmres.
+ */
+int orc_gmres_shift3(int32_t n, const int32_t* rp, const int32_t* ci, const double* va,
+                     const double* b, double* x, double tol, int32_t maxit, int32_t m, int32_t cap,
+                     double* tr_R, double* tr_xi, double* tr_est, double* tr_res, double* tr_sigma,
+                     int32_t* iters_out, int32_t* cycles_out) {
+  *iters_out = 0;
+  if (cycles_out) *cycles_out = 0;
+  if (n <= 0) return ORC_OK;
+  if (m < 1) return ORC_ERR_ARG;
+  double bb = orc_dot(n, b, b);
+  if (bb == 0.0) { memset(x, 0, sizeof(double) * (size_t)n); return ORC_OK; }
+  double bnorm = sqrt(bb);
+  size_t sz = sizeof(double) * (size_t)n;
+  double* V = malloc(sz * (size_t)(m + 1));          /* v_0 .. v_m */
+  double* r = malloc(sz);
+  double* R = calloc((size_t)(m + 1) * (size_t)(m + 1), sizeof(double)); /* unshifted R[j][i] */
+  double* xi = calloc((size_t)(m + 1), sizeof(double));
+  double* eta = calloc((size_t)(m + 1), sizeof(double));
+  if (!V || !r || !R || !xi || !eta) { free(V); free(r); free(R); free(xi); free(eta); return ORC_ERR_OOM; }
+#define VEC(i) (V + (size_t)(i) * (size_t)n)
+#define RR(j, i) R[(size_t)(j) * (size_t)(m + 1) + (size_t)(i)]
+  int status = ORC_NOT_CONVERGED;
+  int32_t total = 0, cycle = 0, est_k = 0;
+  for (;;) {
+    orc_spmv(n, rp, ci, va, x, r);                    /* r0 = b - A x0 */
+    for (int32_t k = 0; k < n; ++k) r[k] = b[k] - r[k];
+    double rho0 = sqrt(orc_dot(n, r, r));
+    record(tr_res, cap, cycle, rho0);
+    if (!isfinite(rho0)) { status = ORC_NAN; break; }
+    if (rho0 <= tol * bnorm) { status = ORC_OK; break; }
+    if (total >= maxit) { status = ORC_NOT_CONVERGED; break; }
+    for (int32_t k = 0; k < n; ++k) VEC(0)[k] = r[k] / rho0;
+    memset(R, 0, sizeof(double) * (size_t)(m + 1) * (size_t)(m + 1));
+    double sumxi2 = 0.0, sigma = 0.0;
+    int32_t kdone = 0;
+    int broke = 0;
+    for (int32_t i = 1; i <= m; ++i) {
+      if (total >= maxit) break;
+      double* vi = VEC(i);
+      const double* vp = VEC(i - 1);
+      orc_spmv(n, rp, ci, va, vp, vi);                 /* w = (A - sigma_i I) v_{i-1} */
+      for (int32_t k = 0; k < n; ++k) vi[k] -= sigma * vp[k];
+      double nu = orc_dot(n, vi, vi);                  /* <w, w> */
+      double rq = orc_dot(n, vp, vi) + sigma;          /* <v_{i-1}, A v_{i-1}> */
+      double sum2 = 0.0;
+      for (int32_t j = 1; j <= i - 1; ++j) {           /* R'_{j,i} = <v_j, w> (CGS) */
+        RR(j, i) = orc_dot(n, VEC(j), vi);
+        sum2 += RR(j, i) * RR(j, i);
+      }
+      double rii2 = nu - sum2;
+      if (!isfinite(rii2)) { status = ORC_NAN; broke = 2; break; }
+      if (!(rii2 > 1e-8 * nu)) { broke = 1; break; }  /* the identity is not trusted: end */
+      double rii = sqrt(rii2);
+      for (int32_t j = 1; j <= i - 1; ++j) {
+        double rji = RR(j, i);
+        const double* vj = VEC(j);
+        for (int32_t k = 0; k < n; ++k) vi[k] -= rji * vj[k];
+      }
+      for (int32_t k = 0; k < n; ++k) vi[k] /= rii;
+      RR(i, i) = rii;
+      if (i >= 2) RR(i - 1, i) += sigma;               /* back to A v_{i-1}'s coefficient */
+      record(tr_sigma, cap, total, sigma);
+      sigma = rq;                                      /* sigma_{i+1} */
+      double xii = orc_dot(n, VEC(0), vi);             /* xi_i = <v_0, v_i> */
+      xi[i] = xii;
+      total++;
+      kdone = i;
+      sumxi2 += xii * xii;
+      double rel2 = 1.0 - sumxi2;
+      if (rel2 < 0.0) rel2 = 0.0;
+      double est = rho0 * sqrt(rel2);
+      record(tr_est, cap, est_k++, est);
+      if (est <= tol * bnorm || rel2 <= 1e-12) break;
+    }
+    if (cycle == 0) {
+      if (tr_R)
+        for (int32_t j = 1; j <= m; ++j)
+          for (int32_t i = 1; i <= m; ++i) tr_R[(size_t)(j - 1) * m + (i - 1)] = RR(j, i);
+      if (tr_xi)
+        for (int32_t i = 1; i <= m; ++i) tr_xi[i - 1] = xi[i];
+    }
+    if (broke == 2) break;
+    if (kdone == 0) { status = ORC_BREAKDOWN; break; }
+    for (int32_t i = kdone; i >= 1; --i) {             /* R eta = xi */
+      double s = xi[i];
+      for (int32_t j = i + 1; j <= kdone; ++j) s -= RR(i, j) * eta[j];
+      eta[i] = s / RR(i, i);
+    }
+    for (int32_t k = 0; k < n; ++k) {                  /* x += rho0 (eta_1 v_0 + ...) */
+      double a = 0.0;
+      for (int32_t i = 1; i <= kdone; ++i) a += eta[i] * VEC(i - 1)[k];
+      x[k] += rho0 * a;
+    }
+    cycle++;
+  }
+#undef VEC
+#undef RR
+  *iters_out = total;
+  if (cycles_out) *cycles_out = cycle;
+  free(V); free(r); free(R); free(xi); free(eta);
   return status;
 }

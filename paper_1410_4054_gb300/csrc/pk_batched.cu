@@ -588,9 +588,6 @@ static TuneVal g_last{512, 2, 1, 0};
 constexpr int kClSizes = 5;  // clusters of 1, 2, 4, 8, 16 CTAs
 constexpr int kClClasses = kBcShapeCount * kClSizes;
 constexpr int kClRowsDefault = 2048;
-// fixed iterations per autotuner candidate run (enough that the per-system setup of the
-// cluster engine does not dominate)
-constexpr int kTuneIters = 20;
 
 // Class of a system of n rows when the batch aims at rows_cta rows per CTA: the CTA shape
 // whose row limit is rows_cta, else the next larger one that holds n on 16 CTAs, with the
@@ -835,10 +832,11 @@ pk_status batched_solve(int32_t nsys, pk_csr* const* A, const double* const* b, 
     have = false;
   }
   if (!have && o->lanes >= 0 && (o->flags & PK_FLAG_AUTOTUNE)) {
-    // autotuner: time every (block size, blocks per SM, lanes per row) candidate on the whole
-    // batch for a few fixed iterations, from x as given (restored afterwards); lanes per row
-    // beyond one only for rows of more than 8 nonzeros on average, and only the given
-    // number when the caller fixes it
+    // autotuner: time every candidate engine and shape on the whole batch solved to the
+    // caller's tol and maxit, from x as given (restored afterwards), so that the spread of
+    // the systems' iteration counts (which decides how the engines balance their load) is
+    // part of the measurement; lanes per row beyond one only for rows of more than 8 nonzeros
+    // on average, and only the given number when the caller fixes it
     std::vector<double*> xsave(nsys, nullptr);
     for (int k = 0; k < nsys; ++k) {
       if (!h[k].n) continue;
@@ -858,7 +856,7 @@ pk_status batched_solve(int32_t nsys, pk_csr* const* A, const double* const* b, 
     if (tiles_ok && o->lanes == 0) {  // the tile engine is one more candidate
       for (int rep = 0; rep < 2; ++rep) {
         PK_CUDA(cudaEventRecord(a0, s));
-        if ((e = run_tiles(dsys, dqueue, nsys, irr, 0.0, kTuneIters, dst, s))) return e;
+        if ((e = run_tiles(dsys, dqueue, nsys, irr, o->tol, o->maxit, dst, s))) return e;
         PK_CUDA(cudaEventRecord(a1, s));
         PK_CUDA(cudaEventSynchronize(a1));
         float ms = 0;
@@ -875,7 +873,7 @@ pk_status batched_solve(int32_t nsys, pk_csr* const* A, const double* const* b, 
         PK_CUDA(cudaMemcpyAsync(dcl, P.sys.data(), sizeof(BatchClSys) * nsys, cudaMemcpyHostToDevice, s));
         for (int rep = 0; rep < 2; ++rep) {
           PK_CUDA(cudaEventRecord(a0, s));
-          if ((e = run_clusters(dcl, P, dqueue + 1, 0.0, kTuneIters, s))) return e;
+          if ((e = run_clusters(dcl, P, dqueue + 1, o->tol, o->maxit, s))) return e;
           PK_CUDA(cudaEventRecord(a1, s));
           PK_CUDA(cudaEventSynchronize(a1));
           float ms = 0;
@@ -892,7 +890,7 @@ pk_status batched_solve(int32_t nsys, pk_csr* const* A, const double* const* b, 
           if (bsz * ps > 2048) continue;
           for (int rep = 0; rep < 2; ++rep) {
             PK_CUDA(cudaEventRecord(a0, s));
-            if ((e = run_batch(dsys, dqueue, nsys, bsz, ps, ln, 0.0, kTuneIters, mixed, s))) return e;
+            if ((e = run_batch(dsys, dqueue, nsys, bsz, ps, ln, o->tol, o->maxit, mixed, s))) return e;
             PK_CUDA(cudaEventRecord(a1, s));
             PK_CUDA(cudaEventSynchronize(a1));
             float ms = 0;
