@@ -674,7 +674,7 @@ def bench_forms(pk, torch, dev, args, emit=None):
 
     put("jacobi_pcg", jacobi_pcg(pk, torch, dev, args.k))
     put("jacobi_right", jacobi_right(pk, torch, dev))
-    put("gmres_cgs2", gmres_cgs2(pk, torch, dev))
+    put("gmres_variants", gmres_variants(pk, torch, dev))
     put("fe_sweep", fe_sweep(pk, torch, dev))
     put("sell", sell_compare(pk, torch, dev, args.k))
     put("nonsymmetric_sweep", nonsymmetric_sweep(pk, torch, dev))
@@ -921,20 +921,23 @@ def fe_sweep(pk, torch, dev):
     return rows
 
 
-def gmres_cgs2(pk, torch, dev):
-    """Pipelined GMRES(30) to 1e-8 with one and with two Gram-Schmidt passes per step
-    (PK_FLAG_CGS2): iterations, cycles, time per step and solve time, on the 128^3
-    convection-diffusion matrix, its diagonally scaled form (spread 100, right Jacobi) and
-    the power-law matrix with 10^6 rows.  Best of two after a warm-up."""
+def gmres_variants(pk, torch, dev):
+    """Pipelined GMRES(30) to 1e-8 in three forms: four kernels per step with one
+    Gram-Schmidt pass ('cgs', Alg. 6), two passes (PK_FLAG_CGS2, six kernels), and the
+    shift-invariant three-kernel form (PK_FLAG_GM_SHIFT): iterations, cycles, time per step
+    and solve time, on the 32^3 and 128^3 convection-diffusion matrices, the 128^3 one
+    diagonally scaled (spread 100, right Jacobi) and the power-law matrix with 10^6 rows.
+    Best of two after a warm-up."""
     out = []
-    for a, pre in ((W.convdiff_3d(128), "none"), (W.diag_scaled(W.convdiff_3d(128), seed=0, spread=100.0), "jacobi"),
+    for a, pre in ((W.convdiff_3d(32), "none"), (W.convdiff_3d(128), "none"),
+                   (W.diag_scaled(W.convdiff_3d(128), seed=0, spread=100.0), "jacobi"),
                    (W.power_law(1_000_000, seed=0), "none")):
         _, b, _ = W.manufactured(a, seed=0)
         A = pk.CSRMatrix.from_workload(a)
         bd = torch.from_numpy(b).to(dev)
         x = torch.zeros(a.n, dtype=torch.float64, device=dev)
         row = {"matrix": a.name, "n": a.n, "nnz": a.nnz, "precond": pre, "tol": 1e-8}
-        for key, fl in (("cgs", 0), ("cgs2", pk.FLAG_CGS2)):
+        for key, fl in (("cgs", 0), ("cgs2", pk.FLAG_CGS2), ("shift3", pk.FLAG_GM_SHIFT)):
             kw = dict(tol=1e-8, maxit=20_000, restart=30, precond=pre)
             pk.gmres_solve(A, bd, x.zero_(), flags=fl, **kw)
             inf = _best(lambda: pk.gmres_solve(A, bd, x.zero_(), flags=fl | pk.FLAG_TRUE_RES, **kw))

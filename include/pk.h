@@ -120,6 +120,20 @@ enum {
                                    issues no copies, so the first wait of every consumer runs
                                    out after pk_opts.wait_ns and the solve returns PK_TIMEOUT
                                    (nothing is in flight; the context stays usable) */
+#define PK_FLAG_GM_SHIFT 128u   /* pipelined GMRES: the shift-invariant three-kernel form that
+                                   Sec. 3.3 names (after l1-GMRES).  A v_{i-1} and
+                                   w = (A - sigma_i I) v_{i-1} have the same part orthogonal
+                                   to v_1 .. v_{i-1}, so R_{i,i} = ||v_i|| before normalisation
+                                   follows from <w,w> and the Gram-Schmidt coefficients:
+                                   R_{i,i}^2 = <w,w> - sum_{j<i-1} R_{j,i}^2 - (R_{i-1,i} -
+                                   sigma_i)^2.  <w,w> is formed with the product, so the
+                                   normalisation and xi_i fuse into the update kernel: 3
+                                   kernels per step instead of 4, R and xi those of the
+                                   4-kernel form.  Shifts: sigma_1 = 0, sigma_{i+1} =
+                                   <v_{i-1}, A v_{i-1}> (the previous basis vector's Rayleigh
+                                   quotient).  While R_{i,i}^2 <= 1e-8 <w,w> the identity is
+                                   not trusted and the cycle ends before step i (restart).
+                                   Not with PK_FLAG_CGS2 or the classical variant (PK_ERR_ARG) */
 
 typedef struct {
   double tol;          /* relative residual tolerance (>= 0) */

@@ -18,8 +18,8 @@
  *                           Gram-Schmidt; classical form updates the residual, pipelined
  *                           form uses xi_i = <v_0, v_i>)
  *   orc_gmres_cgs2          the same with Gram-Schmidt applied twice per step (CGS2)
- *   orc_gmres_shift3        the shift-invariant three-kernel form of Sec. 3.3 (shifted
- *                           basis vectors, ||v_i|| from the Gram-Schmidt inner products)
+ *   orc_gmres_shift3        the shift-invariant three-kernel form of Sec. 3.3 (||v_i||
+ *                           from the Gram-Schmidt inner products of the shifted vector)
  *   orc_jacobi_right_begin  right preconditioning with M = diag(A) for BiCGStab and GMRES:
  *   orc_jacobi_right_end    the solver runs on A M^-1 y = b, and x = M^-1 y
  *   orc_pcg_jacobi          CG with the Jacobi preconditioner M = diag(A) (Sec. 5 names
@@ -632,22 +632,22 @@ static int gmres_run(int32_t n, const int32_t* rp, const int32_t* ci, const doub
 
 /*
  * The shift-invariant variant of the pipelined GMRES(m) that Sec. 3.3 names as the way to
- * drop the normalisation kernel: span{v_0, (A - s I) v_0, ...} is the Krylov space of A for
- * every shift s, so step i may orthogonalise w = (A - sigma_i I) v_{i-1} instead of A v_{i-1},
- * and ||v_i|| then comes from the inner products that the orthogonalisation already forms
- * (v_1 .. v_{i-1} orthonormal, Pythagoras):
- *     R'_{j,i} = <v_j, w>  (j = 1 .. i-1),   nu = <w, w>,
- *     R_{i,i}^2 = nu - sum_j R'_{j,i}^2,     v_i = (w - sum_j R'_{j,i} v_j) / R_{i,i}.
- * Since v_{i-1} is v_{i-1} of the basis, A v_{i-1} = w + sigma_i v_{i-1} has the same
- * coefficients except R_{i-1,i} = R'_{i-1,i} + sigma_i (i >= 2), so the R of Algorithm 6, and
- * with it xi, eta and x, are unchanged in exact arithmetic.  The shift (the paper gives none;
- * this is the reading that needs no extra inner product): sigma_1 = 0 and
- * sigma_{i+1} = <v_{i-1}, A v_{i-1}> = <v_{i-1}, w> + sigma_i, the Rayleigh quotient of the
- * previous basis vector, which removes the largest term of the difference nu - sum R'^2.
- * The difference is only trusted while R_{i,i}^2 > 1e-8 nu (below, its rounding error is a
- * visible fraction of it): otherwise the cycle ends before step i, as in a lucky breakdown.
- * Everything else (xi_i = <v_0, v_i>, the estimate, the end of a cycle, the update, the
- * restart from the true residual) is Algorithm 6 as in orc_gmres.
+ * drop the normalisation kernel.  For i >= 2, v_{i-1} is in span{v_1 .. v_{i-1}}, so
+ * A v_{i-1} and w = (A - sigma I) v_{i-1} have the same part orthogonal to that span for every
+ * shift sigma (the Krylov space does not change under a shift), and the norm of that part,
+ * R_{i,i}, follows from inner products the step already forms (v_1 .. v_{i-1} orthonormal,
+ * Pythagoras applied to w):
+ *     y = A v_{i-1},  R_{j,i} = <v_j, y> (j = 1 .. i-1),  nu = <w, w> = ||y - sigma v_{i-1}||^2,
+ *     R_{i,i}^2 = nu - sum_{j < i-1} R_{j,i}^2 - (R_{i-1,i} - sigma)^2,
+ *     v_i = (y - sum_j R_{j,i} v_j) / R_{i,i}.
+ * R, xi, eta and x are those of Algorithm 6; only R_{i,i} comes from the identity instead of
+ * a separate norm.  The shift reduces the cancellation in the difference: the paper gives
+ * none, and the reading here needs no extra inner product: sigma_1 = 0 (v_0 is not in the
+ * span) and sigma_{i+1} = <v_{i-1}, A v_{i-1}>, the Rayleigh quotient of the previous basis
+ * vector, which step i forms anyway (it is R_{i-1,i} for i >= 2, and <v_0, A v_0> for i = 1).  The difference is only trusted while R_{i,i}^2 > 1e-8 nu
+ * (below, its rounding error is a visible fraction of it): otherwise the cycle ends before
+ * step i, as in a lucky breakdown.  Everything else (xi_i = <v_0, v_i>, the estimate, the end
+ * of a cycle, the update, the restart from the true residual) is Algorithm 6 as in orc_gmres.
  */
 int orc_gmres_shift3(int32_t n, const int32_t* rp, const int32_t* ci, const double* va,
                      const double* b, double* x, double tol, int32_t maxit, int32_t m, int32_t cap,
@@ -663,10 +663,13 @@ int orc_gmres_shift3(int32_t n, const int32_t* rp, const int32_t* ci, const doub
   size_t sz = sizeof(double) * (size_t)n;
   double* V = malloc(sz * (size_t)(m + 1));          /* v_0 .. v_m */
   double* r = malloc(sz);
-  double* R = calloc((size_t)(m + 1) * (size_t)(m + 1), sizeof(double)); /* unshifted R[j][i] */
+  double* acc = malloc(sz);                           /* w = (A - sigma I) v_{i-1} */
+  double* R = calloc((size_t)(m + 1) * (size_t)(m + 1), sizeof(double)); /* R[j][i] */
   double* xi = calloc((size_t)(m + 1), sizeof(double));
   double* eta = calloc((size_t)(m + 1), sizeof(double));
-  if (!V || !r || !R || !xi || !eta) { free(V); free(r); free(R); free(xi); free(eta); return ORC_ERR_OOM; }
+  if (!V || !r || !acc || !R || !xi || !eta) {
+    free(V); free(r); free(acc); free(R); free(xi); free(eta); return ORC_ERR_OOM;
+  }
 #define VEC(i) (V + (size_t)(i) * (size_t)n)
 #define RR(j, i) R[(size_t)(j) * (size_t)(m + 1) + (size_t)(i)]
   int status = ORC_NOT_CONVERGED;
@@ -688,14 +691,15 @@ int orc_gmres_shift3(int32_t n, const int32_t* rp, const int32_t* ci, const doub
       if (total >= maxit) break;
       double* vi = VEC(i);
       const double* vp = VEC(i - 1);
-      orc_spmv(n, rp, ci, va, vp, vi);                 /* w = (A - sigma_i I) v_{i-1} */
-      for (int32_t k = 0; k < n; ++k) vi[k] -= sigma * vp[k];
-      double nu = orc_dot(n, vi, vi);                  /* <w, w> */
-      double rq = orc_dot(n, vp, vi) + sigma;          /* <v_{i-1}, A v_{i-1}> */
+      orc_spmv(n, rp, ci, va, vp, vi);                 /* y = A v_{i-1} */
+      for (int32_t k = 0; k < n; ++k) acc[k] = vi[k] - sigma * vp[k];  /* w = y - sigma v_{i-1} */
+      double nu = orc_dot(n, acc, acc);                /* <w, w> */
+      double rq = orc_dot(n, vp, vi);                  /* <v_{i-1}, A v_{i-1}> */
       double sum2 = 0.0;
-      for (int32_t j = 1; j <= i - 1; ++j) {           /* R'_{j,i} = <v_j, w> (CGS) */
+      for (int32_t j = 1; j <= i - 1; ++j) {           /* R_{j,i} = <v_j, y> (CGS) */
         RR(j, i) = orc_dot(n, VEC(j), vi);
-        sum2 += RR(j, i) * RR(j, i);
+        double c = j == i - 1 ? RR(j, i) - sigma : RR(j, i);  /* <v_j, w> */
+        sum2 += c * c;
       }
       double rii2 = nu - sum2;
       if (!isfinite(rii2)) { status = ORC_NAN; broke = 2; break; }
@@ -708,7 +712,6 @@ int orc_gmres_shift3(int32_t n, const int32_t* rp, const int32_t* ci, const doub
       }
       for (int32_t k = 0; k < n; ++k) vi[k] /= rii;
       RR(i, i) = rii;
-      if (i >= 2) RR(i - 1, i) += sigma;               /* back to A v_{i-1}'s coefficient */
       record(tr_sigma, cap, total, sigma);
       sigma = rq;                                      /* sigma_{i+1} */
       double xii = orc_dot(n, VEC(0), vi);             /* xi_i = <v_0, v_i> */
@@ -747,6 +750,6 @@ int orc_gmres_shift3(int32_t n, const int32_t* rp, const int32_t* ci, const doub
 #undef RR
   *iters_out = total;
   if (cycles_out) *cycles_out = cycle;
-  free(V); free(r); free(R); free(xi); free(eta);
+  free(V); free(r); free(acc); free(R); free(xi); free(eta);
   return status;
 }

@@ -18,6 +18,15 @@
 // PK_FLAG_CGS2 applies Gram-Schmidt twice per step: K-GM-3 without the norm, then K-GM-2
 // for c_j = <v_j, v_i>, j = 1 .. i-1, and K-GM-3 again with v_i -= sum c_j v_j,
 // R_{j,i} += c_j and ||v_i|| (two more launches per step).
+// PK_FLAG_GM_SHIFT, the shift-invariant three-kernel form (Sec. 3.3): A v_{i-1} and
+// w = (A - sigma_i I) v_{i-1} have the same part orthogonal to v_1 .. v_{i-1}, so its norm is
+// R_{i,i}^2 = <w,w> - sum_{j<i-1} R_{j,i}^2 - (R_{i-1,i} - sigma_i)^2.  K-GM-1 adds the first
+// stage of <w, w> to its product; K-GM-2 as above; K-GM-3 takes R_{i,i} from the identity
+// (every block, from the same values in the same order), writes
+// v_i = (A v_{i-1} - sum_j R_{j,i} v_j) / R_{i,i} and forms the first stage of
+// xi_i = <v_0, v_i>, so K-GM-4 is not needed.  sigma_1 = 0, sigma_{i+1} = <v_{i-1}, A v_{i-1}>
+// (the Rayleigh quotient that K-GM-1 forms anyway).  The identity is trusted while
+// R_{i,i}^2 > 1e-8 <w,w>; otherwise the cycle ends before step i.
 // The graph is an outer WHILE loop over cycles around an inner WHILE loop over steps.
 #include <algorithm>
 #include <cmath>
@@ -37,6 +46,8 @@ constexpr int kXiOff = kRld * kRld;  // xi after R
 // O(1) terms accumulated over up to 64 steps, with classical Gram-Schmidt's loss of
 // orthogonality on top), and the true residual at the restart decides.
 constexpr double kGmEstFloor = 1e-12;
+// Three-kernel form: R_{i,i}^2 = <w,w> - sum R'^2 is used only above this fraction of <w,w>.
+constexpr double kGmShiftFloor = 1e-8;
 
 struct GmArgs {
   int n, ld;
@@ -110,6 +121,7 @@ __global__ void __launch_bounds__(kTileThreads, 2) k_gm_start(CsrTiles T, GmArgs
         st->s[0] = sqrt(t[0]);  // rho0
         st->s[3] = 1.0 / st->s[0];  // once here, not in every thread of the scaling kernel
         st->s[1] = 0.0;         // sum of xi^2
+        st->s[2] = 0.0;         // three-kernel form: sigma_1
         st->gm_i = 1;
         st->gm_k = 0;
         st->gm_phase = GM_STEP;
@@ -148,27 +160,42 @@ __global__ void __launch_bounds__(kTileThreads, 2) k_gm_scale(GmArgs g) {
 }
 
 // K-GM-1: v_i = A v_{i-1} and the first stage of <v_{i-1}, v_i> (i >= 2).
-template <bool IRR>
+// SHIFT (three-kernel form): also the first stage of <w, w>, w = v_i - sigma_i v_{i-1}; the
+// last block keeps <w, w> and sigma_{i+1} = <v_{i-1}, A v_{i-1}>.
+template <bool IRR, bool SHIFT>
 __global__ void __launch_bounds__(kTileThreads, 2) k_gm1(CsrTiles T, GmArgs g) {
   extern __shared__ __align__(128) unsigned char smem[];
   DevState* st = g.st;
   count_pass(st);
   const int i = __ldcg(&st->gm_i);
+  const double sigma = SHIFT ? __ldcg(&st->s[2]) : 0.0;
   const double* vp = g.V + (size_t)(i - 1) * g.ld;
   double* vi = g.V + (size_t)i * g.ld;
-  double v[1] = {0.0};
+  constexpr int NV = SHIFT ? 2 : 1;
+  double v[NV];
+#pragma unroll
+  for (int k = 0; k < NV; ++k) v[k] = 0.0;
   const bool live = csr_tiles<IRR>(T, smem, st, [&]() { return gm_step_live(st); }, vp,
                               [&](int row, double y) {
+    const double p = __ldg(vp + row);
     vi[row] = y;
-    v[0] = fma(__ldg(vp + row), y, v[0]);
+    v[0] = fma(p, y, v[0]);
+    if (SHIFT) {
+      const double w = fma(-sigma, p, y);
+      v[NV - 1] = fma(w, w, v[NV - 1]);
+    }
   });
   if (!__syncthreads_or(threadIdx.x < kConsumers && live)) return;
-  tile_block_partials<1>(v, g.partials);
+  tile_block_partials<NV>(v, g.partials);
   if (arrive_last(&st->counter)) {
-    double t[1];
-    final_sums<1>(g.partials, t);
+    double t[NV];
+    final_sums<NV>(g.partials, t);
     if (threadIdx.x == 0) {
       if (i >= 2) g.R[(i - 1) * kRld + i] = t[0];
+      if (SHIFT) {
+        st->s[5] = t[NV - 1];  // <w, w>
+        st->s[4] = t[0];       // sigma_{i+1} = <v_{i-1}, A v_{i-1}> (s[4] is K-GM-4's otherwise)
+      }
       st->counter = 0;
     }
   }
@@ -389,11 +416,37 @@ __global__ void __launch_bounds__(kTileThreads, 2) k_gm2(GmArgs g, int pass) {
   }
 }
 
+// End-of-step bookkeeping shared by the pipelined and classical forms.
+__device__ __forceinline__ void gm_step_done(DevState* st, GmArgs& g, int i, double xi_i, double rel2) {
+  g.xi[i] = xi_i;
+  st->iter += 1;
+  st->gm_k = i;
+  if (rel2 < 0.0) rel2 = 0.0;
+  const double est = st->s[0] * sqrt(rel2);
+  const int step = st->iter - 1;
+  trace_put(st, step, 0, i >= 2 ? g.R[(i - 1) * kRld + i] : 0.0);
+  trace_put(st, step, 1, g.R[i * kRld + i]);
+  trace_put(st, step, 2, xi_i);
+  trace_put(st, step, 3, est);
+  if (!isfinite(xi_i)) {
+    gm_finish(st, PK_ERR_NAN);
+  } else if (est * est <= st->thr2 || rel2 <= kGmEstFloor || i >= st->gm_m || st->iter >= st->maxit) {
+    st->gm_phase = GM_END;
+    cond2_set(st, 0u);
+  } else {
+    st->gm_i = i + 1;
+  }
+}
+
 // K-GM-3: v_i -= sum_{j=1}^{i-1} R_{j,i} v_j (in order j = 1, 2, ...) with the first stage of
 // ||v_i||^2.  Tiles outer, column groups inner: each consumer thread keeps its row of v_i in
 // a register across the groups of the tile, then stores it.  Last block: R_{i,i} and the
 // lucky-breakdown test (R13).  mode 1 (CGS2, first pass): no norm, no epilogue; mode 2 (CGS2,
 // second pass): coefficients c_j from C, then R_{j,i} += c_j before R_{i,i} and the test.
+// mode 3 (three-kernel form): v_i = (v_i - sum_j R_{j,i} v_j) / R_{i,i} with R_{i,i} from the
+// norm identity (computed by every block before the pass) and the first stage of
+// xi_i = <v_0, v_i> (v_0 streamed with the first column group, which then holds 15 columns);
+// last block: R's diagonal, the next shift and the end of the step.
 __global__ void __launch_bounds__(kTileThreads, 2) k_gm3(GmArgs g, int mode) {
   extern __shared__ __align__(128) unsigned char smem[];
   DevState* st = g.st;
@@ -406,34 +459,57 @@ __global__ void __launch_bounds__(kTileThreads, 2) k_gm3(GmArgs g, int mode) {
   ew_range(g.n, r0, r1);
   const int ntiles = r1 > r0 ? (r1 - r0 + kBsRows - 1) / kBsRows : 0;
   const int ncols = i - 1;                                     // v_1 .. v_{i-1}
-  const int ngroups = max(1, (ncols + kBsCols - 1) / kBsCols);
+  const bool shift = mode == 3;
+  const int cpg = shift ? kBsCols - 1 : kBsCols;               // columns per group
+  const int ngroups = max(1, (ncols + cpg - 1) / cpg);
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   double* vi = g.V + (size_t)i * g.ld;
   const BasisRing R = basis_ring(smem);  // (its __syncthreads also publishes coef)
+  // three-kernel form: R_{i,i}^2 = <w,w> - sum_{j<i-1} R_{j,i}^2 - (R_{i-1,i} - sigma_i)^2,
+  // the same bits in every block
+  double rii2 = 0.0, inv = 0.0;
+  bool go = true;
+  if (shift) {
+    const double sigma = __ldcg(&st->s[2]);
+    double sum2 = 0.0;
+    for (int j = 0; j < ncols; ++j) {
+      const double c = j == ncols - 1 ? coef[j] - sigma : coef[j];
+      sum2 = fma(c, c, sum2);
+    }
+    const double nu = __ldcg(&st->s[5]);
+    rii2 = nu - sum2;
+    go = isfinite(rii2) && rii2 > kGmShiftFloor * nu;
+    inv = go ? 1.0 / sqrt(rii2) : 0.0;
+  }
+  const int ntl = go ? ntiles : 0;  // (a step that the identity cannot take streams nothing)
   double v[1] = {0.0};
   if (warp == kConsumerWarps) {
     if (lane == 0)
-      basis_produce(R, ntiles * ngroups, st, [&](int q, const double** src, int& row0, int& rows, int& nv) {
+      basis_produce(R, ntl * ngroups, st, [&](int q, const double** src, int& row0, int& rows, int& nv) {
         const int t = q / ngroups, grp = q % ngroups;
-        const int j0 = 1 + grp * kBsCols, nc = max(0, min(kBsCols, ncols - j0 + 1));
+        const int j0 = 1 + grp * cpg, nc = max(0, min(cpg, ncols - j0 + 1));
         row0 = r0 + t * kBsRows;
         rows = min(kBsRows, r1 - row0);
         nv = nc + (grp == 0);
         src[0] = grp == 0 ? vi : nullptr;
         for (int c = 0; c < kBsCols; ++c) src[1 + c] = c < nc ? g.V + (size_t)(j0 + c) * g.ld : nullptr;
+        if (shift && grp == 0) src[kBsVecs - 1] = g.V;  // v_0
       });
   } else {
-    for (int t = 0; t < ntiles; ++t) {
+    for (int t = 0; t < ntl; ++t) {
       const int row0 = r0 + t * kBsRows, rows = min(kBsRows, r1 - row0);
       const bool mine = (int)threadIdx.x < rows;
-      double w = 0.0;
+      double w = 0.0, v0r = 0.0;
       bool ok = true;
       for (int grp = 0; grp < ngroups; ++grp) {
         const int q = t * ngroups + grp, s = q % kBsStages;
         if (!mbar_wait_st(&R.full[s], (q / kBsStages) & 1, st)) { report_timeout(st); ok = false; break; }
-        const int j0 = 1 + grp * kBsCols, nc = max(0, min(kBsCols, ncols - j0 + 1));
+        const int j0 = 1 + grp * cpg, nc = max(0, min(cpg, ncols - j0 + 1));
         if (mine) {
-          if (grp == 0) w = R.slot(s, 0)[threadIdx.x];
+          if (grp == 0) {
+            w = R.slot(s, 0)[threadIdx.x];
+            if (shift) v0r = R.slot(s, kBsVecs - 1)[threadIdx.x];
+          }
           const double* cf = coef + (j0 - 1);
           switch (nc) {
 #define PK_GM3_CASE(N) \
@@ -448,13 +524,44 @@ __global__ void __launch_bounds__(kTileThreads, 2) k_gm3(GmArgs g, int mode) {
       }
       if (!ok) break;
       if (mine) {
-        vi[row0 + threadIdx.x] = w;
-        if (mode != 1) v[0] = fma(w, w, v[0]);
+        if (shift) {
+          w *= inv;
+          vi[row0 + threadIdx.x] = w;
+          v[0] = fma(v0r, w, v[0]);
+        } else {
+          vi[row0 + threadIdx.x] = w;
+          if (mode != 1) v[0] = fma(w, w, v[0]);
+        }
       }
     }
   }
   if (mode == 1) return;
   tile_block_partials<1>(v, g.partials);
+  if (shift) {
+    if (arrive_last(&st->counter)) {
+      double t[1];
+      final_sums<1>(g.partials, t);
+      if (threadIdx.x == 0) {
+        if (__ldcg(&st->timeout)) {
+          gm_finish(st, PK_TIMEOUT);
+        } else if (!isfinite(rii2)) {
+          gm_finish(st, PK_ERR_NAN);
+        } else if (!go) {
+          st->gm_k = i - 1;  // the cycle ends before step i
+          st->gm_phase = GM_END;
+          cond2_set(st, 0u);
+        } else {
+          g.R[i * kRld + i] = sqrt(rii2);
+          st->s[2] = st->s[4];  // sigma_{i+1}
+          const double xi_i = t[0];
+          st->s[1] += xi_i * xi_i;
+          gm_step_done(st, g, i, xi_i, 1.0 - st->s[1]);
+        }
+        st->counter = 0;
+      }
+    }
+    return;
+  }
   if (arrive_last(&st->counter)) {
     double t[1];
     final_sums<1>(g.partials, t);
@@ -480,28 +587,6 @@ __global__ void __launch_bounds__(kTileThreads, 2) k_gm3(GmArgs g, int mode) {
       }
       st->counter = 0;
     }
-  }
-}
-
-// End-of-step bookkeeping shared by the pipelined and classical forms.
-__device__ __forceinline__ void gm_step_done(DevState* st, GmArgs& g, int i, double xi_i, double rel2) {
-  g.xi[i] = xi_i;
-  st->iter += 1;
-  st->gm_k = i;
-  if (rel2 < 0.0) rel2 = 0.0;
-  const double est = st->s[0] * sqrt(rel2);
-  const int step = st->iter - 1;
-  trace_put(st, step, 0, i >= 2 ? g.R[(i - 1) * kRld + i] : 0.0);
-  trace_put(st, step, 1, g.R[i * kRld + i]);
-  trace_put(st, step, 2, xi_i);
-  trace_put(st, step, 3, est);
-  if (!isfinite(xi_i)) {
-    gm_finish(st, PK_ERR_NAN);
-  } else if (est * est <= st->thr2 || rel2 <= kGmEstFloor || i >= st->gm_m || st->iter >= st->maxit) {
-    st->gm_phase = GM_END;
-    cond2_set(st, 0u);
-  } else {
-    st->gm_i = i + 1;
   }
 }
 
@@ -659,7 +744,8 @@ __global__ void k_gm_init(DevState* st, int m) {
 static pk_status gm_setup() {
   static bool done = false;
   if (!done) {
-    for (auto k : {k_gm_start<false>, k_gm_start<true>, k_gm1<false>, k_gm1<true>})
+    for (auto k : {k_gm_start<false>, k_gm_start<true>, k_gm1<false, false>, k_gm1<true, false>, k_gm1<false, true>,
+                   k_gm1<true, true>})
       PK_CUDA(cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, csr_smem_bytes()));
     PK_CUDA(cudaFuncSetAttribute(k_gm_scale, cudaFuncAttributeMaxDynamicSharedMemorySize, stream_smem_bytes<1>()));
     PK_CUDA(cudaFuncSetAttribute(k_gm4, cudaFuncAttributeMaxDynamicSharedMemorySize, stream_smem_bytes<2, double, 4>()));
@@ -688,6 +774,11 @@ pk_status gmres_solve(pk_csr* A, const double* b, double* x, const pk_opts* o, p
   if (o->precond != PK_PRECOND_NONE && o->precond != PK_PRECOND_JACOBI) { set_error("bad precond"); return PK_ERR_ARG; }
   if (o->flags & PK_FLAG_SELL) { set_error("PK_FLAG_SELL applies to pipelined FP64 CG"); return PK_ERR_ARG; }
   const bool cgs2 = (o->flags & PK_FLAG_CGS2) != 0;
+  const bool shift = (o->flags & PK_FLAG_GM_SHIFT) != 0;
+  if (shift && (cgs2 || o->variant != PK_VARIANT_PIPELINED)) {
+    set_error("PK_FLAG_GM_SHIFT is a form of pipelined GMRES with one Gram-Schmidt pass (not with PK_FLAG_CGS2)");
+    return PK_ERR_ARG;
+  }
   if (!A->tma_ok) { set_error("GMRES needs the tile engine"); return PK_ERR_ARG; }
   if ((e = gm_setup())) return e;
   const int n = A->n;
@@ -749,12 +840,14 @@ pk_status gmres_solve(pk_csr* A, const double* b, double* x, const pk_opts* o, p
   };
   auto step = [&](cudaStream_t cs, Timer* t) {
     if (t) t->begin(PK_SLOT_SPMV_DOTS);
-    (irr ? k_gm1<true> : k_gm1<false>)<<<Gt, kTileThreads, csr_smem_bytes(), cs>>>(ct, g);
+    auto k1 = shift ? (irr ? k_gm1<true, true> : k_gm1<false, true>) : (irr ? k_gm1<true, false> : k_gm1<false, false>);
+    k1<<<Gt, kTileThreads, csr_smem_bytes(), cs>>>(ct, g);
     if (t) { t->end(); t->begin(PK_SLOT_MULTIDOT); }
     k_gm2<<<Gs, kTileThreads, kBsSmem, cs>>>(g, 0);
     if (t) { t->end(); t->begin(PK_SLOT_ORTHO); }
-    k_gm3<<<Gs, kTileThreads, kBsSmem, cs>>>(g, cgs2 ? 1 : 0);
+    k_gm3<<<Gs, kTileThreads, kBsSmem, cs>>>(g, shift ? 3 : cgs2 ? 1 : 0);
     if (t) t->end();
+    if (shift) return;  // (K-GM-3 normalised v_i and formed xi_i)
     if (cgs2) {  // second Gram-Schmidt pass
       if (t) t->begin(PK_SLOT_MULTIDOT);
       k_gm2<<<Gs, kTileThreads, kBsSmem, cs>>>(g, 1);
@@ -783,11 +876,11 @@ pk_status gmres_solve(pk_csr* A, const double* b, double* x, const pk_opts* o, p
     k_gm_end<<<Ge, kBlock, 0, cs>>>(g);
     if (t) t->end();
   };
-  const int step_kernels = (classical ? 7 : 4) + (cgs2 ? 2 : 0);
+  const int step_kernels = shift ? 3 : (classical ? 7 : 4) + (cgs2 ? 2 : 0);
   const bool graph = o->loop != PK_LOOP_HOST && !T.on;
   if (graph) {
     const void* keys[4] = {v.x_dev, v.b_dev, nullptr, nullptr};
-    const int64_t ikeys[4] = {o->variant, m, o->precond, cgs2};  // precond: values of A or of A M^-1
+    const int64_t ikeys[4] = {o->variant, m, o->precond, (int64_t)cgs2 | (int64_t)shift << 1};  // precond: values of A or of A M^-1
     pk_graph_entry* ge = nullptr;
     if ((e = build_nested_graph(A, 6 + (classical ? 1 : 0), keys, ikeys,
                                 [&](cudaStream_t cs) { pre(cs, nullptr); },

@@ -32,6 +32,7 @@ FLAG_AUTOTUNE = 8
 FLAG_SELL = 16
 FLAG_CGS2 = 32
 FLAG_TEST_STALL = 64
+FLAG_GM_SHIFT = 128
 SLOTS = ["spmv_dots", "update", "multidot", "ortho", "spmv", "blas1", "other", "resident"]
 MAX_SLOTS = 8
 

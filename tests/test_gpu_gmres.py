@@ -52,12 +52,13 @@ MATRICES = {
 }
 
 
-def oracle_sensitivity(a, b, variant, m, tol, maxit, nsamp=3, precond="none", cgs2=False):
+def oracle_sensitivity(a, b, variant, m, tol, maxit, nsamp=3, precond="none", cgs2=False, shift3=False):
     """The oracle's own rounding sensitivity: rerun it with b perturbed by about one ulp
     (relative 2^-52, three seeds); running maxima of the change of R (relative to max |R|)
     and xi per step of the first cycle, of the iteration count and of x at a fixed count."""
-    base = O.gmres(a, b, tol=tol, maxit=maxit, m=m, variant=variant, precond=precond, cgs2=cgs2)
-    fixed = O.gmres(a, b, tol=0.0, maxit=max(base["iters"], 1), m=m, variant=variant, precond=precond, cgs2=cgs2)
+    kw = dict(m=m, variant=variant, precond=precond, cgs2=cgs2, shift3=shift3)
+    base = O.gmres(a, b, tol=tol, maxit=maxit, **kw)
+    fixed = O.gmres(a, b, tol=0.0, maxit=max(base["iters"], 1), **kw)
     k = min(m, max(base["iters"], 1))
     sR = np.zeros(k)
     sX = np.zeros(k)
@@ -65,12 +66,12 @@ def oracle_sensitivity(a, b, variant, m, tol, maxit, nsamp=3, precond="none", cg
     scale = np.abs(base["R"][:k, :k]).max()
     for smp in range(nsamp):
         bp = b * (1 + 2.0 ** -52 * W.uniform_pm1(100 + smp, a.n))
-        r = O.gmres(a, bp, tol=tol, maxit=maxit, m=m, variant=variant, precond=precond, cgs2=cgs2)
+        r = O.gmres(a, bp, tol=tol, maxit=maxit, **kw)
         dR = np.abs(r["R"][:k, :k] - base["R"][:k, :k]).max(axis=0) / scale
         sR = np.fmax(sR, dR)
         sX = np.fmax(sX, np.abs(r["xi"][:k] - base["xi"][:k]))
         it_spread = max(it_spread, abs(r["iters"] - base["iters"]))
-        rf = O.gmres(a, bp, tol=0.0, maxit=max(base["iters"], 1), m=m, variant=variant, precond=precond, cgs2=cgs2)
+        rf = O.gmres(a, bp, tol=0.0, maxit=max(base["iters"], 1), **kw)
         x_spread = max(x_spread, rel(rf["x"], fixed["x"]))
     return base, fixed, np.maximum.accumulate(sR), np.maximum.accumulate(sX), it_spread, x_spread
 
@@ -148,26 +149,49 @@ CGS2_MATRICES = {
 }
 
 
-@pytest.mark.parametrize("variant", ["pipelined", "classical"])
-@pytest.mark.parametrize("name", sorted(MATRICES) + [f"jacobi:{k}" for k in sorted(JACOBI_MATRICES)]
-                         + [f"cgs2:{k}" for k in sorted(CGS2_MATRICES)])
+# the shift-invariant three-kernel form (pipelined only)
+SHIFT3_MATRICES = {
+    "convdiff_16": lambda: W.convdiff_3d(16),
+    "convdiff_23": lambda: W.convdiff_3d(23),
+    "powerlaw_1e4": lambda: W.power_law(10_000, seed=1),
+    "fe3d_elast_540": lambda: W.fe_elasticity_3d(5),
+    "lap2d_ragged": lambda: W.laplace_2d(97, 41),
+    "rand28": lambda: W.random_uniform(4000, 28, seed=2),
+    "dense_rows_1e4": lambda: W.spd_dense_rows(),
+}
+
+PARITY_CASES = ([(n, v) for n in sorted(MATRICES) + [f"jacobi:{k}" for k in sorted(JACOBI_MATRICES)]
+                 + [f"cgs2:{k}" for k in sorted(CGS2_MATRICES)] for v in ("classical", "pipelined")]
+                + [(f"shift3:{k}", "pipelined") for k in sorted(SHIFT3_MATRICES)]
+                + [("shift3:jacobi:convdiff_16_scaled", "pipelined")])
+
+
+@pytest.mark.parametrize("name,variant", PARITY_CASES)
 def test_gmres_parity(name, variant):
     """'jacobi:' cases: right preconditioning with M = diag(A) on both sides; 'cgs2:' cases:
-    Gram-Schmidt applied twice per step on both sides."""
+    Gram-Schmidt applied twice per step on both sides; 'shift3:' cases: the shift-invariant
+    three-kernel form on both sides."""
+    shift3 = name.startswith("shift3:")
+    if shift3:
+        name = name[7:]
     precond = "jacobi" if name.startswith("jacobi:") else "none"
     cgs2 = name.startswith("cgs2:")
     if precond == "jacobi":
         a = JACOBI_MATRICES[name[7:]]()
     elif cgs2:
         a = CGS2_MATRICES[name[5:]]()
+    elif shift3:
+        a = SHIFT3_MATRICES[name]()
     else:
         a = MATRICES[name]()
     _, b, _ = W.manufactured(a, seed=0)
     m = 30
     ref, fixed, sR, sX, it_spread, x_spread = oracle_sensitivity(a, b, variant, m, 1e-8, 20_000,
-                                                                 precond=precond, cgs2=cgs2)
+                                                                 precond=precond, cgs2=cgs2, shift3=shift3)
     assert ref["status"] == O.OK
-    fl = pk.FLAG_CGS2 if cgs2 else 0
+    fl = pk.FLAG_CGS2 if cgs2 else pk.FLAG_GM_SHIFT if shift3 else 0
+    if shift3:
+        name = "shift3:" + name
     A = pk.CSRMatrix.from_workload(a)
     info, x, tr = solve(a, b, A=A, tol=1e-8, maxit=20_000, restart=m, variant=variant,
                         flags=pk.FLAG_TRUE_RES | fl, trace_cap=max(256, ref["iters"] + 8), precond=precond)
@@ -197,7 +221,8 @@ def test_gmres_parity(name, variant):
                abs(info["iters"] - ref["iters"]), 2, m, oracle_spread=it_spread)
         assert info["iters"] <= ref["iters"] + m
         k = min(k_orc, k_gpu)
-        _, fixed_k, _, _, _, xs_k = oracle_sensitivity(a, b, variant, m, 0.0, k, precond=precond, cgs2=cgs2)
+        _, fixed_k, _, _, _, xs_k = oracle_sensitivity(a, b, variant, m, 0.0, k, precond=precond, cgs2=cgs2,
+                                                       shift3=shift3)
         info2, x2, _ = solve(a, b, tol=0.0, maxit=k, restart=m, variant=variant, precond=precond, flags=fl)
         assert info2["iters"] == k and info2["cycles"] == fixed_k["cycles"]
         assert rel(x2, fixed_k["x"]) <= max(1e-9, 10 * xs_k)
@@ -238,16 +263,40 @@ def test_gmres_restart_lengths_and_loops(m, loop):
 
 def test_gmres_launch_counts():
     """Sec. 3.3: four kernels per pipelined Arnoldi step (the classical form here: seven);
-    CGS2 adds a second K-GM-2 / K-GM-3 pair."""
+    CGS2 adds a second K-GM-2 / K-GM-3 pair; the shift-invariant form takes three."""
     a = W.convdiff_3d(10)
     _, b, _ = W.manufactured(a)
     per = {}
     for variant in ("pipelined", "classical"):
-        for fl, tag in ((0, ""), (pk.FLAG_CGS2, "+cgs2")):
+        for fl, tag in ((0, ""), (pk.FLAG_CGS2, "+cgs2"), (pk.FLAG_GM_SHIFT, "+shift")):
+            if variant == "classical" and fl == pk.FLAG_GM_SHIFT:
+                continue
             i10, _, _ = solve(a, b, tol=0.0, maxit=10, restart=30, variant=variant, flags=fl)
             i20, _, _ = solve(a, b, tol=0.0, maxit=20, restart=30, variant=variant, flags=fl)
             per[variant + tag] = (i20["launches"] - i10["launches"]) / 10
-    assert per == {"pipelined": 4, "classical": 7, "pipelined+cgs2": 6, "classical+cgs2": 9}
+    assert per == {"pipelined": 4, "classical": 7, "pipelined+cgs2": 6, "classical+cgs2": 9, "pipelined+shift": 3}
+
+
+def test_gmres_shift_form_rejections_and_loops():
+    """PK_FLAG_GM_SHIFT is a form of pipelined GMRES with one Gram-Schmidt pass; the host loop
+    and the graph give the same iterates; restart lengths 1 .. 64 match the oracle."""
+    a = W.convdiff_3d(12)
+    _, b, _ = W.manufactured(a, seed=3)
+    A = pk.CSRMatrix.from_workload(a)
+    for kw in (dict(variant="classical"), dict(flags=pk.FLAG_GM_SHIFT | pk.FLAG_CGS2)):
+        kw.setdefault("flags", pk.FLAG_GM_SHIFT)
+        with pytest.raises(RuntimeError, match="PK_FLAG_GM_SHIFT"):
+            pk.gmres_solve(A, dev(b), dev(np.zeros(a.n)), **kw)
+    for m in (1, 5, 30, 64):
+        ref = O.gmres(a, b, tol=1e-9, maxit=5000, m=m, shift3=True)
+        out = {}
+        for loop in ("graph", "host"):
+            info, x, tr = solve(a, b, A=A, tol=1e-9, maxit=5000, restart=m, loop=loop, check_every=1,
+                                flags=pk.FLAG_GM_SHIFT | pk.FLAG_TRUE_RES)
+            assert info["status"] == pk.PK_OK and abs(info["iters"] - ref["iters"]) <= 2, (m, loop, info["iters"])
+            assert info["rel_res_true"] <= 1.5e-9
+            out[loop] = (info["iters"], x)
+        assert out["graph"][0] == out["host"][0] and np.array_equal(out["graph"][1], out["host"][1])
 
 
 @pytest.mark.parametrize("make", [lambda: W.diag_scaled(W.laplace_2d(40), seed=3, spread=1e3),

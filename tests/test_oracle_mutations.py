@@ -52,17 +52,17 @@ EXTRA_MUTANTS = {
                                         "test_oracle_cgs2.py"),
     "cgs2_second_pass_sign": ([("for (int32_t k = 0; k < n; ++k) vi[k] -= c2[j] * vj[k];",
                                 "for (int32_t k = 0; k < n; ++k) vi[k] += c2[j] * vj[k];")], "test_oracle_cgs2.py"),
-    # the three-kernel GMRES: the shift mapped back with the wrong sign, the norm identity
-    # without the projections, the shift left out of w (but still mapped back), and the
-    # shift rule without the previous shift (exact arithmetic does not see the shift's value,
-    # so this one is caught by the closed-form check of the first shifts)
-    "shift3_unshift_sign": ([("if (i >= 2) RR(i - 1, i) += sigma;", "if (i >= 2) RR(i - 1, i) -= sigma;")],
-                            "test_oracle_shift3.py"),
+    # the three-kernel GMRES: the shift's sign in the identity's last coefficient, the norm
+    # identity without the projections, the shift left out of w (but kept in the
+    # coefficient), and the shift rule taking <v_{i-1}, w> instead of the Rayleigh quotient
+    # (exact arithmetic does not see the shift's value, so this one is caught by the
+    # closed-form check of the first shifts)
+    "shift3_coefficient_sign": ([("double c = j == i - 1 ? RR(j, i) - sigma : RR(j, i);",
+                                  "double c = j == i - 1 ? RR(j, i) + sigma : RR(j, i);")], "test_oracle_shift3.py"),
     "shift3_norm_without_projections": ([("double rii2 = nu - sum2;", "double rii2 = nu;")], "test_oracle_shift3.py"),
-    "shift3_w_not_shifted": ([("for (int32_t k = 0; k < n; ++k) vi[k] -= sigma * vp[k];", "")],
-                             "test_oracle_shift3.py"),
-    "shift3_rule_drops_sigma": ([("double rq = orc_dot(n, vp, vi) + sigma;", "double rq = orc_dot(n, vp, vi);")],
-                                "test_oracle_shift3.py"),
+    "shift3_w_not_shifted": ([("acc[k] = vi[k] - sigma * vp[k];", "acc[k] = vi[k];")], "test_oracle_shift3.py"),
+    "shift3_rule_uses_w": ([("double rq = orc_dot(n, vp, vi);", "double rq = orc_dot(n, vp, acc);")],
+                           "test_oracle_shift3.py"),
 }
 
 
