@@ -69,15 +69,18 @@ enum {
                         no host round-trip until the solve ends */
   PK_LOOP_HOST = 1,  /* plain launches; the host reads the device "done" flag every
                         `check_every` iterations (kernels after convergence return at once) */
-  PK_LOOP_PERSISTENT = 2, /* pipelined FP64 CG only: the whole iteration loop in one launch
-                        on one thread-block cluster (16 CTAs where available, else 8) with
-                        p, x, r, Ap in distributed shared memory, hardware cluster barriers,
-                        every CTA summing the block partials itself in a fixed order; for
-                        n <= PK_PERSISTENT_MAX_N.  Larger n, other solvers, variants or
-                        precisions return PK_ERR_ARG */
+  PK_LOOP_PERSISTENT = 2, /* pipelined FP64 CG and pipelined BiCGStab: the whole iteration
+                        loop in one launch on one thread-block cluster (16 CTAs where
+                        available, else 8) with the vectors in distributed shared memory (CG:
+                        p, x, r, Ap; BiCGStab: p, s, r, Ap, As, r0*), hardware cluster
+                        barriers, every CTA summing the block partials itself in a fixed
+                        order; for n <= PK_PERSISTENT_MAX_N.  Larger n, GMRES, other
+                        variants or precisions return PK_ERR_ARG */
   PK_LOOP_AUTO = 3,  /* PK_LOOP_PERSISTENT for pipelined FP64 CG with n <= PK_PERSISTENT_AUTO_N
-                        and nnz <= PK_PERSISTENT_AUTO_NNZ (and no PK_FLAG_TIMING) when the
-                        device can run it, PK_LOOP_GRAPH otherwise */
+                        and nnz <= PK_PERSISTENT_AUTO_NNZ, and for pipelined BiCGStab with
+                        n <= PK_PERSISTENT_BICGSTAB_AUTO_N and nnz <=
+                        PK_PERSISTENT_BICGSTAB_AUTO_NNZ (and no PK_FLAG_TIMING) when the device
+                        can run it, PK_LOOP_GRAPH otherwise */
   PK_LOOP_RESIDENT = 4 /* pipelined FP64 CG only: the whole iteration loop in one cooperative
                         launch of one block per SM.  Each iteration's update (x, r, p) and fused
                         SpMV run back to back in the launch; the SpMV of a block waits only for
@@ -95,6 +98,11 @@ enum {
 /* measured on GB300: the 16-SM cluster loop wins up to ~330k nonzeros (2D 5-point 256^2),
  * the full-GPU graph loop from ~450k (P1 triangles, 65,025 unknowns) */
 #define PK_PERSISTENT_AUTO_NNZ 393216
+/* BiCGStab (four cluster barriers and two products per iteration), measured on GB300 on 3D
+ * convection-diffusion: the cluster loop takes 16 us per iteration against 33 for the graph
+ * at 16^3, 29 against 35 at 32^3 (223k nonzeros), 48 against 36 at 40^3 (438k) */
+#define PK_PERSISTENT_BICGSTAB_AUTO_N 32768
+#define PK_PERSISTENT_BICGSTAB_AUTO_NNZ 262144
 
 /* pk_opts.flags */
 #define PK_FLAG_TIMING 1u    /* time every kernel launch with CUDA events (host loop) and

@@ -19,13 +19,9 @@
 // 256 threads and 2048 rows (2 per SM), 128 threads and 1024 rows (4 per SM).  Each (shape,
 // C) class of the batch is one persistent launch that takes systems from the class's queue;
 // the host puts the classes on streams of their own so that they share the GPU.
-#include <cooperative_groups.h>
-
 #include <algorithm>
 
-#include "pk_internal.cuh"
-
-namespace cg = cooperative_groups;
+#include "pk_cluster.cuh"
 
 namespace pk {
 
@@ -48,94 +44,10 @@ constexpr size_t bc_smem() {
   return sizeof(double) * (4 * (size_t)MAXR + kBcSlots + 2 * NT) + sizeof(int) * (MAXR + 4);
 }
 
-// Fixed-order block sum of NV values, broadcast to every thread: warp 0 adds NT/32 values per
-// lane as a pairwise tree (the NV sums interleaved), then a butterfly (both partners of a
-// pair add the same two values, so every lane ends with the same bits).
-template <int NT, int NV>
-__device__ __forceinline__ void bc_block_sum(const double (&v)[NV], double* buf, double (&out)[NV]) {
-  constexpr int PER = NT / 32;
-  static_assert(PER == 4 || PER == 8 || PER == 16, "4, 8 or 16 values per lane");
-  __shared__ double bc[NV];
-#pragma unroll
-  for (int k = 0; k < NV; ++k) buf[k * NT + threadIdx.x] = v[k];
-  __syncthreads();
-  if (threadIdx.x < 32) {
-    double t[NV][PER];
-#pragma unroll
-    for (int k = 0; k < NV; ++k)
-#pragma unroll
-      for (int m = 0; m < PER; ++m) t[k][m] = buf[k * NT + m * 32 + threadIdx.x];
-#pragma unroll
-    for (int h = PER / 2; h >= 1; h >>= 1)
-#pragma unroll
-      for (int m = 0; m < h; ++m)
-#pragma unroll
-        for (int k = 0; k < NV; ++k) t[k][m] = t[k][m] + t[k][m + h];
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1)
-#pragma unroll
-      for (int k = 0; k < NV; ++k) t[k][0] += __shfl_xor_sync(0xffffffffu, t[k][0], o);
-    if (threadIdx.x == 0) {
-#pragma unroll
-      for (int k = 0; k < NV; ++k) bc[k] = t[k][0];
-    }
-  }
-  __syncthreads();
-#pragma unroll
-  for (int k = 0; k < NV; ++k) out[k] = bc[k];
-}
-
-// Cluster total of slots [s0, s0 + NV) of every CTA (after a cluster barrier): lane c of warp
-// 0 reads CTA c's values, then a butterfly over the lanes; every CTA runs the same additions.
-template <int NV>
-__device__ __forceinline__ void bc_cluster_total(cg::cluster_group& cl, double* slots, int s0, double (&out)[NV]) {
-  __shared__ double bc[NV];
-  if (threadIdx.x < 32) {
-    const int C = (int)cl.num_blocks();
-    double t[NV];
-    const double* rem = threadIdx.x < C ? cl.map_shared_rank(slots, (int)threadIdx.x) : nullptr;
-#pragma unroll
-    for (int k = 0; k < NV; ++k) t[k] = rem ? rem[s0 + k] : 0.0;
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1)
-#pragma unroll
-      for (int k = 0; k < NV; ++k) t[k] += __shfl_xor_sync(0xffffffffu, t[k], o);
-    if (threadIdx.x == 0) {
-#pragma unroll
-      for (int k = 0; k < NV; ++k) bc[k] = t[k];
-    }
-  }
-  __syncthreads();
-#pragma unroll
-  for (int k = 0; k < NV; ++k) out[k] = bc[k];
-}
-
-// Row l of this CTA (row pointers staged in srp) times p: four entries per step with their
-// loads independent, products added left to right.
+// Row l of this CTA (row pointers staged in srp) times p.
 __device__ __forceinline__ double bc_row(const BatchClSys& S, cg::cluster_group& cl, double* sp, const int* srp,
                                          int lg, int l) {
-  const int R1 = (1 << lg) - 1;
-  int j = srp[l];
-  const int j1 = srp[l + 1];
-  double s = 0.0;
-  for (; j + 4 <= j1; j += 4) {
-    int c[4];
-    double w[4], pv[4];
-#pragma unroll
-    for (int k = 0; k < 4; ++k) {
-      c[k] = __ldg(S.ci + j + k);
-      w[k] = __ldg(S.va + j + k);
-    }
-#pragma unroll
-    for (int k = 0; k < 4; ++k) pv[k] = *cl.map_shared_rank(sp + (c[k] & R1), c[k] >> lg);
-#pragma unroll
-    for (int k = 0; k < 4; ++k) s = fma(w[k], pv[k], s);
-  }
-  for (; j < j1; ++j) {
-    const int c = __ldg(S.ci + j);
-    s = fma(__ldg(S.va + j), *cl.map_shared_rank(sp + (c & R1), c >> lg), s);
-  }
-  return s;
+  return cluster_row(cl, S.ci, S.va, sp, lg, srp[l], srp[l + 1]);
 }
 
 }  // namespace
@@ -191,13 +103,13 @@ __global__ void __launch_bounds__(NT, 512 / NT) k_batched_cluster(BatchClArgs a)
       v[1] = fma(bi, bi, v[1]);
     }
     double t[2];
-    bc_block_sum<NT, 2>(v, buf, t);
+    cluster_block_sum<NT, 2>(v, buf, t);
     if (threadIdx.x == 0) {
       slots[0] = t[0];
       slots[1] = t[1];
     }
     cl.sync();  // (also: no CTA reads sp any more)
-    bc_cluster_total<2>(cl, slots, 0, t);
+    cluster_total<2>(cl, slots, 0, t);
     double rr = t[0];
     const double bb = t[1], thr2 = a.tol * a.tol * bb;
     for (int l = threadIdx.x; l < nown; l += NT) sp[l] = sr[l];  // p0 = r0
@@ -218,13 +130,13 @@ __global__ void __launch_bounds__(NT, 512 / NT) k_batched_cluster(BatchClArgs a)
         v[0] = fma(y, y, v[0]);
         v[1] = fma(sp[l], y, v[1]);
       }
-      bc_block_sum<NT, 2>(v, buf, t);
+      cluster_block_sum<NT, 2>(v, buf, t);
       if (threadIdx.x == 0) {
         slots[0] = t[0];
         slots[1] = t[1];
       }
       cl.sync();
-      bc_cluster_total<2>(cl, slots, 0, t);
+      cluster_total<2>(cl, slots, 0, t);
       if (threadIdx.x == 0) {
         int sts = kRunning;
         double al = 0.0, be = 0.0;
@@ -255,10 +167,10 @@ __global__ void __launch_bounds__(NT, 512 / NT) k_batched_cluster(BatchClArgs a)
         w[0] = fma(rn, rn, w[0]);
       }
       double u[1];
-      bc_block_sum<NT, 1>(w, buf, u);
+      cluster_block_sum<NT, 1>(w, buf, u);
       if (threadIdx.x == 0) slots[2] = u[0];
       cl.sync();
-      bc_cluster_total<1>(cl, slots, 2, u);
+      cluster_total<1>(cl, slots, 2, u);
       rr = u[0];
       iters = i + 1;
       if (!isfinite(rr)) status = PK_ERR_NAN;

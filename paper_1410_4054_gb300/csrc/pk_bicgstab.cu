@@ -424,11 +424,15 @@ static pk_status bi_tma_setup() {
   return PK_OK;
 }
 
+// pk_bicgstab_cluster.cu: the whole pipelined loop on one thread-block cluster
+bool bicgstab_persistent_usable(const pk_csr* A);
+pk_status launch_bicgstab_persistent(pk_csr* A, double* x, const double* r, const double* r0s, cudaStream_t s);
+
 pk_status bicgstab_solve(pk_csr* A, const double* b, double* x, const pk_opts* o, pk_info* info,
                          cudaStream_t s) {
   pk_status e = check_opts(A, b, x, o, info);
   if (e) return e;
-  if (o->loop == PK_LOOP_PERSISTENT || o->loop == PK_LOOP_RESIDENT) { set_error("PK_LOOP_PERSISTENT / PK_LOOP_RESIDENT run pipelined CG only"); return PK_ERR_ARG; }
+  if (o->loop == PK_LOOP_RESIDENT) { set_error("PK_LOOP_RESIDENT runs pipelined CG only"); return PK_ERR_ARG; }
   *info = pk_info{};
   info->rel_res_true = -1.0;
   if (A->n == 0) return PK_OK;
@@ -440,6 +444,23 @@ pk_status bicgstab_solve(pk_csr* A, const double* b, double* x, const pk_opts* o
   if (o->precond != PK_PRECOND_NONE && o->precond != PK_PRECOND_JACOBI) { set_error("bad precond"); return PK_ERR_ARG; }
   if (o->flags & PK_FLAG_SELL) { set_error("PK_FLAG_SELL applies to pipelined FP64 CG"); return PK_ERR_ARG; }
   if (o->flags & PK_FLAG_CGS2) { set_error("PK_FLAG_CGS2 applies to GMRES"); return PK_ERR_ARG; }
+  // the whole loop on one thread-block cluster (small systems): asked for, or chosen by AUTO
+  bool persistent = false;
+  if (o->loop == PK_LOOP_PERSISTENT) {
+    if (o->variant != PK_VARIANT_PIPELINED) {
+      set_error("PK_LOOP_PERSISTENT runs the pipelined forms of CG and BiCGStab only");
+      return PK_ERR_ARG;
+    }
+    if (!bicgstab_persistent_usable(A)) {
+      set_error("PK_LOOP_PERSISTENT: the persistent BiCGStab loop needs n <= 16 x 4096 rows (one thread-block cluster) and cluster launch");
+      return PK_ERR_ARG;
+    }
+    persistent = true;
+  } else if (o->loop == PK_LOOP_AUTO) {
+    persistent = o->variant == PK_VARIANT_PIPELINED && A->n <= PK_PERSISTENT_BICGSTAB_AUTO_N &&
+                 A->nnz <= PK_PERSISTENT_BICGSTAB_AUTO_NNZ && !(o->flags & PK_FLAG_TIMING) &&
+                 bicgstab_persistent_usable(A);
+  }
   cudaEvent_t e0, e1;
   PK_CUDA(cudaEventCreate(&e0));
   PK_CUDA(cudaEventCreate(&e1));
@@ -451,7 +472,7 @@ pk_status bicgstab_solve(pk_csr* A, const double* b, double* x, const pk_opts* o
   if ((e = work_vec(A, 0, &r)) || (e = work_vec(A, 1, &p)) || (e = work_vec(A, 2, &ap)) ||
       (e = work_vec(A, 3, &sv)) || (e = work_vec(A, 4, &as)) || (e = work_vec(A, 5, &r0s)))
     return e;
-  const bool tma = A->tma_ok && !(o->flags & PK_FLAG_NO_TMA) && o->variant == PK_VARIANT_PIPELINED;
+  const bool tma = A->tma_ok && !(o->flags & PK_FLAG_NO_TMA) && o->variant == PK_VARIANT_PIPELINED && !persistent;
   // the classical form's SpMV runs on the same tile engine (only the fusion differs)
   const bool tma_spmv = A->tma_ok && !(o->flags & PK_FLAG_NO_TMA);
   double* xd = v.x_dev;
@@ -486,6 +507,25 @@ pk_status bicgstab_solve(pk_csr* A, const double* b, double* x, const pk_opts* o
   launch_zero_x(A, xd, s);
   launches += 2;
   PK_CUDA(cudaGetLastError());
+  if (persistent) {
+    if ((e = T.begin(PK_SLOT_OTHER))) return e;
+    if ((e = launch_bicgstab_persistent(A, xd, r, r0s, s))) return e;
+    if ((e = T.end())) return e;
+    launches += 1;
+    if ((e = T.flush())) return e;
+    if (jac.A) {
+      if ((e = jacobi_right_leave(&jac, xd, s))) return e;
+      launches += 2;
+    }
+    if ((e = finish_info(A, o, info, s, v, e0, e1, launches))) return e;
+    for (int k = 0; k < PK_MAX_KERNEL_SLOTS; ++k) {
+      info->kernel_count[k] = T.count[k];
+      info->kernel_ms[k] = T.count[k] ? T.ms[k] / T.count[k] : 0.0;
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    return (pk_status)info->status;
+  }
 
   LoopSpec L;
   L.keys[0] = xd;

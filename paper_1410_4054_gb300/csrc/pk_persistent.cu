@@ -14,13 +14,9 @@
 // <r,r> and take the same exit decision.  Control flow is uniform across the cluster (no CTA
 // leaves a loop another one continues), there is no spin-wait, and a final cluster barrier
 // keeps every CTA's shared memory alive until the last remote read.
-#include <cooperative_groups.h>
-
 #include <algorithm>
 
-#include "pk_internal.cuh"
-
-namespace cg = cooperative_groups;
+#include "pk_cluster.cuh"
 
 namespace pk {
 
@@ -41,72 +37,6 @@ struct ClusterArgs {
   double* p;
   DevState* st;
 };
-
-// Fixed-order block sum of NV values, broadcast to every thread.  GB300 issues about two
-// FP64 operations per clock per SM and an FP64 add has a long latency, so the sum is done by
-// one warp with short dependency chains: every thread stages its values in shared memory,
-// each lane of warp 0 adds kCT/32 = 16 of them as a pairwise tree (depth 4, the NV sums
-// interleaved), and a butterfly finishes (both partners of a pair add the same two values,
-// so every lane ends with the same bits).
-template <int NV>
-__device__ __forceinline__ void block_sum(const double (&v)[NV], double* buf, double (&out)[NV]) {
-  static_assert(kCT / 32 == 16, "the tree below adds 16 values per lane");
-  __shared__ double bc[NV];
-#pragma unroll
-  for (int k = 0; k < NV; ++k) buf[k * kCT + threadIdx.x] = v[k];
-  __syncthreads();
-  if (threadIdx.x < 32) {
-    double t[NV][16];
-#pragma unroll
-    for (int k = 0; k < NV; ++k)
-#pragma unroll
-      for (int m = 0; m < 16; ++m) t[k][m] = buf[k * kCT + m * 32 + threadIdx.x];
-#pragma unroll
-    for (int h = 8; h >= 1; h >>= 1)
-#pragma unroll
-      for (int m = 0; m < h; ++m)
-#pragma unroll
-        for (int k = 0; k < NV; ++k) t[k][m] = t[k][m] + t[k][m + h];
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1)
-#pragma unroll
-      for (int k = 0; k < NV; ++k) t[k][0] += __shfl_xor_sync(0xffffffffu, t[k][0], o);
-    if (threadIdx.x == 0) {
-#pragma unroll
-      for (int k = 0; k < NV; ++k) bc[k] = t[k][0];
-    }
-  }
-  __syncthreads();
-#pragma unroll
-  for (int k = 0; k < NV; ++k) out[k] = bc[k];
-}
-
-// Cluster total of slots [s0, s0 + NV) of every CTA (after a cluster barrier): lane c of warp
-// 0 reads CTA c's values from distributed shared memory, then a butterfly over the lanes
-// (the NV sums interleaved); every CTA runs the same additions on the same values.
-template <int NV>
-__device__ __forceinline__ void cluster_total(cg::cluster_group& cl, double* slots, int s0,
-                                              double (&out)[NV]) {
-  __shared__ double bc[NV];
-  if (threadIdx.x < 32) {
-    const int C = (int)cl.num_blocks();
-    double t[NV];
-    const double* rem = threadIdx.x < C ? cl.map_shared_rank(slots, (int)threadIdx.x) : nullptr;
-#pragma unroll
-    for (int k = 0; k < NV; ++k) t[k] = rem ? rem[s0 + k] : 0.0;
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1)
-#pragma unroll
-      for (int k = 0; k < NV; ++k) t[k] += __shfl_xor_sync(0xffffffffu, t[k], o);
-    if (threadIdx.x == 0) {
-#pragma unroll
-      for (int k = 0; k < NV; ++k) bc[k] = t[k];
-    }
-  }
-  __syncthreads();
-#pragma unroll
-  for (int k = 0; k < NV; ++k) out[k] = bc[k];
-}
 
 __global__ void __launch_bounds__(kCT, 1) k_cg_cluster(ClusterArgs a) {
   extern __shared__ __align__(16) double sm[];
@@ -148,30 +78,13 @@ __global__ void __launch_bounds__(kCT, 1) k_cg_cluster(ClusterArgs a) {
     double v[2] = {0.0, 0.0};
     for (int l = threadIdx.x; l < nown; l += kCT) {
       const int row = row0 + l;
-      int j = __ldg(a.rp + row);
-      const int j1 = __ldg(a.rp + row + 1);
-      double s = 0.0;
-      for (; j + 4 <= j1; j += 4) {
-        int c[4];
-        double w[4], pv[4];
-#pragma unroll
-        for (int k = 0; k < 4; ++k) { c[k] = __ldg(a.ci + j + k); w[k] = __ldg(a.va + j + k); }
-#pragma unroll
-        for (int k = 0; k < 4; ++k)
-          pv[k] = *cl.map_shared_rank(sp + (c[k] & (R - 1)), c[k] >> a.log_rows);
-#pragma unroll
-        for (int k = 0; k < 4; ++k) s = fma(w[k], pv[k], s);
-      }
-      for (; j < j1; ++j) {
-        const int c = __ldg(a.ci + j);
-        s = fma(__ldg(a.va + j), *cl.map_shared_rank(sp + (c & (R - 1)), c >> a.log_rows), s);
-      }
+      const double s = cluster_row(cl, a.ci, a.va, sp, a.log_rows, __ldg(a.rp + row), __ldg(a.rp + row + 1));
       sa[l] = s;
       v[0] = fma(s, s, v[0]);
       v[1] = fma(sp[l], s, v[1]);
     }
     double t[2];
-    block_sum<2>(v, buf, t);
+    cluster_block_sum<kCT, 2>(v, buf, t);
     if (threadIdx.x == 0) { slots[0] = t[0]; slots[1] = t[1]; }
     cl.sync();
     cluster_total<2>(cl, slots, 0, t);
@@ -212,7 +125,7 @@ __global__ void __launch_bounds__(kCT, 1) k_cg_cluster(ClusterArgs a) {
       w[0] = fma(rn, rn, w[0]);
     }
     double u[1];
-    block_sum<1>(w, buf, u);
+    cluster_block_sum<kCT, 1>(w, buf, u);
     if (threadIdx.x == 0) slots[2] = u[0];
     cl.sync();
     cluster_total<1>(cl, slots, 2, u);

@@ -25,6 +25,8 @@ PRECISIONS = {"fp64": 0, "mixed": 1}
 LOOPS = {"graph": 0, "host": 1, "persistent": 2, "auto": 3, "resident": 4}
 PERSISTENT_AUTO_N = 65536  # PK_PERSISTENT_AUTO_N
 PERSISTENT_AUTO_NNZ = 393216  # PK_PERSISTENT_AUTO_NNZ
+PERSISTENT_BICGSTAB_AUTO_N = 32768  # PK_PERSISTENT_BICGSTAB_AUTO_N
+PERSISTENT_BICGSTAB_AUTO_NNZ = 262144  # PK_PERSISTENT_BICGSTAB_AUTO_NNZ
 FLAG_TIMING = 1
 FLAG_TRUE_RES = 2
 FLAG_NO_TMA = 4

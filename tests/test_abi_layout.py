@@ -16,8 +16,10 @@ CONSTANTS = {
     "PK_ERR_NAN": "PK_ERR_NAN", "PK_TIMEOUT": "PK_TIMEOUT",
     "FLAG_TIMING": "PK_FLAG_TIMING", "FLAG_TRUE_RES": "PK_FLAG_TRUE_RES", "FLAG_NO_TMA": "PK_FLAG_NO_TMA",
     "FLAG_AUTOTUNE": "PK_FLAG_AUTOTUNE", "FLAG_SELL": "PK_FLAG_SELL", "FLAG_CGS2": "PK_FLAG_CGS2",
-    "FLAG_TEST_STALL": "PK_FLAG_TEST_STALL",
+    "FLAG_TEST_STALL": "PK_FLAG_TEST_STALL", "FLAG_GM_SHIFT": "PK_FLAG_GM_SHIFT",
     "PERSISTENT_AUTO_N": "PK_PERSISTENT_AUTO_N", "PERSISTENT_AUTO_NNZ": "PK_PERSISTENT_AUTO_NNZ",
+    "PERSISTENT_BICGSTAB_AUTO_N": "PK_PERSISTENT_BICGSTAB_AUTO_N",
+    "PERSISTENT_BICGSTAB_AUTO_NNZ": "PK_PERSISTENT_BICGSTAB_AUTO_NNZ",
     "MAX_SLOTS": "PK_MAX_KERNEL_SLOTS",
 }
 TABLES = {

@@ -79,14 +79,19 @@ JACOBI_MATRICES = {
 }
 
 
-@pytest.mark.parametrize("variant", ["pipelined", "classical"])
-@pytest.mark.parametrize("name", sorted(MATRICES) + [f"jacobi:{k}" for k in sorted(JACOBI_MATRICES)])
-def test_bicgstab_parity(name, variant):
+PARITY_CASES = [(n, v, lp) for n in sorted(MATRICES) + [f"jacobi:{k}" for k in sorted(JACOBI_MATRICES)]
+                for v, lp in (("classical", "graph"), ("pipelined", "graph"), ("pipelined", "persistent"))]
+
+
+@pytest.mark.parametrize("name,variant,loop", PARITY_CASES)
+def test_bicgstab_parity(name, variant, loop):
     """Bars: alpha/omega/beta within max(1e-12, 100 x the oracle's own one-ulp spread) per
     iteration; the median iteration count over b and eight one-ulp perturbations of it within
     half the oracle's range + 2 of the oracle's median (count_gate); x at the oracle's
     iteration count within max(1e-9, 10 x the oracle's own spread); true residual <= tol.
-    'jacobi:' cases: right preconditioning with M = diag(A) on both sides."""
+    'jacobi:' cases: right preconditioning with M = diag(A) on both sides.  loop 'graph': the
+    four fused kernels per iteration; 'persistent': the whole loop on one thread-block
+    cluster."""
     precond = "jacobi" if name.startswith("jacobi:") else "none"
     a = JACOBI_MATRICES[name[7:]]() if precond == "jacobi" else MATRICES[name]()
     _, b, _ = W.manufactured(a, seed=0)
@@ -94,12 +99,14 @@ def test_bicgstab_parity(name, variant):
     assert ref["status"] == O.OK
     A = pk.CSRMatrix.from_workload(a)
     info, x, tr = solve(a, b, A=A, tol=1e-8, maxit=5000, variant=variant, flags=pk.FLAG_TRUE_RES,
-                        precond=precond)
+                        precond=precond, loop=loop)
     assert info["status"] == pk.PK_OK, info
-    case = f"{name} {variant}"
+    if loop == "persistent":
+        assert info["launches"] <= 4 + (2 if precond == "jacobi" else 0), info["launches"]  # (+1: true residual)
+    case = f"{name} {variant} {loop}"
     # the iteration count: the GPU's counts on the same right-hand sides as the oracle's
     gpu_counts = [info["iters"]] + [solve(a, perturbed_b(W, b, k), A=A, tol=1e-8, maxit=5000, variant=variant,
-                                          precond=precond)[0]["iters"] for k in range(len(orc_counts) - 1)]
+                                          precond=precond, loop=loop)[0]["iters"] for k in range(len(orc_counts) - 1)]
     d_med = abs(median(gpu_counts) - median(orc_counts))
     record("bicgstab_parity", case, "iterations (one run)", abs(info["iters"] - ref["iters"]), 2,
            count_gate(orc_counts), oracle_counts=orc_counts, gpu_counts=gpu_counts)
@@ -113,7 +120,7 @@ def test_bicgstab_parity(name, variant):
                oracle_spread=float(spread[:k].max()))
         assert np.all(dev_ <= bar), (key, dev_, bar)
     assert info["rel_res_true"] <= 1.5e-8
-    info2, x2, _ = solve(a, b, tol=0.0, maxit=ref["iters"], variant=variant, precond=precond)
+    info2, x2, _ = solve(a, b, tol=0.0, maxit=ref["iters"], variant=variant, precond=precond, loop=loop)
     assert info2["iters"] == ref["iters"]
     d_x = rel(x2, fixed["x"])
     record("bicgstab_parity", case, "x at the oracle's count", d_x, 1e-9, max(1e-9, 10 * x_spread),
@@ -170,16 +177,16 @@ def test_bicgstab_launch_counts():
 def test_bicgstab_edge_cases():
     a = W.convdiff_3d(6)
     _, b, _ = W.manufactured(a)
-    for variant in ("pipelined", "classical"):
-        info, x, _ = solve(a, np.zeros(a.n), x0=np.ones(a.n), variant=variant)
+    for variant, loop in (("pipelined", "graph"), ("pipelined", "persistent"), ("classical", "graph")):
+        info, x, _ = solve(a, np.zeros(a.n), x0=np.ones(a.n), variant=variant, loop=loop)
         assert info["status"] == pk.PK_OK and info["iters"] == 0 and not x.any()
-        info, _, _ = solve(a, b, maxit=0, variant=variant)
+        info, _, _ = solve(a, b, maxit=0, variant=variant, loop=loop)
         assert info["status"] == pk.PK_NOT_CONVERGED and info["iters"] == 0
         xs = np.linalg.solve(a.to_dense(), b)
-        info, _, _ = solve(a, b, x0=xs, variant=variant)
+        info, _, _ = solve(a, b, x0=xs, variant=variant, loop=loop)
         assert info["status"] == pk.PK_OK and info["iters"] == 0
         # early exit on a small s: b = A e_j for a diagonal-dominant row converges fast
-        for loop in ("graph", "host"):
+        for loop in ("graph", "host") + (("persistent",) if variant == "pipelined" else ()):
             ref = O.bicgstab(a, b, tol=1e-3, maxit=100, variant=variant)
             info, x, _ = solve(a, b, tol=1e-3, maxit=100, variant=variant, loop=loop)
             assert info["status"] == pk.PK_OK and abs(info["iters"] - ref["iters"]) <= 1
@@ -222,3 +229,51 @@ def test_bicgstab_large_convdiff():
     assert d_x <= max(1e-9, 10 * x_spread)
     info, _, _ = solve(a, b, A=A, tol=1e-8, maxit=10_000, flags=pk.FLAG_TRUE_RES)
     assert info["status"] == pk.PK_OK and info["rel_res_true"] <= 1.5e-8
+
+
+def test_bicgstab_persistent_loop_selection_and_limits():
+    """PK_LOOP_AUTO runs small pipelined solves on one cluster (three launches: setup, x = 0
+    test, the loop) with the same iterates as PK_LOOP_PERSISTENT, and the graph above
+    PK_PERSISTENT_BICGSTAB_AUTO_N; the persistent loop takes the pipelined form only and n up to
+    16 x 4096 rows; a breakdown (<Ap, r0*> = 0 exactly: a skew-symmetric matrix and an
+    integer right-hand side) is reported;
+    maxit stops it with PK_NOT_CONVERGED after exactly maxit iterations."""
+    a = W.convdiff_3d(20)
+    _, b, _ = W.manufactured(a, seed=4)
+    A = pk.CSRMatrix.from_workload(a)
+    ia, xa, ta = solve(a, b, A=A, loop="auto")
+    ip, xp, tp = solve(a, b, A=A, loop="persistent")
+    assert ia["launches"] == 3 and ia["iters"] == ip["iters"] and np.array_equal(xa, xp)
+    assert np.array_equal(ta, tp, equal_nan=True)
+    with pytest.raises(RuntimeError, match="PK_LOOP_PERSISTENT"):
+        solve(a, b, A=A, loop="persistent", variant="classical")
+    big = W.convdiff_3d(41)  # 68,921 rows
+    _, bb, _ = W.manufactured(big, seed=1)
+    with pytest.raises(RuntimeError, match="PK_LOOP_PERSISTENT"):
+        solve(big, bb, loop="persistent")
+    mid = W.convdiff_3d(36)  # 46,656 rows: fits one cluster, above the automatic threshold
+    _, bm, _ = W.manufactured(mid, seed=1)
+    ig, _, _ = solve(mid, bm, loop="auto", tol=0.0, maxit=3)
+    ip, _, _ = solve(mid, bm, loop="persistent", tol=0.0, maxit=3)
+    assert ig["launches"] > 3 and ip["launches"] == 3
+    # skew-symmetric A: <Ap, r0*> = <A r0, r0> = 0 at the first step
+    n = 64
+    rp = np.arange(0, 2 * n + 1, 2, dtype=np.int32)
+    ci = np.empty(2 * n, np.int32)
+    va = np.empty(2 * n)
+    for i in range(n):
+        ci[2 * i], ci[2 * i + 1] = (i - 1) % n, (i + 1) % n
+        va[2 * i], va[2 * i + 1] = -1.0, 1.0
+    order = np.argsort(ci.reshape(n, 2), axis=1)
+    ci = np.take_along_axis(ci.reshape(n, 2), order, 1).ravel()
+    va = np.take_along_axis(va.reshape(n, 2), order, 1).ravel()
+    sk = W.CSR(n, rp, ci, va, "skew_cycle")
+    bs = np.round(3 * W.uniform_pm1(7, n))  # small integers: every product and sum is exact
+    ref = O.bicgstab(sk, bs, tol=1e-10, maxit=50, variant="pipelined")
+    info, _, _ = solve(sk, bs, tol=1e-10, maxit=50, loop="persistent")
+    assert ref["status"] == O.BREAKDOWN and info["status"] == pk.PK_BREAKDOWN
+    ref = O.bicgstab(a, b, tol=0.0, maxit=7, variant="pipelined")
+    info, x, tr = solve(a, b, A=A, tol=0.0, maxit=7, loop="persistent")
+    assert info["status"] == pk.PK_NOT_CONVERGED and info["iters"] == 7
+    assert rel(x, ref["x"]) <= 1e-10
+    np.testing.assert_allclose(tr[:7, 0], ref["alpha"][:7], rtol=1e-12)

@@ -144,11 +144,12 @@ def test_cg_persistent_too_large_falls_back_under_auto():
 
 
 def test_cg_persistent_rejects_other_forms():
+    """The persistent loop runs pipelined CG and pipelined BiCGStab (tested with BiCGStab)."""
     a = W.laplace_2d(16)
     _, b, _ = W.manufactured(a)
     A = pk.CSRMatrix.from_workload(a)
     for call, kw in ((pk.cg_solve, dict(variant="classical")), (pk.cg_solve, dict(precision="mixed")),
-                     (pk.bicgstab_solve, {}), (pk.gmres_solve, {})):
+                     (pk.bicgstab_solve, dict(variant="classical")), (pk.gmres_solve, {})):
         with pytest.raises(RuntimeError, match="PERSISTENT"):
             call(A, dev(b), dev(np.zeros(a.n)), loop="persistent", **kw)
 
