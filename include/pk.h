@@ -402,8 +402,8 @@ pk_status pk_residual_norm2(pk_csr* A, const double* b, const double* x, double*
 /*
  * Learned initial guess for transient problems (an extension; the paper has no counterpart): a 4-layer 3x3x3
  * convolutional network on a D x H x W grid, BF16 operands with FP32 accumulation on the
- * tensor cores as implicit GEMMs (tcgen05 for the forward and backward-data passes, the
- * warp-level m16n8k16 MMA for the weight gradient).  Activations are channels-last BF16
+ * tensor cores as implicit GEMMs on tcgen05 (forward and backward-data: M = 128-voxel tiles;
+ * weight gradient: M = 8 taps x 16 input channels, K = voxels).  Activations are channels-last BF16
  * [D][H][W][16] with channel counts padded to 16 (padded channels are zero); weights are BF16
  * [27][16 co][16 ci], tap = 9(dz+1) + 3(dy+1) + (dx+1); zero padding 1 at the boundary.
  * All pointers are device pointers; calls are stream-ordered and return at once.
@@ -421,7 +421,9 @@ pk_status pk_conv3d_fwd(const void* X, const void* Wt, const float* bias, void* 
  * otherwise.  Synchronises the stream. */
 pk_status pk_conv3d_check(void* stream);
 /* dW[tap][co][ci] = sum_v G[v][co] A[v + tap][ci] (FP32), db[co] = sum_v G[v][co]; scratch:
- * pk_conv3d_wgrad_scratch_floats(D, H, W) floats (deterministic block partials). */
+ * pk_conv3d_wgrad_scratch_floats(D, H, W) floats (deterministic block partials).  A and G
+ * 16-byte aligned (PK_ERR_ARG otherwise); a timed-out wait of the tensor-core kernel is
+ * reported by pk_conv3d_check. */
 int64_t pk_conv3d_wgrad_scratch_floats(int32_t D, int32_t H, int32_t W);
 pk_status pk_conv3d_wgrad(const void* A, const void* G, float* scratch, float* dW, float* db,
                           int32_t D, int32_t H, int32_t W, void* stream);

@@ -9,9 +9,9 @@
 // input blocks, one M128 N16 K16 MMA per tap, FP32 accumulators in tensor memory).  The
 // backward-data pass is the same kernel on flipped, transposed weights with the ReLU mask of
 // the layer input applied in the epilogue.
-// Weight gradient (conv3d_wgrad, warp-level mma.sync): dW[tap] = G^T A_shift(tap), M = 16 output channels,
-// N = 16 input channels, K = voxels: each block accumulates a band of rows in registers
-// (warp w owns taps w, w+4, ...), operands transposed on the fly with ldmatrix.trans, then a
+// Weight gradient (conv3d_wgrad): tcgen05 as well, the taps stacked into M (8 taps x 16 input
+// channels per M128 tile), N = 16 output channels, K = voxels; the K-major operands are
+// written per 64-voxel segment with ldmatrix.trans / stmatrix (see k_conv3d_wgrad_tc), then a
 // fixed-order reduction over blocks (deterministic).
 #include <cuda.h>
 #include <cuda_bf16.h>
@@ -23,40 +23,7 @@
 namespace pk {
 
 constexpr int kCh = 16;         // channels (padded)
-constexpr int kSeg = 64;        // voxels per x segment = 4 warps x 16
-constexpr int kHx = kSeg + 2;   // with the +-1 halo
-constexpr int kVs = 24;         // shared-memory stride of one voxel in BF16 (48 bytes)
-constexpr int kWgradRows = 16;  // (z, y) rows per weight-gradient block
 
-__device__ __forceinline__ uint32_t sa(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
-
-__device__ __forceinline__ void ldsm4t(uint32_t (&r)[4], const void* p) {
-  asm volatile("ldmatrix.sync.aligned.m8n8.x4.trans.shared.b16 {%0,%1,%2,%3}, [%4];"
-               : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3])
-               : "r"(sa(p)));
-}
-
-// D = A B + D, A 16x16 BF16 (row), B 16x8 BF16 (col), D 16x8 FP32.
-__device__ __forceinline__ void mma16816(float (&d)[4], const uint32_t (&a)[4], uint32_t b0, uint32_t b1) {
-  asm volatile(
-      "mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, "
-      "{%0,%1,%2,%3};"
-      : "+f"(d[0]), "+f"(d[1]), "+f"(d[2]), "+f"(d[3])
-      : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b0), "r"(b1));
-}
-
-// Stage the 9 rows (z+dz, y+dy), x in [x0-1, x0+64], into halo[9][66][kVs] (zeros outside).
-__device__ __forceinline__ void load_halo(__nv_bfloat16* halo, const __nv_bfloat16* __restrict__ X,
-                                          int D, int H, int W, int z, int y, int x0) {
-  for (int e = threadIdx.x; e < 9 * kHx * 2; e += blockDim.x) {
-    const int half = e & 1, xx = (e >> 1) % kHx, zy = (e >> 1) / kHx;
-    const int zz = z + zy / 3 - 1, yy = y + zy % 3 - 1, x = x0 + xx - 1;
-    uint4 v = make_uint4(0, 0, 0, 0);
-    if (zz >= 0 && zz < D && yy >= 0 && yy < H && x >= 0 && x < W)
-      v = *reinterpret_cast<const uint4*>(X + (((size_t)zz * H + yy) * W + x) * kCh + 8 * half);
-    *reinterpret_cast<uint4*>(halo + (zy * kHx + xx) * kVs + 8 * half) = v;
-  }
-}
 
 struct ConvArgs {
   const __nv_bfloat16* X;     // input activations [D][H][W][16]
@@ -323,91 +290,273 @@ __global__ void __launch_bounds__(128) k_conv3d_tc(const __grid_constant__ CUten
   }
 }
 
-// Weight and bias gradients of one band of rows: partial[block][tap][co][ci], partial_db[block][co].
-__global__ void __launch_bounds__(128) k_conv3d_wgrad(const __nv_bfloat16* __restrict__ A,
-                                                      const __nv_bfloat16* __restrict__ G,
-                                                      float* partial, float* partial_db, int D,
-                                                      int H, int W) {
-  extern __shared__ __align__(128) unsigned char smem_raw[];
-  __nv_bfloat16* halo = reinterpret_cast<__nv_bfloat16*>(smem_raw);
-  __nv_bfloat16* gsm = halo + 9 * kHx * kVs;
+// ---------------------------------------------------------------- tcgen05 weight gradient
+// dW[tap][co][ci] = sum_v G[v][co] A[v + tap][ci] as implicit GEMMs on the tensor cores:
+// M = (tap, ci) rows, 8 taps x 16 input channels per M128 tile (4 tiles hold the 27 taps),
+// N = 16 output channels, K = voxels.  A block takes 64-voxel x segments of (z, y) rows in
+// turn.  For a segment, TMA brings the 3 x 3 neighbouring rows of A with the x halo (a box of
+// [3][3][66][8] per channel half, zeros outside the grid) and the segment of G ([64][8] per
+// half) into one of two staging buffers, two segments ahead.  The four warps then write the
+// K-major operands of the MMAs -- the im2col of the 27 shifted copies of A, and G transposed
+// -- with ldmatrix.trans / stmatrix: each 8 x 8 block of [voxel][channel] becomes the
+// [channel][voxel] core matrix of the no-swizzle K-major layout (8 rows of 16 bytes;
+// K-adjacent core matrices kWgLbo bytes apart, M-adjacent 128).  One thread issues 4 tiles x
+// 4 K-steps of M128 N16 K16 MMAs into four FP32 accumulators in tensor memory that persist
+// over all of the block's segments; two operand buffers alternate, so the tensor core works
+// on one segment while the next is written.  Every wait is bounded (a wait that runs out sets
+// the device flag that pk_conv3d_check reports, and the block waits, bounded, for what it
+// issued before it frees its tensor memory).  At the end each thread reads its accumulator
+// lane (one (tap, ci) row, 16 co) into the block's partial; a fixed-order reduction over
+// blocks follows (deterministic).
+constexpr int kWgSeg = 64;                       // voxels (K) per segment
+constexpr int kWgTiles = 4;                      // M128 tiles: taps 0-7, 8-15, 16-23, 24-26
+constexpr int kWgKg = kWgSeg / 8;                // K core matrices per segment
+constexpr int kWgLbo = 16 * 128;                 // bytes between K-adjacent core matrices of A
+constexpr int kWgTile = kWgKg * kWgLbo;          // 16 KB per M128 tile
+constexpr int kWgA = kWgTiles * kWgTile;         // 64 KB: A operand of one segment
+constexpr int kWgB = kWgKg * 256;                // 2 KB: G^T (N = 16 rows) of one segment
+constexpr int kWgHx = kWgSeg + 2;                // staged x extent of A (halo of one)
+constexpr int kWgHalf = (9 * kWgHx * 16 + 127) & ~127;  // one channel half of the A box (9,600)
+constexpr int kWgStageA = 2 * kWgHalf;
+constexpr int kWgStage = kWgStageA + 2 * kWgSeg * 16;   // + G, two halves of [64][8]
+constexpr int kWgOp = kWgA + kWgB;              // one operand buffer: A, then G^T (66 KB)
+constexpr int kWgStages = 3;                     // staging buffers (TMA two segments ahead)
+constexpr int kWgSmem = 2 * kWgOp + kWgStages * kWgStage;
+constexpr int kWgMaxBlocks = 256;
+constexpr uint32_t kWgCols = 64;                 // tensor memory: 4 accumulators x 16 columns
+constexpr uint32_t kWgStageBytes = 2 * 9 * kWgHx * 16 + 2 * kWgSeg * 16;  // TMA bytes per segment
+constexpr int kWgThreads = 256;                  // 8 warps write the operands
+
+__device__ __forceinline__ void ldsm4t(uint32_t (&r)[4], uint32_t addr) {
+  asm volatile("ldmatrix.sync.aligned.m8n8.x4.trans.shared.b16 {%0,%1,%2,%3}, [%4];"
+               : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3])
+               : "r"(addr));
+}
+
+__device__ __forceinline__ void stsm4(uint32_t addr, const uint32_t (&r)[4]) {
+  asm volatile("stmatrix.sync.aligned.m8n8.x4.shared.b16 [%0], {%1,%2,%3,%4};" ::"r"(addr), "r"(r[0]), "r"(r[1]),
+               "r"(r[2]), "r"(r[3])
+               : "memory");
+}
+
+__global__ void __launch_bounds__(kWgThreads + 32) k_conv3d_wgrad_tc(const __grid_constant__ CUtensorMap amap,
+                                                                   const __grid_constant__ CUtensorMap gmap,
+                                                                   float* partial, float* partial_db, int D,
+                                                                   int H, int W) {
+  extern __shared__ __align__(1024) unsigned char smem_wg[];
+  unsigned char* obuf = smem_wg;                                // 2 x kWgOp operand buffers
+  unsigned char* stage = smem_wg + 2 * kWgOp;                   // kWgStages staging buffers
+  __shared__ __align__(8) uint64_t full_bar[kWgStages];         // staging buffer loaded (TMA)
+  __shared__ __align__(8) uint64_t ready_bar[2];                // operands written (8 warps)
+  __shared__ __align__(8) uint64_t free_bar[2];                 // operands read (MMA commit)
+  __shared__ uint32_t tmem_slot;
+  __shared__ int abort_flag, consumed;
+  __shared__ float dbs[kWgThreads / kCh][kCh];
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int j = lane >> 3, r = lane & 7;
-  float acc[7][2][4];
+  const bool control = warp == kWgThreads / 32;  // warp 8, lane 0: copies and MMAs
+  const int nseg = (W + kWgSeg - 1) / kWgSeg;
+  const int64_t nchunks = (int64_t)D * H * nseg;
+  const int mine = blockIdx.x < nchunks ? (int)((nchunks - 1 - blockIdx.x) / gridDim.x + 1) : 0;
+  // the rows of tile 3 past tap 26 are never written: zero them (their accumulator rows are
+  // not read, but the tensor core reads the operand)
+  for (int e = threadIdx.x; e < 2 * kWgOp / 16; e += blockDim.x)
+    reinterpret_cast<uint4*>(obuf)[e] = make_uint4(0, 0, 0, 0);
+  proxy_fence();
+  if (threadIdx.x == 0) {
+    for (int k = 0; k < kWgStages; ++k) mbar_init(&full_bar[k], 1);
+    for (int k = 0; k < 2; ++k) {
+      mbar_init(&ready_bar[k], kWgThreads / 32);
+      mbar_init(&free_bar[k], 1);
+    }
+    mbar_fence_init();
+    abort_flag = 0;
+    consumed = 0;
+  }
+  if (warp == 0) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_addr(&tmem_slot)),
+                 "r"(kWgCols)
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+  }
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tmem = tmem_slot;
+  const uint32_t o_base = smem_addr(obuf), s_base = smem_addr(stage);
+  float db = 0.f;  // builders: output channel t % 16 over voxels (t / 16) + 16 k of every segment
+  if (control) {
+    if (lane == 0) {
+      // the TMA copies of segment j into staging buffer j % kWgStages
+      auto load = [&](int j) {
+        const int64_t c = blockIdx.x + (int64_t)j * gridDim.x;
+        const int seg = (int)(c % nseg), zy = (int)(c / nseg);
+        const int z = zy / H, y = zy % H, x0 = seg * kWgSeg;
+        const int sb = j % kWgStages;
+        const uint32_t st = s_base + sb * kWgStage;
+        mbar_expect_tx(&full_bar[sb], kWgStageBytes);
+        for (int h = 0; h < 2; ++h) {
+          tc_tma_box(st + h * kWgHalf, &amap, 8 * h, x0 - 1, y - 1, z - 1, &full_bar[sb]);
+          tc_tma_box(st + kWgStageA + h * kWgSeg * 16, &gmap, 8 * h, x0, y, z, &full_bar[sb]);
+        }
+      };
+      int loaded = 0, issued = 0;
+      for (; loaded < min(kWgStages, mine); ++loaded) load(loaded);
+      for (int j = 0; j < mine; ++j) {
+        const int b = j & 1;
+        if (!mbar_wait(&ready_bar[b], (j >> 1) & 1) || *(volatile int*)&abort_flag) {
+          abort_flag = 1;
+          break;
+        }
+        // staging buffer j % kWgStages has been read: refill it with segment j + kWgStages
+        if (loaded < mine) load(loaded++);
+        tc_fence_after();
+        const uint32_t ob = o_base + b * kWgOp;
 #pragma unroll
-  for (int q = 0; q < 7; ++q)
+        for (int ks = 0; ks < kWgKg / 2; ++ks)
 #pragma unroll
-    for (int nt = 0; nt < 2; ++nt)
-#pragma unroll
-      for (int k = 0; k < 4; ++k) acc[q][nt][k] = 0.f;
-  float db = 0.f;  // thread c < 16: bias gradient of output channel c
-  const int row_lo = blockIdx.x * kWgradRows, row_hi = min(D * H, row_lo + kWgradRows);
-  for (int zy = row_lo; zy < row_hi; ++zy) {
-    const int z = zy / H, y = zy % H;
-    for (int x0 = 0; x0 < W; x0 += kSeg) {
-      __syncthreads();
-      load_halo(halo, A, D, H, W, z, y, x0);
-      for (int e = threadIdx.x; e < kSeg * 2; e += blockDim.x) {
-        const int half = e & 1, xx = e >> 1, x = x0 + xx;
-        uint4 v = make_uint4(0, 0, 0, 0);
-        if (x < W) v = *reinterpret_cast<const uint4*>(G + (((size_t)z * H + y) * W + x) * kCh + 8 * half);
-        *reinterpret_cast<uint4*>(gsm + xx * kVs + 8 * half) = v;
+          for (int t = 0; t < kWgTiles; ++t)
+            tc_mma(tmem + t * 16, tc_desc(ob + t * kWgTile + 2 * ks * kWgLbo, kWgLbo, 128),
+                   tc_desc(ob + kWgA + 2 * ks * 256, 256, 128), (j > 0 || ks > 0) ? 1u : 0u);
+        tc_commit(&free_bar[b]);
+        issued = j + 1;
       }
-      __syncthreads();
-      if (threadIdx.x < kCh) {
-        for (int xx = 0; xx < kSeg; ++xx) db += __bfloat162float(gsm[xx * kVs + threadIdx.x]);
+      // the last commit covers every MMA the block issued
+      if (issued > 0 && !mbar_wait(&free_bar[(issued - 1) & 1], ((issued - 1) >> 1) & 1)) abort_flag = 1;
+      if (abort_flag) {
+        // bounded waits for the copies the builders did not consume before the memory goes
+        for (int k = *(volatile int*)&consumed; k < loaded; ++k)
+          mbar_wait(&full_bar[k % kWgStages], (k / kWgStages) & 1);
       }
+    }
+  } else {
+    // builders: the operand-writing jobs of this thread, 14 blocks of 8 x 8 (two per step of
+    // 8 warps), their source offsets in a staging buffer and destinations in an operand
+    // buffer, the same for every segment: 27 taps x 2 channel halves x 8 K groups of A, then
+    // 2 x 8 of G; lanes 8i .. 8i+7 address the rows of block i of a four-block instruction
+    constexpr int kGroups = (27 * 16 + 16) / 4;  // 112 instructions per segment
+    constexpr int kWarps = kWgThreads / 32;
+    constexpr int kJobs = kGroups / kWarps;      // 14 per warp
+    static_assert(kGroups % (2 * kWarps) == 0, "two instructions per warp per step");
+    uint32_t src_off[kJobs], dst_off[kJobs];
+    {
+      const int r = lane & 7, i = lane >> 3;
 #pragma unroll
-      for (int kk = 0; kk < kSeg / 16; ++kk) {
-        uint32_t af[4];
-        // A = G^T (m = co, k = voxel) from storage rows = voxel, cols = co
-        ldsm4t(af, gsm + (16 * kk + r + 8 * (j >> 1)) * kVs + 8 * (j & 1));
-#pragma unroll
-        for (int q = 0; q < 7; ++q) {
-          const int t = warp + 4 * q;
-          if (t < 27) {
-            const int dzdy = t / 3, dx = t % 3 - 1;
-            uint32_t bf[4];
-            // B = A_shift (k = voxel, n = ci) from storage rows = voxel, cols = ci
-            ldsm4t(bf, halo + (dzdy * kHx + 16 * kk + r + 8 * (j & 1) + dx + 1) * kVs + 8 * (j >> 1));
-            mma16816(acc[q][0], af, bf[0], bf[1]);
-            mma16816(acc[q][1], af, bf[2], bf[3]);
-          }
+      for (int k = 0; k < kJobs; ++k) {
+        const int grp = warp + kWarps * k;
+        const int q = 4 * grp + i;
+        if (q < 27 * 16) {
+          const int tap = q >> 4, h = (q >> 3) & 1, kg = q & 7;
+          const int dzdy = tap / 3, dx = tap % 3 - 1;
+          src_off[k] = h * kWgHalf + (dzdy * kWgHx + kg * 8 + r + dx + 1) * 16;
+          dst_off[k] = (tap >> 3) * kWgTile + kg * kWgLbo + (((tap & 7) << 1) + h) * 128 + r * 16;
+        } else {
+          const int qb = q - 27 * 16, h = qb >> 3, kg = qb & 7;
+          src_off[k] = kWgStageA + h * kWgSeg * 16 + (kg * 8 + r) * 16;
+          dst_off[k] = kWgA + kg * 256 + h * 128 + r * 16;
         }
       }
     }
-  }
-  const int g = lane >> 2, tq = lane & 3;
-  float* P = partial + (size_t)blockIdx.x * 27 * kCh * kCh;
+    const int c = threadIdx.x & (kCh - 1);
+    for (int j = 0; j < mine; ++j) {
+      const int b = j & 1, sb = j % kWgStages;
+      // segment j's data, and operand buffer b free (read by the MMAs of segment j - 2)
+      if (lane == 0) {
+        if (!mbar_wait(&full_bar[sb], (j / kWgStages) & 1) ||
+            (j >= 2 && !mbar_wait(&free_bar[b], ((j - 2) >> 1) & 1)))
+          abort_flag = 1;
+        else if (warp == 0)
+          consumed = j + 1;
+      }
+      __syncwarp();
+      if (*(volatile int*)&abort_flag) break;
+      const uint32_t st = s_base + sb * kWgStage;
+      {
+        const __nv_bfloat16* g16 = reinterpret_cast<const __nv_bfloat16*>(stage + sb * kWgStage + kWgStageA +
+                                                                            (c >> 3) * kWgSeg * 16);
 #pragma unroll
-  for (int q = 0; q < 7; ++q) {
-    const int t = warp + 4 * q;
-    if (t >= 27) continue;
+        for (int xx = threadIdx.x / kCh; xx < kWgSeg; xx += kWgThreads / kCh)
+          db += __bfloat162float(g16[xx * 8 + (c & 7)]);
+      }
+      const uint32_t ob = o_base + b * kWgOp;
 #pragma unroll
-    for (int nt = 0; nt < 2; ++nt) {
-      const int ci = 8 * nt + 2 * tq;
-      P[(t * kCh + g) * kCh + ci] = acc[q][nt][0];
-      P[(t * kCh + g) * kCh + ci + 1] = acc[q][nt][1];
-      P[(t * kCh + g + 8) * kCh + ci] = acc[q][nt][2];
-      P[(t * kCh + g + 8) * kCh + ci + 1] = acc[q][nt][3];
+      for (int k = 0; k < kJobs; k += 2) {  // two instructions' loads in flight before their stores
+        uint32_t f0[4], f1[4];
+        ldsm4t(f0, st + src_off[k]);
+        ldsm4t(f1, st + src_off[k + 1]);
+        stsm4(ob + dst_off[k], f0);
+        stsm4(ob + dst_off[k + 1], f1);
+      }
+      proxy_fence();  // the operands are read by the tensor core (async proxy)
+      __syncwarp();
+      if (lane == 0) mbar_arrive(&ready_bar[b]);
     }
+    dbs[threadIdx.x / kCh][c] = db;
   }
-  if (threadIdx.x < kCh) partial_db[blockIdx.x * kCh + threadIdx.x] = db;
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  float* P = partial + (size_t)blockIdx.x * 27 * kCh * kCh;
+  if (!abort_flag && !control) {
+    // warp w reads tensor-memory lanes 32 (w % 4) .. + 31 of tiles 2 (w / 4) and 2 (w / 4) + 1
+    const int q4 = warp & 3, m = 32 * q4 + lane;  // accumulator row: tap 8t + m / 16, input channel m % 16
+#pragma unroll 1
+    for (int t = 2 * (warp >> 2); t < 2 * (warp >> 2) + 2; ++t) {
+      float v[16];
+      tc_ld16(tmem + ((uint32_t)(32 * q4) << 16) + t * 16, v);
+      const int tap = 8 * t + (m >> 4), ci = m & 15;
+      if (tap < 27) {
+#pragma unroll
+        for (int co = 0; co < 16; ++co) P[(tap * kCh + co) * kCh + ci] = mine > 0 ? v[co] : 0.f;
+      }
+    }
+    if (threadIdx.x < kCh) {
+      float t = 0.f;
+      for (int g = 0; g < kWgThreads / kCh; ++g) t += dbs[g][threadIdx.x];
+      partial_db[blockIdx.x * kCh + threadIdx.x] = t;
+    }
+  } else if (abort_flag && threadIdx.x == 0) {
+    atomicExch(&g_conv_timeout, 1);
+  }
+  tc_fence_before();
+  __syncthreads();
+  if (warp == 0) {
+    tc_fence_after();
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(kWgCols) : "memory");
+  }
 }
 
-// dW = sum over blocks of the partials, in block order (deterministic).
-__global__ void k_conv3d_wgrad_reduce(const float* partial, const float* partial_db, int nblk,
-                                      float* dW, float* db) {
-  const int e = blockIdx.x * blockDim.x + threadIdx.x;
-  if (e < 27 * kCh * kCh) {
-    float s = 0.f;
-    for (int b = 0; b < nblk; ++b) s += partial[(size_t)b * 27 * kCh * kCh + e];
-    dW[e] = s;
-  } else if (e < 27 * kCh * kCh + kCh) {
-    const int c = e - 27 * kCh * kCh;
-    float s = 0.f;
-    for (int b = 0; b < nblk; ++b) s += partial_db[b * kCh + c];
-    db[c] = s;
+// dW = sum over blocks of the partials (deterministic): a block of 8 warps per 32 outputs;
+// warp w adds blocks w, w + 8, ... in order (their loads in flight together), then the 8 sums
+// are added in warp order.
+__global__ void __launch_bounds__(256) k_conv3d_wgrad_reduce(const float* partial, const float* partial_db,
+                                                             int nblk, float* dW, float* db) {
+  __shared__ float part[8][32];
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int e = blockIdx.x * 32 + lane;
+  constexpr int nw = 27 * kCh * kCh;
+  float s = 0.f;
+  if (e < nw + kCh) {
+    const float* src = e < nw ? partial + e : partial_db + (e - nw);
+    const size_t stride = e < nw ? (size_t)nw : (size_t)kCh;
+    int b = warp;
+    for (; b + 8 * 3 < nblk; b += 8 * 4) {
+      const float v0 = src[b * stride], v1 = src[(b + 8) * stride], v2 = src[(b + 16) * stride],
+                  v3 = src[(b + 24) * stride];
+      s += v0;
+      s += v1;
+      s += v2;
+      s += v3;
+    }
+    for (; b < nblk; b += 8) s += src[b * stride];
+  }
+  part[warp][lane] = s;
+  __syncthreads();
+  if (warp == 0 && e < nw + kCh) {
+    float t = 0.f;
+#pragma unroll
+    for (int w = 0; w < 8; ++w) t += part[w][lane];
+    if (e < nw) dW[e] = t;
+    else db[e - nw] = t;
   }
 }
 
@@ -588,7 +737,8 @@ using EncodeTiled = CUresult (*)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, 
                                  CUtensorMapInterleave, CUtensorMapSwizzle, CUtensorMapL2promotion,
                                  CUtensorMapFloatOOBfill);
 
-static pk_status input_map(CUtensorMap* map, const __nv_bfloat16* X, int D, int H, int W) {
+static pk_status input_map(CUtensorMap* map, const __nv_bfloat16* X, int D, int H, int W, int bx = kTcBx,
+                           int by = kTcBy, int bz = 1) {
   static EncodeTiled encode = nullptr;
   if (!encode) {
     void* fn = nullptr;
@@ -602,12 +752,12 @@ static pk_status input_map(CUtensorMap* map, const __nv_bfloat16* X, int D, int 
     encode = reinterpret_cast<EncodeTiled>(fn);
   }
   if (reinterpret_cast<uintptr_t>(X) & 15) {
-    set_error("pk_conv3d_fwd: activations must be 16-byte aligned");
+    set_error("pk_conv3d: activations and gradients must be 16-byte aligned");
     return PK_ERR_ARG;
   }
   const cuuint64_t dims[4] = {(cuuint64_t)kCh, (cuuint64_t)W, (cuuint64_t)H, (cuuint64_t)D};
   const cuuint64_t strides[3] = {(cuuint64_t)kCh * 2, (cuuint64_t)W * kCh * 2, (cuuint64_t)H * W * kCh * 2};
-  const cuuint32_t box[4] = {8, (cuuint32_t)kTcBx, (cuuint32_t)kTcBy, 1};
+  const cuuint32_t box[4] = {8, (cuuint32_t)bx, (cuuint32_t)by, (cuuint32_t)bz};
   const cuuint32_t estr[4] = {1, 1, 1, 1};
   const CUresult r = encode(map, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 4, const_cast<__nv_bfloat16*>(X), dims,
                             strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
@@ -622,13 +772,12 @@ static pk_status input_map(CUtensorMap* map, const __nv_bfloat16* X, int D, int 
 static pk_status conv_setup() {
   static bool done = false;
   if (!done) {
-    const int wg_smem = (9 * kHx * kVs + kSeg * kVs) * 2;
     PK_CUDA(cudaFuncSetAttribute(k_conv3d_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, kTcSmem));
     // several blocks per SM (each with its own chain of accumulating MMAs): the largest
     // shared-memory carveout
     PK_CUDA(cudaFuncSetAttribute(k_conv3d_tc, cudaFuncAttributePreferredSharedMemoryCarveout,
                                  (int)cudaSharedmemCarveoutMaxShared));
-    PK_CUDA(cudaFuncSetAttribute(k_conv3d_wgrad, cudaFuncAttributeMaxDynamicSharedMemorySize, wg_smem));
+    PK_CUDA(cudaFuncSetAttribute(k_conv3d_wgrad_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, kWgSmem));
     done = true;
   }
   return PK_OK;
@@ -701,10 +850,15 @@ pk_status pk_conv3d_check(void* stream) {
   return PK_OK;
 }
 
+// Blocks of the weight-gradient launch: one per SM (its shared memory allows one), at most
+// one per segment and at most kWgMaxBlocks (the scratch size).
+static int wgrad_blocks(int32_t D, int32_t H, int32_t W, int sms) {
+  const int64_t chunks = (int64_t)D * H * ((W + kWgSeg - 1) / kWgSeg);
+  return (int)std::max<int64_t>(1, std::min<int64_t>(chunks, std::min(sms, kWgMaxBlocks)));
+}
+
 int64_t pk_conv3d_wgrad_scratch_floats(int32_t D, int32_t H, int32_t W) {
-  (void)W;
-  const int64_t nblk = ((int64_t)D * H + kWgradRows - 1) / kWgradRows;
-  return nblk * (27 * kCh * kCh + kCh);
+  return (int64_t)wgrad_blocks(D, H, W, kWgMaxBlocks) * (27 * kCh * kCh + kCh);
 }
 
 pk_status pk_conv3d_wgrad(const void* A, const void* G, float* scratch, float* dW, float* db,
@@ -715,15 +869,26 @@ pk_status pk_conv3d_wgrad(const void* A, const void* G, float* scratch, float* d
   }
   pk_status e = conv_setup();
   if (e) return e;
-  const int nblk = (int)(((int64_t)D * H + kWgradRows - 1) / kWgradRows);
+  static int sms = 0;
+  if (!sms) {
+    int dev = 0;
+    PK_CUDA(cudaGetDevice(&dev));
+    PK_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+  }
+  const int nblk = wgrad_blocks(D, H, W, sms);
+  // partials laid out for the scratch size's block count (the launch may use fewer blocks)
+  const int nmax = wgrad_blocks(D, H, W, kWgMaxBlocks);
   float* partial = scratch;
-  float* partial_db = scratch + (size_t)nblk * 27 * kCh * kCh;
-  const int smem = (9 * kHx * kVs + kSeg * kVs) * 2;
+  float* partial_db = scratch + (size_t)nmax * 27 * kCh * kCh;
   cudaStream_t s = (cudaStream_t)stream;
-  k_conv3d_wgrad<<<nblk, 128, smem, s>>>(static_cast<const __nv_bfloat16*>(A),
-                                         static_cast<const __nv_bfloat16*>(G), partial, partial_db,
-                                         D, H, W);
-  k_conv3d_wgrad_reduce<<<(27 * kCh * kCh + kCh + 255) / 256, 256, 0, s>>>(partial, partial_db, nblk, dW, db);
+  // A: boxes of [3 z][3 y][66 x][8 channels] (a segment's neighbour rows with the x halo);
+  // G: [64 x][8 channels]
+  CUtensorMap amap, gmap;
+  if ((e = input_map(&amap, static_cast<const __nv_bfloat16*>(A), D, H, W, kWgHx, 3, 3)) ||
+      (e = input_map(&gmap, static_cast<const __nv_bfloat16*>(G), D, H, W, kWgSeg, 1, 1)))
+    return e;
+  k_conv3d_wgrad_tc<<<nblk, kWgThreads + 32, kWgSmem, s>>>(amap, gmap, partial, partial_db, D, H, W);
+  k_conv3d_wgrad_reduce<<<(27 * kCh * kCh + kCh + 31) / 32, 256, 0, s>>>(partial, partial_db, nblk, dW, db);
   PK_CUDA(cudaGetLastError());
   return PK_OK;
 }
