@@ -291,41 +291,62 @@ __global__ void __launch_bounds__(128) k_conv3d_tc(const __grid_constant__ CUten
 }
 
 // ---------------------------------------------------------------- tcgen05 weight gradient
-// dW[tap][co][ci] = sum_v G[v][co] A[v + tap][ci] as implicit GEMMs on the tensor cores:
-// M = (tap, ci) rows, 8 taps x 16 input channels per M128 tile (4 tiles hold the 27 taps),
-// N = 16 output channels, K = voxels.  A block takes 64-voxel x segments of (z, y) rows in
-// turn.  For a segment, TMA brings the 3 x 3 neighbouring rows of A with the x halo (a box of
-// [3][3][66][8] per channel half, zeros outside the grid) and the segment of G ([64][8] per
-// half) into one of two staging buffers, two segments ahead.  The four warps then write the
-// K-major operands of the MMAs -- the im2col of the 27 shifted copies of A, and G transposed
-// -- with ldmatrix.trans / stmatrix: each 8 x 8 block of [voxel][channel] becomes the
-// [channel][voxel] core matrix of the no-swizzle K-major layout (8 rows of 16 bytes;
-// K-adjacent core matrices kWgLbo bytes apart, M-adjacent 128).  One thread issues 4 tiles x
-// 4 K-steps of M128 N16 K16 MMAs into four FP32 accumulators in tensor memory that persist
-// over all of the block's segments; two operand buffers alternate, so the tensor core works
-// on one segment while the next is written.  Every wait is bounded (a wait that runs out sets
-// the device flag that pk_conv3d_check reports, and the block waits, bounded, for what it
-// issued before it frees its tensor memory).  At the end each thread reads its accumulator
-// lane (one (tap, ci) row, 16 co) into the block's partial; a fixed-order reduction over
-// blocks follows (deterministic).
+// dW[tap][co][ci] = sum_v G[v][co] A[v + s][ci] (s the tap's shift) as one implicit GEMM per
+// 16 voxels on the tensor cores.  The shift is split between the operands: with
+// s = s_a + s_b, sum_v G[v] A[v + s] = sum_k A[k + s_a] G[k - s_b], so a product of
+//   M = 128 rows (s_a, ci): the 8 shifts s_a = (dz, dy, 0) other than (1, 1, 0), x 16 ci,
+//   N = 96 rows (s_b, co): the 6 shifts s_b = (0, 0, dx) and (1, 1, dx), x 16 co,
+// over K = voxels k holds every tap once: s_a + (0, 0, dx) for the 24 taps with (dz, dy) !=
+// (1, 1), and (0, 0, 0) + (1, 1, dx) for the other 3 (the remaining (s_a, s_b) pairs are not
+// taps and are not read).  One M128 N96 K16 MMA per 16 voxels covers all 27 taps.
+// A block takes 64-voxel x segments of (z, y) rows in turn.  For a segment, bulk copies bring
+// the 3 x 3 rows of A around it and the rows (z, y), (z-1, y-1) of G, 66 voxels each with the
+// x halo (one contiguous run of 32-byte voxels per row; the parts outside the grid are not
+// copied, and the operand writers read zeros for them), into one of five staging buffers,
+// four segments ahead.  Eight warps write the K-major operands -- the
+// shifted copies of A and of G, transposed -- with ldmatrix.trans / stmatrix: each 8 x 8
+// block of [voxel][channel] becomes the [channel][voxel] core matrix of the no-swizzle
+// K-major layout (8 rows of 16 bytes; K-adjacent core matrices kWgLboA / kWgLboB bytes apart,
+// M- or N-adjacent 128).  A loader warp issues the copies (one lane per row), and one thread
+// of another warp issues, per segment, 4 MMAs into one
+// FP32 accumulator of 96 columns in tensor memory that persists over all of the block's
+// segments; three operand buffers rotate, so the writers run up to two segments ahead of
+// the tensor core's completions (mbarriers: operands written by the 8 warps, operands read by
+// the MMAs).  Every wait is bounded (a wait that runs out sets the device
+// flag that pk_conv3d_check reports, and the block waits, bounded, for what it issued before
+// it frees its tensor memory).  At the end each thread reads its accumulator lane (one
+// (s_a, ci) row) into the block's partial; a fixed-order reduction over blocks follows.
 constexpr int kWgSeg = 64;                       // voxels (K) per segment
-constexpr int kWgTiles = 4;                      // M128 tiles: taps 0-7, 8-15, 16-23, 24-26
 constexpr int kWgKg = kWgSeg / 8;                // K core matrices per segment
-constexpr int kWgLbo = 16 * 128;                 // bytes between K-adjacent core matrices of A
-constexpr int kWgTile = kWgKg * kWgLbo;          // 16 KB per M128 tile
-constexpr int kWgA = kWgTiles * kWgTile;         // 64 KB: A operand of one segment
-constexpr int kWgB = kWgKg * 256;                // 2 KB: G^T (N = 16 rows) of one segment
-constexpr int kWgHx = kWgSeg + 2;                // staged x extent of A (halo of one)
-constexpr int kWgHalf = (9 * kWgHx * 16 + 127) & ~127;  // one channel half of the A box (9,600)
-constexpr int kWgStageA = 2 * kWgHalf;
-constexpr int kWgStage = kWgStageA + 2 * kWgSeg * 16;   // + G, two halves of [64][8]
-constexpr int kWgOp = kWgA + kWgB;              // one operand buffer: A, then G^T (66 KB)
-constexpr int kWgStages = 3;                     // staging buffers (TMA two segments ahead)
-constexpr int kWgSmem = 2 * kWgOp + kWgStages * kWgStage;
+constexpr int kWgSa = 8, kWgSb = 6;              // shifts on the A side and on the G side
+constexpr int kWgN = kWgSb * 16;                 // 96
+constexpr int kWgLboA = kWgSa * 2 * 128;         // bytes between K-adjacent core matrices of A (2 KB)
+constexpr int kWgLboB = kWgSb * 2 * 128;         // ... of G^T (1.5 KB)
+constexpr int kWgA = kWgKg * kWgLboA;            // 16 KB: A operand of one segment
+constexpr int kWgB = kWgKg * kWgLboB;            // 12 KB: G operand of one segment
+constexpr int kWgHx = kWgSeg + 2;                // staged x extent (halo of one)
+constexpr int kWgRow = kWgHx * 32;               // one staged row: 66 voxels x 16 channels BF16
+constexpr int kWgStageA = 9 * kWgRow;            // A rows (z + dz, y + dy), (dz + 1) 3 + (dy + 1)
+constexpr int kWgStage = (kWgStageA + 2 * kWgRow + 127) & ~127;  // + G rows (z-1, y-1), (z, y)
+constexpr int kWgOp = kWgA + kWgB;               // one operand buffer (28 KB)
+constexpr int kWgStages = 5;                     // staging buffers (copies four segments ahead)
+constexpr int kWgOps = 3;                        // operand buffers (the writers run 2 segments ahead)
+constexpr int kWgSmem = kWgOps * kWgOp + kWgStages * kWgStage;
 constexpr int kWgMaxBlocks = 256;
-constexpr uint32_t kWgCols = 64;                 // tensor memory: 4 accumulators x 16 columns
-constexpr uint32_t kWgStageBytes = 2 * 9 * kWgHx * 16 + 2 * kWgSeg * 16;  // TMA bytes per segment
+constexpr uint32_t kWgCols = 128;                // tensor memory: one accumulator of 96 columns
 constexpr int kWgThreads = 256;                  // 8 warps write the operands
+// instruction descriptor, kind::f16: D FP32, A and B BF16, both K-major, N = 96, M = 128
+constexpr uint32_t kWgIdesc = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(kWgN >> 3) << 17) |
+                              ((uint32_t)(128 >> 4) << 24);
+
+__device__ __forceinline__ void wg_mma(uint32_t tmem_d, uint64_t adesc, uint64_t bdesc, uint32_t accumulate) {
+  asm volatile(
+      "{\n\t.reg .pred p;\n\t"
+      "setp.ne.b32 p, %4, 0;\n\t"
+      "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}" ::"r"(tmem_d),
+      "l"(adesc), "l"(bdesc), "r"(kWgIdesc), "r"(accumulate)
+      : "memory");
+}
 
 __device__ __forceinline__ void ldsm4t(uint32_t (&r)[4], uint32_t addr) {
   asm volatile("ldmatrix.sync.aligned.m8n8.x4.trans.shared.b16 {%0,%1,%2,%3}, [%4];"
@@ -339,38 +360,39 @@ __device__ __forceinline__ void stsm4(uint32_t addr, const uint32_t (&r)[4]) {
                : "memory");
 }
 
-__global__ void __launch_bounds__(kWgThreads + 32) k_conv3d_wgrad_tc(const __grid_constant__ CUtensorMap amap,
-                                                                   const __grid_constant__ CUtensorMap gmap,
+__global__ void __launch_bounds__(kWgThreads + 64) k_conv3d_wgrad_tc(const __nv_bfloat16* __restrict__ A,
+                                                                   const __nv_bfloat16* __restrict__ G,
                                                                    float* partial, float* partial_db, int D,
                                                                    int H, int W) {
   extern __shared__ __align__(1024) unsigned char smem_wg[];
-  unsigned char* obuf = smem_wg;                                // 2 x kWgOp operand buffers
-  unsigned char* stage = smem_wg + 2 * kWgOp;                   // kWgStages staging buffers
-  __shared__ __align__(8) uint64_t full_bar[kWgStages];         // staging buffer loaded (TMA)
-  __shared__ __align__(8) uint64_t ready_bar[2];                // operands written (8 warps)
-  __shared__ __align__(8) uint64_t free_bar[2];                 // operands read (MMA commit)
+  unsigned char* obuf = smem_wg;                                // kWgOps operand buffers
+  unsigned char* stage = smem_wg + kWgOps * kWgOp;              // kWgStages staging buffers
+  __shared__ __align__(8) uint64_t full_bar[kWgStages];         // staging buffer loaded
+  __shared__ __align__(8) uint64_t empty_bar[kWgStages];        // staging buffer read (8 warps)
+  __shared__ __align__(8) uint64_t ready_bar[kWgOps];           // operands written (8 warps)
+  __shared__ __align__(8) uint64_t free_bar[kWgOps];            // operands read (MMA commit)
   __shared__ uint32_t tmem_slot;
   __shared__ int abort_flag, consumed;
+  __shared__ __align__(16) uint4 zero16;  // what the operand writers read outside the grid
   __shared__ float dbs[kWgThreads / kCh][kCh];
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const bool control = warp == kWgThreads / 32;  // warp 8, lane 0: copies and MMAs
   const int nseg = (W + kWgSeg - 1) / kWgSeg;
-  const int64_t nchunks = (int64_t)D * H * nseg;
-  const int mine = blockIdx.x < nchunks ? (int)((nchunks - 1 - blockIdx.x) / gridDim.x + 1) : 0;
-  // the rows of tile 3 past tap 26 are never written: zero them (their accumulator rows are
-  // not read, but the tensor core reads the operand)
-  for (int e = threadIdx.x; e < 2 * kWgOp / 16; e += blockDim.x)
-    reinterpret_cast<uint4*>(obuf)[e] = make_uint4(0, 0, 0, 0);
+  const int nchunks = D * H * nseg;  // (< 2^31: checked by the host)
+  const int mine = (int)blockIdx.x < nchunks ? (nchunks - 1 - (int)blockIdx.x) / (int)gridDim.x + 1 : 0;
   proxy_fence();
   if (threadIdx.x == 0) {
-    for (int k = 0; k < kWgStages; ++k) mbar_init(&full_bar[k], 1);
-    for (int k = 0; k < 2; ++k) {
+    for (int k = 0; k < kWgStages; ++k) {
+      mbar_init(&full_bar[k], 1);
+      mbar_init(&empty_bar[k], kWgThreads / 32);
+    }
+    for (int k = 0; k < kWgOps; ++k) {
       mbar_init(&ready_bar[k], kWgThreads / 32);
       mbar_init(&free_bar[k], 1);
     }
     mbar_fence_init();
     abort_flag = 0;
     consumed = 0;
+    zero16 = make_uint4(0, 0, 0, 0);
   }
   if (warp == 0) {
     asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_addr(&tmem_slot)),
@@ -384,85 +406,110 @@ __global__ void __launch_bounds__(kWgThreads + 32) k_conv3d_wgrad_tc(const __gri
   const uint32_t tmem = tmem_slot;
   const uint32_t o_base = smem_addr(obuf), s_base = smem_addr(stage);
   float db = 0.f;  // builders: output channel t % 16 over voxels (t / 16) + 16 k of every segment
-  if (control) {
+  if (warp == kWgThreads / 32) {
+    // MMA warp, lane 0: per segment, once its operands are written, 4 MMAs and a commit
     if (lane == 0) {
-      // the TMA copies of segment j into staging buffer j % kWgStages
-      auto load = [&](int j) {
-        const int64_t c = blockIdx.x + (int64_t)j * gridDim.x;
-        const int seg = (int)(c % nseg), zy = (int)(c / nseg);
-        const int z = zy / H, y = zy % H, x0 = seg * kWgSeg;
-        const int sb = j % kWgStages;
-        const uint32_t st = s_base + sb * kWgStage;
-        mbar_expect_tx(&full_bar[sb], kWgStageBytes);
-        for (int h = 0; h < 2; ++h) {
-          tc_tma_box(st + h * kWgHalf, &amap, 8 * h, x0 - 1, y - 1, z - 1, &full_bar[sb]);
-          tc_tma_box(st + kWgStageA + h * kWgSeg * 16, &gmap, 8 * h, x0, y, z, &full_bar[sb]);
-        }
-      };
-      int loaded = 0, issued = 0;
-      for (; loaded < min(kWgStages, mine); ++loaded) load(loaded);
+      int issued = 0;
       for (int j = 0; j < mine; ++j) {
-        const int b = j & 1;
-        if (!mbar_wait(&ready_bar[b], (j >> 1) & 1) || *(volatile int*)&abort_flag) {
+        const int b = j % kWgOps;
+        if (!mbar_wait(&ready_bar[b], (j / kWgOps) & 1) || *(volatile int*)&abort_flag) {
           abort_flag = 1;
           break;
         }
-        // staging buffer j % kWgStages has been read: refill it with segment j + kWgStages
-        if (loaded < mine) load(loaded++);
         tc_fence_after();
         const uint32_t ob = o_base + b * kWgOp;
 #pragma unroll
         for (int ks = 0; ks < kWgKg / 2; ++ks)
-#pragma unroll
-          for (int t = 0; t < kWgTiles; ++t)
-            tc_mma(tmem + t * 16, tc_desc(ob + t * kWgTile + 2 * ks * kWgLbo, kWgLbo, 128),
-                   tc_desc(ob + kWgA + 2 * ks * 256, 256, 128), (j > 0 || ks > 0) ? 1u : 0u);
+          wg_mma(tmem, tc_desc(ob + 2 * ks * kWgLboA, kWgLboA, 128), tc_desc(ob + kWgA + 2 * ks * kWgLboB, kWgLboB, 128),
+                 (j > 0 || ks > 0) ? 1u : 0u);
         tc_commit(&free_bar[b]);
         issued = j + 1;
       }
       // the last commit covers every MMA the block issued
-      if (issued > 0 && !mbar_wait(&free_bar[(issued - 1) & 1], ((issued - 1) >> 1) & 1)) abort_flag = 1;
-      if (abort_flag) {
-        // bounded waits for the copies the builders did not consume before the memory goes
-        for (int k = *(volatile int*)&consumed; k < loaded; ++k)
-          mbar_wait(&full_bar[k % kWgStages], (k / kWgStages) & 1);
+      if (issued > 0 && !mbar_wait(&free_bar[(issued - 1) % kWgOps], ((issued - 1) / kWgOps) & 1)) abort_flag = 1;
+    }
+  } else if (warp == kWgThreads / 32 + 1) {
+    // loader warp: the bulk copies of segment j into staging buffer j % kWgStages, once the
+    // writers are done with segment j - kWgStages there (its empty barrier: one phase per use
+    // of the buffer, so the wait cannot mistake a later phase for it); lane r < 11 copies row
+    // r (9 rows of A, then G at (z-1, y-1), (z, y)): the in-grid part [xa, xb) of an in-grid
+    // row, x0 - 1 at staged voxel 0
+    int loaded = 0;
+    for (int j = 0; j < mine; ++j) {
+      if (j >= kWgStages) {
+        const int jr = j - kWgStages;
+        bool ok = true;
+        if (lane == 0) ok = mbar_wait(&empty_bar[j % kWgStages], (jr / kWgStages) & 1) && !*(volatile int*)&abort_flag;
+        if (!__shfl_sync(0xffffffffu, ok, 0)) {
+          if (lane == 0) abort_flag = 1;
+          break;
+        }
       }
+      const int c = (int)blockIdx.x + j * (int)gridDim.x;
+      const int seg = c % nseg, zy = c / nseg;
+      const int z = zy / H, y = zy % H, x0 = seg * kWgSeg;
+      const int xa = max(0, x0 - 1), xb = min(W, x0 + kWgSeg + 1);
+      const uint32_t bytes = (uint32_t)(xb - xa) * 32;
+      const int sb = j % kWgStages;
+      const int row = lane;
+      const int zz = row < 9 ? z + row / 3 - 1 : z + row - 10, yy = row < 9 ? y + row % 3 - 1 : y + row - 10;
+      const bool in = row < 11 && zz >= 0 && zz < D && yy >= 0 && yy < H;
+      const uint32_t total = bytes * (uint32_t)__popc(__ballot_sync(0xffffffffu, in));
+      if (lane == 0) mbar_expect_tx(&full_bar[sb], total);
+      __syncwarp();
+      if (in)
+        bulk_load(stage + sb * kWgStage + (xa - x0 + 1) * 32 + row * kWgRow,
+                  (row < 9 ? A : G) + (((size_t)zz * H + yy) * W + xa) * kCh, bytes, &full_bar[sb]);
+      loaded = j + 1;
+    }
+    if (lane == 0 && *(volatile int*)&abort_flag) {
+      // bounded waits for the copies the writers did not consume before the memory goes
+      for (int k = *(volatile int*)&consumed; k < loaded; ++k)
+        mbar_wait(&full_bar[k % kWgStages], (k / kWgStages) & 1);
     }
   } else {
-    // builders: the operand-writing jobs of this thread, 14 blocks of 8 x 8 (two per step of
-    // 8 warps), their source offsets in a staging buffer and destinations in an operand
-    // buffer, the same for every segment: 27 taps x 2 channel halves x 8 K groups of A, then
-    // 2 x 8 of G; lanes 8i .. 8i+7 address the rows of block i of a four-block instruction
-    constexpr int kGroups = (27 * 16 + 16) / 4;  // 112 instructions per segment
+    // builders: the operand-writing jobs of this thread, 7 blocks of 8 x 8, their source
+    // offsets in a staging buffer and destinations in an operand buffer, the same for every
+    // segment: 8 shifts s_a x 2 channel halves x 8 K groups of A (128 blocks), then 6 shifts
+    // s_b x 2 x 8 of G (96); lanes 8i .. 8i+7 address the rows of block i of a four-block
+    // instruction
+    constexpr int kGroups = (kWgSa + kWgSb) * 2 * kWgKg / 4;  // 56 instructions per segment
     constexpr int kWarps = kWgThreads / 32;
-    constexpr int kJobs = kGroups / kWarps;      // 14 per warp
-    static_assert(kGroups % (2 * kWarps) == 0, "two instructions per warp per step");
-    uint32_t src_off[kJobs], dst_off[kJobs];
+    constexpr int kJobs = kGroups / kWarps;                     // 7 per warp
+    static_assert(kGroups % kWarps == 0, "whole instructions per warp");
+    // where each lane's row comes from: staged row 0 .. 10 and voxel x0 + xoff, read as zeros
+    // outside the grid (coded as row << 8 | (xoff + 1))
+    uint32_t src_off[kJobs], dst_off[kJobs], where[kJobs];
     {
       const int r = lane & 7, i = lane >> 3;
 #pragma unroll
       for (int k = 0; k < kJobs; ++k) {
         const int grp = warp + kWarps * k;
         const int q = 4 * grp + i;
-        if (q < 27 * 16) {
-          const int tap = q >> 4, h = (q >> 3) & 1, kg = q & 7;
-          const int dzdy = tap / 3, dx = tap % 3 - 1;
-          src_off[k] = h * kWgHalf + (dzdy * kWgHx + kg * 8 + r + dx + 1) * 16;
-          dst_off[k] = (tap >> 3) * kWgTile + kg * kWgLbo + (((tap & 7) << 1) + h) * 128 + r * 16;
+        if (q < kWgSa * 2 * kWgKg) {
+          // A[k + s_a][ci], s_a = combo sa of (dz, dy) without (1, 1): staged row sa
+          const int sa = q >> 4, h = (q >> 3) & 1, kg = q & 7;
+          src_off[k] = (sa * kWgHx + kg * 8 + r + 1) * 32 + h * 16;
+          dst_off[k] = kg * kWgLboA + (sa * 2 + h) * 128 + r * 16;
+          where[k] = ((uint32_t)sa << 8) | (uint32_t)(kg * 8 + r + 1);
         } else {
-          const int qb = q - 27 * 16, h = qb >> 3, kg = qb & 7;
-          src_off[k] = kWgStageA + h * kWgSeg * 16 + (kg * 8 + r) * 16;
-          dst_off[k] = kWgA + kg * 256 + h * 128 + r * 16;
+          // G[k - s_b][co]: s_b = (0, 0, dx) reads G row (z, y), (1, 1, dx) row (z-1, y-1)
+          const int qb = q - kWgSa * 2 * kWgKg, sb = qb >> 4, h = (qb >> 3) & 1, kg = qb & 7;
+          const int dx = sb % 3 - 1, grow = sb < 3 ? 10 : 9;
+          src_off[k] = (grow * kWgHx + kg * 8 + r - dx + 1) * 32 + h * 16;
+          dst_off[k] = kWgA + kg * kWgLboB + (sb * 2 + h) * 128 + r * 16;
+          where[k] = ((uint32_t)grow << 8) | (uint32_t)(kg * 8 + r - dx + 1);
         }
       }
     }
+    const uint32_t zero_addr = smem_addr(&zero16);
     const int c = threadIdx.x & (kCh - 1);
     for (int j = 0; j < mine; ++j) {
-      const int b = j & 1, sb = j % kWgStages;
-      // segment j's data, and operand buffer b free (read by the MMAs of segment j - 2)
+      const int b = j % kWgOps, sb = j % kWgStages;
+      // segment j's data, and operand buffer b free (read by the MMAs of segment j - kWgOps)
       if (lane == 0) {
         if (!mbar_wait(&full_bar[sb], (j / kWgStages) & 1) ||
-            (j >= 2 && !mbar_wait(&free_bar[b], ((j - 2) >> 1) & 1)))
+            (j >= kWgOps && !mbar_wait(&free_bar[b], ((j - kWgOps) / kWgOps) & 1)))
           abort_flag = 1;
         else if (warp == 0)
           consumed = j + 1;
@@ -470,25 +517,37 @@ __global__ void __launch_bounds__(kWgThreads + 32) k_conv3d_wgrad_tc(const __gri
       __syncwarp();
       if (*(volatile int*)&abort_flag) break;
       const uint32_t st = s_base + sb * kWgStage;
+      const int cc = (int)blockIdx.x + j * (int)gridDim.x;
+      const int zy = cc / nseg, z = zy / H, y = zy % H, x0 = (cc % nseg) * kWgSeg;
+      uint32_t rows_in = 0;  // staged rows inside the grid (bit = row, as the loader numbers them)
+#pragma unroll
+      for (int row = 0; row < 11; ++row) {
+        const int zz = row < 9 ? z + row / 3 - 1 : z + row - 10, yy = row < 9 ? y + row % 3 - 1 : y + row - 10;
+        if (zz >= 0 && zz < D && yy >= 0 && yy < H) rows_in |= 1u << row;
+      }
       {
-        const __nv_bfloat16* g16 = reinterpret_cast<const __nv_bfloat16*>(stage + sb * kWgStage + kWgStageA +
-                                                                            (c >> 3) * kWgSeg * 16);
+        // G at (z, y), x0 + xx: staged row 10, voxel xx + 1 (inside the grid only)
+        const __nv_bfloat16* g16 = reinterpret_cast<const __nv_bfloat16*>(stage + sb * kWgStage +
+                                                                            (10 * kWgHx + 1) * 32);
 #pragma unroll
         for (int xx = threadIdx.x / kCh; xx < kWgSeg; xx += kWgThreads / kCh)
-          db += __bfloat162float(g16[xx * 8 + (c & 7)]);
+          if (x0 + xx < W) db += __bfloat162float(g16[xx * kCh + c]);
       }
       const uint32_t ob = o_base + b * kWgOp;
+      uint32_t f[kJobs][4];  // all loads in flight before the stores
 #pragma unroll
-      for (int k = 0; k < kJobs; k += 2) {  // two instructions' loads in flight before their stores
-        uint32_t f0[4], f1[4];
-        ldsm4t(f0, st + src_off[k]);
-        ldsm4t(f1, st + src_off[k + 1]);
-        stsm4(ob + dst_off[k], f0);
-        stsm4(ob + dst_off[k + 1], f1);
+      for (int k = 0; k < kJobs; ++k) {
+        const bool in = ((rows_in >> (where[k] >> 8)) & 1u) && (unsigned)(x0 + (int)(where[k] & 255) - 1) < (unsigned)W;
+        ldsm4t(f[k], in ? st + src_off[k] : zero_addr);
       }
+#pragma unroll
+      for (int k = 0; k < kJobs; ++k) stsm4(ob + dst_off[k], f[k]);
       proxy_fence();  // the operands are read by the tensor core (async proxy)
       __syncwarp();
-      if (lane == 0) mbar_arrive(&ready_bar[b]);
+      if (lane == 0) {
+        mbar_arrive(&ready_bar[b]);
+        mbar_arrive(&empty_bar[sb]);
+      }
     }
     dbs[threadIdx.x / kCh][c] = db;
   }
@@ -496,15 +555,20 @@ __global__ void __launch_bounds__(kWgThreads + 32) k_conv3d_wgrad_tc(const __gri
   __syncthreads();
   tc_fence_after();
   float* P = partial + (size_t)blockIdx.x * 27 * kCh * kCh;
-  if (!abort_flag && !control) {
-    // warp w reads tensor-memory lanes 32 (w % 4) .. + 31 of tiles 2 (w / 4) and 2 (w / 4) + 1
-    const int q4 = warp & 3, m = 32 * q4 + lane;  // accumulator row: tap 8t + m / 16, input channel m % 16
+  if (!abort_flag && warp < kWgThreads / 32) {
+    // warp w reads tensor-memory lanes 32 (w % 4) .. + 31, column blocks s_b = 3 (w / 4) ..
+    // + 2; row m = (s_a, ci): s_a = m / 16 is (dz, dy) = combo s_a of the 3 x 3 without (1, 1)
+    const int q4 = warp & 3, m = 32 * q4 + lane;
+    const int sa = m >> 4, ci = m & 15, dzdy = sa;  // combos 0 .. 7 are (dz + 1) 3 + (dy + 1)
 #pragma unroll 1
-    for (int t = 2 * (warp >> 2); t < 2 * (warp >> 2) + 2; ++t) {
+    for (int sb = 3 * (warp >> 2); sb < 3 * (warp >> 2) + 3; ++sb) {
       float v[16];
-      tc_ld16(tmem + ((uint32_t)(32 * q4) << 16) + t * 16, v);
-      const int tap = 8 * t + (m >> 4), ci = m & 15;
-      if (tap < 27) {
+      tc_ld16(tmem + ((uint32_t)(32 * q4) << 16) + sb * 16, v);
+      const int dx = sb % 3 - 1;
+      int tap = -1;
+      if (sb < 3) tap = 3 * dzdy + (dx + 1);             // (dz, dy, dx)
+      else if (dzdy == 4) tap = 3 * 8 + (dx + 1);        // (0, 0, 0) + (1, 1, dx)
+      if (tap >= 0) {
 #pragma unroll
         for (int co = 0; co < 16; ++co) P[(tap * kCh + co) * kCh + ci] = mine > 0 ? v[co] : 0.f;
       }
@@ -538,16 +602,13 @@ __global__ void __launch_bounds__(256) k_conv3d_wgrad_reduce(const float* partia
   if (e < nw + kCh) {
     const float* src = e < nw ? partial + e : partial_db + (e - nw);
     const size_t stride = e < nw ? (size_t)nw : (size_t)kCh;
-    int b = warp;
-    for (; b + 8 * 3 < nblk; b += 8 * 4) {
-      const float v0 = src[b * stride], v1 = src[(b + 8) * stride], v2 = src[(b + 16) * stride],
-                  v3 = src[(b + 24) * stride];
-      s += v0;
-      s += v1;
-      s += v2;
-      s += v3;
-    }
-    for (; b < nblk; b += 8) s += src[b * stride];
+    constexpr int kPer = (kWgMaxBlocks + 7) / 8;  // every load of the thread in flight at once
+    float v[kPer];
+#pragma unroll
+    for (int q = 0; q < kPer; ++q) v[q] = warp + 8 * q < nblk ? src[(size_t)(warp + 8 * q) * stride] : 0.f;
+#pragma unroll
+    for (int q = 0; q < kPer; ++q)
+      if (warp + 8 * q < nblk) s += v[q];
   }
   part[warp][lane] = s;
   __syncthreads();
@@ -863,7 +924,8 @@ int64_t pk_conv3d_wgrad_scratch_floats(int32_t D, int32_t H, int32_t W) {
 
 pk_status pk_conv3d_wgrad(const void* A, const void* G, float* scratch, float* dW, float* db,
                           int32_t D, int32_t H, int32_t W, void* stream) {
-  if (!A || !G || !scratch || !dW || !db || D <= 0 || H <= 0 || W <= 0) {
+  if (!A || !G || !scratch || !dW || !db || D <= 0 || H <= 0 || W <= 0 ||
+      (int64_t)D * H * ((W + kWgSeg - 1) / kWgSeg) >= (int64_t(1) << 31)) {
     set_error("pk_conv3d_wgrad: bad arguments");
     return PK_ERR_ARG;
   }
@@ -881,13 +943,13 @@ pk_status pk_conv3d_wgrad(const void* A, const void* G, float* scratch, float* d
   float* partial = scratch;
   float* partial_db = scratch + (size_t)nmax * 27 * kCh * kCh;
   cudaStream_t s = (cudaStream_t)stream;
-  // A: boxes of [3 z][3 y][66 x][8 channels] (a segment's neighbour rows with the x halo);
-  // G: [64 x][8 channels]
-  CUtensorMap amap, gmap;
-  if ((e = input_map(&amap, static_cast<const __nv_bfloat16*>(A), D, H, W, kWgHx, 3, 3)) ||
-      (e = input_map(&gmap, static_cast<const __nv_bfloat16*>(G), D, H, W, kWgSeg, 1, 1)))
-    return e;
-  k_conv3d_wgrad_tc<<<nblk, kWgThreads + 32, kWgSmem, s>>>(amap, gmap, partial, partial_db, D, H, W);
+  if ((reinterpret_cast<uintptr_t>(A) | reinterpret_cast<uintptr_t>(G)) & 15) {
+    set_error("pk_conv3d_wgrad: activations and gradients must be 16-byte aligned");
+    return PK_ERR_ARG;
+  }
+  k_conv3d_wgrad_tc<<<nblk, kWgThreads + 64, kWgSmem, s>>>(static_cast<const __nv_bfloat16*>(A),
+                                                         static_cast<const __nv_bfloat16*>(G), partial,
+                                                         partial_db, D, H, W);
   k_conv3d_wgrad_reduce<<<(27 * kCh * kCh + kCh + 31) / 32, 256, 0, s>>>(partial, partial_db, nblk, dW, db);
   PK_CUDA(cudaGetLastError());
   return PK_OK;
