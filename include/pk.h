@@ -69,18 +69,23 @@ enum {
                         no host round-trip until the solve ends */
   PK_LOOP_HOST = 1,  /* plain launches; the host reads the device "done" flag every
                         `check_every` iterations (kernels after convergence return at once) */
-  PK_LOOP_PERSISTENT = 2, /* pipelined FP64 CG and pipelined BiCGStab: the whole iteration
+  PK_LOOP_PERSISTENT = 2, /* pipelined FP64 CG, BiCGStab and GMRES(m): the whole iteration
                         loop in one launch on one thread-block cluster (16 CTAs where
-                        available, else 8) with the vectors in distributed shared memory (CG:
-                        p, x, r, Ap; BiCGStab: p, s, r, Ap, As, r0*), hardware cluster
-                        barriers, every CTA summing the block partials itself in a fixed
-                        order; for n <= PK_PERSISTENT_MAX_N.  Larger n, GMRES, other
-                        variants or precisions return PK_ERR_ARG */
+                        available, else 8) with the gathered vectors in distributed shared
+                        memory (CG: p, x, r, Ap; BiCGStab: p, s, r, Ap, As, r0*; GMRES: the
+                        current basis vector, with the basis itself in global memory and R,
+                        xi, eta in every CTA), hardware cluster barriers, every CTA summing
+                        the block partials itself in a fixed order; for n <=
+                        PK_PERSISTENT_MAX_N.  Larger n, other variants, precisions, GMRES
+                        with PK_FLAG_CGS2 or PK_FLAG_GM_SHIFT return PK_ERR_ARG */
   PK_LOOP_AUTO = 3,  /* PK_LOOP_PERSISTENT for pipelined FP64 CG with n <= PK_PERSISTENT_AUTO_N
-                        and nnz <= PK_PERSISTENT_AUTO_NNZ, and for pipelined BiCGStab with
-                        n <= PK_PERSISTENT_BICGSTAB_AUTO_N and nnz <=
-                        PK_PERSISTENT_BICGSTAB_AUTO_NNZ (and no PK_FLAG_TIMING) when the device
-                        can run it, PK_LOOP_GRAPH otherwise */
+                        and nnz <= PK_PERSISTENT_AUTO_NNZ, pipelined BiCGStab with n <=
+                        PK_PERSISTENT_BICGSTAB_AUTO_N and nnz <= PK_PERSISTENT_BICGSTAB_AUTO_NNZ,
+                        and pipelined GMRES (one Gram-Schmidt pass) with n <=
+                        PK_PERSISTENT_GMRES_AUTO_N and nnz <= PK_PERSISTENT_GMRES_AUTO_NNZ (and
+                        no PK_FLAG_TIMING; for BiCGStab and GMRES also no rows of very
+                        different lengths, stats.tiles_long == 0) when the device can run it,
+                        PK_LOOP_GRAPH otherwise */
   PK_LOOP_RESIDENT = 4 /* pipelined FP64 CG only: the whole iteration loop in one cooperative
                         launch of one block per SM.  Each iteration's update (x, r, p) and fused
                         SpMV run back to back in the launch; the SpMV of a block waits only for
@@ -103,6 +108,9 @@ enum {
  * at 16^3, 29 against 35 at 32^3 (223k nonzeros), 48 against 36 at 40^3 (438k) */
 #define PK_PERSISTENT_BICGSTAB_AUTO_N 32768
 #define PK_PERSISTENT_BICGSTAB_AUTO_NNZ 262144
+/* pipelined GMRES(m) (three cluster barriers per step, the basis in global memory) */
+#define PK_PERSISTENT_GMRES_AUTO_N 32768
+#define PK_PERSISTENT_GMRES_AUTO_NNZ 262144
 
 /* pk_opts.flags */
 #define PK_FLAG_TIMING 1u    /* time every kernel launch with CUDA events (host loop) and

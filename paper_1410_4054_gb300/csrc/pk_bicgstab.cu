@@ -457,9 +457,11 @@ pk_status bicgstab_solve(pk_csr* A, const double* b, double* x, const pk_opts* o
     }
     persistent = true;
   } else if (o->loop == PK_LOOP_AUTO) {
+    // (rows of very different lengths stay on the tile engine: one thread per row leaves the
+    // cluster waiting for the longest)
     persistent = o->variant == PK_VARIANT_PIPELINED && A->n <= PK_PERSISTENT_BICGSTAB_AUTO_N &&
-                 A->nnz <= PK_PERSISTENT_BICGSTAB_AUTO_NNZ && !(o->flags & PK_FLAG_TIMING) &&
-                 bicgstab_persistent_usable(A);
+                 A->nnz <= PK_PERSISTENT_BICGSTAB_AUTO_NNZ && A->stats.tiles_long == 0 &&
+                 !(o->flags & PK_FLAG_TIMING) && bicgstab_persistent_usable(A);
   }
   cudaEvent_t e0, e1;
   PK_CUDA(cudaEventCreate(&e0));

@@ -756,11 +756,16 @@ static pk_status gm_setup() {
   return PK_OK;
 }
 
+// pk_gmres_cluster.cu: the whole restarted pipelined loop on one thread-block cluster
+bool gmres_persistent_usable(const pk_csr* A, int m);
+pk_status launch_gmres_persistent(pk_csr* A, const double* b, double* x, int m, double* V, int64_t ld,
+                                  double* Rout, double* xiout, cudaStream_t s);
+
 pk_status gmres_solve(pk_csr* A, const double* b, double* x, const pk_opts* o, pk_info* info,
                       cudaStream_t s) {
   pk_status e = check_opts(A, b, x, o, info);
   if (e) return e;
-  if (o->loop == PK_LOOP_PERSISTENT || o->loop == PK_LOOP_RESIDENT) { set_error("PK_LOOP_PERSISTENT / PK_LOOP_RESIDENT run pipelined CG only"); return PK_ERR_ARG; }
+  if (o->loop == PK_LOOP_RESIDENT) { set_error("PK_LOOP_RESIDENT runs pipelined CG only"); return PK_ERR_ARG; }
   *info = pk_info{};
   info->rel_res_true = -1.0;
   if (A->n == 0) return PK_OK;
@@ -779,7 +784,26 @@ pk_status gmres_solve(pk_csr* A, const double* b, double* x, const pk_opts* o, p
     set_error("PK_FLAG_GM_SHIFT is a form of pipelined GMRES with one Gram-Schmidt pass (not with PK_FLAG_CGS2)");
     return PK_ERR_ARG;
   }
-  if (!A->tma_ok) { set_error("GMRES needs the tile engine"); return PK_ERR_ARG; }
+  // the whole loop on one thread-block cluster (small systems): asked for, or chosen by AUTO
+  bool persistent = false;
+  const bool plain = o->variant == PK_VARIANT_PIPELINED && !cgs2 && !shift;
+  if (o->loop == PK_LOOP_PERSISTENT) {
+    if (!plain) {
+      set_error("PK_LOOP_PERSISTENT runs pipelined GMRES with one Gram-Schmidt pass (no PK_FLAG_CGS2, PK_FLAG_GM_SHIFT)");
+      return PK_ERR_ARG;
+    }
+    if (!gmres_persistent_usable(A, m)) {
+      set_error("PK_LOOP_PERSISTENT: the persistent GMRES loop needs n <= 16 x 4096 rows (one thread-block cluster) and cluster launch");
+      return PK_ERR_ARG;
+    }
+    persistent = true;
+  } else if (o->loop == PK_LOOP_AUTO) {
+    // (rows of very different lengths stay on the tile engine: one thread per row leaves the
+    // cluster waiting for the longest)
+    persistent = plain && A->n <= PK_PERSISTENT_GMRES_AUTO_N && A->nnz <= PK_PERSISTENT_GMRES_AUTO_NNZ &&
+                 A->stats.tiles_long == 0 && !(o->flags & PK_FLAG_TIMING) && gmres_persistent_usable(A, m);
+  }
+  if (!A->tma_ok && !persistent) { set_error("GMRES needs the tile engine"); return PK_ERR_ARG; }
   if ((e = gm_setup())) return e;
   const int n = A->n;
   const int ld = ((n + 31) & ~31) + 32;
@@ -802,6 +826,31 @@ pk_status gmres_solve(pk_csr* A, const double* b, double* x, const pk_opts* o, p
   // right Jacobi preconditioning: iterate on A M^-1 with y = M x (values swapped until leave)
   JacobiRight jac;
   if (o->precond == PK_PRECOND_JACOBI && (e = jacobi_right_enter(A, v.x_dev, s, &jac))) return e;
+  if (persistent) {
+    Timer T;
+    T.A = A;
+    T.on = (o->flags & PK_FLAG_TIMING) != 0;
+    T.s = s;
+    if ((e = T.begin(PK_SLOT_OTHER))) return e;
+    if ((e = launch_gmres_persistent(A, v.b_dev, v.x_dev, m, A->basis, ld, A->small, A->small + kXiOff, s))) return e;
+    if ((e = T.end())) return e;
+    launch_zero_x(A, v.x_dev, s);
+    int launches = 3;  // state, the loop, the b = 0 case
+    if ((e = T.flush())) return e;
+    if (jac.A) {
+      if ((e = jacobi_right_leave(&jac, v.x_dev, s))) return e;
+      launches += 2;
+    }
+    if ((e = finish_info(A, o, info, s, v, e0, e1, launches))) return e;
+    info->cycles = A->st_host->gm_cycle;
+    for (int k = 0; k < PK_MAX_KERNEL_SLOTS; ++k) {
+      info->kernel_count[k] = T.count[k];
+      info->kernel_ms[k] = T.count[k] ? T.ms[k] / T.count[k] : 0.0;
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    return (pk_status)info->status;
+  }
   const bool classical = o->variant == PK_VARIANT_CLASSICAL;
   double* rc = nullptr;
   if (classical && (e = work_vec(A, 6, &rc))) return e;

@@ -27,6 +27,8 @@ PERSISTENT_AUTO_N = 65536  # PK_PERSISTENT_AUTO_N
 PERSISTENT_AUTO_NNZ = 393216  # PK_PERSISTENT_AUTO_NNZ
 PERSISTENT_BICGSTAB_AUTO_N = 32768  # PK_PERSISTENT_BICGSTAB_AUTO_N
 PERSISTENT_BICGSTAB_AUTO_NNZ = 262144  # PK_PERSISTENT_BICGSTAB_AUTO_NNZ
+PERSISTENT_GMRES_AUTO_N = 32768  # PK_PERSISTENT_GMRES_AUTO_N
+PERSISTENT_GMRES_AUTO_NNZ = 262144  # PK_PERSISTENT_GMRES_AUTO_NNZ
 FLAG_TIMING = 1
 FLAG_TRUE_RES = 2
 FLAG_NO_TMA = 4

@@ -20,6 +20,7 @@ CONSTANTS = {
     "PERSISTENT_AUTO_N": "PK_PERSISTENT_AUTO_N", "PERSISTENT_AUTO_NNZ": "PK_PERSISTENT_AUTO_NNZ",
     "PERSISTENT_BICGSTAB_AUTO_N": "PK_PERSISTENT_BICGSTAB_AUTO_N",
     "PERSISTENT_BICGSTAB_AUTO_NNZ": "PK_PERSISTENT_BICGSTAB_AUTO_NNZ",
+    "PERSISTENT_GMRES_AUTO_N": "PK_PERSISTENT_GMRES_AUTO_N", "PERSISTENT_GMRES_AUTO_NNZ": "PK_PERSISTENT_GMRES_AUTO_NNZ",
     "MAX_SLOTS": "PK_MAX_KERNEL_SLOTS",
 }
 TABLES = {

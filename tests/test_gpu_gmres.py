@@ -160,17 +160,19 @@ SHIFT3_MATRICES = {
     "dense_rows_1e4": lambda: W.spd_dense_rows(),
 }
 
-PARITY_CASES = ([(n, v) for n in sorted(MATRICES) + [f"jacobi:{k}" for k in sorted(JACOBI_MATRICES)]
-                 + [f"cgs2:{k}" for k in sorted(CGS2_MATRICES)] for v in ("classical", "pipelined")]
-                + [(f"shift3:{k}", "pipelined") for k in sorted(SHIFT3_MATRICES)]
-                + [("shift3:jacobi:convdiff_16_scaled", "pipelined")])
+PARITY_CASES = ([(n, v, lp) for n in sorted(MATRICES) + [f"jacobi:{k}" for k in sorted(JACOBI_MATRICES)]
+                 for v, lp in (("classical", "graph"), ("pipelined", "graph"), ("pipelined", "persistent"))]
+                + [(f"cgs2:{k}", v, "graph") for k in sorted(CGS2_MATRICES) for v in ("classical", "pipelined")]
+                + [(f"shift3:{k}", "pipelined", "graph") for k in sorted(SHIFT3_MATRICES)]
+                + [("shift3:jacobi:convdiff_16_scaled", "pipelined", "graph")])
 
 
-@pytest.mark.parametrize("name,variant", PARITY_CASES)
-def test_gmres_parity(name, variant):
+@pytest.mark.parametrize("name,variant,loop", PARITY_CASES)
+def test_gmres_parity(name, variant, loop):
     """'jacobi:' cases: right preconditioning with M = diag(A) on both sides; 'cgs2:' cases:
     Gram-Schmidt applied twice per step on both sides; 'shift3:' cases: the shift-invariant
-    three-kernel form on both sides."""
+    three-kernel form on both sides.  loop 'graph': the kernels of a step launched from a CUDA
+    graph; 'persistent': the whole restarted loop on one thread-block cluster."""
     shift3 = name.startswith("shift3:")
     if shift3:
         name = name[7:]
@@ -194,20 +196,22 @@ def test_gmres_parity(name, variant):
         name = "shift3:" + name
     A = pk.CSRMatrix.from_workload(a)
     info, x, tr = solve(a, b, A=A, tol=1e-8, maxit=20_000, restart=m, variant=variant,
-                        flags=pk.FLAG_TRUE_RES | fl, trace_cap=max(256, ref["iters"] + 8), precond=precond)
+                        flags=pk.FLAG_TRUE_RES | fl, trace_cap=max(256, ref["iters"] + 8), precond=precond, loop=loop)
     assert info["status"] == pk.PK_OK, info
     assert info["rel_res_true"] <= 1.5e-8
-    case = f"{name} {variant}"
+    if loop == "persistent":
+        assert info["launches"] <= 4 + (2 if precond == "jacobi" else 0), info["launches"]
+    case = f"{name} {variant} {loop}"
     first_cycle_check(tr, ref, sR, sX, ref["iters"], case)
     k_orc, k_gpu = first_cycle_lengths(tr, ref, ref["iters"])
     full_R_check(A, a, b, ref, sR, sX, min(k_orc, k_gpu, len(sR)), case, m=m, variant=variant,
-                 precond=precond, flags=fl)
+                 precond=precond, flags=fl, loop=loop)
     if k_orc == k_gpu or ref["iters"] <= min(k_orc, k_gpu):
         d_it = abs(info["iters"] - ref["iters"])
         record("gmres_parity", case, "iterations", d_it, 2, max(2, 2 * it_spread), oracle_spread=it_spread)
         assert d_it <= max(2, 2 * it_spread)
         info2, x2, _ = solve(a, b, tol=0.0, maxit=ref["iters"], restart=m, variant=variant, precond=precond,
-                             flags=fl)
+                             flags=fl, loop=loop)
         assert info2["iters"] == ref["iters"] and info2["cycles"] == fixed["cycles"]
         d_x = rel(x2, fixed["x"])
         record("gmres_parity", case, "x at the oracle's count", d_x, 1e-9, max(1e-9, 10 * x_spread),
@@ -223,7 +227,8 @@ def test_gmres_parity(name, variant):
         k = min(k_orc, k_gpu)
         _, fixed_k, _, _, _, xs_k = oracle_sensitivity(a, b, variant, m, 0.0, k, precond=precond, cgs2=cgs2,
                                                        shift3=shift3)
-        info2, x2, _ = solve(a, b, tol=0.0, maxit=k, restart=m, variant=variant, precond=precond, flags=fl)
+        info2, x2, _ = solve(a, b, tol=0.0, maxit=k, restart=m, variant=variant, precond=precond, flags=fl,
+                             loop=loop)
         assert info2["iters"] == k and info2["cycles"] == fixed_k["cycles"]
         assert rel(x2, fixed_k["x"]) <= max(1e-9, 10 * xs_k)
 
@@ -248,7 +253,7 @@ def test_gmres_jacobi_unit_diagonal_and_clean_handle():
     assert ij["status"] == pk.PK_OK and ij["rel_res_true"] <= 1.5e-8 and ij["iters"] < i1["iters"]
 
 
-@pytest.mark.parametrize("loop", ["graph", "host"])
+@pytest.mark.parametrize("loop", ["graph", "host", "persistent"])
 @pytest.mark.parametrize("m", [1, 5, 30, 64])
 def test_gmres_restart_lengths_and_loops(m, loop):
     a = W.convdiff_3d(12)
@@ -271,8 +276,8 @@ def test_gmres_launch_counts():
         for fl, tag in ((0, ""), (pk.FLAG_CGS2, "+cgs2"), (pk.FLAG_GM_SHIFT, "+shift")):
             if variant == "classical" and fl == pk.FLAG_GM_SHIFT:
                 continue
-            i10, _, _ = solve(a, b, tol=0.0, maxit=10, restart=30, variant=variant, flags=fl)
-            i20, _, _ = solve(a, b, tol=0.0, maxit=20, restart=30, variant=variant, flags=fl)
+            i10, _, _ = solve(a, b, tol=0.0, maxit=10, restart=30, variant=variant, flags=fl, loop="graph")
+            i20, _, _ = solve(a, b, tol=0.0, maxit=20, restart=30, variant=variant, flags=fl, loop="graph")
             per[variant + tag] = (i20["launches"] - i10["launches"]) / 10
     assert per == {"pipelined": 4, "classical": 7, "pipelined+cgs2": 6, "classical+cgs2": 9, "pipelined+shift": 3}
 
@@ -368,3 +373,28 @@ def test_gmres_large_convdiff():
     assert rel(xk, ref["x"]) <= 1e-9
     info, _, _ = solve(a, b, A=A, tol=1e-8, maxit=20_000, restart=30, flags=pk.FLAG_TRUE_RES)
     assert info["status"] == pk.PK_OK and info["rel_res_true"] <= 1.5e-8
+
+
+def test_gmres_persistent_selection_and_limits():
+    """PK_LOOP_AUTO runs small pipelined GMRES on one cluster with the iterates of
+    PK_LOOP_PERSISTENT; the persistent loop takes one Gram-Schmidt pass of the pipelined form
+    only, n up to 16 x 4096 rows; the graph runs above PK_PERSISTENT_GMRES_AUTO_N."""
+    a = W.convdiff_3d(20)
+    _, b, _ = W.manufactured(a, seed=5)
+    A = pk.CSRMatrix.from_workload(a)
+    ia, xa, ta = solve(a, b, A=A, loop="auto", restart=30)
+    ip, xp, tp = solve(a, b, A=A, loop="persistent", restart=30)
+    assert ia["launches"] == ip["launches"] <= 4 and ia["iters"] == ip["iters"] and np.array_equal(xa, xp)
+    assert np.array_equal(ta, tp, equal_nan=True)
+    for kw in (dict(variant="classical"), dict(flags=pk.FLAG_CGS2), dict(flags=pk.FLAG_GM_SHIFT)):
+        with pytest.raises(RuntimeError, match="PK_LOOP_PERSISTENT"):
+            solve(a, b, A=A, loop="persistent", **kw)
+    big = W.convdiff_3d(41)  # 68,921 rows
+    _, bb, _ = W.manufactured(big, seed=1)
+    with pytest.raises(RuntimeError, match="PK_LOOP_PERSISTENT"):
+        solve(big, bb, loop="persistent")
+    mid = W.convdiff_3d(36)  # 46,656 rows: fits one cluster, above the automatic threshold
+    _, bm, _ = W.manufactured(mid, seed=1)
+    ig, _, _ = solve(mid, bm, loop="auto", tol=0.0, maxit=3)
+    ip, _, _ = solve(mid, bm, loop="persistent", tol=0.0, maxit=3)
+    assert ig["launches"] > 4 and ip["launches"] <= 4
