@@ -891,8 +891,8 @@ def fe_sweep(pk, torch, dev):
     square, 225 ... 261,121 unknowns (~7 per row), and P1 elasticity on jittered Kuhn
     tetrahedra, 540 ... 324,864 unknowns (3 x 3 blocks, ~43 per row).  CG, BiCGStab and
     GMRES(30), pipelined and classical, a fixed number of iterations (tol 0) through the graph
-    loop; CG and BiCGStab also through PK_LOOP_AUTO (the cluster-resident loop for small
-    systems), GMRES also in the three-kernel form.  Best of two after a warm-up, microseconds
+    loop; CG, BiCGStab and GMRES also through PK_LOOP_AUTO (the cluster-resident loop for
+    small systems), GMRES also in the three-kernel form.  Best of two after a warm-up, microseconds
     per iteration (solve time / iterations)."""
     mats = [("fe2d", lv, lambda lv=lv: W.fe_poisson_2d(lv)) for lv in range(4, 10)]
     mats += [("fe3d", k, lambda k=k: W.fe_elasticity_3d(k)) for k in (5, 11, 23, 47)]
@@ -902,6 +902,7 @@ def fe_sweep(pk, torch, dev):
              ("bicgstab", pk.bicgstab_solve, "classical", "graph", 150, {}),
              ("bicgstab", pk.bicgstab_solve, "pipelined", "auto", 150, {}),
              ("gmres", pk.gmres_solve, "pipelined", "graph", 120, {"restart": 30, "flags": pk.FLAG_GM_SHIFT}),
+             ("gmres", pk.gmres_solve, "pipelined", "auto", 120, {"restart": 30}),
              ("gmres", pk.gmres_solve, "pipelined", "graph", 120, {"restart": 30}),
              ("gmres", pk.gmres_solve, "classical", "graph", 120, {"restart": 30})]
     rows = []
