@@ -144,12 +144,13 @@ def test_cg_persistent_too_large_falls_back_under_auto():
 
 
 def test_cg_persistent_rejects_other_forms():
-    """The persistent loop runs pipelined CG and pipelined BiCGStab (tested with BiCGStab)."""
+    """The persistent loop runs pipelined CG, BiCGStab and GMRES with one Gram-Schmidt pass
+    (tested with those solvers)."""
     a = W.laplace_2d(16)
     _, b, _ = W.manufactured(a)
     A = pk.CSRMatrix.from_workload(a)
     for call, kw in ((pk.cg_solve, dict(variant="classical")), (pk.cg_solve, dict(precision="mixed")),
-                     (pk.bicgstab_solve, dict(variant="classical")), (pk.gmres_solve, {})):
+                     (pk.bicgstab_solve, dict(variant="classical")), (pk.gmres_solve, dict(flags=pk.FLAG_CGS2))):
         with pytest.raises(RuntimeError, match="PERSISTENT"):
             call(A, dev(b), dev(np.zeros(a.n)), loop="persistent", **kw)
 
