@@ -686,6 +686,7 @@ def bench_forms(pk, torch, dev, args, emit=None):
     lw = {k: v for k, v in res.items() if not isinstance(v, list)}
     lw["train_ms_per_sample"] = 1e3 * res["train_s"] / (res["epochs"] * res["train_samples"])
     lw["iteration_gain_vs_plain_warm_start"] = res["baseline_mean_iters"] - res["learned_mean_iters"]
+    lw["relaxed_iteration_gain_vs_extrapolation"] = res["extrap_mean_iters"] - res["learned_relaxed_mean_iters"]
     lw["conv"] = conv_throughput(pk, torch, dev, (64, 64, 64))
     bf16_peak = bf16_peak_tflops()
     lw["conv"]["roofline"] = {"bound": "tensor", "peak": bf16_peak, "unit": "TFLOP/s",

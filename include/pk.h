@@ -462,6 +462,17 @@ pk_status pk_warmstart_apply(int64_t n, const float* out, const double* xm1, con
 pk_status pk_warmstart_apply_energy(pk_csr* A, const float* out, const double* xm1, const double* xm2,
                                     const double* b, const double* scales, double* xhat, double* gamma,
                                     double* scratch, void* stream);
+/* One damped Jacobi sweep on A x = b from the starting guess x:
+ * xout = x + omega (b - A x) / d, d = diag(A) (1 where a row has no nonzero diagonal entry),
+ * each row's products summed left to right.  The learned warm start applies it to the network's
+ * guess: the network's error is rough (rounding of its BF16 operands and approximation error
+ * spread over every frequency), rough error lies at the large eigenvalues of D^-1 A, where a
+ * sweep with omega near 0.8 damps it, and CG removes smooth error fastest.  A, b, x, xout on
+ * the device (n doubles each); omega in (0, 2); xout must not overlap x, b or the matrix
+ * (xout == x returns PK_ERR_ARG).  One pass over A; stream-ordered, no synchronisation.
+ * (An extension; the paper has no learned part.) */
+pk_status pk_warmstart_relax(pk_csr* A, const double* b, const double* x, double omega, double* xout,
+                             void* stream);
 /* Adam (Kingma & Ba) on FP32 parameters, step >= 1; p_bf16 (nullable) receives a BF16 copy. */
 pk_status pk_adam_step(int64_t count, float* p, const float* grad, float* m, float* v, float lr,
                        float beta1, float beta2, float eps, int32_t step, void* p_bf16,

@@ -150,6 +150,27 @@ def warmstart_energy_step(row_ptr, col, val, xm1, xm2, b, out, s0):
     return e + gamma * d, gamma
 
 
+def warmstart_relax(row_ptr, col, val, b, x, omega):
+    """One damped Jacobi sweep on A x = b from the guess x: for every row i,
+    x'_i = x_i + omega (b_i - sum_j a_ij x_j) / d_i with d_i = a_ii (1 where the row has no
+    nonzero diagonal entry); each row's products summed left to right in FP64.  The error
+    x' - x* is (I - omega D^-1 A)(x - x*), which damps error at the large eigenvalues of D^-1 A
+    (rough error on a diagonally dominant operator)."""
+    n = len(row_ptr) - 1
+    x = np.asarray(x, dtype=np.float64)
+    out = np.empty(n)
+    for i in range(n):
+        s, d = 0.0, 0.0
+        for j in range(row_ptr[i], row_ptr[i + 1]):
+            s += val[j] * x[col[j]]
+            if col[j] == i:
+                d = val[j]
+        if d == 0.0:
+            d = 1.0
+        out[i] = x[i] + omega * ((b[i] - s) / d)
+    return out
+
+
 def adam_step(p, g, m, v, step, lr=1e-3, beta1=0.9, beta2=0.999, eps=1e-8):
     """One Adam update (Kingma & Ba, ICLR 2015, Algorithm 1) in FP64; returns (p, m, v)."""
     m = beta1 * m + (1 - beta1) * g

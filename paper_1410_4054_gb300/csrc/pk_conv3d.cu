@@ -775,6 +775,25 @@ __global__ void k_ws_apply_gamma(int n, const float* out, const double* xm1, con
   xhat[v] = fma(gamma[0], scales[0] * (double)out[v], e);
 }
 
+// One damped Jacobi sweep from a starting guess: xout_i = x_i + omega (b_i - sum_j a_ij x_j) / d_i,
+// d_i = a_ii (1 where the row has no nonzero diagonal entry); the row's products are summed
+// left to right.  Applied to the learned guess it damps the rough part of the guess's error,
+// the part CG removes slowest on this operator.
+__global__ void k_ws_relax(int n, const int32_t* __restrict__ rp, const int32_t* __restrict__ ci,
+                           const double* __restrict__ va, const double* __restrict__ b,
+                           const double* __restrict__ x, double omega, double* __restrict__ xout) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  double s = 0.0, d = 0.0;
+  for (int j = rp[i]; j < rp[i + 1]; ++j) {
+    const int c = ci[j];
+    s = fma(va[j], x[c], s);
+    if (c == i) d = va[j];
+  }
+  if (d == 0.0) d = 1.0;
+  xout[i] = fma(omega, (b[i] - s) / d, x[i]);
+}
+
 // Adam on FP32 master parameters, optional BF16 copy.
 __global__ void k_adam(int count, float* p, const float* grad, float* m, float* v, float lr,
                        float b1, float b2, float eps, float c1, float c2, __nv_bfloat16* p16) {
@@ -1022,6 +1041,23 @@ pk_status pk_warmstart_apply_energy(pk_csr* A, const float* out, const double* x
   PK_CUDA(cudaMemsetAsync(scratch + 3 * kWsGrid, 0, sizeof(double), s));
   k_ws_energy<<<kWsGrid, kBlock, 0, s>>>(n, A->rp, A->ci, A->va, out, xm1, xm2, b, scales, gamma, scratch);
   k_ws_apply_gamma<<<(n + 255) / 256, 256, 0, s>>>(n, out, xm1, xm2, scales, gamma, xhat);
+  PK_CUDA(cudaGetLastError());
+  return PK_OK;
+}
+
+pk_status pk_warmstart_relax(pk_csr* A, const double* b, const double* x, double omega, double* xout,
+                             void* stream) {
+  if (!A || !b || !x || !xout || !(omega > 0.0 && omega < 2.0)) {
+    set_error("pk_warmstart_relax: bad arguments (omega must lie in (0, 2))");
+    return PK_ERR_ARG;
+  }
+  if (x == xout) {
+    set_error("pk_warmstart_relax: xout must not be x (rows read x at other rows' columns)");
+    return PK_ERR_ARG;
+  }
+  const int n = A->n;
+  if (n == 0) return PK_OK;
+  k_ws_relax<<<(n + 255) / 256, 256, 0, (cudaStream_t)stream>>>(n, A->rp, A->ci, A->va, b, x, omega, xout);
   PK_CUDA(cudaGetLastError());
   return PK_OK;
 }

@@ -104,6 +104,8 @@ EXPORTS = {
                                      C.c_void_p, C.c_void_p]),
     "pk_warmstart_apply_energy": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p,
                                             C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p]),
+    "pk_warmstart_relax": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_double, C.c_void_p,
+                                     C.c_void_p]),
     "pk_adam_step": (C.c_int, [C.c_int64, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_float,
                                C.c_float, C.c_float, C.c_float, C.c_int32, C.c_void_p, C.c_void_p]),
     "pk_status_string": (C.c_char_p, [C.c_int]),
@@ -420,6 +422,12 @@ def warmstart_apply_energy(A: CSRMatrix, out, xm1, xm2, b, scales, xhat, gamma, 
     _check(lib().pk_warmstart_apply_energy(A.handle, _ptr(out), _ptr(xm1), _ptr(xm2), _ptr(b), _ptr(scales),
                                            _ptr(xhat), _ptr(gamma), _ptr(scratch), _stream_ptr(stream)),
            "pk_warmstart_apply_energy")
+
+
+def warmstart_relax(A: CSRMatrix, b, x, omega, xout, stream=None):
+    """xout = x + omega (b - A x) / diag(A): one damped Jacobi sweep (xout must not be x)."""
+    _check(lib().pk_warmstart_relax(A.handle, _ptr(b), _ptr(x), float(omega), _ptr(xout), _stream_ptr(stream)),
+           "pk_warmstart_relax")
 
 
 def adam_step(p, grad, m, v, lr, step, beta1=0.9, beta2=0.999, eps=1e-8, p_bf16=None, stream=None):

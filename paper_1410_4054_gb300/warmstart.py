@@ -14,8 +14,15 @@ network is told nothing it would have to memorise position by position.  Predict
 x_hat = e + s0 net(input), loss = mean((net - (x_t - e)/s0)^2).  The weights start at the
 identity on channel 0 (relu(z) - relu(-z) = z through two hidden channels), i.e. at the Jacobi
 step, and training moves them from there.
-The solver is always run to the same tolerance: of x_hat and x_{t-1}, the one with the smaller
-residual ||b - A x0|| is the initial guess, so the plain warm start is both fallback and yardstick.
+The network's error is rough (its BF16 operands round every voxel independently), and CG
+removes rough error slowly on this operator while it removes the smooth error of the
+extrapolation in a few iterations; so the learned start takes x_hat through RELAX_SWEEPS damped
+Jacobi sweeps (pk_warmstart_relax), which damp error at the large eigenvalues of D^-1 A and
+leave the smooth part to CG.  The same sweeps applied to the extrapolation are reported as the
+ablation (they do not help it: its error is already smooth).
+The solver is always run to the same tolerance: of the guess and x_{t-1}, the one with the
+smaller residual ||b - A x0|| is the initial guess, so the plain warm start is both fallback and
+yardstick.
 The experiment also reports the extrapolation alone (network output taken as zero), so the
 network's own contribution is visible, and the energy step: the network's correction d taken as
 a search direction from e, x0 = e + gamma d with the gamma that minimises the A-norm of the
@@ -32,6 +39,9 @@ from . import pk
 
 CH = 16
 LAYERS = ((3, 16), (16, 16), (16, 16), (16, 1))
+# damped Jacobi sweeps applied to the learned guess before the residual check (see relax)
+RELAX_OMEGA = 0.8
+RELAX_SWEEPS = 3
 
 
 def initial_weights(seed=0, noise_std=1e-3):
@@ -171,8 +181,22 @@ class ConvNet:
         pk.warmstart_apply_energy(A, self.out, xm1, xm2, b, self.scales, xhat, gamma, self.scratch)
 
 
+def relax(A, b, x, tmp, omega=RELAX_OMEGA, sweeps=RELAX_SWEEPS):
+    """`sweeps` damped Jacobi sweeps on A x = b from x, alternating between x and tmp (a vector
+    of the same size); returns the one that holds the result.  Each sweep damps the guess's
+    error at the large eigenvalues of D^-1 A by |1 - omega lambda|: the rough error a BF16
+    network leaves, which CG reduces slowly, while the smooth error that CG removes in a few
+    iterations is left to CG."""
+    src, dst = x, tmp
+    for _ in range(sweeps):
+        pk.warmstart_relax(A, b, src, omega, dst)
+        src, dst = dst, src
+    return src
+
+
 def run_transient(k=64, steps=300, train_last=150, epochs=30, lr=1e-3, tol=1e-8, seed=0,
-                  device="cuda", log=None, checkpoint=None, resume=False):
+                  device="cuda", log=None, checkpoint=None, resume=False,
+                  relax_omega=None, relax_sweeps=None):
     """The transient experiment: solve the whole sequence with the x_{t-1} warm start, train on
     steps 2..train_last, then re-solve steps train_last+1..steps from (a) the linear
     extrapolation 2 x_{t-1} - x_{t-2} and (b) the learned guess, each measured against x_{t-1} by
@@ -188,6 +212,9 @@ def run_transient(k=64, steps=300, train_last=150, epochs=30, lr=1e-3, tol=1e-8,
     import torch
 
     from . import workloads as W
+
+    relax_omega = RELAX_OMEGA if relax_omega is None else float(relax_omega)
+    relax_sweeps = RELAX_SWEEPS if relax_sweeps is None else int(relax_sweeps)
 
     T = W.transient_heat(k, steps=steps, seed=seed)
     A = pk.CSRMatrix.from_workload(T.M)
@@ -243,6 +270,7 @@ def run_transient(k=64, steps=300, train_last=150, epochs=30, lr=1e-3, tol=1e-8,
                     "base_ms": base_ms, "net": net.state_dict()}, checkpoint)
 
     xhat = zeros.clone()
+    xtmp = zeros.clone()
     r2 = torch.zeros(2, dtype=torch.float64, device=device)
 
     gamma = torch.zeros(1, dtype=torch.float64, device=device)
@@ -255,13 +283,16 @@ def run_transient(k=64, steps=300, train_last=150, epochs=30, lr=1e-3, tol=1e-8,
             st = torch.cuda.Event(enable_timing=True)
             en = torch.cuda.Event(enable_timing=True)
             st.record()
-            if mode == "learned":
+            if mode.startswith("learned"):
                 net.predict(A, xs[t], xs[t - 1], b, xhat)
             elif mode == "energy":
                 net.predict_energy(A, xs[t], xs[t - 1], b, xhat, gamma)
             else:
                 pk.warmstart_apply(n, None, xs[t], xs[t - 1], net.scales, xhat)
-            pk.residual_norm2(A, b, xhat, r2[0:1])
+            guess = xhat
+            if mode.endswith("relaxed"):
+                guess = relax(A, b, xhat, xtmp, relax_omega, relax_sweeps)
+            pk.residual_norm2(A, b, guess, r2[0:1])
             pk.residual_norm2(A, b, xs[t], r2[1:2])
             en.record()
             torch.cuda.synchronize()
@@ -270,7 +301,7 @@ def run_transient(k=64, steps=300, train_last=150, epochs=30, lr=1e-3, tol=1e-8,
             pick = ra < rb
             chosen += int(pick)
             kept.append(np.sqrt(min(ra, rb) / rb) if rb > 0 else 1.0)
-            x = (xhat if pick else xs[t]).clone()
+            x = (guess if pick else xs[t]).clone()
             info = pk.cg_solve(A, b, x, tol=tol, maxit=10_000)
             assert info["status"] == pk.PK_OK, info
             iters.append(info["iters"])
@@ -282,6 +313,8 @@ def run_transient(k=64, steps=300, train_last=150, epochs=30, lr=1e-3, tol=1e-8,
     ex_iters, ex_ms, ex_chosen, ex_ratio, ex_kept = evaluate("extrap")
     ln_iters, ln_ms, ln_chosen, ln_ratio, ln_kept = evaluate("learned")
     en_iters, en_ms, en_chosen, en_ratio, en_kept = evaluate("energy")
+    lr_iters, lr_ms, lr_chosen, lr_ratio, lr_kept = evaluate("learned_relaxed")
+    er_iters, er_ms, er_chosen, er_ratio, er_kept = evaluate("extrap_relaxed")
     ev = slice(train_last, steps)
     return {
         "k": k, "n": n, "steps": steps, "train_samples": len(train), "epochs": epochs,
@@ -302,4 +335,11 @@ def run_transient(k=64, steps=300, train_last=150, epochs=30, lr=1e-3, tol=1e-8,
         "energy_chosen_steps": en_chosen, "energy_max_kept_ratio": en_kept,
         "energy_gamma_mean": float(np.mean(gammas)), "energy_gamma_min": float(np.min(gammas)),
         "energy_gamma_max": float(np.max(gammas)),
+        "relax_omega": relax_omega, "relax_sweeps": relax_sweeps,
+        "learned_relaxed_iters_eval": lr_iters, "learned_relaxed_mean_iters": float(np.mean(lr_iters)),
+        "learned_relaxed_mean_ms": float(np.mean(lr_ms)), "learned_relaxed_residual_ratio": lr_ratio,
+        "learned_relaxed_chosen_steps": lr_chosen, "learned_relaxed_max_kept_ratio": lr_kept,
+        "extrap_relaxed_iters_eval": er_iters, "extrap_relaxed_mean_iters": float(np.mean(er_iters)),
+        "extrap_relaxed_mean_ms": float(np.mean(er_ms)), "extrap_relaxed_residual_ratio": er_ratio,
+        "extrap_relaxed_chosen_steps": er_chosen, "extrap_relaxed_max_kept_ratio": er_kept,
     }

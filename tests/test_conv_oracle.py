@@ -204,3 +204,35 @@ def test_warmstart_energy_step_minimises_the_energy_error():
     assert g2 == pytest.approx(1.0, rel=1e-12)
     _, g3 = C.warmstart_energy_step(*_csr(dense), xm1, xm2, b, np.zeros(n, np.float32), s0)
     assert g3 == 0.0
+
+
+def test_warmstart_relax_pins():
+    """The Jacobi sweep of the learned guess: on a diagonal matrix one sweep with omega = 1 is
+    the exact solution b / diag(A); the solution of a dense LU solve is a fixed point; the error
+    after one sweep equals (I - omega D^-1 A) times the error before it, with D^-1 A formed from
+    the dense matrix; repeated sweeps on a diagonally dominant matrix converge to the LU
+    solution; a row without a diagonal entry divides by 1."""
+    r = rng(21)
+    n = 11
+    diag = r.uniform(1.0, 3.0, n)
+    b = r.standard_normal(n)
+    x0 = r.standard_normal(n)
+    np.testing.assert_allclose(C.warmstart_relax(*_csr(np.diag(diag)), b, x0, 1.0), b / diag,
+                               rtol=1e-15, atol=0)
+    m = r.standard_normal((n, n))
+    m[np.abs(m) < 0.8] = 0.0
+    dense = m + np.diag(np.abs(m).sum(axis=1) * 1.5 + 1.0)   # strictly diagonally dominant
+    xs = np.linalg.solve(dense, b)
+    np.testing.assert_allclose(C.warmstart_relax(*_csr(dense), b, xs, 0.8), xs, rtol=0, atol=1e-13)
+    prop = np.eye(n) - 0.8 * (dense / np.diag(dense)[:, None])
+    np.testing.assert_allclose(C.warmstart_relax(*_csr(dense), b, x0, 0.8) - xs, prop @ (x0 - xs),
+                               rtol=0, atol=1e-13)
+    x = x0.copy()
+    for _ in range(200):
+        x = C.warmstart_relax(*_csr(dense), b, x, 0.8)
+    np.testing.assert_allclose(x, xs, rtol=0, atol=1e-12)
+    # rows 0 and 1 without a diagonal entry: d = 1
+    nodiag = dense.copy()
+    nodiag[0, 0] = nodiag[1, 1] = 0.0
+    got = C.warmstart_relax(*_csr(nodiag), b, x0, 0.5)
+    assert got[0] == pytest.approx(x0[0] + 0.5 * (b[0] - nodiag[0] @ x0), rel=1e-13)
