@@ -206,33 +206,74 @@ def test_warmstart_energy_step_minimises_the_energy_error():
     assert g3 == 0.0
 
 
-def test_warmstart_relax_pins():
-    """The Jacobi sweep of the learned guess: on a diagonal matrix one sweep with omega = 1 is
-    the exact solution b / diag(A); the solution of a dense LU solve is a fixed point; the error
-    after one sweep equals (I - omega D^-1 A) times the error before it, with D^-1 A formed from
-    the dense matrix; repeated sweeps on a diagonally dominant matrix converge to the LU
-    solution; a row without a diagonal entry divides by 1."""
+def _relax_pins(relax):
+    """The pins of one damped Jacobi sweep, applied to an implementation `relax(row_ptr, col,
+    val, b, x, omega)`: on a diagonal matrix one sweep with omega = 1 is the exact solution
+    b / diag(A); the solution of a dense LU solve is a fixed point; the error after one sweep
+    equals (I - omega D^-1 A) times the error before it, with D^-1 A formed from the dense
+    matrix; repeated sweeps on a diagonally dominant matrix converge to the LU solution; a row
+    without a diagonal entry divides by 1."""
     r = rng(21)
     n = 11
     diag = r.uniform(1.0, 3.0, n)
     b = r.standard_normal(n)
     x0 = r.standard_normal(n)
-    np.testing.assert_allclose(C.warmstart_relax(*_csr(np.diag(diag)), b, x0, 1.0), b / diag,
-                               rtol=1e-15, atol=0)
+    np.testing.assert_allclose(relax(*_csr(np.diag(diag)), b, x0, 1.0), b / diag, rtol=1e-15, atol=0)
     m = r.standard_normal((n, n))
     m[np.abs(m) < 0.8] = 0.0
     dense = m + np.diag(np.abs(m).sum(axis=1) * 1.5 + 1.0)   # strictly diagonally dominant
     xs = np.linalg.solve(dense, b)
-    np.testing.assert_allclose(C.warmstart_relax(*_csr(dense), b, xs, 0.8), xs, rtol=0, atol=1e-13)
+    np.testing.assert_allclose(relax(*_csr(dense), b, xs, 0.8), xs, rtol=0, atol=1e-13)
     prop = np.eye(n) - 0.8 * (dense / np.diag(dense)[:, None])
-    np.testing.assert_allclose(C.warmstart_relax(*_csr(dense), b, x0, 0.8) - xs, prop @ (x0 - xs),
-                               rtol=0, atol=1e-13)
+    np.testing.assert_allclose(relax(*_csr(dense), b, x0, 0.8) - xs, prop @ (x0 - xs), rtol=0, atol=1e-13)
     x = x0.copy()
     for _ in range(200):
-        x = C.warmstart_relax(*_csr(dense), b, x, 0.8)
+        x = relax(*_csr(dense), b, x, 0.8)
     np.testing.assert_allclose(x, xs, rtol=0, atol=1e-12)
     # rows 0 and 1 without a diagonal entry: d = 1
     nodiag = dense.copy()
     nodiag[0, 0] = nodiag[1, 1] = 0.0
-    got = C.warmstart_relax(*_csr(nodiag), b, x0, 0.5)
+    got = relax(*_csr(nodiag), b, x0, 0.5)
     assert got[0] == pytest.approx(x0[0] + 0.5 * (b[0] - nodiag[0] @ x0), rel=1e-13)
+
+
+def test_warmstart_relax_pins():
+    _relax_pins(C.warmstart_relax)
+
+
+def _relax_mutant(kind):
+    """A copy of the oracle's sweep with one plausible mistake planted."""
+    def relax(row_ptr, col, val, b, x, omega):
+        n = len(row_ptr) - 1
+        x = np.asarray(x, dtype=np.float64)
+        out = np.empty(n)
+        for i in range(n):
+            s, d, rowsum = 0.0, 0.0, 0.0
+            for j in range(row_ptr[i], row_ptr[i + 1]):
+                s += val[j] * x[col[j]]
+                rowsum += abs(val[j])
+                if col[j] == i:
+                    d = val[j]
+            if d == 0.0:
+                d = 1.0
+            if kind == "sign":              # the residual with the wrong sign
+                out[i] = x[i] + omega * ((s - b[i]) / d)
+            elif kind == "omega_on_x":      # the damping applied to the old iterate
+                out[i] = omega * x[i] + (b[i] - s) / d
+            elif kind == "row_sum":         # the row's absolute sum instead of its diagonal
+                out[i] = x[i] + omega * ((b[i] - s) / rowsum)
+            elif kind == "no_division":     # the residual not scaled by the diagonal
+                out[i] = x[i] + omega * (b[i] - s)
+            elif kind == "updated_gather":  # Gauss-Seidel: rows read values already updated
+                x = x.copy()
+                x[i] = x[i] + omega * ((b[i] - s) / d)
+                out[i] = x[i]
+        return out
+    return relax
+
+
+@pytest.mark.parametrize("kind", ["sign", "omega_on_x", "row_sum", "no_division", "updated_gather"])
+def test_warmstart_relax_pins_catch_mutants(kind):
+    """Each planted mistake in the sweep fails at least one of its pins."""
+    with pytest.raises(AssertionError):
+        _relax_pins(_relax_mutant(kind))
