@@ -473,6 +473,20 @@ pk_status pk_warmstart_apply_energy(pk_csr* A, const float* out, const double* x
  * (An extension; the paper has no learned part.) */
 pk_status pk_warmstart_relax(pk_csr* A, const double* b, const double* x, double omega, double* xout,
                              void* stream);
+/* Training loss of the learned guess in the form CG receives it: after `sweeps` damped Jacobi
+ * sweeps (pk_warmstart_relax with the same omega).  With delta = out - (x_t - 2 x_{t-1} +
+ * x_{t-2}) / s0 (the guess's error in units of s0 = scales[0]) and P = I - omega D^-1 A (one
+ * sweep's error propagator), *loss = mean((P^s delta)^2) and G = bf16(gradient) in channel 0
+ * (other channels 0), gradient = (2/n) (P^T)^s P^s delta with P^T g = g - omega A (D^-1 g),
+ * which holds for a SYMMETRIC A (the implicit heat-equation operator).  sweeps = 0 gives the
+ * loss of pk_warmstart_loss.  omega in (0, 2), sweeps in [0, PK_WS_MAX_SWEEPS], n > 0
+ * (PK_ERR_ARG otherwise).  work: 3 n doubles of device memory owned by the caller; scratch:
+ * pk_warmstart_scratch_doubles() doubles.  1 + 2 sweeps passes over A; stream-ordered.
+ * (An extension; the paper has no learned part.) */
+#define PK_WS_MAX_SWEEPS 8
+pk_status pk_warmstart_loss_swept(pk_csr* A, const float* out, const double* xt, const double* xm1,
+                                  const double* xm2, const double* scales, double omega, int32_t sweeps,
+                                  void* G, double* loss, double* work, double* scratch, void* stream);
 /* Adam (Kingma & Ba) on FP32 parameters, step >= 1; p_bf16 (nullable) receives a BF16 copy. */
 pk_status pk_adam_step(int64_t count, float* p, const float* grad, float* m, float* v, float lr,
                        float beta1, float beta2, float eps, int32_t step, void* p_bf16,

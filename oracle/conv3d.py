@@ -171,6 +171,44 @@ def warmstart_relax(row_ptr, col, val, b, x, omega):
     return out
 
 
+def warmstart_swept_loss(row_ptr, col, val, out, xt, xm1, xm2, s0, omega, sweeps):
+    """Loss of the learned guess in the form CG receives it -- after `sweeps` damped Jacobi
+    sweeps -- and its gradient with respect to the network output, for a symmetric A.
+
+    The guess x_hat = e + s0 out (e = 2 x_{t-1} - x_{t-2}) has the error s0 delta with
+    delta = out - (x_t - e) / s0.  A sweep x <- x + omega D^-1 (b - A x) with b = A x_t maps an
+    error e to P e = e - omega D^-1 A e (b drops out).  loss = mean((P^s delta)^2); its
+    gradient is (2/n) (P^T)^s P^s delta, where P^T g = g - omega A (D^-1 g) because A is
+    symmetric.  d_i = a_ii (1 where the row has no nonzero diagonal entry); rows summed left
+    to right in FP64.  Returns (loss, gradient)."""
+    n = len(row_ptr) - 1
+    d = np.ones(n)
+    for i in range(n):
+        for j in range(row_ptr[i], row_ptr[i + 1]):
+            if col[j] == i and val[j] != 0.0:
+                d[i] = val[j]
+    e = np.asarray(out, dtype=np.float64) - (np.asarray(xt) - 2.0 * np.asarray(xm1) + np.asarray(xm2)) / s0
+    for _ in range(sweeps):
+        nxt = np.empty(n)
+        for i in range(n):
+            acc = 0.0
+            for j in range(row_ptr[i], row_ptr[i + 1]):
+                acc += val[j] * e[col[j]]
+            nxt[i] = e[i] + omega * ((0.0 - acc) / d[i])
+        e = nxt
+    loss = float(np.mean(e * e))
+    g = e
+    for _ in range(sweeps):
+        nxt = np.empty(n)
+        for i in range(n):
+            acc = 0.0
+            for j in range(row_ptr[i], row_ptr[i + 1]):
+                acc += val[j] * (g[col[j]] / d[col[j]])
+            nxt[i] = g[i] - omega * acc
+        g = nxt
+    return loss, 2.0 * g / n
+
+
 def adam_step(p, g, m, v, step, lr=1e-3, beta1=0.9, beta2=0.999, eps=1e-8):
     """One Adam update (Kingma & Ba, ICLR 2015, Algorithm 1) in FP64; returns (p, m, v)."""
     m = beta1 * m + (1 - beta1) * g

@@ -794,6 +794,71 @@ __global__ void k_ws_relax(int n, const int32_t* __restrict__ rp, const int32_t*
   xout[i] = fma(omega, (b[i] - s) / d, x[i]);
 }
 
+// Loss of the learned guess after damped Jacobi sweeps (training through the sweeps).  The
+// guess's error in units of s0 is delta = out - (x_t - 2 x_{t-1} + x_{t-2}) / s0; a sweep maps
+// an error e to P e = e - omega D^-1 A e; the loss is mean((P^s delta)^2) and its gradient
+// (2/n) (P^T)^s P^s delta, P^T g = g - omega A (D^-1 g) for a symmetric A.
+// d_i = a_ii (1 where the row has no nonzero diagonal entry).
+__global__ void k_ws_diag(int n, const int32_t* __restrict__ rp, const int32_t* __restrict__ ci,
+                          const double* __restrict__ va, double* __restrict__ d) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  double di = 1.0;
+  for (int j = rp[i]; j < rp[i + 1]; ++j)
+    if (ci[j] == i && va[j] != 0.0) di = va[j];
+  d[i] = di;
+}
+
+__global__ void k_ws_delta(int n, const float* __restrict__ out, const double* __restrict__ xt,
+                           const double* __restrict__ xm1, const double* __restrict__ xm2,
+                           const double* __restrict__ scales, double* __restrict__ e) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  e[i] = (double)out[i] - (xt[i] - 2.0 * xm1[i] + xm2[i]) / scales[0];
+}
+
+// eout = e - omega D^-1 A e (one sweep's error propagator)
+__global__ void k_ws_prop(int n, const int32_t* __restrict__ rp, const int32_t* __restrict__ ci,
+                          const double* __restrict__ va, const double* __restrict__ d, double omega,
+                          const double* __restrict__ e, double* __restrict__ eout) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  double s = 0.0;
+  for (int j = rp[i]; j < rp[i + 1]; ++j) s = fma(va[j], e[ci[j]], s);
+  eout[i] = fma(omega, (0.0 - s) / d[i], e[i]);
+}
+
+// gout = g - omega A (D^-1 g) (its transpose, A symmetric)
+__global__ void k_ws_prop_t(int n, const int32_t* __restrict__ rp, const int32_t* __restrict__ ci,
+                            const double* __restrict__ va, const double* __restrict__ d, double omega,
+                            const double* __restrict__ g, double* __restrict__ gout) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  double s = 0.0;
+  for (int j = rp[i]; j < rp[i + 1]; ++j) {
+    const int c = ci[j];
+    s = fma(va[j], g[c] / d[c], s);
+  }
+  gout[i] = fma(-omega, s, g[i]);
+}
+
+// *loss = mean(e^2)
+__global__ void __launch_bounds__(kBlock) k_ws_sq_mean(int n, const double* e, double* loss, double* scratch) {
+  double sum[1];
+  bool last;
+  grid_sums<1>(n, scratch, [&](int i, double (&v)[1]) { v[0] = fma(e[i], e[i], v[0]); }, sum, last);
+  if (last && threadIdx.x == 0) *loss = sum[0] / n;
+}
+
+// G[v][0] = bf16(2 g_v / n), other channels 0
+__global__ void k_ws_grad_pack(int n, const double* __restrict__ g, __nv_bfloat16* __restrict__ G) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  __nv_bfloat16* gi = G + (size_t)i * kCh;
+  gi[0] = __float2bfloat16_rn((float)(2.0 * g[i] / n));
+  for (int c = 1; c < kCh; ++c) gi[c] = __float2bfloat16_rn(0.f);
+}
+
 // Adam on FP32 master parameters, optional BF16 copy.
 __global__ void k_adam(int count, float* p, const float* grad, float* m, float* v, float lr,
                        float b1, float b2, float eps, float c1, float c2, __nv_bfloat16* p16) {
@@ -1058,6 +1123,33 @@ pk_status pk_warmstart_relax(pk_csr* A, const double* b, const double* x, double
   const int n = A->n;
   if (n == 0) return PK_OK;
   k_ws_relax<<<(n + 255) / 256, 256, 0, (cudaStream_t)stream>>>(n, A->rp, A->ci, A->va, b, x, omega, xout);
+  PK_CUDA(cudaGetLastError());
+  return PK_OK;
+}
+
+pk_status pk_warmstart_loss_swept(pk_csr* A, const float* out, const double* xt, const double* xm1,
+                                  const double* xm2, const double* scales, double omega, int32_t sweeps,
+                                  void* G, double* loss, double* work, double* scratch, void* stream) {
+  if (!A || !out || !xt || !xm1 || !xm2 || !scales || !G || !loss || !work || !scratch ||
+      !(omega > 0.0 && omega < 2.0) || sweeps < 0 || sweeps > PK_WS_MAX_SWEEPS || A->n == 0) {
+    set_error("pk_warmstart_loss_swept: bad arguments (omega in (0, 2), sweeps in [0, 8], n > 0)");
+    return PK_ERR_ARG;
+  }
+  const int n = A->n;
+  const int nb = (n + 255) / 256;
+  cudaStream_t s = (cudaStream_t)stream;
+  double* d = work;
+  double* buf[2] = {work + n, work + 2 * (size_t)n};
+  k_ws_diag<<<nb, 256, 0, s>>>(n, A->rp, A->ci, A->va, d);
+  k_ws_delta<<<nb, 256, 0, s>>>(n, out, xt, xm1, xm2, scales, buf[0]);
+  int cur = 0;
+  for (int k = 0; k < sweeps; ++k, cur ^= 1)
+    k_ws_prop<<<nb, 256, 0, s>>>(n, A->rp, A->ci, A->va, d, omega, buf[cur], buf[cur ^ 1]);
+  PK_CUDA(cudaMemsetAsync(scratch + 3 * kWsGrid, 0, sizeof(double), s));
+  k_ws_sq_mean<<<kWsGrid, kBlock, 0, s>>>(n, buf[cur], loss, scratch);
+  for (int k = 0; k < sweeps; ++k, cur ^= 1)
+    k_ws_prop_t<<<nb, 256, 0, s>>>(n, A->rp, A->ci, A->va, d, omega, buf[cur], buf[cur ^ 1]);
+  k_ws_grad_pack<<<nb, 256, 0, s>>>(n, buf[cur], static_cast<__nv_bfloat16*>(G));
   PK_CUDA(cudaGetLastError());
   return PK_OK;
 }

@@ -106,6 +106,9 @@ EXPORTS = {
                                             C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p]),
     "pk_warmstart_relax": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_double, C.c_void_p,
                                      C.c_void_p]),
+    "pk_warmstart_loss_swept": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p,
+                                          C.c_void_p, C.c_double, C.c_int32, C.c_void_p, C.c_void_p,
+                                          C.c_void_p, C.c_void_p, C.c_void_p]),
     "pk_adam_step": (C.c_int, [C.c_int64, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_float,
                                C.c_float, C.c_float, C.c_float, C.c_int32, C.c_void_p, C.c_void_p]),
     "pk_status_string": (C.c_char_p, [C.c_int]),
@@ -428,6 +431,14 @@ def warmstart_relax(A: CSRMatrix, b, x, omega, xout, stream=None):
     """xout = x + omega (b - A x) / diag(A): one damped Jacobi sweep (xout must not be x)."""
     _check(lib().pk_warmstart_relax(A.handle, _ptr(b), _ptr(x), float(omega), _ptr(xout), _stream_ptr(stream)),
            "pk_warmstart_relax")
+
+
+def warmstart_loss_swept(A: CSRMatrix, out, xt, xm1, xm2, scales, omega, sweeps, G, loss, work, scratch,
+                         stream=None):
+    """Loss and output gradient of the guess after `sweeps` Jacobi sweeps (A symmetric)."""
+    _check(lib().pk_warmstart_loss_swept(A.handle, _ptr(out), _ptr(xt), _ptr(xm1), _ptr(xm2), _ptr(scales),
+                                         float(omega), int(sweeps), _ptr(G), _ptr(loss), _ptr(work),
+                                         _ptr(scratch), _stream_ptr(stream)), "pk_warmstart_loss_swept")
 
 
 def adam_step(p, grad, m, v, lr, step, beta1=0.9, beta2=0.999, eps=1e-8, p_bf16=None, stream=None):

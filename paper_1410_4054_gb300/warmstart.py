@@ -42,6 +42,8 @@ LAYERS = ((3, 16), (16, 16), (16, 16), (16, 1))
 # damped Jacobi sweeps applied to the learned guess before the residual check (see relax)
 RELAX_OMEGA = 0.8
 RELAX_SWEEPS = 3
+# train on the error of the guess after those sweeps (pk_warmstart_loss_swept)
+TRAIN_SWEPT = False
 
 
 def initial_weights(seed=0, noise_std=1e-3):
@@ -97,6 +99,7 @@ class ConvNet:
         self.scratch = torch.zeros(pk.warmstart_scratch_doubles(), dtype=torch.float64, device=device)
         self.wscratch = torch.zeros(pk.conv3d_wgrad_scratch_floats(self.dims), dtype=torch.float32,
                                     device=device)
+        self.work = None  # 3 n doubles for the swept loss, allocated on first use
         self.step = 0
         self.refresh_flipped()
 
@@ -160,11 +163,20 @@ class ConvNet:
             pk.adam_step(self.b32[li], self.db[li], self.mb[li], self.vb[li], lr, self.step)
         self.refresh_flipped()
 
-    def train_sample(self, A, xm1, xm2, b, xt, lr=1e-3):
+    def train_sample(self, A, xm1, xm2, b, xt, lr=1e-3, swept=None):
+        """One Adam step on one sample.  swept = (omega, sweeps): the loss is taken on the guess
+        after that many damped Jacobi sweeps (the form the solver receives), else on the guess
+        itself."""
         self.pack(A, xm1, xm2, b)
         self.forward()
-        pk.warmstart_loss(self.n, self.out, xt, xm1, xm2, self.scales, self.grads[-1], self.loss,
-                          self.scratch)
+        if swept:
+            if self.work is None:
+                self.work = self.torch.zeros(3 * self.n, dtype=self.torch.float64, device=self.device)
+            pk.warmstart_loss_swept(A, self.out, xt, xm1, xm2, self.scales, swept[0], swept[1],
+                                    self.grads[-1], self.loss, self.work, self.scratch)
+        else:
+            pk.warmstart_loss(self.n, self.out, xt, xm1, xm2, self.scales, self.grads[-1], self.loss,
+                              self.scratch)
         self.backward()
         self.adam(lr)
 
@@ -196,7 +208,7 @@ def relax(A, b, x, tmp, omega=RELAX_OMEGA, sweeps=RELAX_SWEEPS):
 
 def run_transient(k=64, steps=300, train_last=150, epochs=30, lr=1e-3, tol=1e-8, seed=0,
                   device="cuda", log=None, checkpoint=None, resume=False,
-                  relax_omega=None, relax_sweeps=None):
+                  relax_omega=None, relax_sweeps=None, train_swept=None):
     """The transient experiment: solve the whole sequence with the x_{t-1} warm start, train on
     steps 2..train_last, then re-solve steps train_last+1..steps from (a) the linear
     extrapolation 2 x_{t-1} - x_{t-2} and (b) the learned guess, each measured against x_{t-1} by
@@ -215,6 +227,8 @@ def run_transient(k=64, steps=300, train_last=150, epochs=30, lr=1e-3, tol=1e-8,
 
     relax_omega = RELAX_OMEGA if relax_omega is None else float(relax_omega)
     relax_sweeps = RELAX_SWEEPS if relax_sweeps is None else int(relax_sweeps)
+    train_swept = TRAIN_SWEPT if train_swept is None else bool(train_swept)
+    swept = (relax_omega, relax_sweeps) if train_swept else None
 
     T = W.transient_heat(k, steps=steps, seed=seed)
     A = pk.CSRMatrix.from_workload(T.M)
@@ -253,7 +267,7 @@ def run_transient(k=64, steps=300, train_last=150, epochs=30, lr=1e-3, tol=1e-8,
         order = rng.permutation(train)
         acc = 0.0
         for t in order:
-            net.train_sample(A, xs[t], xs[t - 1], bs[t + 1], xs[t + 1], lr=lr)
+            net.train_sample(A, xs[t], xs[t - 1], bs[t + 1], xs[t + 1], lr=lr, swept=swept)
             if ep in (0, epochs - 1):
                 acc += float(net.loss.item())
         if ep == 0:
@@ -335,7 +349,7 @@ def run_transient(k=64, steps=300, train_last=150, epochs=30, lr=1e-3, tol=1e-8,
         "energy_chosen_steps": en_chosen, "energy_max_kept_ratio": en_kept,
         "energy_gamma_mean": float(np.mean(gammas)), "energy_gamma_min": float(np.min(gammas)),
         "energy_gamma_max": float(np.max(gammas)),
-        "relax_omega": relax_omega, "relax_sweeps": relax_sweeps,
+        "relax_omega": relax_omega, "relax_sweeps": relax_sweeps, "train_swept": train_swept,
         "learned_relaxed_iters_eval": lr_iters, "learned_relaxed_mean_iters": float(np.mean(lr_iters)),
         "learned_relaxed_mean_ms": float(np.mean(lr_ms)), "learned_relaxed_residual_ratio": lr_ratio,
         "learned_relaxed_chosen_steps": lr_chosen, "learned_relaxed_max_kept_ratio": lr_kept,

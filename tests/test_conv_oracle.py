@@ -277,3 +277,45 @@ def test_warmstart_relax_pins_catch_mutants(kind):
     """Each planted mistake in the sweep fails at least one of its pins."""
     with pytest.raises(AssertionError):
         _relax_pins(_relax_mutant(kind))
+
+
+def _sym_system(seed, n=10):
+    r = rng(seed)
+    m = r.standard_normal((n, n))
+    m[np.abs(m) < 0.9] = 0.0
+    m = (m + m.T) / 2
+    dense = m + np.diag(np.abs(m).sum(axis=1) * 1.5 + 1.0)   # symmetric, diagonally dominant
+    return dense, r
+
+
+def test_warmstart_swept_loss_pins():
+    """The loss after Jacobi sweeps: with no sweep it is the plain MSE of the output against
+    the target and its gradient 2 (out - y) / n; with sweeps it equals mean((P^s delta)^2) for
+    P = I - omega D^-1 A formed as a dense matrix, and its gradient equals the dense
+    (2/n) (P^s)^T P^s delta (which pins the transposition); central finite differences of the
+    loss agree with the gradient."""
+    dense, r = _sym_system(31)
+    n = dense.shape[0]
+    rp, ci, va = _csr(dense)
+    out = r.standard_normal(n)
+    xt, xm1, xm2 = r.standard_normal((3, n))
+    s0, omega = 0.7, 0.8
+    y = (xt - 2 * xm1 + xm2) / s0
+    loss0, g0 = C.warmstart_swept_loss(rp, ci, va, out, xt, xm1, xm2, s0, omega, 0)
+    assert loss0 == pytest.approx(float(np.mean((out - y) ** 2)), rel=1e-14)
+    np.testing.assert_allclose(g0, 2 * (out - y) / n, rtol=1e-14, atol=0)
+    P = np.eye(n) - omega * (dense / np.diag(dense)[:, None])
+    for sweeps in (1, 3):
+        Ps = np.linalg.matrix_power(P, sweeps)
+        loss, g = C.warmstart_swept_loss(rp, ci, va, out, xt, xm1, xm2, s0, omega, sweeps)
+        e = Ps @ (out - y)
+        assert loss == pytest.approx(float(np.mean(e * e)), rel=1e-12)
+        np.testing.assert_allclose(g, 2.0 / n * (Ps.T @ e), rtol=0, atol=1e-13 * np.abs(g).max())
+        h = 1e-6
+        for k in (0, 4, n - 1):
+            up, dn = out.copy(), out.copy()
+            up[k] += h
+            dn[k] -= h
+            lu, _ = C.warmstart_swept_loss(rp, ci, va, up, xt, xm1, xm2, s0, omega, sweeps)
+            ld, _ = C.warmstart_swept_loss(rp, ci, va, dn, xt, xm1, xm2, s0, omega, sweeps)
+            assert (lu - ld) / (2 * h) == pytest.approx(g[k], rel=1e-6, abs=1e-10)

@@ -158,6 +158,45 @@ def test_warmstart_relax_matches_oracle():
         A.close()
 
 
+def test_warmstart_swept_loss_matches_oracle():
+    """pk_warmstart_loss_swept (the loss after Jacobi sweeps and its output gradient) against
+    the oracle on the transient operator (symmetric): the loss to 1e-12 relative and the BF16
+    gradient within one BF16 step of the oracle's rounded gradient, zeros in the other
+    channels; 0 and 3 sweeps, two calls in a row; bad omega and sweeps rejected."""
+    from paper_1410_4054_gb300 import workloads as W
+
+    T = W.transient_heat(16, steps=3, seed=2)
+    M = T.M
+    A = pk.CSRMatrix.from_workload(M)
+    r = np.random.default_rng(11)
+    n = M.n
+    dv = lambda v: torch.from_numpy(np.ascontiguousarray(v)).to(DEV)  # noqa: E731
+    xt, xm1, xm2 = r.standard_normal((3, n))
+    out = (0.3 * r.standard_normal(n)).astype(np.float32)
+    scales = torch.tensor([0.4, 1.0, 1.0], dtype=torch.float64, device=DEV)
+    G = torch.zeros((n, 16), dtype=torch.bfloat16, device=DEV)
+    loss = torch.zeros(1, dtype=torch.float64, device=DEV)
+    work = torch.zeros(3 * n, dtype=torch.float64, device=DEV)
+    scratch = torch.zeros(pk.warmstart_scratch_doubles(), dtype=torch.float64, device=DEV)
+    for sweeps in (3, 0, 3):
+        pk.warmstart_loss_swept(A, dv(out), dv(xt), dv(xm1), dv(xm2), scales, 0.8, sweeps, G, loss,
+                                work, scratch)
+        torch.cuda.synchronize()
+        ref_loss, ref_g = C.warmstart_swept_loss(M.row_ptr, M.col, M.val, out, xt, xm1, xm2, 0.4, 0.8,
+                                                 sweeps)
+        assert loss.item() == pytest.approx(ref_loss, rel=1e-12)
+        got = host(G)
+        ref = C.bf16(ref_g.astype(np.float32))
+        step = np.abs(ref) * 2.0 ** -7 + 1e-30
+        assert np.all(np.abs(got[:, 0] - ref) <= step)
+        assert np.all(got[:, 1:] == 0.0)
+    with pytest.raises(RuntimeError, match="omega"):
+        pk.warmstart_loss_swept(A, dv(out), dv(xt), dv(xm1), dv(xm2), scales, 0.0, 3, G, loss, work, scratch)
+    with pytest.raises(RuntimeError, match="sweeps"):
+        pk.warmstart_loss_swept(A, dv(out), dv(xt), dv(xm1), dv(xm2), scales, 0.8, 9, G, loss, work, scratch)
+    A.close()
+
+
 def _grid_operator(dims, r):
     """A symmetric 7-point operator on the grid: 1D second differences summed over the three
     axes with random positive weights, plus 1 on the diagonal (an implicit time step)."""
