@@ -289,6 +289,10 @@ def _sym_system(seed, n=10):
 
 
 def test_warmstart_swept_loss_pins():
+    _swept_pins(C.warmstart_swept_loss)
+
+
+def _swept_pins(swept_loss):
     """The loss after Jacobi sweeps: with no sweep it is the plain MSE of the output against
     the target and its gradient 2 (out - y) / n; with sweeps it equals mean((P^s delta)^2) for
     P = I - omega D^-1 A formed as a dense matrix, and its gradient equals the dense
@@ -301,13 +305,13 @@ def test_warmstart_swept_loss_pins():
     xt, xm1, xm2 = r.standard_normal((3, n))
     s0, omega = 0.7, 0.8
     y = (xt - 2 * xm1 + xm2) / s0
-    loss0, g0 = C.warmstart_swept_loss(rp, ci, va, out, xt, xm1, xm2, s0, omega, 0)
+    loss0, g0 = swept_loss(rp, ci, va, out, xt, xm1, xm2, s0, omega, 0)
     assert loss0 == pytest.approx(float(np.mean((out - y) ** 2)), rel=1e-14)
     np.testing.assert_allclose(g0, 2 * (out - y) / n, rtol=1e-14, atol=0)
     P = np.eye(n) - omega * (dense / np.diag(dense)[:, None])
     for sweeps in (1, 3):
         Ps = np.linalg.matrix_power(P, sweeps)
-        loss, g = C.warmstart_swept_loss(rp, ci, va, out, xt, xm1, xm2, s0, omega, sweeps)
+        loss, g = swept_loss(rp, ci, va, out, xt, xm1, xm2, s0, omega, sweeps)
         e = Ps @ (out - y)
         assert loss == pytest.approx(float(np.mean(e * e)), rel=1e-12)
         np.testing.assert_allclose(g, 2.0 / n * (Ps.T @ e), rtol=0, atol=1e-13 * np.abs(g).max())
@@ -316,6 +320,51 @@ def test_warmstart_swept_loss_pins():
             up, dn = out.copy(), out.copy()
             up[k] += h
             dn[k] -= h
-            lu, _ = C.warmstart_swept_loss(rp, ci, va, up, xt, xm1, xm2, s0, omega, sweeps)
-            ld, _ = C.warmstart_swept_loss(rp, ci, va, dn, xt, xm1, xm2, s0, omega, sweeps)
+            lu, _ = swept_loss(rp, ci, va, up, xt, xm1, xm2, s0, omega, sweeps)
+            ld, _ = swept_loss(rp, ci, va, dn, xt, xm1, xm2, s0, omega, sweeps)
             assert (lu - ld) / (2 * h) == pytest.approx(g[k], rel=1e-6, abs=1e-10)
+
+
+def _swept_mutant(kind):
+    """A copy of the oracle's swept loss with one plausible mistake planted."""
+    def swept(row_ptr, col, val, out, xt, xm1, xm2, s0, omega, sweeps):
+        n = len(row_ptr) - 1
+        d = np.ones(n)
+        for i in range(n):
+            for j in range(row_ptr[i], row_ptr[i + 1]):
+                if col[j] == i and val[j] != 0.0:
+                    d[i] = val[j]
+        e = np.asarray(out, dtype=np.float64) - (np.asarray(xt) - 2.0 * np.asarray(xm1) + np.asarray(xm2)) / s0
+
+        def prop(v):
+            return np.array([v[i] - omega * sum(val[j] * v[col[j]] for j in range(row_ptr[i], row_ptr[i + 1])) / d[i]
+                             for i in range(n)])
+
+        def prop_t(g):
+            return np.array([g[i] - omega * sum(val[j] * g[col[j]] / d[col[j]]
+                                                for j in range(row_ptr[i], row_ptr[i + 1])) for i in range(n)])
+
+        for _ in range(sweeps):
+            e = prop(e)
+        loss = float(np.mean(e * e))
+        g = e
+        for _ in range(sweeps):
+            g = prop(g) if kind == "no_transpose" else prop_t(g)
+        if kind == "scale":        # the 2/n factor dropped
+            return loss, g
+        if kind == "one_fewer":    # one transposed sweep short in the backward pass
+            g = e
+            for _ in range(max(sweeps - 1, 0)):
+                g = prop_t(g)
+        if kind == "sign_target":  # the target's extrapolation sign flipped
+            e2 = np.asarray(out, dtype=np.float64) - (np.asarray(xt) + 2.0 * np.asarray(xm1) - np.asarray(xm2)) / s0
+            return float(np.mean(e2 * e2)), 2.0 * e2 / n
+        return loss, 2.0 * g / n
+    return swept
+
+
+@pytest.mark.parametrize("kind", ["no_transpose", "scale", "one_fewer", "sign_target"])
+def test_warmstart_swept_loss_pins_catch_mutants(kind):
+    """Each planted mistake in the swept loss fails at least one of its pins."""
+    with pytest.raises(AssertionError):
+        _swept_pins(_swept_mutant(kind))
